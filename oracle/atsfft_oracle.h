@@ -1,0 +1,124 @@
+/*
+ * atsfft_oracle.h -- plain, slow, FP64 CPU oracle for ATSFFT (arXiv 1908.02461).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library calls, links or
+ * includes this code; only tests/, the smoke check and the benchmark's CPU
+ * baseline leg may load it.  It shares no code with the CUDA path: the two
+ * implement the same readings of the paper independently.
+ *
+ * Everything is computed in FP64 (complex double) from the complex64 input
+ * values widened to FP64.  Each function cites the passage of the paper it
+ * follows; where the paper is silent the reading used is stated in place.
+ *
+ * Conventions (Section II): omega = exp(-2*pi*i/n), unscaled forward DFT,
+ * indices mod n, n and B powers of two with B | n.
+ */
+#ifndef ATSFFT_ORACLE_H
+#define ATSFFT_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    ORC_OK = 0,
+    ORC_E_INVALID_ARG = 1,
+    ORC_E_NOMEM = 2,
+    ORC_E_NOT_CONVERGED = 4, /* tuning hit its trial cap; best result returned */
+    ORC_E_NOT_SPARSE = 5,    /* B reached its upper limit; result at that B returned */
+    ORC_E_CAPACITY = 6       /* output arrays too small; count holds the size needed */
+};
+
+/* Parameters of Algorithm 2 plus the readings of what the paper leaves open. */
+typedef struct {
+    double delta1, delta2;      /* Eq. (14): 0.02, 0.05 */
+    double eps1, eps2;          /* Eq. (13)/(14): 0.5, 1.0 (only these keep B a power of 2) */
+    int tune_max;               /* cap on tuning trials */
+    int loops_loc, loops_est;   /* location / estimation loops (7, 7) */
+    double filter_alpha;        /* transition width as a fraction of a half bucket (0.5) */
+    double filter_tol;          /* Gaussian tail tolerance (1e-6) */
+    double thr_rel, thr_med;    /* local-maximum threshold: max(thr_rel*maxE, thr_med*medianE) */
+    double tie_eta;             /* relative band inside which two energies count as tied */
+    int b_min_log2, b_max_log2; /* tuning range of B (per axis in 2D); 0 = default */
+} orc_params;
+
+#define ORC_MAX_TRIALS 64
+
+typedef struct {
+    int status;
+    int64_t B_star;             /* bucket count chosen by the tuning (per axis in 2D) */
+    int64_t k_star;             /* detected sparsity: local maxima at B_star */
+    int64_t count;              /* number of output coordinates (|I'|) */
+    int n_trials;
+    int64_t trial_B[ORC_MAX_TRIALS];
+    int64_t trial_k[ORC_MAX_TRIALS];
+    double trial_r[ORC_MAX_TRIALS];
+    double min_margin;          /* smallest relative margin of any outcome-deciding comparison */
+} orc_result;
+
+void orc_default_params(orc_params *p);
+
+/* SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): advances *state, returns next word. */
+uint64_t orc_splitmix64_next(uint64_t *state);
+
+/* Hash parameters (Def. 1) for hash `index` of `phase` (0 tune, 1 locate, 2 estimate).
+ * out = {sigma, tau} (ndim 1) or {sigma1, tau1, sigma2, tau2} (ndim 2); sigma odd. */
+void orc_hash_params(uint64_t seed, int phase, int index, int64_t n, int ndim, int64_t *out);
+
+/* Inverse of an odd sigma modulo n (n a power of two). */
+int64_t orc_inv_mod(int64_t sigma, int64_t n);
+
+/* Flat window (Section II-A-2, Eqs. (8),(9)) for length n and B buckets.
+ * Writes h (support half-width) and s (time-domain Gaussian std); if taps is
+ * non-NULL it receives the 2h+1 taps G_{-h..h} (index t+h). */
+int orc_filter_taps(int64_t n, int64_t B, double alpha, double tol,
+                    int64_t *h_out, double *s_out, double *taps);
+
+/* Frequency response Ghat'(o) = (1/n) sum_t G_t cos(2 pi o t / n) at the half-integer
+ * bucket offsets o = j - D/2 + 1/2 (D = n/B), written to resp[j], j in [0, D). */
+int orc_filter_response(int64_t n, int64_t B, double alpha, double tol, double *resp);
+
+/* Own radix-2 FFT, forward, unscaled, in place on len complex values (interleaved re,im). */
+int orc_fft(double *a, int64_t len);
+
+/* One hash (permute, filter, subsample, B-point DFT) of a 1D signal x (n complex,
+ * interleaved FP64) with the hash parameters of (seed, phase, index).
+ * Zhat receives B complex values. */
+int orc_hash_spectrum_1d(const double *x, int64_t n, int64_t B, uint64_t seed, int phase,
+                         int index, double alpha, double tol, double *Zhat);
+
+/* 2D analogue on an N x N row-major image; Zhat receives B*B complex (row-major). */
+int orc_hash_spectrum_2d(const double *x, int64_t N, int64_t B, uint64_t seed, int phase,
+                         int index, double alpha, double tol, double *Zhat);
+
+/* Local maxima of the bucket energies E (1D: ndim=1, nb=B; 2D: ndim=2, nb=B*B with
+ * side B).  Writes ascending bucket indices to list (capacity nb), returns the count.
+ * T_out and margin_out (may be NULL) receive the threshold and the smallest margin. */
+int64_t orc_local_maxima(const double *E, int64_t side, int ndim, double thr_rel,
+                         double thr_med, double eta, int64_t *list, double *T_out,
+                         double *margin_out);
+
+/* Componentwise median of L complex values (interleaved); out = {re, im}. */
+int orc_median_componentwise(const double *v, int L, double *out);
+
+/* Eq. (14) branch for counts k_prev -> k_cur: -1 halve, 0 keep, +1 double. */
+int orc_controller_branch(int64_t k_prev, int64_t k_cur, double delta1, double delta2);
+
+/* Whole ATSFFT (Algorithm 2 with Algorithm 1's location and estimation steps).
+ * x: n complex (interleaved FP64).  loc/val receive up to `capacity` outputs in
+ * ascending location order; res receives the tuning trace and status. */
+int orc_atsfft_1d(const double *x, int64_t n, int64_t k_hint, const orc_params *p,
+                  uint64_t seed, int64_t *loc, double *val, int64_t capacity,
+                  orc_result *res);
+
+/* 2D-SFFT/ATSFFT on an N x N image; loc holds linear indices i*N + j. */
+int orc_atsfft_2d(const double *x, int64_t N, int64_t k_hint, const orc_params *p,
+                  uint64_t seed, int64_t *loc, double *val, int64_t capacity,
+                  orc_result *res);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

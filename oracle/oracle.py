@@ -1,0 +1,226 @@
+"""ctypes wrapper around the C oracle (atsfft_oracle.c) -- TEST INFRASTRUCTURE ONLY.
+
+`build()` compiles the C file with the system gcc into oracle/_build/; every
+other function loads that library on first use (building it if missing).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "atsfft_oracle.c")
+_HDR = os.path.join(_HERE, "atsfft_oracle.h")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MAX_TRIALS = 64
+
+
+class OracleParams(C.Structure):
+    _fields_ = [
+        ("delta1", C.c_double), ("delta2", C.c_double),
+        ("eps1", C.c_double), ("eps2", C.c_double),
+        ("tune_max", C.c_int), ("loops_loc", C.c_int), ("loops_est", C.c_int),
+        ("filter_alpha", C.c_double), ("filter_tol", C.c_double),
+        ("thr_rel", C.c_double), ("thr_med", C.c_double), ("tie_eta", C.c_double),
+        ("b_min_log2", C.c_int), ("b_max_log2", C.c_int),
+    ]
+
+
+class _CResult(C.Structure):
+    _fields_ = [
+        ("status", C.c_int),
+        ("B_star", C.c_int64), ("k_star", C.c_int64), ("count", C.c_int64),
+        ("n_trials", C.c_int),
+        ("trial_B", C.c_int64 * MAX_TRIALS), ("trial_k", C.c_int64 * MAX_TRIALS),
+        ("trial_r", C.c_double * MAX_TRIALS),
+        ("min_margin", C.c_double),
+    ]
+
+
+@dataclass
+class OracleResult:
+    status: int
+    B_star: int
+    k_star: int
+    count: int
+    trials: list            # [(B, k, r), ...]
+    min_margin: float
+    loc: np.ndarray         # int64, ascending
+    val: np.ndarray         # complex128
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, IEEE semantics, no -march flags)."""
+    with _lock:
+        newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+            os.makedirs(_OUT_DIR, exist_ok=True)
+            tmp = _LIB + f".{os.getpid()}.tmp"
+            subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
+                           check=True)
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        i64, i32, dbl, u64 = C.c_int64, C.c_int, C.c_double, C.c_uint64
+        P = C.POINTER
+        L.orc_default_params.argtypes = [P(OracleParams)]
+        L.orc_splitmix64_next.argtypes = [P(u64)]
+        L.orc_splitmix64_next.restype = u64
+        L.orc_hash_params.argtypes = [u64, i32, i32, i64, i32, P(i64)]
+        L.orc_inv_mod.argtypes = [i64, i64]
+        L.orc_inv_mod.restype = i64
+        L.orc_filter_taps.argtypes = [i64, i64, dbl, dbl, P(i64), P(dbl), C.c_void_p]
+        L.orc_filter_response.argtypes = [i64, i64, dbl, dbl, C.c_void_p]
+        L.orc_fft.argtypes = [C.c_void_p, i64]
+        L.orc_hash_spectrum_1d.argtypes = [C.c_void_p, i64, i64, u64, i32, i32, dbl, dbl, C.c_void_p]
+        L.orc_hash_spectrum_2d.argtypes = [C.c_void_p, i64, i64, u64, i32, i32, dbl, dbl, C.c_void_p]
+        L.orc_local_maxima.argtypes = [C.c_void_p, i64, i32, dbl, dbl, dbl, C.c_void_p,
+                                       P(dbl), P(dbl)]
+        L.orc_local_maxima.restype = i64
+        L.orc_controller_branch.argtypes = [i64, i64, dbl, dbl]
+        L.orc_median_componentwise.argtypes = [C.c_void_p, i32, C.c_void_p]
+        L.orc_atsfft_1d.argtypes = [C.c_void_p, i64, i64, P(OracleParams), u64, C.c_void_p,
+                                    C.c_void_p, i64, P(_CResult)]
+        L.orc_atsfft_2d.argtypes = L.orc_atsfft_1d.argtypes
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def default_params(**overrides) -> OracleParams:
+    p = OracleParams()
+    lib().orc_default_params(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def splitmix64_stream(state: int, count: int) -> list:
+    s = C.c_uint64(state)
+    return [lib().orc_splitmix64_next(C.byref(s)) for _ in range(count)]
+
+
+def hash_params(seed, phase, index, n, ndim=1):
+    out = (C.c_int64 * 4)()
+    lib().orc_hash_params(seed, phase, index, n, ndim, out)
+    return list(out)[: 2 * ndim]
+
+
+def inv_mod(sigma, n):
+    return lib().orc_inv_mod(sigma, n)
+
+
+def filter_taps(n, B, alpha=0.5, tol=1e-6):
+    h, s = C.c_int64(), C.c_double()
+    st = lib().orc_filter_taps(n, B, alpha, tol, C.byref(h), C.byref(s), None)
+    if st:
+        raise ValueError(f"orc_filter_taps status {st}")
+    taps = np.zeros(2 * h.value + 1)
+    lib().orc_filter_taps(n, B, alpha, tol, C.byref(h), C.byref(s), _ptr(taps))
+    return h.value, s.value, taps
+
+
+def filter_response(n, B, alpha=0.5, tol=1e-6):
+    resp = np.zeros(n // B)
+    st = lib().orc_filter_response(n, B, alpha, tol, _ptr(resp))
+    if st:
+        raise ValueError(f"orc_filter_response status {st}")
+    return resp
+
+
+def fft(a):
+    buf = np.ascontiguousarray(a, dtype=np.complex128).copy()
+    st = lib().orc_fft(_ptr(buf), len(buf))
+    if st:
+        raise ValueError(f"orc_fft status {st}")
+    return buf
+
+
+def _as_c128(x):
+    return np.ascontiguousarray(np.asarray(x).astype(np.complex128))
+
+
+def hash_spectrum_1d(x, B, seed, phase, index, alpha=0.5, tol=1e-6):
+    xx = _as_c128(x)
+    out = np.zeros(B, dtype=np.complex128)
+    st = lib().orc_hash_spectrum_1d(_ptr(xx), len(xx), B, seed, phase, index, alpha, tol, _ptr(out))
+    if st:
+        raise ValueError(f"orc_hash_spectrum_1d status {st}")
+    return out
+
+
+def hash_spectrum_2d(x, B, seed, phase, index, alpha=0.5, tol=1e-6):
+    xx = _as_c128(x)
+    N = xx.shape[0]
+    out = np.zeros((B, B), dtype=np.complex128)
+    st = lib().orc_hash_spectrum_2d(_ptr(xx), N, B, seed, phase, index, alpha, tol, _ptr(out))
+    if st:
+        raise ValueError(f"orc_hash_spectrum_2d status {st}")
+    return out
+
+
+def local_maxima(E, ndim=1, thr_rel=1e-3, thr_med=20.0, eta=1e-2):
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    side = E.shape[0]
+    lst = np.zeros(E.size, dtype=np.int64)
+    T, m = C.c_double(), C.c_double()
+    cnt = lib().orc_local_maxima(_ptr(E), side, ndim, thr_rel, thr_med, eta, _ptr(lst),
+                                 C.byref(T), C.byref(m))
+    return lst[:cnt].copy(), T.value, m.value
+
+
+def median_componentwise(v):
+    v = np.ascontiguousarray(v, dtype=np.complex128)
+    out = np.zeros(2)
+    st = lib().orc_median_componentwise(_ptr(v), len(v), _ptr(out))
+    if st:
+        raise ValueError(f"orc_median_componentwise status {st}")
+    return complex(out[0], out[1])
+
+
+def controller_branch(k_prev, k_cur, delta1=0.02, delta2=0.05):
+    return lib().orc_controller_branch(k_prev, k_cur, delta1, delta2)
+
+
+def _run(fn, x, side, k_hint, params, seed, capacity):
+    xx = _as_c128(x)
+    if params is None:
+        params = default_params()
+    if capacity is None:
+        capacity = 1 << 20
+    loc = np.zeros(max(capacity, 1), dtype=np.int64)
+    val = np.zeros(max(capacity, 1), dtype=np.complex128)
+    r = _CResult()
+    fn(_ptr(xx), side, k_hint, C.byref(params), seed, _ptr(loc), _ptr(val), capacity, C.byref(r))
+    cnt = min(r.count, capacity)
+    trials = [(r.trial_B[i], r.trial_k[i], r.trial_r[i]) for i in range(r.n_trials)]
+    return OracleResult(r.status, r.B_star, r.k_star, r.count, trials, r.min_margin,
+                        loc[:cnt].copy(), val[:cnt].copy())
+
+
+def atsfft_1d(x, k_hint=0, params=None, seed=0, capacity=None) -> OracleResult:
+    x = np.asarray(x)
+    return _run(lib().orc_atsfft_1d, x, x.shape[0], k_hint, params, seed, capacity)
+
+
+def atsfft_2d(x, k_hint=0, params=None, seed=0, capacity=None) -> OracleResult:
+    x = np.asarray(x)
+    return _run(lib().orc_atsfft_2d, x, x.shape[0], k_hint, params, seed, capacity)

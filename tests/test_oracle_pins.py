@@ -1,0 +1,427 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test checks the oracle against what the paper or the mathematics fixes:
+published test vectors, the paper's worked example (Fig. 5 text), library
+routines (numpy's FFT), closed forms of the window design, Lemmas 1-2 and the
+convolution theorem, brute-force DFTs on tiny inputs, and the exactness of
+Eq. (11) on isolated coefficients.  CPU only.
+"""
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.special import erf
+
+import oracle as O
+from synth import sparse_signal_1d, sparse_signal_2d
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+# --------------------------------------------------------------------------
+# Random numbers and modular arithmetic (Def. 1)
+# --------------------------------------------------------------------------
+
+def test_splitmix64_published_vectors():
+    for v in _gold("splitmix64.json")["vectors"]:
+        got = O.splitmix64_stream(v["seed"], len(v["outputs"]))
+        assert got == [int(s) for s in v["outputs"]]
+
+
+@pytest.mark.parametrize("n", [2 ** 8, 2 ** 14, 2 ** 22, 2 ** 31])
+def test_inverse_mod_is_inverse(n):
+    rng = np.random.default_rng(1)
+    for s in rng.integers(0, n, size=200):
+        s = int(s) | 1
+        inv = O.inv_mod(s, n)
+        assert 0 <= inv < n and (s * inv) % n == 1
+
+
+def test_hash_params_odd_sigma_and_range():
+    seen = set()
+    for phase in range(3):
+        for index in range(20):
+            s1, t1, s2, t2 = O.hash_params(99, phase, index, 4096, ndim=2)
+            for v in (s1, t1, s2, t2):
+                assert 0 <= v < 4096
+            assert s1 % 2 == 1 and s2 % 2 == 1
+            seen.add((s1, t1))
+    assert len(seen) == 60  # every (phase, index) draws its own permutation
+
+
+# --------------------------------------------------------------------------
+# DFT (the paper's unscaled convention, Eq. (1))
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 64, 1024, 4096])
+def test_fft_matches_numpy(n):
+    rng = np.random.default_rng(n)
+    a = rng.normal(size=n) + 1j * rng.normal(size=n)
+    assert np.allclose(O.fft(a), np.fft.fft(a), rtol=0, atol=1e-11 * max(1, np.sqrt(n)))
+
+
+def test_fft_rejects_non_power_of_two():
+    with pytest.raises(ValueError):
+        O.fft(np.zeros(12))
+
+
+# --------------------------------------------------------------------------
+# Flat window (Section II-A-2): box car of one bucket width convolved with a Gaussian
+# --------------------------------------------------------------------------
+
+def _erf_profile(o, D, sf):
+    """Continuous box of width D (edges +-D/2) convolved with a unit-area Gaussian of
+    standard deviation sf: the closed form the window design approximates."""
+    z = math.sqrt(2.0) * sf
+    return 0.5 * (erf((D / 2 - o) / z) + erf((D / 2 + o) / z))
+
+
+@pytest.mark.parametrize("n,B", [(2 ** 12, 64), (2 ** 14, 256), (2 ** 16, 512), (2 ** 14, 1024)])
+def test_window_response_matches_box_conv_gaussian(n, B):
+    h, s, taps = O.filter_taps(n, B)
+    assert taps.shape == (2 * h + 1,)
+    assert np.allclose(taps, taps[::-1])                 # real, symmetric
+    assert abs(taps.sum() - n) < 1e-9 * n                # Ghat'(0) = 1 normalisation
+    D = n // B
+    sf = n / (2 * math.pi * s)                          # frequency-domain std of the Gaussian
+    resp = O.filter_response(n, B)
+    offs = np.arange(D) - D / 2 + 0.5
+    ideal = np.array([_erf_profile(o, D, sf) for o in offs])
+    assert np.max(np.abs(resp - ideal)) < 2e-5
+    # symmetric in the offset and exactly one half at the bucket edge in the ideal
+    assert np.allclose(resp, resp[::-1], atol=1e-12)
+    assert resp.min() > 0.45 and resp.max() <= 1 + 1e-6
+
+
+@pytest.mark.parametrize("n,B", [(2 ** 12, 64), (2 ** 13, 512)])
+def test_window_response_equals_dft_of_taps(n, B):
+    """Ghat' at the half-integer offsets o equals the (2n)-point DFT of the taps at the
+    odd frequency 2o (numpy's FFT as the independent route)."""
+    h, s, taps = O.filter_taps(n, B)
+    buf = np.zeros(2 * n)
+    for t in range(-h, h + 1):
+        buf[t % (2 * n)] += taps[t + h]
+    spec = np.fft.fft(buf).real / n
+    D = n // B
+    resp = O.filter_response(n, B)
+    for j in range(D):
+        o2 = 2 * j - D + 1
+        assert abs(resp[j] - spec[o2 % (2 * n)]) < 1e-12
+
+
+def test_window_stopband():
+    n, B = 2 ** 14, 128
+    h, s, taps = O.filter_taps(n, B)
+    D = n // B
+    buf = np.zeros(n)
+    for t in range(-h, h + 1):
+        buf[t % n] += taps[t + h]
+    spec = np.abs(np.fft.fft(buf)) / n
+    f = np.minimum(np.arange(n), n - np.arange(n))
+    # beyond (1 + alpha) D / 2 from the centre the gain is at the tolerance level
+    assert spec[f >= (1 + 0.5) * D / 2 + 1].max() < 1e-5
+    # inside (1 - alpha) D / 2 it is flat
+    assert np.all(np.abs(spec[f <= (1 - 0.5) * D / 2 - 1] - 1) < 1e-5)
+
+
+# --------------------------------------------------------------------------
+# Hash function (Lemma 1, Lemma 2, convolution theorem): the bucket spectrum
+# --------------------------------------------------------------------------
+
+def _response_at(taps, h, n, phi):
+    t = np.arange(-h, h + 1)
+    return float(np.sum(taps * np.cos(2 * np.pi * phi * t / n))) / n
+
+
+@pytest.mark.parametrize("n,B,seed", [(256, 16, 0), (512, 32, 1), (1024, 64, 2)])
+def test_hash_spectrum_brute_force(n, B, seed):
+    """Zhat_c = sum_i xhat_i omega^{-tau i} Ghat'(c D - 1/2 - sigma i) for every bucket c,
+    with xhat from numpy's FFT: Lemma 1 moves xhat_i to sigma i with phase omega^{-tau i},
+    the window multiplies in time (convolution in frequency) and Lemma 2 samples every
+    D-th frequency of the half-bin-shifted filtered spectrum."""
+    rng = np.random.default_rng(seed)
+    x = (rng.normal(size=n) + 1j * rng.normal(size=n)).astype(np.complex64).astype(np.complex128)
+    xh = np.fft.fft(x)
+    h, s, taps = O.filter_taps(n, B)
+    D = n // B
+    for phase, index in [(0, 3), (1, 0), (2, 5)]:
+        sigma, tau = O.hash_params(seed, phase, index, n)
+        Z = O.hash_spectrum_1d(x, B, seed, phase, index)
+        i = np.arange(n)
+        p = (sigma * i) % n
+        ph = np.exp(2j * np.pi * ((tau * i) % n) / n)      # omega^{-tau i}
+        expect = np.zeros(B, dtype=complex)
+        for c in range(B):
+            d = (c * D - 0.5 - p) % n
+            d = np.where(d > n / 2, d - n, d)
+            g = np.array([_response_at(taps, h, n, dd) for dd in d])
+            expect[c] = np.sum(xh * ph * g)
+        assert np.max(np.abs(Z - expect)) < 1e-9 * np.max(np.abs(expect))
+
+
+def test_hash_spectrum_2d_brute_force():
+    N, B, seed = 32, 8, 4
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
+    xh = np.fft.fft2(x)
+    h, s, taps = O.filter_taps(N, B)
+    D = N // B
+    s1, t1, s2, t2 = O.hash_params(seed, 1, 2, N, ndim=2)
+    Z = O.hash_spectrum_2d(x, B, seed, 1, 2)
+    i = np.arange(N)
+    g1 = {}
+    expect = np.zeros((B, B), dtype=complex)
+    for c1 in range(B):
+        for c2 in range(B):
+            acc = 0
+            for a in range(N):
+                d1 = (c1 * D - 0.5 - s1 * a) % N
+                d1 = d1 - N if d1 > N / 2 else d1
+                if (c1, a) not in g1:
+                    g1[(c1, a)] = _response_at(taps, h, N, d1)
+                d2 = (c2 * D - 0.5 - s2 * i) % N
+                d2 = np.where(d2 > N / 2, d2 - N, d2)
+                gg = np.array([_response_at(taps, h, N, dd) for dd in d2])
+                ph = np.exp(2j * np.pi * ((t1 * a + t2 * i) % N) / N)
+                acc += np.sum(xh[a, :] * ph * g1[(c1, a)] * gg)
+            expect[c1, c2] = acc
+    assert np.max(np.abs(Z - expect)) < 1e-9 * np.max(np.abs(expect))
+
+
+def test_lemma1_and_lemma2_conventions():
+    """The identities the oracle's hash relies on, checked with numpy alone:
+    Lemma 1 (permutation) and Lemma 2 (aliasing), in the paper's DFT convention."""
+    n, B = 256, 16
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=n) + 1j * rng.normal(size=n)
+    sigma, tau = 77, 13
+    Px = x[(sigma * np.arange(n) + tau) % n]
+    lhs = np.fft.fft(Px)[(sigma * np.arange(n)) % n]
+    rhs = np.fft.fft(x) * np.exp(2j * np.pi * tau * np.arange(n) / n)
+    assert np.allclose(lhs, rhs, atol=1e-9)
+    y = x.reshape(n // B, B).sum(axis=0)
+    assert np.allclose(np.fft.fft(y), np.fft.fft(x)[:: n // B], atol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# Estimator (Eq. (11)) exactness on isolated coefficients
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,B", [(1024, 32), (4096, 256)])
+def test_isolated_coefficient_estimate_exact(n, B):
+    D = n // B
+    resp = O.filter_response(n, B)
+    for f, val in [(0, 1.0), (5, 0.3 - 0.4j), (n // 2, -1j), (n - 1, 2.0 + 0.5j), (777 % n, 1j)]:
+        xh = np.zeros(n, complex)
+        xh[f] = val
+        x = np.fft.ifft(xh)
+        for l in range(4):
+            sigma, tau = O.hash_params(3, 2, l, n)
+            Z = O.hash_spectrum_1d(x, B, 3, 2, l)
+            p = (sigma * f) % n
+            q = (2 * p + 1 + D) // (2 * D)
+            hb, o2 = q % B, 2 * p + 1 - 2 * q * D
+            est = Z[hb] * np.exp(-2j * np.pi * ((tau * f) % n) / n) / resp[(o2 + D - 1) // 2]
+            assert abs(est - val) < 1e-9
+            others = np.delete(np.abs(Z), hb)
+            assert others.max() <= 0.5 * abs(val) + 1e-9   # only neighbours see leakage
+
+
+# --------------------------------------------------------------------------
+# Local maxima (Section III-A) and the controller (Eqs. (12)-(14))
+# --------------------------------------------------------------------------
+
+def test_fig5_worked_example():
+    g = _gold("fig5_local_maxima.json")
+    N, B, k = g["N"], g["B"], g["k"]
+    hits = 0
+    for seed in range(4):
+        sig = sparse_signal_2d(N, k, seed)
+        Z = O.hash_spectrum_2d(sig.x, B, seed, 0, 0)
+        lm, T, _ = O.local_maxima(np.abs(Z) ** 2, ndim=2)
+        hits += len(lm) == g["local_maxima"]
+    assert hits == 4
+
+
+def test_local_maxima_synthetic_1d():
+    B = 64
+    E = np.full(B, 1e-6)
+    spikes = [3, 10, 40, 63]
+    for c in spikes:
+        E[c] = 1.0
+    E[11] = 0.3                          # shoulder next to a spike: not a maximum
+    E[0] = 0.9                           # cyclic neighbour of 63: 63 dominates it
+    lm, T, _ = O.local_maxima(E)
+    assert lm.tolist() == [3, 10, 40, 63]
+    # exact tie between neighbours: the later bucket (cyclically) wins, one maximum
+    E2 = np.full(B, 1e-6)
+    E2[20] = E2[21] = 1.0
+    E2[63] = E2[0] = 0.5
+    lm2, _, _ = O.local_maxima(E2)
+    assert lm2.tolist() == [0, 21]
+    # below the threshold max(thr_rel * max, thr_med * median) nothing counts
+    E3 = np.full(B, 1.0)
+    E3[5] = 15.0
+    lm3, T3, _ = O.local_maxima(E3)
+    assert T3 == pytest.approx(20.0) and lm3.tolist() == []
+
+
+def test_local_maxima_synthetic_2d():
+    B = 16
+    E = np.full((B, B), 1e-6)
+    E[2, 3] = 1.0
+    E[2, 4] = 0.8                        # 8-neighbour, smaller
+    E[9, 9] = 0.5
+    E[10, 10] = 0.5                      # diagonal exact tie: (10,10) is later, wins
+    E[15, 0] = 0.7
+    E[0, 15] = 0.6                       # diagonal across both wraps: (15,0) and (0,15) are neighbours
+    lm, _, _ = O.local_maxima(E, ndim=2)
+    assert sorted(lm.tolist()) == sorted([2 * B + 3, 10 * B + 10, 15 * B + 0])
+
+
+def test_controller_branches_eq14():
+    g = _gold("eq14_controller.json")
+    for kp, kc, br in g["cases_k_prev_k_cur_branch"]:
+        assert O.controller_branch(kp, kc, g["delta1"], g["delta2"]) == br, (kp, kc)
+    assert O.controller_branch(0, 5) == 1 and O.controller_branch(7, 0) == 1
+
+
+def test_median_componentwise_matches_numpy():
+    rng = np.random.default_rng(5)
+    for L in (1, 3, 5, 7, 9):
+        v = rng.normal(size=L) + 1j * rng.normal(size=L)
+        m = O.median_componentwise(v)
+        assert m == complex(np.median(v.real), np.median(v.imag))
+
+
+# --------------------------------------------------------------------------
+# Whole transform against a brute-force DFT on tiny inputs
+# --------------------------------------------------------------------------
+
+CASES_1D = [(1024, 1, 0), (1024, 2, 0), (1024, 4, 2), (4096, 2, 2), (4096, 4, 1), (4096, 6, 0),
+            (4096, 6, 3), (16384, 16, 0), (16384, 16, 1)]
+
+
+@pytest.mark.parametrize("n,k,seed", CASES_1D)
+def test_atsfft_1d_brute_force(n, k, seed):
+    sig = sparse_signal_1d(n, k, seed)
+    xh = np.fft.fft(sig.x.astype(np.complex128))          # exact DFT of the given input
+    r = O.atsfft_1d(sig.x, seed=seed)
+    assert r.status == 0
+    assert set(sig.support.tolist()) <= set(r.loc.tolist())
+    assert np.all(np.diff(r.loc) > 0)
+    got = dict(zip(r.loc.tolist(), r.val.tolist()))
+    for i in range(n):
+        if i in got:
+            assert abs(got[i] - xh[i]) < 1e-5
+    assert r.k_star <= k
+
+
+CASES_2D = [(64, 1, 0), (128, 3, 1), (128, 6, 2), (256, 10, 0)]
+
+
+@pytest.mark.parametrize("N,k,seed", CASES_2D)
+def test_atsfft_2d_brute_force(N, k, seed):
+    sig = sparse_signal_2d(N, k, seed)
+    xh = np.fft.fft2(sig.x.astype(np.complex128)).ravel()
+    r = O.atsfft_2d(sig.x, seed=seed)
+    assert r.status in (0, 5)
+    assert r.loc.tolist() == sig.support.tolist()
+    assert np.max(np.abs(r.val - xh[r.loc])) < 1e-5
+
+
+def test_2d_transposed_support_is_distinguished():
+    """A support that is not symmetric under transposition must come back untransposed."""
+    N = 128
+    xh = np.zeros((N, N), complex)
+    xh[3, 70] = 1.0
+    xh[100, 5] = 0.5j
+    x = np.fft.ifft2(xh).astype(np.complex64)
+    r = O.atsfft_2d(x, seed=1)
+    got = dict(zip(r.loc.tolist(), r.val.tolist()))
+    assert abs(got[3 * N + 70] - 1.0) < 1e-5 and abs(got[100 * N + 5] - 0.5j) < 1e-5
+    assert 70 * N + 3 not in got and 5 * N + 100 not in got
+    extras = [abs(v) for i, v in got.items() if i not in (3 * N + 70, 100 * N + 5)]
+    assert max(extras, default=0.0) < 1e-5
+
+
+# --------------------------------------------------------------------------
+# Degenerate cases and limits
+# --------------------------------------------------------------------------
+
+def test_zero_signal_gives_empty_output():
+    r = O.atsfft_1d(np.zeros(4096, np.complex64))
+    assert r.status == 0 and r.count == 0 and r.k_star == 0
+    r2 = O.atsfft_2d(np.zeros((64, 64), np.complex64))
+    assert r2.status == 0 and r2.count == 0
+
+
+def test_capacity_reports_needed_count():
+    sig = sparse_signal_1d(4096, 4, 1)
+    r = O.atsfft_1d(sig.x, seed=1, capacity=2)
+    assert r.status == 6 and r.count >= 4 and len(r.loc) == 2
+
+
+def test_trial_cap_not_converged():
+    sig = sparse_signal_1d(1 << 16, 50, 3, 40)
+    r = O.atsfft_1d(sig.x, seed=3, params=O.default_params(tune_max=2))
+    assert r.status == 4 and len(r.trials) == 2
+
+
+def test_pure_noise_is_not_sparse():
+    rng = np.random.default_rng(0)
+    x = (rng.normal(size=1 << 14) + 1j * rng.normal(size=1 << 14)).astype(np.complex64)
+    r = O.atsfft_1d(x, seed=0)
+    assert r.status == 5 and r.B_star == (1 << 14) // 16
+
+
+def test_invalid_arguments():
+    r = O.atsfft_1d(np.zeros(1000, np.complex64))
+    assert r.status == 1
+    r = O.atsfft_1d(np.zeros(4096, np.complex64), params=O.default_params(eps1=0.3))
+    assert r.status == 1
+    r = O.atsfft_1d(np.zeros(4096, np.complex64), params=O.default_params(delta1=0.06))
+    assert r.status == 1
+
+
+def test_k_hint_starts_higher():
+    sig = sparse_signal_1d(1 << 16, 50, 3, 40)
+    r = O.atsfft_1d(sig.x, seed=3, k_hint=50)
+    assert r.trials[0][0] == 128
+
+
+def test_vote_rule_single_and_three_loops():
+    """Section II-B keeps coordinates found in at least half of the location loops.
+    With one loop that is exactly the union of the preimages of the selected buckets
+    (D = n/B coordinates each, disjoint); with three loops a coordinate needs two votes.
+    Seed 3 is a case where no location hash has more local maxima than k*, so every
+    local maximum is selected."""
+    n, seed = 1 << 14, 3
+    sig = sparse_signal_1d(n, 16, seed)
+    r1 = O.atsfft_1d(sig.x, seed=seed, params=O.default_params(loops_loc=1))
+    B, D = r1.B_star, n // r1.B_star
+    Z = O.hash_spectrum_1d(sig.x, B, seed, 1, 0)
+    lm, _, _ = O.local_maxima(np.abs(Z) ** 2)
+    assert r1.count == min(len(lm), r1.k_star) * D
+    sigma, _ = O.hash_params(seed, 1, 0, n)
+    p = (sigma * r1.loc) % n
+    assert set(((2 * p + 1 + D) // (2 * D)) % B) <= set(lm.tolist())
+    r3 = O.atsfft_1d(sig.x, seed=seed, params=O.default_params(loops_loc=3))
+    assert r3.B_star == B
+    votes = np.zeros(n, int)
+    for l in range(3):
+        Z = O.hash_spectrum_1d(sig.x, B, seed, 1, l)
+        lm, _, _ = O.local_maxima(np.abs(Z) ** 2)
+        assert len(lm) <= r3.k_star
+        sigma, _ = O.hash_params(seed, 1, l, n)
+        q = ((2 * ((sigma * np.arange(n)) % n) + 1 + D) // (2 * D)) % B
+        votes += np.isin(q, lm)
+    assert r3.loc.tolist() == np.flatnonzero(votes >= 2).tolist()
