@@ -1,0 +1,125 @@
+/*
+ * atsfft.h -- C ABI of the GB300 (sm_103a) ATSFFT library.
+ *
+ * ATSFFT (Shi, Yang, Zhang, You, arXiv 1908.02461) is a sparse FFT that also detects
+ * the sparsity k.  Each transform runs, entirely on the GPU:
+ *   tuning   (Algorithm 2, Eqs. (12)-(14)): hashes at growing bucket counts B, each
+ *            counting the local maxima of the bucket energies, until the count is
+ *            stable; the final B is B*, its count k*;
+ *   location (Algorithm 1, Section II-B): L_loc hashes at B*, the k* largest local
+ *            maxima of each vote for the coordinates that hash to them; coordinates
+ *            with votes >= ceil(L_loc/2) are kept;
+ *   estimation (Eq. (11), Section II-B): L_est hashes at B*, per kept coordinate the
+ *            componentwise median of Zhat_h(i) * omega^(tau i) / Ghat'(o(i)).
+ * A hash is the random spectrum permutation of Def. 1, the flat window of Section
+ * II-A-2 (box car of one bucket width convolved with a Gaussian, Eqs. (8),(9)),
+ * subsampling into B buckets (Lemma 2) and a B-point DFT.
+ *
+ * Conventions (Section II): the DFT is unscaled, xhat[f] = sum_t x[t] exp(-2 pi i f t/n);
+ * sizes are powers of two; 2D images are N x N, row-major, and 2D locations are linear
+ * indices i*N + j (i = row frequency, j = column frequency).
+ *
+ * Memory: every `d_` pointer is device memory owned by the caller; the plan owns its
+ * tables and scratch.  Calls that take a stream only enqueue work on it and never
+ * synchronise, except where stated.  A plan may be used by one stream at a time
+ * (one scratch set).  Errors are returned as status codes; nothing aborts or throws.
+ */
+#ifndef ATSFFT_H
+#define ATSFFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct atsfft_plan_s *atsfft_plan_t;
+
+typedef enum {
+    ATSFFT_OK = 0,
+    ATSFFT_E_INVALID_ARG = 1,   /* bad size, pointer or parameter                         */
+    ATSFFT_E_NOMEM = 2,         /* device or host allocation failed                       */
+    ATSFFT_E_CUDA = 3,          /* a CUDA call or launch failed                           */
+    ATSFFT_E_NOT_CONVERGED = 4, /* tuning used all its trials; result at the last B       */
+    ATSFFT_E_NOT_SPARSE = 5,    /* tuning wanted B beyond its maximum; result at the max  */
+    ATSFFT_E_CAPACITY = 6       /* more outputs than `capacity`; *d_count = number needed */
+} atsfft_status;
+
+/* Parameters of Algorithm 2 and of the readings of points the paper leaves open. */
+typedef struct {
+    double delta1, delta2;      /* Eq. (14) ratio bands, paper: 0.02, 0.05                */
+    double eps1, eps2;          /* Eq. (13)/(14) factors, paper: 0.5, 1.0 (only values
+                                   accepted: they keep B a power of two)                 */
+    int tune_max;               /* cap on tuning trials (default 32)                     */
+    int loops_loc, loops_est;   /* location / estimation hashes (default 7, 7)           */
+    double filter_alpha;        /* window transition width, fraction of half a bucket    */
+    double filter_tol;          /* window Gaussian tail tolerance (default 1e-6)         */
+    double thr_rel, thr_med;    /* local-maximum threshold max(thr_rel*maxE,
+                                   thr_med*medianE) (default 1e-3, 20)                   */
+    double tie_eta;             /* relative band inside which energies tie (1e-2)        */
+    int b_min_log2, b_max_log2; /* tuning range of log2 B (per axis in 2D); 0 = default:
+                                   1D [4, log2 n - 4], 2D [3, log2 N - 2]                */
+} atsfft_params;
+
+/* Fills *p with the defaults listed above. */
+void atsfft_default_params(atsfft_params *p);
+
+/* Creates a plan for 1D signals of length shape[0] (ndim = 1; a power of two in
+ * [2^8, 2^30]) or N x N images (ndim = 2, shape = {N, N}, N a power of two in
+ * [2^5, 2^14]).  k_hint > 0 starts the tuning at the smallest power-of-two B >= 2 k_hint
+ * (2D: B^2 >= 2 k_hint); 0 means k is unknown.  p = NULL takes the defaults.  seed
+ * keys the SplitMix64 streams of the hash permutations (Def. 1).  Builds the window
+ * tables (Section II-A-2) for every B of the tuning range on the current device and
+ * synchronises it.  On error *out is NULL. */
+atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t *shape, int64_t k_hint,
+                          const atsfft_params *p, uint64_t seed);
+
+/* One 1D transform of d_x (n complex64, interleaved re/im floats, device).
+ *   d_loc   int64[capacity]: kept coordinates (frequencies), ascending;
+ *   d_val   complex64[capacity]: their estimated DFT values (Eq. (11), median);
+ *   d_count int64: number of kept coordinates (may exceed capacity);
+ *   d_k     int64: detected sparsity k*;
+ *   d_status int32: atsfft_status of the transform (OK, NOT_CONVERGED, NOT_SPARSE,
+ *           CAPACITY).  All outputs are device memory, written by the GPU on `stream`
+ *           (a cudaStream_t; NULL = legacy default stream).  The return value only
+ *           reports argument and launch errors. */
+atsfft_status atsfft_exec(atsfft_plan_t plan, const void *d_x, int64_t *d_loc, void *d_val,
+                          int64_t capacity, int64_t *d_count, int64_t *d_k, int32_t *d_status,
+                          void *stream);
+
+/* One 2D transform of the N x N row-major complex64 image d_img; locations are
+ * linear indices i*N + j.  Other arguments as atsfft_exec. */
+atsfft_status atsfft_exec_2d(atsfft_plan_t plan, const void *d_img, int64_t *d_loc, void *d_val,
+                             int64_t capacity, int64_t *d_count, int64_t *d_k,
+                             int32_t *d_status, void *stream);
+
+/* Releases the plan's device and host memory (synchronises the device first). */
+atsfft_status atsfft_destroy(atsfft_plan_t plan);
+
+/* Static, NUL-terminated description of a status code. */
+const char *atsfft_status_string(atsfft_status s);
+
+/* ---- inspection (tests and diagnostics) ---------------------------------------- */
+
+/* One hash of the plan's signal shape at bucket count B (per axis in 2D), for
+ * (phase, index) = (0 tuning, log2 B), (1 location, l) or (2 estimation, l): writes the
+ * bucket spectrum Zhat (complex64; B values, or B*B row-major in 2D) to d_zhat on
+ * `stream`.  B must lie in the plan's tuning range. */
+atsfft_status atsfft_hash_spectrum(atsfft_plan_t plan, const void *d_x, int64_t B, int phase,
+                                   int index, void *d_zhat, void *stream);
+
+/* Copies the plan's window response Ghat'(o) at the half-integer bucket offsets
+ * o = j - D/2 + 1/2, j in [0, D), D = n/B (per axis in 2D), to the host array h_resp
+ * (double[D]).  Synchronous. */
+atsfft_status atsfft_window_response(atsfft_plan_t plan, int64_t B, double *h_resp);
+
+/* After an exec has completed on its stream: the tuning trajectory of that exec
+ * (B and local-maximum count of each trial, in order) into host arrays of length
+ * max_trials, and the number of trials.  Synchronises `stream`. */
+atsfft_status atsfft_last_trace(atsfft_plan_t plan, int64_t *h_B, int64_t *h_k, int max_trials,
+                                int *h_ntrials, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,134 @@
+"""GB300 (sm_103a) ATSFFT: sparse FFT with sparsity detection (arXiv 1908.02461).
+
+The compute path is the CUDA library behind include/atsfft.h; this package is its
+ctypes binding (`_lib`, same function names as the C ABI) plus `Plan`, a small
+convenience wrapper that allocates the output buffers with torch.  PyTorch only
+provides device memory and streams here.  There is no CPU fallback: using a plan
+without the built library or without a GPU raises.
+"""
+
+from __future__ import annotations
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    E_CAPACITY,
+    E_CUDA,
+    E_INVALID_ARG,
+    E_NOMEM,
+    E_NOT_CONVERGED,
+    E_NOT_SPARSE,
+    OK,
+    atsfft_default_params,
+    atsfft_destroy,
+    atsfft_exec,
+    atsfft_exec_2d,
+    atsfft_hash_spectrum,
+    atsfft_last_trace,
+    atsfft_params,
+    atsfft_plan,
+    atsfft_status_string,
+    atsfft_window_response,
+)
+from .build import build  # noqa: F401
+
+
+class ATSFFTError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {atsfft_status_string(status)} (status {status})")
+        self.status = status
+
+
+def params(**overrides) -> atsfft_params:
+    p = atsfft_default_params()
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+class Plan:
+    """A plan for 1D signals of length n (shape=(n,)) or N x N images (shape=(N, N))."""
+
+    def __init__(self, shape, k_hint: int = 0, params: atsfft_params | None = None, seed: int = 0):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("ATSFFT needs a CUDA GPU; there is no CPU path")
+        self.shape = tuple(int(s) for s in shape)
+        self.ndim = len(self.shape)
+        st, h = atsfft_plan(self.ndim, self.shape, k_hint, params, seed)
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_plan")
+        self.handle = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._scalars = torch.zeros(3, dtype=torch.int64, device=self.device)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            atsfft_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def exec_async(self, x, loc, val, count, k, status, stream=None):
+        """Enqueue one transform into caller-provided device buffers."""
+        import torch
+
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        fn = atsfft_exec if self.ndim == 1 else atsfft_exec_2d
+        st = fn(self.handle, x, loc, val, loc.numel(), count, k, status, s)
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_exec")
+
+    def __call__(self, x, capacity: int | None = None):
+        """Transform x (complex64 CUDA tensor); returns (loc, val, k_star, status) after sync."""
+        import torch
+
+        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous complex64 CUDA tensor")
+        if tuple(x.shape) != self.shape:
+            raise ValueError(f"x has shape {tuple(x.shape)}, plan expects {self.shape}")
+        cap = capacity if capacity is not None else 1 << 16
+        loc = torch.empty(cap, dtype=torch.int64, device=x.device)
+        val = torch.empty(cap, dtype=torch.complex64, device=x.device)
+        count = torch.zeros(1, dtype=torch.int64, device=x.device)
+        k = torch.zeros(1, dtype=torch.int64, device=x.device)
+        status = torch.zeros(1, dtype=torch.int32, device=x.device)
+        self.exec_async(x, loc, val, count, k, status)
+        n = int(count.item())
+        m = min(n, cap)
+        return loc[:m], val[:m], int(k.item()), int(status.item()), n
+
+    def hash_spectrum(self, x, B: int, phase: int, index: int):
+        import torch
+
+        out = torch.empty((B,) if self.ndim == 1 else (B, B), dtype=torch.complex64, device=x.device)
+        st = atsfft_hash_spectrum(self.handle, x, B, phase, index, out,
+                                  torch.cuda.current_stream().cuda_stream)
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_hash_spectrum")
+        return out
+
+    def window_response(self, B: int):
+        import numpy as np
+
+        D = self.shape[0] // B
+        out = np.zeros(D, dtype=np.float64)
+        st = atsfft_window_response(self.handle, B, out)
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_window_response")
+        return out
+
+    def last_trace(self):
+        import numpy as np
+        import torch
+
+        Bs = np.zeros(64, dtype=np.int64)
+        ks = np.zeros(64, dtype=np.int64)
+        st, nt = atsfft_last_trace(self.handle, Bs, ks, 64, torch.cuda.current_stream().cuda_stream)
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_last_trace")
+        return list(zip(Bs[:nt].tolist(), ks[:nt].tolist()))

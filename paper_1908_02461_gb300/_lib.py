@@ -1,0 +1,135 @@
+"""ctypes binding of the ATSFFT C ABI (include/atsfft.h).
+
+Argument marshalling only: every step of a transform runs in the CUDA library.  The
+functions keep the C names; device buffers are passed as torch CUDA tensors (their
+data pointers) or raw integers.  Loading fails loudly when the library is missing.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from .build import LIB_PATH
+
+OK = 0
+E_INVALID_ARG = 1
+E_NOMEM = 2
+E_CUDA = 3
+E_NOT_CONVERGED = 4
+E_NOT_SPARSE = 5
+E_CAPACITY = 6
+
+
+class atsfft_params(C.Structure):
+    _fields_ = [
+        ("delta1", C.c_double), ("delta2", C.c_double),
+        ("eps1", C.c_double), ("eps2", C.c_double),
+        ("tune_max", C.c_int), ("loops_loc", C.c_int), ("loops_est", C.c_int),
+        ("filter_alpha", C.c_double), ("filter_tol", C.c_double),
+        ("thr_rel", C.c_double), ("thr_med", C.c_double), ("tie_eta", C.c_double),
+        ("b_min_log2", C.c_int), ("b_max_log2", C.c_int),
+    ]
+
+
+EXPORTED = ["atsfft_default_params", "atsfft_plan", "atsfft_exec", "atsfft_exec_2d",
+            "atsfft_destroy", "atsfft_status_string", "atsfft_hash_spectrum",
+            "atsfft_window_response", "atsfft_last_trace"]
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libatsfft.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"ATSFFT CUDA library not built ({p}); run "
+                          "paper_1908_02461_gb300.build.build() first")
+    L = C.CDLL(p)
+    vp, i64, i32, u64, P = C.c_void_p, C.c_int64, C.c_int, C.c_uint64, C.POINTER
+    L.atsfft_default_params.argtypes = [P(atsfft_params)]
+    L.atsfft_default_params.restype = None
+    L.atsfft_plan.argtypes = [P(vp), i32, P(i64), i64, P(atsfft_params), u64]
+    L.atsfft_plan.restype = i32
+    L.atsfft_exec.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp]
+    L.atsfft_exec.restype = i32
+    L.atsfft_exec_2d.argtypes = L.atsfft_exec.argtypes
+    L.atsfft_exec_2d.restype = i32
+    L.atsfft_destroy.argtypes = [vp]
+    L.atsfft_destroy.restype = i32
+    L.atsfft_status_string.argtypes = [i32]
+    L.atsfft_status_string.restype = C.c_char_p
+    L.atsfft_hash_spectrum.argtypes = [vp, vp, i64, i32, i32, vp, vp]
+    L.atsfft_hash_spectrum.restype = i32
+    L.atsfft_window_response.argtypes = [vp, i64, vp]
+    L.atsfft_window_response.restype = i32
+    L.atsfft_last_trace.argtypes = [vp, vp, vp, i32, P(i32), vp]
+    L.atsfft_last_trace.restype = i32
+    if path is None:
+        _lib = L
+    return L
+
+
+def _ptr(t):
+    """Device (or host) address of a tensor / array / integer."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):
+        return t.ctypes.data
+    raise TypeError(f"cannot take the address of {type(t)}")
+
+
+def atsfft_default_params() -> atsfft_params:
+    p = atsfft_params()
+    load().atsfft_default_params(C.byref(p))
+    return p
+
+
+def atsfft_status_string(status: int) -> str:
+    return load().atsfft_status_string(status).decode()
+
+
+def atsfft_plan(ndim: int, shape, k_hint: int = 0, params: atsfft_params | None = None,
+                seed: int = 0):
+    """Returns (status, plan handle)."""
+    h = C.c_void_p()
+    sh = (C.c_int64 * 2)(*(list(shape) + [0] * (2 - len(shape))))
+    st = load().atsfft_plan(C.byref(h), ndim, sh, k_hint, C.byref(params) if params else None,
+                            seed & 0xFFFFFFFFFFFFFFFF)
+    return st, h.value
+
+
+def atsfft_exec(plan, d_x, d_loc, d_val, capacity, d_count, d_k, d_status, stream=None) -> int:
+    return load().atsfft_exec(plan, _ptr(d_x), _ptr(d_loc), _ptr(d_val), capacity, _ptr(d_count),
+                              _ptr(d_k), _ptr(d_status), _ptr(stream))
+
+
+def atsfft_exec_2d(plan, d_img, d_loc, d_val, capacity, d_count, d_k, d_status, stream=None) -> int:
+    return load().atsfft_exec_2d(plan, _ptr(d_img), _ptr(d_loc), _ptr(d_val), capacity,
+                                 _ptr(d_count), _ptr(d_k), _ptr(d_status), _ptr(stream))
+
+
+def atsfft_destroy(plan) -> int:
+    return load().atsfft_destroy(plan)
+
+
+def atsfft_hash_spectrum(plan, d_x, B, phase, index, d_zhat, stream=None) -> int:
+    return load().atsfft_hash_spectrum(plan, _ptr(d_x), B, phase, index, _ptr(d_zhat), _ptr(stream))
+
+
+def atsfft_window_response(plan, B, h_resp) -> int:
+    return load().atsfft_window_response(plan, B, _ptr(h_resp))
+
+
+def atsfft_last_trace(plan, h_B, h_k, max_trials, stream=None):
+    """Returns (status, number of trials)."""
+    nt = C.c_int()
+    st = load().atsfft_last_trace(plan, _ptr(h_B), _ptr(h_k), max_trials, C.byref(nt), _ptr(stream))
+    return st, nt.value

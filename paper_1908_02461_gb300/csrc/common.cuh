@@ -1,0 +1,184 @@
+// common.cuh -- internal definitions shared by the ATSFFT CUDA translation units.
+//
+// Data layout convention ("residue order").  For a hash (sigma, tau) at B buckets the
+// binning kernels store the bucket sums not at bucket index b but at the residue
+// r = (sigma b + tau) mod B of the samples that feed it (a = r mod B for every sample
+// a of bucket b).  The bucket FFT transforms that array as it is, giving P.  By the
+// permutation property (Lemma 1 applied to the B-point DFT) the bucket spectrum is
+//     Zhat[c] = P[sigma' c mod B] * exp(2 pi i c sigma' tau / B),  sigma' = sigma^{-1} mod B,
+// per axis in 2D.  Energies |Zhat[c]|^2 = |P[sigma' c]|^2 need no phase; the estimator
+// applies the phase together with omega^{tau i} in one FP64 angle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "atsfft.h"
+
+namespace atsfft {
+
+constexpr int kMaxLoops = 31;        // location / estimation hashes each
+constexpr int kMaxLogB = 26;         // log2 B range table size
+constexpr int kSmallFFT = 4096;      // largest FFT done in one CTA
+constexpr int kMaxTrialsTrace = 64;
+constexpr int kHistBins = 4096;      // radix-select histogram bins (12-bit digits)
+constexpr int kPersistCtas = 4;      // persistent CTAs per SM
+
+// Permutation of one hash (Def. 1), per axis.
+struct HashParam {
+    uint32_t sigma[2];   // odd, < n
+    uint32_t tau[2];     // < n
+    uint32_t sinv[2];    // sigma^{-1} mod n
+};
+
+// Window of one bucket count B (Section II-A-2): taps t in [-h, h],
+// G_t = A exp(-t^2/(2 s^2)) sin(pi t/B)/(pi t/n) applied with exp(i pi t/n).
+struct WindowParam {
+    int32_t h;
+    float k2;            // log2(e) / (2 s^2)
+    float log2c;         // log2(A n / pi): scale of the per-sample factor
+    float cA_D;          // A * D (the centre tap G_0)
+    double s;
+    double A;
+};
+
+// A set of equally shaped hashes processed together (the tuning hash of one B, or the
+// location + estimation hashes at B*).  Written by the host for tuning, by the
+// controller kernel for B*.
+struct Job {
+    int32_t logB;        // per axis
+    int32_t nh;          // hashes in this job
+    int32_t chunks;      // residue-stream row chunks (partials summed by the FFT)
+    int32_t stream;      // 1: residue-stream binning, 0: warp-per-bucket gather
+    int32_t active;      // 0: nothing to do (skipped by every kernel)
+    int32_t pad[3];
+};
+
+// One hash's spectrum for the energy / threshold / local-maximum kernels.
+struct StatJob {
+    const float2 *spec;    // P (residue-order FFT output), B or B^2 values
+    float *energy;         // |P|^2, same layout
+    const HashParam *hash;
+    int32_t logB;          // per axis
+    int32_t slot;          // HashStats slot
+    int32_t list;          // >= 0: append local maxima (bucket indices c) to that list
+    int32_t active;
+};
+
+// Per-hash statistics of the bucket energies (Section III-A local maxima).
+struct HashStats {
+    uint32_t max_bits;     // bits of max E (E >= 0: bit order = value order)
+    uint32_t above;        // #{E > X}, X just below thr_rel/thr_med * max
+    uint32_t need_median;  // 1 if the median can exceed X (then it is computed exactly)
+    uint32_t prefix;       // radix-select: digits fixed so far
+    uint32_t rank;         // radix-select: rank within the prefix class
+    uint32_t med_bits;
+    float T;               // threshold
+    uint32_t nmax;         // local maxima
+    uint32_t nsel;         // selected by the top-num cutoff
+    uint32_t pad[7];
+};
+
+// Device-resident state of one exec.
+struct ExecState {
+    int32_t b_star;        // log2 B* (per axis)
+    int32_t status;
+    int64_t k_star;
+    int64_t count;         // kept coordinates
+    int32_t ntrials;
+    int32_t empty;         // 1: nothing to locate
+    int64_t vote_items;    // sum over location hashes of nsel * D^ndim
+    int64_t trial_B[kMaxTrialsTrace];
+    int64_t trial_k[kMaxTrialsTrace];
+    Job job;               // location + estimation job at B*
+};
+
+}  // namespace atsfft
+
+struct atsfft_plan_s {
+    int ndim;
+    int logn;              // log2 n (1D) or log2 N (2D, per axis)
+    int64_t n;             // n or N
+    int64_t ncoord;        // n or N^2
+    atsfft_params p;
+    uint64_t seed;
+    int b_lo, b_hi, b0;
+    int L_loc, L_est;
+    int device;
+    int num_sms;
+
+    atsfft::HashParam h_tune[atsfft::kMaxLogB];   // tuning hash of each log2 B
+    atsfft::HashParam h_le[2 * atsfft::kMaxLoops]; // location then estimation hashes
+    atsfft::WindowParam h_win[atsfft::kMaxLogB];
+    int64_t resp_off[atsfft::kMaxLogB];
+    atsfft::Job h_tjob[atsfft::kMaxLogB];
+
+    atsfft::HashParam *d_tune, *d_le;
+    atsfft::WindowParam *d_win;
+    double *d_resp;        // Ghat' tables for every B of the range, concatenated
+    float2 *d_tw;          // exp(-2 pi i j / kSmallFFT)
+
+    float2 *d_part;        // binning partial sums (residue order)
+    size_t part_elems;
+    float2 *d_tz;          // tuning spectra P, all B concatenated (offsets tz_off)
+    int64_t tz_off[atsfft::kMaxLogB];
+    float2 *d_z;           // location + estimation spectra at B*
+    float2 *d_fft_tmp;     // four-step intermediate
+    float *d_energy;       // energies (tuning region then location region)
+    int64_t e_loc_off;
+    atsfft::HashStats *d_stats;   // [kMaxLogB tuning slots][L_loc location slots]
+    uint32_t *d_hist;             // [slots][kHistBins]
+    int32_t *d_lmax;              // local-maximum lists [L_loc][lmax_cap]
+    int32_t *d_sel;               // selected buckets    [L_loc][lmax_cap]
+    int64_t lmax_cap;
+    uint32_t *d_votes;            // packed byte counters
+    int64_t nvote_words;
+    uint32_t *d_blk;              // compaction per-block counts / offsets
+    int64_t nblk;
+    atsfft::ExecState *d_state;
+    atsfft::Job *d_tjob;
+    atsfft::StatJob *d_tstat;     // tuning stat jobs (built at plan time)
+    atsfft::StatJob *d_lstat;     // location stat jobs (written by the controller)
+    int ntstat;
+};
+
+namespace atsfft {
+
+atsfft_status cuda_status(cudaError_t e);
+
+inline int stats_slot_tune(int logB) { return logB; }
+inline int stats_slot_loc(int l) { return kMaxLogB + l; }
+
+// plan.cu
+uint64_t splitmix64_next(uint64_t *state);
+void hash_params_for(uint64_t seed, int phase, int index, int64_t n, int ndim, HashParam *out);
+uint32_t inv_mod_pow2(uint32_t sigma, int64_t n);
+WindowParam window_shape(int64_t n, int logB, double alpha, double tol);
+Job make_job(const atsfft_plan_s *P, int logB, int nh);
+
+// bin.cu
+void launch_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, const Job &job_host,
+                bool dynamic, const HashParam *hashes, int logB_static, cudaStream_t s);
+
+// fft.cu
+void launch_bucket_fft(const atsfft_plan_s *P, const Job *job_dev, bool dynamic, int logB_static,
+                       int nh_static, const float2 *part, float2 *out, cudaStream_t s);
+
+// select.cu
+void launch_stats(const atsfft_plan_s *P, const StatJob *jobs, int njobs, int64_t max_nb,
+                  cudaStream_t s);
+void launch_controller(const atsfft_plan_s *P, cudaStream_t s);
+void launch_topnum_vote(const atsfft_plan_s *P, cudaStream_t s);
+void launch_reset(const atsfft_plan_s *P, cudaStream_t s);
+
+// locate.cu
+void launch_compact(const atsfft_plan_s *P, int64_t *d_loc, int64_t capacity, cudaStream_t s);
+
+// estimate.cu
+void launch_estimate(const atsfft_plan_s *P, const int64_t *d_loc, float2 *d_val,
+                     int64_t capacity, int64_t *d_count, int64_t *d_k, int32_t *d_status,
+                     cudaStream_t s);
+void launch_unpermute(const atsfft_plan_s *P, const float2 *spec, const HashParam *hash_dev,
+                      int logB, float2 *out, cudaStream_t s);
+
+}  // namespace atsfft

@@ -1,0 +1,466 @@
+// plan.cu -- plan creation: hash permutations (Def. 1), window shapes and tables
+// (Section II-A-2), scratch allocation.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+
+namespace atsfft {
+
+atsfft_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return ATSFFT_OK;
+    if (e == cudaErrorMemoryAllocation) return ATSFFT_E_NOMEM;
+    return ATSFFT_E_CUDA;
+}
+
+// SplitMix64 (Steele, Lea and Flood, 2014).
+uint64_t splitmix64_next(uint64_t *state)
+{
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Inverse of odd sigma modulo the power of two n: Newton steps y <- y (2 - sigma y)
+// each double the number of correct low bits (y = sigma is right to 3 bits).
+uint32_t inv_mod_pow2(uint32_t sigma, int64_t n)
+{
+    uint64_t y = sigma;
+    for (int i = 0; i < 6; i++) y = y * (2 - (uint64_t)sigma * y);
+    return (uint32_t)(y & (uint64_t)(n - 1));
+}
+
+// Hash `index` of `phase` (0 tuning, 1 location, 2 estimation): one SplitMix64 stream
+// keyed by (seed, phase, index) draws sigma (odd) and tau per axis.
+void hash_params_for(uint64_t seed, int phase, int index, int64_t n, int ndim, HashParam *out)
+{
+    uint64_t st = seed ^ ((uint64_t)(phase + 1) << 56) ^ ((uint64_t)(uint32_t)index << 32);
+    uint64_t mask = (uint64_t)n - 1;
+    memset(out, 0, sizeof(*out));
+    for (int d = 0; d < ndim; d++) {
+        out->sigma[d] = (uint32_t)((splitmix64_next(&st) & mask) | 1u);
+        out->tau[d] = (uint32_t)(splitmix64_next(&st) & mask);
+        out->sinv[d] = inv_mod_pow2(out->sigma[d], n);
+    }
+}
+
+// Window of B = 2^logB buckets over length n: box car of one bucket width convolved
+// with a Gaussian reaching `tol` at alpha * D / 2 beyond the box edge.  Time-domain
+// std s = B q / (pi alpha), q = sqrt(2 ln(1/tol)), support h = ceil(s q); when that
+// exceeds n/2 - 1 the support is clamped and s shrunk to h / q.
+WindowParam window_shape(int64_t n, int logB, double alpha, double tol)
+{
+    WindowParam w;
+    double B = ldexp(1.0, logB);
+    double q = sqrt(2.0 * log(1.0 / tol));
+    double s = B * q / (M_PI * alpha);
+    double hh = ceil(s * q);
+    int64_t hmax = n / 2 - 1;
+    if (hh > (double)hmax) {
+        w.h = (int32_t)hmax;
+        w.s = (double)hmax / q;
+    } else {
+        w.h = (int32_t)hh;
+        w.s = s;
+    }
+    w.k2 = (float)(1.4426950408889634 / (2.0 * w.s * w.s));
+    w.A = 0.0;
+    w.log2c = 0.0f;
+    w.cA_D = 0.0f;
+    return w;
+}
+
+// Residue-stream binning when the window covers at least a fifth of the signal and
+// the per-bucket rotation table fits in shared memory; warp-per-bucket gather below.
+Job make_job(const atsfft_plan_s *P, int logB, int nh)
+{
+    Job j;
+    memset(&j, 0, sizeof(j));
+    j.logB = logB;
+    j.nh = nh;
+    j.active = 1;
+    int64_t w = 2 * (int64_t)P->h_win[logB].h + 1;
+    int64_t D = P->n >> logB;
+    if (P->ndim == 1) {
+        j.stream = (5 * w >= P->n && D <= 4096) ? 1 : 0;
+        if (j.stream) {
+            // about 2^18 threads: residues x row chunks
+            int64_t B = (int64_t)1 << logB;
+            int64_t rows = P->n >> logB;
+            int64_t chunks = ((int64_t)1 << 18) / B;
+            if (chunks < 1) chunks = 1;
+            if (chunks > rows) chunks = rows;
+            j.chunks = (int32_t)chunks;
+        } else {
+            j.chunks = 1;
+        }
+    } else {
+        // 2D: residue-stream over (r1, r2) once the window covers a fifth of each axis
+        j.stream = (5 * w >= P->n) ? 1 : 0;
+        int64_t B2 = (int64_t)1 << (2 * logB);
+        int64_t rows = D;  // row blocks per residue pair along axis 1
+        int64_t chunks = j.stream ? ((int64_t)1 << 18) / B2 : 1;
+        if (chunks < 1) chunks = 1;
+        if (chunks > rows) chunks = rows;
+        j.chunks = (int32_t)chunks;
+    }
+    return j;
+}
+
+// ---- plan-time window tables (FP64) ---------------------------------------------
+
+// Unnormalised tap T_t = exp(-t^2/(2 s^2)) * box(t), box(0) = D, box(t) = sin(pi t/B)/(pi t/n),
+// with sin(pi t / B) reduced exactly in integers.
+__device__ double window_term(int64_t t, int64_t n, int logB, double s)
+{
+    int64_t B = (int64_t)1 << logB;
+    double env = exp(-((double)t * (double)t) / (2.0 * s * s));
+    if (t == 0) return env * (double)(n >> logB);
+    int64_t r = t % (2 * B);
+    if (r < 0) r += 2 * B;
+    double sn = (r == 0 || r == B) ? 0.0 : sinpi((double)r / (double)B);
+    return env * sn / (M_PI * (double)t / (double)n);
+}
+
+// Partial sums over a chunk of t in [0, h] of w_t T_t cos(pi o2 t / n) (w_0 = 1, else 2)
+// for every half-integer offset o2 = 2j - D + 1, j in [0, D), and o2 = 0 (j = D, the
+// normalising sum).  The cosine advances by an exact FP64 rotation from an exactly
+// reduced start.
+constexpr int kRespThreads = 128;
+constexpr int kRespTile = 128;
+constexpr int64_t kRespChunk = 8192;
+
+__global__ void k_window_partial(int64_t n, int logB, double s, int h, double *partial,
+                                 int nchunks)
+{
+    __shared__ double terms[kRespTile];
+    int64_t D = n >> logB;
+    int64_t j = (int64_t)blockIdx.x * kRespThreads + threadIdx.x;
+    int chunk = blockIdx.y;
+    int64_t t0 = (int64_t)chunk * kRespChunk;
+    int64_t t1 = t0 + kRespChunk - 1;
+    if (t1 > h) t1 = h;
+    int64_t o2 = (j < D) ? 2 * j - D + 1 : 0;
+    // start angle pi * o2 * t0 / n, reduced mod 2n exactly
+    int64_t m = (o2 * t0) % (2 * n);
+    if (m < 0) m += 2 * n;
+    double c, sn;
+    sincospi((double)m / (double)n, &sn, &c);
+    double cr, sr;
+    sincospi((double)o2 / (double)n, &sr, &cr);
+    double acc = 0.0;
+    for (int64_t tb = t0; tb <= t1; tb += kRespTile) {
+        __syncthreads();
+        int64_t tt = tb + threadIdx.x;
+        terms[threadIdx.x] = (tt <= t1) ? window_term(tt, n, logB, s) * (tt == 0 ? 1.0 : 2.0) : 0.0;
+        __syncthreads();
+        int cnt = (int)((t1 - tb + 1) < kRespTile ? (t1 - tb + 1) : kRespTile);
+        for (int k = 0; k < cnt; k++) {
+            acc += terms[k] * c;
+            double c2 = c * cr - sn * sr;
+            sn = sn * cr + c * sr;
+            c = c2;
+        }
+    }
+    if (j <= D) partial[j * nchunks + chunk] = acc;
+}
+
+// Sums the chunk partials in order; resp[j] = S(o2_j) / S(0).
+__global__ void k_window_finish(int64_t D, const double *partial, int nchunks, double *resp,
+                                double *S0_out)
+{
+    __shared__ double S0;
+    if (threadIdx.x == 0) {
+        double s0 = 0.0;
+        for (int c = 0; c < nchunks; c++) s0 += partial[D * nchunks + c];
+        S0 = s0;
+        *S0_out = s0;
+    }
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < D; j += blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < nchunks; c++) acc += partial[j * nchunks + c];
+        resp[j] = acc / S0;
+    }
+}
+
+// Twiddles exp(-2 pi i j / kSmallFFT) for the shared-memory FFT, from exact fractions.
+__global__ void k_twiddles(float2 *tw)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < kSmallFFT) {
+        double s, c;
+        sincospi(-2.0 * (double)j / (double)kSmallFFT, &s, &c);
+        tw[j] = make_float2((float)c, (float)s);
+    }
+}
+
+}  // namespace atsfft
+
+using namespace atsfft;
+
+extern "C" void atsfft_default_params(atsfft_params *p)
+{
+    if (!p) return;
+    p->delta1 = 0.02;
+    p->delta2 = 0.05;
+    p->eps1 = 0.5;
+    p->eps2 = 1.0;
+    p->tune_max = 32;
+    p->loops_loc = 7;
+    p->loops_est = 7;
+    p->filter_alpha = 0.5;
+    p->filter_tol = 1e-6;
+    p->thr_rel = 1e-3;
+    p->thr_med = 20.0;
+    p->tie_eta = 1e-2;
+    p->b_min_log2 = 0;
+    p->b_max_log2 = 0;
+}
+
+extern "C" const char *atsfft_status_string(atsfft_status s)
+{
+    switch (s) {
+    case ATSFFT_OK: return "ok";
+    case ATSFFT_E_INVALID_ARG: return "invalid argument";
+    case ATSFFT_E_NOMEM: return "out of memory";
+    case ATSFFT_E_CUDA: return "CUDA error";
+    case ATSFFT_E_NOT_CONVERGED: return "tuning did not converge within tune_max trials";
+    case ATSFFT_E_NOT_SPARSE: return "signal not sparse enough for the largest B";
+    case ATSFFT_E_CAPACITY: return "output capacity too small";
+    }
+    return "unknown status";
+}
+
+static bool params_ok(const atsfft_params *p)
+{
+    if (!(p->delta1 > 0 && p->delta1 < p->delta2 && p->delta2 < 1)) return false;
+    if (p->eps1 != 0.5 || p->eps2 != 1.0) return false;
+    if (p->tune_max < 1 || p->tune_max > kMaxTrialsTrace) return false;
+    if (p->loops_loc < 1 || p->loops_loc > kMaxLoops || p->loops_est < 1 ||
+        p->loops_est > kMaxLoops)
+        return false;
+    if (!(p->filter_alpha > 0 && p->filter_alpha <= 2)) return false;
+    if (!(p->filter_tol > 0 && p->filter_tol < 1)) return false;
+    if (!(p->thr_rel >= 0 && p->thr_med >= 0 && p->tie_eta >= 0 && p->tie_eta < 1)) return false;
+    return true;
+}
+
+static void plan_free(atsfft_plan_s *P)
+{
+    void *ptrs[] = {P->d_tune, P->d_le, P->d_win, P->d_resp, P->d_tw, P->d_part, P->d_tz,
+                    P->d_z, P->d_fft_tmp, P->d_energy, P->d_stats, P->d_hist, P->d_lmax,
+                    P->d_sel, P->d_votes, P->d_blk, P->d_state, P->d_tjob, P->d_tstat,
+                    P->d_lstat};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    delete P;
+}
+
+static int ilog2_ceil(int64_t v)
+{
+    int r = 0;
+    while (((int64_t)1 << r) < v) r++;
+    return r;
+}
+
+extern "C" atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t *shape,
+                                     int64_t k_hint, const atsfft_params *pp, uint64_t seed)
+{
+    if (!out) return ATSFFT_E_INVALID_ARG;
+    *out = nullptr;
+    if (!shape || (ndim != 1 && ndim != 2) || k_hint < 0) return ATSFFT_E_INVALID_ARG;
+    atsfft_params p;
+    if (pp)
+        p = *pp;
+    else
+        atsfft_default_params(&p);
+    if (!params_ok(&p)) return ATSFFT_E_INVALID_ARG;
+    int64_t n = shape[0];
+    if (n <= 0 || (n & (n - 1))) return ATSFFT_E_INVALID_ARG;
+    if (ndim == 1 && (n < 256 || n > ((int64_t)1 << 28))) return ATSFFT_E_INVALID_ARG;
+    if (ndim == 2 && (shape[1] != n || n < 32 || n > ((int64_t)1 << 14))) return ATSFFT_E_INVALID_ARG;
+
+    atsfft_plan_s *P = new (std::nothrow) atsfft_plan_s;
+    if (!P) return ATSFFT_E_NOMEM;
+    memset(P, 0, sizeof(*P));
+    P->ndim = ndim;
+    P->n = n;
+    P->logn = ilog2_ceil(n);
+    P->ncoord = ndim == 1 ? n : n * n;
+    P->p = p;
+    P->seed = seed;
+    P->L_loc = p.loops_loc;
+    P->L_est = p.loops_est;
+    P->b_lo = p.b_min_log2 ? p.b_min_log2 : (ndim == 1 ? 4 : 3);
+    P->b_hi = p.b_max_log2 ? p.b_max_log2 : (ndim == 1 ? P->logn - 4 : P->logn - 2);
+    if (P->b_lo < 1 || P->b_hi > P->logn - 1 || P->b_lo > P->b_hi ||
+        (ndim == 1 && P->b_hi > 24) || (ndim == 2 && P->b_hi > 12)) {
+        delete P;
+        return ATSFFT_E_INVALID_ARG;
+    }
+    P->b0 = P->b_lo;
+    if (k_hint > 0) {
+        int want = ndim == 1 ? ilog2_ceil(2 * k_hint) : (ilog2_ceil(2 * k_hint) + 1) / 2;
+        if (want > P->b0) P->b0 = want;
+        if (P->b0 > P->b_hi) P->b0 = P->b_hi;
+    }
+    if (cudaGetDevice(&P->device) != cudaSuccess) {
+        delete P;
+        return ATSFFT_E_CUDA;
+    }
+    cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device);
+
+    for (int b = P->b0; b <= P->b_hi; b++) hash_params_for(seed, 0, b, n, ndim, &P->h_tune[b]);
+    for (int l = 0; l < P->L_loc; l++) hash_params_for(seed, 1, l, n, ndim, &P->h_le[l]);
+    for (int l = 0; l < P->L_est; l++) hash_params_for(seed, 2, l, n, ndim, &P->h_le[P->L_loc + l]);
+
+    // ---- allocations ----
+    atsfft_status st = ATSFFT_OK;
+    auto A = [&](void **ptr, size_t bytes) {
+        if (st != ATSFFT_OK) return;
+        cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
+        if (e != cudaSuccess) st = cuda_status(e);
+    };
+    int64_t resp_total = 0;
+    int64_t tz_total = 0;
+    for (int b = P->b0; b <= P->b_hi; b++) {
+        P->h_win[b] = window_shape(n, b, p.filter_alpha, p.filter_tol);
+        P->resp_off[b] = resp_total;
+        resp_total += n >> b;
+        P->tz_off[b] = tz_total;
+        tz_total += ndim == 1 ? ((int64_t)1 << b) : ((int64_t)1 << (2 * b));
+    }
+    for (int b = P->b0; b <= P->b_hi; b++) P->h_tjob[b] = make_job(P, b, 1);
+    int64_t nb_max = ndim == 1 ? ((int64_t)1 << P->b_hi) : ((int64_t)1 << (2 * P->b_hi));
+    int nh_le = P->L_loc + P->L_est;
+    // partials: largest of (tuning single hash, location + estimation) x chunks
+    size_t part = 0;
+    for (int b = P->b0; b <= P->b_hi; b++) {
+        int64_t nb = ndim == 1 ? ((int64_t)1 << b) : ((int64_t)1 << (2 * b));
+        Job j = make_job(P, b, nh_le);
+        size_t need = (size_t)j.chunks * (size_t)nh_le * (size_t)nb;
+        if (need > part) part = need;
+    }
+    P->part_elems = part;
+    P->lmax_cap = ndim == 1 ? nb_max / 2 + 1 : nb_max / 4 + 1;
+    P->nvote_words = (P->ncoord + 3) / 4;
+    P->nblk = (P->nvote_words + 1023) / 1024;
+    P->e_loc_off = tz_total;
+
+    A((void **)&P->d_tune, sizeof(HashParam) * kMaxLogB);
+    A((void **)&P->d_le, sizeof(HashParam) * (2 * kMaxLoops + 1));
+    A((void **)&P->d_win, sizeof(WindowParam) * kMaxLogB);
+    A((void **)&P->d_resp, sizeof(double) * resp_total);
+    A((void **)&P->d_tw, sizeof(float2) * kSmallFFT);
+    A((void **)&P->d_part, sizeof(float2) * part);
+    A((void **)&P->d_tz, sizeof(float2) * tz_total);
+    A((void **)&P->d_z, sizeof(float2) * nh_le * nb_max);
+    // four-step intermediate (1D) or per-axis tap tables, nh x 2 x N (2D)
+    size_t tmp_elems = (size_t)nh_le * (size_t)nb_max;
+    if (ndim == 2 && (size_t)nh_le * 2 * (size_t)n > tmp_elems) tmp_elems = (size_t)nh_le * 2 * (size_t)n;
+    A((void **)&P->d_fft_tmp, sizeof(float2) * tmp_elems);
+    A((void **)&P->d_energy, sizeof(float) * (tz_total + P->L_loc * nb_max));
+    A((void **)&P->d_stats, sizeof(HashStats) * (kMaxLogB + kMaxLoops));
+    A((void **)&P->d_hist, sizeof(uint32_t) * kHistBins * (kMaxLogB + kMaxLoops));
+    A((void **)&P->d_lmax, sizeof(int32_t) * P->L_loc * P->lmax_cap);
+    A((void **)&P->d_sel, sizeof(int32_t) * P->L_loc * P->lmax_cap);
+    A((void **)&P->d_votes, sizeof(uint32_t) * P->nvote_words);
+    A((void **)&P->d_blk, sizeof(uint32_t) * (P->nblk + 1));
+    A((void **)&P->d_state, sizeof(ExecState));
+    A((void **)&P->d_tjob, sizeof(Job) * kMaxLogB);
+    A((void **)&P->d_tstat, sizeof(StatJob) * kMaxLogB);
+    A((void **)&P->d_lstat, sizeof(StatJob) * kMaxLoops);
+    if (st != ATSFFT_OK) {
+        plan_free(P);
+        return st;
+    }
+
+    // ---- window tables (plan time, synchronous) ----
+    cudaError_t e = cudaSuccess;
+    double *d_partial = nullptr, *d_S0 = nullptr;
+    int64_t max_nch = 0, max_D = 0;
+    for (int b = P->b0; b <= P->b_hi; b++) {
+        int64_t nch = (P->h_win[b].h + kRespChunk) / kRespChunk;
+        if (nch > max_nch) max_nch = nch;
+        if ((n >> b) > max_D) max_D = n >> b;
+    }
+    e = cudaMalloc(&d_partial, sizeof(double) * (size_t)(max_D + 1) * (size_t)max_nch);
+    if (e == cudaSuccess) e = cudaMalloc(&d_S0, sizeof(double) * kMaxLogB);
+    for (int b = P->b0; b <= P->b_hi && e == cudaSuccess; b++) {
+        WindowParam &w = P->h_win[b];
+        int64_t D = n >> b;
+        int nch = (int)((w.h + kRespChunk) / kRespChunk);
+        dim3 grid((unsigned)((D + 1 + kRespThreads - 1) / kRespThreads), (unsigned)nch);
+        k_window_partial<<<grid, kRespThreads>>>(n, b, w.s, w.h, d_partial, nch);
+        k_window_finish<<<1, 256>>>(D, d_partial, nch, P->d_resp + P->resp_off[b], d_S0 + b);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_twiddles<<<kSmallFFT / 256, 256>>>(P->d_tw);
+        e = cudaGetLastError();
+    }
+    double S0[kMaxLogB];
+    if (e == cudaSuccess) e = cudaMemcpy(S0, d_S0, sizeof(double) * kMaxLogB, cudaMemcpyDeviceToHost);
+    if (d_partial) cudaFree(d_partial);
+    if (d_S0) cudaFree(d_S0);
+    if (e == cudaSuccess) {
+        for (int b = P->b0; b <= P->b_hi; b++) {
+            WindowParam &w = P->h_win[b];
+            w.A = (double)n / S0[b];
+            w.log2c = (float)log2(w.A * (double)n / M_PI);
+            w.cA_D = (float)(w.A * (double)(n >> b));
+        }
+        e = cudaMemcpy(P->d_win, P->h_win, sizeof(P->h_win), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(P->d_tune, P->h_tune, sizeof(P->h_tune), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->d_le, P->h_le, sizeof(P->h_le), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->d_tjob, P->h_tjob, sizeof(P->h_tjob), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        // tuning stat jobs: one per B of the range, spectra and energies at tz_off[b]
+        StatJob ts[kMaxLogB];
+        P->ntstat = 0;
+        for (int b = P->b0; b <= P->b_hi; b++) {
+            StatJob &j = ts[P->ntstat++];
+            j.spec = P->d_tz + P->tz_off[b];
+            j.energy = P->d_energy + P->tz_off[b];
+            j.hash = P->d_tune + b;
+            j.logB = b;
+            j.slot = b;
+            j.list = -1;
+            j.active = 1;
+        }
+        e = cudaMemcpy(P->d_tstat, ts, sizeof(StatJob) * P->ntstat, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemset(P->d_votes, 0, sizeof(uint32_t) * P->nvote_words);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        plan_free(P);
+        return cuda_status(e);
+    }
+    *out = P;
+    return ATSFFT_OK;
+}
+
+extern "C" atsfft_status atsfft_destroy(atsfft_plan_t P)
+{
+    if (!P) return ATSFFT_E_INVALID_ARG;
+    cudaDeviceSynchronize();
+    plan_free(P);
+    return ATSFFT_OK;
+}
+
+extern "C" atsfft_status atsfft_window_response(atsfft_plan_t P, int64_t B, double *h_resp)
+{
+    if (!P || !h_resp || B <= 0 || (B & (B - 1))) return ATSFFT_E_INVALID_ARG;
+    int b = ilog2_ceil(B);
+    if (b < P->b0 || b > P->b_hi) return ATSFFT_E_INVALID_ARG;
+    cudaError_t e = cudaMemcpy(h_resp, P->d_resp + P->resp_off[b], sizeof(double) * (P->n >> b),
+                               cudaMemcpyDeviceToHost);
+    return cuda_status(e);
+}

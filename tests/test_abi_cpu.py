@@ -1,0 +1,64 @@
+"""The C ABI library builds, loads without a GPU and exports every declared symbol."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "atsfft.h")).read()
+    return sorted(set(re.findall(r"\b(atsfft_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1908_02461_gb300 import build
+
+    return ctypes.CDLL(build())
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "atsfft_exec" in names and "atsfft_plan" in names and "atsfft_exec_2d" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_header():
+    import paper_1908_02461_gb300._lib as L
+
+    assert sorted(L.EXPORTED) == _declared()
+
+
+def test_host_only_calls(lib):
+    import paper_1908_02461_gb300 as A
+
+    p = A.atsfft_default_params()
+    assert p.delta1 == 0.02 and p.delta2 == 0.05 and p.eps1 == 0.5 and p.eps2 == 1.0
+    assert p.loops_loc == 7 and p.loops_est == 7 and p.tie_eta == 0.01
+    assert A.atsfft_status_string(0) == "ok"
+    assert "capacity" in A.atsfft_status_string(6)
+    # argument checks happen before any device call
+    st, h = A.atsfft_plan(1, (1000,), 0, None, 0)
+    assert st == A.E_INVALID_ARG and h is None
+    st, h = A.atsfft_plan(3, (1024,), 0, None, 0)
+    assert st == A.E_INVALID_ARG
+    bad = A.params(eps1=0.25)
+    st, h = A.atsfft_plan(1, (1 << 14,), 0, bad, 0)
+    assert st == A.E_INVALID_ARG
+    assert A.atsfft_exec(None, 0, 0, 0, 0, 0, 0, 0, None) == A.E_INVALID_ARG
+
+
+def test_product_package_never_imports_oracle():
+    """The product path shares no code with the oracle and never loads it."""
+    pkg = os.path.join(ROOT, "paper_1908_02461_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                for bad in ("import oracle", "from oracle", "atsfft_oracle", "orc_"):
+                    assert bad not in txt, (f, bad)
