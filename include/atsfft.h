@@ -119,6 +119,21 @@ atsfft_status atsfft_window_response(atsfft_plan_t plan, int64_t B, double *h_re
 atsfft_status atsfft_last_trace(atsfft_plan_t plan, int64_t *h_B, int64_t *h_k, int max_trials,
                                 int *h_ntrials, void *stream);
 
+/* Turns per-phase CUDA events on (1) or off (0) for later execs of this plan.  The
+ * nine phases of one exec, in order: 0 tuning binning + bucket FFTs, 1 tuning
+ * statistics, 2 controller, 3 binning of the location/estimation hashes in the
+ * residue-stream form (1D; 2D: tap tables + stream form), 4 the same in the gather
+ * form, 5 their bucket FFTs, 6 location statistics, 7 top-num cutoff, votes and
+ * compaction, 8 estimation and median.  A form or shape that does not apply to B*
+ * exits at once, so its phase measures only an empty launch. */
+atsfft_status atsfft_set_profiling(atsfft_plan_t plan, int on);
+
+/* After an exec: per-phase device times in ms (h_ms[max_phases], read only if profiling
+ * was on for that exec; synchronises `stream`), the number of phases, and the number of
+ * kernel launches that exec enqueued (h_launches may be NULL). */
+atsfft_status atsfft_phase_times(atsfft_plan_t plan, float *h_ms, int max_phases, int *h_nphases,
+                                 int64_t *h_launches, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

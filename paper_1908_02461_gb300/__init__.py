@@ -25,7 +25,9 @@ from ._lib import (  # noqa: F401
     atsfft_hash_spectrum,
     atsfft_last_trace,
     atsfft_params,
+    atsfft_phase_times,
     atsfft_plan,
+    atsfft_set_profiling,
     atsfft_status_string,
     atsfft_window_response,
 )
@@ -121,6 +123,25 @@ class Plan:
         if st != OK:
             raise ATSFFTError(st, "atsfft_window_response")
         return out
+
+    def set_profiling(self, on: bool = True):
+        st = atsfft_set_profiling(self.handle, on)
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_set_profiling")
+
+    def phase_times(self, stream=None):
+        """Per-phase ms of the last exec (dict) and its kernel launch count."""
+        import numpy as np
+        import torch
+
+        from ._lib import PHASES
+
+        ms = np.zeros(len(PHASES), dtype=np.float32)
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        st, nph, nl = atsfft_phase_times(self.handle, ms, len(PHASES), s)
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_phase_times")
+        return dict(zip(PHASES[:nph], ms[:nph].tolist())), nl
 
     def last_trace(self):
         import numpy as np

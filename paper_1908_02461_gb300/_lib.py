@@ -34,7 +34,11 @@ class atsfft_params(C.Structure):
 
 EXPORTED = ["atsfft_default_params", "atsfft_plan", "atsfft_exec", "atsfft_exec_2d",
             "atsfft_destroy", "atsfft_status_string", "atsfft_hash_spectrum",
-            "atsfft_window_response", "atsfft_last_trace"]
+            "atsfft_window_response", "atsfft_last_trace", "atsfft_set_profiling",
+            "atsfft_phase_times"]
+
+PHASES = ["tune_bin_fft", "tune_stats", "controller", "le_bin_stream", "le_bin_gather",
+          "le_fft", "le_stats", "locate", "estimate"]
 
 _lib = None
 
@@ -68,6 +72,10 @@ def load(path: str | None = None):
     L.atsfft_window_response.restype = i32
     L.atsfft_last_trace.argtypes = [vp, vp, vp, i32, P(i32), vp]
     L.atsfft_last_trace.restype = i32
+    L.atsfft_set_profiling.argtypes = [vp, i32]
+    L.atsfft_set_profiling.restype = i32
+    L.atsfft_phase_times.argtypes = [vp, vp, i32, P(i32), P(i64), vp]
+    L.atsfft_phase_times.restype = i32
     if path is None:
         _lib = L
     return L
@@ -133,3 +141,16 @@ def atsfft_last_trace(plan, h_B, h_k, max_trials, stream=None):
     nt = C.c_int()
     st = load().atsfft_last_trace(plan, _ptr(h_B), _ptr(h_k), max_trials, C.byref(nt), _ptr(stream))
     return st, nt.value
+
+
+def atsfft_set_profiling(plan, on: bool) -> int:
+    return load().atsfft_set_profiling(plan, 1 if on else 0)
+
+
+def atsfft_phase_times(plan, h_ms, max_phases, stream=None):
+    """Returns (status, number of phases, launches of the last exec)."""
+    nph = C.c_int()
+    nl = C.c_int64()
+    st = load().atsfft_phase_times(plan, _ptr(h_ms), max_phases, C.byref(nph), C.byref(nl),
+                                   _ptr(stream))
+    return st, nph.value, nl.value

@@ -28,24 +28,28 @@ static atsfft_status exec_common(atsfft_plan_t P, int ndim, const void *d_x, int
     cudaStream_t s = (cudaStream_t)stream;
     const float2 *x = (const float2 *)d_x;
     cudaGetLastError();   // clear a stale error so the status below is this call's
+    P->launches = 0;
     launch_reset(P, s);
-    for (int b = P->b0; b <= P->b_hi; b++) {
-        launch_bin(P, x, nullptr, P->h_tjob[b], false, P->d_tune + b, b, s);
-        launch_bucket_fft(P, nullptr, false, b, 1, P->d_part, P->d_tz + P->tz_off[b], s);
-    }
+    prof_mark(P, 0, s);
+    launch_tuning(P, x, s);
+    prof_mark(P, 1, s);
     const int64_t nb_hi = ndim == 1 ? ((int64_t)1 << P->b_hi) : ((int64_t)1 << (2 * P->b_hi));
     launch_stats(P, P->d_tstat, P->ntstat, nb_hi, s);
+    prof_mark(P, 2, s);
     launch_controller(P, s);
-    Job jl;
-    memset(&jl, 0, sizeof(jl));
-    jl.nh = P->L_loc + P->L_est;
+    prof_mark(P, 3, s);
     const Job *jd = &P->d_state->job;
-    launch_bin(P, x, jd, jl, true, P->d_le, 0, s);
-    launch_bucket_fft(P, jd, true, 0, jl.nh, P->d_part, P->d_z, s);
+    launch_le_bin(P, x, jd, s);   // marks phase 4 after the stream-form kernel
+    prof_mark(P, 5, s);
+    launch_bucket_fft_dynamic(P, jd, P->d_part, P->d_z, s);
+    prof_mark(P, 6, s);
     launch_stats(P, P->d_lstat, P->L_loc, nb_hi, s);
+    prof_mark(P, 7, s);
     launch_topnum_vote(P, s);
     launch_compact(P, d_loc, capacity, s);
+    prof_mark(P, 8, s);
     launch_estimate(P, d_loc, (float2 *)d_val, capacity, d_count, d_k, d_status, s);
+    prof_mark(P, 9, s);
     return cuda_status(cudaGetLastError());
 }
 
@@ -79,9 +83,7 @@ extern "C" atsfft_status atsfft_hash_spectrum(atsfft_plan_t P, const void *d_x, 
     cudaGetLastError();
     cudaError_t e = cudaMemcpyAsync(d_hp, &hp, sizeof(hp), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_status(e);
-    Job j = P->h_tjob[b];
-    launch_bin(P, (const float2 *)d_x, nullptr, j, false, d_hp, b, s);
-    launch_bucket_fft(P, nullptr, false, b, 1, P->d_part, P->d_z, s);
+    launch_single_hash(P, (const float2 *)d_x, b, hp, d_hp, P->d_z, s);
     launch_unpermute(P, P->d_z, d_hp, b, (float2 *)d_zhat, s);
     e = cudaStreamSynchronize(s);   // hp lives on this call's stack
     if (e != cudaSuccess) return cuda_status(e);
@@ -102,6 +104,40 @@ extern "C" atsfft_status atsfft_last_trace(atsfft_plan_t P, int64_t *h_B, int64_
     for (int i = 0; i < max_trials && i < st.ntrials && i < kMaxTrialsTrace; i++) {
         h_B[i] = st.trial_B[i];
         h_k[i] = st.trial_k[i];
+    }
+    return ATSFFT_OK;
+}
+
+extern "C" atsfft_status atsfft_set_profiling(atsfft_plan_t P, int on)
+{
+    if (!P) return ATSFFT_E_INVALID_ARG;
+    if (on && !P->prof) {
+        for (int i = 0; i <= kPhases; i++) {
+            cudaError_t e = cudaEventCreate(&P->ev[i]);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+    }
+    if (!on && P->prof)
+        for (int i = 0; i <= kPhases; i++) cudaEventDestroy(P->ev[i]);
+    P->prof = on ? 1 : 0;
+    return ATSFFT_OK;
+}
+
+extern "C" atsfft_status atsfft_phase_times(atsfft_plan_t P, float *h_ms, int max_phases,
+                                            int *h_nphases, int64_t *h_launches, void *stream)
+{
+    if (!P || !h_nphases || max_phases < 0 || (max_phases > 0 && !h_ms)) return ATSFFT_E_INVALID_ARG;
+    if (h_launches) *h_launches = P->launches;
+    if (!P->prof) {
+        *h_nphases = 0;
+        return ATSFFT_OK;
+    }
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    *h_nphases = kPhases;
+    for (int i = 0; i < kPhases && i < max_phases; i++) {
+        e = cudaEventElapsedTime(&h_ms[i], P->ev[i], P->ev[i + 1]);
+        if (e != cudaSuccess) return cuda_status(e);
     }
     return ATSFFT_OK;
 }

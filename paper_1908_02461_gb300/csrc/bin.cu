@@ -9,6 +9,8 @@
 //   R_u = (-1)^u exp(i pi u / D)                   (D = n / B, period 2D in u),
 // because sin(pi t / B) = (-1)^u sin(pi b / B).  The centre tap t = 0 (bucket 0, where
 // S_0 = 0) is G_0 = A D.  Bucket sums are stored in residue order (common.cuh).
+#include <string.h>
+
 #include "common.cuh"
 
 namespace atsfft {
@@ -128,93 +130,202 @@ __global__ void k_bin_gather_1d(const float2 *__restrict__ x, int logn, const Ha
 }
 
 // ---------------------------------------------------------------------------------
-// 1D residue stream: thread = (residue r, row chunk).  Samples a = r + j B are read
-// coalesced; for every hash the bucket of all of them is the same, b = sigma^{-1}(r - tau)
-// mod B, so each thread keeps one accumulator per hash and no reduction is needed.
-// Output: part[(chunk * nh + l) * B + r].
+// 1D residue stream.  Thread = (residue r mod R, row chunk c); it reads the samples
+// a = r + j R of its rows coalesced.  For a hash with B | R buckets every such sample
+// falls in the same bucket b = sigma^{-1}(r - tau) mod B, so the thread keeps one
+// accumulator per hash.  Hash l writes block (c * R/B_l + r / B_l) of B_l partial sums,
+// element r mod B_l (residue order); the bucket FFT adds the blocks up.
+// Per-hash constants live in the kernel parameter space.
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_bin_stream_1d(const float2 *__restrict__ x, int logn,
-                                                       const HashParam *hashes, int nh,
-                                                       const WindowParam *win, const Job *job_dev,
-                                                       int logB_static, int chunks_static,
-                                                       float2 *__restrict__ part)
+constexpr int kMaxStream = 16;
+
+struct StreamHash {
+    uint32_t sinv, c0, tau;   // c0 = -sinv * tau (mod 2^32)
+    int32_t logB, h;          // static passes: bucket count and window of this hash
+    float k2, log2c, cAD;
+    int32_t rot_off;          // its R_u table in shared memory (2 D entries)
+    int64_t out_off;          // its first partial block in `part`
+};
+
+struct StreamArgs {
+    int nh;                   // hashes in this launch (<= kMaxStream)
+    int hash_base;            // dynamic pass: index of the first hash (output block offset)
+    int logR;                 // residue modulus (static passes)
+    int chunks;               // row chunks (static passes)
+    StreamHash h[kMaxStream];
+};
+
+// Window constants of one hash inside the inner loop: uniform across the CTA.
+struct TapConst {
+    int h, logB, roff;
+    uint32_t rmask;
+    float k2, l2c;
+};
+
+// One (sample, hash) pair: t = sigma^{-1}(a - tau) mod n as a signed integer, window test
+// as a select (no branch), f_t R_u, complex multiply-add.  ts = 0 (centre tap, bucket 0
+// only) yields inf, which stays in bucket 0's discarded accumulator.
+__device__ __forceinline__ void tap_mac(float2 &acc, float2 v, uint32_t a, uint32_t sinv,
+                                        uint32_t c0, uint32_t mask, int sh, const TapConst &T,
+                                        const float2 *rot)
 {
-    extern __shared__ float2 rot[];   // R_u for u in [0, 2D)
-    int logB = logB_static, chunks = chunks_static;
-    if (job_dev) {
+    const uint32_t t = (sinv * a + c0) & mask;
+    const int ts = (int)(t << sh) >> sh;
+    const bool in = (ts <= T.h) & (ts >= -T.h);
+    const float2 Ru = rot[T.roff + ((uint32_t)(ts >> T.logB) & T.rmask)];
+    const float tf = (float)ts;
+    float f = fast_exp2(fmaf(-T.k2 * tf, tf, T.l2c)) * fast_rcp(tf);
+    f = in ? f : 0.f;
+    const float cr = f * Ru.x, ci = f * Ru.y;
+    acc.x = fmaf(cr, v.x, fmaf(-ci, v.y, acc.x));
+    acc.y = fmaf(cr, v.y, fmaf(ci, v.x, acc.y));
+}
+
+template <int NH, bool DYN>
+__global__ void __launch_bounds__(256) k_bin_stream(const float2 *__restrict__ x, int logn,
+                                                    const StreamArgs A, const Job *job_dev,
+                                                    const WindowParam *win,
+                                                    float2 *__restrict__ part)
+{
+    extern __shared__ float2 rot[];
+    int logR = A.logR, chunks = A.chunks;
+    WindowParam w = {};
+    if (DYN) {
         if (!job_dev->active || !job_dev->stream) return;
-        logB = job_dev->logB;
-        nh = job_dev->nh;
+        logR = job_dev->logB;
         chunks = job_dev->chunks;
+        w = win[logR];
     }
-    const int group0 = blockIdx.y * kGroup;
-    if (group0 >= nh) return;
-    const int ng = min(kGroup, nh - group0);
-    const uint32_t n = 1u << logn, mask = n - 1, B = 1u << logB;
-    const uint32_t D = n >> logB;
-    const WindowParam w = win[logB];
-    const bool full = (2 * (int64_t)w.h + 1) >= (int64_t)n - 1;   // every t but -n/2 inside
-    for (uint32_t u = threadIdx.x; u < 2 * D; u += blockDim.x) {
-        float s, c;
-        sincospif(ldexpf((float)u, -(logn - logB)), &s, &c);
-        rot[u] = (u & 1) ? make_float2(-c, -s) : make_float2(c, s);
+    const uint32_t n = 1u << logn, mask = n - 1, R = 1u << logR;
+    // R_u = (-1)^u exp(i pi u / D), u in [0, 2D): one table (dynamic) or one per hash
+    if (DYN) {
+        const uint32_t D = n >> logR;
+        for (uint32_t u = threadIdx.x; u < 2 * D; u += blockDim.x) {
+            float sn, cs;
+            sincospif(ldexpf((float)u, -(logn - logR)), &sn, &cs);
+            rot[u] = (u & 1) ? make_float2(-cs, -sn) : make_float2(cs, sn);
+        }
+    } else {
+        for (int g = 0; g < NH; g++) {
+            const int lb = A.h[g].logB;
+            const uint32_t D = n >> lb;
+            for (uint32_t u = threadIdx.x; u < 2 * D; u += blockDim.x) {
+                float sn, cs;
+                sincospif(ldexpf((float)u, -(logn - lb)), &sn, &cs);
+                rot[A.h[g].rot_off + u] = (u & 1) ? make_float2(-cs, -sn) : make_float2(cs, sn);
+            }
+        }
     }
     __syncthreads();
-    const uint32_t rows = D / (uint32_t)chunks;
-    const int64_t items = (int64_t)B * chunks;
-    uint32_t sinv[kGroup], c0[kGroup];
+    TapConst T[NH];
 #pragma unroll
-    for (int g = 0; g < kGroup; g++) {
-        const HashParam hp = hashes[group0 + (g < ng ? g : 0)];
-        sinv[g] = hp.sinv[0];
-        c0[g] = 0u - hp.sinv[0] * hp.tau[0];
+    for (int g = 0; g < NH; g++) {
+        if (DYN) {
+            T[g] = TapConst{w.h, logR, 0, 2 * (n >> logR) - 1, w.k2, w.log2c};
+        } else {
+            const StreamHash &H = A.h[g];
+            T[g] = TapConst{H.h, H.logB, H.rot_off, 2 * (n >> H.logB) - 1, H.k2, H.log2c};
+        }
     }
+    const uint32_t rows = (n >> logR) / (uint32_t)chunks;
+    const int64_t items = (int64_t)R * chunks;
     const int sh = 32 - logn;
     for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
          it += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t r = (uint32_t)(it & (B - 1));
-        const uint32_t ch = (uint32_t)(it >> logB);
-        float2 acc[kGroup];
-        float2 cen[kGroup];
+        const uint32_t r = (uint32_t)(it & (R - 1));
+        const uint32_t c = (uint32_t)(it >> logR);
+        float2 acc[NH];
 #pragma unroll
-        for (int g = 0; g < kGroup; g++) {
-            acc[g] = make_float2(0.f, 0.f);
-            cen[g] = make_float2(0.f, 0.f);
-        }
-        const uint32_t j0 = ch * rows;
+        for (int g = 0; g < NH; g++) acc[g] = make_float2(0.f, 0.f);
+        const uint32_t j0 = c * rows;
+#pragma unroll 2
         for (uint32_t j = j0; j < j0 + rows; j++) {
-            const uint32_t a = r + (j << logB);
+            const uint32_t a = r + (j << logR);
             const float2 v = __ldg(&x[a]);
 #pragma unroll
-            for (int g = 0; g < kGroup; g++) {
-                if (g < ng) {
-                    const uint32_t t = (sinv[g] * a + c0[g]) & mask;
-                    const int ts = (int)(t << sh) >> sh;
-                    if (ts == 0) {
-                        cen[g] = v;
-                        continue;
-                    }
-                    if (!full && (ts > w.h || ts < -w.h)) continue;
-                    if (full && ts == -(int)(n >> 1)) continue;
-                    const float tf = (float)ts;
-                    const float f = fast_exp2(fmaf(-w.k2 * tf, tf, w.log2c)) * fast_rcp(tf);
-                    const float2 R = rot[(uint32_t)(ts >> logB) & (2 * D - 1)];
-                    const float cr = f * R.x, ci = f * R.y;
-                    acc[g].x = fmaf(cr, v.x, fmaf(-ci, v.y, acc[g].x));
-                    acc[g].y = fmaf(cr, v.y, fmaf(ci, v.x, acc[g].y));
-                }
-            }
+            for (int g = 0; g < NH; g++)
+                tap_mac(acc[g], v, a, A.h[g].sinv, A.h[g].c0, mask, sh, T[g], rot);
         }
 #pragma unroll
-        for (int g = 0; g < kGroup; g++) {
-            if (g < ng) {
-                const uint32_t b = (sinv[g] * r + c0[g]) & (B - 1);
-                const float2 Sb = bucket_factor(b, logB, logn);
-                float2 z = cmul(Sb, acc[g]);
-                z.x += w.cA_D * cen[g].x;
-                z.y += w.cA_D * cen[g].y;
-                part[((int64_t)ch * nh + group0 + g) * B + r] = z;
+        for (int g = 0; g < NH; g++) {
+            const int logB = DYN ? logR : A.h[g].logB;
+            const uint32_t Bm = (1u << logB) - 1;
+            const uint32_t b = (A.h[g].sinv * r + A.h[g].c0) & Bm;
+            float2 z;
+            if (b == 0) {
+                // centre tap G_0 = A D on sample a = tau, added once (its residue, chunk)
+                const uint32_t tau = A.h[g].tau;
+                const bool mine = r == (tau & (R - 1)) && c == ((tau >> logR) / rows);
+                const float cad = DYN ? w.cA_D : A.h[g].cAD;
+                const float2 v = __ldg(&x[tau & mask]);
+                z = mine ? make_float2(cad * v.x, cad * v.y) : make_float2(0.f, 0.f);
+            } else {
+                z = cmul(bucket_factor(b, logB, logn), acc[g]);
             }
+            const int64_t out_off = DYN ? (int64_t)(A.hash_base + g) * chunks * R : A.h[g].out_off;
+            const uint32_t per_chunk = R >> logB;
+            part[out_off + ((int64_t)c * per_chunk + (r >> logB)) * (Bm + 1) + (r & Bm)] = z;
+        }
+    }
+}
+
+struct GatherHash {
+    uint32_t sig, tau;
+    int32_t logB, h;
+    float k2, log2c, cAD;
+    int64_t out_off;
+    int64_t warp_start;
+};
+
+struct GatherArgs {
+    int njobs;
+    int64_t total_warps;
+    GatherHash j[kMaxLogB];
+};
+
+// Tuning hashes with small windows: warp per (hash, bucket) over all of them in one
+// launch; warp ids are assigned to hashes by prefix sums of their bucket counts.
+__global__ void k_bin_gather_tune(const float2 *__restrict__ x, int logn, const GatherArgs A,
+                                  float2 *__restrict__ part)
+{
+    const uint32_t n = 1u << logn, mask = n - 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+         wid < A.total_warps; wid += warps) {
+        int jb = 0;
+        while (jb + 1 < A.njobs && wid >= A.j[jb + 1].warp_start) jb++;
+        const GatherHash &H = A.j[jb];
+        const int logB = H.logB;
+        const uint32_t B = 1u << logB;
+        const int b = (int)(wid - H.warp_start);
+        const int u_lo = -((H.h + b) >> logB), u_hi = (H.h - b) >> logB;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int u = u_lo + lane; u <= u_hi; u += 32) {
+            const int t = b + u * (int)B;
+            if (t == 0) continue;
+            const float tf = (float)t;
+            const float f = fast_exp2(fmaf(-H.k2 * tf, tf, H.log2c)) * fast_rcp(tf);
+            float rs, rc;
+            sincospif(ldexpf((float)u, -(logn - logB)), &rs, &rc);
+            if (u & 1) { rs = -rs; rc = -rc; }
+            const float2 c = make_float2(f * rc, f * rs);
+            const float2 v = __ldg(&x[(H.sig * (uint32_t)t + H.tau) & mask]);
+            acc.x = fmaf(c.x, v.x, fmaf(-c.y, v.y, acc.x));
+            acc.y = fmaf(c.x, v.y, fmaf(c.y, v.x, acc.y));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (lane == 0) {
+            float2 z = cmul(bucket_factor((uint32_t)b, logB, logn), acc);
+            if (b == 0) {
+                const float2 v = __ldg(&x[H.tau & mask]);
+                z = make_float2(H.cAD * v.x, H.cAD * v.y);
+            }
+            part[H.out_off + ((H.sig * (uint32_t)b + H.tau) & (B - 1))] = z;
         }
     }
 }
@@ -324,7 +435,7 @@ __global__ void __launch_bounds__(256) k_bin_stream_2d(const float2 *__restrict_
         }
 #pragma unroll
         for (int g = 0; g < kGroup; g++)
-            if (g < ng) part[((int64_t)ch * nh + group0 + g) * B2 + (int64_t)r1 * B + r2] = acc[g];
+            if (g < ng) part[((int64_t)(group0 + g) * chunks + ch) * B2 + (int64_t)r1 * B + r2] = acc[g];
     }
 }
 
@@ -383,48 +494,232 @@ __global__ void k_bin_gather_2d(const float2 *__restrict__ x, int logn, const Ha
 }
 
 // ---------------------------------------------------------------------------------
-// Launch: job_host gives the static shape (tuning); dynamic = the job at B* written by
-// the controller (every form is launched and all but the matching one exit at once).
-// Partial sums go to P->d_part in residue order, [chunk][hash][bucket].
+// Launches
 // ---------------------------------------------------------------------------------
-void launch_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, const Job &job_host,
-                bool dynamic, const HashParam *hashes, int logB_static, cudaStream_t s)
+
+static GatherHash gather_hash(const atsfft_plan_s *P, const HashParam &hp, int b, int64_t out_off)
+{
+    const WindowParam &w = P->h_win[b];
+    GatherHash g;
+    g.sig = hp.sigma[0];
+    g.tau = hp.tau[0];
+    g.logB = b;
+    g.h = w.h;
+    g.k2 = w.k2;
+    g.log2c = w.log2c;
+    g.cAD = w.cA_D;
+    g.out_off = out_off;
+    g.warp_start = 0;
+    return g;
+}
+
+static StreamHash stream_hash(const atsfft_plan_s *P, const HashParam &hp, int b, int64_t out_off)
+{
+    StreamHash h;
+    memset(&h, 0, sizeof(h));
+    h.sinv = hp.sinv[0];
+    h.c0 = 0u - hp.sinv[0] * hp.tau[0];
+    h.tau = hp.tau[0];
+    if (b >= 0) {
+        const WindowParam &w = P->h_win[b];
+        h.logB = b;
+        h.h = w.h;
+        h.k2 = w.k2;
+        h.log2c = w.log2c;
+        h.cAD = w.cA_D;
+    }
+    h.out_off = out_off;
+    return h;
+}
+
+static int occupancy_grid(const atsfft_plan_s *P, const void *fn, size_t smem)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem);
+    if (per_sm < 1) per_sm = 1;
+    return P->num_sms * per_sm;
+}
+
+template <int NH, bool DYN>
+static void launch_stream(const atsfft_plan_s *P, const float2 *x, const StreamArgs &A,
+                          const Job *job_dev, size_t smem, int64_t items_hint, cudaStream_t s)
+{
+    const void *fn = (const void *)k_bin_stream<NH, DYN>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int64_t grid = occupancy_grid(P, fn, smem);
+    const int64_t need = (items_hint + 255) / 256;
+    if (items_hint > 0 && need < grid) grid = need;
+    k_bin_stream<NH, DYN><<<(unsigned)grid, 256, smem, s>>>(x, P->logn, A, job_dev, P->d_win,
+                                                            P->d_part);
+    count_launch(P);
+}
+
+template <bool DYN>
+static void launch_stream_nh(const atsfft_plan_s *P, const float2 *x, const StreamArgs &A,
+                             const Job *job_dev, size_t smem, int64_t items_hint, cudaStream_t s)
+{
+#define ATSFFT_NH(k) case k: launch_stream<k, DYN>(P, x, A, job_dev, smem, items_hint, s); break;
+    switch (A.nh) {
+    ATSFFT_NH(1) ATSFFT_NH(2) ATSFFT_NH(3) ATSFFT_NH(4) ATSFFT_NH(5) ATSFFT_NH(6) ATSFFT_NH(7)
+    ATSFFT_NH(8) ATSFFT_NH(9) ATSFFT_NH(10) ATSFFT_NH(11) ATSFFT_NH(12) ATSFFT_NH(13)
+    ATSFFT_NH(14) ATSFFT_NH(15) ATSFFT_NH(16)
+    default: break;
+    }
+#undef ATSFFT_NH
+}
+
+// Tuning: every B of the range, one hash each.  1D: the small-window hashes in one
+// gather launch, the large-window ones in one residue-stream pass with R = the largest
+// of their B; 2D: one launch per B.  Then all bucket FFTs in one batch.
+void launch_tuning(const atsfft_plan_s *P, const float2 *x, cudaStream_t s)
+{
+    int logB[kMaxLogB], chunks[kMaxLogB], nj = 0;
+    int64_t in_off[kMaxLogB], out_off[kMaxLogB];
+    if (P->ndim == 1) {
+        GatherArgs G;
+        G.njobs = 0;
+        G.total_warps = 0;
+        StreamArgs S;
+        memset(&S, 0, sizeof(S));
+        int rot_total = 0;
+        for (int b = P->b0; b <= P->b_hi; b++) {
+            if (P->h_tjob[b].stream) {
+                StreamHash &h = S.h[S.nh++];
+                h = stream_hash(P, P->h_tune[b], b, P->tpart_off[b]);
+                h.rot_off = rot_total;
+                rot_total += 2 * (int)(P->n >> b);
+            } else {
+                GatherHash &g = G.j[G.njobs++];
+                g = gather_hash(P, P->h_tune[b], b, P->tpart_off[b]);
+                g.warp_start = G.total_warps;
+                G.total_warps += (int64_t)1 << b;
+            }
+            logB[nj] = b;
+            chunks[nj] = P->tchunks[b];
+            in_off[nj] = P->tpart_off[b];
+            out_off[nj] = P->tz_off[b];
+            nj++;
+        }
+        if (G.njobs) {
+            const int64_t blocks = (G.total_warps + 7) / 8;
+            const int64_t cap = (int64_t)P->num_sms * 8;
+            k_bin_gather_tune<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(x, P->logn, G,
+                                                                                     P->d_part);
+            count_launch(P);
+        }
+        if (S.nh) {
+            S.logR = P->tstream_logR;
+            S.chunks = P->tstream_chunks;
+            launch_stream_nh<false>(P, x, S, nullptr, sizeof(float2) * rot_total,
+                                    ((int64_t)1 << S.logR) * S.chunks, s);
+        }
+    } else {
+        for (int b = P->b0; b <= P->b_hi; b++) {
+            launch_bin_2d(P, x, nullptr, P->h_tjob[b], false, P->d_tune + b, b,
+                          P->d_part + P->tpart_off[b], s);
+            logB[nj] = b;
+            chunks[nj] = P->tchunks[b];
+            in_off[nj] = P->tpart_off[b];
+            out_off[nj] = P->tz_off[b];
+            nj++;
+        }
+    }
+    launch_bucket_fft_batch(P, nj, logB, chunks, in_off, out_off, P->d_part, P->d_tz, s);
+}
+
+// Location + estimation hashes at the device-chosen B*: every form is launched, the
+// one matching the job runs.  1D stream launches take at most kMaxStream hashes each.
+void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, cudaStream_t s)
+{
+    const int nh = P->L_loc + P->L_est;
+    if (P->ndim == 1) {
+        // shared memory for the R_u table of the smallest B the stream form can take
+        size_t smem = 16;
+        for (int b = P->b0; b <= P->b_hi; b++)
+            if (P->h_tjob[b].stream) {
+                smem = sizeof(float2) * 2 * (size_t)(P->n >> b);
+                break;
+            }
+        for (int g0 = 0; g0 < nh; g0 += kMaxStream) {
+            StreamArgs S;
+            memset(&S, 0, sizeof(S));
+            S.nh = nh - g0 < kMaxStream ? nh - g0 : kMaxStream;
+            S.hash_base = g0;
+            for (int g = 0; g < S.nh; g++) S.h[g] = stream_hash(P, P->h_le[g0 + g], -1, 0);
+            launch_stream_nh<true>(P, x, S, job_dev, smem, 0, s);
+        }
+        prof_mark(P, 4, s);
+        const int groups = (nh + kGroup - 1) / kGroup;
+        dim3 grid(P->num_sms * kPersistCtas, groups);
+        k_bin_gather_1d<<<grid, 256, 0, s>>>(x, P->logn, P->d_le, nh, P->d_win, job_dev, 0,
+                                             P->d_part);
+        count_launch(P);
+    } else {
+        Job jl;
+        memset(&jl, 0, sizeof(jl));
+        jl.nh = nh;
+        launch_bin_2d(P, x, job_dev, jl, true, P->d_le, 0, P->d_part, s);
+    }
+}
+
+// One hash (inspection): bins into P->d_part and transforms into `out` (B or B^2 values).
+void launch_single_hash(const atsfft_plan_s *P, const float2 *x, int b, const HashParam &hp,
+                        const HashParam *hp_dev, float2 *out, cudaStream_t s)
+{
+    const Job &j = P->h_tjob[b];
+    int chunks = j.chunks;
+    if (P->ndim == 1) {
+        if (j.stream) {
+            StreamArgs S;
+            memset(&S, 0, sizeof(S));
+            S.nh = 1;
+            S.logR = b;
+            S.chunks = j.chunks;
+            S.h[0] = stream_hash(P, hp, b, 0);
+            launch_stream_nh<false>(P, x, S, nullptr, sizeof(float2) * 2 * (size_t)(P->n >> b),
+                                    ((int64_t)1 << b) * j.chunks, s);
+        } else {
+            GatherArgs G;
+            G.njobs = 1;
+            G.j[0] = gather_hash(P, hp, b, 0);
+            G.total_warps = (int64_t)1 << b;
+            const int64_t blocks = (G.total_warps + 7) / 8;
+            const int64_t cap = (int64_t)P->num_sms * 8;
+            k_bin_gather_tune<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(x, P->logn, G,
+                                                                                     P->d_part);
+            count_launch(P);
+            chunks = 1;
+        }
+    } else {
+        launch_bin_2d(P, x, nullptr, j, false, hp_dev, b, P->d_part, s);
+    }
+    const int64_t zero = 0;
+    launch_bucket_fft_batch(P, 1, &b, &chunks, &zero, &zero, P->d_part, out, s);
+}
+
+void launch_bin_2d(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, const Job &job_host,
+                   bool dynamic, const HashParam *hashes, int logB_static, float2 *part,
+                   cudaStream_t s)
 {
     const int persist = P->num_sms * kPersistCtas;
     const int groups = (job_host.nh + kGroup - 1) / kGroup;
     const Job *jd = dynamic ? job_dev : nullptr;
-    if (P->ndim == 1) {
-        if (dynamic || !job_host.stream) {
-            const int64_t want = ((int64_t)1 << logB_static) / 8 + 1;
-            dim3 grid(dynamic ? persist : (unsigned)(want < persist ? want : persist), groups);
-            k_bin_gather_1d<<<grid, 256, 0, s>>>(x, P->logn, hashes, job_host.nh, P->d_win, jd,
-                                                 logB_static, P->d_part);
-        }
-        if (dynamic || job_host.stream) {
-            // rotation table: 2D entries for the smallest D the stream form can see
-            int minb = dynamic ? P->b0 : logB_static;
-            size_t smem = sizeof(float2) * 2 * (size_t)(P->n >> minb);
-            if (smem > 64 * 1024) smem = 64 * 1024;   // stream form requires D <= 4096
-            cudaFuncSetAttribute(k_bin_stream_1d, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-            dim3 grid(persist, groups);
-            k_bin_stream_1d<<<grid, 256, smem, s>>>(x, P->logn, hashes, job_host.nh, P->d_win, jd,
-                                                    logB_static, job_host.chunks, P->d_part);
-        }
-    } else {
-        float2 *taps = P->d_fft_tmp;   // per-axis tap tables: nh x 2 x N (fits: nh * 2N <= nh * B^2)
-        k_taps_2d<<<P->num_sms * 2, 256, 0, s>>>(P->logn, hashes, job_host.nh, P->d_win, jd,
-                                                  logB_static, taps);
-        if (dynamic || !job_host.stream) {
-            dim3 grid(persist, job_host.nh);
-            k_bin_gather_2d<<<grid, 256, 0, s>>>(x, P->logn, hashes, job_host.nh, P->d_win, jd,
-                                                 logB_static, taps, P->d_part);
-        }
-        if (dynamic || job_host.stream) {
-            dim3 grid(persist, groups);
-            k_bin_stream_2d<<<grid, 256, 0, s>>>(x, P->logn, job_host.nh, jd, logB_static,
-                                                 job_host.chunks, taps, P->d_part);
-        }
+    float2 *taps = P->d_fft_tmp;   // per-axis tap tables: nh x 2 x N
+    k_taps_2d<<<P->num_sms * 2, 256, 0, s>>>(P->logn, hashes, job_host.nh, P->d_win, jd,
+                                              logB_static, taps);
+    count_launch(P);
+    if (dynamic || job_host.stream) {
+        dim3 grid(persist, groups);
+        k_bin_stream_2d<<<grid, 256, 0, s>>>(x, P->logn, job_host.nh, jd, logB_static,
+                                             job_host.chunks, taps, part);
+        count_launch(P);
+    }
+    if (dynamic) prof_mark(P, 4, s);
+    if (dynamic || !job_host.stream) {
+        dim3 grid(persist, job_host.nh);
+        k_bin_gather_2d<<<grid, 256, 0, s>>>(x, P->logn, hashes, job_host.nh, P->d_win, jd,
+                                             logB_static, taps, part);
+        count_launch(P);
     }
 }
 

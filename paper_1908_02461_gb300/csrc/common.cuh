@@ -23,6 +23,7 @@ constexpr int kSmallFFT = 4096;      // largest FFT done in one CTA
 constexpr int kMaxTrialsTrace = 64;
 constexpr int kHistBins = 4096;      // radix-select histogram bins (12-bit digits)
 constexpr int kPersistCtas = 4;      // persistent CTAs per SM
+constexpr int kPhases = 9;           // profiled phases of one exec (see atsfft.h)
 
 // Permutation of one hash (Def. 1), per axis.
 struct HashParam {
@@ -112,6 +113,9 @@ struct atsfft_plan_s {
     atsfft::WindowParam h_win[atsfft::kMaxLogB];
     int64_t resp_off[atsfft::kMaxLogB];
     atsfft::Job h_tjob[atsfft::kMaxLogB];
+    int64_t tpart_off[atsfft::kMaxLogB];          // tuning partial sums of each B in d_part
+    int tchunks[atsfft::kMaxLogB];                // partial blocks the FFT adds up per B
+    int tstream_logR, tstream_chunks;             // the 1D multi-B residue-stream pass
 
     atsfft::HashParam *d_tune, *d_le;
     atsfft::WindowParam *d_win;
@@ -140,11 +144,22 @@ struct atsfft_plan_s {
     atsfft::StatJob *d_tstat;     // tuning stat jobs (built at plan time)
     atsfft::StatJob *d_lstat;     // location stat jobs (written by the controller)
     int ntstat;
+
+    // profiling: events at phase boundaries (when enabled) and a launch counter
+    int prof;
+    cudaEvent_t ev[atsfft::kPhases + 1];
+    mutable int64_t launches;     // kernel launches enqueued by the last exec
 };
 
 namespace atsfft {
 
 atsfft_status cuda_status(cudaError_t e);
+
+inline void prof_mark(const atsfft_plan_s *P, int i, cudaStream_t s)
+{
+    if (P->prof) cudaEventRecord(P->ev[i], s);
+}
+inline void count_launch(const atsfft_plan_s *P, int k = 1) { P->launches += k; }
 
 inline int stats_slot_tune(int logB) { return logB; }
 inline int stats_slot_loc(int l) { return kMaxLogB + l; }
@@ -157,12 +172,20 @@ WindowParam window_shape(int64_t n, int logB, double alpha, double tol);
 Job make_job(const atsfft_plan_s *P, int logB, int nh);
 
 // bin.cu
-void launch_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, const Job &job_host,
-                bool dynamic, const HashParam *hashes, int logB_static, cudaStream_t s);
+void launch_tuning(const atsfft_plan_s *P, const float2 *x, cudaStream_t s);
+void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, cudaStream_t s);
+void launch_single_hash(const atsfft_plan_s *P, const float2 *x, int b, const HashParam &hp,
+                        const HashParam *hp_dev, float2 *out, cudaStream_t s);
+void launch_bin_2d(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, const Job &job_host,
+                   bool dynamic, const HashParam *hashes, int logB_static, float2 *part,
+                   cudaStream_t s);
 
 // fft.cu
-void launch_bucket_fft(const atsfft_plan_s *P, const Job *job_dev, bool dynamic, int logB_static,
-                       int nh_static, const float2 *part, float2 *out, cudaStream_t s);
+void launch_bucket_fft_dynamic(const atsfft_plan_s *P, const Job *job, const float2 *part,
+                               float2 *out, cudaStream_t s);
+void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB, const int *chunks,
+                             const int64_t *in_off, const int64_t *out_off, const float2 *part,
+                             float2 *out, cudaStream_t s);
 
 // select.cu
 void launch_stats(const atsfft_plan_s *P, const StatJob *jobs, int njobs, int64_t max_nb,

@@ -107,6 +107,7 @@ void launch_estimate(const atsfft_plan_s *P, const int64_t *d_loc, float2 *d_val
 {
     RespOffsets ro;
     for (int b = 0; b < kMaxLogB; b++) ro.off[b] = P->resp_off[b];
+    count_launch(P, 2);
     k_estimate<<<P->num_sms * 2, 128, 0, s>>>(d_loc, d_val, capacity, P->d_state, P->d_z, P->d_le,
                                               P->L_loc, P->L_est, P->d_resp, ro, P->ndim, P->logn);
     k_finalize<<<1, 32, 0, s>>>(P->d_state, capacity, d_count, d_k, d_status);
@@ -142,6 +143,7 @@ __global__ void k_unpermute(const float2 *spec, const HashParam *hp_dev, int ndi
 void launch_unpermute(const atsfft_plan_s *P, const float2 *spec, const HashParam *hash_dev,
                       int logB, float2 *out, cudaStream_t s)
 {
+    count_launch(P);
     k_unpermute<<<P->num_sms * 2, 256, 0, s>>>(spec, hash_dev, P->ndim, logB, out);
 }
 

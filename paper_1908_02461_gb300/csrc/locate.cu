@@ -107,6 +107,7 @@ void launch_compact(const atsfft_plan_s *P, int64_t *d_loc, int64_t capacity, cu
     const uint32_t need = (uint32_t)((P->L_loc + 1) / 2);
     const int64_t per_block = (int64_t)kCompactThreads * kWordsPerThread;
     const int64_t nblk = (P->nvote_words + per_block - 1) / per_block;
+    count_launch(P, 3);
     k_compact_count<<<(unsigned)nblk, kCompactThreads, 0, s>>>(P->d_votes, P->nvote_words, need,
                                                               P->d_blk);
     k_compact_scan<<<1, 1024, 0, s>>>(P->d_blk, nblk, P->d_state);

@@ -259,6 +259,8 @@ static void plan_free(atsfft_plan_s *P)
                     P->d_lstat};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    if (P->prof)
+        for (int i = 0; i <= kPhases; i++) cudaEventDestroy(P->ev[i]);
     delete P;
 }
 
@@ -346,6 +348,29 @@ extern "C" atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t
         Job j = make_job(P, b, nh_le);
         size_t need = (size_t)j.chunks * (size_t)nh_le * (size_t)nb;
         if (need > part) part = need;
+    }
+    // tuning partials: every B of the range gets its own region so all bins run before
+    // one batched FFT.  1D large-window B's share one residue-stream pass with modulus
+    // R = the largest of them; B's hash writes chunks(R) * R / B blocks of B values.
+    {
+        int64_t off = 0;
+        P->tstream_logR = -1;
+        for (int b = P->b0; b <= P->b_hi; b++)
+            if (ndim == 1 && P->h_tjob[b].stream) P->tstream_logR = b;
+        P->tstream_chunks = P->tstream_logR >= 0 ? P->h_tjob[P->tstream_logR].chunks : 1;
+        for (int b = P->b0; b <= P->b_hi; b++) {
+            int64_t nb = ndim == 1 ? ((int64_t)1 << b) : ((int64_t)1 << (2 * b));
+            P->tpart_off[b] = off;
+            if (ndim == 1 && P->h_tjob[b].stream) {
+                P->tchunks[b] = P->tstream_chunks << (P->tstream_logR - b);
+            } else if (ndim == 1) {
+                P->tchunks[b] = 1;
+            } else {
+                P->tchunks[b] = P->h_tjob[b].chunks;
+            }
+            off += nb * P->tchunks[b];
+        }
+        if ((size_t)off > part) part = (size_t)off;
     }
     P->part_elems = part;
     P->lmax_cap = ndim == 1 ? nb_max / 2 + 1 : nb_max / 4 + 1;

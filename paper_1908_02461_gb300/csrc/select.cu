@@ -231,6 +231,7 @@ void launch_stats(const atsfft_plan_s *P, const StatJob *jobs, int njobs, int64_
     const bool use_median = p.thr_med > 0;
     const float ratio = use_median ? (float)(p.thr_rel / p.thr_med * (1.0 - 1.0 / 1048576.0)) : 0.f;
     k_stats_energy<<<grid, 256, 0, s>>>(jobs, ndim, P->d_stats);
+    count_launch(P, use_median ? 10 : 2);
     if (use_median) {
         k_stats_above<<<grid, 256, 0, s>>>(jobs, ndim, P->d_stats, ratio);
         k_stats_decide<<<njobs, 256, 0, s>>>(jobs, ndim, P->d_stats, P->d_hist, 1);
@@ -312,6 +313,7 @@ __global__ void k_controller(int ndim, int b0, int b_hi, int tune_max, double de
 
 void launch_controller(const atsfft_plan_s *P, cudaStream_t s)
 {
+    count_launch(P);
     k_controller<<<1, 32, 0, s>>>(P->ndim, P->b0, P->b_hi, P->p.tune_max, P->p.delta1,
                                   P->p.delta2, P->d_stats, P->d_tjob, P->L_loc + P->L_est,
                                   P->L_loc, P->d_state, P->d_lstat, P->d_z,
@@ -470,6 +472,7 @@ __global__ void k_vote(const HashStats *stats, const int32_t *sel, int64_t cap,
 
 void launch_topnum_vote(const atsfft_plan_s *P, cudaStream_t s)
 {
+    count_launch(P, 2);
     k_topnum<<<P->L_loc, 256, 0, s>>>(P->d_lstat, P->d_stats, P->d_lmax, P->d_sel, P->lmax_cap,
                                       P->d_state, (float)(1.0 + P->p.tie_eta),
                                       (float)(1.0 - P->p.tie_eta), P->ndim);
