@@ -170,6 +170,87 @@ def cpu_baseline(sigs, budget_s=20.0):
             "sample": f"{done} transforms of the step's signals (k cycling), single-threaded FP64"}
 
 
+# ---- roofline model ---------------------------------------------------------------------
+# Algorithmic bytes (or sample-hash pairs) per launch of each single-kernel phase, from
+# the plan's defaults (alpha 0.5, tol 1e-6, 7 + 7 hashes, B range [2^4, n/16]); the
+# formulas are listed in the design doc.
+L_LOC, L_EST, NH = 7, 7, 14
+SFU_PER_SM_CLK, SMS, SM_MAX_MHZ = 16, 152, 2070.0
+
+
+def _window_h(n, B, alpha=0.5, tol=1e-6):
+    import math
+
+    q = math.sqrt(2 * math.log(1 / tol))
+    s = B * q / (math.pi * alpha)
+    h = math.ceil(s * q)
+    return min(h, n // 2 - 1)
+
+
+def _chunks(n, B):
+    return max(1, min((1 << 18) // B, n // B))
+
+
+def _stream(n, B):
+    return 5 * (2 * _window_h(n, B) + 1) >= n and n // B <= 4096
+
+
+def roofline(per_signal, traces, n):
+    peaks, src = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    pair_peak = SFU_PER_SM_CLK * SMS * SM_MAX_MHZ * 1e6 / 2.0   # 2 SFU ops per pair
+    logn = n.bit_length() - 1
+    Bs = [1 << b for b in range(4, logn - 4 + 1)]
+    rows = {}
+    for k, ph in per_signal.items():
+        Bstar = traces[k][-1][0]
+        D = n // Bstar
+        model = {}
+        gB = [B for B in Bs if not _stream(n, B)]
+        sB = [B for B in Bs if _stream(n, B)]
+        model["tune_gather"] = ("hbm", sum(8 * (2 * _window_h(n, B) + 1) + 8 * B for B in gB))
+        if sB:
+            R = max(sB)
+            model["tune_stream"] = ("alu", len(sB) * n)
+        model["tune_fft"] = ("hbm", sum(8 * B * (_chunks(n, max(sB)) * max(sB) // B if B in sB else 1)
+                                        + 8 * B + (16 * B if B > 4096 else 0) for B in Bs))
+        model["tune_tail"] = ("hbm", sum(8 * B + 4 * B + 12 * B for B in Bs))
+        if _stream(n, Bstar):
+            model["le_bin_stream"] = ("alu", NH * n)
+        else:
+            model["le_bin_gather"] = ("hbm", NH * 8 * (2 * _window_h(n, Bstar) + 1) + 8 * NH * Bstar)
+        ch = _chunks(n, Bstar) if _stream(n, Bstar) else 1
+        model["le_fft"] = ("hbm", 8 * NH * Bstar * (ch + 1) + (16 * NH * Bstar if Bstar > 4096 else 0))
+        model["loc_tail"] = ("hbm", L_LOC * Bstar * (8 + 4 + 12) + 3 * n)
+        for nm, (bound, units) in model.items():
+            t = ph[nm] / 1e3
+            if t <= 0:
+                continue
+            if bound == "alu":
+                ach = units / t / 1e9
+                rows.setdefault(nm, []).append((t, ach, ach / (pair_peak / 1e9), units, bound))
+            else:
+                ach = units / t / 1e9
+                rows.setdefault(nm, []).append((t, ach, ach / hbm, units, bound))
+    out = {}
+    for nm, lst in rows.items():
+        t = float(np.mean([r[0] for r in lst]))
+        ach = float(np.mean([r[1] for r in lst]))
+        out[nm] = {"bound": lst[0][4], "ms_per_launch": 1e3 * t, "achieved": ach,
+                   "unit": "Gpair/s" if lst[0][4] == "alu" else "GB/s",
+                   "frac": float(np.mean([r[2] for r in lst])), "launches_per_step": len(lst)}
+    # dominant single-kernel phase: largest total time per step
+    dom = max(out, key=lambda nm: out[nm]["ms_per_launch"] * out[nm]["launches_per_step"])
+    d = out[dom]
+    peak = pair_peak / 1e9 if d["bound"] == "alu" else hbm
+    roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": peak,
+            "unit": d["unit"], "frac": d["achieved"] / peak, "traffic": None,
+            "peak_source": ("derived: 16 SFU ops/clk/SM x 152 SMs x 2070 MHz / 2 SFU ops per "
+                            "sample-hash pair") if d["bound"] == "alu" else f"{src} hbm_gbs",
+            "ms_per_launch": d["ms_per_launch"]}
+    return roof, out
+
+
 def ncu_case(k):
     """Small fixed case for ncu captures: no timing, no other kernels than the exec's."""
     import torch
@@ -244,7 +325,7 @@ def main():
         step()
     torch.cuda.synchronize()
 
-    step_ms, phase_acc, launches = [], [], 0
+    step_ms, phase_acc, launches, stamp_acc = [], [], 0, []
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if ws > 1:
         torch.distributed.barrier()
@@ -262,6 +343,10 @@ def main():
                 ph, nl = p.phase_times()
                 phase_acc.append(ph)
                 launches += nl
+            if args.phases:
+                for p in plans:
+                    st_ = p.tail_stamps()
+                    stamp_acc.append([(b - st_[0]) / 1e3 for b in st_])
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if ws > 1:
@@ -285,27 +370,9 @@ def main():
     for i, k in enumerate(KS):
         rows = phase_acc[i::len(KS)]
         per_signal[k] = {nm: float(np.mean([r[nm] for r in rows])) for nm in names}
-    # the location/estimation binning pass (one kernel: residue stream or gather form)
     bin_ms = {k: per_signal[k]["le_bin_stream"] + per_signal[k]["le_bin_gather"] for k in KS}
-    peaks, peak_src = _peaks()
-    # algorithmic bytes of the residue-stream launch: the signal once (8 n) plus the
-    # bucket partial sums it writes (chunks x 14 hashes x B* x 8); see the design doc
-    ref_k = 1000
-    roof = None
-    try:
-        Bstar = [tr[-1][0] for tr in [plans[KS.index(ref_k)].last_trace()]][0]
-        chunks = max(1, min((1 << 18) // Bstar, n // Bstar))
-        alg_bytes = 8 * n + chunks * 14 * Bstar * 8
-        t_s = per_signal[ref_k]["le_bin_stream"] / 1e3
-        achieved = alg_bytes / t_s / 1e9
-        roof = {"kernel": "k_bin_stream_1d (location+estimation binning, 14 hashes at B*=%d, k=%d)"
-                % (Bstar, ref_k),
-                "bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": achieved / peaks.get("hbm_gbs"),
-                "traffic": None, "peak_source": peak_src,
-                "algorithmic_bytes": alg_bytes, "ms_per_launch": t_s * 1e3}
-    except Exception as e:  # noqa: BLE001
-        roof = {"error": str(e)}
+    traces = {k: p.last_trace() for k, p in zip(KS, plans)}
+    roof, phase_rooflines = roofline(per_signal, traces, n)
 
     # ---- end to end through the C ABI with host buffers -----------------------------
     host_out = [dict(loc=torch.empty(CAPACITY, dtype=torch.int64).pin_memory(),
@@ -350,6 +417,9 @@ def main():
     if args.phases and rank == 0:
         print(json.dumps({"per_signal_phase_ms": per_signal, "mean_phase_ms": mean_phase},
                          indent=1), file=sys.stderr)
+        for i, k in enumerate(KS):
+            print("tail stamps us k=%d:" % k, [round(v, 1) for v in stamp_acc[-len(KS) + i]],
+                  file=sys.stderr)
     for p in plans:
         p.close()
     if ws > 1:
@@ -370,6 +440,7 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roof,
+        "phase_rooflines": phase_rooflines,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }

@@ -120,12 +120,13 @@ atsfft_status atsfft_last_trace(atsfft_plan_t plan, int64_t *h_B, int64_t *h_k, 
                                 int *h_ntrials, void *stream);
 
 /* Turns per-phase CUDA events on (1) or off (0) for later execs of this plan.  The
- * nine phases of one exec, in order: 0 tuning binning + bucket FFTs, 1 tuning
- * statistics, 2 controller, 3 binning of the location/estimation hashes in the
- * residue-stream form (1D; 2D: tap tables + stream form), 4 the same in the gather
- * form, 5 their bucket FFTs, 6 location statistics, 7 top-num cutoff, votes and
- * compaction, 8 estimation and median.  A form or shape that does not apply to B*
- * exits at once, so its phase measures only an empty launch. */
+ * eight phases of one exec, in order: 0 tuning binning in the gather form (1D; 2D: the
+ * whole tuning binning), 1 tuning binning in the residue-stream form (1D), 2 tuning
+ * bucket FFTs, 3 tuning statistics and controller, 4 binning of the location/estimation
+ * hashes in the residue-stream form (1D; 2D: tap tables + stream form), 5 the same in
+ * the gather form, 6 their bucket FFTs, 7 location statistics, top-num cutoff, votes,
+ * compaction, estimation and median.  A form or shape that does not apply exits at once,
+ * so its phase measures only an empty launch. */
 atsfft_status atsfft_set_profiling(atsfft_plan_t plan, int on);
 
 /* After an exec: per-phase device times in ms (h_ms[max_phases], read only if profiling
@@ -133,6 +134,12 @@ atsfft_status atsfft_set_profiling(atsfft_plan_t plan, int on);
  * kernel launches that exec enqueued (h_launches may be NULL). */
 atsfft_status atsfft_phase_times(atsfft_plan_t plan, float *h_ms, int max_phases, int *h_nphases,
                                  int64_t *h_launches, void *stream);
+
+/* Diagnostics after an exec: device time stamps (ns, %globaltimer) taken at the start
+ * of the two cooperative tail kernels and at every grid barrier inside them, in the
+ * order they happened (at most 32).  Synchronises `stream`. */
+atsfft_status atsfft_tail_stamps(atsfft_plan_t plan, uint64_t *h_ns, int max_stamps,
+                                 int *h_nstamps, void *stream);
 
 #ifdef __cplusplus
 }

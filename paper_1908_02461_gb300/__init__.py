@@ -29,6 +29,7 @@ from ._lib import (  # noqa: F401
     atsfft_plan,
     atsfft_set_profiling,
     atsfft_status_string,
+    atsfft_tail_stamps,
     atsfft_window_response,
 )
 from .build import build  # noqa: F401
@@ -142,6 +143,17 @@ class Plan:
         if st != OK:
             raise ATSFFTError(st, "atsfft_phase_times")
         return dict(zip(PHASES[:nph], ms[:nph].tolist())), nl
+
+    def tail_stamps(self):
+        """Device ns stamps of the last exec's tail kernels (starts and barriers)."""
+        import numpy as np
+        import torch
+
+        buf = np.zeros(32, dtype=np.uint64)
+        st, n = atsfft_tail_stamps(self.handle, buf, 32, torch.cuda.current_stream().cuda_stream)
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_tail_stamps")
+        return buf[:n].tolist()
 
     def last_trace(self):
         import numpy as np

@@ -35,10 +35,10 @@ class atsfft_params(C.Structure):
 EXPORTED = ["atsfft_default_params", "atsfft_plan", "atsfft_exec", "atsfft_exec_2d",
             "atsfft_destroy", "atsfft_status_string", "atsfft_hash_spectrum",
             "atsfft_window_response", "atsfft_last_trace", "atsfft_set_profiling",
-            "atsfft_phase_times"]
+            "atsfft_phase_times", "atsfft_tail_stamps"]
 
-PHASES = ["tune_bin_fft", "tune_stats", "controller", "le_bin_stream", "le_bin_gather",
-          "le_fft", "le_stats", "locate", "estimate"]
+PHASES = ["tune_gather", "tune_stream", "tune_fft", "tune_tail", "le_bin_stream", "le_bin_gather",
+          "le_fft", "loc_tail"]
 
 _lib = None
 
@@ -76,6 +76,8 @@ def load(path: str | None = None):
     L.atsfft_set_profiling.restype = i32
     L.atsfft_phase_times.argtypes = [vp, vp, i32, P(i32), P(i64), vp]
     L.atsfft_phase_times.restype = i32
+    L.atsfft_tail_stamps.argtypes = [vp, vp, i32, P(i32), vp]
+    L.atsfft_tail_stamps.restype = i32
     if path is None:
         _lib = L
     return L
@@ -154,3 +156,10 @@ def atsfft_phase_times(plan, h_ms, max_phases, stream=None):
     st = load().atsfft_phase_times(plan, _ptr(h_ms), max_phases, C.byref(nph), C.byref(nl),
                                    _ptr(stream))
     return st, nph.value, nl.value
+
+
+def atsfft_tail_stamps(plan, h_ns, max_stamps, stream=None):
+    """Returns (status, number of stamps)."""
+    n = C.c_int()
+    st = load().atsfft_tail_stamps(plan, _ptr(h_ns), max_stamps, C.byref(n), _ptr(stream))
+    return st, n.value

@@ -2,7 +2,7 @@
 // enqueued on the caller's stream with no host synchronisation.
 //
 //  tuning   : the hash of every B in the plan's range is evaluated (bin, bucket FFT,
-//             energies, threshold, local-maximum count); the controller kernel then walks
+//             energies, threshold, local-maximum count); the controller then walks
 //             Eqs. (12)/(14) over those counts on the device and fixes B*, k*.  Because the
 //             stop reading visits every B at most once, evaluating all of them up front
 //             gives exactly the sequential trajectory while replacing a chain of dependent
@@ -31,25 +31,17 @@ static atsfft_status exec_common(atsfft_plan_t P, int ndim, const void *d_x, int
     P->launches = 0;
     launch_reset(P, s);
     prof_mark(P, 0, s);
-    launch_tuning(P, x, s);
-    prof_mark(P, 1, s);
-    const int64_t nb_hi = ndim == 1 ? ((int64_t)1 << P->b_hi) : ((int64_t)1 << (2 * P->b_hi));
-    launch_stats(P, P->d_tstat, P->ntstat, nb_hi, s);
-    prof_mark(P, 2, s);
-    launch_controller(P, s);
+    launch_tuning(P, x, s);       // marks phases 1 and 2 between its kernels
     prof_mark(P, 3, s);
+    launch_tune_tail(P, s);
+    prof_mark(P, 4, s);
     const Job *jd = &P->d_state->job;
-    launch_le_bin(P, x, jd, s);   // marks phase 4 after the stream-form kernel
-    prof_mark(P, 5, s);
-    launch_bucket_fft_dynamic(P, jd, P->d_part, P->d_z, s);
+    launch_le_bin(P, x, jd, s);   // marks phase 5 after the stream-form kernel
     prof_mark(P, 6, s);
-    launch_stats(P, P->d_lstat, P->L_loc, nb_hi, s);
+    launch_bucket_fft_dynamic(P, jd, P->d_part, P->d_z, s);
     prof_mark(P, 7, s);
-    launch_topnum_vote(P, s);
-    launch_compact(P, d_loc, capacity, s);
+    launch_loc_tail(P, d_loc, (float2 *)d_val, capacity, d_count, d_k, d_status, s);
     prof_mark(P, 8, s);
-    launch_estimate(P, d_loc, (float2 *)d_val, capacity, d_count, d_k, d_status, s);
-    prof_mark(P, 9, s);
     return cuda_status(cudaGetLastError());
 }
 
@@ -139,5 +131,20 @@ extern "C" atsfft_status atsfft_phase_times(atsfft_plan_t P, float *h_ms, int ma
         e = cudaEventElapsedTime(&h_ms[i], P->ev[i], P->ev[i + 1]);
         if (e != cudaSuccess) return cuda_status(e);
     }
+    return ATSFFT_OK;
+}
+
+extern "C" atsfft_status atsfft_tail_stamps(atsfft_plan_t P, uint64_t *h_ns, int max_stamps,
+                                            int *h_nstamps, void *stream)
+{
+    if (!P || !h_nstamps || max_stamps < 0 || (max_stamps > 0 && !h_ns)) return ATSFFT_E_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    GridBarrier gb;
+    e = cudaMemcpy(&gb, &P->d_state->bar, sizeof(gb), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int n = gb.nstamp < 32 ? (int)gb.nstamp : 32;
+    *h_nstamps = n;
+    for (int i = 0; i < n && i < max_stamps; i++) h_ns[i] = gb.stamp[i];
     return ATSFFT_OK;
 }

@@ -157,23 +157,33 @@ struct StreamArgs {
 
 // Window constants of one hash inside the inner loop: uniform across the CTA.
 struct TapConst {
-    int h, logB, roff;
+    uint32_t c0h;        // c0 + h: t' = sigma^{-1} a + c0 + h (mod n) is in the window iff t' <= 2h
+    uint32_t two_h;
+    int h, logB;
+    int roff;
     uint32_t rmask;
     float k2, l2c;
 };
 
+// Exact int -> float for |v| < 2^22 without the conversion unit: the float with bits
+// 0x4B400000 + v is 1.5 * 2^23 + v.
+__device__ __forceinline__ float small_int_to_float(int v)
+{
+    return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
+
 // One (sample, hash) pair: t = sigma^{-1}(a - tau) mod n as a signed integer, window test
 // as a select (no branch), f_t R_u, complex multiply-add.  ts = 0 (centre tap, bucket 0
 // only) yields inf, which stays in bucket 0's discarded accumulator.
+template <bool SMALL_N>
 __device__ __forceinline__ void tap_mac(float2 &acc, float2 v, uint32_t a, uint32_t sinv,
-                                        uint32_t c0, uint32_t mask, int sh, const TapConst &T,
-                                        const float2 *rot)
+                                        uint32_t mask, const TapConst &T, const float2 *rot)
 {
-    const uint32_t t = (sinv * a + c0) & mask;
-    const int ts = (int)(t << sh) >> sh;
-    const bool in = (ts <= T.h) & (ts >= -T.h);
+    const uint32_t tsh = (sinv * a + T.c0h) & mask;
+    const bool in = tsh <= T.two_h;
+    const int ts = (int)tsh - T.h;
     const float2 Ru = rot[T.roff + ((uint32_t)(ts >> T.logB) & T.rmask)];
-    const float tf = (float)ts;
+    const float tf = SMALL_N ? small_int_to_float(ts) : (float)ts;
     float f = fast_exp2(fmaf(-T.k2 * tf, tf, T.l2c)) * fast_rcp(tf);
     f = in ? f : 0.f;
     const float cr = f * Ru.x, ci = f * Ru.y;
@@ -220,16 +230,19 @@ __global__ void __launch_bounds__(256) k_bin_stream(const float2 *__restrict__ x
     TapConst T[NH];
 #pragma unroll
     for (int g = 0; g < NH; g++) {
-        if (DYN) {
-            T[g] = TapConst{w.h, logR, 0, 2 * (n >> logR) - 1, w.k2, w.log2c};
-        } else {
-            const StreamHash &H = A.h[g];
-            T[g] = TapConst{H.h, H.logB, H.rot_off, 2 * (n >> H.logB) - 1, H.k2, H.log2c};
-        }
+        const int h = DYN ? w.h : A.h[g].h;
+        T[g].c0h = A.h[g].c0 + (uint32_t)h;
+        T[g].two_h = 2u * (uint32_t)h;
+        T[g].h = h;
+        T[g].logB = DYN ? logR : A.h[g].logB;
+        T[g].roff = DYN ? 0 : A.h[g].rot_off;
+        T[g].rmask = 2 * (n >> T[g].logB) - 1;
+        T[g].k2 = DYN ? w.k2 : A.h[g].k2;
+        T[g].l2c = DYN ? w.log2c : A.h[g].log2c;
     }
     const uint32_t rows = (n >> logR) / (uint32_t)chunks;
     const int64_t items = (int64_t)R * chunks;
-    const int sh = 32 - logn;
+    const bool small_n = logn <= 23;
     for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
          it += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t r = (uint32_t)(it & (R - 1));
@@ -238,13 +251,20 @@ __global__ void __launch_bounds__(256) k_bin_stream(const float2 *__restrict__ x
 #pragma unroll
         for (int g = 0; g < NH; g++) acc[g] = make_float2(0.f, 0.f);
         const uint32_t j0 = c * rows;
-#pragma unroll 2
-        for (uint32_t j = j0; j < j0 + rows; j++) {
-            const uint32_t a = r + (j << logR);
-            const float2 v = __ldg(&x[a]);
+        if (small_n) {
+            for (uint32_t j = j0; j < j0 + rows; j++) {
+                const uint32_t a = r + (j << logR);
+                const float2 v = __ldg(&x[a]);
 #pragma unroll
-            for (int g = 0; g < NH; g++)
-                tap_mac(acc[g], v, a, A.h[g].sinv, A.h[g].c0, mask, sh, T[g], rot);
+                for (int g = 0; g < NH; g++) tap_mac<true>(acc[g], v, a, A.h[g].sinv, mask, T[g], rot);
+            }
+        } else {
+            for (uint32_t j = j0; j < j0 + rows; j++) {
+                const uint32_t a = r + (j << logR);
+                const float2 v = __ldg(&x[a]);
+#pragma unroll
+                for (int g = 0; g < NH; g++) tap_mac<false>(acc[g], v, a, A.h[g].sinv, mask, T[g], rot);
+            }
         }
 #pragma unroll
         for (int g = 0; g < NH; g++) {
@@ -607,13 +627,16 @@ void launch_tuning(const atsfft_plan_s *P, const float2 *x, cudaStream_t s)
                                                                                      P->d_part);
             count_launch(P);
         }
+        prof_mark(P, 1, s);
         if (S.nh) {
             S.logR = P->tstream_logR;
             S.chunks = P->tstream_chunks;
             launch_stream_nh<false>(P, x, S, nullptr, sizeof(float2) * rot_total,
                                     ((int64_t)1 << S.logR) * S.chunks, s);
         }
+        prof_mark(P, 2, s);
     } else {
+        prof_mark(P, 1, s);
         for (int b = P->b0; b <= P->b_hi; b++) {
             launch_bin_2d(P, x, nullptr, P->h_tjob[b], false, P->d_tune + b, b,
                           P->d_part + P->tpart_off[b], s);
@@ -623,6 +646,7 @@ void launch_tuning(const atsfft_plan_s *P, const float2 *x, cudaStream_t s)
             out_off[nj] = P->tz_off[b];
             nj++;
         }
+        prof_mark(P, 2, s);
     }
     launch_bucket_fft_batch(P, nj, logB, chunks, in_off, out_off, P->d_part, P->d_tz, s);
 }
@@ -648,7 +672,7 @@ void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
             for (int g = 0; g < S.nh; g++) S.h[g] = stream_hash(P, P->h_le[g0 + g], -1, 0);
             launch_stream_nh<true>(P, x, S, job_dev, smem, 0, s);
         }
-        prof_mark(P, 4, s);
+        prof_mark(P, 5, s);
         const int groups = (nh + kGroup - 1) / kGroup;
         dim3 grid(P->num_sms * kPersistCtas, groups);
         k_bin_gather_1d<<<grid, 256, 0, s>>>(x, P->logn, P->d_le, nh, P->d_win, job_dev, 0,
@@ -714,7 +738,7 @@ void launch_bin_2d(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
                                              job_host.chunks, taps, part);
         count_launch(P);
     }
-    if (dynamic) prof_mark(P, 4, s);
+    if (dynamic) prof_mark(P, 5, s);
     if (dynamic || !job_host.stream) {
         dim3 grid(persist, job_host.nh);
         k_bin_gather_2d<<<grid, 256, 0, s>>>(x, P->logn, hashes, job_host.nh, P->d_win, jd,

@@ -23,7 +23,7 @@ constexpr int kSmallFFT = 4096;      // largest FFT done in one CTA
 constexpr int kMaxTrialsTrace = 64;
 constexpr int kHistBins = 4096;      // radix-select histogram bins (12-bit digits)
 constexpr int kPersistCtas = 4;      // persistent CTAs per SM
-constexpr int kPhases = 9;           // profiled phases of one exec (see atsfft.h)
+constexpr int kPhases = 8;           // profiled phases of one exec (see atsfft.h)
 
 // Permutation of one hash (Def. 1), per axis.
 struct HashParam {
@@ -80,8 +80,18 @@ struct HashStats {
     uint32_t pad[7];
 };
 
+// Grid-wide barrier of the cooperative kernels (tail.cu).
+struct GridBarrier {
+    unsigned count;
+    unsigned gen;
+    int err;
+    unsigned nstamp;
+    unsigned long long stamp[32];   // %globaltimer at kernel starts and barrier releases
+};
+
 // Device-resident state of one exec.
 struct ExecState {
+    GridBarrier bar;
     int32_t b_star;        // log2 B* (per axis)
     int32_t status;
     int64_t k_star;
@@ -187,20 +197,13 @@ void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB,
                              const int64_t *in_off, const int64_t *out_off, const float2 *part,
                              float2 *out, cudaStream_t s);
 
-// select.cu
-void launch_stats(const atsfft_plan_s *P, const StatJob *jobs, int njobs, int64_t max_nb,
-                  cudaStream_t s);
-void launch_controller(const atsfft_plan_s *P, cudaStream_t s);
-void launch_topnum_vote(const atsfft_plan_s *P, cudaStream_t s);
+// tail.cu
+void launch_tune_tail(const atsfft_plan_s *P, cudaStream_t s);
+void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, int64_t capacity,
+                     int64_t *d_count, int64_t *d_k, int32_t *d_status, cudaStream_t s);
+
+// inspect.cu
 void launch_reset(const atsfft_plan_s *P, cudaStream_t s);
-
-// locate.cu
-void launch_compact(const atsfft_plan_s *P, int64_t *d_loc, int64_t capacity, cudaStream_t s);
-
-// estimate.cu
-void launch_estimate(const atsfft_plan_s *P, const int64_t *d_loc, float2 *d_val,
-                     int64_t capacity, int64_t *d_count, int64_t *d_k, int32_t *d_status,
-                     cudaStream_t s);
 void launch_unpermute(const atsfft_plan_s *P, const float2 *spec, const HashParam *hash_dev,
                       int logB, float2 *out, cudaStream_t s);
 

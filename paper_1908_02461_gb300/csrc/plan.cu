@@ -396,7 +396,10 @@ extern "C" atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t
     A((void **)&P->d_lmax, sizeof(int32_t) * P->L_loc * P->lmax_cap);
     A((void **)&P->d_sel, sizeof(int32_t) * P->L_loc * P->lmax_cap);
     A((void **)&P->d_votes, sizeof(uint32_t) * P->nvote_words);
-    A((void **)&P->d_blk, sizeof(uint32_t) * (P->nblk + 1));
+    // per-block counts of the compaction (cooperative grid: at most a few blocks per SM)
+    A((void **)&P->d_blk, sizeof(uint32_t) * (size_t)((P->nblk + 1) > (int64_t)P->num_sms * 32
+                                                          ? (P->nblk + 1)
+                                                          : (int64_t)P->num_sms * 32));
     A((void **)&P->d_state, sizeof(ExecState));
     A((void **)&P->d_tjob, sizeof(Job) * kMaxLogB);
     A((void **)&P->d_tstat, sizeof(StatJob) * kMaxLogB);

@@ -1,0 +1,1013 @@
+// tail.cu -- everything after the bucket FFTs, as two cooperative (persistent) kernels
+// whose phases are separated by a grid barrier:
+//
+//   k_tune_tail : bucket energies, threshold, local-maximum counts of every tuning trial
+//                 (Section III-A), then the controller walk over Eqs. (12)/(14)
+//                 (Algorithm 2) by one thread, which fixes B*, k* and the jobs at B*.
+//   k_loc_tail  : the same statistics for the location hashes at B* (with the maxima
+//                 listed), the top-num cutoff (Algorithm 1 "find num largest"), votes
+//                 (reverse hash), the ordered compaction of coordinates with votes >=
+//                 ceil(L_loc/2) (Section II-B), the estimates of Eq. (11) with their
+//                 componentwise median, and the caller's status words.
+//
+// Threshold T = max(thr_rel * maxE, thr_med * medianE), median = element floor(nb/2) of
+// the ascending energies.  With #{E > X'} <= nb - floor(nb/2) - 1 for
+// X' = (thr_rel/thr_med) maxE (1 - 2^-20) the median is <= X' and T = thr_rel * maxE
+// exactly, so the local maxima are found with that T at once; only when the count says
+// the median could matter is it found exactly (three-digit radix select on the energy
+// bit patterns) and the maxima recounted.
+//
+// The grid barrier spins on a generation word with a bounded number of polls; when the
+// bound runs out the block records ATSFFT_E_CUDA in the exec state and every block
+// returns at its next barrier (cooperative launch makes all blocks co-resident, so a
+// timeout means the device misbehaved, not a lost block).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace atsfft {
+
+constexpr uint32_t kBarrierPolls = 1u << 24;   // ~1 s at 64 ns per poll
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Diagnostic time stamp (kernel start or barrier release), kept in the exec state.
+__device__ __forceinline__ void stamp(GridBarrier *gb)
+{
+    const unsigned i = atomicAdd(&gb->nstamp, 1u);
+    if (i < 32) gb->stamp[i] = global_ns();
+}
+
+__device__ bool grid_sync(GridBarrier *gb, int *status)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *vgen = &gb->gen;
+        volatile int *verr = &gb->err;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&gb->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            stamp(gb);
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            uint32_t polls = 0;
+            while (*vgen == g && !*verr) {
+                if (++polls > kBarrierPolls) {
+                    atomicExch(&gb->err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*verr) {
+            ok = 0;
+            *status = ATSFFT_E_CUDA;
+        }
+    }
+    __syncthreads();
+    return ok;
+}
+
+__device__ __forceinline__ int64_t nb_of(int ndim, int logB)
+{
+    return ndim == 1 ? ((int64_t)1 << logB) : ((int64_t)1 << (2 * logB));
+}
+
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+constexpr int64_t kTask = 4096;   // buckets per statistics task
+
+__device__ float block_max(float v)
+{
+    __shared__ float red[8];
+    v = warp_max(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float m = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) m = fmaxf(m, red[i]);
+    return m;
+}
+
+__device__ uint32_t block_sum(uint32_t v)
+{
+    __shared__ uint32_t red[8];
+    v = warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += red[i];
+    return t;
+}
+
+// Does a bucket of energy ec dominate its neighbour (displacement d1, d2) of energy em?
+// Beyond the relative tie band the larger wins; inside it the neighbour loses iff it
+// lies before the bucket in cyclic order (d1 < 0, or d1 == 0 and d2 < 0).
+__device__ __forceinline__ bool dominates(float ec, float em, float up, int d1, int d2)
+{
+    if (ec > up * em) return true;
+    if (em > up * ec) return false;
+    return d1 < 0 || (d1 == 0 && d2 < 0);
+}
+
+struct StatsParams {
+    int ndim;
+    float thr_rel, thr_med, up, ratio;   // up = 1 + eta; ratio = X' / maxE
+    int use_median;
+    HashStats *stats;
+    uint32_t *hist;
+    int32_t *lists;
+    int64_t cap;
+};
+
+__device__ float threshold_of(const HashStats &st, const StatsParams &S)
+{
+    float T = S.thr_rel * __uint_as_float(st.max_bits);
+    if (st.need_median) T = fmaxf(T, S.thr_med * __uint_as_float(st.med_bits));
+    return T;
+}
+
+// Local maxima of one job over P-indices j = j0, j0 + step, ... < j1 (bucket
+// c = sigma j, neighbours at j +- sigma'); returns how many energies exceed X.
+__device__ uint32_t localmax_range(const StatJob &J, const StatsParams &S, float T, int64_t j0,
+                                   int64_t j1, int64_t step, float X)
+{
+    HashStats &st = S.stats[J.slot];
+    const int logB = J.logB;
+    const uint32_t B = 1u << logB, mask = B - 1;
+    const float *E = J.energy;
+    const uint32_t s1 = J.hash->sigma[0] & mask, p1 = J.hash->sinv[0] & mask;
+    const uint32_t s2 = J.hash->sigma[1] & mask, p2 = J.hash->sinv[1] & mask;
+    uint32_t above = 0;
+    for (int64_t j = j0; j < j1; j += step) {
+        const float e = E[j];
+        above += e > X;
+        if (!(e > T)) continue;
+        bool ok = true;
+        int32_t c;
+        if (S.ndim == 1) {
+            const uint32_t jj = (uint32_t)j;
+            c = (int32_t)((s1 * jj) & mask);
+            ok = dominates(e, E[(jj - p1) & mask], S.up, 0, -1) &&
+                 dominates(e, E[(jj + p1) & mask], S.up, 0, 1);
+        } else {
+            const uint32_t jA = (uint32_t)(j >> logB), jB = (uint32_t)(j & mask);
+            c = (int32_t)((((s1 * jA) & mask) << logB) | ((s2 * jB) & mask));
+            for (int d1 = -1; d1 <= 1 && ok; d1++)
+                for (int d2 = -1; d2 <= 1 && ok; d2++) {
+                    if (d1 == 0 && d2 == 0) continue;
+                    const uint32_t m1 = (jA + (uint32_t)d1 * p1) & mask;
+                    const uint32_t m2 = (jB + (uint32_t)d2 * p2) & mask;
+                    ok = dominates(e, E[((int64_t)m1 << logB) | m2], S.up, d1, d2);
+                }
+        }
+        if (ok) {
+            const uint32_t pos = atomicAdd(&st.nmax, 1u);
+            if (J.list >= 0 && pos < S.cap) S.lists[(int64_t)J.list * S.cap + pos] = c;
+        }
+    }
+    return above;
+}
+
+__device__ void localmax_job(const StatJob &J, const StatsParams &S, float T, int64_t gtid,
+                             int64_t gthreads, uint32_t *above_out, float X)
+{
+    (void)above_out;
+    localmax_range(J, S, T, gtid, nb_of(S.ndim, J.logB), gthreads, X);
+}
+
+// digit 0: bits [20, 32), digit 1: [8, 20), digit 2: [0, 8)
+__device__ __forceinline__ void digit_range(int digit, int &lo, int &width)
+{
+    lo = digit == 0 ? 20 : (digit == 1 ? 8 : 0);
+    width = digit == 2 ? 8 : 12;
+}
+
+// Whole block (blockDim.x = 256): exclusive prefix sum of one value per thread;
+// *total (shared) receives the block sum.
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total)
+{
+    __shared__ uint32_t wtot[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) wtot[w] = incl;
+    __syncthreads();
+    uint32_t before = incl - v;
+    uint32_t all = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+        if (i < w) before += wtot[i];
+        all += wtot[i];
+    }
+    if (total && threadIdx.x == 0) *total = all;
+    __syncthreads();
+    return before;
+}
+
+// Whole block (blockDim.x = 256): find the bin b of hist[0..nbins) (shared or global)
+// with cum(b) <= rank < cum(b) + hist[b], where cum is the exclusive prefix sum.  The
+// block's thread t sums bins [t*per, (t+1)*per); a warp-shuffle scan gives each thread
+// its offset; the owner walks its few bins.  Result in *bin, *rem (shared), after a sync.
+__device__ void block_find_rank(const uint32_t *hist, int nbins, uint32_t rank, uint32_t *bin,
+                                uint32_t *rem)
+{
+    __shared__ uint32_t wtot[8];
+    const int per = nbins >= 256 ? nbins / 256 : 1;
+    const int t = threadIdx.x;
+    uint32_t sum = 0;
+    if (t * per < nbins)
+        for (int k = 0; k < per; k++) sum += hist[t * per + k];
+    const int lane = t & 31, w = t >> 5;
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wtot[w] = incl;
+    __syncthreads();
+    uint32_t before = incl - sum;
+    for (int i = 0; i < w; i++) before += wtot[i];
+    if (sum && rank >= before && rank < before + sum) {
+        uint32_t cum = before;
+        for (int k = 0; k < per; k++) {
+            const uint32_t v = hist[t * per + k];
+            if (rank < cum + v) {
+                *bin = (uint32_t)(t * per + k);
+                *rem = rank - cum;
+                break;
+            }
+            cum += v;
+        }
+    }
+    __syncthreads();
+}
+
+constexpr int kSmallMedian = 8192;
+
+// Exact median (element floor(nb/2) of the ascending energies, as bits) of nb <= 8192
+// energies by one block: the values are staged in shared memory and selected with
+// three radix digits (11, 11, 10 bits) over their bit patterns.
+__device__ uint32_t block_median(const float *E, int nb)
+{
+    extern __shared__ uint32_t dsm[];   // phase scratch shared by the tail's phases
+    uint32_t *vals = dsm;               // kSmallMedian entries
+    uint32_t *hist = dsm + kSmallMedian; // 2048 entries
+    __shared__ uint32_t sh_prefix, sh_rank;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) vals[i] = __float_as_uint(E[i]);
+    if (threadIdx.x == 0) {
+        sh_prefix = 0;
+        sh_rank = (uint32_t)(nb / 2);
+    }
+    __syncthreads();
+    const int los[3] = {21, 10, 0}, widths[3] = {11, 11, 10};
+    for (int d = 0; d < 3; d++) {
+        const int lo = los[d], width = widths[d], hi = lo + width;
+        for (int b = threadIdx.x; b < (1 << width); b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        const uint32_t prefix = sh_prefix;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+            const uint32_t v = vals[i];
+            if (d == 0 || (v >> hi) == prefix) atomicAdd(&hist[(v >> lo) & ((1u << width) - 1)], 1u);
+        }
+        __syncthreads();
+        __shared__ uint32_t fb, fr;
+        block_find_rank(hist, 1 << width, sh_rank, &fb, &fr);
+        if (threadIdx.x == 0) {
+            sh_prefix = (prefix << width) | fb;
+            sh_rank = fr;
+        }
+        __syncthreads();
+    }
+    return sh_prefix;
+}
+
+// Local maxima of one job by one block (the recount after an exact median).
+__device__ void localmax_block(const StatJob &J, const StatsParams &S, float T)
+{
+    localmax_job(J, S, T, threadIdx.x, blockDim.x, nullptr, INFINITY);
+    __syncthreads();
+}
+
+// Energies, threshold and local maxima of njobs hashes.  Returns false if a barrier
+// failed.
+__device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &S,
+                             GridBarrier *gb, int *status)
+{
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+    // work split into tasks of kTask buckets over all jobs (prefix table in shared memory)
+    __shared__ int64_t tstart[kMaxLoops + kMaxLogB + 1];
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int jb = 0; jb < njobs; jb++) {
+            tstart[jb] = acc;
+            if (jobs[jb].active) acc += (nb_of(S.ndim, jobs[jb].logB) + kTask - 1) / kTask;
+        }
+        tstart[njobs] = acc;
+    }
+    __syncthreads();
+    const int64_t ntasks = tstart[njobs];
+    // A: energies and their maximum
+    for (int64_t task = blockIdx.x; task < ntasks; task += gridDim.x) {
+        int jb = 0;
+        while (task >= tstart[jb + 1]) jb++;
+        const StatJob &J = jobs[jb];
+        const int64_t nb = nb_of(S.ndim, J.logB);
+        const int64_t e0 = (task - tstart[jb]) * kTask;
+        const int64_t e1 = min(e0 + kTask, nb);
+        float m = 0.f;
+        for (int64_t j = e0 + threadIdx.x; j < e1; j += blockDim.x) {
+            const float2 v = J.spec[j];
+            const float e = v.x * v.x + v.y * v.y;
+            J.energy[j] = e;
+            m = fmaxf(m, e);
+        }
+        m = block_max(m);
+        if (threadIdx.x == 0 && m > 0.f) atomicMax(&S.stats[J.slot].max_bits, __float_as_uint(m));
+    }
+    if (!grid_sync(gb, status)) return false;
+    // B: local maxima with T = thr_rel * maxE, and the count deciding if the median matters
+    for (int64_t task = blockIdx.x; task < ntasks; task += gridDim.x) {
+        int jb = 0;
+        while (task >= tstart[jb + 1]) jb++;
+        const StatJob &J = jobs[jb];
+        HashStats &st = S.stats[J.slot];
+        const int64_t nb = nb_of(S.ndim, J.logB);
+        const int64_t e0 = (task - tstart[jb]) * kTask;
+        const int64_t e1 = min(e0 + kTask, nb);
+        const float M = __uint_as_float(st.max_bits);
+        const float X = S.use_median ? M * S.ratio : INFINITY;
+        uint32_t above = localmax_range(J, S, S.thr_rel * M, e0 + threadIdx.x, e1, blockDim.x, X);
+        above = block_sum(above);
+        if (threadIdx.x == 0 && above) atomicAdd(&st.above, above);
+    }
+    if (!grid_sync(gb, status)) return false;
+    // C: exact median where it can matter, then recount those hashes' maxima.
+    // C1: hashes with at most kSmallMedian buckets, one block each, in shared memory.
+    bool any_small = false, any_large = false;
+    for (int jb = 0; jb < njobs; jb++) {
+        const StatJob &J = jobs[jb];
+        if (!J.active) continue;
+        const HashStats &st = S.stats[J.slot];
+        const int64_t nb = nb_of(S.ndim, J.logB);
+        if (S.use_median && (int64_t)st.above > nb - nb / 2 - 1) {
+            if (nb <= kSmallMedian) any_small = true;
+            else any_large = true;
+        }
+    }
+    if (!any_small && !any_large) return true;   // uniform: every block read the same counts
+    if (any_small) {
+        for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
+            const StatJob &J = jobs[jb];
+            if (!J.active) continue;
+            HashStats &st = S.stats[J.slot];
+            const int64_t nb = nb_of(S.ndim, J.logB);
+            if (nb > kSmallMedian || !((int64_t)st.above > nb - nb / 2 - 1)) continue;
+            const uint32_t med = block_median(J.energy, (int)nb);
+            if (threadIdx.x == 0) {
+                st.need_median = 1;
+                st.med_bits = med;
+                st.nmax = 0;
+            }
+            __syncthreads();
+            localmax_block(J, S, threshold_of(st, S));
+        }
+    }
+    if (!any_large) return grid_sync(gb, status);
+    // C2: larger hashes, grid-wide radix select
+    extern __shared__ uint32_t dsm[];
+    uint32_t *h = dsm;   // kHistBins entries
+    for (int digit = 0; digit < 3; digit++) {
+        int lo, width;
+        digit_range(digit, lo, width);
+        const int hi = lo + width;
+        for (int jb = 0; jb < njobs; jb++) {
+            const StatJob &J = jobs[jb];
+            if (!J.active) continue;
+            HashStats &st = S.stats[J.slot];
+            const int64_t nb = nb_of(S.ndim, J.logB);
+            if (nb <= kSmallMedian || !((int64_t)st.above > nb - nb / 2 - 1)) continue;
+            if (digit == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+                st.need_median = 1;
+                st.prefix = 0;
+                st.rank = (uint32_t)(nb / 2);
+            }
+            const uint32_t prefix = digit == 0 ? 0u : st.prefix;
+            for (int b = threadIdx.x; b < (1 << width); b += blockDim.x) h[b] = 0;
+            __syncthreads();
+            for (int64_t j = gtid; j < nb; j += gthreads) {
+                const uint32_t bits = __float_as_uint(J.energy[j]);
+                if (digit == 0 || (bits >> hi) == prefix) atomicAdd(&h[(bits >> lo) & ((1u << width) - 1)], 1u);
+            }
+            __syncthreads();
+            for (int b = threadIdx.x; b < (1 << width); b += blockDim.x)
+                if (h[b]) atomicAdd(&S.hist[(int64_t)J.slot * kHistBins + b], h[b]);
+            __syncthreads();
+        }
+        if (!grid_sync(gb, status)) return false;
+        // pick: block jb % gridDim handles job jb
+        for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
+            const StatJob &J = jobs[jb];
+            if (!J.active) continue;
+            HashStats &st = S.stats[J.slot];
+            const int64_t nb = nb_of(S.ndim, J.logB);
+            if (nb <= kSmallMedian || !((int64_t)st.above > nb - nb / 2 - 1)) continue;
+            uint32_t *hh = S.hist + (int64_t)J.slot * kHistBins;
+            const uint32_t rank = digit == 0 ? (uint32_t)(nb / 2) : st.rank;
+            __shared__ uint32_t fb, fr;
+            block_find_rank(hh, 1 << width, rank, &fb, &fr);
+            if (threadIdx.x == 0) {
+                const uint32_t pre = digit == 0 ? 0u : st.prefix;
+                st.prefix = (pre << width) | fb;
+                st.rank = fr;
+                if (digit == 2) {
+                    st.med_bits = st.prefix;
+                    st.nmax = 0;   // recount below with the exact threshold
+                }
+            }
+            __syncthreads();
+            for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) hh[b] = 0;
+            __syncthreads();
+        }
+        if (!grid_sync(gb, status)) return false;
+    }
+    for (int jb = 0; jb < njobs; jb++) {
+        const StatJob &J = jobs[jb];
+        if (!J.active) continue;
+        HashStats &st = S.stats[J.slot];
+        const int64_t nb = nb_of(S.ndim, J.logB);
+        if (!st.need_median || nb <= kSmallMedian) continue;
+        localmax_job(J, S, threshold_of(st, S), gtid, gthreads, nullptr, INFINITY);
+    }
+    return grid_sync(gb, status);
+}
+
+// ---------------------------------------------------------------------------------
+// Tuning tail: statistics of every trial, then the controller.
+// ---------------------------------------------------------------------------------
+struct TuneTailArgs {
+    StatsParams S;
+    const StatJob *jobs;
+    int njobs;
+    int b0, b_hi, tune_max;
+    double delta2;
+    const Job *tjob;
+    int nh_le, L_loc;
+    StatJob *lstat;
+    const float2 *z;
+    float *e_loc;
+    const HashParam *le;
+    ExecState *state;
+};
+
+// One thread walks the trials B0, 2 B0, ... through Eq. (12) and Eq. (14) until the
+// stop reading: the first trial with r < delta2 (keep branch, or halve branch onto the
+// already evaluated B/2); r = inf when either count is 0; a trial whose energies are
+// all exactly 0 ends with k* = 0.  Then it writes the jobs at B*.
+__device__ void controller(const TuneTailArgs &A)
+{
+    const HashStats *stats = A.S.stats;
+    ExecState *state = A.state;
+    int b = A.b0, trial = 0;
+    int64_t kprev = 0, k = 0;
+    int status = state->status, empty = 0;
+    for (;; trial++) {
+        k = stats[b].nmax;
+        if (trial < kMaxTrialsTrace) {
+            state->trial_B[trial] = (int64_t)1 << b;
+            state->trial_k[trial] = k;
+        }
+        if (stats[b].max_bits == 0) {
+            empty = 1;
+            k = 0;
+            break;
+        }
+        double r = NAN;
+        if (trial > 0) r = (kprev == 0 || k == 0) ? INFINITY : fabs(1.0 - (double)k / (double)kprev);
+        if (trial > 0 && r < A.delta2) break;
+        if (b == A.b_hi) {
+            if (trial > 0 && status == ATSFFT_OK) status = ATSFFT_E_NOT_SPARSE;
+            break;
+        }
+        if (trial + 1 >= A.tune_max) {
+            if (status == ATSFFT_OK) status = ATSFFT_E_NOT_CONVERGED;
+            break;
+        }
+        kprev = k;
+        b++;
+    }
+    if (k == 0) empty = 1;
+    state->ntrials = trial + 1;
+    state->b_star = b;
+    state->k_star = k;
+    state->status = status;
+    state->empty = empty;
+    Job j = A.tjob[b];
+    j.nh = A.nh_le;
+    j.active = !empty;
+    state->job = j;
+    const int64_t nb = nb_of(A.S.ndim, b);
+    for (int l = 0; l < A.L_loc; l++) {
+        StatJob s;
+        s.spec = A.z + (int64_t)l * nb;
+        s.energy = A.e_loc + (int64_t)l * nb;
+        s.hash = A.le + l;
+        s.logB = b;
+        s.slot = kMaxLogB + l;
+        s.list = l;
+        s.active = !empty;
+        A.lstat[l] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_tune_tail(const TuneTailArgs A)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) stamp(&A.state->bar);
+    if (!stats_phases(A.jobs, A.njobs, A.S, &A.state->bar, &A.state->status)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) controller(A);
+}
+
+// ---------------------------------------------------------------------------------
+// Location tail
+// ---------------------------------------------------------------------------------
+struct RespOffsets {
+    int64_t off[kMaxLogB];
+};
+
+struct LocTailArgs {
+    StatsParams S;
+    const StatJob *jobs;    // the location jobs at B*, written by the controller
+    int L_loc, L_est;
+    int est_group;          // lanes per coordinate in the estimates: power of two >= L_est
+    float eta_up, eta_dn;
+    int32_t *sel;
+    uint32_t *votes;
+    int64_t nvote_words;
+    uint32_t need;          // votes needed: ceil(L_loc / 2)
+    uint32_t *blk;          // per-block kept counts / offsets (gridDim entries)
+    const HashParam *le;    // location then estimation hashes
+    const float2 *z;        // spectra at B*: location then estimation hashes
+    const double *resp;
+    RespOffsets ro;
+    int logn;
+    int64_t *loc;
+    float2 *val;
+    int64_t capacity;
+    int64_t *d_count, *d_k;
+    int32_t *d_status;
+    ExecState *state;
+};
+
+// k-th smallest (0-based) key among entries i < cnt with pred(i): four 8-bit radix
+// passes with a shared histogram.  Whole block must call.
+template <class KeyF, class PredF>
+__device__ uint32_t block_kth(int64_t cnt, uint32_t k, KeyF key, PredF pred)
+{
+    __shared__ uint32_t hist[256];
+    __shared__ uint32_t sh_prefix, sh_k;
+    if (threadIdx.x == 0) {
+        sh_prefix = 0;
+        sh_k = k;
+    }
+    for (int pass = 0; pass < 4; pass++) {
+        const int shift = 24 - 8 * pass;
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        const uint32_t prefix = sh_prefix;
+        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+            if (!pred(i)) continue;
+            const uint32_t kk = key(i);
+            if (pass == 0 || (kk >> (shift + 8)) == prefix) atomicAdd(&hist[(kk >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        __shared__ uint32_t fb, fr;
+        block_find_rank(hist, 256, sh_k, &fb, &fr);
+        if (threadIdx.x == 0) {
+            sh_prefix = (prefix << 8) | fb;
+            sh_k = fr;
+        }
+        __syncthreads();
+    }
+    return sh_prefix;
+}
+
+constexpr int kTopStage = 4096;
+
+// Top-num cutoff of one location hash by one block: keep every maximum above
+// V(1+eta) (V = the num-th largest energy) and fill up from [V(1-eta), V(1+eta)] in
+// ascending bucket order.
+__device__ void topnum_block(const StatJob &J, const LocTailArgs &A, int64_t num)
+{
+    __shared__ uint32_t n_sel, n_hi;
+    HashStats &st = A.S.stats[J.slot];
+    const int ndim = A.S.ndim;
+    const int logB = J.logB;
+    const uint32_t mask = (1u << logB) - 1;
+    const uint32_t p1 = J.hash->sinv[0] & mask, p2 = J.hash->sinv[1] & mask;
+    const int64_t cnt = min((int64_t)st.nmax, A.S.cap);
+    const int32_t *list = A.S.lists + (int64_t)J.list * A.S.cap;
+    int32_t *out = A.sel + (int64_t)J.list * A.S.cap;
+    const float *E = J.energy;
+    auto energy_global = [&](int64_t i) -> float {
+        const uint32_t c = (uint32_t)list[i];
+        if (ndim == 1) return E[(p1 * c) & mask];
+        const uint32_t c1 = c >> logB, c2 = c & mask;
+        return E[((int64_t)((p1 * c1) & mask) << logB) | ((p2 * c2) & mask)];
+    };
+    // the candidates' energies, staged once when they fit
+    extern __shared__ uint32_t dsm[];
+    float *es = reinterpret_cast<float *>(dsm);   // kTopStage entries
+    const bool staged = cnt <= kTopStage;
+    if (staged)
+        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) es[i] = energy_global(i);
+    auto energy_of = [&](int64_t i) -> float { return staged ? es[i] : energy_global(i); };
+    if (threadIdx.x == 0) {
+        n_sel = 0;
+        n_hi = 0;
+    }
+    __syncthreads();
+    if (cnt <= num) {
+        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) out[i] = list[i];
+        if (threadIdx.x == 0) n_sel = (uint32_t)cnt;
+    } else {
+        const uint32_t vb = ~block_kth(
+            cnt, (uint32_t)(num - 1), [&](int64_t i) { return ~__float_as_uint(energy_of(i)); },
+            [&](int64_t) { return true; });
+        const float V = __uint_as_float(vb);
+        const float hi = V * A.eta_up, lo = V * A.eta_dn;
+        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x)
+            if (energy_of(i) > hi) atomicAdd(&n_hi, 1u);
+        __syncthreads();
+        const uint32_t need = (uint32_t)num - n_hi;
+        const uint32_t cthr = block_kth(
+            cnt, need - 1, [&](int64_t i) { return (uint32_t)list[i]; },
+            [&](int64_t i) {
+                const float e = energy_of(i);
+                return e >= lo && e <= hi;
+            });
+        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const float e = energy_of(i);
+            if (e > hi || (e >= lo && e <= hi && (uint32_t)list[i] <= cthr)) {
+                const uint32_t pos = atomicAdd(&n_sel, 1u);
+                out[pos] = list[i];
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st.nsel = n_sel;
+    __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t count_kept(uint32_t w, uint32_t need)
+{
+    return ((w & 0xffu) >= need) + (((w >> 8) & 0xffu) >= need) + (((w >> 16) & 0xffu) >= need) +
+           ((w >> 24) >= need);
+}
+
+__device__ __forceinline__ void axis_terms(uint64_t i, const HashParam &hp, int axis, int logn,
+                                           int logB, uint64_t &jP, uint64_t &kph, int64_t &oidx,
+                                           uint64_t &mtau)
+{
+    const uint64_t n = 1ull << logn, D = 1ull << (logn - logB), Bm = (1ull << logB) - 1;
+    const uint64_t p = ((uint64_t)hp.sigma[axis] * i) & (n - 1);
+    const uint64_t q = (2 * p + 1 + D) / (2 * D);
+    const int64_t o2 = (int64_t)(2 * p + 1) - (int64_t)(2 * q * D);   // odd, in (-D, D)
+    const uint64_t h = q & Bm;
+    const uint64_t sp = (uint64_t)hp.sinv[axis] & Bm;                   // sigma^{-1} mod B
+    jP = (sp * h) & Bm;
+    kph = (jP * ((uint64_t)hp.tau[axis] & Bm)) & Bm;                    // h sigma' tau mod B
+    oidx = (o2 + (int64_t)D - 1) / 2;
+    mtau = ((uint64_t)hp.tau[axis] * i) & (n - 1);
+}
+
+// Eq. (11) for coordinate `coord` and estimation hash l, in FP64.
+__device__ void estimate_term(uint64_t coord, const LocTailArgs &A, int b, int l, double &re,
+                              double &im)
+{
+    const int logn = A.logn, ndim = A.S.ndim;
+    const uint64_t n = 1ull << logn, D = 1ull << (logn - b);
+    const int64_t nb = nb_of(ndim, b);
+    const double *G = A.resp + A.ro.off[b];
+    const HashParam hp = A.le[A.L_loc + l];
+    const float2 *Pz = A.z + (int64_t)(A.L_loc + l) * nb;
+    uint64_t jP, kph, m;
+    int64_t oi;
+    float2 pv;
+    double gain;
+    uint64_t kang;
+    if (ndim == 1) {
+        axis_terms(coord, hp, 0, logn, b, jP, kph, oi, m);
+        pv = Pz[jP];
+        gain = G[oi];
+        kang = (kph * D + n - m) & (n - 1);
+    } else {
+        const uint64_t i = coord >> logn, j = coord & (n - 1);
+        uint64_t jP2, kph2, m2;
+        int64_t oi2;
+        axis_terms(i, hp, 0, logn, b, jP, kph, oi, m);
+        axis_terms(j, hp, 1, logn, b, jP2, kph2, oi2, m2);
+        pv = Pz[(jP << b) | jP2];
+        gain = G[oi] * G[oi2];
+        kang = ((kph + kph2) * D + 2 * n - m - m2) & (n - 1);
+    }
+    double sn, cs;
+    sincospi(2.0 * (double)kang / (double)n, &sn, &cs);
+    re = ((double)pv.x * cs - (double)pv.y * sn) / gain;
+    im = ((double)pv.x * sn + (double)pv.y * cs) / gain;
+}
+
+// Estimates of the kept coordinates: a group of `grp` lanes (grp >= L_est, a power of two)
+// per coordinate, lane l computing hash l; the group's first lane gathers the values by
+// shuffles and takes the componentwise median (element floor(L/2) after sorting).
+__device__ void estimate_all(const LocTailArgs &A, int64_t cnt, int b)
+{
+    const int grp = A.est_group;
+    const int lane = threadIdx.x & 31, gl = lane & (grp - 1);
+    const int per_warp = 32 / grp;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * per_warp; base < cnt; base += nwarps * per_warp) {
+        const int64_t s = base + lane / grp;
+        const bool valid = s < cnt;
+        double re = 0.0, im = 0.0;
+        if (valid && gl < A.L_est) estimate_term((uint64_t)A.loc[s], A, b, gl, re, im);
+        double vr[kMaxLoops], vi[kMaxLoops];
+        for (int l = 0; l < A.L_est; l++) {
+            vr[l] = __shfl_sync(0xffffffffu, re, l, grp);
+            vi[l] = __shfl_sync(0xffffffffu, im, l, grp);
+        }
+        if (valid && gl == 0) {
+            for (int a = 1; a < A.L_est; a++) {
+                const double r = vr[a], q = vi[a];
+                int k = a - 1;
+                while (k >= 0 && vr[k] > r) { vr[k + 1] = vr[k]; k--; }
+                vr[k + 1] = r;
+                k = a - 1;
+                while (k >= 0 && vi[k] > q) { vi[k + 1] = vi[k]; k--; }
+                vi[k + 1] = q;
+            }
+            A.val[s] = make_float2((float)vr[A.L_est / 2], (float)vi[A.L_est / 2]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_loc_tail(const LocTailArgs A)
+{
+    ExecState *state = A.state;
+    GridBarrier *gb = &state->bar;
+    if (blockIdx.x == 0 && threadIdx.x == 0) stamp(gb);
+    int *status = &state->status;
+    const bool empty = state->empty != 0;
+    const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (!empty) {
+        if (!stats_phases(A.jobs, A.L_loc, A.S, gb, status)) return;
+        // top-num cutoff: one block per location hash
+        const int64_t num = state->k_star;
+        for (int l = blockIdx.x; l < A.L_loc; l += gridDim.x) topnum_block(A.jobs[l], A, num);
+        if (!grid_sync(gb, status)) return;
+        // votes: every coordinate whose permuted position rounds to a selected bucket
+        const int b = state->b_star;
+        const int logn = A.logn, logD = logn - b, ndim = A.S.ndim;
+        const int64_t D = (int64_t)1 << logD;
+        const int64_t Dd = ndim == 1 ? D : D * D;
+        __shared__ int64_t off[kMaxLoops + 1];
+        if (threadIdx.x == 0) {
+            int64_t acc = 0;
+            for (int l = 0; l < A.L_loc; l++) {
+                off[l] = acc;
+                acc += (int64_t)A.S.stats[kMaxLogB + l].nsel * Dd;
+            }
+            off[A.L_loc] = acc;
+        }
+        __syncthreads();
+        const uint32_t n = 1u << logn, nmask = n - 1, Bm = (1u << b) - 1;
+        for (int64_t it = gtid; it < off[A.L_loc]; it += gthreads) {
+            int l = 0;
+            while (it >= off[l + 1]) l++;
+            const int64_t rem = it - off[l];
+            const int64_t sidx = rem >> (ndim == 1 ? logD : 2 * logD);
+            const uint32_t q = (uint32_t)(rem & (Dd - 1));
+            const uint32_t c = (uint32_t)A.sel[(int64_t)l * A.S.cap + sidx];
+            const HashParam hp = A.le[l];
+            int64_t coord;
+            if (ndim == 1) {
+                // bucket c collects permuted positions p in [c D - D/2, c D + D/2 - 1]
+                const uint32_t pp = ((c << logD) - (uint32_t)(D >> 1) + q) & nmask;
+                coord = (hp.sinv[0] * pp) & nmask;
+            } else {
+                const uint32_t c1 = c >> b, c2 = c & Bm;
+                const uint32_t q1 = q >> logD, q2 = q & (uint32_t)(D - 1);
+                const uint32_t pp1 = ((c1 << logD) - (uint32_t)(D >> 1) + q1) & nmask;
+                const uint32_t pp2 = ((c2 << logD) - (uint32_t)(D >> 1) + q2) & nmask;
+                coord = ((int64_t)((hp.sinv[0] * pp1) & nmask) << logn) | ((hp.sinv[1] * pp2) & nmask);
+            }
+            atomicAdd(&A.votes[coord >> 2], 1u << (8 * (coord & 3)));
+        }
+        if (!grid_sync(gb, status)) return;
+    } else {
+        // nothing voted; the (zero) counters still go through the compaction
+    }
+    // ordered compaction: block b owns a contiguous range of vote words, walked in
+    // chunks of 4 words per thread
+    const int64_t per = ((A.nvote_words + gridDim.x - 1) / gridDim.x + 3) & ~(int64_t)3;
+    const int64_t w0 = blockIdx.x * per;
+    const int64_t w1 = min(w0 + per, A.nvote_words);
+    uint32_t c = 0;
+    for (int64_t w = w0 + 4 * threadIdx.x; w < w1; w += 4 * blockDim.x) {
+        if (w + 3 < w1) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(A.votes + w);
+            c += count_kept(q.x, A.need) + count_kept(q.y, A.need) + count_kept(q.z, A.need) +
+                 count_kept(q.w, A.need);
+        } else {
+            for (int64_t u = w; u < w1; u++) c += count_kept(A.votes[u], A.need);
+        }
+    }
+    c = block_sum(c);
+    if (threadIdx.x == 0) A.blk[blockIdx.x] = c;
+    if (!grid_sync(gb, status)) return;
+    if (blockIdx.x == 0) {
+        // exclusive scan of the per-block counts (gridDim.x <= 8 * 256 here)
+        __shared__ uint32_t carry, tot;
+        if (threadIdx.x == 0) carry = 0;
+        __syncthreads();
+        for (unsigned i0 = 0; i0 < gridDim.x; i0 += blockDim.x) {
+            const unsigned i = i0 + threadIdx.x;
+            const uint32_t v = i < gridDim.x ? A.blk[i] : 0u;
+            const uint32_t ex = block_exclusive_scan(v, &tot);
+            if (i < gridDim.x) A.blk[i] = carry + ex;
+            __syncthreads();
+            if (threadIdx.x == 0) carry += tot;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) state->count = carry;
+    }
+    if (!grid_sync(gb, status)) return;
+    {
+        // in-order write of this block's range: 4 words per thread per chunk
+        int64_t base = A.blk[blockIdx.x];
+        __shared__ uint32_t tot;
+        for (int64_t wb = w0; wb < w1; wb += 4 * blockDim.x) {
+            const int64_t w = wb + 4 * threadIdx.x;
+            uint32_t words[4];
+            for (int q = 0; q < 4; q++) words[q] = (w + q < w1) ? A.votes[w + q] : 0u;
+            uint32_t k = 0;
+            for (int q = 0; q < 4; q++) k += count_kept(words[q], A.need);
+            int64_t pos = base + block_exclusive_scan(k, &tot);
+            for (int q = 0; q < 4; q++) {
+                for (int by = 0; by < 4; by++)
+                    if (((words[q] >> (8 * by)) & 0xffu) >= A.need) {
+                        if (pos < A.capacity) A.loc[pos] = (w + q) * 4 + by;
+                        pos++;
+                    }
+                if (w + q < w1 && words[q]) A.votes[w + q] = 0u;
+            }
+            base += tot;
+            __syncthreads();
+        }
+    }
+    if (!grid_sync(gb, status)) return;
+    // estimates of the kept coordinates
+    const int64_t count = state->count;
+    if (!empty) {
+        const int64_t cnt = min(count, A.capacity);
+        estimate_all(A, cnt, state->b_star);
+    }
+    if (!grid_sync(gb, status)) return;   // (stamps the end of the estimates)
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int st = state->status;
+        const int64_t cnt = empty ? 0 : count;
+        if (cnt > A.capacity && st == ATSFFT_OK) st = ATSFFT_E_CAPACITY;
+        *A.d_count = cnt;
+        *A.d_k = state->k_star;
+        *A.d_status = st;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Launches
+// ---------------------------------------------------------------------------------
+static StatsParams stats_params(const atsfft_plan_s *P)
+{
+    StatsParams S;
+    S.ndim = P->ndim;
+    S.thr_rel = (float)P->p.thr_rel;
+    S.thr_med = (float)P->p.thr_med;
+    S.up = (float)(1.0 + P->p.tie_eta);
+    S.use_median = P->p.thr_med > 0;
+    S.ratio = S.use_median ? (float)(P->p.thr_rel / P->p.thr_med * (1.0 - 1.0 / 1048576.0)) : 0.f;
+    S.stats = P->d_stats;
+    S.hist = P->d_hist;
+    S.lists = P->d_lmax;
+    S.cap = P->lmax_cap;
+    return S;
+}
+
+// Dynamic shared memory of the tail kernels: the largest phase scratch (the small-hash
+// median: kSmallMedian values + 2048 histogram bins).
+constexpr size_t kTailSmem = sizeof(uint32_t) * (kSmallMedian + 2048);
+
+static cudaError_t launch_coop(const void *fn, int grid, void *arg, cudaStream_t s)
+{
+    void *args[] = {arg};
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem);
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, kTailSmem, s);
+}
+
+static int coop_grid(const atsfft_plan_s *P, const void *fn)
+{
+    int per_sm = 0;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, kTailSmem);
+    if (per_sm > 2) per_sm = 2;
+    if (per_sm < 1) per_sm = 1;
+    return P->num_sms * per_sm;
+}
+
+void launch_tune_tail(const atsfft_plan_s *P, cudaStream_t s)
+{
+    TuneTailArgs A;
+    A.S = stats_params(P);
+    A.jobs = P->d_tstat;
+    A.njobs = P->ntstat;
+    A.b0 = P->b0;
+    A.b_hi = P->b_hi;
+    A.tune_max = P->p.tune_max;
+    A.delta2 = P->p.delta2;
+    A.tjob = P->d_tjob;
+    A.nh_le = P->L_loc + P->L_est;
+    A.L_loc = P->L_loc;
+    A.lstat = P->d_lstat;
+    A.z = P->d_z;
+    A.e_loc = P->d_energy + P->e_loc_off;
+    A.le = P->d_le;
+    A.state = P->d_state;
+    const void *fn = (const void *)k_tune_tail;
+    launch_coop(fn, coop_grid(P, fn), &A, s);
+    count_launch(P);
+}
+
+void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, int64_t capacity,
+                     int64_t *d_count, int64_t *d_k, int32_t *d_status, cudaStream_t s)
+{
+    LocTailArgs A;
+    A.S = stats_params(P);
+    A.jobs = P->d_lstat;
+    A.L_loc = P->L_loc;
+    A.L_est = P->L_est;
+    A.est_group = 1;
+    while (A.est_group < P->L_est) A.est_group *= 2;
+    A.eta_up = (float)(1.0 + P->p.tie_eta);
+    A.eta_dn = (float)(1.0 - P->p.tie_eta);
+    A.sel = P->d_sel;
+    A.votes = P->d_votes;
+    A.nvote_words = P->nvote_words;
+    A.need = (uint32_t)((P->L_loc + 1) / 2);
+    A.blk = P->d_blk;
+    A.le = P->d_le;
+    A.z = P->d_z;
+    A.resp = P->d_resp;
+    for (int b = 0; b < kMaxLogB; b++) A.ro.off[b] = P->resp_off[b];
+    A.logn = P->logn;
+    A.loc = d_loc;
+    A.val = d_val;
+    A.capacity = capacity;
+    A.d_count = d_count;
+    A.d_k = d_k;
+    A.d_status = d_status;
+    A.state = P->d_state;
+    const void *fn = (const void *)k_loc_tail;
+    launch_coop(fn, coop_grid(P, fn), &A, s);
+    count_launch(P);
+}
+
+}  // namespace atsfft
