@@ -141,6 +141,29 @@ atsfft_status atsfft_phase_times(atsfft_plan_t plan, float *h_ms, int max_phases
 atsfft_status atsfft_tail_stamps(atsfft_plan_t plan, uint64_t *h_ns, int max_stamps,
                                  int *h_nstamps, void *stream);
 
+/* ---- allocation-free variant ---------------------------------------------------- */
+
+/* The bucket spectrum of one hash of a 1D signal -- the same values atsfft_hash_spectrum
+ * gives for a plan of length n with the default parameters and this seed -- computed
+ * without a plan and without allocating any memory.  The paper has no counterpart: this
+ * call exists for callers that cannot allocate device memory when they need the result
+ * (cudaMalloc can synchronise the whole device, which a host callback or a latency-
+ * critical serving loop must not do; a process whose device memory belongs to another
+ * allocator with a fixed budget may not be allowed extra cudaMalloc calls).
+ *
+ * Scratch: a fixed 12 MiB array inside the library, held by every GPU that loads the
+ * library until the process exits.  Sizes are limited so that everything fits: n a power
+ * of two in [2^8, 2^22], B a power of two in [16, n/16]; anything else returns
+ * ATSFFT_E_INVALID_ARG.  d_x: n complex64 on the current device; d_zhat: B complex64
+ * (bucket order) written on `stream`.  The first call on a device also sets that device
+ * up (looks up the array's device address and fills a twiddle table); make that first
+ * call before any stream capture.  Each call synchronises `stream` once (to read back
+ * the window normalisation).  All calls share the one array and every call writes all
+ * of it that it reads, so nothing needs clearing between calls; calls that overlap on
+ * the GPU (other streams, other threads) race on it. */
+atsfft_status atsfft_hash_spectrum_noalloc(const void *d_x, int64_t n, int64_t B, uint64_t seed,
+                                           int phase, int index, void *d_zhat, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,7 @@ from ._lib import (  # noqa: F401
     atsfft_exec,
     atsfft_exec_2d,
     atsfft_hash_spectrum,
+    atsfft_hash_spectrum_noalloc,
     atsfft_last_trace,
     atsfft_params,
     atsfft_phase_times,

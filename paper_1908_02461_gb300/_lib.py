@@ -35,7 +35,7 @@ class atsfft_params(C.Structure):
 EXPORTED = ["atsfft_default_params", "atsfft_plan", "atsfft_exec", "atsfft_exec_2d",
             "atsfft_destroy", "atsfft_status_string", "atsfft_hash_spectrum",
             "atsfft_window_response", "atsfft_last_trace", "atsfft_set_profiling",
-            "atsfft_phase_times", "atsfft_tail_stamps"]
+            "atsfft_phase_times", "atsfft_tail_stamps", "atsfft_hash_spectrum_noalloc"]
 
 PHASES = ["tune_gather", "tune_stream", "tune_fft", "tune_tail", "le_bin_stream", "le_bin_gather",
           "le_fft", "loc_tail"]
@@ -78,6 +78,8 @@ def load(path: str | None = None):
     L.atsfft_phase_times.restype = i32
     L.atsfft_tail_stamps.argtypes = [vp, vp, i32, P(i32), vp]
     L.atsfft_tail_stamps.restype = i32
+    L.atsfft_hash_spectrum_noalloc.argtypes = [vp, i64, i64, u64, i32, i32, vp, vp]
+    L.atsfft_hash_spectrum_noalloc.restype = i32
     if path is None:
         _lib = L
     return L
@@ -163,3 +165,9 @@ def atsfft_tail_stamps(plan, h_ns, max_stamps, stream=None):
     n = C.c_int()
     st = load().atsfft_tail_stamps(plan, _ptr(h_ns), max_stamps, C.byref(n), _ptr(stream))
     return st, n.value
+
+
+def atsfft_hash_spectrum_noalloc(d_x, n, B, seed, phase, index, d_zhat, stream=None) -> int:
+    """One hash's bucket spectrum without a plan or any allocation (see include/atsfft.h)."""
+    return load().atsfft_hash_spectrum_noalloc(_ptr(d_x), n, B, seed & 0xFFFFFFFFFFFFFFFF, phase,
+                                               index, _ptr(d_zhat), _ptr(stream))
