@@ -53,6 +53,13 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+# DRAM bytes of one launch of a phase's kernel, from one ncu capture of the current
+# kernel (dram__bytes_read.sum + dram__bytes_write.sum); None once the kernel changes.
+NCU_TRAFFIC = {
+    "loc_tail": (8788992, "k=1000 launch (B*=2^16), ncu --set full, bench.py --ncu-case 1000"),
+}
+
+
 def _signals():
     from synth import sparse_signal_1d
 
@@ -113,6 +120,39 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
                 "reasons": reasons, "samples": len(rows),
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def aggregate(local_ms, world_size, device=None):
+    """Max over ranks of a rank's device time (ms); identity for one rank."""
+    if world_size <= 1:
+        return float(local_ms)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cufft_reference_ms(n, dev, reps=20):
+    """Dense cuFFT C2C complex64 of length n (torch.fft), median of `reps` event timings
+    with L2 flushed in between -- a comparison only, not part of the method."""
+    import torch
+
+    x = torch.randn(n, dtype=torch.complex64, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        torch.fft.fft(x)
+    ts = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(reps):
+        flush.zero_()
+        e0.record()
+        torch.fft.fft(x)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(statistics.median(ts))
 
 
 def _dist():
@@ -244,7 +284,9 @@ def roofline(per_signal, traces, n):
     d = out[dom]
     peak = pair_peak / 1e9 if d["bound"] == "alu" else hbm
     roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": peak,
-            "unit": d["unit"], "frac": d["achieved"] / peak, "traffic": None,
+            "unit": d["unit"], "frac": d["achieved"] / peak,
+            "traffic": NCU_TRAFFIC[dom][0] if dom in NCU_TRAFFIC else None,
+            "traffic_launch": NCU_TRAFFIC[dom][1] if dom in NCU_TRAFFIC else None,
             "peak_source": ("derived: 16 SFU ops/clk/SM x 152 SMs x 2070 MHz / 2 SFU ops per "
                             "sample-hash pair") if d["bound"] == "alu" else f"{src} hbm_gbs",
             "ms_per_launch": d["ms_per_launch"]}
@@ -272,11 +314,13 @@ def ncu_case(k):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--phases", action="store_true", help="print per-phase times to stderr")
+    ap.add_argument("--streams", type=int, default=4,
+                    help="run the step's transforms on this many CUDA streams (1 = in order)")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="K",
                     help="profiling case for ncu: one plan, the k=K signal, three transforms")
     args = ap.parse_args()
@@ -303,7 +347,9 @@ def main():
     n = 1 << N_LOG2
     host = [torch.from_numpy(s.x).pin_memory() for s in sigs]
     xs = [h.to(dev) for h in host]
-    plans = [A.Plan((n,), seed=SEED) for _ in sigs]
+    nstreams = max(1, min(args.streams, len(sigs)))
+    pp = A.params(coop_blocks_per_sm=1) if nstreams > 1 else None
+    plans = [A.Plan((n,), params=pp, seed=SEED) for _ in sigs]
     for p in plans:
         p.set_profiling(True)
     outs = []
@@ -315,18 +361,60 @@ def main():
                          status=torch.zeros(1, dtype=torch.int32, device=dev)))
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    side = [stream] + [torch.cuda.Stream(device=dev) for _ in range(nstreams - 1)]
 
     def step():
+        # transforms on `nstreams` streams, joined back into the timing stream
+        if nstreams == 1:
+            for p, x, o in zip(plans, xs, outs):
+                p.exec_async(x, o["loc"], o["val"], o["count"], o["k"], o["status"], stream.cuda_stream)
+            return
+        start = torch.cuda.Event()
+        start.record(stream)
+        for i, (p, x, o) in enumerate(zip(plans, xs, outs)):
+            st = side[i % nstreams]
+            st.wait_event(start)
+            p.exec_async(x, o["loc"], o["val"], o["count"], o["k"], o["status"], st.cuda_stream)
+        for st in side[1:]:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            stream.wait_event(ev)
+
+    def plain_step():
         for p, x, o in zip(plans, xs, outs):
             p.exec_async(x, o["loc"], o["val"], o["count"], o["k"], o["status"], stream.cuda_stream)
 
     for _ in range(args.warmup):
         flush.zero_()
         step()
+        flush.zero_()
+        plain_step()
     torch.cuda.synchronize()
-
-    step_ms, phase_acc, launches, stamp_acc = [], [], 0, []
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    # ---- plain per-signal path, in order, with per-kernel phase events -----------------
+    for p in plans:
+        p.set_profiling(True)
+    plain_ms, phase_acc, stamp_acc = [], [], []
+    for _ in range(max(3, args.steps // 4)):
+        flush.zero_()
+        ev0.record(stream)
+        plain_step()
+        ev1.record(stream)
+        ev1.synchronize()
+        plain_ms.append(ev0.elapsed_time(ev1))
+        for p in plans:
+            ph, _ = p.phase_times()
+            phase_acc.append(ph)
+            if args.phases:
+                st_ = p.tail_stamps()
+                stamp_acc.append([(b - st_[0]) / 1e3 for b in st_])
+    for p in plans:
+        p.set_profiling(False)
+    plain_value = len(sigs) * len(plain_ms) / (sum(plain_ms) / 1e3)
+
+    # ---- timed region: the step on `nstreams` streams ----------------------------------
+    step_ms, launches = [], 0
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -340,22 +428,12 @@ def main():
             ev1.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
             for p in plans:
-                ph, nl = p.phase_times()
-                phase_acc.append(ph)
-                launches += nl
-            if args.phases:
-                for p in plans:
-                    st_ = p.tail_stamps()
-                    stamp_acc.append([(b - st_[0]) / 1e3 for b in st_])
+                launches += p.phase_times()[1]
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if ws > 1:
         torch.distributed.barrier()
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = aggregate(sum(step_ms), ws, dev)
     ntrans = len(sigs) * args.steps * ws
     value = ntrans / (total_ms / 1e3)
 
@@ -363,7 +441,7 @@ def main():
     kstar = [int(o["k"].item()) for o in outs]
     counts = [int(o["count"].item()) for o in outs]
 
-    # ---- dominant kernel of the step and its roofline -------------------------------
+    # ---- dominant kernel of the plain step and its roofline -------------------------
     names = list(phase_acc[0].keys())
     mean_phase = {nm: float(np.mean([ph[nm] for ph in phase_acc])) for nm in names}
     per_signal = {}
@@ -378,17 +456,24 @@ def main():
     host_out = [dict(loc=torch.empty(CAPACITY, dtype=torch.int64).pin_memory(),
                      val=torch.empty(CAPACITY, dtype=torch.complex64).pin_memory(),
                      scal=torch.empty(3, dtype=torch.int64).pin_memory()) for _ in sigs]
-    for p in plans:
-        p.set_profiling(False)
 
     def e2e_step():
-        for p, h, x, o, ho in zip(plans, host, xs, outs, host_out):
-            x.copy_(h, non_blocking=True)
-            p.exec_async(x, o["loc"], o["val"], o["count"], o["k"], o["status"], stream.cuda_stream)
-            ho["loc"].copy_(o["loc"], non_blocking=True)
-            ho["val"].copy_(o["val"], non_blocking=True)
-            ho["scal"][0:1].copy_(o["count"], non_blocking=True)
-            ho["scal"][1:2].copy_(o["k"], non_blocking=True)
+        start = torch.cuda.Event()
+        start.record(stream)
+        for i, (p, h, x, o, ho) in enumerate(zip(plans, host, xs, outs, host_out)):
+            st = side[i % nstreams]
+            st.wait_event(start)
+            with torch.cuda.stream(st):
+                x.copy_(h, non_blocking=True)
+                p.exec_async(x, o["loc"], o["val"], o["count"], o["k"], o["status"], st.cuda_stream)
+                ho["loc"].copy_(o["loc"], non_blocking=True)
+                ho["val"].copy_(o["val"], non_blocking=True)
+                ho["scal"][0:1].copy_(o["count"], non_blocking=True)
+                ho["scal"][1:2].copy_(o["k"], non_blocking=True)
+        for st in side[1:]:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            stream.wait_event(ev)
 
     for _ in range(2):
         e2e_step()
@@ -401,11 +486,8 @@ def main():
         ev1.record(stream)
         ev1.synchronize()
         e2e_ms.append(ev0.elapsed_time(ev1))
-    e2e_total = sum(e2e_ms)
-    if ws > 1:
-        t = torch.tensor([e2e_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = aggregate(sum(e2e_ms), ws, dev)
+    cufft_ms = cufft_reference_ms(n, dev) if rank == 0 else None
     h2d = sum(h.numel() * 8 for h in host)
     d2h = len(sigs) * (CAPACITY * 8 + CAPACITY * 8 + 16)
 
@@ -418,8 +500,9 @@ def main():
         print(json.dumps({"per_signal_phase_ms": per_signal, "mean_phase_ms": mean_phase},
                          indent=1), file=sys.stderr)
         for i, k in enumerate(KS):
-            print("tail stamps us k=%d:" % k, [round(v, 1) for v in stamp_acc[-len(KS) + i]],
-                  file=sys.stderr)
+            if stamp_acc:
+                print("tail stamps us k=%d:" % k, [round(v, 1) for v in stamp_acc[-len(KS) + i]],
+                      file=sys.stderr)
     for p in plans:
         p.close()
     if ws > 1:
@@ -434,7 +517,13 @@ def main():
         "config": {"workload": WORKLOAD, "n": n, "ks": list(KS), "snr_db": SNR_DB,
                    "parallelism": f"replicas x{ws}", "l2": "flushed between steps (256 MiB write)",
                    "gsamples_per_s": value * n / 1e9,
+                   "plain_path_transforms_per_s": plain_value,
+                   "plain_path_ms_per_step": float(np.mean(plain_ms)),
                    "k_star": kstar, "counts": counts, "status": status,
+                   "path": ("plain per-signal path (one exec per transform)" if nstreams == 1 else
+                            f"per-signal execs on {nstreams} concurrent streams"),
+                   "cufft_c2c_ms": cufft_ms,
+                   "cufft_c2c_transforms_per_s": (1e3 / cufft_ms) if cufft_ms else None,
                    "bin_pass_ms": bin_ms, "wall_s": wall},
         "e2e": {"value": ntrans / (e2e_total / 1e3), "unit": "transforms/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

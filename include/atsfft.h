@@ -59,13 +59,16 @@ typedef struct {
     double tie_eta;             /* relative band inside which energies tie (1e-2)        */
     int b_min_log2, b_max_log2; /* tuning range of log2 B (per axis in 2D); 0 = default:
                                    1D [4, log2 n - 4], 2D [3, log2 N - 2]                */
+    int coop_blocks_per_sm;     /* blocks per SM of the two cooperative tail kernels
+                                   (0 = 2); 1 lets several plans' tails run at once on
+                                   different streams, all co-resident                   */
 } atsfft_params;
 
 /* Fills *p with the defaults listed above. */
 void atsfft_default_params(atsfft_params *p);
 
 /* Creates a plan for 1D signals of length shape[0] (ndim = 1; a power of two in
- * [2^8, 2^30]) or N x N images (ndim = 2, shape = {N, N}, N a power of two in
+ * [2^8, 2^28]) or N x N images (ndim = 2, shape = {N, N}, N a power of two in
  * [2^5, 2^14]).  k_hint > 0 starts the tuning at the smallest power-of-two B >= 2 k_hint
  * (2D: B^2 >= 2 k_hint); 0 means k is unknown.  p = NULL takes the defaults.  seed
  * keys the SplitMix64 streams of the hash permutations (Def. 1).  Builds the window

@@ -29,6 +29,7 @@ class atsfft_params(C.Structure):
         ("filter_alpha", C.c_double), ("filter_tol", C.c_double),
         ("thr_rel", C.c_double), ("thr_med", C.c_double), ("tie_eta", C.c_double),
         ("b_min_log2", C.c_int), ("b_max_log2", C.c_int),
+        ("coop_blocks_per_sm", C.c_int),
     ]
 
 

@@ -221,6 +221,7 @@ extern "C" void atsfft_default_params(atsfft_params *p)
     p->tie_eta = 1e-2;
     p->b_min_log2 = 0;
     p->b_max_log2 = 0;
+    p->coop_blocks_per_sm = 0;
 }
 
 extern "C" const char *atsfft_status_string(atsfft_status s)
@@ -248,6 +249,7 @@ static bool params_ok(const atsfft_params *p)
     if (!(p->filter_alpha > 0 && p->filter_alpha <= 2)) return false;
     if (!(p->filter_tol > 0 && p->filter_tol < 1)) return false;
     if (!(p->thr_rel >= 0 && p->thr_med >= 0 && p->tie_eta >= 0 && p->tie_eta < 1)) return false;
+    if (p->coop_blocks_per_sm < 0 || p->coop_blocks_per_sm > 8) return false;
     return true;
 }
 

@@ -948,7 +948,8 @@ static int coop_grid(const atsfft_plan_s *P, const void *fn)
     int per_sm = 0;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, kTailSmem);
-    if (per_sm > 2) per_sm = 2;
+    const int want = P->p.coop_blocks_per_sm > 0 ? P->p.coop_blocks_per_sm : 2;
+    if (per_sm > want) per_sm = want;
     if (per_sm < 1) per_sm = 1;
     return P->num_sms * per_sm;
 }
