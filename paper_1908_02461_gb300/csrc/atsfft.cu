@@ -38,7 +38,7 @@ static atsfft_status exec_common(atsfft_plan_t P, int ndim, const void *d_x, int
     const Job *jd = &P->d_state->job;
     launch_le_bin(P, x, jd, s);   // marks phase 5 after the stream-form kernel
     prof_mark(P, 6, s);
-    launch_bucket_fft_dynamic(P, jd, P->d_part, P->d_z, s);
+    launch_bucket_fft_dynamic(P, jd, P->d_part, P->d_z, P->d_energy + P->e_loc_off, P->L_loc, s);
     prof_mark(P, 7, s);
     launch_loc_tail(P, d_loc, (float2 *)d_val, capacity, d_count, d_k, d_status, s);
     prof_mark(P, 8, s);

@@ -648,7 +648,8 @@ void launch_tuning(const atsfft_plan_s *P, const float2 *x, cudaStream_t s)
         }
         prof_mark(P, 2, s);
     }
-    launch_bucket_fft_batch(P, nj, logB, chunks, in_off, out_off, P->d_part, P->d_tz, s);
+    launch_bucket_fft_batch(P, nj, logB, chunks, in_off, out_off, P->d_part, P->d_tz, P->d_energy,
+                            s);
 }
 
 // Location + estimation hashes at the device-chosen B*: every form is launched, the
@@ -718,7 +719,7 @@ void launch_single_hash(const atsfft_plan_s *P, const float2 *x, int b, const Ha
         launch_bin_2d(P, x, nullptr, j, false, hp_dev, b, P->d_part, s);
     }
     const int64_t zero = 0;
-    launch_bucket_fft_batch(P, 1, &b, &chunks, &zero, &zero, P->d_part, out, s);
+    launch_bucket_fft_batch(P, 1, &b, &chunks, &zero, &zero, P->d_part, out, nullptr, s);
 }
 
 void launch_bin_2d(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, const Job &job_host,

@@ -20,6 +20,7 @@ namespace atsfft {
 constexpr int kMaxLoops = 31;        // location / estimation hashes each
 constexpr int kMaxLogB = 26;         // log2 B range table size
 constexpr int kSmallFFT = 4096;      // largest FFT done in one CTA
+constexpr int kTwEntries = 2 * kSmallFFT;   // coarse exp(-2 pi i j / 4096), fine exp(-2 pi i j / 2^24)
 constexpr int kMaxTrialsTrace = 64;
 constexpr int kHistBins = 4096;      // radix-select histogram bins (12-bit digits)
 constexpr int kPersistCtas = 4;      // persistent CTAs per SM
@@ -130,7 +131,10 @@ struct atsfft_plan_s {
     atsfft::HashParam *d_tune, *d_le;
     atsfft::WindowParam *d_win;
     double *d_resp;        // Ghat' tables for every B of the range, concatenated
-    float2 *d_tw;          // exp(-2 pi i j / kSmallFFT)
+    float *d_rgain;        // 1 / Ghat', same layout, rounded to FP32
+    float2 *d_phase;       // exp(2 pi i m / n): [2^phase_s] low part, [n >> phase_s] high part
+    int phase_s;
+    float2 *d_tw;          // [0, 4096): exp(-2 pi i j / 4096); [4096, 8192): exp(-2 pi i j / 2^24)
 
     float2 *d_part;        // binning partial sums (residue order)
     size_t part_elems;
@@ -191,11 +195,14 @@ void launch_bin_2d(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
                    cudaStream_t s);
 
 // fft.cu
+// Bucket FFTs.  energy != nullptr: the final pass also writes |Zhat|^2 (same layout as
+// the spectra) and the per-hash maximum into the HashStats slot of the hash (dynamic
+// job: the first n_energy hashes, slots kMaxLogB + h; batch: slot logB).
 void launch_bucket_fft_dynamic(const atsfft_plan_s *P, const Job *job, const float2 *part,
-                               float2 *out, cudaStream_t s);
+                               float2 *out, float *energy, int n_energy, cudaStream_t s);
 void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB, const int *chunks,
                              const int64_t *in_off, const int64_t *out_off, const float2 *part,
-                             float2 *out, cudaStream_t s);
+                             float2 *out, float *energy, cudaStream_t s);
 
 // tail.cu
 void launch_tune_tail(const atsfft_plan_s *P, cudaStream_t s);

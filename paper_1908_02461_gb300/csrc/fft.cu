@@ -2,7 +2,7 @@
 // B x B in 2D): Zhat_c = sum_b z_b exp(-2 pi i c b / B), unscaled.
 //
 // One CTA transforms up to kSmallFFT points in shared memory (radix-2 decimation in
-// time, bit-reversed load, table twiddles).  Larger 1D transforms use the four-step
+// time, bit reversal folded into the first register pass, table twiddles).  Larger 1D transforms use the four-step
 // split B = P1 * P2 (j = j1 + P1 j2, k = k2 + P2 k1):
 //   pass 0: Y[j1 + P1 k2] = exp(-2 pi i j1 k2 / B) * sum_j2 z[j1 + P1 j2] w_P2^(j2 k2)
 //   pass 1: X[k2 + P2 k1] = sum_j1 Y[j1 + P1 k2] w_P1^(j1 k1).
@@ -55,15 +55,104 @@ __device__ FftShape fft_shape(int ndim, int logB, int pass)
     return f;
 }
 
+// Shared-memory index with one pad slot per 16 entries: the register passes below read
+// 8-value groups at strides 1, 8, 64, ... (positions in a group are a power of two
+// apart) and the padding spreads each half-warp's 64-bit accesses over the banks.
+constexpr int kSmemPadded = kSmallFFT + kSmallFFT / 16;
+constexpr int kMaxRadixLog = 3;     // 8-value register groups
+constexpr int kFftThreads = kSmallFFT >> kMaxRadixLog;
+
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+
+__device__ __forceinline__ void butterfly(float2 &a, float2 &b, float2 w)
+{
+    const float2 wb = make_float2(w.x * b.x - w.y * b.y, w.x * b.y + w.y * b.x);
+    b = make_float2(a.x - wb.x, a.y - wb.y);
+    a = make_float2(a.x + wb.x, a.y + wb.y);
+}
+
+// R consecutive radix-2 decimation-in-time stages lm0 .. lm0+R-1 on one group of 2^R
+// values held in registers: v[j] is the value at position base + q + j * 2^(lm0-1).
+// Stage lm pairs positions p and p + 2^(lm-1) with the twiddle w_(2^lm)^(p mod 2^(lm-1)),
+// exactly as the one-stage-at-a-time form.
+template <int R>
+__device__ __forceinline__ void group_stages(float2 (&v)[1 << R], int q, int lm0,
+                                             const float2 *__restrict__ tw)
+{
+    const int half = 1 << (lm0 - 1);
+#pragma unroll
+    for (int s = 0; s < R; s++) {
+        const int twstep = kSmallFFT >> (lm0 + s);
+#pragma unroll
+        for (int j0 = 0; j0 < (1 << R); j0++) {
+            if (j0 & (1 << s)) continue;
+            const int qq = q + (j0 & ((1 << s) - 1)) * half;
+            butterfly(v[j0], v[j0 | (1 << s)], __ldg(&tw[qq * twstep]));
+        }
+    }
+}
+
+// First group of stages (lm0 = 1): the inputs sit in natural order in shared memory and
+// the group at bit-reversed positions g 2^R + j reads natural index bitrev(g 2^R + j) of
+// its transform.  Every thread reads its group before any thread writes (the positions
+// differ), so a CTA does all TP / 2^R groups at once: TP / 2^R <= blockDim.x holds for
+// every tile (TP <= 4096 = 8 kFftThreads with R = 3).
+template <int R>
+__device__ __forceinline__ void first_stages(float2 *sm, int TP, int logP,
+                                             const float2 *__restrict__ tw)
+{
+    constexpr int E = 1 << R;
+    const int g = threadIdx.x;
+    const bool have = g < (TP >> R);
+    float2 v[E];
+    if (have) {
+        const int P = 1 << logP;
+#pragma unroll
+        for (int j = 0; j < E; j++) {
+            const int p = g * E + j;
+            const int nat = (p & ~(P - 1)) | (int)(__brev((unsigned)(p & (P - 1))) >> (32 - logP));
+            v[j] = sm[padi(nat)];
+        }
+    }
+    __syncthreads();
+    if (have) {
+        group_stages<R>(v, 0, 1, tw);
+#pragma unroll
+        for (int j = 0; j < E; j++) sm[padi(g * E + j)] = v[j];
+    }
+    __syncthreads();
+}
+
+// Later groups of stages, in place: each group reads and writes only its own positions.
+template <int R>
+__device__ __forceinline__ void next_stages(float2 *sm, int TP, int lm0,
+                                            const float2 *__restrict__ tw)
+{
+    constexpr int E = 1 << R;
+    const int half = 1 << (lm0 - 1);
+    for (int g = threadIdx.x; g < (TP >> R); g += blockDim.x) {
+        const int q = g & (half - 1);
+        const int base = ((g >> (lm0 - 1)) << (lm0 - 1 + R)) + q;
+        float2 v[E];
+#pragma unroll
+        for (int j = 0; j < E; j++) v[j] = sm[padi(base + j * half)];
+        group_stages<R>(v, q, lm0, tw);
+#pragma unroll
+        for (int j = 0; j < E; j++) sm[padi(base + j * half)] = v[j];
+    }
+    __syncthreads();
+}
+
 // T adjacent transforms t0..t0+T-1 by the whole CTA (T * P <= kSmallFFT): element j of
 // transform t0+u is src[u * in_bs + j * in_es] summed over `chunks` blocks
 // chunk_stride apart; the result k (optionally twiddled by exp(-2 pi i t k / 2^tw_logB))
 // goes to dst[u * out_bs + k * out_es].  Threads walk the tile along whichever stride
-// is 1, so strided (column) transforms still load and store whole segments.
+// is 1, so strided (column) transforms still load and store whole segments.  The
+// log2 P radix-2 stages run three at a time on 8-value groups in registers.
 __device__ void fft_tile(const float2 *src, int64_t in_es, int64_t in_bs, int chunks,
                          int64_t chunk_stride, float2 *dst, int64_t out_es, int64_t out_bs,
                          int logP, int T, int tw_logB, int64_t t0, float2 *sm,
-                         const float2 *__restrict__ tw)
+                         const float2 *__restrict__ tw, float *edst, uint32_t *emax)
 {
     const int P = 1 << logP;
     const int TP = T * P;
@@ -78,39 +167,62 @@ __device__ void fft_tile(const float2 *src, int64_t in_es, int64_t in_bs, int ch
             v.x += w.x;
             v.y += w.y;
         }
-        const int r = logP ? (int)(__brev((unsigned)j) >> (32 - logP)) : 0;
-        sm[u * P + r] = v;
+        sm[padi(u * P + j)] = v;
     }
     __syncthreads();
-    for (int lm = 1; lm <= logP; lm++) {
-        const int half = 1 << (lm - 1);
-        const int twstep = kSmallFFT >> lm;
-        for (int k = threadIdx.x; k < TP / 2; k += blockDim.x) {
-            const int u = k >> (logP - 1);
-            const int kk = k & (P / 2 - 1);
-            const int q = kk & (half - 1);
-            const int i0 = u * P + ((kk >> (lm - 1)) << lm) + q;
-            const int i1 = i0 + half;
-            const float2 w = tw[q * twstep];
-            const float2 a = sm[i0], b = sm[i1];
-            const float2 wb = make_float2(w.x * b.x - w.y * b.y, w.x * b.y + w.y * b.x);
-            sm[i0] = make_float2(a.x + wb.x, a.y + wb.y);
-            sm[i1] = make_float2(a.x - wb.x, a.y - wb.y);
+    // stages 1 .. logP: groups of three, the first one also doing the bit reversal
+    const int r0 = logP < kMaxRadixLog ? logP : kMaxRadixLog;
+    switch (r0) {
+    case 4: first_stages<4>(sm, TP, logP, tw); break;
+    case 3: first_stages<3>(sm, TP, logP, tw); break;
+    case 2: first_stages<2>(sm, TP, logP, tw); break;
+    case 1: first_stages<1>(sm, TP, logP, tw); break;
+    default: break;
+    }
+    for (int lm0 = r0 + 1; lm0 <= logP;) {
+        const int r = logP - lm0 + 1 < kMaxRadixLog ? logP - lm0 + 1 : kMaxRadixLog;
+        switch (r) {
+        case 4: next_stages<4>(sm, TP, lm0, tw); break;
+        case 3: next_stages<3>(sm, TP, lm0, tw); break;
+        case 2: next_stages<2>(sm, TP, lm0, tw); break;
+        default: next_stages<1>(sm, TP, lm0, tw); break;
         }
-        __syncthreads();
+        lm0 += r;
     }
     const bool out_rows = out_es == 1;
+    const int tw_shift = tw_logB - 12;   // four-step twiddle: coarse and fine table parts
+    float m = 0.f;
     for (int idx = threadIdx.x; idx < TP; idx += blockDim.x) {
         const int u = out_rows ? idx >> logP : idx % T;
         const int k = out_rows ? idx & (P - 1) : idx / T;
-        float2 v = sm[u * P + k];
+        float2 v = sm[padi(u * P + k)];
         if (tw_logB >= 0) {
-            const int64_t m = ((t0 + u) * k) & (((int64_t)1 << tw_logB) - 1);
-            float sn, cs;
-            sincospif(-ldexpf((float)m, 1 - tw_logB), &sn, &cs);
-            v = make_float2(v.x * cs - v.y * sn, v.x * sn + v.y * cs);
+            // exp(-2 pi i m / B), m = t k mod B, B = 2^tw_logB in (2^12, 2^24]
+            const uint32_t m = (uint32_t)(((t0 + u) * k) & (((int64_t)1 << tw_logB) - 1));
+            const float2 c = __ldg(&tw[m >> tw_shift]);
+            const float2 f = __ldg(&tw[kSmallFFT + ((m & ((1u << tw_shift) - 1)) << (24 - tw_logB))]);
+            const float2 w = make_float2(c.x * f.x - c.y * f.y, c.x * f.y + c.y * f.x);
+            v = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
         }
-        dst[(int64_t)u * out_bs + (int64_t)k * out_es] = v;
+        const int64_t o = (int64_t)u * out_bs + (int64_t)k * out_es;
+        dst[o] = v;
+        if (edst) {
+            const float e = fmaf(v.x, v.x, v.y * v.y);
+            edst[o] = e;
+            m = fmaxf(m, e);
+        }
+    }
+    if (emax) {
+        // block maximum of the energies, one atomic per tile (E >= 0: bit order = order)
+        __shared__ float wmax[kSmallFFT / 256];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = fmaxf(m, wmax[w]);
+            if (m > 0.f) atomicMax(emax, __float_as_uint(m));
+        }
     }
     __syncthreads();
 }
@@ -125,14 +237,23 @@ __device__ __forceinline__ int tile_of(const FftShape &f)
     return T;
 }
 
+// Is `pass` the one that writes the final spectrum?
+__device__ __forceinline__ bool final_pass(int ndim, int logB, int pass)
+{
+    return (ndim == 1 && logB <= 12) ? pass == 0 : pass == 1;
+}
+
 // Dynamic pass over the nh hashes of the job at B* (shape read on the device).
 // part: [hash][chunk][B or B^2]; 1D four-step pass 0 writes `tmp`, pass 1 reads it;
-// everything else ends in `fin` (2D pass 1 in place).
-__global__ void __launch_bounds__(256) k_fft_pass(int ndim, int pass, const Job *job,
+// everything else ends in `fin` (2D pass 1 in place).  The final pass also writes the
+// energies |Zhat|^2 of the first n_energy hashes (layout of `fin`, base `energy`) and
+// their maxima into stats[kMaxLogB + h].max_bits.
+__global__ void __launch_bounds__(kFftThreads, 2) k_fft_pass(int ndim, int pass, const Job *job,
                                                   const float2 *__restrict__ part, float2 *tmp,
-                                                  float2 *fin, const float2 *__restrict__ tw)
+                                                  float2 *fin, const float2 *__restrict__ tw,
+                                                  float *energy, HashStats *stats, int n_energy)
 {
-    __shared__ float2 sm[kSmallFFT];
+    __shared__ float2 sm[kSmemPadded];
     if (!job->active) return;
     const int logB = job->logB, nh = job->nh;
     const int chunks = pass == 0 ? job->chunks : 1;
@@ -145,11 +266,14 @@ __global__ void __launch_bounds__(256) k_fft_pass(int ndim, int pass, const Job 
     const int T = tile_of(f);
     const int64_t tiles = f.ntrans / T;
     const int64_t total = (int64_t)nh * tiles;
+    const bool fin_pass = energy && final_pass(ndim, logB, pass);
     for (int64_t tr = blockIdx.x; tr < total; tr += gridDim.x) {
         const int64_t h = tr / tiles, t = (tr % tiles) * T;
+        const bool e = fin_pass && h < n_energy;
         fft_tile(in + h * in_hash + t * f.in_bs, f.in_es, f.in_bs, chunks, f.hash_stride,
                  out + h * f.hash_stride + t * f.out_bs, f.out_es, f.out_bs, f.logP, T, f.tw_logB,
-                 t, sm, tw);
+                 t, sm, tw, e ? energy + h * f.hash_stride + t * f.out_bs : nullptr,
+                 e ? &stats[kMaxLogB + h].max_bits : nullptr);
     }
 }
 
@@ -166,11 +290,14 @@ struct FftBatch {
     FftJob j[kMaxLogB];
 };
 
-__global__ void __launch_bounds__(256) k_fft_batch(int ndim, int pass, const FftBatch Bt,
+// energy != nullptr: the final pass also writes |Zhat|^2 at the output offsets of
+// `energy` and the maximum into stats[logB].max_bits (the tuning trial's slot).
+__global__ void __launch_bounds__(kFftThreads, 2) k_fft_batch(int ndim, int pass, const FftBatch Bt,
                                                    const float2 *__restrict__ part, float2 *tmp,
-                                                   float2 *fin, const float2 *__restrict__ tw)
+                                                   float2 *fin, const float2 *__restrict__ tw,
+                                                   float *energy, HashStats *stats)
 {
-    __shared__ float2 sm[kSmallFFT];
+    __shared__ float2 sm[kSmemPadded];
     for (int64_t tr = blockIdx.x; tr < Bt.total; tr += gridDim.x) {
         int jb = 0;
         while (jb + 1 < Bt.njobs && tr >= Bt.j[jb + 1].tr_start) jb++;
@@ -183,20 +310,25 @@ __global__ void __launch_bounds__(256) k_fft_batch(int ndim, int pass, const Fft
             pass == 0 ? part + J.in_off : (ndim == 1 ? tmp + J.tmp_off : fin + J.out_off);
         float2 *out = (pass == 0 && four_step) ? tmp + J.tmp_off : fin + J.out_off;
         const int chunks = pass == 0 ? J.chunks : 1;
+        const bool e = energy && final_pass(ndim, J.logB, pass);
         fft_tile(in + t * f.in_bs, f.in_es, f.in_bs, chunks, f.hash_stride, out + t * f.out_bs,
-                 f.out_es, f.out_bs, f.logP, T, f.tw_logB, t, sm, tw);
+                 f.out_es, f.out_bs, f.logP, T, f.tw_logB, t, sm, tw,
+                 e ? energy + J.out_off + t * f.out_bs : nullptr,
+                 e ? &stats[J.logB].max_bits : nullptr);
     }
 }
 
 // Dynamic job at B*: both passes always launched; each decides on the device.
 void launch_bucket_fft_dynamic(const atsfft_plan_s *P, const Job *job, const float2 *part,
-                               float2 *out, cudaStream_t s)
+                               float2 *out, float *energy, int n_energy, cudaStream_t s)
 {
-    const int grid = P->num_sms * 8;
-    k_fft_pass<<<grid, 256, 0, s>>>(P->ndim, 0, job, part, P->d_fft_tmp, out, P->d_tw);
+    const int grid = P->num_sms * 2;   // resident CTAs; a grid-stride loop covers the tiles
+    k_fft_pass<<<grid, kFftThreads, 0, s>>>(P->ndim, 0, job, part, P->d_fft_tmp, out, P->d_tw,
+                                            energy, P->d_stats, n_energy);
     count_launch(P);
     if (P->ndim == 2 || P->b_hi > 12) {
-        k_fft_pass<<<grid, 256, 0, s>>>(P->ndim, 1, job, part, P->d_fft_tmp, out, P->d_tw);
+        k_fft_pass<<<grid, kFftThreads, 0, s>>>(P->ndim, 1, job, part, P->d_fft_tmp, out, P->d_tw,
+                                                energy, P->d_stats, n_energy);
         count_launch(P);
     }
 }
@@ -205,7 +337,7 @@ void launch_bucket_fft_dynamic(const atsfft_plan_s *P, const Job *job, const flo
 // output offset out_off[i]); the four-step intermediate reuses the output offsets.
 void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB, const int *chunks,
                              const int64_t *in_off, const int64_t *out_off, const float2 *part,
-                             float2 *out, cudaStream_t s)
+                             float2 *out, float *energy, cudaStream_t s)
 {
     for (int pass = 0; pass < 2; pass++) {
         FftBatch Bt;
@@ -250,10 +382,10 @@ void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB,
             Bt.total += ntrans;
         }
         if (Bt.njobs == 0) continue;
-        const int64_t cap = (int64_t)P->num_sms * 8;
+        const int64_t cap = (int64_t)P->num_sms * 2;
         const int64_t grid = Bt.total < cap ? Bt.total : cap;
-        k_fft_batch<<<(unsigned)grid, 256, 0, s>>>(P->ndim, pass, Bt, part, P->d_fft_tmp, out,
-                                                   P->d_tw);
+        k_fft_batch<<<(unsigned)grid, kFftThreads, 0, s>>>(P->ndim, pass, Bt, part, P->d_fft_tmp, out,
+                                                   P->d_tw, energy, P->d_stats);
         count_launch(P);
     }
 }

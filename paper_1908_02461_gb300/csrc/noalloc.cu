@@ -39,24 +39,13 @@ constexpr size_t kOffPart = 0;
 constexpr size_t kOffTmp = kOffPart + kElems18 * sizeof(float2);
 constexpr size_t kOffZ = kOffTmp + kElems18 * sizeof(float2);
 constexpr size_t kOffTw = kOffZ + kElems18 * sizeof(float2);
-constexpr size_t kOffWin = kOffTw + (size_t)kSmallFFT * sizeof(float2);
+constexpr size_t kOffWin = kOffTw + (size_t)kTwEntries * sizeof(float2);
 constexpr size_t kOffS0 = kOffWin + 4096;                         // WindowParam table
 constexpr size_t kOffResp = kOffS0 + 256;
 constexpr size_t kOffPartial = kOffResp + kElems18 * sizeof(double);
 constexpr size_t kPartialDoubles = (kNoAllocBytes - kOffPartial) / sizeof(double);
 static_assert(kOffPartial < kNoAllocBytes, "no-alloc scratch layout overflows");
 static_assert(sizeof(WindowParam) * kMaxLogB <= 4096, "window table slot too small");
-
-// Twiddles exp(-2 pi i j / kSmallFFT) (same values as the plan's table).
-__global__ void k_noalloc_twiddles(float2 *tw)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < kSmallFFT) {
-        double s, c;
-        sincospi(-2.0 * (double)j / (double)kSmallFFT, &s, &c);
-        tw[j] = make_float2((float)c, (float)s);
-    }
-}
 
 // Bucket order: Zhat[c] = P[sigma' c] exp(2 pi i c sigma' tau / B), hash passed by value.
 __global__ void k_noalloc_unpermute(const float2 *spec, HashParam hp, int logB, float2 *out)
@@ -73,7 +62,8 @@ __global__ void k_noalloc_unpermute(const float2 *spec, HashParam hp, int logB, 
     }
 }
 
-// plan.cu's plan-time window kernels
+// plan.cu's plan-time kernels: window normalisation, FFT twiddles
+__global__ void k_twiddles(float2 *tw);
 __global__ void k_window_partial(int64_t n, int logB, double s, int h, double *partial, int nchunks);
 __global__ void k_window_finish(int64_t D, const double *partial, int nchunks, double *resp,
                                 double *S0_out);
@@ -88,7 +78,7 @@ static atsfft_status noalloc_setup(int dev, cudaStream_t s, unsigned char **base
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_status(e);
         d.base = (unsigned char *)ptr;
-        k_noalloc_twiddles<<<kSmallFFT / 256, 256, 0, s>>>((float2 *)(d.base + kOffTw));
+        k_twiddles<<<kTwEntries / 256, 256, 0, s>>>((float2 *)(d.base + kOffTw));
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_status(e);

@@ -189,13 +189,41 @@ __global__ void k_window_finish(int64_t D, const double *partial, int nchunks, d
     }
 }
 
-// Twiddles exp(-2 pi i j / kSmallFFT) for the shared-memory FFT, from exact fractions.
+// Reciprocal gains 1 / Ghat'(o) in FP32 for the estimates of Eq. (11).
+__global__ void k_recip_gain(const double *resp, int64_t count, float *rgain)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count;
+         j += (int64_t)gridDim.x * blockDim.x)
+        rgain[j] = (float)(1.0 / resp[j]);
+}
+
+// Phase factors exp(2 pi i m / n) for an exact integer m in [0, n): m = hi 2^s + lo,
+// table entries lo < 2^s, then 2^s + hi for hi < n / 2^s, each from an exact fraction
+// in FP64 and rounded to FP32; the product of the two is within 2 FP32 ulps.
+__global__ void k_phase_table(int logn, int s_bits, float2 *tab)
+{
+    const int64_t nlo = (int64_t)1 << s_bits, nhi = ((int64_t)1 << logn) >> s_bits;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nlo + nhi;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = j < nlo ? j : (j - nlo) << s_bits;
+        double sn, cs;
+        sincospi(ldexp(2.0 * (double)m, -logn), &sn, &cs);
+        tab[j] = make_float2((float)cs, (float)sn);
+    }
+}
+
+// Twiddles from exact fractions, for the shared-memory FFT: entry j < 4096 is
+// exp(-2 pi i j / 4096); entry 4096 + j is exp(-2 pi i j / 2^24), the fine factor of
+// the four-step twiddle exp(-2 pi i m / B) = coarse(m >> (b - 12)) fine(low bits of m).
 __global__ void k_twiddles(float2 *tw)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < kSmallFFT) {
+    if (j < kTwEntries) {
         double s, c;
-        sincospi(-2.0 * (double)j / (double)kSmallFFT, &s, &c);
+        if (j < kSmallFFT)
+            sincospi(-2.0 * (double)j / (double)kSmallFFT, &s, &c);
+        else
+            sincospi(-2.0 * (double)(j - kSmallFFT) / 16777216.0, &s, &c);
         tw[j] = make_float2((float)c, (float)s);
     }
 }
@@ -255,7 +283,7 @@ static bool params_ok(const atsfft_params *p)
 
 static void plan_free(atsfft_plan_s *P)
 {
-    void *ptrs[] = {P->d_tune, P->d_le, P->d_win, P->d_resp, P->d_tw, P->d_part, P->d_tz,
+    void *ptrs[] = {P->d_tune, P->d_le, P->d_win, P->d_resp, P->d_rgain, P->d_phase, P->d_tw, P->d_part, P->d_tz,
                     P->d_z, P->d_fft_tmp, P->d_energy, P->d_stats, P->d_hist, P->d_lmax,
                     P->d_sel, P->d_votes, P->d_blk, P->d_state, P->d_tjob, P->d_tstat,
                     P->d_lstat};
@@ -384,7 +412,10 @@ extern "C" atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t
     A((void **)&P->d_le, sizeof(HashParam) * (2 * kMaxLoops + 1));
     A((void **)&P->d_win, sizeof(WindowParam) * kMaxLogB);
     A((void **)&P->d_resp, sizeof(double) * resp_total);
-    A((void **)&P->d_tw, sizeof(float2) * kSmallFFT);
+    A((void **)&P->d_rgain, sizeof(float) * resp_total);
+    P->phase_s = (P->logn + 1) / 2;
+    A((void **)&P->d_phase, sizeof(float2) * (((size_t)1 << P->phase_s) + ((size_t)P->n >> P->phase_s)));
+    A((void **)&P->d_tw, sizeof(float2) * kTwEntries);
     A((void **)&P->d_part, sizeof(float2) * part);
     A((void **)&P->d_tz, sizeof(float2) * tz_total);
     A((void **)&P->d_z, sizeof(float2) * nh_le * nb_max);
@@ -432,7 +463,9 @@ extern "C" atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        k_twiddles<<<kSmallFFT / 256, 256>>>(P->d_tw);
+        k_twiddles<<<kTwEntries / 256, 256>>>(P->d_tw);
+        k_recip_gain<<<P->num_sms * 4, 256>>>(P->d_resp, resp_total, P->d_rgain);
+        k_phase_table<<<P->num_sms, 256>>>(P->logn, P->phase_s, P->d_phase);
         e = cudaGetLastError();
     }
     double S0[kMaxLogB];

@@ -151,43 +151,71 @@ __device__ float threshold_of(const HashStats &st, const StatsParams &S)
     return T;
 }
 
+// Appends bucket c to the job's list of maxima when `is_max`: one atomic per warp for
+// all its lanes that found one (the list order is immaterial).
+__device__ __forceinline__ void append_max(HashStats &st, const StatJob &J, const StatsParams &S,
+                                           bool is_max, int32_t c)
+{
+    const unsigned am = __activemask();
+    const unsigned bal = __ballot_sync(am, is_max);
+    if (!bal) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(bal) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&st.nmax, (uint32_t)__popc(bal));
+    base = __shfl_sync(am, base, leader);
+    if (is_max && J.list >= 0) {
+        const uint32_t pos = base + __popc(bal & ((1u << lane) - 1));
+        if (pos < S.cap) S.lists[(int64_t)J.list * S.cap + pos] = c;
+    }
+}
+
 // Local maxima of one job over P-indices j = j0, j0 + step, ... < j1 (bucket
-// c = sigma j, neighbours at j +- sigma'); returns how many energies exceed X.
+// c = sigma j, neighbours at j +- sigma'); returns how many energies exceed X.  Four
+// energies are loaded before any is tested.
 __device__ uint32_t localmax_range(const StatJob &J, const StatsParams &S, float T, int64_t j0,
                                    int64_t j1, int64_t step, float X)
 {
     HashStats &st = S.stats[J.slot];
     const int logB = J.logB;
     const uint32_t B = 1u << logB, mask = B - 1;
-    const float *E = J.energy;
+    const float *__restrict__ E = J.energy;
     const uint32_t s1 = J.hash->sigma[0] & mask, p1 = J.hash->sinv[0] & mask;
     const uint32_t s2 = J.hash->sigma[1] & mask, p2 = J.hash->sinv[1] & mask;
     uint32_t above = 0;
-    for (int64_t j = j0; j < j1; j += step) {
-        const float e = E[j];
-        above += e > X;
-        if (!(e > T)) continue;
-        bool ok = true;
-        int32_t c;
-        if (S.ndim == 1) {
-            const uint32_t jj = (uint32_t)j;
-            c = (int32_t)((s1 * jj) & mask);
-            ok = dominates(e, E[(jj - p1) & mask], S.up, 0, -1) &&
-                 dominates(e, E[(jj + p1) & mask], S.up, 0, 1);
-        } else {
-            const uint32_t jA = (uint32_t)(j >> logB), jB = (uint32_t)(j & mask);
-            c = (int32_t)((((s1 * jA) & mask) << logB) | ((s2 * jB) & mask));
-            for (int d1 = -1; d1 <= 1 && ok; d1++)
-                for (int d2 = -1; d2 <= 1 && ok; d2++) {
-                    if (d1 == 0 && d2 == 0) continue;
-                    const uint32_t m1 = (jA + (uint32_t)d1 * p1) & mask;
-                    const uint32_t m2 = (jB + (uint32_t)d2 * p2) & mask;
-                    ok = dominates(e, E[((int64_t)m1 << logB) | m2], S.up, d1, d2);
-                }
+    for (int64_t jb = j0; jb < j1; jb += 4 * step) {
+        float ev[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t j = jb + u * step;
+            ev[u] = j < j1 ? __ldg(&E[j]) : 0.f;
         }
-        if (ok) {
-            const uint32_t pos = atomicAdd(&st.nmax, 1u);
-            if (J.list >= 0 && pos < S.cap) S.lists[(int64_t)J.list * S.cap + pos] = c;
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int64_t j = jb + u * step;
+            const float e = ev[u];
+            const bool valid = j < j1;
+            above += valid && e > X;
+            bool ok = valid && e > T;
+            int32_t c = 0;
+            if (ok) {
+                if (S.ndim == 1) {
+                    const uint32_t jj = (uint32_t)j;
+                    c = (int32_t)((s1 * jj) & mask);
+                    ok = dominates(e, __ldg(&E[(jj - p1) & mask]), S.up, 0, -1) &&
+                         dominates(e, __ldg(&E[(jj + p1) & mask]), S.up, 0, 1);
+                } else {
+                    const uint32_t jA = (uint32_t)(j >> logB), jB = (uint32_t)(j & mask);
+                    c = (int32_t)((((s1 * jA) & mask) << logB) | ((s2 * jB) & mask));
+                    for (int d1 = -1; d1 <= 1 && ok; d1++)
+                        for (int d2 = -1; d2 <= 1 && ok; d2++) {
+                            if (d1 == 0 && d2 == 0) continue;
+                            const uint32_t m1 = (jA + (uint32_t)d1 * p1) & mask;
+                            const uint32_t m2 = (jB + (uint32_t)d2 * p2) & mask;
+                            ok = dominates(e, __ldg(&E[((int64_t)m1 << logB) | m2]), S.up, d1, d2);
+                        }
+                }
+            }
+            append_max(st, J, S, ok, c);
         }
     }
     return above;
@@ -198,6 +226,15 @@ __device__ void localmax_job(const StatJob &J, const StatsParams &S, float T, in
 {
     (void)above_out;
     localmax_range(J, S, T, gtid, nb_of(S.ndim, J.logB), gthreads, X);
+}
+
+// hist[bin] += 1 for every calling lane, one shared atomic per distinct bin in the warp
+// (radix digits of nearly equal energies share a few bins).
+__device__ __forceinline__ void hist_add(uint32_t *hist, uint32_t bin)
+{
+    const unsigned am = __activemask();
+    const unsigned peers = __match_any_sync(am, bin);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
 }
 
 // digit 0: bits [20, 32), digit 1: [8, 20), digit 2: [0, 8)
@@ -296,7 +333,7 @@ __device__ uint32_t block_median(const float *E, int nb)
         const uint32_t prefix = sh_prefix;
         for (int i = threadIdx.x; i < nb; i += blockDim.x) {
             const uint32_t v = vals[i];
-            if (d == 0 || (v >> hi) == prefix) atomicAdd(&hist[(v >> lo) & ((1u << width) - 1)], 1u);
+            if (d == 0 || (v >> hi) == prefix) hist_add(hist, (v >> lo) & ((1u << width) - 1));
         }
         __syncthreads();
         __shared__ uint32_t fb, fr;
@@ -317,8 +354,8 @@ __device__ void localmax_block(const StatJob &J, const StatsParams &S, float T)
     __syncthreads();
 }
 
-// Energies, threshold and local maxima of njobs hashes.  Returns false if a barrier
-// failed.
+// Threshold and local maxima of njobs hashes whose energies and maxima the bucket FFTs
+// wrote.  Returns false if a barrier failed.
 __device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &S,
                              GridBarrier *gb, int *status)
 {
@@ -336,25 +373,7 @@ __device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &
     }
     __syncthreads();
     const int64_t ntasks = tstart[njobs];
-    // A: energies and their maximum
-    for (int64_t task = blockIdx.x; task < ntasks; task += gridDim.x) {
-        int jb = 0;
-        while (task >= tstart[jb + 1]) jb++;
-        const StatJob &J = jobs[jb];
-        const int64_t nb = nb_of(S.ndim, J.logB);
-        const int64_t e0 = (task - tstart[jb]) * kTask;
-        const int64_t e1 = min(e0 + kTask, nb);
-        float m = 0.f;
-        for (int64_t j = e0 + threadIdx.x; j < e1; j += blockDim.x) {
-            const float2 v = J.spec[j];
-            const float e = v.x * v.x + v.y * v.y;
-            J.energy[j] = e;
-            m = fmaxf(m, e);
-        }
-        m = block_max(m);
-        if (threadIdx.x == 0 && m > 0.f) atomicMax(&S.stats[J.slot].max_bits, __float_as_uint(m));
-    }
-    if (!grid_sync(gb, status)) return false;
+    // (the energies and their maximum come from the bucket FFTs' final pass)
     // B: local maxima with T = thr_rel * maxE, and the count deciding if the median matters
     for (int64_t task = blockIdx.x; task < ntasks; task += gridDim.x) {
         int jb = 0;
@@ -426,7 +445,7 @@ __device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &
             __syncthreads();
             for (int64_t j = gtid; j < nb; j += gthreads) {
                 const uint32_t bits = __float_as_uint(J.energy[j]);
-                if (digit == 0 || (bits >> hi) == prefix) atomicAdd(&h[(bits >> lo) & ((1u << width) - 1)], 1u);
+                if (digit == 0 || (bits >> hi) == prefix) hist_add(h, (bits >> lo) & ((1u << width) - 1));
             }
             __syncthreads();
             for (int b = threadIdx.x; b < (1 << width); b += blockDim.x)
@@ -576,8 +595,10 @@ struct LocTailArgs {
     uint32_t *blk;          // per-block kept counts / offsets (gridDim entries)
     const HashParam *le;    // location then estimation hashes
     const float2 *z;        // spectra at B*: location then estimation hashes
-    const double *resp;
+    const float *rgain;     // 1 / Ghat' per B (offsets ro)
     RespOffsets ro;
+    const float2 *phase;    // exp(2 pi i m / n) tables, split at phase_s bits
+    int phase_s;
     int logn;
     int64_t *loc;
     float2 *val;
@@ -606,7 +627,7 @@ __device__ uint32_t block_kth(int64_t cnt, uint32_t k, KeyF key, PredF pred)
         for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
             if (!pred(i)) continue;
             const uint32_t kk = key(i);
-            if (pass == 0 || (kk >> (shift + 8)) == prefix) atomicAdd(&hist[(kk >> shift) & 255u], 1u);
+            if (pass == 0 || (kk >> (shift + 8)) == prefix) hist_add(hist, (kk >> shift) & 255u);
         }
         __syncthreads();
         __shared__ uint32_t fb, fr;
@@ -627,7 +648,7 @@ constexpr int kTopStage = 4096;
 // ascending bucket order.
 __device__ void topnum_block(const StatJob &J, const LocTailArgs &A, int64_t num)
 {
-    __shared__ uint32_t n_sel, n_hi;
+    __shared__ uint32_t n_sel;
     HashStats &st = A.S.stats[J.slot];
     const int ndim = A.S.ndim;
     const int logB = J.logB;
@@ -650,10 +671,7 @@ __device__ void topnum_block(const StatJob &J, const LocTailArgs &A, int64_t num
     if (staged)
         for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) es[i] = energy_global(i);
     auto energy_of = [&](int64_t i) -> float { return staged ? es[i] : energy_global(i); };
-    if (threadIdx.x == 0) {
-        n_sel = 0;
-        n_hi = 0;
-    }
+    if (threadIdx.x == 0) n_sel = 0;
     __syncthreads();
     if (cnt <= num) {
         for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) out[i] = list[i];
@@ -664,22 +682,30 @@ __device__ void topnum_block(const StatJob &J, const LocTailArgs &A, int64_t num
             [&](int64_t) { return true; });
         const float V = __uint_as_float(vb);
         const float hi = V * A.eta_up, lo = V * A.eta_dn;
-        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x)
-            if (energy_of(i) > hi) atomicAdd(&n_hi, 1u);
-        __syncthreads();
-        const uint32_t need = (uint32_t)num - n_hi;
+        uint32_t mine = 0;
+        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) mine += energy_of(i) > hi;
+        const uint32_t nhi = block_sum(mine);
+        const uint32_t need = (uint32_t)num - nhi;
         const uint32_t cthr = block_kth(
             cnt, need - 1, [&](int64_t i) { return (uint32_t)list[i]; },
             [&](int64_t i) {
                 const float e = energy_of(i);
                 return e >= lo && e <= hi;
             });
-        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-            const float e = energy_of(i);
-            if (e > hi || (e >= lo && e <= hi && (uint32_t)list[i] <= cthr)) {
-                const uint32_t pos = atomicAdd(&n_sel, 1u);
-                out[pos] = list[i];
+        // the kept maxima, appended with one shared atomic per warp and round
+        const int lane = threadIdx.x & 31;
+        for (int64_t i0 = 0; i0 < cnt; i0 += blockDim.x) {
+            const int64_t i = i0 + threadIdx.x;
+            bool keep = false;
+            if (i < cnt) {
+                const float e = energy_of(i);
+                keep = e > hi || (e >= lo && e <= hi && (uint32_t)list[i] <= cthr);
             }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            uint32_t base = 0;
+            if (lane == 0 && bal) base = atomicAdd(&n_sel, (uint32_t)__popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (keep) out[base + __popc(bal & ((1u << lane) - 1))] = list[i];
         }
     }
     __syncthreads();
@@ -709,25 +735,34 @@ __device__ __forceinline__ void axis_terms(uint64_t i, const HashParam &hp, int 
     mtau = ((uint64_t)hp.tau[axis] * i) & (n - 1);
 }
 
-// Eq. (11) for coordinate `coord` and estimation hash l, in FP64.
-__device__ void estimate_term(uint64_t coord, const LocTailArgs &A, int b, int l, double &re,
-                              double &im)
+// exp(2 pi i m / n) for an exact integer m in [0, n): product of the two table parts.
+__device__ __forceinline__ float2 phase_of(uint64_t m, const LocTailArgs &A)
+{
+    const float2 lo = __ldg(&A.phase[m & ((1ull << A.phase_s) - 1)]);
+    const float2 hi = __ldg(&A.phase[(1ull << A.phase_s) + (m >> A.phase_s)]);
+    return make_float2(lo.x * hi.x - lo.y * hi.y, lo.x * hi.y + lo.y * hi.x);
+}
+
+// Eq. (11) for coordinate `coord` and estimation hash l: the bucket value times the
+// phase exp(2 pi i m / n) (m from exact integer index arithmetic) divided by the window
+// gain Ghat'(o) (as a reciprocal from the plan's FP64 table).
+__device__ float2 estimate_term(uint64_t coord, const LocTailArgs &A, int b, int l)
 {
     const int logn = A.logn, ndim = A.S.ndim;
     const uint64_t n = 1ull << logn, D = 1ull << (logn - b);
     const int64_t nb = nb_of(ndim, b);
-    const double *G = A.resp + A.ro.off[b];
+    const float *RG = A.rgain + A.ro.off[b];
     const HashParam hp = A.le[A.L_loc + l];
     const float2 *Pz = A.z + (int64_t)(A.L_loc + l) * nb;
     uint64_t jP, kph, m;
     int64_t oi;
     float2 pv;
-    double gain;
+    float rg;
     uint64_t kang;
     if (ndim == 1) {
         axis_terms(coord, hp, 0, logn, b, jP, kph, oi, m);
         pv = Pz[jP];
-        gain = G[oi];
+        rg = __ldg(&RG[oi]);
         kang = (kph * D + n - m) & (n - 1);
     } else {
         const uint64_t i = coord >> logn, j = coord & (n - 1);
@@ -736,13 +771,11 @@ __device__ void estimate_term(uint64_t coord, const LocTailArgs &A, int b, int l
         axis_terms(i, hp, 0, logn, b, jP, kph, oi, m);
         axis_terms(j, hp, 1, logn, b, jP2, kph2, oi2, m2);
         pv = Pz[(jP << b) | jP2];
-        gain = G[oi] * G[oi2];
+        rg = __ldg(&RG[oi]) * __ldg(&RG[oi2]);
         kang = ((kph + kph2) * D + 2 * n - m - m2) & (n - 1);
     }
-    double sn, cs;
-    sincospi(2.0 * (double)kang / (double)n, &sn, &cs);
-    re = ((double)pv.x * cs - (double)pv.y * sn) / gain;
-    im = ((double)pv.x * sn + (double)pv.y * cs) / gain;
+    const float2 w = phase_of(kang, A);
+    return make_float2((pv.x * w.x - pv.y * w.y) * rg, (pv.x * w.y + pv.y * w.x) * rg);
 }
 
 // Estimates of the kept coordinates: a group of `grp` lanes (grp >= L_est, a power of two)
@@ -758,24 +791,34 @@ __device__ void estimate_all(const LocTailArgs &A, int64_t cnt, int b)
     for (int64_t base = warp * per_warp; base < cnt; base += nwarps * per_warp) {
         const int64_t s = base + lane / grp;
         const bool valid = s < cnt;
-        double re = 0.0, im = 0.0;
-        if (valid && gl < A.L_est) estimate_term((uint64_t)A.loc[s], A, b, gl, re, im);
-        double vr[kMaxLoops], vi[kMaxLoops];
-        for (int l = 0; l < A.L_est; l++) {
-            vr[l] = __shfl_sync(0xffffffffu, re, l, grp);
-            vi[l] = __shfl_sync(0xffffffffu, im, l, grp);
+        float2 v = make_float2(0.f, 0.f);
+        if (valid && gl < A.L_est) v = estimate_term((uint64_t)A.loc[s], A, b, gl);
+        float vr[kMaxLoops], vi[kMaxLoops];
+#pragma unroll
+        for (int l = 0; l < kMaxLoops; l++) {
+            if (l < A.L_est) {
+                vr[l] = __shfl_sync(0xffffffffu, v.x, l, grp);
+                vi[l] = __shfl_sync(0xffffffffu, v.y, l, grp);
+            }
         }
         if (valid && gl == 0) {
-            for (int a = 1; a < A.L_est; a++) {
-                const double r = vr[a], q = vi[a];
-                int k = a - 1;
-                while (k >= 0 && vr[k] > r) { vr[k + 1] = vr[k]; k--; }
-                vr[k + 1] = r;
-                k = a - 1;
-                while (k >= 0 && vi[k] > q) { vi[k + 1] = vi[k]; k--; }
-                vi[k + 1] = q;
+            // rank selection of element floor(L/2) per component (ties by hash index)
+            const int L = A.L_est, want = L / 2;
+            float mr = 0.f, mi = 0.f;
+#pragma unroll
+            for (int a = 0; a < kMaxLoops; a++) {
+                if (a >= L) break;
+                int rr = 0, ri = 0;
+#pragma unroll
+                for (int c = 0; c < kMaxLoops; c++) {
+                    if (c >= L) break;
+                    rr += vr[c] < vr[a] || (vr[c] == vr[a] && c < a);
+                    ri += vi[c] < vi[a] || (vi[c] == vi[a] && c < a);
+                }
+                if (rr == want) mr = vr[a];
+                if (ri == want) mi = vi[a];
             }
-            A.val[s] = make_float2((float)vr[A.L_est / 2], (float)vi[A.L_est / 2]);
+            A.val[s] = make_float2(mr, mi);
         }
     }
 }
@@ -810,28 +853,52 @@ __global__ void __launch_bounds__(256) k_loc_tail(const LocTailArgs A)
             off[A.L_loc] = acc;
         }
         __syncthreads();
+        __shared__ uint32_t sh_sinv[kMaxLoops][2];
+        if (threadIdx.x < A.L_loc) {
+            sh_sinv[threadIdx.x][0] = (uint32_t)A.le[threadIdx.x].sinv[0];
+            sh_sinv[threadIdx.x][1] = (uint32_t)A.le[threadIdx.x].sinv[1];
+        }
+        __syncthreads();
         const uint32_t n = 1u << logn, nmask = n - 1, Bm = (1u << b) - 1;
-        for (int64_t it = gtid; it < off[A.L_loc]; it += gthreads) {
-            int l = 0;
-            while (it >= off[l + 1]) l++;
-            const int64_t rem = it - off[l];
-            const int64_t sidx = rem >> (ndim == 1 ? logD : 2 * logD);
-            const uint32_t q = (uint32_t)(rem & (Dd - 1));
-            const uint32_t c = (uint32_t)A.sel[(int64_t)l * A.S.cap + sidx];
-            const HashParam hp = A.le[l];
-            int64_t coord;
-            if (ndim == 1) {
-                // bucket c collects permuted positions p in [c D - D/2, c D + D/2 - 1]
-                const uint32_t pp = ((c << logD) - (uint32_t)(D >> 1) + q) & nmask;
-                coord = (hp.sinv[0] * pp) & nmask;
-            } else {
-                const uint32_t c1 = c >> b, c2 = c & Bm;
-                const uint32_t q1 = q >> logD, q2 = q & (uint32_t)(D - 1);
-                const uint32_t pp1 = ((c1 << logD) - (uint32_t)(D >> 1) + q1) & nmask;
-                const uint32_t pp2 = ((c2 << logD) - (uint32_t)(D >> 1) + q2) & nmask;
-                coord = ((int64_t)((hp.sinv[0] * pp1) & nmask) << logn) | ((hp.sinv[1] * pp2) & nmask);
+        const int64_t total = off[A.L_loc];
+        // four items per thread per round: their buckets are loaded before any vote
+        constexpr int kU = 4;
+        for (int64_t it0 = gtid; it0 < total; it0 += kU * gthreads) {
+            uint32_t cb[kU], qq[kU];
+            int ll[kU];
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                const int64_t it = it0 + u * gthreads;
+                ll[u] = -1;
+                if (it < total) {
+                    int l = 0;
+                    while (it >= off[l + 1]) l++;
+                    const int64_t rem = it - off[l];
+                    const int64_t sidx = rem >> (ndim == 1 ? logD : 2 * logD);
+                    qq[u] = (uint32_t)(rem & (Dd - 1));
+                    cb[u] = (uint32_t)A.sel[(int64_t)l * A.S.cap + sidx];
+                    ll[u] = l;
+                }
             }
-            atomicAdd(&A.votes[coord >> 2], 1u << (8 * (coord & 3)));
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                if (ll[u] < 0) continue;
+                const uint32_t c = cb[u], q = qq[u];
+                const uint32_t *si = sh_sinv[ll[u]];
+                uint32_t coord;
+                if (ndim == 1) {
+                    // bucket c collects permuted positions p in [c D - D/2, c D + D/2 - 1]
+                    const uint32_t pp = ((c << logD) - (uint32_t)(D >> 1) + q) & nmask;
+                    coord = (si[0] * pp) & nmask;
+                } else {
+                    const uint32_t c1 = c >> b, c2 = c & Bm;
+                    const uint32_t q1 = q >> logD, q2 = q & (uint32_t)(D - 1);
+                    const uint32_t pp1 = ((c1 << logD) - (uint32_t)(D >> 1) + q1) & nmask;
+                    const uint32_t pp2 = ((c2 << logD) - (uint32_t)(D >> 1) + q2) & nmask;
+                    coord = (((si[0] * pp1) & nmask) << logn) | ((si[1] * pp2) & nmask);
+                }
+                atomicAdd(&A.votes[coord >> 2], 1u << (8 * (coord & 3)));
+            }
         }
         if (!grid_sync(gb, status)) return;
     } else {
@@ -996,8 +1063,10 @@ void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, int6
     A.blk = P->d_blk;
     A.le = P->d_le;
     A.z = P->d_z;
-    A.resp = P->d_resp;
+    A.rgain = P->d_rgain;
     for (int b = 0; b < kMaxLogB; b++) A.ro.off[b] = P->resp_off[b];
+    A.phase = P->d_phase;
+    A.phase_s = P->phase_s;
     A.logn = P->logn;
     A.loc = d_loc;
     A.val = d_val;
