@@ -23,6 +23,7 @@ constexpr int kSmallFFT = 4096;      // largest FFT done in one CTA
 constexpr int kTwEntries = 2 * kSmallFFT;   // coarse exp(-2 pi i j / 4096), fine exp(-2 pi i j / 2^24)
 constexpr int kMaxTrialsTrace = 64;
 constexpr int kHistBins = 4096;      // radix-select histogram bins (12-bit digits)
+constexpr int kKeptCap = 8192;       // kept coordinates ordered by rank (beyond: bitmap compaction)
 constexpr int kPersistCtas = 4;      // persistent CTAs per SM
 constexpr int kPhases = 8;           // profiled phases of one exec (see atsfft.h)
 
@@ -78,7 +79,8 @@ struct HashStats {
     float T;               // threshold
     uint32_t nmax;         // local maxima
     uint32_t nsel;         // selected by the top-num cutoff
-    uint32_t pad[7];
+    uint32_t v_bits;       // top-num pivot: bits of the num-th largest maximum energy
+    uint32_t pad[6];
 };
 
 // Grid-wide barrier of the cooperative kernels (tail.cu).
@@ -99,7 +101,6 @@ struct ExecState {
     int64_t count;         // kept coordinates
     int32_t ntrials;
     int32_t empty;         // 1: nothing to locate
-    int64_t vote_items;    // sum over location hashes of nsel * D^ndim
     int64_t trial_B[kMaxTrialsTrace];
     int64_t trial_k[kMaxTrialsTrace];
     Job job;               // location + estimation job at B*
@@ -149,10 +150,13 @@ struct atsfft_plan_s {
     int32_t *d_lmax;              // local-maximum lists [L_loc][lmax_cap]
     int32_t *d_sel;               // selected buckets    [L_loc][lmax_cap]
     int64_t lmax_cap;
-    uint32_t *d_votes;            // packed byte counters
-    int64_t nvote_words;
+    uint32_t *d_bucketbits;       // [L_loc][bucket_words] selected location buckets
+    int64_t bucket_words;
+    uint32_t *d_kept;             // kept coordinates of the last transform, unordered
+    int64_t kept_cap;
+    uint32_t *d_coordbits;        // one bit per coordinate, zero between transforms
+    int64_t coord_words;
     uint32_t *d_blk;              // compaction per-block counts / offsets
-    int64_t nblk;
     atsfft::ExecState *d_state;
     atsfft::Job *d_tjob;
     atsfft::StatJob *d_tstat;     // tuning stat jobs (built at plan time)

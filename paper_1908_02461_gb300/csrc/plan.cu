@@ -285,7 +285,7 @@ static void plan_free(atsfft_plan_s *P)
 {
     void *ptrs[] = {P->d_tune, P->d_le, P->d_win, P->d_resp, P->d_rgain, P->d_phase, P->d_tw, P->d_part, P->d_tz,
                     P->d_z, P->d_fft_tmp, P->d_energy, P->d_stats, P->d_hist, P->d_lmax,
-                    P->d_sel, P->d_votes, P->d_blk, P->d_state, P->d_tjob, P->d_tstat,
+                    P->d_sel, P->d_bucketbits, P->d_kept, P->d_coordbits, P->d_blk, P->d_state, P->d_tjob, P->d_tstat,
                     P->d_lstat};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -404,8 +404,9 @@ extern "C" atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t
     }
     P->part_elems = part;
     P->lmax_cap = ndim == 1 ? nb_max / 2 + 1 : nb_max / 4 + 1;
-    P->nvote_words = (P->ncoord + 3) / 4;
-    P->nblk = (P->nvote_words + 1023) / 1024;
+    P->bucket_words = (nb_max + 31) / 32;
+    P->kept_cap = kKeptCap;
+    P->coord_words = (P->ncoord + 31) / 32;
     P->e_loc_off = tz_total;
 
     A((void **)&P->d_tune, sizeof(HashParam) * kMaxLogB);
@@ -428,11 +429,11 @@ extern "C" atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t
     A((void **)&P->d_hist, sizeof(uint32_t) * kHistBins * (kMaxLogB + kMaxLoops));
     A((void **)&P->d_lmax, sizeof(int32_t) * P->L_loc * P->lmax_cap);
     A((void **)&P->d_sel, sizeof(int32_t) * P->L_loc * P->lmax_cap);
-    A((void **)&P->d_votes, sizeof(uint32_t) * P->nvote_words);
+    A((void **)&P->d_bucketbits, sizeof(uint32_t) * (size_t)P->L_loc * (size_t)P->bucket_words);
+    A((void **)&P->d_kept, sizeof(uint32_t) * (size_t)P->kept_cap);
+    A((void **)&P->d_coordbits, sizeof(uint32_t) * (size_t)P->coord_words);
     // per-block counts of the compaction (cooperative grid: at most a few blocks per SM)
-    A((void **)&P->d_blk, sizeof(uint32_t) * (size_t)((P->nblk + 1) > (int64_t)P->num_sms * 32
-                                                          ? (P->nblk + 1)
-                                                          : (int64_t)P->num_sms * 32));
+    A((void **)&P->d_blk, sizeof(uint32_t) * (size_t)P->num_sms * 32);
     A((void **)&P->d_state, sizeof(ExecState));
     A((void **)&P->d_tjob, sizeof(Job) * kMaxLogB);
     A((void **)&P->d_tstat, sizeof(StatJob) * kMaxLogB);
@@ -500,7 +501,7 @@ extern "C" atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t
         }
         e = cudaMemcpy(P->d_tstat, ts, sizeof(StatJob) * P->ntstat, cudaMemcpyHostToDevice);
     }
-    if (e == cudaSuccess) e = cudaMemset(P->d_votes, 0, sizeof(uint32_t) * P->nvote_words);
+    if (e == cudaSuccess) e = cudaMemset(P->d_coordbits, 0, sizeof(uint32_t) * P->coord_words);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         plan_free(P);

@@ -354,6 +354,82 @@ __device__ void localmax_block(const StatJob &J, const StatsParams &S, float T)
     __syncthreads();
 }
 
+// Local maxima of buckets [e0, e1) of one job by the whole block (e1 - e0 <= 16 x 256):
+// thread t tests P-indices e0 + t + 256 u, u < 16, from energies loaded up front; the
+// block's maxima are appended with one atomic, and the count of energies above X with
+// another.
+__device__ void localmax_task(const StatJob &J, const StatsParams &S, float T, int64_t e0,
+                              int64_t e1, float X)
+{
+    constexpr int kPer = (int)(kTask / 256);
+    HashStats &st = S.stats[J.slot];
+    const int logB = J.logB;
+    const uint32_t mask = (1u << logB) - 1;
+    const float *__restrict__ E = J.energy;
+    const uint32_t s1 = J.hash->sigma[0] & mask, p1 = J.hash->sinv[0] & mask;
+    const uint32_t s2 = J.hash->sigma[1] & mask, p2 = J.hash->sinv[1] & mask;
+    float ev[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; u++) {
+        const int64_t j = e0 + threadIdx.x + 256 * u;
+        ev[u] = j < e1 ? __ldg(&E[j]) : 0.f;
+    }
+    uint32_t above = 0, found = 0;
+#pragma unroll
+    for (int u = 0; u < kPer; u++) {
+        const int64_t j = e0 + threadIdx.x + 256 * u;
+        const float e = ev[u];
+        above += j < e1 && e > X;
+        if (j < e1 && e > T) {
+            bool ok;
+            if (S.ndim == 1) {
+                const uint32_t jj = (uint32_t)j;
+                ok = dominates(e, __ldg(&E[(jj - p1) & mask]), S.up, 0, -1) &&
+                     dominates(e, __ldg(&E[(jj + p1) & mask]), S.up, 0, 1);
+            } else {
+                const uint32_t jA = (uint32_t)(j >> logB), jB = (uint32_t)(j & mask);
+                ok = true;
+                for (int d1 = -1; d1 <= 1 && ok; d1++)
+                    for (int d2 = -1; d2 <= 1 && ok; d2++) {
+                        if (d1 == 0 && d2 == 0) continue;
+                        const uint32_t m1 = (jA + (uint32_t)d1 * p1) & mask;
+                        const uint32_t m2 = (jB + (uint32_t)d2 * p2) & mask;
+                        ok = dominates(e, __ldg(&E[((int64_t)m1 << logB) | m2]), S.up, d1, d2);
+                    }
+            }
+            if (ok) found |= 1u << u;
+        }
+    }
+    __shared__ uint32_t base_sh;
+    uint32_t total;
+    const uint32_t before = block_exclusive_scan((uint32_t)__popc(found), &total);
+    const uint32_t nabove = block_sum(above);
+    if (threadIdx.x == 0) {
+        base_sh = total ? atomicAdd(&st.nmax, total) : 0u;
+        if (nabove) atomicAdd(&st.above, nabove);
+    }
+    __syncthreads();
+    if (found && J.list >= 0) {
+        uint32_t pos = base_sh + before;
+        int32_t *lst = S.lists + (int64_t)J.list * S.cap;
+#pragma unroll
+        for (int u = 0; u < kPer; u++) {
+            if (!(found & (1u << u))) continue;
+            const int64_t j = e0 + threadIdx.x + 256 * u;
+            int32_t c;
+            if (S.ndim == 1) {
+                c = (int32_t)((s1 * (uint32_t)j) & mask);
+            } else {
+                const uint32_t jA = (uint32_t)(j >> logB), jB = (uint32_t)(j & mask);
+                c = (int32_t)((((s1 * jA) & mask) << logB) | ((s2 * jB) & mask));
+            }
+            if (pos < S.cap) lst[pos] = c;
+            pos++;
+        }
+    }
+    __syncthreads();
+}
+
 // Threshold and local maxima of njobs hashes whose energies and maxima the bucket FFTs
 // wrote.  Returns false if a barrier failed.
 __device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &S,
@@ -385,9 +461,7 @@ __device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &
         const int64_t e1 = min(e0 + kTask, nb);
         const float M = __uint_as_float(st.max_bits);
         const float X = S.use_median ? M * S.ratio : INFINITY;
-        uint32_t above = localmax_range(J, S, S.thr_rel * M, e0 + threadIdx.x, e1, blockDim.x, X);
-        above = block_sum(above);
-        if (threadIdx.x == 0 && above) atomicAdd(&st.above, above);
+        localmax_task(J, S, S.thr_rel * M, e0, e1, X);
     }
     if (!grid_sync(gb, status)) return false;
     // C: exact median where it can matter, then recount those hashes' maxima.
@@ -588,11 +662,15 @@ struct LocTailArgs {
     int L_loc, L_est;
     int est_group;          // lanes per coordinate in the estimates: power of two >= L_est
     float eta_up, eta_dn;
-    int32_t *sel;
-    uint32_t *votes;
-    int64_t nvote_words;
+    int32_t *sel;           // [L_loc][S.cap] selected buckets per location hash
     uint32_t need;          // votes needed: ceil(L_loc / 2)
-    uint32_t *blk;          // per-block kept counts / offsets (gridDim entries)
+    uint32_t *bucketbits;   // [L_loc][bucket_words] selected-bucket bitmaps
+    int64_t bucket_words;
+    uint32_t *kept;         // kept coordinates, unordered (kept_cap entries)
+    int64_t kept_cap;
+    uint32_t *coordbits;    // one bit per coordinate (all zero between transforms)
+    int64_t coord_words;
+    uint32_t *blk;          // per-block counts / offsets of the bitmap compaction
     const HashParam *le;    // location then estimation hashes
     const float2 *z;        // spectra at B*: location then estimation hashes
     const float *rgain;     // 1 / Ghat' per B (offsets ro)
@@ -713,12 +791,6 @@ __device__ void topnum_block(const StatJob &J, const LocTailArgs &A, int64_t num
     __syncthreads();
 }
 
-__device__ __forceinline__ uint32_t count_kept(uint32_t w, uint32_t need)
-{
-    return ((w & 0xffu) >= need) + (((w >> 8) & 0xffu) >= need) + (((w >> 16) & 0xffu) >= need) +
-           ((w >> 24) >= need);
-}
-
 __device__ __forceinline__ void axis_terms(uint64_t i, const HashParam &hp, int axis, int logn,
                                            int logB, uint64_t &jP, uint64_t &kph, int64_t &oidx,
                                            uint64_t &mtau)
@@ -778,6 +850,29 @@ __device__ float2 estimate_term(uint64_t coord, const LocTailArgs &A, int b, int
     return make_float2((pv.x * w.x - pv.y * w.y) * rg, (pv.x * w.y + pv.y * w.x) * rg);
 }
 
+// Componentwise median of L values (element floor(L/2) of each sorted component; equal
+// values ordered by hash index), by ranks.
+__device__ __forceinline__ float2 median_of(const float (&vr)[kMaxLoops], const float (&vi)[kMaxLoops],
+                                            int L)
+{
+    const int want = L / 2;
+    float mr = 0.f, mi = 0.f;
+#pragma unroll
+    for (int a = 0; a < kMaxLoops; a++) {
+        if (a >= L) break;
+        int rr = 0, ri = 0;
+#pragma unroll
+        for (int c = 0; c < kMaxLoops; c++) {
+            if (c >= L) break;
+            rr += vr[c] < vr[a] || (vr[c] == vr[a] && c < a);
+            ri += vi[c] < vi[a] || (vi[c] == vi[a] && c < a);
+        }
+        if (rr == want) mr = vr[a];
+        if (ri == want) mi = vi[a];
+    }
+    return make_float2(mr, mi);
+}
+
 // Estimates of the kept coordinates: a group of `grp` lanes (grp >= L_est, a power of two)
 // per coordinate, lane l computing hash l; the group's first lane gathers the values by
 // shuffles and takes the componentwise median (element floor(L/2) after sorting).
@@ -801,28 +896,41 @@ __device__ void estimate_all(const LocTailArgs &A, int64_t cnt, int b)
                 vi[l] = __shfl_sync(0xffffffffu, v.y, l, grp);
             }
         }
-        if (valid && gl == 0) {
-            // rank selection of element floor(L/2) per component (ties by hash index)
-            const int L = A.L_est, want = L / 2;
-            float mr = 0.f, mi = 0.f;
-#pragma unroll
-            for (int a = 0; a < kMaxLoops; a++) {
-                if (a >= L) break;
-                int rr = 0, ri = 0;
-#pragma unroll
-                for (int c = 0; c < kMaxLoops; c++) {
-                    if (c >= L) break;
-                    rr += vr[c] < vr[a] || (vr[c] == vr[a] && c < a);
-                    ri += vi[c] < vi[a] || (vi[c] == vi[a] && c < a);
-                }
-                if (rr == want) mr = vr[a];
-                if (ri == want) mi = vi[a];
-            }
-            A.val[s] = make_float2(mr, mi);
-        }
+        if (valid && gl == 0) A.val[s] = median_of(vr, vi, A.L_est);
     }
 }
 
+// Bucket of coordinate i under hash hp on one axis (Eq. (10) with the half-bin reading):
+// round((sigma i mod n + 1/2) / D) mod B.
+__device__ __forceinline__ uint32_t bucket_of(uint32_t i, uint32_t sigma, int logn, int logB)
+{
+    const uint32_t nmask = (1u << logn) - 1, D = 1u << (logn - logB);
+    const uint32_t p = (sigma * i) & nmask;
+    return (uint32_t)(((2ull * p + 1 + D) / (2ull * D)) & ((1u << logB) - 1));
+}
+
+constexpr int kRankStage = 2048;   // top-num by ranking: candidates staged per block
+
+// Index of hash l's bucket c in its bitmap (c is the linear bucket index, 2D: c1 B + c2).
+__device__ __forceinline__ bool bucket_selected(const LocTailArgs &A, int l, uint32_t c)
+{
+    return (A.bucketbits[(int64_t)l * A.bucket_words + (c >> 5)] >> (c & 31)) & 1u;
+}
+
+// The location tail.  Phases, each ended by a grid barrier:
+//   P1  thresholds and local maxima of the L_loc location hashes (stats_phases);
+//   P2a top-num pivot: every candidate's rank by energy among its hash's maxima, the one
+//       of rank num - 1 publishes V (hashes with more than kRankStage maxima: one block
+//       does the whole cutoff with radix selection instead);
+//   P2b cutoff (keep E > V(1 + eta), fill from the band [V(1 - eta), V(1 + eta)] in
+//       ascending bucket order) and the selected-bucket bitmaps;
+//   P3  votes: a kept coordinate lies in >= need selected preimages, hence in one of the
+//       first L_loc - need + 1 hashes' preimages; each such preimage counts the hashes
+//       whose bucket of it is selected (emitted once, by the first hash that has it);
+//   P4  ascending order by rank among the kept coordinates, Eq. (11) estimates and the
+//       componentwise median, written in place.  More kept coordinates than the kept
+//       list holds: ordered compaction of the coordinate bitmap instead (three more
+//       phases) and the estimates after it.
 __global__ void __launch_bounds__(256) k_loc_tail(const LocTailArgs A)
 {
     ExecState *state = A.state;
@@ -832,98 +940,282 @@ __global__ void __launch_bounds__(256) k_loc_tail(const LocTailArgs A)
     const bool empty = state->empty != 0;
     const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (!empty) {
-        if (!stats_phases(A.jobs, A.L_loc, A.S, gb, status)) return;
-        // top-num cutoff: one block per location hash
-        const int64_t num = state->k_star;
-        for (int l = blockIdx.x; l < A.L_loc; l += gridDim.x) topnum_block(A.jobs[l], A, num);
-        if (!grid_sync(gb, status)) return;
-        // votes: every coordinate whose permuted position rounds to a selected bucket
-        const int b = state->b_star;
-        const int logn = A.logn, logD = logn - b, ndim = A.S.ndim;
-        const int64_t D = (int64_t)1 << logD;
-        const int64_t Dd = ndim == 1 ? D : D * D;
-        __shared__ int64_t off[kMaxLoops + 1];
-        if (threadIdx.x == 0) {
-            int64_t acc = 0;
-            for (int l = 0; l < A.L_loc; l++) {
-                off[l] = acc;
-                acc += (int64_t)A.S.stats[kMaxLogB + l].nsel * Dd;
+    const int lane = threadIdx.x & 31;
+    extern __shared__ uint32_t dsm[];
+    if (empty) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            *A.d_count = 0;
+            *A.d_k = state->k_star;
+            *A.d_status = state->status;
+        }
+        return;
+    }
+    const int b = state->b_star;
+    const int64_t num = state->k_star;
+    const int logn = A.logn, logD = logn - b, ndim = A.S.ndim;
+    const int64_t nb = nb_of(ndim, b);
+    // clear the selected-bucket bitmaps (P1's barrier orders this before P2b)
+    {
+        const int64_t words = (nb + 31) >> 5;
+        for (int64_t w = gtid; w < (int64_t)A.L_loc * words; w += gthreads)
+            A.bucketbits[(w / words) * A.bucket_words + (w % words)] = 0u;
+    }
+    // ---- P1 ----
+    if (!stats_phases(A.jobs, A.L_loc, A.S, gb, status)) return;
+
+    // ---- P2a: pivot ranks ----
+    // blocks [l G, (l + 1) G) serve hash l; their candidates (and energies) stay staged
+    // in shared memory through P2b
+    const int G = gridDim.x / A.L_loc;
+    const int l_mine = G > 0 ? (int)blockIdx.x / G : A.L_loc;
+    const int sb = G > 0 ? (int)blockIdx.x % G : 0;
+    float *es = reinterpret_cast<float *>(dsm);                   // kRankStage energies
+    uint32_t *cs = dsm + kRankStage;                                // kRankStage buckets
+    uint32_t *band = dsm + 2 * kRankStage;                          // kRankStage band buckets
+    int64_t cnt = 0;
+    bool ranked = false;
+    if (l_mine < A.L_loc) {
+        const StatJob &J = A.jobs[l_mine];
+        HashStats &st = A.S.stats[J.slot];
+        cnt = min((int64_t)st.nmax, A.S.cap);
+        const uint32_t mask = (uint32_t)(nb_of(1, b) - 1);
+        const uint32_t p1 = (uint32_t)J.hash->sinv[0] & mask, p2 = (uint32_t)J.hash->sinv[1] & mask;
+        const int32_t *list = A.S.lists + (int64_t)J.list * A.S.cap;
+        if (cnt > num && cnt <= kRankStage) {
+            ranked = true;
+            for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+                const uint32_t c = (uint32_t)list[i];
+                const int64_t pj = ndim == 1 ? (int64_t)((p1 * c) & mask)
+                                             : ((int64_t)((p1 * (c >> b)) & mask) << b) |
+                                                   ((p2 * (c & mask)) & mask);
+                cs[i] = c;
+                es[i] = J.energy[pj];
             }
-            off[A.L_loc] = acc;
+            __syncthreads();
+            for (int64_t i = (int64_t)sb * blockDim.x + threadIdx.x; i < cnt;
+                 i += (int64_t)G * blockDim.x) {
+                const float e = es[i];
+                uint32_t r = 0;
+                for (int64_t j = 0; j < cnt; j++) {
+                    const float f = es[j];
+                    r += f > e || (f == e && j < i);
+                }
+                if (r == (uint32_t)(num - 1)) st.v_bits = __float_as_uint(e);
+            }
+        } else if (cnt > num && sb == 0) {
+            topnum_block(J, A, num);   // writes sel and nsel itself
         }
-        __syncthreads();
-        __shared__ uint32_t sh_sinv[kMaxLoops][2];
-        if (threadIdx.x < A.L_loc) {
-            sh_sinv[threadIdx.x][0] = (uint32_t)A.le[threadIdx.x].sinv[0];
-            sh_sinv[threadIdx.x][1] = (uint32_t)A.le[threadIdx.x].sinv[1];
-        }
-        __syncthreads();
-        const uint32_t n = 1u << logn, nmask = n - 1, Bm = (1u << b) - 1;
-        const int64_t total = off[A.L_loc];
-        // four items per thread per round: their buckets are loaded before any vote
-        constexpr int kU = 4;
-        for (int64_t it0 = gtid; it0 < total; it0 += kU * gthreads) {
-            uint32_t cb[kU], qq[kU];
-            int ll[kU];
-#pragma unroll
-            for (int u = 0; u < kU; u++) {
-                const int64_t it = it0 + u * gthreads;
-                ll[u] = -1;
-                if (it < total) {
-                    int l = 0;
-                    while (it >= off[l + 1]) l++;
-                    const int64_t rem = it - off[l];
-                    const int64_t sidx = rem >> (ndim == 1 ? logD : 2 * logD);
-                    qq[u] = (uint32_t)(rem & (Dd - 1));
-                    cb[u] = (uint32_t)A.sel[(int64_t)l * A.S.cap + sidx];
-                    ll[u] = l;
+    }
+    if (!grid_sync(gb, status)) return;
+
+    // ---- P2b: cutoff and bitmaps ----
+    if (l_mine < A.L_loc) {
+        const StatJob &J = A.jobs[l_mine];
+        HashStats &st = A.S.stats[J.slot];
+        uint32_t *bits = A.bucketbits + (int64_t)l_mine * A.bucket_words;
+        int32_t *out = A.sel + (int64_t)J.list * A.S.cap;
+        const int32_t *list = A.S.lists + (int64_t)J.list * A.S.cap;
+        if (ranked) {
+            const float V = __uint_as_float(st.v_bits);
+            const float hi = V * A.eta_up, lo = V * A.eta_dn;
+            __shared__ uint32_t nband;
+            if (threadIdx.x == 0) nband = 0;
+            __syncthreads();
+            uint32_t mine = 0;
+            for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+                const float e = es[i];
+                mine += e > hi;
+                if (e >= lo && e <= hi) band[atomicAdd(&nband, 1u)] = cs[i];
+            }
+            const uint32_t nhi = block_sum(mine);   // (synchronises: nband complete)
+            const uint32_t need_band = (uint32_t)num - nhi;
+            // the need_band-th smallest band bucket: the band member with that many below
+            __shared__ uint32_t cthr;
+            for (uint32_t i = threadIdx.x; i < nband; i += blockDim.x) {
+                const uint32_t c = band[i];
+                uint32_t r = 0;
+                for (uint32_t j = 0; j < nband; j++) r += band[j] < c;
+                if (r == need_band - 1) cthr = c;
+            }
+            __syncthreads();
+            const uint32_t ct = cthr;
+            for (int64_t i0 = (int64_t)sb * blockDim.x; i0 < cnt; i0 += (int64_t)G * blockDim.x) {
+                const int64_t i = i0 + threadIdx.x;
+                bool keep = false;
+                uint32_t c = 0;
+                if (i < cnt) {
+                    const float e = es[i];
+                    c = cs[i];
+                    keep = e > hi || (e >= lo && e <= hi && c <= ct);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                uint32_t base = 0;
+                if (lane == 0 && bal) base = atomicAdd(&st.nsel, (uint32_t)__popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (keep) {
+                    out[base + __popc(bal & ((1u << lane) - 1))] = (int32_t)c;
+                    atomicOr(&bits[c >> 5], 1u << (c & 31));
                 }
             }
-#pragma unroll
-            for (int u = 0; u < kU; u++) {
-                if (ll[u] < 0) continue;
-                const uint32_t c = cb[u], q = qq[u];
-                const uint32_t *si = sh_sinv[ll[u]];
-                uint32_t coord;
+        } else if (cnt <= num) {
+            // every maximum is kept: the list is the selection
+            for (int64_t i = (int64_t)sb * blockDim.x + threadIdx.x; i < cnt;
+                 i += (int64_t)G * blockDim.x) {
+                const uint32_t c = (uint32_t)list[i];
+                out[i] = (int32_t)c;
+                atomicOr(&bits[c >> 5], 1u << (c & 31));
+            }
+            if (sb == 0 && threadIdx.x == 0) st.nsel = (uint32_t)cnt;
+        } else {
+            // selected by one block in P2a
+            const int64_t ns = st.nsel;
+            for (int64_t i = (int64_t)sb * blockDim.x + threadIdx.x; i < ns;
+                 i += (int64_t)G * blockDim.x) {
+                const uint32_t c = (uint32_t)out[i];
+                atomicOr(&bits[c >> 5], 1u << (c & 31));
+            }
+        }
+    }
+    if (!grid_sync(gb, status)) return;
+
+    // ---- P3: votes on the preimages of the first L_cand hashes ----
+    const int L_cand = A.L_loc - (int)A.need + 1;
+    const uint32_t n = 1u << logn, nmask = n - 1, Bm = (1u << b) - 1;
+    const int64_t D = (int64_t)1 << logD;
+    const int64_t Dd = ndim == 1 ? D : D * D;
+    __shared__ int64_t off[kMaxLoops + 1];
+    __shared__ uint32_t sh_sig[kMaxLoops][2], sh_sinv[kMaxLoops][2];
+    if (threadIdx.x < A.L_loc) {
+        sh_sig[threadIdx.x][0] = (uint32_t)A.le[threadIdx.x].sigma[0];
+        sh_sig[threadIdx.x][1] = (uint32_t)A.le[threadIdx.x].sigma[1];
+        sh_sinv[threadIdx.x][0] = (uint32_t)A.le[threadIdx.x].sinv[0];
+        sh_sinv[threadIdx.x][1] = (uint32_t)A.le[threadIdx.x].sinv[1];
+    }
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int l = 0; l < L_cand; l++) {
+            off[l] = acc;
+            acc += (int64_t)A.S.stats[kMaxLogB + l].nsel * Dd;
+        }
+        off[L_cand] = acc;
+    }
+    __syncthreads();
+    {
+        const int64_t total = off[L_cand];
+        for (int64_t it0 = (int64_t)blockIdx.x * blockDim.x; it0 < total; it0 += gthreads) {
+            const int64_t it = it0 + threadIdx.x;
+            bool keep = false;
+            uint32_t coord = 0;
+            if (it < total) {
+                int l0 = 0;
+                while (it >= off[l0 + 1]) l0++;
+                const int64_t rem = it - off[l0];
+                const int64_t sidx = rem >> (ndim == 1 ? logD : 2 * logD);
+                const uint32_t q = (uint32_t)(rem & (Dd - 1));
+                const uint32_t c = (uint32_t)A.sel[(int64_t)l0 * A.S.cap + sidx];
                 if (ndim == 1) {
                     // bucket c collects permuted positions p in [c D - D/2, c D + D/2 - 1]
                     const uint32_t pp = ((c << logD) - (uint32_t)(D >> 1) + q) & nmask;
-                    coord = (si[0] * pp) & nmask;
+                    coord = (sh_sinv[l0][0] * pp) & nmask;
                 } else {
                     const uint32_t c1 = c >> b, c2 = c & Bm;
                     const uint32_t q1 = q >> logD, q2 = q & (uint32_t)(D - 1);
                     const uint32_t pp1 = ((c1 << logD) - (uint32_t)(D >> 1) + q1) & nmask;
                     const uint32_t pp2 = ((c2 << logD) - (uint32_t)(D >> 1) + q2) & nmask;
-                    coord = (((si[0] * pp1) & nmask) << logn) | ((si[1] * pp2) & nmask);
+                    coord = (((sh_sinv[l0][0] * pp1) & nmask) << logn) | ((sh_sinv[l0][1] * pp2) & nmask);
                 }
-                atomicAdd(&A.votes[coord >> 2], 1u << (8 * (coord & 3)));
+                const uint32_t ci = ndim == 1 ? coord : coord >> logn;
+                const uint32_t cj = ndim == 1 ? 0u : coord & nmask;
+                uint32_t votes = 1;   // hash l0 itself
+                bool first = true;
+                for (int l = 0; l < A.L_loc; l++) {
+                    if (l == l0) continue;
+                    uint32_t c_l = bucket_of(ci, sh_sig[l][0], logn, b);
+                    if (ndim == 2) c_l = (c_l << b) | bucket_of(cj, sh_sig[l][1], logn, b);
+                    const bool sel = bucket_selected(A, l, c_l);
+                    votes += sel;
+                    if (sel && l < l0) first = false;
+                }
+                keep = first && votes >= A.need;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            uint32_t base = 0;
+            if (lane == 0 && bal) base = (uint32_t)atomicAdd((unsigned long long *)&state->count,
+                                                             (unsigned long long)__popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (keep) {
+                const uint32_t pos = base + __popc(bal & ((1u << lane) - 1));
+                if (pos < A.kept_cap) A.kept[pos] = coord;
+                atomicOr(&A.coordbits[coord >> 5], 1u << (coord & 31));
             }
         }
-        if (!grid_sync(gb, status)) return;
-    } else {
-        // nothing voted; the (zero) counters still go through the compaction
     }
-    // ordered compaction: block b owns a contiguous range of vote words, walked in
-    // chunks of 4 words per thread
-    const int64_t per = ((A.nvote_words + gridDim.x - 1) / gridDim.x + 3) & ~(int64_t)3;
-    const int64_t w0 = blockIdx.x * per;
-    const int64_t w1 = min(w0 + per, A.nvote_words);
-    uint32_t c = 0;
-    for (int64_t w = w0 + 4 * threadIdx.x; w < w1; w += 4 * blockDim.x) {
-        if (w + 3 < w1) {
-            const uint4 q = *reinterpret_cast<const uint4 *>(A.votes + w);
-            c += count_kept(q.x, A.need) + count_kept(q.y, A.need) + count_kept(q.z, A.need) +
-                 count_kept(q.w, A.need);
-        } else {
-            for (int64_t u = w; u < w1; u++) c += count_kept(A.votes[u], A.need);
+    if (!grid_sync(gb, status)) return;
+
+    // ---- P4: order, estimates, outputs ----
+    const int64_t K = state->count;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int st = state->status;
+        if (K > A.capacity && st == ATSFFT_OK) st = ATSFFT_E_CAPACITY;
+        *A.d_count = K;
+        *A.d_k = num;
+        *A.d_status = st;
+    }
+    if (K <= A.kept_cap) {
+        // rank = number of kept coordinates below; a lane group per coordinate splits the
+        // comparisons, then computes the L_est estimates of its coordinate
+        const int grp = A.est_group;
+        const int gl = lane & (grp - 1);
+        const int per_block = (int)blockDim.x / grp;
+        uint32_t *ks = dsm;   // staged kept list chunk
+        constexpr int kChunk = 3 * kRankStage;
+        for (int64_t base = (int64_t)blockIdx.x * per_block; base < K;
+             base += (int64_t)gridDim.x * per_block) {
+            const int64_t k = base + threadIdx.x / grp;
+            const bool valid = k < K;
+            const uint32_t coord = valid ? A.kept[k] : 0u;
+            uint32_t r = 0;
+            for (int64_t c0 = 0; c0 < K; c0 += kChunk) {
+                const int64_t c1 = min(c0 + (int64_t)kChunk, K);
+                __syncthreads();
+                for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) ks[i - c0] = A.kept[i];
+                __syncthreads();
+                if (valid)
+                    for (int64_t i = c0 + gl; i < c1; i += grp) r += ks[i - c0] < coord;
+            }
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1)
+                if (o < grp) r += __shfl_xor_sync(0xffffffffu, r, o, grp);
+            float2 v = make_float2(0.f, 0.f);
+            if (valid && r < A.capacity && gl < A.L_est) v = estimate_term(coord, A, b, gl);
+            float vr[kMaxLoops], vi[kMaxLoops];
+#pragma unroll
+            for (int l = 0; l < kMaxLoops; l++) {
+                if (l < A.L_est) {
+                    vr[l] = __shfl_sync(0xffffffffu, v.x, l, grp);
+                    vi[l] = __shfl_sync(0xffffffffu, v.y, l, grp);
+                }
+            }
+            if (valid && gl == 0) {
+                A.coordbits[coord >> 5] = 0u;   // only kept coordinates set bits
+                if (r < A.capacity) {
+                    A.loc[r] = coord;
+                    A.val[r] = median_of(vr, vi, A.L_est);
+                }
+            }
         }
+        return;
     }
+    // fallback: ordered compaction of the coordinate bitmap, clearing it
+    const int64_t per = (A.coord_words + gridDim.x - 1) / gridDim.x;
+    const int64_t w0 = blockIdx.x * per;
+    const int64_t w1 = min(w0 + per, A.coord_words);
+    uint32_t c = 0;
+    for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) c += __popc(A.coordbits[w]);
     c = block_sum(c);
     if (threadIdx.x == 0) A.blk[blockIdx.x] = c;
     if (!grid_sync(gb, status)) return;
     if (blockIdx.x == 0) {
-        // exclusive scan of the per-block counts (gridDim.x <= 8 * 256 here)
         __shared__ uint32_t carry, tot;
         if (threadIdx.x == 0) carry = 0;
         __syncthreads();
@@ -936,48 +1228,28 @@ __global__ void __launch_bounds__(256) k_loc_tail(const LocTailArgs A)
             if (threadIdx.x == 0) carry += tot;
             __syncthreads();
         }
-        if (threadIdx.x == 0) state->count = carry;
     }
     if (!grid_sync(gb, status)) return;
     {
-        // in-order write of this block's range: 4 words per thread per chunk
         int64_t base = A.blk[blockIdx.x];
         __shared__ uint32_t tot;
-        for (int64_t wb = w0; wb < w1; wb += 4 * blockDim.x) {
-            const int64_t w = wb + 4 * threadIdx.x;
-            uint32_t words[4];
-            for (int q = 0; q < 4; q++) words[q] = (w + q < w1) ? A.votes[w + q] : 0u;
-            uint32_t k = 0;
-            for (int q = 0; q < 4; q++) k += count_kept(words[q], A.need);
-            int64_t pos = base + block_exclusive_scan(k, &tot);
-            for (int q = 0; q < 4; q++) {
-                for (int by = 0; by < 4; by++)
-                    if (((words[q] >> (8 * by)) & 0xffu) >= A.need) {
-                        if (pos < A.capacity) A.loc[pos] = (w + q) * 4 + by;
-                        pos++;
-                    }
-                if (w + q < w1 && words[q]) A.votes[w + q] = 0u;
+        for (int64_t wb = w0; wb < w1; wb += blockDim.x) {
+            const int64_t w = wb + threadIdx.x;
+            uint32_t word = w < w1 ? A.coordbits[w] : 0u;
+            int64_t pos = base + block_exclusive_scan((uint32_t)__popc(word), &tot);
+            if (word) A.coordbits[w] = 0u;
+            while (word) {
+                const int bit = __ffs(word) - 1;
+                word &= word - 1;
+                if (pos < A.capacity) A.loc[pos] = w * 32 + bit;
+                pos++;
             }
             base += tot;
             __syncthreads();
         }
     }
     if (!grid_sync(gb, status)) return;
-    // estimates of the kept coordinates
-    const int64_t count = state->count;
-    if (!empty) {
-        const int64_t cnt = min(count, A.capacity);
-        estimate_all(A, cnt, state->b_star);
-    }
-    if (!grid_sync(gb, status)) return;   // (stamps the end of the estimates)
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        int st = state->status;
-        const int64_t cnt = empty ? 0 : count;
-        if (cnt > A.capacity && st == ATSFFT_OK) st = ATSFFT_E_CAPACITY;
-        *A.d_count = cnt;
-        *A.d_k = state->k_star;
-        *A.d_status = st;
-    }
+    estimate_all(A, min(K, A.capacity), b);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1057,9 +1329,13 @@ void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, int6
     A.eta_up = (float)(1.0 + P->p.tie_eta);
     A.eta_dn = (float)(1.0 - P->p.tie_eta);
     A.sel = P->d_sel;
-    A.votes = P->d_votes;
-    A.nvote_words = P->nvote_words;
     A.need = (uint32_t)((P->L_loc + 1) / 2);
+    A.bucketbits = P->d_bucketbits;
+    A.bucket_words = P->bucket_words;
+    A.kept = P->d_kept;
+    A.kept_cap = P->kept_cap;
+    A.coordbits = P->d_coordbits;
+    A.coord_words = P->coord_words;
     A.blk = P->d_blk;
     A.le = P->d_le;
     A.z = P->d_z;
