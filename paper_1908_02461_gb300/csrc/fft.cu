@@ -237,6 +237,10 @@ __device__ __forceinline__ int tile_of(const FftShape &f)
     return T;
 }
 
+// Input loads per tile (values x partial chunks) above which a strided tile is split
+// further, so that hashes with many partial chunks spread over more CTAs.
+constexpr int64_t kTileLoads = 8192;
+
 // Is `pass` the one that writes the final spectrum?
 __device__ __forceinline__ bool final_pass(int ndim, int logB, int pass)
 {
@@ -263,7 +267,9 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_fft_pass(int ndim, int pass,
     const float2 *in = pass == 0 ? part : (ndim == 1 ? tmp : fin);
     float2 *out = (pass == 0 && four_step) ? tmp : fin;
     const int64_t in_hash = (int64_t)chunks * f.hash_stride;
-    const int T = tile_of(f);
+    int T = tile_of(f);
+    if (f.in_es != 1 || f.out_es != 1)
+        while (T > 4 && ((int64_t)T << f.logP) * chunks > kTileLoads) T >>= 1;
     const int64_t tiles = f.ntrans / T;
     const int64_t total = (int64_t)nh * tiles;
     const bool fin_pass = energy && final_pass(ndim, logB, pass);
@@ -280,9 +286,11 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_fft_pass(int ndim, int pass,
 // Static batch: every job is one hash of its own B (the tuning trials).
 struct FftJob {
     int32_t logB, chunks;
+    int32_t T, pad;      // transforms per tile in this pass
     int64_t in_off, tmp_off, out_off;
-    int64_t tr_start;    // first transform of this job in the launch (per pass)
+    int64_t tr_start;    // first tile of this job in the launch
 };
+
 
 struct FftBatch {
     int njobs;
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_fft_batch(int ndim, int pass
         while (jb + 1 < Bt.njobs && tr >= Bt.j[jb + 1].tr_start) jb++;
         const FftJob &J = Bt.j[jb];
         const FftShape f = fft_shape(ndim, J.logB, pass);
-        const int T = tile_of(f);
+        const int T = J.T;
         const int64_t t = (tr - J.tr_start) * T;
         const bool four_step = ndim == 1 && J.logB > 12;
         const float2 *in =
@@ -364,17 +372,22 @@ void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB,
                 logP = lb;
                 strided = pass == 1;
             }
-            // tiles of adjacent transforms, as tile_of() on the device
+            // tiles of adjacent transforms (whole 32-byte sectors: T >= 4 when strided),
+            // smaller where the partial chunks make a tile's input large
             int64_t T = 1;
             if (strided) {
                 T = (int64_t)kSmallFFT >> logP;
                 if (T > 16) T = 16;
                 if (T > ntrans) T = ntrans;
+                const int64_t ch = pass == 0 ? chunks[i] : 1;
+                while (T > 4 && (T << logP) * ch > kTileLoads) T >>= 1;
             }
             ntrans /= T;
             FftJob &J = Bt.j[Bt.njobs++];
             J.logB = lb;
             J.chunks = chunks[i];
+            J.T = (int32_t)T;
+            J.pad = 0;
             J.in_off = in_off[i];
             J.tmp_off = out_off[i];
             J.out_off = out_off[i];

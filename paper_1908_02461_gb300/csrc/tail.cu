@@ -151,83 +151,6 @@ __device__ float threshold_of(const HashStats &st, const StatsParams &S)
     return T;
 }
 
-// Appends bucket c to the job's list of maxima when `is_max`: one atomic per warp for
-// all its lanes that found one (the list order is immaterial).
-__device__ __forceinline__ void append_max(HashStats &st, const StatJob &J, const StatsParams &S,
-                                           bool is_max, int32_t c)
-{
-    const unsigned am = __activemask();
-    const unsigned bal = __ballot_sync(am, is_max);
-    if (!bal) return;
-    const int lane = threadIdx.x & 31, leader = __ffs(bal) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(&st.nmax, (uint32_t)__popc(bal));
-    base = __shfl_sync(am, base, leader);
-    if (is_max && J.list >= 0) {
-        const uint32_t pos = base + __popc(bal & ((1u << lane) - 1));
-        if (pos < S.cap) S.lists[(int64_t)J.list * S.cap + pos] = c;
-    }
-}
-
-// Local maxima of one job over P-indices j = j0, j0 + step, ... < j1 (bucket
-// c = sigma j, neighbours at j +- sigma'); returns how many energies exceed X.  Four
-// energies are loaded before any is tested.
-__device__ uint32_t localmax_range(const StatJob &J, const StatsParams &S, float T, int64_t j0,
-                                   int64_t j1, int64_t step, float X)
-{
-    HashStats &st = S.stats[J.slot];
-    const int logB = J.logB;
-    const uint32_t B = 1u << logB, mask = B - 1;
-    const float *__restrict__ E = J.energy;
-    const uint32_t s1 = J.hash->sigma[0] & mask, p1 = J.hash->sinv[0] & mask;
-    const uint32_t s2 = J.hash->sigma[1] & mask, p2 = J.hash->sinv[1] & mask;
-    uint32_t above = 0;
-    for (int64_t jb = j0; jb < j1; jb += 4 * step) {
-        float ev[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int64_t j = jb + u * step;
-            ev[u] = j < j1 ? __ldg(&E[j]) : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int64_t j = jb + u * step;
-            const float e = ev[u];
-            const bool valid = j < j1;
-            above += valid && e > X;
-            bool ok = valid && e > T;
-            int32_t c = 0;
-            if (ok) {
-                if (S.ndim == 1) {
-                    const uint32_t jj = (uint32_t)j;
-                    c = (int32_t)((s1 * jj) & mask);
-                    ok = dominates(e, __ldg(&E[(jj - p1) & mask]), S.up, 0, -1) &&
-                         dominates(e, __ldg(&E[(jj + p1) & mask]), S.up, 0, 1);
-                } else {
-                    const uint32_t jA = (uint32_t)(j >> logB), jB = (uint32_t)(j & mask);
-                    c = (int32_t)((((s1 * jA) & mask) << logB) | ((s2 * jB) & mask));
-                    for (int d1 = -1; d1 <= 1 && ok; d1++)
-                        for (int d2 = -1; d2 <= 1 && ok; d2++) {
-                            if (d1 == 0 && d2 == 0) continue;
-                            const uint32_t m1 = (jA + (uint32_t)d1 * p1) & mask;
-                            const uint32_t m2 = (jB + (uint32_t)d2 * p2) & mask;
-                            ok = dominates(e, __ldg(&E[((int64_t)m1 << logB) | m2]), S.up, d1, d2);
-                        }
-                }
-            }
-            append_max(st, J, S, ok, c);
-        }
-    }
-    return above;
-}
-
-__device__ void localmax_job(const StatJob &J, const StatsParams &S, float T, int64_t gtid,
-                             int64_t gthreads, uint32_t *above_out, float X)
-{
-    (void)above_out;
-    localmax_range(J, S, T, gtid, nb_of(S.ndim, J.logB), gthreads, X);
-}
-
 // hist[bin] += 1 for every calling lane, one shared atomic per distinct bin in the warp
 // (radix digits of nearly equal energies share a few bins).
 __device__ __forceinline__ void hist_add(uint32_t *hist, uint32_t bin)
@@ -315,7 +238,7 @@ constexpr int kSmallMedian = 8192;
 // three radix digits (11, 11, 10 bits) over their bit patterns.
 __device__ uint32_t block_median(const float *E, int nb)
 {
-    extern __shared__ uint32_t dsm[];   // phase scratch shared by the tail's phases
+    extern __shared__ __align__(16) uint32_t dsm[];   // phase scratch shared by the tail's phases
     uint32_t *vals = dsm;               // kSmallMedian entries
     uint32_t *hist = dsm + kSmallMedian; // 2048 entries
     __shared__ uint32_t sh_prefix, sh_rank;
@@ -347,27 +270,28 @@ __device__ uint32_t block_median(const float *E, int nb)
     return sh_prefix;
 }
 
-// Local maxima of one job by one block (the recount after an exact median).
-__device__ void localmax_block(const StatJob &J, const StatsParams &S, float T)
-{
-    localmax_job(J, S, T, threadIdx.x, blockDim.x, nullptr, INFINITY);
-    __syncthreads();
-}
+// One statistics job as the phases use it, staged in shared memory (all fields loaded
+// in parallel at the start of the phases).
+struct JobView {
+    const float *E;        // energies (P-index order)
+    HashStats *st;
+    int32_t logB, list, active, pad;
+    uint32_t s1, p1, s2, p2;   // sigma and sigma^{-1} mod B per axis
+};
 
 // Local maxima of buckets [e0, e1) of one job by the whole block (e1 - e0 <= 16 x 256):
 // thread t tests P-indices e0 + t + 256 u, u < 16, from energies loaded up front; the
 // block's maxima are appended with one atomic, and the count of energies above X with
 // another.
-__device__ void localmax_task(const StatJob &J, const StatsParams &S, float T, int64_t e0,
+__device__ void localmax_task(const JobView &J, const StatsParams &S, float T, int64_t e0,
                               int64_t e1, float X)
 {
     constexpr int kPer = (int)(kTask / 256);
-    HashStats &st = S.stats[J.slot];
+    HashStats &st = *J.st;
     const int logB = J.logB;
     const uint32_t mask = (1u << logB) - 1;
-    const float *__restrict__ E = J.energy;
-    const uint32_t s1 = J.hash->sigma[0] & mask, p1 = J.hash->sinv[0] & mask;
-    const uint32_t s2 = J.hash->sigma[1] & mask, p2 = J.hash->sinv[1] & mask;
+    const float *__restrict__ E = J.E;
+    const uint32_t s1 = J.s1, p1 = J.p1, s2 = J.s2, p2 = J.p2;
     float ev[kPer];
 #pragma unroll
     for (int u = 0; u < kPer; u++) {
@@ -375,29 +299,63 @@ __device__ void localmax_task(const StatJob &J, const StatsParams &S, float T, i
         ev[u] = j < e1 ? __ldg(&E[j]) : 0.f;
     }
     uint32_t above = 0, found = 0;
+    if (S.ndim == 1) {
+        // both neighbours of every element requested at once (coalesced: consecutive
+        // threads hold consecutive P-indices)
+        float el[kPer], er[kPer];
 #pragma unroll
-    for (int u = 0; u < kPer; u++) {
-        const int64_t j = e0 + threadIdx.x + 256 * u;
-        const float e = ev[u];
-        above += j < e1 && e > X;
-        if (j < e1 && e > T) {
-            bool ok;
-            if (S.ndim == 1) {
-                const uint32_t jj = (uint32_t)j;
-                ok = dominates(e, __ldg(&E[(jj - p1) & mask]), S.up, 0, -1) &&
-                     dominates(e, __ldg(&E[(jj + p1) & mask]), S.up, 0, 1);
-            } else {
-                const uint32_t jA = (uint32_t)(j >> logB), jB = (uint32_t)(j & mask);
-                ok = true;
-                for (int d1 = -1; d1 <= 1 && ok; d1++)
-                    for (int d2 = -1; d2 <= 1 && ok; d2++) {
+        for (int u = 0; u < kPer; u++) {
+            const uint32_t jj = (uint32_t)(e0 + threadIdx.x + 256 * u);
+            el[u] = __ldg(&E[(jj - p1) & mask]);
+            er[u] = __ldg(&E[(jj + p1) & mask]);
+        }
+#pragma unroll
+        for (int u = 0; u < kPer; u++) {
+            const int64_t j = e0 + threadIdx.x + 256 * u;
+            const float e = ev[u];
+            above += j < e1 && e > X;
+            if (j < e1 && e > T && dominates(e, el[u], S.up, 0, -1) && dominates(e, er[u], S.up, 0, 1))
+                found |= 1u << u;
+        }
+    } else {
+        // eight neighbours, four elements at a time
+#pragma unroll
+        for (int u0 = 0; u0 < kPer; u0 += 4) {
+            float nbv[4][8];
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const int64_t j = e0 + threadIdx.x + 256 * (u0 + v);
+                const uint32_t jA = (uint32_t)(j >> logB) & mask, jB = (uint32_t)(j & mask);
+                int q = 0;
+#pragma unroll
+                for (int d1 = -1; d1 <= 1; d1++)
+#pragma unroll
+                    for (int d2 = -1; d2 <= 1; d2++) {
                         if (d1 == 0 && d2 == 0) continue;
                         const uint32_t m1 = (jA + (uint32_t)d1 * p1) & mask;
                         const uint32_t m2 = (jB + (uint32_t)d2 * p2) & mask;
-                        ok = dominates(e, __ldg(&E[((int64_t)m1 << logB) | m2]), S.up, d1, d2);
+                        nbv[v][q++] = __ldg(&E[((int64_t)m1 << logB) | m2]);
                     }
             }
-            if (ok) found |= 1u << u;
+#pragma unroll
+            for (int v = 0; v < 4; v++) {
+                const int u = u0 + v;
+                const int64_t j = e0 + threadIdx.x + 256 * u;
+                const float e = ev[u];
+                above += j < e1 && e > X;
+                if (!(j < e1 && e > T)) continue;
+                bool ok = true;
+                int q = 0;
+#pragma unroll
+                for (int d1 = -1; d1 <= 1; d1++)
+#pragma unroll
+                    for (int d2 = -1; d2 <= 1; d2++) {
+                        if (d1 == 0 && d2 == 0) continue;
+                        ok = ok && dominates(e, nbv[v][q], S.up, d1, d2);
+                        q++;
+                    }
+                if (ok) found |= 1u << u;
+            }
         }
     }
     __shared__ uint32_t base_sh;
@@ -430,6 +388,13 @@ __device__ void localmax_task(const StatJob &J, const StatsParams &S, float T, i
     __syncthreads();
 }
 
+// The recount after an exact median (rare): one out-of-line copy.
+__device__ __noinline__ void localmax_task_cold(const JobView &J, const StatsParams &S, float T,
+                                                int64_t e0, int64_t e1)
+{
+    localmax_task(J, S, T, e0, e1, INFINITY);
+}
+
 // Threshold and local maxima of njobs hashes whose energies and maxima the bucket FFTs
 // wrote.  Returns false if a barrier failed.
 __device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &S,
@@ -437,13 +402,33 @@ __device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &
 {
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
-    // work split into tasks of kTask buckets over all jobs (prefix table in shared memory)
+    // the jobs, loaded in parallel, and the work split into tasks of kTask buckets over
+    // all jobs (prefix table in shared memory)
+    __shared__ JobView jv[kMaxLoops + kMaxLogB];
     __shared__ int64_t tstart[kMaxLoops + kMaxLogB + 1];
+    __shared__ uint8_t med[kMaxLoops + kMaxLogB];
+    if (threadIdx.x < njobs) {
+        const StatJob J = jobs[threadIdx.x];
+        const uint32_t mask = (1u << J.logB) - 1;
+        JobView v;
+        v.E = J.energy;
+        v.st = S.stats + J.slot;
+        v.logB = J.logB;
+        v.list = J.list;
+        v.active = J.active;
+        v.pad = 0;
+        v.s1 = (uint32_t)J.hash->sigma[0] & mask;
+        v.p1 = (uint32_t)J.hash->sinv[0] & mask;
+        v.s2 = (uint32_t)J.hash->sigma[1] & mask;
+        v.p2 = (uint32_t)J.hash->sinv[1] & mask;
+        jv[threadIdx.x] = v;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         int64_t acc = 0;
         for (int jb = 0; jb < njobs; jb++) {
             tstart[jb] = acc;
-            if (jobs[jb].active) acc += (nb_of(S.ndim, jobs[jb].logB) + kTask - 1) / kTask;
+            if (jv[jb].active) acc += (nb_of(S.ndim, jv[jb].logB) + kTask - 1) / kTask;
         }
         tstart[njobs] = acc;
     }
@@ -454,61 +439,59 @@ __device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &
     for (int64_t task = blockIdx.x; task < ntasks; task += gridDim.x) {
         int jb = 0;
         while (task >= tstart[jb + 1]) jb++;
-        const StatJob &J = jobs[jb];
-        HashStats &st = S.stats[J.slot];
+        const JobView &J = jv[jb];
         const int64_t nb = nb_of(S.ndim, J.logB);
         const int64_t e0 = (task - tstart[jb]) * kTask;
         const int64_t e1 = min(e0 + kTask, nb);
-        const float M = __uint_as_float(st.max_bits);
+        const float M = __uint_as_float(J.st->max_bits);
         const float X = S.use_median ? M * S.ratio : INFINITY;
         localmax_task(J, S, S.thr_rel * M, e0, e1, X);
     }
     if (!grid_sync(gb, status)) return false;
     // C: exact median where it can matter, then recount those hashes' maxima.
     // C1: hashes with at most kSmallMedian buckets, one block each, in shared memory.
-    bool any_small = false, any_large = false;
-    for (int jb = 0; jb < njobs; jb++) {
-        const StatJob &J = jobs[jb];
-        if (!J.active) continue;
-        const HashStats &st = S.stats[J.slot];
+    bool mine_small = false, mine_large = false;
+    if (threadIdx.x < njobs) {
+        const JobView &J = jv[threadIdx.x];
         const int64_t nb = nb_of(S.ndim, J.logB);
-        if (S.use_median && (int64_t)st.above > nb - nb / 2 - 1) {
-            if (nb <= kSmallMedian) any_small = true;
-            else any_large = true;
-        }
+        med[threadIdx.x] = J.active && S.use_median && (int64_t)J.st->above > nb - nb / 2 - 1;
+        mine_small = med[threadIdx.x] && nb <= kSmallMedian;
+        mine_large = med[threadIdx.x] && nb > kSmallMedian;
     }
+    const bool any_small = __syncthreads_or(mine_small);
+    const bool any_large = __syncthreads_or(mine_large);
     if (!any_small && !any_large) return true;   // uniform: every block read the same counts
     if (any_small) {
         for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
-            const StatJob &J = jobs[jb];
-            if (!J.active) continue;
-            HashStats &st = S.stats[J.slot];
+            const JobView &J = jv[jb];
+            HashStats &st = *J.st;
             const int64_t nb = nb_of(S.ndim, J.logB);
-            if (nb > kSmallMedian || !((int64_t)st.above > nb - nb / 2 - 1)) continue;
-            const uint32_t med = block_median(J.energy, (int)nb);
+            if (!med[jb] || nb > kSmallMedian) continue;
+            const uint32_t m = block_median(J.E, (int)nb);
             if (threadIdx.x == 0) {
                 st.need_median = 1;
-                st.med_bits = med;
+                st.med_bits = m;
                 st.nmax = 0;
             }
             __syncthreads();
-            localmax_block(J, S, threshold_of(st, S));
+            const float T = threshold_of(st, S);
+            for (int64_t e0 = 0; e0 < nb; e0 += kTask) localmax_task_cold(J, S, T, e0, min(e0 + kTask, nb));
         }
     }
     if (!any_large) return grid_sync(gb, status);
     // C2: larger hashes, grid-wide radix select
-    extern __shared__ uint32_t dsm[];
+    extern __shared__ __align__(16) uint32_t dsm[];
     uint32_t *h = dsm;   // kHistBins entries
     for (int digit = 0; digit < 3; digit++) {
         int lo, width;
         digit_range(digit, lo, width);
         const int hi = lo + width;
         for (int jb = 0; jb < njobs; jb++) {
-            const StatJob &J = jobs[jb];
-            if (!J.active) continue;
-            HashStats &st = S.stats[J.slot];
+            const JobView &J = jv[jb];
+            HashStats &st = *J.st;
             const int64_t nb = nb_of(S.ndim, J.logB);
-            if (nb <= kSmallMedian || !((int64_t)st.above > nb - nb / 2 - 1)) continue;
+            const int slot = (int)(J.st - S.stats);
+            if (nb <= kSmallMedian || !med[jb]) continue;
             if (digit == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
                 st.need_median = 1;
                 st.prefix = 0;
@@ -518,23 +501,22 @@ __device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &
             for (int b = threadIdx.x; b < (1 << width); b += blockDim.x) h[b] = 0;
             __syncthreads();
             for (int64_t j = gtid; j < nb; j += gthreads) {
-                const uint32_t bits = __float_as_uint(J.energy[j]);
+                const uint32_t bits = __float_as_uint(J.E[j]);
                 if (digit == 0 || (bits >> hi) == prefix) hist_add(h, (bits >> lo) & ((1u << width) - 1));
             }
             __syncthreads();
             for (int b = threadIdx.x; b < (1 << width); b += blockDim.x)
-                if (h[b]) atomicAdd(&S.hist[(int64_t)J.slot * kHistBins + b], h[b]);
+                if (h[b]) atomicAdd(&S.hist[(int64_t)slot * kHistBins + b], h[b]);
             __syncthreads();
         }
         if (!grid_sync(gb, status)) return false;
         // pick: block jb % gridDim handles job jb
         for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
-            const StatJob &J = jobs[jb];
-            if (!J.active) continue;
-            HashStats &st = S.stats[J.slot];
+            const JobView &J = jv[jb];
+            HashStats &st = *J.st;
             const int64_t nb = nb_of(S.ndim, J.logB);
-            if (nb <= kSmallMedian || !((int64_t)st.above > nb - nb / 2 - 1)) continue;
-            uint32_t *hh = S.hist + (int64_t)J.slot * kHistBins;
+            if (nb <= kSmallMedian || !med[jb]) continue;
+            uint32_t *hh = S.hist + (int64_t)(J.st - S.stats) * kHistBins;
             const uint32_t rank = digit == 0 ? (uint32_t)(nb / 2) : st.rank;
             __shared__ uint32_t fb, fr;
             block_find_rank(hh, 1 << width, rank, &fb, &fr);
@@ -554,12 +536,13 @@ __device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &
         if (!grid_sync(gb, status)) return false;
     }
     for (int jb = 0; jb < njobs; jb++) {
-        const StatJob &J = jobs[jb];
-        if (!J.active) continue;
-        HashStats &st = S.stats[J.slot];
+        const JobView &J = jv[jb];
+        HashStats &st = *J.st;
         const int64_t nb = nb_of(S.ndim, J.logB);
-        if (!st.need_median || nb <= kSmallMedian) continue;
-        localmax_job(J, S, threshold_of(st, S), gtid, gthreads, nullptr, INFINITY);
+        if (!med[jb] || nb <= kSmallMedian) continue;
+        const float T = threshold_of(st, S);
+        for (int64_t e0 = (int64_t)blockIdx.x * kTask; e0 < nb; e0 += (int64_t)gridDim.x * kTask)
+            localmax_task_cold(J, S, T, e0, min(e0 + kTask, nb));
     }
     return grid_sync(gb, status);
 }
@@ -642,7 +625,7 @@ __device__ void controller(const TuneTailArgs &A)
     }
 }
 
-__global__ void __launch_bounds__(256) k_tune_tail(const TuneTailArgs A)
+__global__ void __launch_bounds__(256, 2) k_tune_tail(const TuneTailArgs A)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) stamp(&A.state->bar);
     if (!stats_phases(A.jobs, A.njobs, A.S, &A.state->bar, &A.state->status)) return;
@@ -743,7 +726,7 @@ __device__ void topnum_block(const StatJob &J, const LocTailArgs &A, int64_t num
         return E[((int64_t)((p1 * c1) & mask) << logB) | ((p2 * c2) & mask)];
     };
     // the candidates' energies, staged once when they fit
-    extern __shared__ uint32_t dsm[];
+    extern __shared__ __align__(16) uint32_t dsm[];
     float *es = reinterpret_cast<float *>(dsm);   // kTopStage entries
     const bool staged = cnt <= kTopStage;
     if (staged)
@@ -850,32 +833,28 @@ __device__ float2 estimate_term(uint64_t coord, const LocTailArgs &A, int b, int
     return make_float2((pv.x * w.x - pv.y * w.y) * rg, (pv.x * w.y + pv.y * w.x) * rg);
 }
 
-// Componentwise median of L values (element floor(L/2) of each sorted component; equal
-// values ordered by hash index), by ranks.
-__device__ __forceinline__ float2 median_of(const float (&vr)[kMaxLoops], const float (&vi)[kMaxLoops],
-                                            int L)
+// Componentwise median (element floor(L/2) of each sorted component; equal values
+// ordered by hash index) of the values v held by lanes 0..L-1 of a group of grp lanes:
+// each lane ranks its own value against the group's by shuffles, and the lane of rank
+// floor(L/2) stores that component to *out.  All lanes of the warp must call.
+__device__ __forceinline__ void group_median(float2 v, int L, int grp, bool valid, float2 *out)
 {
-    const int want = L / 2;
-    float mr = 0.f, mi = 0.f;
-#pragma unroll
-    for (int a = 0; a < kMaxLoops; a++) {
-        if (a >= L) break;
-        int rr = 0, ri = 0;
-#pragma unroll
-        for (int c = 0; c < kMaxLoops; c++) {
-            if (c >= L) break;
-            rr += vr[c] < vr[a] || (vr[c] == vr[a] && c < a);
-            ri += vi[c] < vi[a] || (vi[c] == vi[a] && c < a);
-        }
-        if (rr == want) mr = vr[a];
-        if (ri == want) mi = vi[a];
+    const int gl = (int)(threadIdx.x & 31) & (grp - 1);
+    int rr = 0, ri = 0;
+    for (int c = 0; c < L; c++) {
+        const float xr = __shfl_sync(0xffffffffu, v.x, c, grp);
+        const float xi = __shfl_sync(0xffffffffu, v.y, c, grp);
+        rr += xr < v.x || (xr == v.x && c < gl);
+        ri += xi < v.y || (xi == v.y && c < gl);
     }
-    return make_float2(mr, mi);
+    if (valid && gl < L) {
+        if (rr == L / 2) out->x = v.x;
+        if (ri == L / 2) out->y = v.y;
+    }
 }
 
 // Estimates of the kept coordinates: a group of `grp` lanes (grp >= L_est, a power of two)
-// per coordinate, lane l computing hash l; the group's first lane gathers the values by
-// shuffles and takes the componentwise median (element floor(L/2) after sorting).
+// per coordinate, lane l computing hash l, then the group's componentwise median.
 __device__ void estimate_all(const LocTailArgs &A, int64_t cnt, int b)
 {
     const int grp = A.est_group;
@@ -888,15 +867,7 @@ __device__ void estimate_all(const LocTailArgs &A, int64_t cnt, int b)
         const bool valid = s < cnt;
         float2 v = make_float2(0.f, 0.f);
         if (valid && gl < A.L_est) v = estimate_term((uint64_t)A.loc[s], A, b, gl);
-        float vr[kMaxLoops], vi[kMaxLoops];
-#pragma unroll
-        for (int l = 0; l < kMaxLoops; l++) {
-            if (l < A.L_est) {
-                vr[l] = __shfl_sync(0xffffffffu, v.x, l, grp);
-                vi[l] = __shfl_sync(0xffffffffu, v.y, l, grp);
-            }
-        }
-        if (valid && gl == 0) A.val[s] = median_of(vr, vi, A.L_est);
+        group_median(v, A.L_est, grp, valid, &A.val[valid ? s : 0]);
     }
 }
 
@@ -905,16 +876,81 @@ __device__ void estimate_all(const LocTailArgs &A, int64_t cnt, int b)
 __device__ __forceinline__ uint32_t bucket_of(uint32_t i, uint32_t sigma, int logn, int logB)
 {
     const uint32_t nmask = (1u << logn) - 1, D = 1u << (logn - logB);
-    const uint32_t p = (sigma * i) & nmask;
-    return (uint32_t)(((2ull * p + 1 + D) / (2ull * D)) & ((1u << logB) - 1));
+    const uint32_t p = (sigma * i) & nmask;   // 2p + 1 + D < 2^30 for n <= 2^28
+    return ((2u * p + 1u + D) >> (logn - logB + 1)) & ((1u << logB) - 1);
 }
 
-constexpr int kRankStage = 2048;   // top-num by ranking: candidates staged per block
+constexpr int kRankStage = 4096;   // top-num by ranking: candidates staged per block
+constexpr int kRankLanes = 8;      // lanes sharing one candidate's rank
+constexpr int kSelBlocks = 4;      // blocks per location hash in the cutoff
+constexpr int kPivots = 32;
+constexpr int kVoteUnroll = 8;     // location hashes whose bitmap words are fetched together
 
-// Index of hash l's bucket c in its bitmap (c is the linear bucket index, 2D: c1 B + c2).
-__device__ __forceinline__ bool bucket_selected(const LocTailArgs &A, int l, uint32_t c)
+// Value of descending rank r (0-based; equal values ordered by index) among es[0..cnt),
+// by the whole block.  kPivots sampled values are counted against all elements; only the
+// elements between the two pivots that bracket rank r are then ranked exactly (a
+// group of kRankLanes lanes per element).  scratch: cnt entries of shared memory.
+__device__ __noinline__ float block_select_desc(const float *es, int cnt, uint32_t r, uint32_t *scratch)
 {
-    return (A.bucketbits[(int64_t)l * A.bucket_words + (c >> 5)] >> (c & 31)) & 1u;
+    __shared__ float pv[kPivots];
+    __shared__ uint32_t pg[kPivots];
+    __shared__ float lo_sh, hi_sh, v_sh;
+    __shared__ uint32_t nbr;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    if (threadIdx.x < kPivots) pv[threadIdx.x] = es[(int64_t)threadIdx.x * cnt / kPivots];
+    if (threadIdx.x == 0) nbr = 0;
+    __syncthreads();
+    // g[p] = #{e > pv[p]}: a warp per pivot, lanes over the elements
+    for (int p = warp; p < kPivots; p += nwarp) {
+        const float v = pv[p];
+        uint32_t g = 0;
+        for (int j = lane; j < cnt; j += 32) g += es[j] > v;
+        g = warp_sum(g);
+        if (lane == 0) pg[p] = g;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // V lies in (L, U]: L the largest pivot with >= r + 1 elements above it, U the
+        // smallest pivot with <= r elements above it
+        float L = -INFINITY, U = INFINITY;
+        for (int p = 0; p < kPivots; p++) {
+            if (pg[p] >= r + 1) L = fmaxf(L, pv[p]);
+            else U = fminf(U, pv[p]);
+        }
+        lo_sh = L;
+        hi_sh = U;
+    }
+    __syncthreads();
+    const float L = lo_sh, U = hi_sh;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const float e = es[i];
+        if (e > L && e <= U) scratch[atomicAdd(&nbr, 1u)] = (uint32_t)i;
+    }
+    __syncthreads();
+    // every element outside (L, U] is either above U (there are g(U) of those) or at most
+    // L, so a bracket member's rank is g(U) plus its rank inside the bracket
+    __shared__ uint32_t above_u;
+    if (threadIdx.x == 0) {
+        uint32_t g = 0;
+        for (int p = 0; p < kPivots; p++)
+            if (pv[p] == U) g = pg[p];
+        above_u = U == INFINITY ? 0u : g;
+    }
+    __syncthreads();
+    const int nb = (int)nbr;
+    for (int m = threadIdx.x; m < nb; m += blockDim.x) {
+        const int i = (int)scratch[m];
+        const float e = es[i];
+        uint32_t rk = above_u;
+        for (int q = 0; q < nb; q++) {
+            const int j = (int)scratch[q];
+            const float f = es[j];
+            rk += f > e || (f == e && j < i);
+        }
+        if (rk == r) v_sh = e;
+    }
+    __syncthreads();
+    return v_sh;
 }
 
 // The location tail.  Phases, each ended by a grid barrier:
@@ -931,7 +967,7 @@ __device__ __forceinline__ bool bucket_selected(const LocTailArgs &A, int l, uin
 //       componentwise median, written in place.  More kept coordinates than the kept
 //       list holds: ordered compaction of the coordinate bitmap instead (three more
 //       phases) and the estimates after it.
-__global__ void __launch_bounds__(256) k_loc_tail(const LocTailArgs A)
+__global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
 {
     ExecState *state = A.state;
     GridBarrier *gb = &state->bar;
@@ -941,7 +977,7 @@ __global__ void __launch_bounds__(256) k_loc_tail(const LocTailArgs A)
     const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    extern __shared__ uint32_t dsm[];
+    extern __shared__ __align__(16) uint32_t dsm[];
     if (empty) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             *A.d_count = 0;
@@ -963,60 +999,62 @@ __global__ void __launch_bounds__(256) k_loc_tail(const LocTailArgs A)
     // ---- P1 ----
     if (!stats_phases(A.jobs, A.L_loc, A.S, gb, status)) return;
 
-    // ---- P2a: pivot ranks ----
-    // blocks [l G, (l + 1) G) serve hash l; their candidates (and energies) stay staged
-    // in shared memory through P2b
-    const int G = gridDim.x / A.L_loc;
-    const int l_mine = G > 0 ? (int)blockIdx.x / G : A.L_loc;
-    const int sb = G > 0 ? (int)blockIdx.x % G : 0;
-    float *es = reinterpret_cast<float *>(dsm);                   // kRankStage energies
-    uint32_t *cs = dsm + kRankStage;                                // kRankStage buckets
-    uint32_t *band = dsm + 2 * kRankStage;                          // kRankStage band buckets
-    int64_t cnt = 0;
-    bool ranked = false;
+    // ---- P2: top-num cutoff and the selected-bucket bitmaps ----
+    // blocks [l G, (l + 1) G) serve hash l; each finds the pivot V itself and decides a
+    // share of the candidates
+    const int G = min(kSelBlocks, (int)gridDim.x / A.L_loc);
+    const int l_mine = (int)blockIdx.x / G;
+    const int sb = (int)blockIdx.x % G;
     if (l_mine < A.L_loc) {
         const StatJob &J = A.jobs[l_mine];
         HashStats &st = A.S.stats[J.slot];
-        cnt = min((int64_t)st.nmax, A.S.cap);
-        const uint32_t mask = (uint32_t)(nb_of(1, b) - 1);
-        const uint32_t p1 = (uint32_t)J.hash->sinv[0] & mask, p2 = (uint32_t)J.hash->sinv[1] & mask;
-        const int32_t *list = A.S.lists + (int64_t)J.list * A.S.cap;
-        if (cnt > num && cnt <= kRankStage) {
-            ranked = true;
-            for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-                const uint32_t c = (uint32_t)list[i];
-                const int64_t pj = ndim == 1 ? (int64_t)((p1 * c) & mask)
-                                             : ((int64_t)((p1 * (c >> b)) & mask) << b) |
-                                                   ((p2 * (c & mask)) & mask);
-                cs[i] = c;
-                es[i] = J.energy[pj];
-            }
-            __syncthreads();
-            for (int64_t i = (int64_t)sb * blockDim.x + threadIdx.x; i < cnt;
-                 i += (int64_t)G * blockDim.x) {
-                const float e = es[i];
-                uint32_t r = 0;
-                for (int64_t j = 0; j < cnt; j++) {
-                    const float f = es[j];
-                    r += f > e || (f == e && j < i);
-                }
-                if (r == (uint32_t)(num - 1)) st.v_bits = __float_as_uint(e);
-            }
-        } else if (cnt > num && sb == 0) {
-            topnum_block(J, A, num);   // writes sel and nsel itself
-        }
-    }
-    if (!grid_sync(gb, status)) return;
-
-    // ---- P2b: cutoff and bitmaps ----
-    if (l_mine < A.L_loc) {
-        const StatJob &J = A.jobs[l_mine];
-        HashStats &st = A.S.stats[J.slot];
+        const int64_t cnt = min((int64_t)st.nmax, A.S.cap);
         uint32_t *bits = A.bucketbits + (int64_t)l_mine * A.bucket_words;
         int32_t *out = A.sel + (int64_t)J.list * A.S.cap;
         const int32_t *list = A.S.lists + (int64_t)J.list * A.S.cap;
-        if (ranked) {
-            const float V = __uint_as_float(st.v_bits);
+        if (cnt <= num) {
+            // every maximum is kept: the list is the selection
+            for (int64_t i = (int64_t)sb * blockDim.x + threadIdx.x; i < cnt;
+                 i += (int64_t)G * blockDim.x) {
+                const uint32_t c = (uint32_t)list[i];
+                out[i] = (int32_t)c;
+                atomicOr(&bits[c >> 5], 1u << (c & 31));
+            }
+            if (sb == 0 && threadIdx.x == 0) st.nsel = (uint32_t)cnt;
+        } else if (cnt <= kRankStage) {
+            float *es = reinterpret_cast<float *>(dsm);   // kRankStage energies
+            uint32_t *cs = dsm + kRankStage;              // kRankStage buckets
+            uint32_t *band = dsm + 2 * kRankStage;        // band buckets / bracket members
+            const uint32_t mask = (uint32_t)(nb_of(1, b) - 1);
+            const uint32_t p1 = (uint32_t)J.hash->sinv[0] & mask, p2 = (uint32_t)J.hash->sinv[1] & mask;
+            // staged eight per thread at a time: the buckets, then their energies
+            for (int64_t i0 = 0; i0 < cnt; i0 += 8 * blockDim.x) {
+                uint32_t cc[8];
+                float ee[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const int64_t i = i0 + u * blockDim.x + threadIdx.x;
+                    cc[u] = i < cnt ? (uint32_t)list[i] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const uint32_t c = cc[u];
+                    const int64_t pj = ndim == 1 ? (int64_t)((p1 * c) & mask)
+                                                 : ((int64_t)((p1 * (c >> b)) & mask) << b) |
+                                                       ((p2 * (c & mask)) & mask);
+                    ee[u] = __ldg(&J.energy[pj]);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    const int64_t i = i0 + u * blockDim.x + threadIdx.x;
+                    if (i < cnt) {
+                        cs[i] = cc[u];
+                        es[i] = ee[u];
+                    }
+                }
+            }
+            __syncthreads();
+            const float V = block_select_desc(es, (int)cnt, (uint32_t)(num - 1), band);
             const float hi = V * A.eta_up, lo = V * A.eta_dn;
             __shared__ uint32_t nband;
             if (threadIdx.x == 0) nband = 0;
@@ -1057,20 +1095,11 @@ __global__ void __launch_bounds__(256) k_loc_tail(const LocTailArgs A)
                     atomicOr(&bits[c >> 5], 1u << (c & 31));
                 }
             }
-        } else if (cnt <= num) {
-            // every maximum is kept: the list is the selection
-            for (int64_t i = (int64_t)sb * blockDim.x + threadIdx.x; i < cnt;
-                 i += (int64_t)G * blockDim.x) {
-                const uint32_t c = (uint32_t)list[i];
-                out[i] = (int32_t)c;
-                atomicOr(&bits[c >> 5], 1u << (c & 31));
-            }
-            if (sb == 0 && threadIdx.x == 0) st.nsel = (uint32_t)cnt;
-        } else {
-            // selected by one block in P2a
+        } else if (sb == 0) {
+            // more maxima than stage: one block selects by radix selection, then marks them
+            topnum_block(J, A, num);
             const int64_t ns = st.nsel;
-            for (int64_t i = (int64_t)sb * blockDim.x + threadIdx.x; i < ns;
-                 i += (int64_t)G * blockDim.x) {
+            for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) {
                 const uint32_t c = (uint32_t)out[i];
                 atomicOr(&bits[c >> 5], 1u << (c & 31));
             }
@@ -1101,52 +1130,95 @@ __global__ void __launch_bounds__(256) k_loc_tail(const LocTailArgs A)
     }
     __syncthreads();
     {
+        // four preimages per thread per round: their buckets and the other hashes' bitmap
+        // words are all requested before any is used
+        constexpr int kU = 4;
         const int64_t total = off[L_cand];
-        for (int64_t it0 = (int64_t)blockIdx.x * blockDim.x; it0 < total; it0 += gthreads) {
-            const int64_t it = it0 + threadIdx.x;
-            bool keep = false;
-            uint32_t coord = 0;
-            if (it < total) {
-                int l0 = 0;
-                while (it >= off[l0 + 1]) l0++;
-                const int64_t rem = it - off[l0];
-                const int64_t sidx = rem >> (ndim == 1 ? logD : 2 * logD);
-                const uint32_t q = (uint32_t)(rem & (Dd - 1));
-                const uint32_t c = (uint32_t)A.sel[(int64_t)l0 * A.S.cap + sidx];
+        for (int64_t it0 = (int64_t)blockIdx.x * blockDim.x; it0 < total; it0 += kU * gthreads) {
+            uint32_t coord[kU], cb[kU], qv[kU];
+            int l0v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                const int64_t it = it0 + (int64_t)u * gthreads + threadIdx.x;
+                l0v[u] = -1;
+                if (it < total) {
+                    int l0 = 0;
+                    while (it >= off[l0 + 1]) l0++;
+                    const int64_t rem = it - off[l0];
+                    const int64_t sidx = rem >> (ndim == 1 ? logD : 2 * logD);
+                    qv[u] = (uint32_t)(rem & (Dd - 1));
+                    cb[u] = (uint32_t)A.sel[(int64_t)l0 * A.S.cap + sidx];
+                    l0v[u] = l0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                coord[u] = 0;
+                if (l0v[u] < 0) continue;
+                const int l0 = l0v[u];
+                const uint32_t c = cb[u], q = qv[u];
                 if (ndim == 1) {
                     // bucket c collects permuted positions p in [c D - D/2, c D + D/2 - 1]
                     const uint32_t pp = ((c << logD) - (uint32_t)(D >> 1) + q) & nmask;
-                    coord = (sh_sinv[l0][0] * pp) & nmask;
+                    coord[u] = (sh_sinv[l0][0] * pp) & nmask;
                 } else {
                     const uint32_t c1 = c >> b, c2 = c & Bm;
                     const uint32_t q1 = q >> logD, q2 = q & (uint32_t)(D - 1);
                     const uint32_t pp1 = ((c1 << logD) - (uint32_t)(D >> 1) + q1) & nmask;
                     const uint32_t pp2 = ((c2 << logD) - (uint32_t)(D >> 1) + q2) & nmask;
-                    coord = (((sh_sinv[l0][0] * pp1) & nmask) << logn) | ((sh_sinv[l0][1] * pp2) & nmask);
+                    coord[u] = (((sh_sinv[l0][0] * pp1) & nmask) << logn) |
+                               ((sh_sinv[l0][1] * pp2) & nmask);
                 }
-                const uint32_t ci = ndim == 1 ? coord : coord >> logn;
-                const uint32_t cj = ndim == 1 ? 0u : coord & nmask;
-                uint32_t votes = 1;   // hash l0 itself
-                bool first = true;
-                for (int l = 0; l < A.L_loc; l++) {
-                    if (l == l0) continue;
-                    uint32_t c_l = bucket_of(ci, sh_sig[l][0], logn, b);
-                    if (ndim == 2) c_l = (c_l << b) | bucket_of(cj, sh_sig[l][1], logn, b);
-                    const bool sel = bucket_selected(A, l, c_l);
-                    votes += sel;
-                    if (sel && l < l0) first = false;
-                }
-                keep = first && votes >= A.need;
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            uint32_t base = 0;
-            if (lane == 0 && bal) base = (uint32_t)atomicAdd((unsigned long long *)&state->count,
-                                                             (unsigned long long)__popc(bal));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (keep) {
-                const uint32_t pos = base + __popc(bal & ((1u << lane) - 1));
-                if (pos < A.kept_cap) A.kept[pos] = coord;
-                atomicOr(&A.coordbits[coord >> 5], 1u << (coord & 31));
+            uint32_t votes[kU], earlier[kU];
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                votes[u] = 0;
+                earlier[u] = 0;
+            }
+            // the bitmap word of every (preimage, hash) pair is requested before any is
+            // tested; up to kVoteUnroll hashes at a time
+            for (int l0 = 0; l0 < A.L_loc; l0 += kVoteUnroll) {
+                uint32_t w[kU][kVoteUnroll];
+#pragma unroll
+                for (int dl = 0; dl < kVoteUnroll; dl++) {
+                    const int l = l0 + dl;
+#pragma unroll
+                    for (int u = 0; u < kU; u++) {
+                        w[u][dl] = 0;
+                        if (l < A.L_loc && l0v[u] >= 0) {
+                            const uint32_t ci = ndim == 1 ? coord[u] : coord[u] >> logn;
+                            uint32_t c_l = bucket_of(ci, sh_sig[l][0], logn, b);
+                            if (ndim == 2) c_l = (c_l << b) | bucket_of(coord[u] & nmask, sh_sig[l][1], logn, b);
+                            w[u][dl] = A.bucketbits[(int64_t)l * A.bucket_words + (c_l >> 5)] >> (c_l & 31);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int dl = 0; dl < kVoteUnroll; dl++) {
+#pragma unroll
+                    for (int u = 0; u < kU; u++) {
+                        const uint32_t sel = w[u][dl] & 1u;
+                        votes[u] += sel;
+                        earlier[u] |= sel && l0 + dl < l0v[u];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; u++) {
+                const bool keep = l0v[u] >= 0 && !earlier[u] && votes[u] >= A.need;
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                if (!bal) continue;
+                uint32_t base = 0;
+                if (lane == __ffs(bal) - 1)
+                    base = (uint32_t)atomicAdd((unsigned long long *)&state->count,
+                                               (unsigned long long)__popc(bal));
+                base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+                if (keep) {
+                    const uint32_t pos = base + __popc(bal & ((1u << lane) - 1));
+                    if (pos < A.kept_cap) A.kept[pos] = coord[u];
+                    atomicOr(&A.coordbits[coord[u] >> 5], 1u << (coord[u] & 31));
+                }
             }
         }
     }
@@ -1178,7 +1250,19 @@ __global__ void __launch_bounds__(256) k_loc_tail(const LocTailArgs A)
             for (int64_t c0 = 0; c0 < K; c0 += kChunk) {
                 const int64_t c1 = min(c0 + (int64_t)kChunk, K);
                 __syncthreads();
-                for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x) ks[i - c0] = A.kept[i];
+                for (int64_t i0 = c0; i0 < c1; i0 += 8 * blockDim.x) {
+                    uint32_t kv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; u++) {
+                        const int64_t i = i0 + u * blockDim.x + threadIdx.x;
+                        kv[u] = i < c1 ? A.kept[i] : 0u;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; u++) {
+                        const int64_t i = i0 + u * blockDim.x + threadIdx.x;
+                        if (i < c1) ks[i - c0] = kv[u];
+                    }
+                }
                 __syncthreads();
                 if (valid)
                     for (int64_t i = c0 + gl; i < c1; i += grp) r += ks[i - c0] < coord;
@@ -1188,20 +1272,11 @@ __global__ void __launch_bounds__(256) k_loc_tail(const LocTailArgs A)
                 if (o < grp) r += __shfl_xor_sync(0xffffffffu, r, o, grp);
             float2 v = make_float2(0.f, 0.f);
             if (valid && r < A.capacity && gl < A.L_est) v = estimate_term(coord, A, b, gl);
-            float vr[kMaxLoops], vi[kMaxLoops];
-#pragma unroll
-            for (int l = 0; l < kMaxLoops; l++) {
-                if (l < A.L_est) {
-                    vr[l] = __shfl_sync(0xffffffffu, v.x, l, grp);
-                    vi[l] = __shfl_sync(0xffffffffu, v.y, l, grp);
-                }
-            }
+            const bool inside = valid && r < A.capacity;
+            group_median(v, A.L_est, grp, inside, &A.val[inside ? r : 0]);
             if (valid && gl == 0) {
                 A.coordbits[coord >> 5] = 0u;   // only kept coordinates set bits
-                if (r < A.capacity) {
-                    A.loc[r] = coord;
-                    A.val[r] = median_of(vr, vi, A.L_est);
-                }
+                if (inside) A.loc[r] = coord;
             }
         }
         return;
@@ -1272,8 +1347,10 @@ static StatsParams stats_params(const atsfft_plan_s *P)
 }
 
 // Dynamic shared memory of the tail kernels: the largest phase scratch (the small-hash
-// median: kSmallMedian values + 2048 histogram bins).
-constexpr size_t kTailSmem = sizeof(uint32_t) * (kSmallMedian + 2048);
+// median: kSmallMedian values + 2048 histogram bins; the cutoff: 3 kRankStage words).
+constexpr size_t kTailSmemWords = (kSmallMedian + 2048) > 3 * kRankStage ? (kSmallMedian + 2048)
+                                                                          : 3 * kRankStage;
+constexpr size_t kTailSmem = sizeof(uint32_t) * kTailSmemWords;
 
 static cudaError_t launch_coop(const void *fn, int grid, void *arg, cudaStream_t s)
 {
