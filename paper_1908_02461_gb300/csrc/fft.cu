@@ -143,37 +143,74 @@ __device__ __forceinline__ void next_stages(float2 *sm, int TP, int lm0,
     __syncthreads();
 }
 
-// T adjacent transforms t0..t0+T-1 by the whole CTA (T * P <= kSmallFFT): element j of
-// transform t0+u is src[u * in_bs + j * in_es] summed over `chunks` blocks
+constexpr int kMaxTile = 8;    // transforms per tile
+
+// exp(-2 pi i m / B) for B = 2^logB in (2^12, 2^24]: coarse table entry times fine entry.
+__device__ __forceinline__ float2 four_step_twiddle(uint32_t m, int logB, const float2 *__restrict__ tw)
+{
+    const int sh = logB - 12;
+    const float2 c = __ldg(&tw[m >> sh]);
+    const float2 f = __ldg(&tw[kSmallFFT + ((m & ((1u << sh) - 1)) << (24 - logB))]);
+    return make_float2(c.x * f.x - c.y * f.y, c.x * f.y + c.y * f.x);
+}
+
+// T = 2^logT adjacent transforms t0..t0+T-1 by the whole CTA (T * P <= kSmallFFT):
+// element j of transform t0+u is src[u * in_bs + j * in_es] summed over `chunks` blocks
 // chunk_stride apart; the result k (optionally twiddled by exp(-2 pi i t k / 2^tw_logB))
-// goes to dst[u * out_bs + k * out_es].  Threads walk the tile along whichever stride
-// is 1, so strided (column) transforms still load and store whole segments.  The
+// goes to dst[u * out_bs + k * out_es] (all offsets inside a tile fit in 32 bits).
+// Either in_es == 1 (each transform contiguous:
+// threads walk j) or in_bs == 1 (the T transforms interleaved: a thread moves the T
+// contiguous values of one j with 16-byte accesses); the same for the output.  The
 // log2 P radix-2 stages run three at a time on 8-value groups in registers.
-__device__ void fft_tile(const float2 *src, int64_t in_es, int64_t in_bs, int chunks,
-                         int64_t chunk_stride, float2 *dst, int64_t out_es, int64_t out_bs,
-                         int logP, int T, int tw_logB, int64_t t0, float2 *sm,
+__device__ void fft_tile(const float2 *src, int in_es, int in_bs, int chunks,
+                         int chunk_stride, float2 *dst, int out_es, int out_bs,
+                         int logP, int logT, int tw_logB, int64_t t0, float2 *sm,
                          const float2 *__restrict__ tw, float *edst, uint32_t *emax)
 {
-    const int P = 1 << logP;
-    const int TP = T * P;
-    const bool in_rows = in_es == 1;     // walk j fastest, else walk the transforms fastest
-    for (int idx = threadIdx.x; idx < TP; idx += blockDim.x) {
-        const int u = in_rows ? idx >> logP : idx % T;
-        const int j = in_rows ? idx & (P - 1) : idx / T;
-        const float2 *p = src + (int64_t)u * in_bs + (int64_t)j * in_es;
-        float2 v = p[0];
-        for (int c = 1; c < chunks; c++) {
-            const float2 w = p[(int64_t)c * chunk_stride];
-            v.x += w.x;
-            v.y += w.y;
+    const int P = 1 << logP, T = 1 << logT;
+    const int TP = T << logP;
+    if (in_es == 1 || T == 1) {
+        for (int idx = threadIdx.x; idx < TP; idx += blockDim.x) {
+            const int u = idx >> logP, j = idx & (P - 1);
+            const float2 *p = src + u * in_bs + j;
+            float2 v = p[0];
+            for (int c = 1; c < chunks; c++) {
+                const float2 w = p[c * chunk_stride];
+                v.x += w.x;
+                v.y += w.y;
+            }
+            sm[padi((u << logP) + j)] = v;
         }
-        sm[padi(u * P + j)] = v;
+    } else {
+        for (int j = threadIdx.x; j < P; j += blockDim.x) {
+            const float4 *p = reinterpret_cast<const float4 *>(src + j * in_es);
+            // four transforms (two 16-byte loads per chunk) at a time
+#pragma unroll 1
+            for (int u = 0; u < T; u += 4) {
+                const bool two = u + 2 < T;
+                float4 a = p[u >> 1], b = two ? p[(u >> 1) + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int c = 1; c < chunks; c++) {
+                    const float4 *pc = p + ((c * chunk_stride) >> 1);
+                    const float4 wa = pc[u >> 1];
+                    a.x += wa.x; a.y += wa.y; a.z += wa.z; a.w += wa.w;
+                    if (two) {
+                        const float4 wb = pc[(u >> 1) + 1];
+                        b.x += wb.x; b.y += wb.y; b.z += wb.z; b.w += wb.w;
+                    }
+                }
+                sm[padi((u << logP) + j)] = make_float2(a.x, a.y);
+                sm[padi(((u + 1) << logP) + j)] = make_float2(a.z, a.w);
+                if (two) {
+                    sm[padi(((u + 2) << logP) + j)] = make_float2(b.x, b.y);
+                    sm[padi(((u + 3) << logP) + j)] = make_float2(b.z, b.w);
+                }
+            }
+        }
     }
     __syncthreads();
     // stages 1 .. logP: groups of three, the first one also doing the bit reversal
     const int r0 = logP < kMaxRadixLog ? logP : kMaxRadixLog;
     switch (r0) {
-    case 4: first_stages<4>(sm, TP, logP, tw); break;
     case 3: first_stages<3>(sm, TP, logP, tw); break;
     case 2: first_stages<2>(sm, TP, logP, tw); break;
     case 1: first_stages<1>(sm, TP, logP, tw); break;
@@ -182,46 +219,64 @@ __device__ void fft_tile(const float2 *src, int64_t in_es, int64_t in_bs, int ch
     for (int lm0 = r0 + 1; lm0 <= logP;) {
         const int r = logP - lm0 + 1 < kMaxRadixLog ? logP - lm0 + 1 : kMaxRadixLog;
         switch (r) {
-        case 4: next_stages<4>(sm, TP, lm0, tw); break;
         case 3: next_stages<3>(sm, TP, lm0, tw); break;
         case 2: next_stages<2>(sm, TP, lm0, tw); break;
         default: next_stages<1>(sm, TP, lm0, tw); break;
         }
         lm0 += r;
     }
-    const bool out_rows = out_es == 1;
-    const int tw_shift = tw_logB - 12;   // four-step twiddle: coarse and fine table parts
-    float m = 0.f;
-    for (int idx = threadIdx.x; idx < TP; idx += blockDim.x) {
-        const int u = out_rows ? idx >> logP : idx % T;
-        const int k = out_rows ? idx & (P - 1) : idx / T;
-        float2 v = sm[padi(u * P + k)];
-        if (tw_logB >= 0) {
-            // exp(-2 pi i m / B), m = t k mod B, B = 2^tw_logB in (2^12, 2^24]
-            const uint32_t m = (uint32_t)(((t0 + u) * k) & (((int64_t)1 << tw_logB) - 1));
-            const float2 c = __ldg(&tw[m >> tw_shift]);
-            const float2 f = __ldg(&tw[kSmallFFT + ((m & ((1u << tw_shift) - 1)) << (24 - tw_logB))]);
-            const float2 w = make_float2(c.x * f.x - c.y * f.y, c.x * f.y + c.y * f.x);
-            v = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
+    const uint32_t bmask = tw_logB >= 0 ? (uint32_t)((1 << tw_logB) - 1) : 0u;
+    float emx = 0.f;
+    if (out_es == 1 || T == 1) {
+        for (int idx = threadIdx.x; idx < TP; idx += blockDim.x) {
+            const int u = idx >> logP, k = idx & (P - 1);
+            float2 v = sm[padi(idx)];
+            if (tw_logB >= 0) {
+                const float2 w = four_step_twiddle((uint32_t)((t0 + u) * k) & bmask, tw_logB, tw);
+                v = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
+            }
+            const int o = u * out_bs + k;
+            dst[o] = v;
+            if (edst) {
+                const float e = fmaf(v.x, v.x, v.y * v.y);
+                edst[o] = e;
+                emx = fmaxf(emx, e);
+            }
         }
-        const int64_t o = (int64_t)u * out_bs + (int64_t)k * out_es;
-        dst[o] = v;
-        if (edst) {
-            const float e = fmaf(v.x, v.x, v.y * v.y);
-            edst[o] = e;
-            m = fmaxf(m, e);
+    } else {
+        for (int k = threadIdx.x; k < P; k += blockDim.x) {
+            float4 *q = reinterpret_cast<float4 *>(dst + k * out_es);
+            float *eo = edst ? edst + k * out_es : nullptr;
+            // two transforms at a time: one 16-byte store
+#pragma unroll 1
+            for (int u = 0; u < T; u += 2) {
+                float2 a = sm[padi((u << logP) + k)], c = sm[padi(((u + 1) << logP) + k)];
+                if (tw_logB >= 0) {
+                    const float2 wa = four_step_twiddle((uint32_t)((t0 + u) * k) & bmask, tw_logB, tw);
+                    const float2 wc = four_step_twiddle((uint32_t)((t0 + u + 1) * k) & bmask, tw_logB, tw);
+                    a = make_float2(a.x * wa.x - a.y * wa.y, a.x * wa.y + a.y * wa.x);
+                    c = make_float2(c.x * wc.x - c.y * wc.y, c.x * wc.y + c.y * wc.x);
+                }
+                q[u >> 1] = make_float4(a.x, a.y, c.x, c.y);
+                if (eo) {
+                    const float ea = fmaf(a.x, a.x, a.y * a.y), ec = fmaf(c.x, c.x, c.y * c.y);
+                    eo[u] = ea;
+                    eo[u + 1] = ec;
+                    emx = fmaxf(emx, fmaxf(ea, ec));
+                }
+            }
         }
     }
     if (emax) {
         // block maximum of the energies, one atomic per tile (E >= 0: bit order = order)
-        __shared__ float wmax[kSmallFFT / 256];
+        __shared__ float wmax[32];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+        for (int off = 16; off > 0; off >>= 1) emx = fmaxf(emx, __shfl_xor_sync(0xffffffffu, emx, off));
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = emx;
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = fmaxf(m, wmax[w]);
-            if (m > 0.f) atomicMax(emax, __float_as_uint(m));
+            for (int w = 1; w < (int)(blockDim.x >> 5); w++) emx = fmaxf(emx, wmax[w]);
+            if (emx > 0.f) atomicMax(emax, __float_as_uint(emx));
         }
     }
     __syncthreads();
@@ -232,7 +287,7 @@ __device__ __forceinline__ int tile_of(const FftShape &f)
 {
     if (f.in_es == 1 && f.out_es == 1) return 1;
     int T = kSmallFFT >> f.logP;
-    if (T > 16) T = 16;
+    if (T > kMaxTile) T = kMaxTile;
     if (T > f.ntrans) T = f.ntrans;
     return T;
 }
@@ -277,7 +332,8 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_fft_pass(int ndim, int pass,
         const int64_t h = tr / tiles, t = (tr % tiles) * T;
         const bool e = fin_pass && h < n_energy;
         fft_tile(in + h * in_hash + t * f.in_bs, f.in_es, f.in_bs, chunks, f.hash_stride,
-                 out + h * f.hash_stride + t * f.out_bs, f.out_es, f.out_bs, f.logP, T, f.tw_logB,
+                 out + h * f.hash_stride + t * f.out_bs, f.out_es, f.out_bs, f.logP, __ffs(T) - 1,
+                 f.tw_logB,
                  t, sm, tw, e ? energy + h * f.hash_stride + t * f.out_bs : nullptr,
                  e ? &stats[kMaxLogB + h].max_bits : nullptr);
     }
@@ -320,7 +376,7 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_fft_batch(int ndim, int pass
         const int chunks = pass == 0 ? J.chunks : 1;
         const bool e = energy && final_pass(ndim, J.logB, pass);
         fft_tile(in + t * f.in_bs, f.in_es, f.in_bs, chunks, f.hash_stride, out + t * f.out_bs,
-                 f.out_es, f.out_bs, f.logP, T, f.tw_logB, t, sm, tw,
+                 f.out_es, f.out_bs, f.logP, __ffs(T) - 1, f.tw_logB, t, sm, tw,
                  e ? energy + J.out_off + t * f.out_bs : nullptr,
                  e ? &stats[J.logB].max_bits : nullptr);
     }
@@ -377,7 +433,7 @@ void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB,
             int64_t T = 1;
             if (strided) {
                 T = (int64_t)kSmallFFT >> logP;
-                if (T > 16) T = 16;
+                if (T > kMaxTile) T = kMaxTile;
                 if (T > ntrans) T = ntrans;
                 const int64_t ch = pass == 0 ? chunks[i] : 1;
                 while (T > 4 && (T << logP) * ch > kTileLoads) T >>= 1;
