@@ -55,9 +55,7 @@ def _peaks():
 
 # DRAM bytes of one launch of a phase's kernel, from one ncu capture of the current
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum); None once the kernel changes.
-NCU_TRAFFIC = {
-    "loc_tail": (8788992, "k=1000 launch (B*=2^16), ncu --set full, bench.py --ncu-case 1000"),
-}
+NCU_TRAFFIC = {}
 
 
 def _signals():
@@ -236,42 +234,52 @@ def _stream(n, B):
 
 
 def roofline(per_signal, traces, n):
+    """Algorithmic work of each profiled phase per launch, achieved rate, fraction of peak.
+
+    Bytes (HBM-bound phases) count each input and output value once; pairs (the
+    residue-stream binning, bound by its two MUFU operations per (sample, hash) pair)
+    count samples x hashes.  The two tuning stages split the trials at the last one
+    binned in the gather form; the second stage only counts for transforms whose
+    controller walked past that trial (it exits at once otherwise)."""
     peaks, src = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     pair_peak = SFU_PER_SM_CLK * SMS * SM_MAX_MHZ * 1e6 / 2.0   # 2 SFU ops per pair
     logn = n.bit_length() - 1
     Bs = [1 << b for b in range(4, logn - 4 + 1)]
+    gB = [B for B in Bs if not _stream(n, B)]
+    sB = [B for B in Bs if _stream(n, B)]
+    split = max(gB) if gB else 0
+
+    def fft_bytes(B, chunks):
+        return 8 * B * chunks + 8 * B + 4 * B + (16 * B if B > 4096 else 0)
+
     rows = {}
     for k, ph in per_signal.items():
         Bstar = traces[k][-1][0]
-        D = n // Bstar
+        stage2 = max(b for b, _ in traces[k]) > split
         model = {}
-        gB = [B for B in Bs if not _stream(n, B)]
-        sB = [B for B in Bs if _stream(n, B)]
-        model["tune_gather"] = ("hbm", sum(8 * (2 * _window_h(n, B) + 1) + 8 * B for B in gB))
-        if sB:
+        model["tune1_bin"] = ("hbm", sum(8 * (2 * _window_h(n, B) + 1) + 8 * B for B in gB))
+        model["tune1_fft"] = ("hbm", sum(fft_bytes(B, 1) for B in gB))
+        model["tune1_tail"] = ("hbm", sum(4 * B + 4 * B for B in gB))
+        if sB and stage2:
             R = max(sB)
-            model["tune_stream"] = ("alu", len(sB) * n)
-        model["tune_fft"] = ("hbm", sum(8 * B * (_chunks(n, max(sB)) * max(sB) // B if B in sB else 1)
-                                        + 8 * B + (16 * B if B > 4096 else 0) for B in Bs))
-        model["tune_tail"] = ("hbm", sum(8 * B + 4 * B + 12 * B for B in Bs))
+            model["tune2_bin"] = ("alu", len(sB) * n)
+            model["tune2_fft"] = ("hbm", sum(fft_bytes(B, _chunks(n, R) * R // B) for B in sB))
+            model["tune2_tail"] = ("hbm", sum(4 * B + 4 * B for B in sB))
         if _stream(n, Bstar):
             model["le_bin_stream"] = ("alu", NH * n)
         else:
             model["le_bin_gather"] = ("hbm", NH * 8 * (2 * _window_h(n, Bstar) + 1) + 8 * NH * Bstar)
         ch = _chunks(n, Bstar) if _stream(n, Bstar) else 1
-        model["le_fft"] = ("hbm", 8 * NH * Bstar * (ch + 1) + (16 * NH * Bstar if Bstar > 4096 else 0))
-        model["loc_tail"] = ("hbm", L_LOC * Bstar * (8 + 4 + 12) + 3 * n)
+        model["le_fft"] = ("hbm", sum(fft_bytes(Bstar, ch) for _ in range(NH)))
+        model["loc_tail"] = ("hbm", L_LOC * Bstar * (4 + 4))
         for nm, (bound, units) in model.items():
             t = ph[nm] / 1e3
             if t <= 0:
                 continue
-            if bound == "alu":
-                ach = units / t / 1e9
-                rows.setdefault(nm, []).append((t, ach, ach / (pair_peak / 1e9), units, bound))
-            else:
-                ach = units / t / 1e9
-                rows.setdefault(nm, []).append((t, ach, ach / hbm, units, bound))
+            ach = units / t / 1e9
+            frac = ach / (pair_peak / 1e9) if bound == "alu" else ach / hbm
+            rows.setdefault(nm, []).append((t, ach, frac, units, bound))
     out = {}
     for nm, lst in rows.items():
         t = float(np.mean([r[0] for r in lst]))
@@ -320,7 +328,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--phases", action="store_true", help="print per-phase times to stderr")
     ap.add_argument("--streams", type=int, default=4,
-                    help="run the step's transforms on this many CUDA streams (1 = in order)")
+                    help="without --no-graph: ignored; with it, run the step's transforms on "
+                         "this many CUDA streams (1 = in order)")
+    ap.add_argument("--tune-stages", type=int, default=2, choices=[1, 2],
+                    help="1D tuning in one batch (1) or small-window trials first (2)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time per-signal execs on streams instead of one graph launch per step")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="K",
                     help="profiling case for ncu: one plan, the k=K signal, three transforms")
     args = ap.parse_args()
@@ -348,10 +361,12 @@ def main():
     host = [torch.from_numpy(s.x).pin_memory() for s in sigs]
     xs = [h.to(dev) for h in host]
     nstreams = max(1, min(args.streams, len(sigs)))
-    pp = A.params(coop_blocks_per_sm=1) if nstreams > 1 else None
+    use_graph = not args.no_graph
+    # concurrent transforms (graph branches or streams): tails at one CTA per SM so that
+    # several cooperative grids are resident together
+    pp = A.params(coop_blocks_per_sm=1 if (nstreams > 1 or use_graph) else 0,
+                  tune_stages=args.tune_stages)
     plans = [A.Plan((n,), params=pp, seed=SEED) for _ in sigs]
-    for p in plans:
-        p.set_profiling(True)
     outs = []
     for _ in sigs:
         outs.append(dict(loc=torch.empty(CAPACITY, dtype=torch.int64, device=dev),
@@ -362,8 +377,16 @@ def main():
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     side = [stream] + [torch.cuda.Stream(device=dev) for _ in range(nstreams - 1)]
+    batch = None
+    if use_graph:
+        # the step's transforms as one CUDA graph with a branch per signal
+        batch = A.Batch([(p, x, o["loc"], o["val"], o["count"], o["k"], o["status"])
+                         for p, x, o in zip(plans, xs, outs)])
 
     def step():
+        if batch is not None:
+            batch.launch(stream.cuda_stream)
+            return
         # transforms on `nstreams` streams, joined back into the timing stream
         if nstreams == 1:
             for p, x, o in zip(plans, xs, outs):
@@ -427,8 +450,7 @@ def main():
             ev1.record(stream)
             ev1.synchronize()
             step_ms.append(ev0.elapsed_time(ev1))
-            for p in plans:
-                launches += p.phase_times()[1]
+            launches += batch.kernels() if batch is not None else sum(p.phase_times()[1] for p in plans)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if ws > 1:
@@ -449,6 +471,8 @@ def main():
         rows = phase_acc[i::len(KS)]
         per_signal[k] = {nm: float(np.mean([r[nm] for r in rows])) for nm in names}
     bin_ms = {k: per_signal[k]["le_bin_stream"] + per_signal[k]["le_bin_gather"] for k in KS}
+    tune_stage2 = {k: per_signal[k]["tune2_bin"] + per_signal[k]["tune2_fft"] + per_signal[k]["tune2_tail"]
+                   for k in KS}
     traces = {k: p.last_trace() for k, p in zip(KS, plans)}
     roof, phase_rooflines = roofline(per_signal, traces, n)
 
@@ -503,6 +527,8 @@ def main():
             if stamp_acc:
                 print("tail stamps us k=%d:" % k, [round(v, 1) for v in stamp_acc[-len(KS) + i]],
                       file=sys.stderr)
+    if batch is not None:
+        batch.close()
     for p in plans:
         p.close()
     if ws > 1:
@@ -520,11 +546,14 @@ def main():
                    "plain_path_transforms_per_s": plain_value,
                    "plain_path_ms_per_step": float(np.mean(plain_ms)),
                    "k_star": kstar, "counts": counts, "status": status,
-                   "path": ("plain per-signal path (one exec per transform)" if nstreams == 1 else
+                   "tune_stages": args.tune_stages,
+                   "path": ("one CUDA graph per step (atsfft_batch_launch), a branch per signal"
+                            if use_graph else
+                            "plain per-signal path (one exec per transform)" if nstreams == 1 else
                             f"per-signal execs on {nstreams} concurrent streams"),
                    "cufft_c2c_ms": cufft_ms,
                    "cufft_c2c_transforms_per_s": (1e3 / cufft_ms) if cufft_ms else None,
-                   "bin_pass_ms": bin_ms, "wall_s": wall},
+                   "bin_pass_ms": bin_ms, "tune_stage2_ms": tune_stage2, "wall_s": wall},
         "e2e": {"value": ntrans / (e2e_total / 1e3), "unit": "transforms/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,

@@ -62,6 +62,10 @@ typedef struct {
     int coop_blocks_per_sm;     /* blocks per SM of the two cooperative tail kernels
                                    (0 = 2); 1 lets several plans' tails run at once on
                                    different streams, all co-resident                   */
+    int tune_stages;            /* 1D tuning batches: 2 (default) evaluates the trials with
+                                   gather-form windows first and the residue-stream trials
+                                   only if the controller has not stopped; 1 evaluates
+                                   every trial in one batch.  Same results either way     */
 } atsfft_params;
 
 /* Fills *p with the defaults listed above. */
@@ -122,14 +126,16 @@ atsfft_status atsfft_window_response(atsfft_plan_t plan, int64_t B, double *h_re
 atsfft_status atsfft_last_trace(atsfft_plan_t plan, int64_t *h_B, int64_t *h_k, int max_trials,
                                 int *h_ntrials, void *stream);
 
-/* Turns per-phase CUDA events on (1) or off (0) for later execs of this plan.  The
- * eight phases of one exec, in order: 0 tuning binning in the gather form (1D; 2D: the
- * whole tuning binning), 1 tuning binning in the residue-stream form (1D), 2 tuning
- * bucket FFTs, 3 tuning statistics and controller, 4 binning of the location/estimation
- * hashes in the residue-stream form (1D; 2D: tap tables + stream form), 5 the same in
- * the gather form, 6 their bucket FFTs, 7 location statistics, top-num cutoff, votes,
- * compaction, estimation and median.  A form or shape that does not apply exits at once,
- * so its phase measures only an empty launch. */
+/* Turns per-phase CUDA events on (1) or off (0) for later execs of this plan.  The ten
+ * phases of one exec, in order: 0 binning of the first tuning stage (1D: the trials with
+ * gather-form windows; 2D: every trial), 1 their bucket FFTs, 2 their statistics and the
+ * controller, 3 binning of the second tuning stage (1D: the residue-stream trials, run
+ * only when the controller did not stop within the first stage), 4 its bucket FFTs,
+ * 5 its statistics and the controller, 6 binning of the location/estimation hashes in
+ * the residue-stream form (1D; 2D: tap tables + stream form), 7 the same in the gather
+ * form, 8 their bucket FFTs, 9 location statistics, top-num cutoff, votes, ordering,
+ * estimation and median.  A form, shape or stage that does not apply exits at once (or
+ * is not launched), so its phase measures only an empty launch or nothing. */
 atsfft_status atsfft_set_profiling(atsfft_plan_t plan, int on);
 
 /* After an exec: per-phase device times in ms (h_ms[max_phases], read only if profiling
@@ -143,6 +149,33 @@ atsfft_status atsfft_phase_times(atsfft_plan_t plan, float *h_ms, int max_phases
  * order they happened (at most 32).  Synchronises `stream`. */
 atsfft_status atsfft_tail_stamps(atsfft_plan_t plan, uint64_t *h_ns, int max_stamps,
                                  int *h_nstamps, void *stream);
+
+/* ---- batched execution in one CUDA graph ----------------------------------------- */
+
+typedef struct atsfft_batch_s *atsfft_batch_t;
+
+/* Records the transforms of n distinct plans -- plan i on input d_x[i] with outputs
+ * d_loc[i], d_val[i], capacity[i], d_count[i], d_k[i], d_status[i], exactly as
+ * atsfft_exec (1D plans) or atsfft_exec_2d (2D plans) take them -- into one CUDA graph
+ * whose n branches run concurrently, and instantiates it on the current device.  Nothing
+ * runs yet.  The pointers are fixed in the graph: the buffers must stay allocated and
+ * are re-read on every launch.  Profiling must be off on every plan.  A plan may appear
+ * at most once (each branch uses its plan's scratch).  On error *out is NULL. */
+atsfft_status atsfft_batch_create(int n, const atsfft_plan_t *plans, const void *const *d_x,
+                                  int64_t *const *d_loc, void *const *d_val,
+                                  const int64_t *capacity, int64_t *const *d_count,
+                                  int64_t *const *d_k, int32_t *const *d_status,
+                                  atsfft_batch_t *out);
+
+/* Runs the n transforms of the batch on `stream` (one graph launch; asynchronous).  The
+ * outputs of each branch are those of the corresponding plain exec. */
+atsfft_status atsfft_batch_launch(atsfft_batch_t batch, void *stream);
+
+/* Kernel launches one batch launch makes (the sum over its branches). */
+atsfft_status atsfft_batch_kernels(atsfft_batch_t batch, int64_t *h_kernels);
+
+/* Frees the graph.  The plans stay valid. */
+atsfft_status atsfft_batch_destroy(atsfft_batch_t batch);
 
 /* ---- allocation-free variant ---------------------------------------------------- */
 

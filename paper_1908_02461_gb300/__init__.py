@@ -18,6 +18,10 @@ from ._lib import (  # noqa: F401
     E_NOT_CONVERGED,
     E_NOT_SPARSE,
     OK,
+    atsfft_batch_create,
+    atsfft_batch_destroy,
+    atsfft_batch_kernels,
+    atsfft_batch_launch,
     atsfft_default_params,
     atsfft_destroy,
     atsfft_exec,
@@ -166,3 +170,47 @@ class Plan:
         if st != OK:
             raise ATSFFTError(st, "atsfft_last_trace")
         return list(zip(Bs[:nt].tolist(), ks[:nt].tolist()))
+
+
+class Batch:
+    """Several plans' transforms recorded into one CUDA graph (atsfft_batch_create).
+
+    `items` is a sequence of (plan, x, loc, val, count, k, status) with device tensors
+    that must stay alive and in place; `launch()` replays all transforms at once."""
+
+    def __init__(self, items):
+        import torch
+
+        self._keep = list(items)   # the graph holds raw pointers into these tensors
+        plans = [it[0].handle for it in items]
+        st, h = atsfft_batch_create(plans, [it[1] for it in items], [it[2] for it in items],
+                                    [it[3] for it in items], [it[2].numel() for it in items],
+                                    [it[4] for it in items], [it[5] for it in items],
+                                    [it[6] for it in items])
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_batch_create")
+        self.handle = h
+        self._torch = torch
+
+    def launch(self, stream=None):
+        s = stream if stream is not None else self._torch.cuda.current_stream().cuda_stream
+        st = atsfft_batch_launch(self.handle, s)
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_batch_launch")
+
+    def kernels(self) -> int:
+        st, k = atsfft_batch_kernels(self.handle)
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_batch_kernels")
+        return k
+
+    def close(self):
+        if getattr(self, "handle", None):
+            atsfft_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -30,16 +30,19 @@ class atsfft_params(C.Structure):
         ("thr_rel", C.c_double), ("thr_med", C.c_double), ("tie_eta", C.c_double),
         ("b_min_log2", C.c_int), ("b_max_log2", C.c_int),
         ("coop_blocks_per_sm", C.c_int),
+        ("tune_stages", C.c_int),
     ]
 
 
 EXPORTED = ["atsfft_default_params", "atsfft_plan", "atsfft_exec", "atsfft_exec_2d",
             "atsfft_destroy", "atsfft_status_string", "atsfft_hash_spectrum",
             "atsfft_window_response", "atsfft_last_trace", "atsfft_set_profiling",
-            "atsfft_phase_times", "atsfft_tail_stamps", "atsfft_hash_spectrum_noalloc"]
+            "atsfft_phase_times", "atsfft_tail_stamps", "atsfft_hash_spectrum_noalloc",
+            "atsfft_batch_create", "atsfft_batch_launch", "atsfft_batch_kernels",
+            "atsfft_batch_destroy"]
 
-PHASES = ["tune_gather", "tune_stream", "tune_fft", "tune_tail", "le_bin_stream", "le_bin_gather",
-          "le_fft", "loc_tail"]
+PHASES = ["tune1_bin", "tune1_fft", "tune1_tail", "tune2_bin", "tune2_fft", "tune2_tail",
+          "le_bin_stream", "le_bin_gather", "le_fft", "loc_tail"]
 
 _lib = None
 
@@ -81,6 +84,14 @@ def load(path: str | None = None):
     L.atsfft_tail_stamps.restype = i32
     L.atsfft_hash_spectrum_noalloc.argtypes = [vp, i64, i64, u64, i32, i32, vp, vp]
     L.atsfft_hash_spectrum_noalloc.restype = i32
+    L.atsfft_batch_create.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, P(vp)]
+    L.atsfft_batch_create.restype = i32
+    L.atsfft_batch_launch.argtypes = [vp, vp]
+    L.atsfft_batch_launch.restype = i32
+    L.atsfft_batch_kernels.argtypes = [vp, P(i64)]
+    L.atsfft_batch_kernels.restype = i32
+    L.atsfft_batch_destroy.argtypes = [vp]
+    L.atsfft_batch_destroy.restype = i32
     if path is None:
         _lib = L
     return L
@@ -172,3 +183,29 @@ def atsfft_hash_spectrum_noalloc(d_x, n, B, seed, phase, index, d_zhat, stream=N
     """One hash's bucket spectrum without a plan or any allocation (see include/atsfft.h)."""
     return load().atsfft_hash_spectrum_noalloc(_ptr(d_x), n, B, seed & 0xFFFFFFFFFFFFFFFF, phase,
                                                index, _ptr(d_zhat), _ptr(stream))
+
+
+def atsfft_batch_create(plans, d_x, d_loc, d_val, capacity, d_count, d_k, d_status):
+    """Returns (status, batch handle).  Every argument is a sequence of equal length."""
+    n = len(plans)
+    arr = lambda xs: (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    h = C.c_void_p()
+    st = load().atsfft_batch_create(n, (C.c_void_p * n)(*plans), arr(d_x), arr(d_loc), arr(d_val),
+                                    (C.c_int64 * n)(*capacity), arr(d_count), arr(d_k),
+                                    arr(d_status), C.byref(h))
+    return st, h.value
+
+
+def atsfft_batch_launch(batch, stream=None) -> int:
+    return load().atsfft_batch_launch(batch, _ptr(stream))
+
+
+def atsfft_batch_kernels(batch):
+    """Returns (status, kernel launches per batch launch)."""
+    k = C.c_int64()
+    st = load().atsfft_batch_kernels(batch, C.byref(k))
+    return st, k.value
+
+
+def atsfft_batch_destroy(batch) -> int:
+    return load().atsfft_batch_destroy(batch)

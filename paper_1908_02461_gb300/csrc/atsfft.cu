@@ -4,15 +4,19 @@
 //  tuning   : the hash of every B in the plan's range is evaluated (bin, bucket FFT,
 //             energies, threshold, local-maximum count); the controller then walks
 //             Eqs. (12)/(14) over those counts on the device and fixes B*, k*.  Because the
-//             stop reading visits every B at most once, evaluating all of them up front
-//             gives exactly the sequential trajectory while replacing a chain of dependent
-//             trials by one batch.
+//             stop reading visits every B at most once, evaluating them up front gives
+//             exactly the sequential trajectory while replacing a chain of dependent
+//             trials by a batch.  1D runs two batches: the small-window trials, then --
+//             only if the walk has not stopped among them (a device flag every kernel of
+//             the second batch reads) -- the residue-stream trials.
 //  location : the L_loc + L_est hashes at B* are binned in one pass over the signal,
 //             transformed, and the location hashes' maxima are cut to k* and vote.
 //  estimate : kept coordinates in ascending order, Eq. (11), median.
 // Kernels that depend on B* read it from device memory; every shape they could need is
 // launched and the ones that do not match exit at once.
+#include <new>
 #include <string.h>
+#include <vector>
 
 #include "common.cuh"
 
@@ -31,17 +35,21 @@ static atsfft_status exec_common(atsfft_plan_t P, int ndim, const void *d_x, int
     P->launches = 0;
     launch_reset(P, s);
     prof_mark(P, 0, s);
-    launch_tuning(P, x, s);       // marks phases 1 and 2 between its kernels
+    launch_tuning(P, x, 1, s);    // marks phase 1 between its binning and its FFTs
+    prof_mark(P, 2, s);
+    launch_tune_tail(P, 1, s);
     prof_mark(P, 3, s);
-    launch_tune_tail(P, s);
-    prof_mark(P, 4, s);
-    const Job *jd = &P->d_state->job;
-    launch_le_bin(P, x, jd, s);   // marks phase 5 after the stream-form kernel
+    launch_tuning(P, x, 2, s);    // marks phase 4
+    prof_mark(P, 5, s);
+    launch_tune_tail(P, 2, s);
     prof_mark(P, 6, s);
-    launch_bucket_fft_dynamic(P, jd, P->d_part, P->d_z, P->d_energy + P->e_loc_off, P->L_loc, s);
-    prof_mark(P, 7, s);
-    launch_loc_tail(P, d_loc, (float2 *)d_val, capacity, d_count, d_k, d_status, s);
+    const Job *jd = &P->d_state->job;
+    launch_le_bin(P, x, jd, s);   // marks phase 7 after the stream-form kernel
     prof_mark(P, 8, s);
+    launch_bucket_fft_dynamic(P, jd, P->d_part, P->d_z, P->d_energy + P->e_loc_off, P->L_loc, s);
+    prof_mark(P, 9, s);
+    launch_loc_tail(P, d_loc, (float2 *)d_val, capacity, d_count, d_k, d_status, s);
+    prof_mark(P, 10, s);
     return cuda_status(cudaGetLastError());
 }
 
@@ -146,5 +154,110 @@ extern "C" atsfft_status atsfft_tail_stamps(atsfft_plan_t P, uint64_t *h_ns, int
     const int n = gb.nstamp < 32 ? (int)gb.nstamp : 32;
     *h_nstamps = n;
     for (int i = 0; i < n && i < max_stamps; i++) h_ns[i] = gb.stamp[i];
+    return ATSFFT_OK;
+}
+
+// ---- batched execution: one graph with a branch per plan --------------------------
+
+struct atsfft_batch_s {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    int64_t kernels;
+};
+
+extern "C" atsfft_status atsfft_batch_create(int n, const atsfft_plan_t *plans,
+                                             const void *const *d_x, int64_t *const *d_loc,
+                                             void *const *d_val, const int64_t *capacity,
+                                             int64_t *const *d_count, int64_t *const *d_k,
+                                             int32_t *const *d_status, atsfft_batch_t *out)
+{
+    if (!out) return ATSFFT_E_INVALID_ARG;
+    *out = nullptr;
+    if (n <= 0 || !plans || !d_x || !d_loc || !d_val || !capacity || !d_count || !d_k || !d_status)
+        return ATSFFT_E_INVALID_ARG;
+    for (int i = 0; i < n; i++) {
+        if (!plans[i] || plans[i]->prof) return ATSFFT_E_INVALID_ARG;
+        for (int j = 0; j < i; j++)
+            if (plans[j] == plans[i]) return ATSFFT_E_INVALID_ARG;
+    }
+    atsfft_batch_s *B = new (std::nothrow) atsfft_batch_s;
+    if (!B) return ATSFFT_E_NOMEM;
+    memset(B, 0, sizeof(*B));
+    // capture: fork from `main` to one stream per plan, each runs its exec, join back
+    cudaStream_t main = nullptr;
+    std::vector<cudaStream_t> side(n, nullptr);
+    std::vector<cudaEvent_t> done(n, nullptr);
+    cudaEvent_t fork = nullptr;
+    atsfft_status st = ATSFFT_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&main, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; i++) {
+        e = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
+    }
+    bool capturing = false;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(main, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        capturing = true;
+        e = cudaEventRecord(fork, main);
+    }
+    for (int i = 0; i < n && e == cudaSuccess && st == ATSFFT_OK; i++) {
+        e = cudaStreamWaitEvent(side[i], fork, 0);
+        if (e != cudaSuccess) break;
+        atsfft_plan_s *P = plans[i];
+        st = exec_common(P, P->ndim, d_x[i], d_loc[i], d_val[i], capacity[i], d_count[i], d_k[i],
+                         d_status[i], side[i]);
+        B->kernels += P->launches;
+        if (st == ATSFFT_OK) e = cudaEventRecord(done[i], side[i]);
+        if (e == cudaSuccess && st == ATSFFT_OK) e = cudaStreamWaitEvent(main, done[i], 0);
+    }
+    if (capturing) {
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(main, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess && st == ATSFFT_OK) {
+            B->graph = g;
+            e = cudaGraphInstantiate(&B->exec, g, 0);
+        } else if (g) {
+            cudaGraphDestroy(g);
+        }
+    }
+    for (int i = 0; i < n; i++) {
+        if (done[i]) cudaEventDestroy(done[i]);
+        if (side[i]) cudaStreamDestroy(side[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+    if (main) cudaStreamDestroy(main);
+    if (st == ATSFFT_OK && e != cudaSuccess) st = cuda_status(e);
+    if (st != ATSFFT_OK) {
+        if (B->exec) cudaGraphExecDestroy(B->exec);
+        if (B->graph) cudaGraphDestroy(B->graph);
+        delete B;
+        cudaGetLastError();
+        return st;
+    }
+    *out = B;
+    return ATSFFT_OK;
+}
+
+extern "C" atsfft_status atsfft_batch_launch(atsfft_batch_t B, void *stream)
+{
+    if (!B || !B->exec) return ATSFFT_E_INVALID_ARG;
+    return cuda_status(cudaGraphLaunch(B->exec, (cudaStream_t)stream));
+}
+
+extern "C" atsfft_status atsfft_batch_kernels(atsfft_batch_t B, int64_t *h_kernels)
+{
+    if (!B || !h_kernels) return ATSFFT_E_INVALID_ARG;
+    *h_kernels = B->kernels;
+    return ATSFFT_OK;
+}
+
+extern "C" atsfft_status atsfft_batch_destroy(atsfft_batch_t B)
+{
+    if (!B) return ATSFFT_E_INVALID_ARG;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    delete B;
     return ATSFFT_OK;
 }

@@ -195,9 +195,10 @@ template <int NH, bool DYN>
 __global__ void __launch_bounds__(256) k_bin_stream(const float2 *__restrict__ x, int logn,
                                                     const StreamArgs A, const Job *job_dev,
                                                     const WindowParam *win,
-                                                    float2 *__restrict__ part)
+                                                    float2 *__restrict__ part, const int *skip)
 {
     extern __shared__ float2 rot[];
+    if (skip && *skip) return;
     int logR = A.logR, chunks = A.chunks;
     WindowParam w = {};
     if (DYN) {
@@ -562,7 +563,8 @@ static int occupancy_grid(const atsfft_plan_s *P, const void *fn, size_t smem)
 
 template <int NH, bool DYN>
 static void launch_stream(const atsfft_plan_s *P, const float2 *x, const StreamArgs &A,
-                          const Job *job_dev, size_t smem, int64_t items_hint, cudaStream_t s)
+                          const Job *job_dev, size_t smem, int64_t items_hint, const int *skip,
+                          cudaStream_t s)
 {
     const void *fn = (const void *)k_bin_stream<NH, DYN>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -570,15 +572,16 @@ static void launch_stream(const atsfft_plan_s *P, const float2 *x, const StreamA
     const int64_t need = (items_hint + 255) / 256;
     if (items_hint > 0 && need < grid) grid = need;
     k_bin_stream<NH, DYN><<<(unsigned)grid, 256, smem, s>>>(x, P->logn, A, job_dev, P->d_win,
-                                                            P->d_part);
+                                                            P->d_part, skip);
     count_launch(P);
 }
 
 template <bool DYN>
 static void launch_stream_nh(const atsfft_plan_s *P, const float2 *x, const StreamArgs &A,
-                             const Job *job_dev, size_t smem, int64_t items_hint, cudaStream_t s)
+                             const Job *job_dev, size_t smem, int64_t items_hint, cudaStream_t s,
+                             const int *skip = nullptr)
 {
-#define ATSFFT_NH(k) case k: launch_stream<k, DYN>(P, x, A, job_dev, smem, items_hint, s); break;
+#define ATSFFT_NH(k) case k: launch_stream<k, DYN>(P, x, A, job_dev, smem, items_hint, skip, s); break;
     switch (A.nh) {
     ATSFFT_NH(1) ATSFFT_NH(2) ATSFFT_NH(3) ATSFFT_NH(4) ATSFFT_NH(5) ATSFFT_NH(6) ATSFFT_NH(7)
     ATSFFT_NH(8) ATSFFT_NH(9) ATSFFT_NH(10) ATSFFT_NH(11) ATSFFT_NH(12) ATSFFT_NH(13)
@@ -588,21 +591,30 @@ static void launch_stream_nh(const atsfft_plan_s *P, const float2 *x, const Stre
 #undef ATSFFT_NH
 }
 
-// Tuning: every B of the range, one hash each.  1D: the small-window hashes in one
-// gather launch, the large-window ones in one residue-stream pass with R = the largest
-// of their B; 2D: one launch per B.  Then all bucket FFTs in one batch.
-void launch_tuning(const atsfft_plan_s *P, const float2 *x, cudaStream_t s)
+// Tuning: every B of the range, one hash each, in two stages.  1D stage 1: the
+// small-window trials (b <= tune_split) in one gather launch; stage 2: the large-window
+// ones in one residue-stream pass with R = the largest of their B, every kernel of it
+// returning at once when stage 1 already settled the controller.  2D: one stage, one
+// launch per B.  Each stage ends with the bucket FFTs of its trials in one batch.
+void launch_tuning(const atsfft_plan_s *P, const float2 *x, int stage, cudaStream_t s)
 {
     int logB[kMaxLogB], chunks[kMaxLogB], nj = 0;
     int64_t in_off[kMaxLogB], out_off[kMaxLogB];
+    const int *skip = nullptr;
     if (P->ndim == 1) {
+        const int lo = stage == 1 ? P->b0 : P->tune_split + 1;
+        const int hi = stage == 1 ? P->tune_split : P->b_hi;
+        if (lo > hi) {
+            prof_mark(P, stage == 1 ? 1 : 4, s);
+            return;
+        }
         GatherArgs G;
         G.njobs = 0;
         G.total_warps = 0;
         StreamArgs S;
         memset(&S, 0, sizeof(S));
         int rot_total = 0;
-        for (int b = P->b0; b <= P->b_hi; b++) {
+        for (int b = lo; b <= hi; b++) {
             if (P->h_tjob[b].stream) {
                 StreamHash &h = S.h[S.nh++];
                 h = stream_hash(P, P->h_tune[b], b, P->tpart_off[b]);
@@ -627,16 +639,18 @@ void launch_tuning(const atsfft_plan_s *P, const float2 *x, cudaStream_t s)
                                                                                      P->d_part);
             count_launch(P);
         }
-        prof_mark(P, 1, s);
         if (S.nh) {
             S.logR = P->tstream_logR;
             S.chunks = P->tstream_chunks;
+            if (stage == 2) skip = &P->d_state->tune_done;
             launch_stream_nh<false>(P, x, S, nullptr, sizeof(float2) * rot_total,
-                                    ((int64_t)1 << S.logR) * S.chunks, s);
+                                    ((int64_t)1 << S.logR) * S.chunks, s, skip);
         }
-        prof_mark(P, 2, s);
     } else {
-        prof_mark(P, 1, s);
+        if (stage != 1) {
+            prof_mark(P, 4, s);
+            return;
+        }
         for (int b = P->b0; b <= P->b_hi; b++) {
             launch_bin_2d(P, x, nullptr, P->h_tjob[b], false, P->d_tune + b, b,
                           P->d_part + P->tpart_off[b], s);
@@ -646,10 +660,10 @@ void launch_tuning(const atsfft_plan_s *P, const float2 *x, cudaStream_t s)
             out_off[nj] = P->tz_off[b];
             nj++;
         }
-        prof_mark(P, 2, s);
     }
+    prof_mark(P, stage == 1 ? 1 : 4, s);
     launch_bucket_fft_batch(P, nj, logB, chunks, in_off, out_off, P->d_part, P->d_tz, P->d_energy,
-                            s);
+                            skip, s);
 }
 
 // Location + estimation hashes at the device-chosen B*: every form is launched, the
@@ -673,7 +687,7 @@ void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
             for (int g = 0; g < S.nh; g++) S.h[g] = stream_hash(P, P->h_le[g0 + g], -1, 0);
             launch_stream_nh<true>(P, x, S, job_dev, smem, 0, s);
         }
-        prof_mark(P, 5, s);
+        prof_mark(P, 7, s);
         const int groups = (nh + kGroup - 1) / kGroup;
         dim3 grid(P->num_sms * kPersistCtas, groups);
         k_bin_gather_1d<<<grid, 256, 0, s>>>(x, P->logn, P->d_le, nh, P->d_win, job_dev, 0,
@@ -719,7 +733,7 @@ void launch_single_hash(const atsfft_plan_s *P, const float2 *x, int b, const Ha
         launch_bin_2d(P, x, nullptr, j, false, hp_dev, b, P->d_part, s);
     }
     const int64_t zero = 0;
-    launch_bucket_fft_batch(P, 1, &b, &chunks, &zero, &zero, P->d_part, out, nullptr, s);
+    launch_bucket_fft_batch(P, 1, &b, &chunks, &zero, &zero, P->d_part, out, nullptr, nullptr, s);
 }
 
 void launch_bin_2d(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, const Job &job_host,
@@ -739,7 +753,7 @@ void launch_bin_2d(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
                                              job_host.chunks, taps, part);
         count_launch(P);
     }
-    if (dynamic) prof_mark(P, 5, s);
+    if (dynamic) prof_mark(P, 7, s);
     if (dynamic || !job_host.stream) {
         dim3 grid(persist, job_host.nh);
         k_bin_gather_2d<<<grid, 256, 0, s>>>(x, P->logn, hashes, job_host.nh, P->d_win, jd,

@@ -25,7 +25,7 @@ constexpr int kMaxTrialsTrace = 64;
 constexpr int kHistBins = 4096;      // radix-select histogram bins (12-bit digits)
 constexpr int kKeptCap = 8192;       // kept coordinates ordered by rank (beyond: bitmap compaction)
 constexpr int kPersistCtas = 4;      // persistent CTAs per SM
-constexpr int kPhases = 8;           // profiled phases of one exec (see atsfft.h)
+constexpr int kPhases = 10;          // profiled phases of one exec (see atsfft.h)
 
 // Permutation of one hash (Def. 1), per axis.
 struct HashParam {
@@ -101,6 +101,8 @@ struct ExecState {
     int64_t count;         // kept coordinates
     int32_t ntrials;
     int32_t empty;         // 1: nothing to locate
+    int32_t tune_done;     // 1: the controller stopped within the small-B trials (1D)
+    int32_t pad0;
     int64_t trial_B[kMaxTrialsTrace];
     int64_t trial_k[kMaxTrialsTrace];
     Job job;               // location + estimation job at B*
@@ -128,6 +130,7 @@ struct atsfft_plan_s {
     int64_t tpart_off[atsfft::kMaxLogB];          // tuning partial sums of each B in d_part
     int tchunks[atsfft::kMaxLogB];                // partial blocks the FFT adds up per B
     int tstream_logR, tstream_chunks;             // the 1D multi-B residue-stream pass
+    int tune_split;        // last log2 B of the first tuning stage (b_hi: one stage)
 
     atsfft::HashParam *d_tune, *d_le;
     atsfft::WindowParam *d_win;
@@ -190,7 +193,9 @@ WindowParam window_shape(int64_t n, int logB, double alpha, double tol);
 Job make_job(const atsfft_plan_s *P, int logB, int nh);
 
 // bin.cu
-void launch_tuning(const atsfft_plan_s *P, const float2 *x, cudaStream_t s);
+// Tuning stage 1 (every trial in 2D; the small-window trials in 1D) or stage 2 (1D: the
+// residue-stream trials, skipped on the device when stage 1 settled the controller).
+void launch_tuning(const atsfft_plan_s *P, const float2 *x, int stage, cudaStream_t s);
 void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, cudaStream_t s);
 void launch_single_hash(const atsfft_plan_s *P, const float2 *x, int b, const HashParam &hp,
                         const HashParam *hp_dev, float2 *out, cudaStream_t s);
@@ -206,10 +211,10 @@ void launch_bucket_fft_dynamic(const atsfft_plan_s *P, const Job *job, const flo
                                float2 *out, float *energy, int n_energy, cudaStream_t s);
 void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB, const int *chunks,
                              const int64_t *in_off, const int64_t *out_off, const float2 *part,
-                             float2 *out, float *energy, cudaStream_t s);
+                             float2 *out, float *energy, const int *skip, cudaStream_t s);
 
 // tail.cu
-void launch_tune_tail(const atsfft_plan_s *P, cudaStream_t s);
+void launch_tune_tail(const atsfft_plan_s *P, int stage, cudaStream_t s);
 void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, int64_t capacity,
                      int64_t *d_count, int64_t *d_k, int32_t *d_status, cudaStream_t s);
 

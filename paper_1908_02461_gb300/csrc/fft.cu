@@ -355,13 +355,16 @@ struct FftBatch {
 };
 
 // energy != nullptr: the final pass also writes |Zhat|^2 at the output offsets of
-// `energy` and the maximum into stats[logB].max_bits (the tuning trial's slot).
+// `energy` and the maximum into stats[logB].max_bits (the tuning trial's slot).  A set
+// *skip (device flag) makes every CTA return at once.
 __global__ void __launch_bounds__(kFftThreads, 2) k_fft_batch(int ndim, int pass, const FftBatch Bt,
                                                    const float2 *__restrict__ part, float2 *tmp,
                                                    float2 *fin, const float2 *__restrict__ tw,
-                                                   float *energy, HashStats *stats)
+                                                   float *energy, HashStats *stats,
+                                                   const int *skip)
 {
     __shared__ float2 sm[kSmemPadded];
+    if (skip && *skip) return;
     for (int64_t tr = blockIdx.x; tr < Bt.total; tr += gridDim.x) {
         int jb = 0;
         while (jb + 1 < Bt.njobs && tr >= Bt.j[jb + 1].tr_start) jb++;
@@ -401,7 +404,7 @@ void launch_bucket_fft_dynamic(const atsfft_plan_s *P, const Job *job, const flo
 // output offset out_off[i]); the four-step intermediate reuses the output offsets.
 void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB, const int *chunks,
                              const int64_t *in_off, const int64_t *out_off, const float2 *part,
-                             float2 *out, float *energy, cudaStream_t s)
+                             float2 *out, float *energy, const int *skip, cudaStream_t s)
 {
     for (int pass = 0; pass < 2; pass++) {
         FftBatch Bt;
@@ -454,7 +457,7 @@ void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB,
         const int64_t cap = (int64_t)P->num_sms * 2;
         const int64_t grid = Bt.total < cap ? Bt.total : cap;
         k_fft_batch<<<(unsigned)grid, kFftThreads, 0, s>>>(P->ndim, pass, Bt, part, P->d_fft_tmp, out,
-                                                   P->d_tw, energy, P->d_stats);
+                                                   P->d_tw, energy, P->d_stats, skip);
         count_launch(P);
     }
 }

@@ -250,6 +250,7 @@ extern "C" void atsfft_default_params(atsfft_params *p)
     p->b_min_log2 = 0;
     p->b_max_log2 = 0;
     p->coop_blocks_per_sm = 0;
+    p->tune_stages = 2;
 }
 
 extern "C" const char *atsfft_status_string(atsfft_status s)
@@ -278,6 +279,7 @@ static bool params_ok(const atsfft_params *p)
     if (!(p->filter_tol > 0 && p->filter_tol < 1)) return false;
     if (!(p->thr_rel >= 0 && p->thr_med >= 0 && p->tie_eta >= 0 && p->tie_eta < 1)) return false;
     if (p->coop_blocks_per_sm < 0 || p->coop_blocks_per_sm > 8) return false;
+    if (p->tune_stages != 1 && p->tune_stages != 2) return false;
     return true;
 }
 
@@ -388,6 +390,12 @@ extern "C" atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t
         for (int b = P->b0; b <= P->b_hi; b++)
             if (ndim == 1 && P->h_tjob[b].stream) P->tstream_logR = b;
         P->tstream_chunks = P->tstream_logR >= 0 ? P->h_tjob[P->tstream_logR].chunks : 1;
+        // two tuning stages in 1D: the leading gather-form trials, then the rest
+        P->tune_split = P->b_hi;
+        if (ndim == 1 && p.tune_stages == 2) {
+            P->tune_split = P->b0 - 1;
+            for (int b = P->b0; b <= P->b_hi && !P->h_tjob[b].stream; b++) P->tune_split = b;
+        }
         for (int b = P->b0; b <= P->b_hi; b++) {
             int64_t nb = ndim == 1 ? ((int64_t)1 << b) : ((int64_t)1 << (2 * b));
             P->tpart_off[b] = off;

@@ -552,8 +552,10 @@ __device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &
 // ---------------------------------------------------------------------------------
 struct TuneTailArgs {
     StatsParams S;
-    const StatJob *jobs;
+    const StatJob *jobs;   // this stage's trials
     int njobs;
+    int stage;             // 2: return at once if stage 1 settled the controller
+    int limit_b;           // the controller may visit trials up to this log2 B
     int b0, b_hi, tune_max;
     double delta2;
     const Job *tjob;
@@ -568,7 +570,9 @@ struct TuneTailArgs {
 // One thread walks the trials B0, 2 B0, ... through Eq. (12) and Eq. (14) until the
 // stop reading: the first trial with r < delta2 (keep branch, or halve branch onto the
 // already evaluated B/2); r = inf when either count is 0; a trial whose energies are
-// all exactly 0 ends with k* = 0.  Then it writes the jobs at B*.
+// all exactly 0 ends with k* = 0.  Then it writes the jobs at B*.  A walk that would
+// step past limit_b (the trials evaluated so far) writes nothing and leaves tune_done
+// at 0 for the second stage, which walks again from B0 over all trials.
 __device__ void controller(const TuneTailArgs &A)
 {
     const HashStats *stats = A.S.stats;
@@ -598,9 +602,11 @@ __device__ void controller(const TuneTailArgs &A)
             if (status == ATSFFT_OK) status = ATSFFT_E_NOT_CONVERGED;
             break;
         }
+        if (b == A.limit_b) return;   // needs the trials of the second stage
         kprev = k;
         b++;
     }
+    state->tune_done = 1;
     if (k == 0) empty = 1;
     state->ntrials = trial + 1;
     state->b_star = b;
@@ -627,6 +633,7 @@ __device__ void controller(const TuneTailArgs &A)
 
 __global__ void __launch_bounds__(256, 2) k_tune_tail(const TuneTailArgs A)
 {
+    if (A.stage == 2 && A.state->tune_done) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) stamp(&A.state->bar);
     if (!stats_phases(A.jobs, A.njobs, A.S, &A.state->bar, &A.state->status)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) controller(A);
@@ -1370,12 +1377,18 @@ static int coop_grid(const atsfft_plan_s *P, const void *fn)
     return P->num_sms * per_sm;
 }
 
-void launch_tune_tail(const atsfft_plan_s *P, cudaStream_t s)
+void launch_tune_tail(const atsfft_plan_s *P, int stage, cudaStream_t s)
 {
+    // the stage's trials: stat jobs are ordered by log2 B from b0
+    const int first = stage == 1 ? 0 : P->tune_split + 1 - P->b0;
+    const int last = stage == 1 ? P->tune_split - P->b0 : P->ntstat - 1;
+    if (first > last) return;
     TuneTailArgs A;
     A.S = stats_params(P);
-    A.jobs = P->d_tstat;
-    A.njobs = P->ntstat;
+    A.jobs = P->d_tstat + first;
+    A.njobs = last - first + 1;
+    A.stage = stage;
+    A.limit_b = stage == 1 ? P->tune_split : P->b_hi;
     A.b0 = P->b0;
     A.b_hi = P->b_hi;
     A.tune_max = P->p.tune_max;

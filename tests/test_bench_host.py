@@ -54,11 +54,25 @@ def test_roofline_model_picks_dominant_phase():
     import bench
 
     n = 1 << 22
-    ph = {"tune_gather": 0.02, "tune_stream": 0.03, "tune_fft": 0.06, "tune_tail": 0.05,
-          "le_bin_stream": 0.06, "le_bin_gather": 0.006, "le_fft": 0.07, "loc_tail": 0.12}
+    ph = {"tune1_bin": 0.02, "tune1_fft": 0.01, "tune1_tail": 0.02, "tune2_bin": 0.03,
+          "tune2_fft": 0.03, "tune2_tail": 0.02, "le_bin_stream": 0.06, "le_bin_gather": 0.006,
+          "le_fft": 0.035, "loc_tail": 0.12}
     traces = {2000: [(16, 0), (65536, 1900)]}
     roof, rows = bench.roofline({2000: ph}, traces, n)
     assert roof["kernel"] == "loc_tail" and roof["bound"] == "hbm"
     assert rows["le_bin_stream"]["bound"] == "alu"
     # 14 hashes x n pairs in 0.06 ms
     assert rows["le_bin_stream"]["achieved"] == pytest.approx(14 * n / 0.06e-3 / 1e9)
+    # the second tuning stage ran (the walk reached B = 2^16, past the gather trials)
+    assert rows["tune2_bin"]["bound"] == "alu"
+
+
+def test_roofline_model_skips_unused_second_stage():
+    import bench
+
+    n = 1 << 22
+    ph = {nm: 0.01 for nm in ("tune1_bin", "tune1_fft", "tune1_tail", "tune2_bin", "tune2_fft",
+                              "tune2_tail", "le_bin_stream", "le_bin_gather", "le_fft", "loc_tail")}
+    traces = {50: [(16, 0), (4096, 49)]}
+    _, rows = bench.roofline({50: ph}, traces, n)
+    assert "tune2_bin" not in rows and "tune2_fft" not in rows

@@ -1,0 +1,98 @@
+"""Batched execution through one CUDA graph (atsfft_batch_*): every branch gives exactly
+the outputs of the plain exec of its plan, and relaunches re-read the inputs.  Needs a GPU."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def A():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1908_02461_gb300 as A
+
+    A.build()
+    return A
+
+
+def _outputs(torch, cap):
+    return dict(loc=torch.empty(cap, dtype=torch.int64, device="cuda"),
+                val=torch.empty(cap, dtype=torch.complex64, device="cuda"),
+                count=torch.zeros(1, dtype=torch.int64, device="cuda"),
+                k=torch.zeros(1, dtype=torch.int64, device="cuda"),
+                status=torch.zeros(1, dtype=torch.int32, device="cuda"))
+
+
+def _result(o):
+    n = int(o["count"].item())
+    m = min(n, o["loc"].numel())
+    return (n, int(o["k"].item()), int(o["status"].item()), o["loc"][:m].cpu().numpy(),
+            o["val"][:m].cpu().numpy())
+
+
+def _same(a, b):
+    assert a[:3] == b[:3]
+    assert np.array_equal(a[3], b[3])
+    assert np.array_equal(a[4], b[4])
+
+
+def test_batch_matches_plain_execs_and_relaunches(A):
+    import torch
+
+    from synth import sparse_signal_1d, sparse_signal_2d
+
+    cases = [((1 << 14,), sparse_signal_1d(1 << 14, 16, 11).x),
+             ((1 << 18,), sparse_signal_1d(1 << 18, 200, 12, snr_db=40.0).x),
+             ((256, 256), sparse_signal_2d(256, 10, 13).x)]
+    cap = 1 << 12
+    plans, xs, outs, refs = [], [], [], []
+    for shape, x in cases:
+        p = A.Plan(shape, seed=5)
+        xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        o = _outputs(torch, cap)
+        p.exec_async(xd, o["loc"], o["val"], o["count"], o["k"], o["status"])
+        torch.cuda.synchronize()
+        refs.append(_result(o))
+        plans.append(p)
+        xs.append(xd)
+        outs.append(_outputs(torch, cap))
+    batch = A.Batch([(p, x, o["loc"], o["val"], o["count"], o["k"], o["status"])
+                     for p, x, o in zip(plans, xs, outs)])
+    assert batch.kernels() > 0
+    for _ in range(2):
+        batch.launch()
+        torch.cuda.synchronize()
+        for o, ref in zip(outs, refs):
+            _same(_result(o), ref)
+    # new input in place: the next launch transforms it
+    x2 = sparse_signal_1d(1 << 14, 16, 99).x
+    xs[0].copy_(torch.from_numpy(x2))
+    o = _outputs(torch, cap)
+    plans[0].exec_async(xs[0], o["loc"], o["val"], o["count"], o["k"], o["status"])
+    torch.cuda.synchronize()
+    ref2 = _result(o)
+    batch.launch()
+    torch.cuda.synchronize()
+    _same(_result(outs[0]), ref2)
+    batch.close()
+    for p in plans:
+        p.close()
+
+
+def test_batch_rejects_duplicate_plans_and_profiling(A):
+    import torch
+
+    p = A.Plan((1 << 14,), seed=1)
+    x = torch.zeros(1 << 14, dtype=torch.complex64, device="cuda")
+    o = _outputs(torch, 16)
+    item = (p, x, o["loc"], o["val"], o["count"], o["k"], o["status"])
+    with pytest.raises(A.ATSFFTError):
+        A.Batch([item, item])
+    p.set_profiling(True)
+    with pytest.raises(A.ATSFFTError):
+        A.Batch([item])
+    p.set_profiling(False)
+    p.close()
