@@ -321,6 +321,110 @@ def ncu_case(k):
     plan.close()
 
 
+MIXED_SIGNALS = 512
+MIXED_LOGN = (16, 18, 20, 22)
+MIXED_BRANCHES = 64      # graph branches per batch
+
+
+def mixed_workload(args):
+    """512 independent signals, n uniform over {2^16, 2^18, 2^20, 2^22}, k log-uniform in
+    [10, 1000], 40 dB noise: one plan per signal (clones of one template per size), the
+    transforms recorded into CUDA graphs of MIXED_BRANCHES branches; a step transforms all
+    512 signals.  Prints one JSON line (transforms/s and Gsamples/s)."""
+    import torch
+
+    import paper_1908_02461_gb300 as A
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    A.build()
+    dev = torch.device("cuda", local)
+    rng = np.random.default_rng(4242 + rank)
+    sizes = [1 << int(rng.choice(MIXED_LOGN)) for _ in range(MIXED_SIGNALS)]
+    ks = [int(round(np.exp(rng.uniform(np.log(10), np.log(1000))))) for _ in range(MIXED_SIGNALS)]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(777 + rank)
+    xs = []
+    for n, k in zip(sizes, ks):
+        # x = IDFT of a k-sparse spectrum (unit magnitudes, uniform phases) + complex
+        # Gaussian noise at 40 dB of the signal power, synthesised on the device
+        loc = rng.choice(n, size=k, replace=False)
+        spec = torch.zeros(n, dtype=torch.complex128, device=dev)
+        spec[torch.from_numpy(loc).to(dev)] = torch.from_numpy(
+            np.exp(2j * np.pi * rng.uniform(size=k))).to(dev)
+        x = torch.fft.ifft(spec)
+        p_sig = float((x.abs() ** 2).mean())
+        sd = np.sqrt(p_sig * 10 ** (-SNR_DB / 10) / 2)
+        noise = torch.complex(torch.randn(n, generator=gen, device=dev, dtype=torch.float64),
+                              torch.randn(n, generator=gen, device=dev, dtype=torch.float64)) * sd
+        xs.append((x + noise).to(torch.complex64).contiguous())
+    pp = A.params(coop_blocks_per_sm=1)
+    templates = {n: A.Plan((n,), params=pp, seed=SEED) for n in sorted(set(sizes))}
+    t0 = time.perf_counter()
+    plans = [templates[n].clone() for n in sizes]
+    t_clone = time.perf_counter() - t0
+    outs = [dict(loc=torch.empty(CAPACITY, dtype=torch.int64, device=dev),
+                 val=torch.empty(CAPACITY, dtype=torch.complex64, device=dev),
+                 count=torch.zeros(1, dtype=torch.int64, device=dev),
+                 k=torch.zeros(1, dtype=torch.int64, device=dev),
+                 status=torch.zeros(1, dtype=torch.int32, device=dev)) for _ in sizes]
+    batches = []
+    for b0 in range(0, MIXED_SIGNALS, MIXED_BRANCHES):
+        items = [(plans[i], xs[i], outs[i]["loc"], outs[i]["val"], outs[i]["count"],
+                  outs[i]["k"], outs[i]["status"]) for i in range(b0, min(b0 + MIXED_BRANCHES, MIXED_SIGNALS))]
+        batches.append(A.Batch(items))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        for bt in batches:
+            bt.launch(stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(1, args.steps // 100)
+    ms = []
+    if ws > 1:
+        torch.distributed.barrier()
+    with ClockSampler(local) as clk:
+        for _ in range(steps):
+            flush.zero_()
+            ev0.record(stream)
+            step()
+            ev1.record(stream)
+            ev1.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+    total_ms = aggregate(sum(ms), ws, dev)
+    ntrans = MIXED_SIGNALS * steps * ws
+    status = [int(o["status"].item()) for o in outs]
+    kstar = [int(o["k"].item()) for o in outs]
+    samples = sum(sizes) * steps * ws
+    launches = sum(bt.kernels() for bt in batches) * steps
+    for bt in batches:
+        bt.close()
+    for p in plans + list(templates.values()):
+        p.close()
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": "transforms/s", "value": ntrans / (total_ms / 1e3), "unit": "transforms/s",
+        "n_gpus": ws, "steps": steps, "warmup": args.warmup, "ms_per_step": total_ms / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "512 signals, n uniform in {2^16,2^18,2^20,2^22}, k log-uniform "
+                               "in [10,1000], 40 dB noise; one step = 512 transforms",
+                   "gsamples_per_s": samples / (total_ms / 1e3) / 1e9,
+                   "graphs": len(batches), "branches_per_graph": MIXED_BRANCHES,
+                   "clone_s": t_clone, "status_counts": {str(v): status.count(v) for v in sorted(set(status))},
+                   "k_star_vs_k_median_ratio": float(np.median(np.array(kstar) / np.array(ks))),
+                   "l2": "flushed between steps (256 MiB write)"},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -336,6 +440,8 @@ def main():
                     help="1D tuning in one batch (1) or small-window trials first (2)")
     ap.add_argument("--no-graph", action="store_true",
                     help="time per-signal execs on streams instead of one graph launch per step")
+    ap.add_argument("--workload", default="headline", choices=["headline", "mixed512"],
+                    help="mixed512: the 512-signal mixed-size batch instead of the headline step")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="K",
                     help="profiling case for ncu: one plan, the k=K signal, three transforms")
     args = ap.parse_args()
@@ -344,6 +450,9 @@ def main():
         return
     if args.ncu_case:
         ncu_case(args.ncu_case)
+        return
+    if args.workload == "mixed512":
+        mixed_workload(args)
         return
 
     import torch

@@ -81,6 +81,14 @@ void atsfft_default_params(atsfft_params *p);
 atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t *shape, int64_t k_hint,
                           const atsfft_params *p, uint64_t seed);
 
+/* A new plan equal to `src` (same shape, parameters, hint and seed, so its transforms
+ * give bit-identical results) with its own scratch, on the current device (which must be
+ * src's).  The window, phase and twiddle tables are copied from src rather than
+ * computed, so this is much cheaper than atsfft_plan; one plan per concurrent transform
+ * (a batch branch, a stream) is what the scratch ownership requires.  src stays
+ * independent: either may be destroyed first. */
+atsfft_status atsfft_plan_clone(atsfft_plan_t src, atsfft_plan_t *out);
+
 /* One 1D transform of d_x (n complex64, interleaved re/im floats, device).
  *   d_loc   int64[capacity]: kept coordinates (frequencies), ascending;
  *   d_val   complex64[capacity]: their estimated DFT values (Eq. (11), median);

@@ -32,6 +32,7 @@ from ._lib import (  # noqa: F401
     atsfft_params,
     atsfft_phase_times,
     atsfft_plan,
+    atsfft_plan_clone,
     atsfft_set_profiling,
     atsfft_status_string,
     atsfft_tail_stamps,
@@ -70,6 +71,18 @@ class Plan:
         self.device = torch.device("cuda", torch.cuda.current_device())
         self._scalars = torch.zeros(3, dtype=torch.int64, device=self.device)
 
+    def clone(self) -> "Plan":
+        """A plan with the same tables and its own scratch (atsfft_plan_clone)."""
+        import torch
+
+        st, h = atsfft_plan_clone(self.handle)
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_plan_clone")
+        other = Plan.__new__(Plan)
+        other.shape, other.ndim, other.handle, other.device = self.shape, self.ndim, h, self.device
+        other._scalars = torch.zeros(3, dtype=torch.int64, device=self.device)
+        return other
+
     def close(self):
         if getattr(self, "handle", None):
             atsfft_destroy(self.handle)
@@ -92,7 +105,7 @@ class Plan:
             raise ATSFFTError(st, "atsfft_exec")
 
     def __call__(self, x, capacity: int | None = None):
-        """Transform x (complex64 CUDA tensor); returns (loc, val, k_star, status) after sync."""
+        """Transform x (complex64 CUDA tensor); returns (loc, val, k_star, status, count) after sync."""
         import torch
 
         if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():

@@ -39,7 +39,7 @@ EXPORTED = ["atsfft_default_params", "atsfft_plan", "atsfft_exec", "atsfft_exec_
             "atsfft_window_response", "atsfft_last_trace", "atsfft_set_profiling",
             "atsfft_phase_times", "atsfft_tail_stamps", "atsfft_hash_spectrum_noalloc",
             "atsfft_batch_create", "atsfft_batch_launch", "atsfft_batch_kernels",
-            "atsfft_batch_destroy"]
+            "atsfft_batch_destroy", "atsfft_plan_clone"]
 
 PHASES = ["tune1_bin", "tune1_fft", "tune1_tail", "tune2_bin", "tune2_fft", "tune2_tail",
           "le_bin_stream", "le_bin_gather", "le_fft", "loc_tail"]
@@ -84,6 +84,8 @@ def load(path: str | None = None):
     L.atsfft_tail_stamps.restype = i32
     L.atsfft_hash_spectrum_noalloc.argtypes = [vp, i64, i64, u64, i32, i32, vp, vp]
     L.atsfft_hash_spectrum_noalloc.restype = i32
+    L.atsfft_plan_clone.argtypes = [vp, P(vp)]
+    L.atsfft_plan_clone.restype = i32
     L.atsfft_batch_create.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, P(vp)]
     L.atsfft_batch_create.restype = i32
     L.atsfft_batch_launch.argtypes = [vp, vp]
@@ -209,3 +211,10 @@ def atsfft_batch_kernels(batch):
 
 def atsfft_batch_destroy(batch) -> int:
     return load().atsfft_batch_destroy(batch)
+
+
+def atsfft_plan_clone(src):
+    """Returns (status, plan handle)."""
+    h = C.c_void_p()
+    st = load().atsfft_plan_clone(src, C.byref(h))
+    return st, h.value

@@ -118,6 +118,7 @@ struct atsfft_plan_s {
     atsfft_params p;
     uint64_t seed;
     int b_lo, b_hi, b0;
+    int64_t k_hint;
     int L_loc, L_est;
     int device;
     int num_sms;

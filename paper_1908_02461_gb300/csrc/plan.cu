@@ -303,8 +303,11 @@ static int ilog2_ceil(int64_t v)
     return r;
 }
 
-extern "C" atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t *shape,
-                                     int64_t k_hint, const atsfft_params *pp, uint64_t seed)
+// Plan creation; with `tmpl` (a plan of the same shape, parameters, hint and seed) the
+// window, phase and twiddle tables are copied from it instead of being computed.
+static atsfft_status plan_create(atsfft_plan_t *out, int ndim, const int64_t *shape,
+                                 int64_t k_hint, const atsfft_params *pp, uint64_t seed,
+                                 const atsfft_plan_s *tmpl)
 {
     if (!out) return ATSFFT_E_INVALID_ARG;
     *out = nullptr;
@@ -339,6 +342,7 @@ extern "C" atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t
         return ATSFFT_E_INVALID_ARG;
     }
     P->b0 = P->b_lo;
+    P->k_hint = k_hint;
     if (k_hint > 0) {
         int want = ndim == 1 ? ilog2_ceil(2 * k_hint) : (ilog2_ceil(2 * k_hint) + 1) / 2;
         if (want > P->b0) P->b0 = want;
@@ -460,9 +464,10 @@ extern "C" atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t
         if (nch > max_nch) max_nch = nch;
         if ((n >> b) > max_D) max_D = n >> b;
     }
-    e = cudaMalloc(&d_partial, sizeof(double) * (size_t)(max_D + 1) * (size_t)max_nch);
+    if (tmpl) max_nch = 0;   // no window kernels: the tables come from the template
+    e = cudaMalloc(&d_partial, sizeof(double) * (size_t)(max_D + 1) * (size_t)(max_nch ? max_nch : 1));
     if (e == cudaSuccess) e = cudaMalloc(&d_S0, sizeof(double) * kMaxLogB);
-    for (int b = P->b0; b <= P->b_hi && e == cudaSuccess; b++) {
+    for (int b = P->b0; b <= P->b_hi && e == cudaSuccess && !tmpl; b++) {
         WindowParam &w = P->h_win[b];
         int64_t D = n >> b;
         int nch = (int)((w.h + kRespChunk) / kRespChunk);
@@ -471,23 +476,36 @@ extern "C" atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t
         k_window_finish<<<1, 256>>>(D, d_partial, nch, P->d_resp + P->resp_off[b], d_S0 + b);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !tmpl) {
         k_twiddles<<<kTwEntries / 256, 256>>>(P->d_tw);
         k_recip_gain<<<P->num_sms * 4, 256>>>(P->d_resp, resp_total, P->d_rgain);
         k_phase_table<<<P->num_sms, 256>>>(P->logn, P->phase_s, P->d_phase);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess && tmpl) {
+        const size_t nphase = ((size_t)1 << P->phase_s) + ((size_t)n >> P->phase_s);
+        e = cudaMemcpy(P->d_tw, tmpl->d_tw, sizeof(float2) * kTwEntries, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(P->d_resp, tmpl->d_resp, sizeof(double) * resp_total, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(P->d_rgain, tmpl->d_rgain, sizeof(float) * resp_total, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(P->d_phase, tmpl->d_phase, sizeof(float2) * nphase, cudaMemcpyDeviceToDevice);
+        memcpy(P->h_win, tmpl->h_win, sizeof(P->h_win));
+    }
     double S0[kMaxLogB];
-    if (e == cudaSuccess) e = cudaMemcpy(S0, d_S0, sizeof(double) * kMaxLogB, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && !tmpl)
+        e = cudaMemcpy(S0, d_S0, sizeof(double) * kMaxLogB, cudaMemcpyDeviceToHost);
     if (d_partial) cudaFree(d_partial);
     if (d_S0) cudaFree(d_S0);
     if (e == cudaSuccess) {
-        for (int b = P->b0; b <= P->b_hi; b++) {
-            WindowParam &w = P->h_win[b];
-            w.A = (double)n / S0[b];
-            w.log2c = (float)log2(w.A * (double)n / M_PI);
-            w.cA_D = (float)(w.A * (double)(n >> b));
-        }
+        if (!tmpl)
+            for (int b = P->b0; b <= P->b_hi; b++) {
+                WindowParam &w = P->h_win[b];
+                w.A = (double)n / S0[b];
+                w.log2c = (float)log2(w.A * (double)n / M_PI);
+                w.cA_D = (float)(w.A * (double)(n >> b));
+            }
         e = cudaMemcpy(P->d_win, P->h_win, sizeof(P->h_win), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMemcpy(P->d_tune, P->h_tune, sizeof(P->h_tune), cudaMemcpyHostToDevice);
@@ -517,6 +535,24 @@ extern "C" atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t
     }
     *out = P;
     return ATSFFT_OK;
+}
+
+extern "C" atsfft_status atsfft_plan(atsfft_plan_t *out, int ndim, const int64_t *shape,
+                                     int64_t k_hint, const atsfft_params *pp, uint64_t seed)
+{
+    return plan_create(out, ndim, shape, k_hint, pp, seed, nullptr);
+}
+
+extern "C" atsfft_status atsfft_plan_clone(atsfft_plan_t src, atsfft_plan_t *out)
+{
+    if (!out) return ATSFFT_E_INVALID_ARG;
+    *out = nullptr;
+    if (!src) return ATSFFT_E_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ATSFFT_E_CUDA;
+    if (dev != src->device) return ATSFFT_E_INVALID_ARG;
+    const int64_t shape[2] = {src->n, src->n};
+    return plan_create(out, src->ndim, shape, src->k_hint, &src->p, src->seed, src);
 }
 
 extern "C" atsfft_status atsfft_destroy(atsfft_plan_t P)

@@ -96,3 +96,22 @@ def test_batch_rejects_duplicate_plans_and_profiling(A):
         A.Batch([item])
     p.set_profiling(False)
     p.close()
+
+
+def test_clone_gives_identical_transforms(A):
+    import torch
+
+    from synth import sparse_signal_1d, sparse_signal_2d
+
+    for shape, x in [((1 << 16,), sparse_signal_1d(1 << 16, 40, 21, snr_db=40.0).x),
+                     ((128, 128), sparse_signal_2d(128, 6, 22).x)]:
+        p = A.Plan(shape, k_hint=8, seed=9)
+        c = p.clone()
+        xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        ra = p(xd, capacity=1 << 10)
+        p.close()   # the clone owns its tables
+        rb = c(xd, capacity=1 << 10)
+        assert ra[2:] == rb[2:]
+        assert np.array_equal(ra[0].cpu().numpy(), rb[0].cpu().numpy())
+        assert np.array_equal(ra[1].cpu().numpy(), rb[1].cpu().numpy())
+        c.close()
