@@ -158,6 +158,37 @@ atsfft_status atsfft_phase_times(atsfft_plan_t plan, float *h_ms, int max_phases
 atsfft_status atsfft_tail_stamps(atsfft_plan_t plan, uint64_t *h_ns, int max_stamps,
                                  int *h_nstamps, void *stream);
 
+/* ---- gradients at a fixed recovered support (1D) ---------------------------------- */
+
+/* atsfft_exec (or atsfft_exec_2d) that also writes, for each output position p <
+ * capacity, the estimation-hash indices the componentwise median selected (Section II-B,
+ * Eq. (11)): d_medsel[2p] for the real part, d_medsel[2p + 1] for the imaginary part
+ * (uint8, 0 .. loops_est - 1).  Together with the locations and B* (the last entry of
+ * atsfft_last_trace) they fix the real-linear map atsfft_estimate_apply evaluates and
+ * atsfft_estimate_adjoint transposes. */
+atsfft_status atsfft_exec_sel(atsfft_plan_t plan, const void *d_x, int64_t *d_loc, void *d_val,
+                              uint8_t *d_medsel, int64_t capacity, int64_t *d_count, int64_t *d_k,
+                              int32_t *d_status, void *stream);
+
+/* Eq. (11) at a fixed support as a function of the input, for a 1D plan: d_out[p] =
+ * (Re v_{l_r}(p), Im v_{l_i}(p)) where v_l(p) is the estimate of coordinate d_loc[p]
+ * from estimation hash l of the plan at B buckets applied to d_u (n complex64), and
+ * (l_r, l_i) = d_medsel[2p], d_medsel[2p + 1].  For d_u = the transformed signal this
+ * reproduces the transform's values.  Uses the plan's scratch (not reentrant with its
+ * execs); B must lie in the plan's tuning range. */
+atsfft_status atsfft_estimate_apply(atsfft_plan_t plan, int64_t B, const void *d_u,
+                                    const int64_t *d_loc, const uint8_t *d_medsel, int64_t count,
+                                    void *d_out, void *stream);
+
+/* The adjoint of atsfft_estimate_apply with respect to the real inner products of the
+ * input and output: given d_gval[p] = dL/dRe y_p + i dL/dIm y_p for count outputs, writes
+ * d_gx[a] = dL/dRe u_a + i dL/dIm u_a for every sample a < n (complex64, overwritten).
+ * This is the permuted, conjugate-phase scatter of the gradient back through Eq. (11),
+ * the bucket DFT, the binning and the window.  Same arguments and scratch rules. */
+atsfft_status atsfft_estimate_adjoint(atsfft_plan_t plan, int64_t B, const int64_t *d_loc,
+                                      const uint8_t *d_medsel, int64_t count, const void *d_gval,
+                                      void *d_gx, void *stream);
+
 /* ---- batched execution in one CUDA graph ----------------------------------------- */
 
 typedef struct atsfft_batch_s *atsfft_batch_t;

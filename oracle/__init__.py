@@ -24,4 +24,5 @@ from .oracle import (  # noqa: F401
     median_componentwise,
     atsfft_1d,
     atsfft_2d,
+    estimates_1d,
 )

@@ -621,6 +621,36 @@ static int hash_any(const ctx_t *cx, int64_t B, int phase, int index, const wind
     return ORC_OK;
 }
 
+/* Eq. (11) for estimation hash l (bucket-order spectrum Z at B, filter response resp):
+ * est[s * L + l] = Z[h(i)] omega^{tau i} / Ghat'(o(i)) for each kept coordinate keep[s]
+ * (2D: i * N + j, per-axis buckets and gains multiplied). */
+static void estimate_hash(const ctx_t *cx, int64_t B, int l, const cplx *Z, const double *resp,
+                          const int64_t *keep, int64_t nkeep, cplx *est, int L)
+{
+    int64_t n = cx->n, D = n / B;
+    int ndim = cx->ndim;
+    int64_t hp[4];
+    orc_hash_params(cx->seed, 2, l, n, ndim, hp);
+    for (int64_t s = 0; s < nkeep; s++) {
+        int64_t i = ndim == 1 ? keep[s] : keep[s] / n;
+        int64_t j = ndim == 1 ? 0 : keep[s] % n;
+        int64_t h1, o1, h2 = 0, o2 = 0;
+        bucket_of(i, hp[0], n, B, &h1, &o1);
+        int64_t m = mulmod(hp[1], i, n);
+        double gain = resp[(o1 + D - 1) / 2];
+        int64_t bucket = h1;
+        if (ndim == 2) {
+            bucket_of(j, hp[2], n, B, &h2, &o2);
+            m = (m + mulmod(hp[3], j, n)) % n;
+            gain *= resp[(o2 + D - 1) / 2];
+            bucket = h1 * B + h2;
+        }
+        double ang = -2.0 * M_PI * (double)m / (double)n; /* omega^{tau i} */
+        cplx ph = cos(ang) + I * sin(ang);
+        est[s * L + l] = Z[bucket] * ph / gain;
+    }
+}
+
 static int atsfft_any(const ctx_t *cx, int64_t k_hint, int64_t *loc, double *val_,
                       int64_t capacity, orc_result *res)
 {
@@ -769,26 +799,7 @@ static int atsfft_any(const ctx_t *cx, int64_t k_hint, int64_t *loc, double *val
         cplx *est = (cplx *)malloc(sizeof(cplx) * (size_t)(nkeep ? nkeep : 1) * (size_t)L);
         for (int l = 0; l < L; l++) {
             hash_any(cx, B, 2, l, &w, Z);
-            int64_t hp[4];
-            orc_hash_params(cx->seed, 2, l, n, ndim, hp);
-            for (int64_t s = 0; s < nkeep; s++) {
-                int64_t i = ndim == 1 ? keep[s] : keep[s] / n;
-                int64_t j = ndim == 1 ? 0 : keep[s] % n;
-                int64_t h1, o1, h2 = 0, o2 = 0;
-                bucket_of(i, hp[0], n, B, &h1, &o1);
-                int64_t m = mulmod(hp[1], i, n);
-                double gain = resp[(o1 + D - 1) / 2];
-                int64_t bucket = h1;
-                if (ndim == 2) {
-                    bucket_of(j, hp[2], n, B, &h2, &o2);
-                    m = (m + mulmod(hp[3], j, n)) % n;
-                    gain *= resp[(o2 + D - 1) / 2];
-                    bucket = h1 * B + h2;
-                }
-                double ang = -2.0 * M_PI * (double)m / (double)n; /* omega^{tau i} */
-                cplx ph = cos(ang) + I * sin(ang);
-                est[s * L + l] = Z[bucket] * ph / gain;
-            }
+            estimate_hash(cx, B, l, Z, resp, keep, nkeep, est, L);
         }
         free(resp);
         free(w.taps);
@@ -843,4 +854,43 @@ int orc_atsfft_2d(const double *x, int64_t N, int64_t k_hint, const orc_params *
     }
     ctx_t cx = {(const cplx *)x, N, 2, p, seed};
     return atsfft_any(&cx, k_hint, loc, val, capacity, res);
+}
+
+/* The L_est estimates of Eq. (11) of each coordinate loc[0..count) of a 1D signal at B
+ * buckets, without the median: out[s * L_est + l] (complex, interleaved) is estimation
+ * hash l's value (the support is given, nothing is located). */
+int orc_estimates_1d(const double *x, int64_t n, int64_t B, const orc_params *p, uint64_t seed,
+                     const int64_t *loc, int64_t count, double *out)
+{
+    orc_params dp;
+    if (!p) {
+        orc_default_params(&dp);
+        p = &dp;
+    }
+    if (!x || !out || (count > 0 && !loc) || !is_pow2(n) || !is_pow2(B) || B > n / 2 ||
+        count < 0 || !check_params(p))
+        return ORC_E_INVALID_ARG;
+    for (int64_t s = 0; s < count; s++)
+        if (loc[s] < 0 || loc[s] >= n) return ORC_E_INVALID_ARG;
+    ctx_t cx = {(const cplx *)x, n, 1, p, seed};
+    window_t w;
+    if (window_make(&w, n, B, p->filter_alpha, p->filter_tol) != ORC_OK) return ORC_E_NOMEM;
+    int64_t D = n / B;
+    double *resp = (double *)malloc(sizeof(double) * (size_t)D);
+    cplx *Z = (cplx *)malloc(sizeof(cplx) * (size_t)B);
+    if (!resp || !Z) {
+        free(resp);
+        free(Z);
+        free(w.taps);
+        return ORC_E_NOMEM;
+    }
+    orc_filter_response(n, B, p->filter_alpha, p->filter_tol, resp);
+    for (int l = 0; l < p->loops_est; l++) {
+        hash_any(&cx, B, 2, l, &w, Z);
+        estimate_hash(&cx, B, l, Z, resp, loc, count, (cplx *)out, p->loops_est);
+    }
+    free(resp);
+    free(Z);
+    free(w.taps);
+    return ORC_OK;
 }

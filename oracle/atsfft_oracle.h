@@ -118,6 +118,11 @@ int orc_atsfft_2d(const double *x, int64_t N, int64_t k_hint, const orc_params *
                   uint64_t seed, int64_t *loc, double *val, int64_t capacity,
                   orc_result *res);
 
+/* The loops_est estimates of Eq. (11) (no median) of coordinates loc[0..count) of a 1D
+ * signal at B buckets; out: count x loops_est complex values, interleaved (re, im). */
+int orc_estimates_1d(const double *x, int64_t n, int64_t B, const orc_params *p, uint64_t seed,
+                     const int64_t *loc, int64_t count, double *out);
+
 #ifdef __cplusplus
 }
 #endif

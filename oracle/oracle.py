@@ -97,6 +97,8 @@ def lib():
         L.orc_atsfft_1d.argtypes = [C.c_void_p, i64, i64, P(OracleParams), u64, C.c_void_p,
                                     C.c_void_p, i64, P(_CResult)]
         L.orc_atsfft_2d.argtypes = L.orc_atsfft_1d.argtypes
+        L.orc_estimates_1d.argtypes = [C.c_void_p, i64, i64, P(OracleParams), u64, C.c_void_p, i64,
+                                       C.c_void_p]
         _lib = L
     return _lib
 
@@ -224,3 +226,17 @@ def atsfft_1d(x, k_hint=0, params=None, seed=0, capacity=None) -> OracleResult:
 def atsfft_2d(x, k_hint=0, params=None, seed=0, capacity=None) -> OracleResult:
     x = np.asarray(x)
     return _run(lib().orc_atsfft_2d, x, x.shape[0], k_hint, params, seed, capacity)
+
+
+def estimates_1d(x, B, loc, params=None, seed=0):
+    """All loops_est estimates (Eq. (11), FP64, no median) of the coordinates `loc` of a
+    1D signal at B buckets: complex array [len(loc), loops_est]."""
+    x = _as_c128(x)
+    p = params or default_params()
+    loc = np.ascontiguousarray(np.asarray(loc, dtype=np.int64))
+    out = np.zeros((len(loc), p.loops_est), dtype=np.complex128)
+    st = lib().orc_estimates_1d(_ptr(x), x.size, B, C.byref(p), seed & 0xFFFFFFFFFFFFFFFF,
+                                _ptr(loc), len(loc), _ptr(out))
+    if st != 0:
+        raise ValueError(f"orc_estimates_1d: status {st}")
+    return out

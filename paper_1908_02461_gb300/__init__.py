@@ -24,6 +24,9 @@ from ._lib import (  # noqa: F401
     atsfft_batch_launch,
     atsfft_default_params,
     atsfft_destroy,
+    atsfft_estimate_adjoint,
+    atsfft_estimate_apply,
+    atsfft_exec_sel,
     atsfft_exec,
     atsfft_exec_2d,
     atsfft_hash_spectrum,
@@ -122,6 +125,53 @@ class Plan:
         n = int(count.item())
         m = min(n, cap)
         return loc[:m], val[:m], int(k.item()), int(status.item()), n
+
+    def exec_sel(self, x, capacity: int | None = None):
+        """Transform x (1D or 2D) and also return the median's hash selections.
+
+        Returns (loc, val, medsel, B_star, k_star, status, count); medsel is uint8
+        [count, 2]: the estimation hash of the real and of the imaginary median."""
+        import torch
+
+        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError("x must be a contiguous complex64 CUDA tensor")
+        cap = capacity if capacity is not None else 1 << 16
+        loc = torch.empty(cap, dtype=torch.int64, device=x.device)
+        val = torch.empty(cap, dtype=torch.complex64, device=x.device)
+        msel = torch.zeros(cap, 2, dtype=torch.uint8, device=x.device)
+        count = torch.zeros(1, dtype=torch.int64, device=x.device)
+        k = torch.zeros(1, dtype=torch.int64, device=x.device)
+        status = torch.zeros(1, dtype=torch.int32, device=x.device)
+        st = atsfft_exec_sel(self.handle, x, loc, val, msel, cap, count, k, status,
+                             torch.cuda.current_stream().cuda_stream)
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_exec_sel")
+        n = int(count.item())
+        m = min(n, cap)
+        B = self.last_trace()[-1][0]
+        return loc[:m], val[:m], msel[:m], B, int(k.item()), int(status.item()), n
+
+    def estimate_apply(self, B: int, u, loc, msel):
+        """Eq. (11) at the fixed support `loc` with median selections `msel`, applied to u."""
+        import torch
+
+        out = torch.empty(loc.numel(), dtype=torch.complex64, device=u.device)
+        st = atsfft_estimate_apply(self.handle, B, u, loc, msel, loc.numel(), out,
+                                   torch.cuda.current_stream().cuda_stream)
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_estimate_apply")
+        return out
+
+    def estimate_adjoint(self, B: int, loc, msel, g):
+        """Adjoint of estimate_apply for the output gradient g (complex64 [count])."""
+        import torch
+
+        gx = torch.empty(self.shape[0], dtype=torch.complex64, device=g.device)
+        st = atsfft_estimate_adjoint(self.handle, B, loc, msel, loc.numel(), g.contiguous(), gx,
+                                     torch.cuda.current_stream().cuda_stream)
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_estimate_adjoint")
+        return gx
 
     def hash_spectrum(self, x, B: int, phase: int, index: int):
         import torch
@@ -227,3 +277,50 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def sparse_fft(x, plan: "Plan", capacity: int | None = None):
+    """Differentiable 1D ATSFFT: returns (loc, val) with val differentiable in x.
+
+    The support (loc) and the median's hash selections are fixed by the forward pass;
+    the gradient flows through Eq. (11), the bucket DFTs, the binning and the window at
+    that support (atsfft_estimate_adjoint)."""
+    return _SparseFFT.apply(x, plan, capacity)
+
+
+def _sparse_fft_class():
+    import torch
+
+    class SparseFFT(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x, plan, capacity):
+            loc, val, msel, B, _, _, _ = plan.exec_sel(x.detach().contiguous(), capacity)
+            ctx.plan, ctx.B = plan, B
+            ctx.save_for_backward(loc, msel)
+            ctx.mark_non_differentiable(loc)
+            return loc, val.clone()
+
+        @staticmethod
+        def backward(ctx, g_loc, g_val):
+            loc, msel = ctx.saved_tensors
+            if g_val is None:
+                return None, None, None
+            gx = ctx.plan.estimate_adjoint(ctx.B, loc, msel, g_val.to(torch.complex64))
+            return gx, None, None
+
+    return SparseFFT
+
+
+class _Lazy:
+    """Creates the autograd Function on first use (torch is imported lazily)."""
+
+    def __init__(self, make):
+        self._make, self._cls = make, None
+
+    def apply(self, *args):
+        if self._cls is None:
+            self._cls = self._make()
+        return self._cls.apply(*args)
+
+
+_SparseFFT = _Lazy(_sparse_fft_class)

@@ -39,7 +39,8 @@ EXPORTED = ["atsfft_default_params", "atsfft_plan", "atsfft_exec", "atsfft_exec_
             "atsfft_window_response", "atsfft_last_trace", "atsfft_set_profiling",
             "atsfft_phase_times", "atsfft_tail_stamps", "atsfft_hash_spectrum_noalloc",
             "atsfft_batch_create", "atsfft_batch_launch", "atsfft_batch_kernels",
-            "atsfft_batch_destroy", "atsfft_plan_clone"]
+            "atsfft_batch_destroy", "atsfft_plan_clone", "atsfft_exec_sel",
+            "atsfft_estimate_apply", "atsfft_estimate_adjoint"]
 
 PHASES = ["tune1_bin", "tune1_fft", "tune1_tail", "tune2_bin", "tune2_fft", "tune2_tail",
           "le_bin_stream", "le_bin_gather", "le_fft", "loc_tail"]
@@ -84,6 +85,12 @@ def load(path: str | None = None):
     L.atsfft_tail_stamps.restype = i32
     L.atsfft_hash_spectrum_noalloc.argtypes = [vp, i64, i64, u64, i32, i32, vp, vp]
     L.atsfft_hash_spectrum_noalloc.restype = i32
+    L.atsfft_exec_sel.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp, vp]
+    L.atsfft_exec_sel.restype = i32
+    L.atsfft_estimate_apply.argtypes = [vp, i64, vp, vp, vp, i64, vp, vp]
+    L.atsfft_estimate_apply.restype = i32
+    L.atsfft_estimate_adjoint.argtypes = [vp, i64, vp, vp, i64, vp, vp, vp]
+    L.atsfft_estimate_adjoint.restype = i32
     L.atsfft_plan_clone.argtypes = [vp, P(vp)]
     L.atsfft_plan_clone.restype = i32
     L.atsfft_batch_create.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, P(vp)]
@@ -218,3 +225,19 @@ def atsfft_plan_clone(src):
     h = C.c_void_p()
     st = load().atsfft_plan_clone(src, C.byref(h))
     return st, h.value
+
+
+def atsfft_exec_sel(plan, d_x, d_loc, d_val, d_medsel, capacity, d_count, d_k, d_status,
+                    stream=None) -> int:
+    return load().atsfft_exec_sel(plan, _ptr(d_x), _ptr(d_loc), _ptr(d_val), _ptr(d_medsel),
+                                  capacity, _ptr(d_count), _ptr(d_k), _ptr(d_status), _ptr(stream))
+
+
+def atsfft_estimate_apply(plan, B, d_u, d_loc, d_medsel, count, d_out, stream=None) -> int:
+    return load().atsfft_estimate_apply(plan, B, _ptr(d_u), _ptr(d_loc), _ptr(d_medsel), count,
+                                        _ptr(d_out), _ptr(stream))
+
+
+def atsfft_estimate_adjoint(plan, B, d_loc, d_medsel, count, d_gval, d_gx, stream=None) -> int:
+    return load().atsfft_estimate_adjoint(plan, B, _ptr(d_loc), _ptr(d_medsel), count,
+                                          _ptr(d_gval), _ptr(d_gx), _ptr(stream))

@@ -24,7 +24,7 @@ using namespace atsfft;
 
 static atsfft_status exec_common(atsfft_plan_t P, int ndim, const void *d_x, int64_t *d_loc,
                                  void *d_val, int64_t capacity, int64_t *d_count, int64_t *d_k,
-                                 int32_t *d_status, void *stream)
+                                 int32_t *d_status, void *stream, uint8_t *d_msel = nullptr)
 {
     if (!P || P->ndim != ndim || !d_x || capacity < 0 || (capacity > 0 && (!d_loc || !d_val)) ||
         !d_count || !d_k || !d_status)
@@ -48,7 +48,7 @@ static atsfft_status exec_common(atsfft_plan_t P, int ndim, const void *d_x, int
     prof_mark(P, 8, s);
     launch_bucket_fft_dynamic(P, jd, P->d_part, P->d_z, P->d_energy + P->e_loc_off, P->L_loc, s);
     prof_mark(P, 9, s);
-    launch_loc_tail(P, d_loc, (float2 *)d_val, capacity, d_count, d_k, d_status, s);
+    launch_loc_tail(P, d_loc, (float2 *)d_val, d_msel, capacity, d_count, d_k, d_status, s);
     prof_mark(P, 10, s);
     return cuda_status(cudaGetLastError());
 }
@@ -65,6 +65,16 @@ extern "C" atsfft_status atsfft_exec_2d(atsfft_plan_t plan, const void *d_img, i
                                         int64_t *d_k, int32_t *d_status, void *stream)
 {
     return exec_common(plan, 2, d_img, d_loc, d_val, capacity, d_count, d_k, d_status, stream);
+}
+
+extern "C" atsfft_status atsfft_exec_sel(atsfft_plan_t plan, const void *d_x, int64_t *d_loc,
+                                         void *d_val, uint8_t *d_medsel, int64_t capacity,
+                                         int64_t *d_count, int64_t *d_k, int32_t *d_status,
+                                         void *stream)
+{
+    if (!plan || (capacity > 0 && !d_medsel)) return ATSFFT_E_INVALID_ARG;
+    return exec_common(plan, plan->ndim, d_x, d_loc, d_val, capacity, d_count, d_k, d_status,
+                       stream, d_medsel);
 }
 
 extern "C" atsfft_status atsfft_hash_spectrum(atsfft_plan_t P, const void *d_x, int64_t B,

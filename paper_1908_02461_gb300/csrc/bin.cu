@@ -11,39 +11,11 @@
 // S_0 = 0) is G_0 = A D.  Bucket sums are stored in residue order (common.cuh).
 #include <string.h>
 
-#include "common.cuh"
+#include "devmath.cuh"
 
 namespace atsfft {
 
 constexpr int kGroup = 16;   // hashes accumulated together per thread
-
-__device__ __forceinline__ float fast_exp2(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float fast_rcp(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b)
-{
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// S_b = sin(pi b / B) exp(i pi b / n)
-__device__ __forceinline__ float2 bucket_factor(uint32_t b, int logB, int logn)
-{
-    float s1 = sinpif(ldexpf((float)b, -logB));
-    float sc, cc;
-    sincospif(ldexpf((float)b, -logn), &sc, &cc);
-    return make_float2(s1 * cc, s1 * sc);
-}
 
 // ---------------------------------------------------------------------------------
 // 1D, warp per bucket: lanes walk the taps t = b + u B of the window, each tap computed
@@ -734,6 +706,36 @@ void launch_single_hash(const atsfft_plan_s *P, const float2 *x, int b, const Ha
     }
     const int64_t zero = 0;
     launch_bucket_fft_batch(P, 1, &b, &chunks, &zero, &zero, P->d_part, out, nullptr, nullptr, s);
+}
+
+// The L_est estimation hashes of a 1D plan at B = 2^b into P->d_part, layout
+// [hash][chunk][B] (the form the plan uses at this B); returns the chunk count.
+int launch_est_bin(const atsfft_plan_s *P, const float2 *x, int b, cudaStream_t s)
+{
+    const int L = P->L_est;
+    const Job &j = P->h_tjob[b];
+    if (j.stream) {
+        for (int g0 = 0; g0 < L; g0 += kMaxStream) {
+            StreamArgs S;
+            memset(&S, 0, sizeof(S));
+            S.nh = L - g0 < kMaxStream ? L - g0 : kMaxStream;
+            S.logR = b;
+            S.chunks = j.chunks;
+            for (int g = 0; g < S.nh; g++) {
+                S.h[g] = stream_hash(P, P->h_le[P->L_loc + g0 + g], b,
+                                     ((int64_t)(g0 + g) * j.chunks) << b);
+                S.h[g].rot_off = 0;   // one B: every hash's R_u table is the same
+            }
+            launch_stream_nh<false>(P, x, S, nullptr, sizeof(float2) * 2 * (size_t)(P->n >> b),
+                                    ((int64_t)1 << b) * j.chunks, s);
+        }
+        return j.chunks;
+    }
+    dim3 grid(P->num_sms * kPersistCtas, (L + kGroup - 1) / kGroup);
+    k_bin_gather_1d<<<grid, 256, 0, s>>>(x, P->logn, P->d_le + P->L_loc, L, P->d_win, nullptr, b,
+                                         P->d_part);
+    count_launch(P);
+    return 1;
 }
 
 void launch_bin_2d(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, const Job &job_host,

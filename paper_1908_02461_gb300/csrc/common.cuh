@@ -24,6 +24,7 @@ constexpr int kTwEntries = 2 * kSmallFFT;   // coarse exp(-2 pi i j / 4096), fin
 constexpr int kMaxTrialsTrace = 64;
 constexpr int kHistBins = 4096;      // radix-select histogram bins (12-bit digits)
 constexpr int kKeptCap = 8192;       // kept coordinates ordered by rank (beyond: bitmap compaction)
+constexpr int kAdjRotMax = 8192;     // adjoint: R_u table entries kept in shared memory
 constexpr int kPersistCtas = 4;      // persistent CTAs per SM
 constexpr int kPhases = 10;          // profiled phases of one exec (see atsfft.h)
 
@@ -200,6 +201,7 @@ void launch_tuning(const atsfft_plan_s *P, const float2 *x, int stage, cudaStrea
 void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, cudaStream_t s);
 void launch_single_hash(const atsfft_plan_s *P, const float2 *x, int b, const HashParam &hp,
                         const HashParam *hp_dev, float2 *out, cudaStream_t s);
+int launch_est_bin(const atsfft_plan_s *P, const float2 *x, int b, cudaStream_t s);
 void launch_bin_2d(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, const Job &job_host,
                    bool dynamic, const HashParam *hashes, int logB_static, float2 *part,
                    cudaStream_t s);
@@ -216,8 +218,9 @@ void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB,
 
 // tail.cu
 void launch_tune_tail(const atsfft_plan_s *P, int stage, cudaStream_t s);
-void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, int64_t capacity,
-                     int64_t *d_count, int64_t *d_k, int32_t *d_status, cudaStream_t s);
+void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, uint8_t *d_msel,
+                     int64_t capacity, int64_t *d_count, int64_t *d_k, int32_t *d_status,
+                     cudaStream_t s);
 
 // inspect.cu
 void launch_reset(const atsfft_plan_s *P, cudaStream_t s);

@@ -1,0 +1,95 @@
+// devmath.cuh -- device helpers shared by the forward estimate (tail.cu), the binning
+// (bin.cu) and the adjoint (adjoint.cu), so that the forward map and its transpose use
+// the same arithmetic.
+#pragma once
+
+#include "common.cuh"
+
+namespace atsfft {
+
+__device__ __forceinline__ float fast_exp2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float fast_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// S_b = sin(pi b / B) exp(i pi b / n)
+__device__ __forceinline__ float2 bucket_factor(uint32_t b, int logB, int logn)
+{
+    float s1 = sinpif(ldexpf((float)b, -logB));
+    float sc, cc;
+    sincospif(ldexpf((float)b, -logn), &sc, &cc);
+    return make_float2(s1 * cc, s1 * sc);
+}
+
+// Eq. (11) index terms of coordinate i on one axis of a hash (Eq. (10) half-bin reading):
+// P-index jP of its bucket, the bucket's phase term kph = jP sigma' tau mod B, the
+// offset index into the Ghat' table and m = tau i mod n, all in exact integers.
+__device__ __forceinline__ void axis_terms(uint64_t i, const HashParam &hp, int axis, int logn,
+                                           int logB, uint64_t &jP, uint64_t &kph, int64_t &oidx,
+                                           uint64_t &mtau)
+{
+    const uint64_t n = 1ull << logn, D = 1ull << (logn - logB), Bm = (1ull << logB) - 1;
+    const uint64_t p = ((uint64_t)hp.sigma[axis] * i) & (n - 1);
+    const uint64_t q = (2 * p + 1 + D) / (2 * D);
+    const int64_t o2 = (int64_t)(2 * p + 1) - (int64_t)(2 * q * D);   // odd, in (-D, D)
+    const uint64_t h = q & Bm;
+    const uint64_t sp = (uint64_t)hp.sinv[axis] & Bm;                   // sigma^{-1} mod B
+    jP = (sp * h) & Bm;
+    kph = (jP * ((uint64_t)hp.tau[axis] & Bm)) & Bm;                    // h sigma' tau mod B
+    oidx = (o2 + (int64_t)D - 1) / 2;
+    mtau = ((uint64_t)hp.tau[axis] * i) & (n - 1);
+}
+
+// exp(2 pi i m / n) for an exact integer m in [0, n): product of the two table parts
+// (entries m mod 2^s, then 2^s + m >> s).
+__device__ __forceinline__ float2 phase_lookup(uint64_t m, const float2 *tab, int s)
+{
+    const float2 lo = __ldg(&tab[m & ((1ull << s) - 1)]);
+    const float2 hi = __ldg(&tab[(1ull << s) + (m >> s)]);
+    return make_float2(lo.x * hi.x - lo.y * hi.y, lo.x * hi.y + lo.y * hi.x);
+}
+
+// Eq. (11) as a linear functional of the hash's P-order spectrum: the estimate of
+// coordinate `coord` (1D index, or i * N + j in 2D) is Pz[*idx] * C.
+__device__ __forceinline__ float2 estimate_coef(uint64_t coord, const HashParam &hp, int ndim,
+                                                int logn, int b, const float *rgain_b,
+                                                const float2 *phase, int phase_s, int64_t *idx)
+{
+    const uint64_t n = 1ull << logn, D = 1ull << (logn - b);
+    uint64_t jP, kph, m, kang;
+    int64_t oi;
+    float rg;
+    if (ndim == 1) {
+        axis_terms(coord, hp, 0, logn, b, jP, kph, oi, m);
+        *idx = (int64_t)jP;
+        rg = __ldg(&rgain_b[oi]);
+        kang = (kph * D + n - m) & (n - 1);
+    } else {
+        const uint64_t i = coord >> logn, j = coord & (n - 1);
+        uint64_t jP2, kph2, m2;
+        int64_t oi2;
+        axis_terms(i, hp, 0, logn, b, jP, kph, oi, m);
+        axis_terms(j, hp, 1, logn, b, jP2, kph2, oi2, m2);
+        *idx = (int64_t)((jP << b) | jP2);
+        rg = __ldg(&rgain_b[oi]) * __ldg(&rgain_b[oi2]);
+        kang = ((kph + kph2) * D + 2 * n - m - m2) & (n - 1);
+    }
+    const float2 w = phase_lookup(kang, phase, phase_s);
+    return make_float2(w.x * rg, w.y * rg);
+}
+
+}  // namespace atsfft

@@ -23,7 +23,7 @@
 // timeout means the device misbehaved, not a lost block).
 #include <math.h>
 
-#include "common.cuh"
+#include "devmath.cuh"
 
 namespace atsfft {
 
@@ -670,6 +670,7 @@ struct LocTailArgs {
     int logn;
     int64_t *loc;
     float2 *val;
+    uint8_t *msel;          // optional: median hash indices (real, imaginary) per output
     int64_t capacity;
     int64_t *d_count, *d_k;
     int32_t *d_status;
@@ -781,70 +782,27 @@ __device__ void topnum_block(const StatJob &J, const LocTailArgs &A, int64_t num
     __syncthreads();
 }
 
-__device__ __forceinline__ void axis_terms(uint64_t i, const HashParam &hp, int axis, int logn,
-                                           int logB, uint64_t &jP, uint64_t &kph, int64_t &oidx,
-                                           uint64_t &mtau)
-{
-    const uint64_t n = 1ull << logn, D = 1ull << (logn - logB), Bm = (1ull << logB) - 1;
-    const uint64_t p = ((uint64_t)hp.sigma[axis] * i) & (n - 1);
-    const uint64_t q = (2 * p + 1 + D) / (2 * D);
-    const int64_t o2 = (int64_t)(2 * p + 1) - (int64_t)(2 * q * D);   // odd, in (-D, D)
-    const uint64_t h = q & Bm;
-    const uint64_t sp = (uint64_t)hp.sinv[axis] & Bm;                   // sigma^{-1} mod B
-    jP = (sp * h) & Bm;
-    kph = (jP * ((uint64_t)hp.tau[axis] & Bm)) & Bm;                    // h sigma' tau mod B
-    oidx = (o2 + (int64_t)D - 1) / 2;
-    mtau = ((uint64_t)hp.tau[axis] * i) & (n - 1);
-}
-
-// exp(2 pi i m / n) for an exact integer m in [0, n): product of the two table parts.
-__device__ __forceinline__ float2 phase_of(uint64_t m, const LocTailArgs &A)
-{
-    const float2 lo = __ldg(&A.phase[m & ((1ull << A.phase_s) - 1)]);
-    const float2 hi = __ldg(&A.phase[(1ull << A.phase_s) + (m >> A.phase_s)]);
-    return make_float2(lo.x * hi.x - lo.y * hi.y, lo.x * hi.y + lo.y * hi.x);
-}
-
 // Eq. (11) for coordinate `coord` and estimation hash l: the bucket value times the
 // phase exp(2 pi i m / n) (m from exact integer index arithmetic) divided by the window
 // gain Ghat'(o) (as a reciprocal from the plan's FP64 table).
 __device__ float2 estimate_term(uint64_t coord, const LocTailArgs &A, int b, int l)
 {
-    const int logn = A.logn, ndim = A.S.ndim;
-    const uint64_t n = 1ull << logn, D = 1ull << (logn - b);
-    const int64_t nb = nb_of(ndim, b);
-    const float *RG = A.rgain + A.ro.off[b];
-    const HashParam hp = A.le[A.L_loc + l];
+    const int64_t nb = nb_of(A.S.ndim, b);
     const float2 *Pz = A.z + (int64_t)(A.L_loc + l) * nb;
-    uint64_t jP, kph, m;
-    int64_t oi;
-    float2 pv;
-    float rg;
-    uint64_t kang;
-    if (ndim == 1) {
-        axis_terms(coord, hp, 0, logn, b, jP, kph, oi, m);
-        pv = Pz[jP];
-        rg = __ldg(&RG[oi]);
-        kang = (kph * D + n - m) & (n - 1);
-    } else {
-        const uint64_t i = coord >> logn, j = coord & (n - 1);
-        uint64_t jP2, kph2, m2;
-        int64_t oi2;
-        axis_terms(i, hp, 0, logn, b, jP, kph, oi, m);
-        axis_terms(j, hp, 1, logn, b, jP2, kph2, oi2, m2);
-        pv = Pz[(jP << b) | jP2];
-        rg = __ldg(&RG[oi]) * __ldg(&RG[oi2]);
-        kang = ((kph + kph2) * D + 2 * n - m - m2) & (n - 1);
-    }
-    const float2 w = phase_of(kang, A);
-    return make_float2((pv.x * w.x - pv.y * w.y) * rg, (pv.x * w.y + pv.y * w.x) * rg);
+    int64_t idx;
+    const float2 c = estimate_coef(coord, A.le[A.L_loc + l], A.S.ndim, A.logn, b,
+                                   A.rgain + A.ro.off[b], A.phase, A.phase_s, &idx);
+    return cmul(Pz[idx], c);
 }
 
 // Componentwise median (element floor(L/2) of each sorted component; equal values
 // ordered by hash index) of the values v held by lanes 0..L-1 of a group of grp lanes:
 // each lane ranks its own value against the group's by shuffles, and the lane of rank
-// floor(L/2) stores that component to *out.  All lanes of the warp must call.
-__device__ __forceinline__ void group_median(float2 v, int L, int grp, bool valid, float2 *out)
+// floor(L/2) stores that component to *out (and, with sel != nullptr, its hash index to
+// sel[0] for the real part, sel[1] for the imaginary part).  All lanes of the warp must
+// call.
+__device__ __forceinline__ void group_median(float2 v, int L, int grp, bool valid, float2 *out,
+                                             uint8_t *sel)
 {
     const int gl = (int)(threadIdx.x & 31) & (grp - 1);
     int rr = 0, ri = 0;
@@ -855,8 +813,14 @@ __device__ __forceinline__ void group_median(float2 v, int L, int grp, bool vali
         ri += xi < v.y || (xi == v.y && c < gl);
     }
     if (valid && gl < L) {
-        if (rr == L / 2) out->x = v.x;
-        if (ri == L / 2) out->y = v.y;
+        if (rr == L / 2) {
+            out->x = v.x;
+            if (sel) sel[0] = (uint8_t)gl;
+        }
+        if (ri == L / 2) {
+            out->y = v.y;
+            if (sel) sel[1] = (uint8_t)gl;
+        }
     }
 }
 
@@ -874,7 +838,8 @@ __device__ void estimate_all(const LocTailArgs &A, int64_t cnt, int b)
         const bool valid = s < cnt;
         float2 v = make_float2(0.f, 0.f);
         if (valid && gl < A.L_est) v = estimate_term((uint64_t)A.loc[s], A, b, gl);
-        group_median(v, A.L_est, grp, valid, &A.val[valid ? s : 0]);
+        group_median(v, A.L_est, grp, valid, &A.val[valid ? s : 0],
+                     A.msel && valid ? A.msel + 2 * s : nullptr);
     }
 }
 
@@ -1280,7 +1245,8 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
             float2 v = make_float2(0.f, 0.f);
             if (valid && r < A.capacity && gl < A.L_est) v = estimate_term(coord, A, b, gl);
             const bool inside = valid && r < A.capacity;
-            group_median(v, A.L_est, grp, inside, &A.val[inside ? r : 0]);
+            group_median(v, A.L_est, grp, inside, &A.val[inside ? r : 0],
+                         A.msel && inside ? A.msel + 2 * (int64_t)r : nullptr);
             if (valid && gl == 0) {
                 A.coordbits[coord >> 5] = 0u;   // only kept coordinates set bits
                 if (inside) A.loc[r] = coord;
@@ -1406,8 +1372,9 @@ void launch_tune_tail(const atsfft_plan_s *P, int stage, cudaStream_t s)
     count_launch(P);
 }
 
-void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, int64_t capacity,
-                     int64_t *d_count, int64_t *d_k, int32_t *d_status, cudaStream_t s)
+void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, uint8_t *d_msel,
+                     int64_t capacity, int64_t *d_count, int64_t *d_k, int32_t *d_status,
+                     cudaStream_t s)
 {
     LocTailArgs A;
     A.S = stats_params(P);
@@ -1436,6 +1403,7 @@ void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, int6
     A.logn = P->logn;
     A.loc = d_loc;
     A.val = d_val;
+    A.msel = d_msel;
     A.capacity = capacity;
     A.d_count = d_count;
     A.d_k = d_k;

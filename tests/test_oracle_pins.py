@@ -425,3 +425,31 @@ def test_vote_rule_single_and_three_loops():
         q = ((2 * ((sigma * np.arange(n)) % n) + 1 + D) // (2 * D)) % B
         votes += np.isin(q, lm)
     assert r3.loc.tolist() == np.flatnonzero(votes >= 2).tolist()
+
+
+def test_fixed_support_estimates_are_linear_and_equal_the_dft_on_sparse_inputs():
+    """Eq. (11) at a fixed support: every loop's estimate is a linear functional of the
+    signal (superposition), and on an exactly sparse signal it equals the DFT value at
+    each support point wherever the coefficient is alone in its bucket (window gain
+    divided out), so the componentwise median is the DFT value."""
+    import oracle as O
+    from synth import sparse_signal_1d
+
+    n, B = 1 << 12, 256
+    sig = sparse_signal_1d(n, 8, 3)
+    loc = sig.support
+    X = np.fft.fft(sig.x.astype(np.complex128))
+    est = O.estimates_1d(sig.x, B, loc, seed=5)
+    assert est.shape == (8, 7)
+    # each loop is exact unless another coefficient shares its bucket; the median is exact
+    exact = np.abs(est - X[loc][:, None]) < 1e-7
+    assert exact.mean() > 0.9
+    med = np.sort(est.real, axis=1)[:, 3] + 1j * np.sort(est.imag, axis=1)[:, 3]
+    assert np.abs(med - X[loc]).max() < 1e-7
+    rng = np.random.default_rng(0)
+    u = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    a, b = 0.7 - 0.2j, -1.3 + 0.4j
+    lhs = O.estimates_1d(a * u + b * v, B, loc, seed=5)
+    rhs = a * O.estimates_1d(u, B, loc, seed=5) + b * O.estimates_1d(v, B, loc, seed=5)
+    assert np.abs(lhs - rhs).max() < 1e-9 * np.abs(rhs).max()
