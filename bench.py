@@ -358,8 +358,16 @@ def mixed_workload(args):
         noise = torch.complex(torch.randn(n, generator=gen, device=dev, dtype=torch.float64),
                               torch.randn(n, generator=gen, device=dev, dtype=torch.float64)) * sd
         xs.append((x + noise).to(torch.complex64).contiguous())
-    pp = A.params(coop_blocks_per_sm=1)
-    templates = {n: A.Plan((n,), params=pp, seed=SEED) for n in sorted(set(sizes))}
+    # per size: parameters from the autotuner (probe signals of the same family)
+    from paper_1908_02461_gb300.autotune import autotune
+
+    tuned, t_tune = {}, time.perf_counter()
+    for n in sorted(set(sizes)):
+        res = autotune(n, k_range=(10, 1000), snr_db=SNR_DB, probes=3, reps=2, seed=SEED)
+        tuned[n] = res
+    t_tune = time.perf_counter() - t_tune
+    templates = {n: A.Plan((n,), params=A.params(coop_blocks_per_sm=1, **tuned[n].params),
+                           seed=SEED) for n in sorted(set(sizes))}
     t0 = time.perf_counter()
     plans = [templates[n].clone() for n in sizes]
     t_clone = time.perf_counter() - t0
@@ -417,6 +425,9 @@ def mixed_workload(args):
                                "in [10,1000], 40 dB noise; one step = 512 transforms",
                    "gsamples_per_s": samples / (total_ms / 1e3) / 1e9,
                    "graphs": len(batches), "branches_per_graph": MIXED_BRANCHES,
+                   "autotune_s": t_tune,
+                   "autotuned": {str(n): dict(r.params, ms=r.ms_per_transform, err=r.error)
+                                 for n, r in tuned.items()},
                    "clone_s": t_clone, "status_counts": {str(v): status.count(v) for v in sorted(set(status))},
                    "k_star_vs_k_median_ratio": float(np.median(np.array(kstar) / np.array(ks))),
                    "l2": "flushed between steps (256 MiB write)"},

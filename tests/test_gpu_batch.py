@@ -115,3 +115,17 @@ def test_clone_gives_identical_transforms(A):
         assert np.array_equal(ra[0].cpu().numpy(), rb[0].cpu().numpy())
         assert np.array_equal(ra[1].cpu().numpy(), rb[1].cpu().numpy())
         c.close()
+
+
+def test_autotune_meets_the_error_target(A):
+    from paper_1908_02461_gb300.autotune import autotune
+
+    grid = {"loops": [(7, 7), (5, 5)], "filter_tol": [1e-6], "filter_alpha": [0.5],
+            "tune_stages": [2]}
+    res = autotune(1 << 14, k_range=(8, 64), snr_db=40.0, error_target=1e-2, probes=2, reps=1,
+                   grid=grid)
+    assert len(res.table) == 2
+    assert res.error <= 1e-2 and 0.9 <= res.k_ratio <= 1.1
+    assert res.ms_per_transform == min(r[1] for r in res.table if r[4])
+    p = A.Plan((1 << 14,), params=A.params(**res.params))
+    p.close()
