@@ -79,6 +79,8 @@ void orc_default_params(orc_params *p)
     p->tie_eta = 1e-2;
     p->b_min_log2 = 0;
     p->b_max_log2 = 0;
+    p->fixed_k = 0;
+    p->est_reuse_loc = 0;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -598,6 +600,9 @@ static int check_params(const orc_params *p)
     if (!(p->filter_alpha > 0 && p->filter_alpha <= 2)) return 0;
     if (!(p->filter_tol > 0 && p->filter_tol < 1)) return 0;
     if (!(p->thr_rel >= 0 && p->thr_med >= 0 && p->tie_eta >= 0 && p->tie_eta < 1)) return 0;
+    if (p->fixed_k != 0 && p->fixed_k != 1) return 0;
+    if (p->est_reuse_loc != 0 && p->est_reuse_loc != 1) return 0;
+    if (p->est_reuse_loc && p->loops_est > p->loops_loc) return 0;
     return 1;
 }
 
@@ -621,7 +626,8 @@ static int hash_any(const ctx_t *cx, int64_t B, int phase, int index, const wind
     return ORC_OK;
 }
 
-/* Eq. (11) for estimation hash l (bucket-order spectrum Z at B, filter response resp):
+/* Eq. (11) for estimation hash l (bucket-order spectrum Z at B, filter response resp;
+ * with est_reuse_loc the l-th location hash, else the l-th estimation hash):
  * est[s * L + l] = Z[h(i)] omega^{tau i} / Ghat'(o(i)) for each kept coordinate keep[s]
  * (2D: i * N + j, per-axis buckets and gains multiplied). */
 static void estimate_hash(const ctx_t *cx, int64_t B, int l, const cplx *Z, const double *resp,
@@ -630,7 +636,7 @@ static void estimate_hash(const ctx_t *cx, int64_t B, int l, const cplx *Z, cons
     int64_t n = cx->n, D = n / B;
     int ndim = cx->ndim;
     int64_t hp[4];
-    orc_hash_params(cx->seed, 2, l, n, ndim, hp);
+    orc_hash_params(cx->seed, cx->p->est_reuse_loc ? 1 : 2, l, n, ndim, hp);
     for (int64_t s = 0; s < nkeep; s++) {
         int64_t i = ndim == 1 ? keep[s] : keep[s] / n;
         int64_t j = ndim == 1 ? 0 : keep[s] % n;
@@ -688,7 +694,21 @@ static int atsfft_any(const ctx_t *cx, int64_t k_hint, int64_t *loc, double *val
     int b = b0;
     int64_t k_prev = 0, k_cur = 0;
     int zero_signal = 0;
-    for (int trial = 0;; trial++) {
+    if (p->fixed_k) {
+        /* fixed-k mode (the SFFT setting the tuning replaces): no trials, B from k_hint */
+        if (k_hint <= 0) {
+            free(Z); free(E); free(lm);
+            return res->status = ORC_E_INVALID_ARG;
+        }
+        int m = ilog2(ndim == 1 ? n * k_hint : n * n * k_hint);   /* ceil(log2) */
+        int bf = ndim == 1 ? (m + 1) / 2 : (m + 3) / 4;
+        if (bf < b_lo) bf = b_lo;
+        if (bf > b_hi) bf = b_hi;
+        res->B_star = (int64_t)1 << bf;
+        res->k_star = k_hint;
+        res->n_trials = 0;
+    }
+    for (int trial = 0; !p->fixed_k; trial++) {
         int64_t B = (int64_t)1 << b;
         int64_t nb = ndim == 1 ? B : B * B;
         window_t w;
@@ -798,7 +818,7 @@ static int atsfft_any(const ctx_t *cx, int64_t k_hint, int64_t *loc, double *val
         orc_filter_response(n, B, p->filter_alpha, p->filter_tol, resp);
         cplx *est = (cplx *)malloc(sizeof(cplx) * (size_t)(nkeep ? nkeep : 1) * (size_t)L);
         for (int l = 0; l < L; l++) {
-            hash_any(cx, B, 2, l, &w, Z);
+            hash_any(cx, B, p->est_reuse_loc ? 1 : 2, l, &w, Z);
             estimate_hash(cx, B, l, Z, resp, keep, nkeep, est, L);
         }
         free(resp);
@@ -886,7 +906,7 @@ int orc_estimates_1d(const double *x, int64_t n, int64_t B, const orc_params *p,
     }
     orc_filter_response(n, B, p->filter_alpha, p->filter_tol, resp);
     for (int l = 0; l < p->loops_est; l++) {
-        hash_any(&cx, B, 2, l, &w, Z);
+        hash_any(&cx, B, p->est_reuse_loc ? 1 : 2, l, &w, Z);
         estimate_hash(&cx, B, l, Z, resp, loc, count, (cplx *)out, p->loops_est);
     }
     free(resp);

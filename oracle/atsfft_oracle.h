@@ -42,6 +42,10 @@ typedef struct {
     double thr_rel, thr_med;    /* local-maximum threshold: max(thr_rel*maxE, thr_med*medianE) */
     double tie_eta;             /* relative band inside which two energies count as tied */
     int b_min_log2, b_max_log2; /* tuning range of B (per axis in 2D); 0 = default */
+    int fixed_k;                /* 1: no tuning; B = the smallest power of two with B >= sqrt(n k)
+                                   (2D: B^2 >= N sqrt(k)) for k = k_hint, k* = k_hint      */
+    int est_reuse_loc;          /* 1: the estimation loops reuse the location hashes
+                                   (loops_est <= loops_loc) instead of fresh ones          */
 } orc_params;
 
 #define ORC_MAX_TRIALS 64

@@ -33,6 +33,7 @@ class OracleParams(C.Structure):
         ("filter_alpha", C.c_double), ("filter_tol", C.c_double),
         ("thr_rel", C.c_double), ("thr_med", C.c_double), ("tie_eta", C.c_double),
         ("b_min_log2", C.c_int), ("b_max_log2", C.c_int),
+        ("fixed_k", C.c_int), ("est_reuse_loc", C.c_int),
     ]
 
 

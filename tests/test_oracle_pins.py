@@ -453,3 +453,55 @@ def test_fixed_support_estimates_are_linear_and_equal_the_dft_on_sparse_inputs()
     lhs = O.estimates_1d(a * u + b * v, B, loc, seed=5)
     rhs = a * O.estimates_1d(u, B, loc, seed=5) + b * O.estimates_1d(v, B, loc, seed=5)
     assert np.abs(lhs - rhs).max() < 1e-9 * np.abs(rhs).max()
+
+
+def test_fixed_k_mode_bucket_count_and_recovery():
+    """Fixed-k mode (no tuning): B is the smallest power of two with B^2 >= n k (2D:
+    B^4 >= N^2 k), k* = the hint, and an exactly sparse input is recovered exactly."""
+    import oracle as O
+    from synth import sparse_signal_1d, sparse_signal_2d
+
+    for n, k, want in [(1 << 14, 16, 9), (1 << 14, 17, 10), (1 << 20, 1000, 15)]:
+        x = np.zeros(n, np.complex64)
+        r = O.atsfft_1d(x, k_hint=k, seed=1, params=O.default_params(fixed_k=1))
+        assert r.B_star == 1 << want and r.k_star == k and len(r.trials) == 0
+    r = O.atsfft_2d(np.zeros((256, 256), np.complex64), k_hint=10, seed=1,
+                    params=O.default_params(fixed_k=1))
+    assert r.B_star == 1 << 5   # N^2 k = 655360 -> ceil(log2) = 20 -> ceil(20/4) = 5
+    sig = sparse_signal_1d(1 << 12, 8, 5)
+    r = O.atsfft_1d(sig.x, k_hint=8, seed=5, params=O.default_params(fixed_k=1))
+    X = np.fft.fft(sig.x.astype(np.complex128))
+    assert r.loc.tolist() == sorted(sig.support.tolist())
+    assert np.abs(r.val - X[r.loc]).max() < 1e-6
+    sig2 = sparse_signal_2d(64, 5, 6)
+    r2 = O.atsfft_2d(sig2.x, k_hint=5, seed=6, params=O.default_params(fixed_k=1))
+    X2 = np.fft.fft2(sig2.x.astype(np.complex128)).ravel()
+    # the small fixed B of 2D (16 x 16 buckets for k = 5) lets a few preimages collect
+    # the votes too; the true support is all there, with exact values
+    true = np.isin(r2.loc, sig2.support)
+    assert true.sum() == len(sig2.support)
+    assert np.abs(r2.val - X2[r2.loc])[true].max() < 1e-6
+    assert O.atsfft_1d(sig.x, k_hint=0, seed=5, params=O.default_params(fixed_k=1)).status == 1
+
+
+def test_estimation_reusing_location_hashes():
+    """With est_reuse_loc the estimates come from the location hashes: an exactly sparse
+    input is still recovered exactly, the location stage is unchanged, and more
+    estimation than location loops is rejected."""
+    import oracle as O
+    from synth import sparse_signal_1d
+
+    sig = sparse_signal_1d(1 << 12, 8, 9)
+    a = O.atsfft_1d(sig.x, seed=9)
+    b = O.atsfft_1d(sig.x, seed=9, params=O.default_params(est_reuse_loc=1))
+    X = np.fft.fft(sig.x.astype(np.complex128))
+    assert a.loc.tolist() == b.loc.tolist() and a.k_star == b.k_star
+    # within the window's stop-band leakage (tolerance 1e-6 per neighbour coefficient)
+    assert np.abs(b.val - X[b.loc]).max() < 1e-5
+    # the reused estimates are exactly the location hashes' Eq. (11) values
+    est_loc = O.estimates_1d(sig.x, a.trials[-1][0], b.loc, seed=9,
+                             params=O.default_params(est_reuse_loc=1))
+    est_new = O.estimates_1d(sig.x, a.trials[-1][0], b.loc, seed=9)
+    assert not np.allclose(est_loc, est_new, atol=0, rtol=0)
+    bad = O.default_params(est_reuse_loc=1, loops_loc=5, loops_est=7)
+    assert O.atsfft_1d(sig.x, seed=9, params=bad).status == 1   # invalid argument
