@@ -479,7 +479,7 @@ def grad_workload(args):
             L.atsfft_exec_sel(p.handle, x, b["loc"], b["val"], b["msel"], cap, b["count"], b["k"],
                               b["status"], s)
         counts = [min(int(b["count"].item()), cap) for b in bufs]   # (synchronises)
-        Bs = [p.last_trace()[-1][0] for p in plans]
+        Bs = [L.atsfft_last_result(p.handle, s)[1] for p in plans]
         for p, b, c, B, t in zip(plans, bufs, counts, Bs, targets):
             g = 2.0 * (b["val"][:c] - t[:c])          # dL/dRe y + i dL/dIm y
             L.atsfft_estimate_adjoint(p.handle, B, b["loc"], b["msel"], c, g, b["gx"], s)
@@ -533,6 +533,10 @@ def main():
                          "this many CUDA streams (1 = in order)")
     ap.add_argument("--tune-stages", type=int, default=2, choices=[1, 2],
                     help="1D tuning in one batch (1) or small-window trials first (2)")
+    ap.add_argument("--est-reuse-loc", action="store_true",
+                    help="estimation loops reuse the location hashes (off: fresh hashes)")
+    ap.add_argument("--fixed-k", action="store_true",
+                    help="no tuning: B from the true k given as the hint (the SFFT setting)")
     ap.add_argument("--no-graph", action="store_true",
                     help="time per-signal execs on streams instead of one graph launch per step")
     ap.add_argument("--workload", default="headline", choices=["headline", "mixed512", "grad64"],
@@ -575,8 +579,9 @@ def main():
     # concurrent transforms (graph branches or streams): tails at one CTA per SM so that
     # several cooperative grids are resident together
     pp = A.params(coop_blocks_per_sm=1 if (nstreams > 1 or use_graph) else 0,
-                  tune_stages=args.tune_stages)
-    plans = [A.Plan((n,), params=pp, seed=SEED) for _ in sigs]
+                  tune_stages=args.tune_stages, est_reuse_loc=int(args.est_reuse_loc),
+                  fixed_k=int(args.fixed_k))
+    plans = [A.Plan((n,), params=pp, seed=SEED, k_hint=k if args.fixed_k else 0) for k in KS]
     outs = []
     for _ in sigs:
         outs.append(dict(loc=torch.empty(CAPACITY, dtype=torch.int64, device=dev),
@@ -756,7 +761,8 @@ def main():
                    "plain_path_transforms_per_s": plain_value,
                    "plain_path_ms_per_step": float(np.mean(plain_ms)),
                    "k_star": kstar, "counts": counts, "status": status,
-                   "tune_stages": args.tune_stages,
+                   "tune_stages": args.tune_stages, "est_reuse_loc": bool(args.est_reuse_loc),
+                   "fixed_k": bool(args.fixed_k),
                    "path": ("one CUDA graph per step (atsfft_batch_launch), a branch per signal"
                             if use_graph else
                             "plain per-signal path (one exec per transform)" if nstreams == 1 else

@@ -66,6 +66,12 @@ typedef struct {
                                    gather-form windows first and the residue-stream trials
                                    only if the controller has not stopped; 1 evaluates
                                    every trial in one batch.  Same results either way     */
+    int fixed_k;                /* 1: no tuning (the SFFT setting): B is the smallest power of
+                                   two with B^2 >= n k (2D: B^4 >= N^2 k) for k = k_hint,
+                                   which must then be > 0; k* = k_hint.  0 (default): tune */
+    int est_reuse_loc;          /* 1: the estimation loops reuse the location hashes
+                                   (requires loops_est <= loops_loc): half the binning and
+                                   FFT work at B*.  0 (default): fresh estimation hashes  */
 } atsfft_params;
 
 /* Fills *p with the defaults listed above. */
@@ -133,6 +139,10 @@ atsfft_status atsfft_window_response(atsfft_plan_t plan, int64_t B, double *h_re
  * max_trials, and the number of trials.  Synchronises `stream`. */
 atsfft_status atsfft_last_trace(atsfft_plan_t plan, int64_t *h_B, int64_t *h_k, int max_trials,
                                 int *h_ntrials, void *stream);
+
+/* After an exec: B* (per axis in 2D) and k* of the last transform of this plan
+ * (synchronises `stream`). */
+atsfft_status atsfft_last_result(atsfft_plan_t plan, int64_t *h_B, int64_t *h_k, void *stream);
 
 /* Turns per-phase CUDA events on (1) or off (0) for later execs of this plan.  The ten
  * phases of one exec, in order: 0 binning of the first tuning stage (1D: the trials with

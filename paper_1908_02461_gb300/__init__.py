@@ -31,6 +31,7 @@ from ._lib import (  # noqa: F401
     atsfft_exec_2d,
     atsfft_hash_spectrum,
     atsfft_hash_spectrum_noalloc,
+    atsfft_last_result,
     atsfft_last_trace,
     atsfft_params,
     atsfft_phase_times,
@@ -148,7 +149,9 @@ class Plan:
             raise ATSFFTError(st, "atsfft_exec_sel")
         n = int(count.item())
         m = min(n, cap)
-        B = self.last_trace()[-1][0]
+        st, B, _ = atsfft_last_result(self.handle, torch.cuda.current_stream().cuda_stream)
+        if st != OK:
+            raise ATSFFTError(st, "atsfft_last_result")
         return loc[:m], val[:m], msel[:m], B, int(k.item()), int(status.item()), n
 
     def estimate_apply(self, B: int, u, loc, msel):

@@ -31,6 +31,7 @@ class atsfft_params(C.Structure):
         ("b_min_log2", C.c_int), ("b_max_log2", C.c_int),
         ("coop_blocks_per_sm", C.c_int),
         ("tune_stages", C.c_int),
+        ("fixed_k", C.c_int), ("est_reuse_loc", C.c_int),
     ]
 
 
@@ -40,7 +41,7 @@ EXPORTED = ["atsfft_default_params", "atsfft_plan", "atsfft_exec", "atsfft_exec_
             "atsfft_phase_times", "atsfft_tail_stamps", "atsfft_hash_spectrum_noalloc",
             "atsfft_batch_create", "atsfft_batch_launch", "atsfft_batch_kernels",
             "atsfft_batch_destroy", "atsfft_plan_clone", "atsfft_exec_sel",
-            "atsfft_estimate_apply", "atsfft_estimate_adjoint"]
+            "atsfft_estimate_apply", "atsfft_estimate_adjoint", "atsfft_last_result"]
 
 PHASES = ["tune1_bin", "tune1_fft", "tune1_tail", "tune2_bin", "tune2_fft", "tune2_tail",
           "le_bin_stream", "le_bin_gather", "le_fft", "loc_tail"]
@@ -85,6 +86,8 @@ def load(path: str | None = None):
     L.atsfft_tail_stamps.restype = i32
     L.atsfft_hash_spectrum_noalloc.argtypes = [vp, i64, i64, u64, i32, i32, vp, vp]
     L.atsfft_hash_spectrum_noalloc.restype = i32
+    L.atsfft_last_result.argtypes = [vp, P(i64), P(i64), vp]
+    L.atsfft_last_result.restype = i32
     L.atsfft_exec_sel.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp, vp, vp]
     L.atsfft_exec_sel.restype = i32
     L.atsfft_estimate_apply.argtypes = [vp, i64, vp, vp, vp, i64, vp, vp]
@@ -241,3 +244,10 @@ def atsfft_estimate_apply(plan, B, d_u, d_loc, d_medsel, count, d_out, stream=No
 def atsfft_estimate_adjoint(plan, B, d_loc, d_medsel, count, d_gval, d_gx, stream=None) -> int:
     return load().atsfft_estimate_adjoint(plan, B, _ptr(d_loc), _ptr(d_medsel), count,
                                           _ptr(d_gval), _ptr(d_gx), _ptr(stream))
+
+
+def atsfft_last_result(plan, stream=None):
+    """Returns (status, B*, k*) of the plan's last transform."""
+    B, k = C.c_int64(), C.c_int64()
+    st = load().atsfft_last_result(plan, C.byref(B), C.byref(k), _ptr(stream))
+    return st, B.value, k.value

@@ -155,7 +155,7 @@ static atsfft_status est_args(const atsfft_plan_s *P, int64_t B, const int64_t *
     E->loc = d_loc;
     E->msel = d_msel;
     E->count = count;
-    E->est = P->d_le + P->L_loc;
+    E->est = P->d_le + P->est_base;
     E->L_est = P->L_est;
     E->logn = P->logn;
     E->logB = b;

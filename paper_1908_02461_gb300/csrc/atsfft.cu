@@ -35,14 +35,19 @@ static atsfft_status exec_common(atsfft_plan_t P, int ndim, const void *d_x, int
     P->launches = 0;
     launch_reset(P, s);
     prof_mark(P, 0, s);
-    launch_tuning(P, x, 1, s);    // marks phase 1 between its binning and its FFTs
-    prof_mark(P, 2, s);
-    launch_tune_tail(P, 1, s);
-    prof_mark(P, 3, s);
-    launch_tuning(P, x, 2, s);    // marks phase 4
-    prof_mark(P, 5, s);
-    launch_tune_tail(P, 2, s);
-    prof_mark(P, 6, s);
+    if (P->p.fixed_k) {
+        launch_fixed_setup(P, s);   // B* and k* from the plan: the tuning phases are empty
+        for (int i = 1; i <= 6; i++) prof_mark(P, i, s);
+    } else {
+        launch_tuning(P, x, 1, s);  // marks phase 1 between its binning and its FFTs
+        prof_mark(P, 2, s);
+        launch_tune_tail(P, 1, s);
+        prof_mark(P, 3, s);
+        launch_tuning(P, x, 2, s);  // marks phase 4
+        prof_mark(P, 5, s);
+        launch_tune_tail(P, 2, s);
+        prof_mark(P, 6, s);
+    }
     const Job *jd = &P->d_state->job;
     launch_le_bin(P, x, jd, s);   // marks phase 7 after the stream-form kernel
     prof_mark(P, 8, s);
@@ -115,6 +120,22 @@ extern "C" atsfft_status atsfft_last_trace(atsfft_plan_t P, int64_t *h_B, int64_
         h_B[i] = st.trial_B[i];
         h_k[i] = st.trial_k[i];
     }
+    return ATSFFT_OK;
+}
+
+extern "C" atsfft_status atsfft_last_result(atsfft_plan_t P, int64_t *h_B, int64_t *h_k,
+                                            void *stream)
+{
+    if (!P || !h_B || !h_k) return ATSFFT_E_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    int32_t b = 0;
+    int64_t k = 0;
+    e = cudaMemcpy(&b, &P->d_state->b_star, sizeof(b), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&k, &P->d_state->k_star, sizeof(k), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    *h_B = (int64_t)1 << b;
+    *h_k = k;
     return ATSFFT_OK;
 }
 

@@ -642,7 +642,7 @@ void launch_tuning(const atsfft_plan_s *P, const float2 *x, int stage, cudaStrea
 // one matching the job runs.  1D stream launches take at most kMaxStream hashes each.
 void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, cudaStream_t s)
 {
-    const int nh = P->L_loc + P->L_est;
+    const int nh = P->nh_le;
     if (P->ndim == 1) {
         // shared memory for the R_u table of the smallest B the stream form can take
         size_t smem = 16;
@@ -722,7 +722,7 @@ int launch_est_bin(const atsfft_plan_s *P, const float2 *x, int b, cudaStream_t 
             S.logR = b;
             S.chunks = j.chunks;
             for (int g = 0; g < S.nh; g++) {
-                S.h[g] = stream_hash(P, P->h_le[P->L_loc + g0 + g], b,
+                S.h[g] = stream_hash(P, P->h_le[P->est_base + g0 + g], b,
                                      ((int64_t)(g0 + g) * j.chunks) << b);
                 S.h[g].rot_off = 0;   // one B: every hash's R_u table is the same
             }
@@ -732,7 +732,7 @@ int launch_est_bin(const atsfft_plan_s *P, const float2 *x, int b, cudaStream_t 
         return j.chunks;
     }
     dim3 grid(P->num_sms * kPersistCtas, (L + kGroup - 1) / kGroup);
-    k_bin_gather_1d<<<grid, 256, 0, s>>>(x, P->logn, P->d_le + P->L_loc, L, P->d_win, nullptr, b,
+    k_bin_gather_1d<<<grid, 256, 0, s>>>(x, P->logn, P->d_le + P->est_base, L, P->d_win, nullptr, b,
                                          P->d_part);
     count_launch(P);
     return 1;

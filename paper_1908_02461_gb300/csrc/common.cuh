@@ -120,6 +120,9 @@ struct atsfft_plan_s {
     uint64_t seed;
     int b_lo, b_hi, b0;
     int64_t k_hint;
+    int b_fixed;           // fixed-k mode: log2 B (per axis)
+    int est_base;          // index of the first estimation hash in h_le / d_le
+    int nh_le;             // location + estimation hashes binned at B* (distinct ones)
     int L_loc, L_est;
     int device;
     int num_sms;
@@ -218,6 +221,7 @@ void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB,
 
 // tail.cu
 void launch_tune_tail(const atsfft_plan_s *P, int stage, cudaStream_t s);
+void launch_fixed_setup(const atsfft_plan_s *P, cudaStream_t s);   // fixed-k mode
 void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, uint8_t *d_msel,
                      int64_t capacity, int64_t *d_count, int64_t *d_k, int32_t *d_status,
                      cudaStream_t s);

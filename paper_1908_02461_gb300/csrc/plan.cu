@@ -251,6 +251,8 @@ extern "C" void atsfft_default_params(atsfft_params *p)
     p->b_max_log2 = 0;
     p->coop_blocks_per_sm = 0;
     p->tune_stages = 2;
+    p->fixed_k = 0;
+    p->est_reuse_loc = 0;
 }
 
 extern "C" const char *atsfft_status_string(atsfft_status s)
@@ -280,6 +282,9 @@ static bool params_ok(const atsfft_params *p)
     if (!(p->thr_rel >= 0 && p->thr_med >= 0 && p->tie_eta >= 0 && p->tie_eta < 1)) return false;
     if (p->coop_blocks_per_sm < 0 || p->coop_blocks_per_sm > 8) return false;
     if (p->tune_stages != 1 && p->tune_stages != 2) return false;
+    if (p->fixed_k != 0 && p->fixed_k != 1) return false;
+    if (p->est_reuse_loc != 0 && p->est_reuse_loc != 1) return false;
+    if (p->est_reuse_loc && p->loops_est > p->loops_loc) return false;
     return true;
 }
 
@@ -312,6 +317,7 @@ static atsfft_status plan_create(atsfft_plan_t *out, int ndim, const int64_t *sh
     if (!out) return ATSFFT_E_INVALID_ARG;
     *out = nullptr;
     if (!shape || (ndim != 1 && ndim != 2) || k_hint < 0) return ATSFFT_E_INVALID_ARG;
+    if (shape[0] > 0 && k_hint > (ndim == 1 ? shape[0] : shape[0] * shape[0])) return ATSFFT_E_INVALID_ARG;
     atsfft_params p;
     if (pp)
         p = *pp;
@@ -356,7 +362,22 @@ static atsfft_status plan_create(atsfft_plan_t *out, int ndim, const int64_t *sh
 
     for (int b = P->b0; b <= P->b_hi; b++) hash_params_for(seed, 0, b, n, ndim, &P->h_tune[b]);
     for (int l = 0; l < P->L_loc; l++) hash_params_for(seed, 1, l, n, ndim, &P->h_le[l]);
-    for (int l = 0; l < P->L_est; l++) hash_params_for(seed, 2, l, n, ndim, &P->h_le[P->L_loc + l]);
+    P->est_base = p.est_reuse_loc ? 0 : P->L_loc;
+    P->nh_le = p.est_reuse_loc ? P->L_loc : P->L_loc + P->L_est;
+    if (!p.est_reuse_loc)
+        for (int l = 0; l < P->L_est; l++) hash_params_for(seed, 2, l, n, ndim, &P->h_le[P->L_loc + l]);
+    if (p.fixed_k) {
+        // B^2 >= n k (1D) or B^4 >= N^2 k (2D), clamped to the range
+        if (k_hint <= 0) {
+            delete P;
+            return ATSFFT_E_INVALID_ARG;
+        }
+        const int m = ilog2_ceil(ndim == 1 ? n * k_hint : n * n * k_hint);
+        int bf = ndim == 1 ? (m + 1) / 2 : (m + 3) / 4;
+        if (bf < P->b_lo) bf = P->b_lo;
+        if (bf > P->b_hi) bf = P->b_hi;
+        P->b_fixed = bf;
+    }
 
     // ---- allocations ----
     atsfft_status st = ATSFFT_OK;
@@ -376,7 +397,7 @@ static atsfft_status plan_create(atsfft_plan_t *out, int ndim, const int64_t *sh
     }
     for (int b = P->b0; b <= P->b_hi; b++) P->h_tjob[b] = make_job(P, b, 1);
     int64_t nb_max = ndim == 1 ? ((int64_t)1 << P->b_hi) : ((int64_t)1 << (2 * P->b_hi));
-    int nh_le = P->L_loc + P->L_est;
+    int nh_le = P->nh_le;
     // partials: largest of (tuning single hash, location + estimation) x chunks
     size_t part = 0;
     for (int b = P->b0; b <= P->b_hi; b++) {

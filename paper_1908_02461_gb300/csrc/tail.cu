@@ -22,6 +22,7 @@
 // returns at its next barrier (cooperative launch makes all blocks co-resident, so a
 // timeout means the device misbehaved, not a lost block).
 #include <math.h>
+#include <string.h>
 
 #include "devmath.cuh"
 
@@ -567,6 +568,36 @@ struct TuneTailArgs {
     ExecState *state;
 };
 
+// Records B* = 2^b and k* for the location stage: the state words, the job at B* (all
+// nh_le hashes) and the statistics jobs of the location hashes.
+__device__ void publish_bstar(const TuneTailArgs &A, int b, int64_t k, int status, int empty,
+                              int ntrials)
+{
+    ExecState *state = A.state;
+    state->ntrials = ntrials;
+    state->b_star = b;
+    state->k_star = k;
+    state->status = status;
+    state->empty = empty;
+    state->tune_done = 1;
+    Job j = A.tjob[b];
+    j.nh = A.nh_le;
+    j.active = !empty;
+    state->job = j;
+    const int64_t nb = nb_of(A.S.ndim, b);
+    for (int l = 0; l < A.L_loc; l++) {
+        StatJob s;
+        s.spec = A.z + (int64_t)l * nb;
+        s.energy = A.e_loc + (int64_t)l * nb;
+        s.hash = A.le + l;
+        s.logB = b;
+        s.slot = kMaxLogB + l;
+        s.list = l;
+        s.active = !empty;
+        A.lstat[l] = s;
+    }
+}
+
 // One thread walks the trials B0, 2 B0, ... through Eq. (12) and Eq. (14) until the
 // stop reading: the first trial with r < delta2 (keep branch, or halve branch onto the
 // already evaluated B/2); r = inf when either count is 0; a trial whose energies are
@@ -606,29 +637,14 @@ __device__ void controller(const TuneTailArgs &A)
         kprev = k;
         b++;
     }
-    state->tune_done = 1;
     if (k == 0) empty = 1;
-    state->ntrials = trial + 1;
-    state->b_star = b;
-    state->k_star = k;
-    state->status = status;
-    state->empty = empty;
-    Job j = A.tjob[b];
-    j.nh = A.nh_le;
-    j.active = !empty;
-    state->job = j;
-    const int64_t nb = nb_of(A.S.ndim, b);
-    for (int l = 0; l < A.L_loc; l++) {
-        StatJob s;
-        s.spec = A.z + (int64_t)l * nb;
-        s.energy = A.e_loc + (int64_t)l * nb;
-        s.hash = A.le + l;
-        s.logB = b;
-        s.slot = kMaxLogB + l;
-        s.list = l;
-        s.active = !empty;
-        A.lstat[l] = s;
-    }
+    publish_bstar(A, b, k, status, empty, trial + 1);
+}
+
+// Fixed-k mode: B* and k* come from the plan (no trials); one thread.
+__global__ void k_fixed_setup(const TuneTailArgs A, int b, int64_t k)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) publish_bstar(A, b, k, A.state->status, 0, 0);
 }
 
 __global__ void __launch_bounds__(256, 2) k_tune_tail(const TuneTailArgs A)
@@ -650,6 +666,7 @@ struct LocTailArgs {
     StatsParams S;
     const StatJob *jobs;    // the location jobs at B*, written by the controller
     int L_loc, L_est;
+    int est_base;           // first estimation hash in le / z (0 when they reuse location's)
     int est_group;          // lanes per coordinate in the estimates: power of two >= L_est
     float eta_up, eta_dn;
     int32_t *sel;           // [L_loc][S.cap] selected buckets per location hash
@@ -788,9 +805,9 @@ __device__ void topnum_block(const StatJob &J, const LocTailArgs &A, int64_t num
 __device__ float2 estimate_term(uint64_t coord, const LocTailArgs &A, int b, int l)
 {
     const int64_t nb = nb_of(A.S.ndim, b);
-    const float2 *Pz = A.z + (int64_t)(A.L_loc + l) * nb;
+    const float2 *Pz = A.z + (int64_t)(A.est_base + l) * nb;
     int64_t idx;
-    const float2 c = estimate_coef(coord, A.le[A.L_loc + l], A.S.ndim, A.logn, b,
+    const float2 c = estimate_coef(coord, A.le[A.est_base + l], A.S.ndim, A.logn, b,
                                    A.rgain + A.ro.off[b], A.phase, A.phase_s, &idx);
     return cmul(Pz[idx], c);
 }
@@ -1343,30 +1360,44 @@ static int coop_grid(const atsfft_plan_s *P, const void *fn)
     return P->num_sms * per_sm;
 }
 
-void launch_tune_tail(const atsfft_plan_s *P, int stage, cudaStream_t s)
+static TuneTailArgs tune_args(const atsfft_plan_s *P)
 {
-    // the stage's trials: stat jobs are ordered by log2 B from b0
-    const int first = stage == 1 ? 0 : P->tune_split + 1 - P->b0;
-    const int last = stage == 1 ? P->tune_split - P->b0 : P->ntstat - 1;
-    if (first > last) return;
     TuneTailArgs A;
+    memset(&A, 0, sizeof(A));
     A.S = stats_params(P);
-    A.jobs = P->d_tstat + first;
-    A.njobs = last - first + 1;
-    A.stage = stage;
-    A.limit_b = stage == 1 ? P->tune_split : P->b_hi;
     A.b0 = P->b0;
     A.b_hi = P->b_hi;
     A.tune_max = P->p.tune_max;
     A.delta2 = P->p.delta2;
     A.tjob = P->d_tjob;
-    A.nh_le = P->L_loc + P->L_est;
+    A.nh_le = P->nh_le;
     A.L_loc = P->L_loc;
     A.lstat = P->d_lstat;
     A.z = P->d_z;
     A.e_loc = P->d_energy + P->e_loc_off;
     A.le = P->d_le;
     A.state = P->d_state;
+    return A;
+}
+
+void launch_fixed_setup(const atsfft_plan_s *P, cudaStream_t s)
+{
+    const TuneTailArgs A = tune_args(P);
+    k_fixed_setup<<<1, 32, 0, s>>>(A, P->b_fixed, P->k_hint);
+    count_launch(P);
+}
+
+void launch_tune_tail(const atsfft_plan_s *P, int stage, cudaStream_t s)
+{
+    // the stage's trials: stat jobs are ordered by log2 B from b0
+    const int first = stage == 1 ? 0 : P->tune_split + 1 - P->b0;
+    const int last = stage == 1 ? P->tune_split - P->b0 : P->ntstat - 1;
+    if (first > last) return;
+    TuneTailArgs A = tune_args(P);
+    A.jobs = P->d_tstat + first;
+    A.njobs = last - first + 1;
+    A.stage = stage;
+    A.limit_b = stage == 1 ? P->tune_split : P->b_hi;
     const void *fn = (const void *)k_tune_tail;
     launch_coop(fn, coop_grid(P, fn), &A, s);
     count_launch(P);
@@ -1381,6 +1412,7 @@ void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, uint
     A.jobs = P->d_lstat;
     A.L_loc = P->L_loc;
     A.L_est = P->L_est;
+    A.est_base = P->est_base;
     A.est_group = 1;
     while (A.est_group < P->L_est) A.est_group *= 2;
     A.eta_up = (float)(1.0 + P->p.tie_eta);

@@ -266,3 +266,32 @@ def test_exec_argument_errors(A):
     assert A.atsfft_exec_2d(plan.handle, x, out, out, 4, out, out, out, None) == A.E_INVALID_ARG
     assert A.atsfft_exec(plan.handle, 0, out, out, 4, out, out, out, None) == A.E_INVALID_ARG
     plan.close()
+
+
+# --------------------------------------------------------------------------
+# Modes: fixed-k (no tuning) and estimation reusing the location hashes
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,k,seed,snr", [(1 << 14, 16, 2, None), (1 << 22, 1000, 2000, 40.0)])
+def test_fixed_k_mode(A, O, n, k, seed, snr):
+    from synth import sparse_signal_1d
+
+    sig = sparse_signal_1d(n, k, seed, snr_db=snr)
+    info, _ = _check_transform(A, O, sig.x, 7, 1, params_kw={"fixed_k": 1}, k_hint=k)
+    assert info["k_gpu"] == k
+
+
+def test_fixed_k_mode_2d(A, O):
+    from synth import sparse_signal_2d
+
+    sig = sparse_signal_2d(256, 10, 4)
+    info, _ = _check_transform(A, O, sig.x, 4, 2, params_kw={"fixed_k": 1}, k_hint=10)
+    assert info["k_gpu"] == 10
+
+
+@pytest.mark.parametrize("n,k,seed,snr", [(1 << 14, 16, 3, None), (1 << 22, 200, 1200, 40.0)])
+def test_estimation_reusing_location_hashes(A, O, n, k, seed, snr):
+    from synth import sparse_signal_1d
+
+    sig = sparse_signal_1d(n, k, seed, snr_db=snr)
+    _check_transform(A, O, sig.x, 7, 1, params_kw={"est_reuse_loc": 1})
