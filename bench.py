@@ -257,12 +257,15 @@ def roofline(per_signal, traces, n):
 
     rows = {}
     for k, ph in per_signal.items():
+        # the trace's last trial is B*; an empty trace (fixed-k mode) carries B* alone
         Bstar = traces[k][-1][0]
-        stage2 = max(b for b, _ in traces[k]) > split
+        stage2 = len(traces[k]) > 1 and max(b for b, _ in traces[k]) > split
+        tuned = len(traces[k]) > 1 or traces[k][0][1] is not None
         model = {}
-        model["tune1_bin"] = ("hbm", sum(8 * (2 * _window_h(n, B) + 1) + 8 * B for B in gB))
-        model["tune1_fft"] = ("hbm", sum(fft_bytes(B, 1) for B in gB))
-        model["tune1_tail"] = ("hbm", sum(4 * B + 4 * B for B in gB))
+        if tuned:
+            model["tune1_bin"] = ("hbm", sum(8 * (2 * _window_h(n, B) + 1) + 8 * B for B in gB))
+            model["tune1_fft"] = ("hbm", sum(fft_bytes(B, 1) for B in gB))
+            model["tune1_tail"] = ("hbm", sum(4 * B + 4 * B for B in gB))
         if sB and stage2:
             R = max(sB)
             model["tune2_bin"] = ("alu", len(sB) * n)
@@ -688,7 +691,12 @@ def main():
     bin_ms = {k: per_signal[k]["le_bin_stream"] + per_signal[k]["le_bin_gather"] for k in KS}
     tune_stage2 = {k: per_signal[k]["tune2_bin"] + per_signal[k]["tune2_fft"] + per_signal[k]["tune2_tail"]
                    for k in KS}
-    traces = {k: p.last_trace() for k, p in zip(KS, plans)}
+    traces = {}
+    for k, p in zip(KS, plans):
+        tr = p.last_trace()
+        if not tr:   # fixed-k mode: no trials, B* from the plan's last result
+            tr = [(A._lib.atsfft_last_result(p.handle)[1], None)]
+        traces[k] = tr
     roof, phase_rooflines = roofline(per_signal, traces, n)
 
     # ---- end to end through the C ABI with host buffers -----------------------------
