@@ -92,6 +92,56 @@ __device__ __forceinline__ void group_stages(float2 (&v)[1 << R], int q, int lm0
     }
 }
 
+// The three radix-2 stages of a group of 8 (positions base + q + j 2^(lm0-1)) with the
+// twiddles factored: stage s uses W_(2^(lm0+s))^q times W_(2^(s+1))^(j0 mod 2^s), and
+// W_(2^(lm0+s))^q = t2^(2^(2-s)) with t2 = W_(2^(lm0+2))^q, so one table entry (t2) and
+// the constants 1, -i, W_8, -i W_8 give all twelve butterfly twiddles.
+__device__ __forceinline__ float2 mul_mi(float2 b) { return make_float2(b.y, -b.x); }   // -i b
+
+__device__ __forceinline__ void bfly(float2 &a, float2 &b, float2 wb)
+{
+    b = make_float2(a.x - wb.x, a.y - wb.y);
+    a = make_float2(a.x + wb.x, a.y + wb.y);
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ void radix8_stages(float2 (&v)[8], float2 t2)
+{
+    constexpr float r2 = 0.70710678118654752440f;
+    const float2 t1 = cmulf(t2, t2), t0 = cmulf(t1, t1);
+    const float2 t2w = make_float2((t2.x + t2.y) * r2, (t2.y - t2.x) * r2);   // t2 W_8
+#pragma unroll
+    for (int j0 = 0; j0 < 8; j0 += 2) bfly(v[j0], v[j0 + 1], cmulf(t0, v[j0 + 1]));
+    bfly(v[0], v[2], cmulf(t1, v[2]));
+    bfly(v[1], v[3], mul_mi(cmulf(t1, v[3])));
+    bfly(v[4], v[6], cmulf(t1, v[6]));
+    bfly(v[5], v[7], mul_mi(cmulf(t1, v[7])));
+    bfly(v[0], v[4], cmulf(t2, v[4]));
+    bfly(v[1], v[5], cmulf(t2w, v[5]));
+    bfly(v[2], v[6], mul_mi(cmulf(t2, v[6])));
+    bfly(v[3], v[7], mul_mi(cmulf(t2w, v[7])));
+}
+
+// The same for q = 0 (the first three stages): all twiddles are 1, -i, W_8 or -i W_8.
+__device__ __forceinline__ void radix8_first(float2 (&v)[8])
+{
+    constexpr float r2 = 0.70710678118654752440f;
+#pragma unroll
+    for (int j0 = 0; j0 < 8; j0 += 2) bfly(v[j0], v[j0 + 1], v[j0 + 1]);
+    bfly(v[0], v[2], v[2]);
+    bfly(v[1], v[3], mul_mi(v[3]));
+    bfly(v[4], v[6], v[6]);
+    bfly(v[5], v[7], mul_mi(v[7]));
+    bfly(v[0], v[4], v[4]);
+    bfly(v[1], v[5], make_float2((v[5].x + v[5].y) * r2, (v[5].y - v[5].x) * r2));
+    bfly(v[2], v[6], mul_mi(v[6]));
+    bfly(v[3], v[7], make_float2((v[7].y - v[7].x) * r2, -(v[7].x + v[7].y) * r2));
+}
+
 // First group of stages (lm0 = 1): the inputs sit in natural order in shared memory and
 // the group at bit-reversed positions g 2^R + j reads natural index bitrev(g 2^R + j) of
 // its transform.  Every thread reads its group before any thread writes (the positions
@@ -116,7 +166,10 @@ __device__ __forceinline__ void first_stages(float2 *sm, int TP, int logP,
     }
     __syncthreads();
     if (have) {
-        group_stages<R>(v, 0, 1, tw);
+        if constexpr (R == 3)
+            radix8_first(v);
+        else
+            group_stages<R>(v, 0, 1, tw);
 #pragma unroll
         for (int j = 0; j < E; j++) sm[padi(g * E + j)] = v[j];
     }
@@ -136,7 +189,10 @@ __device__ __forceinline__ void next_stages(float2 *sm, int TP, int lm0,
         float2 v[E];
 #pragma unroll
         for (int j = 0; j < E; j++) v[j] = sm[padi(base + j * half)];
-        group_stages<R>(v, q, lm0, tw);
+        if constexpr (R == 3)
+            radix8_stages(v, __ldg(&tw[q * (kSmallFFT >> (lm0 + 2))]));
+        else
+            group_stages<R>(v, q, lm0, tw);
 #pragma unroll
         for (int j = 0; j < E; j++) sm[padi(base + j * half)] = v[j];
     }
