@@ -1119,9 +1119,9 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
     }
     __syncthreads();
     {
-        // four preimages per thread per round: their buckets and the other hashes' bitmap
-        // words are all requested before any is used
-        constexpr int kU = 4;
+        // one preimage per thread per round (wider rounds measured slower: register and
+        // memory-queue pressure); its bitmap words in all hashes are requested at once
+        constexpr int kU = 1;
         const int64_t total = off[L_cand];
         for (int64_t it0 = (int64_t)blockIdx.x * blockDim.x; it0 < total; it0 += kU * gthreads) {
             uint32_t coord[kU], cb[kU], qv[kU];
