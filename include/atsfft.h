@@ -72,6 +72,12 @@ typedef struct {
     int est_reuse_loc;          /* 1: the estimation loops reuse the location hashes
                                    (requires loops_est <= loops_loc): half the binning and
                                    FFT work at B*.  0 (default): fresh estimation hashes  */
+    int precision;              /* 0 (default): complex64 input and values, FP32 path.
+                                   1 (1D only): complex128 input and values; locations
+                                   as in the FP32 path (on the input rounded to complex64),
+                                   the estimation stage in FP64 (Eq. (11) values to
+                                   ~1e-12 of an FP64 evaluation).  Slow: FP64 runs at
+                                   1/64 of the FP32 rate on GB300                         */
 } atsfft_params;
 
 /* Fills *p with the defaults listed above. */

@@ -74,6 +74,8 @@ class Plan:
         self.handle = h
         self.device = torch.device("cuda", torch.cuda.current_device())
         self._scalars = torch.zeros(3, dtype=torch.int64, device=self.device)
+        # input and value dtype: complex128 for the FP64 path
+        self.dtype = torch.complex128 if (params is not None and params.precision == 1) else torch.complex64
 
     def clone(self) -> "Plan":
         """A plan with the same tables and its own scratch (atsfft_plan_clone)."""
@@ -84,6 +86,7 @@ class Plan:
             raise ATSFFTError(st, "atsfft_plan_clone")
         other = Plan.__new__(Plan)
         other.shape, other.ndim, other.handle, other.device = self.shape, self.ndim, h, self.device
+        other.dtype = self.dtype
         other._scalars = torch.zeros(3, dtype=torch.int64, device=self.device)
         return other
 
@@ -112,13 +115,13 @@ class Plan:
         """Transform x (complex64 CUDA tensor); returns (loc, val, k_star, status, count) after sync."""
         import torch
 
-        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
-            raise ValueError("x must be a contiguous complex64 CUDA tensor")
+        if x.dtype != self.dtype or not x.is_cuda or not x.is_contiguous():
+            raise ValueError(f"x must be a contiguous {self.dtype} CUDA tensor")
         if tuple(x.shape) != self.shape:
             raise ValueError(f"x has shape {tuple(x.shape)}, plan expects {self.shape}")
         cap = capacity if capacity is not None else 1 << 16
         loc = torch.empty(cap, dtype=torch.int64, device=x.device)
-        val = torch.empty(cap, dtype=torch.complex64, device=x.device)
+        val = torch.empty(cap, dtype=self.dtype, device=x.device)
         count = torch.zeros(1, dtype=torch.int64, device=x.device)
         k = torch.zeros(1, dtype=torch.int64, device=x.device)
         status = torch.zeros(1, dtype=torch.int32, device=x.device)

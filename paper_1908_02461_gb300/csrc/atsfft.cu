@@ -33,6 +33,12 @@ static atsfft_status exec_common(atsfft_plan_t P, int ndim, const void *d_x, int
     const float2 *x = (const float2 *)d_x;
     cudaGetLastError();   // clear a stale error so the status below is this call's
     P->launches = 0;
+    const bool fp64 = P->p.precision == 1;
+    if (fp64) {
+        if (d_msel) return ATSFFT_E_INVALID_ARG;   // selections belong to the FP32 estimates
+        launch_to_f32(P, d_x, s);
+        x = P->d_x32;
+    }
     launch_reset(P, s);
     prof_mark(P, 0, s);
     if (P->p.fixed_k) {
@@ -54,6 +60,7 @@ static atsfft_status exec_common(atsfft_plan_t P, int ndim, const void *d_x, int
     launch_bucket_fft_dynamic(P, jd, P->d_part, P->d_z, P->d_energy + P->e_loc_off, P->L_loc, s);
     prof_mark(P, 9, s);
     launch_loc_tail(P, d_loc, (float2 *)d_val, d_msel, capacity, d_count, d_k, d_status, s);
+    if (fp64) launch_estimate_fp64(P, d_x, d_loc, d_val, capacity, s);
     prof_mark(P, 10, s);
     return cuda_status(cudaGetLastError());
 }

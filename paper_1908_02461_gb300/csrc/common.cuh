@@ -58,6 +58,11 @@ struct Job {
     int32_t pad[3];
 };
 
+// Offsets of each B's table in the plan's concatenated Ghat' tables (by log2 B).
+struct RespOffsets {
+    int64_t off[kMaxLogB];
+};
+
 // One hash's spectrum for the energy / threshold / local-maximum kernels.
 struct StatJob {
     const float2 *spec;    // P (residue-order FFT output), B or B^2 values
@@ -123,6 +128,10 @@ struct atsfft_plan_s {
     int b_fixed;           // fixed-k mode: log2 B (per axis)
     int est_base;          // index of the first estimation hash in h_le / d_le
     int nh_le;             // location + estimation hashes binned at B* (distinct ones)
+    // FP64 path (precision 1): FP32 copy of the input, FP64 estimation spectra (two
+    // Stockham buffers, [L_est][B*]) and their twiddles
+    float2 *d_x32;
+    double2 *d_f64a, *d_f64b, *d_tw64;
     int L_loc, L_est;
     int device;
     int num_sms;
@@ -222,6 +231,11 @@ void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB,
 // tail.cu
 void launch_tune_tail(const atsfft_plan_s *P, int stage, cudaStream_t s);
 void launch_fixed_setup(const atsfft_plan_s *P, cudaStream_t s);   // fixed-k mode
+
+// fp64.cu (precision 1)
+void launch_to_f32(const atsfft_plan_s *P, const void *d_x, cudaStream_t s);
+void launch_estimate_fp64(const atsfft_plan_s *P, const void *d_x, const int64_t *d_loc,
+                          void *d_val, int64_t capacity, cudaStream_t s);
 void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, uint8_t *d_msel,
                      int64_t capacity, int64_t *d_count, int64_t *d_k, int32_t *d_status,
                      cudaStream_t s);

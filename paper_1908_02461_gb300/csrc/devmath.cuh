@@ -92,4 +92,17 @@ __device__ __forceinline__ float2 estimate_coef(uint64_t coord, const HashParam 
     return make_float2(w.x * rg, w.y * rg);
 }
 
+// Unnormalised tap T_t = exp(-t^2/(2 s^2)) * box(t), box(0) = D, box(t) = sin(pi t/B)/(pi t/n),
+// with sin(pi t / B) reduced exactly in integers.
+__device__ __forceinline__ double window_term(int64_t t, int64_t n, int logB, double s)
+{
+    int64_t B = (int64_t)1 << logB;
+    double env = exp(-((double)t * (double)t) / (2.0 * s * s));
+    if (t == 0) return env * (double)(n >> logB);
+    int64_t r = t % (2 * B);
+    if (r < 0) r += 2 * B;
+    double sn = (r == 0 || r == B) ? 0.0 : sinpi((double)r / (double)B);
+    return env * sn / (M_PI * (double)t / (double)n);
+}
+
 }  // namespace atsfft

@@ -6,7 +6,7 @@
 
 #include <new>
 
-#include "common.cuh"
+#include "devmath.cuh"
 
 namespace atsfft {
 
@@ -114,18 +114,6 @@ Job make_job(const atsfft_plan_s *P, int logB, int nh)
 
 // ---- plan-time window tables (FP64) ---------------------------------------------
 
-// Unnormalised tap T_t = exp(-t^2/(2 s^2)) * box(t), box(0) = D, box(t) = sin(pi t/B)/(pi t/n),
-// with sin(pi t / B) reduced exactly in integers.
-__device__ double window_term(int64_t t, int64_t n, int logB, double s)
-{
-    int64_t B = (int64_t)1 << logB;
-    double env = exp(-((double)t * (double)t) / (2.0 * s * s));
-    if (t == 0) return env * (double)(n >> logB);
-    int64_t r = t % (2 * B);
-    if (r < 0) r += 2 * B;
-    double sn = (r == 0 || r == B) ? 0.0 : sinpi((double)r / (double)B);
-    return env * sn / (M_PI * (double)t / (double)n);
-}
 
 // Partial sums over a chunk of t in [0, h] of w_t T_t cos(pi o2 t / n) (w_0 = 1, else 2)
 // for every half-integer offset o2 = 2j - D + 1, j in [0, D), and o2 = 0 (j = D, the
@@ -253,6 +241,7 @@ extern "C" void atsfft_default_params(atsfft_params *p)
     p->tune_stages = 2;
     p->fixed_k = 0;
     p->est_reuse_loc = 0;
+    p->precision = 0;
 }
 
 extern "C" const char *atsfft_status_string(atsfft_status s)
@@ -285,6 +274,7 @@ static bool params_ok(const atsfft_params *p)
     if (p->fixed_k != 0 && p->fixed_k != 1) return false;
     if (p->est_reuse_loc != 0 && p->est_reuse_loc != 1) return false;
     if (p->est_reuse_loc && p->loops_est > p->loops_loc) return false;
+    if (p->precision != 0 && p->precision != 1) return false;
     return true;
 }
 
@@ -292,7 +282,8 @@ static void plan_free(atsfft_plan_s *P)
 {
     void *ptrs[] = {P->d_tune, P->d_le, P->d_win, P->d_resp, P->d_rgain, P->d_phase, P->d_tw, P->d_part, P->d_tz,
                     P->d_z, P->d_fft_tmp, P->d_energy, P->d_stats, P->d_hist, P->d_lmax,
-                    P->d_sel, P->d_bucketbits, P->d_kept, P->d_coordbits, P->d_blk, P->d_state, P->d_tjob, P->d_tstat,
+                    P->d_sel, P->d_bucketbits, P->d_kept, P->d_coordbits, P->d_blk, P->d_x32, P->d_f64a,
+                    P->d_f64b, P->d_tw64, P->d_state, P->d_tjob, P->d_tstat,
                     P->d_lstat};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -328,6 +319,7 @@ static atsfft_status plan_create(atsfft_plan_t *out, int ndim, const int64_t *sh
     if (n <= 0 || (n & (n - 1))) return ATSFFT_E_INVALID_ARG;
     if (ndim == 1 && (n < 256 || n > ((int64_t)1 << 28))) return ATSFFT_E_INVALID_ARG;
     if (ndim == 2 && (shape[1] != n || n < 32 || n > ((int64_t)1 << 14))) return ATSFFT_E_INVALID_ARG;
+    if (ndim == 2 && p.precision == 1) return ATSFFT_E_INVALID_ARG;   // the FP64 path is 1D
 
     atsfft_plan_s *P = new (std::nothrow) atsfft_plan_s;
     if (!P) return ATSFFT_E_NOMEM;
@@ -467,6 +459,12 @@ static atsfft_status plan_create(atsfft_plan_t *out, int ndim, const int64_t *sh
     A((void **)&P->d_coordbits, sizeof(uint32_t) * (size_t)P->coord_words);
     // per-block counts of the compaction (cooperative grid: at most a few blocks per SM)
     A((void **)&P->d_blk, sizeof(uint32_t) * (size_t)P->num_sms * 32);
+    if (p.precision == 1) {
+        A((void **)&P->d_x32, sizeof(float2) * (size_t)n);
+        A((void **)&P->d_f64a, sizeof(double2) * (size_t)P->L_est * (size_t)nb_max);
+        A((void **)&P->d_f64b, sizeof(double2) * (size_t)P->L_est * (size_t)nb_max);
+        A((void **)&P->d_tw64, sizeof(double2) * (size_t)(nb_max / 2 + 1));
+    }
     A((void **)&P->d_state, sizeof(ExecState));
     A((void **)&P->d_tjob, sizeof(Job) * kMaxLogB);
     A((void **)&P->d_tstat, sizeof(StatJob) * kMaxLogB);

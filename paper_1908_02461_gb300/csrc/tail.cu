@@ -658,9 +658,6 @@ __global__ void __launch_bounds__(256, 2) k_tune_tail(const TuneTailArgs A)
 // ---------------------------------------------------------------------------------
 // Location tail
 // ---------------------------------------------------------------------------------
-struct RespOffsets {
-    int64_t off[kMaxLogB];
-};
 
 struct LocTailArgs {
     StatsParams S;
@@ -688,6 +685,7 @@ struct LocTailArgs {
     int64_t *loc;
     float2 *val;
     uint8_t *msel;          // optional: median hash indices (real, imaginary) per output
+    int skip_est;           // 1: locations only (the FP64 path estimates afterwards)
     int64_t capacity;
     int64_t *d_count, *d_k;
     int32_t *d_status;
@@ -1259,11 +1257,13 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1)
                 if (o < grp) r += __shfl_xor_sync(0xffffffffu, r, o, grp);
-            float2 v = make_float2(0.f, 0.f);
-            if (valid && r < A.capacity && gl < A.L_est) v = estimate_term(coord, A, b, gl);
             const bool inside = valid && r < A.capacity;
-            group_median(v, A.L_est, grp, inside, &A.val[inside ? r : 0],
-                         A.msel && inside ? A.msel + 2 * (int64_t)r : nullptr);
+            if (!A.skip_est) {
+                float2 v = make_float2(0.f, 0.f);
+                if (inside && gl < A.L_est) v = estimate_term(coord, A, b, gl);
+                group_median(v, A.L_est, grp, inside, &A.val[inside ? r : 0],
+                             A.msel && inside ? A.msel + 2 * (int64_t)r : nullptr);
+            }
             if (valid && gl == 0) {
                 A.coordbits[coord >> 5] = 0u;   // only kept coordinates set bits
                 if (inside) A.loc[r] = coord;
@@ -1314,7 +1314,7 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
         }
     }
     if (!grid_sync(gb, status)) return;
-    estimate_all(A, min(K, A.capacity), b);
+    if (!A.skip_est) estimate_all(A, min(K, A.capacity), b);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1436,6 +1436,7 @@ void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, uint
     A.loc = d_loc;
     A.val = d_val;
     A.msel = d_msel;
+    A.skip_est = P->p.precision == 1;
     A.capacity = capacity;
     A.d_count = d_count;
     A.d_k = d_k;

@@ -45,11 +45,12 @@ def _add_noise(rng, x, snr_db):
 
 
 def sparse_signal_1d(n: int, k: int, seed: int, snr_db: float | None = None,
-                     mag="unit") -> SparseSignal:
+                     mag="unit", dtype=np.complex64) -> SparseSignal:
     """n-sample signal whose DFT has exactly k nonzero bins (plus optional noise).
 
     Locations: k distinct values drawn uniformly from [0, n); phases uniform in
-    [0, 2*pi); magnitudes 1 ("unit") or ("loguniform", lo, hi).
+    [0, 2*pi); magnitudes 1 ("unit") or ("loguniform", lo, hi).  The samples are
+    computed in FP64 and stored as `dtype` (complex64 by default).
     """
     rng = np.random.default_rng(seed)
     support = np.sort(rng.choice(n, size=k, replace=False)).astype(np.int64)
@@ -60,7 +61,7 @@ def sparse_signal_1d(n: int, k: int, seed: int, snr_db: float | None = None,
     xhat[support] = coeffs
     x = np.fft.ifft(xhat)
     x, var = _add_noise(rng, x, snr_db)
-    return SparseSignal(x.astype(np.complex64), support, coeffs, var)
+    return SparseSignal(x.astype(dtype), support, coeffs, var)
 
 
 def sparse_signal_2d(N: int, k: int, seed: int, snr_db: float | None = None,

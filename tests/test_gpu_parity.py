@@ -295,3 +295,33 @@ def test_estimation_reusing_location_hashes(A, O, n, k, seed, snr):
 
     sig = sparse_signal_1d(n, k, seed, snr_db=snr)
     _check_transform(A, O, sig.x, 7, 1, params_kw={"est_reuse_loc": 1})
+
+
+# --------------------------------------------------------------------------
+# FP64 path (precision 1): complex128 input, values to ~1e-12 of the FP64 oracle
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,k,seed,snr", [(1 << 14, 16, 2, None), (1 << 16, 40, 21, 40.0),
+                                          (1 << 20, 300, 5, 40.0)])
+def test_fp64_path_values(A, O, n, k, seed, snr):
+    import torch
+
+    from synth import sparse_signal_1d
+
+    sig = sparse_signal_1d(n, k, seed, snr_db=snr, dtype=np.complex128)
+    plan = A.Plan((n,), params=A.params(precision=1), seed=7)
+    x = torch.from_numpy(sig.x).cuda()
+    loc, val, kk, st, cnt = plan(x, capacity=1 << 14)
+    assert val.dtype == torch.complex128
+    ref = O.atsfft_1d(sig.x, seed=7, capacity=1 << 14)
+    # decisions as in the FP32 path (on the input rounded to complex64)
+    ref32 = O.atsfft_1d(sig.x.astype(np.complex64), seed=7, capacity=1 << 14)
+    if ref32.min_margin > MARGIN_SAFE:
+        assert kk == ref32.k_star and cnt == ref32.count
+        assert loc.cpu().numpy().tolist() == ref32.loc.tolist()
+    if ref.loc.tolist() == loc.cpu().numpy().tolist():
+        v = val.cpu().numpy()
+        err = np.abs(v - ref.val).max() / np.abs(ref.val).max()
+        print(f"[fp64] n={n} k*={kk} count={cnt} value err={err:.1e}")
+        assert err < 1e-10, err
+    plan.close()
