@@ -131,7 +131,8 @@ const char *atsfft_status_string(atsfft_status s);
 /* One hash of the plan's signal shape at bucket count B (per axis in 2D), for
  * (phase, index) = (0 tuning, log2 B), (1 location, l) or (2 estimation, l): writes the
  * bucket spectrum Zhat (complex64; B values, or B*B row-major in 2D) to d_zhat on
- * `stream`.  B must lie in the plan's tuning range. */
+ * `stream`.  B must lie in the plan's tuning range.  FP32 plans (precision 0) only:
+ * ATSFFT_E_INVALID_ARG otherwise. */
 atsfft_status atsfft_hash_spectrum(atsfft_plan_t plan, const void *d_x, int64_t B, int phase,
                                    int index, void *d_zhat, void *stream);
 
@@ -191,7 +192,8 @@ atsfft_status atsfft_exec_sel(atsfft_plan_t plan, const void *d_x, int64_t *d_lo
  * from estimation hash l of the plan at B buckets applied to d_u (n complex64), and
  * (l_r, l_i) = d_medsel[2p], d_medsel[2p + 1].  For d_u = the transformed signal this
  * reproduces the transform's values.  Uses the plan's scratch (not reentrant with its
- * execs); B must lie in the plan's tuning range. */
+ * execs); B must lie in the plan's tuning range.  FP32 plans (precision 0) only:
+ * ATSFFT_E_INVALID_ARG otherwise. */
 atsfft_status atsfft_estimate_apply(atsfft_plan_t plan, int64_t B, const void *d_u,
                                     const int64_t *d_loc, const uint8_t *d_medsel, int64_t count,
                                     void *d_out, void *stream);

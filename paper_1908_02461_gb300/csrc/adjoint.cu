@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_adj_stream(const HashParam *est, int L_
 static atsfft_status est_args(const atsfft_plan_s *P, int64_t B, const int64_t *d_loc,
                               const uint8_t *d_msel, int64_t count, EstArgs *E, int *b_out)
 {
-    if (!P || P->ndim != 1 || B <= 0 || (B & (B - 1)) || count < 0 ||
+    if (!P || P->ndim != 1 || P->p.precision != 0 || B <= 0 || (B & (B - 1)) || count < 0 ||
         (count > 0 && (!d_loc || !d_msel)))
         return ATSFFT_E_INVALID_ARG;
     int b = 0;

@@ -92,7 +92,8 @@ extern "C" atsfft_status atsfft_exec_sel(atsfft_plan_t plan, const void *d_x, in
 extern "C" atsfft_status atsfft_hash_spectrum(atsfft_plan_t P, const void *d_x, int64_t B,
                                               int phase, int index, void *d_zhat, void *stream)
 {
-    if (!P || !d_x || !d_zhat || B <= 0 || (B & (B - 1)) || phase < 0 || phase > 2 || index < 0)
+    if (!P || !d_x || !d_zhat || B <= 0 || (B & (B - 1)) || phase < 0 || phase > 2 || index < 0 ||
+        P->p.precision != 0)
         return ATSFFT_E_INVALID_ARG;
     int b = 0;
     while (((int64_t)1 << b) < B) b++;

@@ -235,8 +235,9 @@ __device__ void block_find_rank(const uint32_t *hist, int nbins, uint32_t rank, 
 constexpr int kSmallMedian = 8192;
 
 // Exact median (element floor(nb/2) of the ascending energies, as bits) of nb <= 8192
-// energies by one block: the values are staged in shared memory and selected with
-// three radix digits (11, 11, 10 bits) over their bit patterns.
+// energies by one block: the values are staged in shared memory and selected by rank
+// comparison when there are at most blockDim of them, else with three radix digits
+// (11, 11, 10 bits) over their bit patterns (E >= 0: bit order = value order).
 __device__ uint32_t block_median(const float *E, int nb)
 {
     extern __shared__ __align__(16) uint32_t dsm[];   // phase scratch shared by the tail's phases
@@ -244,6 +245,23 @@ __device__ uint32_t block_median(const float *E, int nb)
     uint32_t *hist = dsm + kSmallMedian; // 2048 entries
     __shared__ uint32_t sh_prefix, sh_rank;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) vals[i] = __float_as_uint(E[i]);
+    if (nb <= (int)blockDim.x) {
+        // few values: the element whose rank (ties by index) is floor(nb/2), one per thread
+        if (threadIdx.x == 0) sh_prefix = 0;
+        __syncthreads();
+        const int i = threadIdx.x;
+        if (i < nb) {
+            const uint32_t v = vals[i];
+            int r = 0;
+            for (int j = 0; j < nb; j++) {
+                const uint32_t u = vals[j];
+                r += u < v || (u == v && j < i);
+            }
+            if (r == nb / 2) sh_prefix = v;
+        }
+        __syncthreads();
+        return sh_prefix;
+    }
     if (threadIdx.x == 0) {
         sh_prefix = 0;
         sh_rank = (uint32_t)(nb / 2);
@@ -870,7 +888,7 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t i, uint32_t sigma, int lo
 constexpr int kRankStage = 4096;   // top-num by ranking: candidates staged per block
 constexpr int kRankLanes = 8;      // lanes sharing one candidate's rank
 constexpr int kSelBlocks = 4;      // blocks per location hash in the cutoff
-constexpr int kPivots = 32;
+constexpr int kPivots = 32;   // one warp: lane p holds pivot p
 constexpr int kVoteUnroll = 8;     // location hashes whose bitmap words are fetched together
 
 // Value of descending rank r (0-based; equal values ordered by index) among es[0..cnt),
@@ -896,32 +914,38 @@ __device__ __noinline__ float block_select_desc(const float *es, int cnt, uint32
         if (lane == 0) pg[p] = g;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    __shared__ uint32_t above_u;
+    if (warp == 0) {
         // V lies in (L, U]: L the largest pivot with >= r + 1 elements above it, U the
-        // smallest pivot with <= r elements above it
-        float L = -INFINITY, U = INFINITY;
-        for (int p = 0; p < kPivots; p++) {
-            if (pg[p] >= r + 1) L = fmaxf(L, pv[p]);
-            else U = fminf(U, pv[p]);
+        // smallest pivot with <= r elements above it (lane p holds pivot p)
+        const float v = pv[lane];
+        const uint32_t g = pg[lane];
+        float L = g >= r + 1 ? v : -INFINITY, U = g >= r + 1 ? INFINITY : v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            L = fmaxf(L, __shfl_xor_sync(0xffffffffu, L, o));
+            U = fminf(U, __shfl_xor_sync(0xffffffffu, U, o));
         }
-        lo_sh = L;
-        hi_sh = U;
+        // every element outside (L, U] is either above U (g(U) of them) or at most L, so
+        // a bracket member's rank is g(U) plus its rank inside the bracket
+        const unsigned at_u = __ballot_sync(0xffffffffu, v == U);
+        const uint32_t gu = __shfl_sync(0xffffffffu, g, at_u ? __ffs(at_u) - 1 : 0);
+        if (lane == 0) {
+            lo_sh = L;
+            hi_sh = U;
+            above_u = U == INFINITY ? 0u : gu;
+        }
     }
     __syncthreads();
     const float L = lo_sh, U = hi_sh;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const float e = es[i];
-        if (e > L && e <= U) scratch[atomicAdd(&nbr, 1u)] = (uint32_t)i;
-    }
-    __syncthreads();
-    // every element outside (L, U] is either above U (there are g(U) of those) or at most
-    // L, so a bracket member's rank is g(U) plus its rank inside the bracket
-    __shared__ uint32_t above_u;
-    if (threadIdx.x == 0) {
-        uint32_t g = 0;
-        for (int p = 0; p < kPivots; p++)
-            if (pv[p] == U) g = pg[p];
-        above_u = U == INFINITY ? 0u : g;
+    for (int i0 = 0; i0 < cnt; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const bool in = i < cnt && es[i] > L && es[i] <= U;
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        uint32_t base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&nbr, (uint32_t)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (in) scratch[base + __popc(bal & ((1u << lane) - 1))] = (uint32_t)i;
     }
     __syncthreads();
     const int nb = (int)nbr;
