@@ -325,3 +325,22 @@ def test_fp64_path_values(A, O, n, k, seed, snr):
         print(f"[fp64] n={n} k*={kk} count={cnt} value err={err:.1e}")
         assert err < 1e-10, err
     plan.close()
+
+
+def test_fp64_plan_rejects_fp32_entries(A):
+    """hash_spectrum and the fixed-support estimate map read complex64 input: an FP64
+    plan refuses them with an argument error before any launch."""
+    import torch
+
+    n = 1 << 14
+    plan = A.Plan((n,), params=A.params(precision=1), seed=7)
+    x = torch.zeros(n, dtype=torch.complex64, device="cuda")
+    loc = torch.zeros(1, dtype=torch.int64, device="cuda")
+    msel = torch.zeros(2, dtype=torch.uint8, device="cuda")
+    with pytest.raises(A.ATSFFTError):
+        plan.hash_spectrum(x, 64, 1, 0)
+    with pytest.raises(A.ATSFFTError):
+        plan.estimate_apply(64, x, loc, msel)
+    with pytest.raises(A.ATSFFTError):
+        plan.estimate_adjoint(64, loc, msel, torch.zeros(1, dtype=torch.complex64, device="cuda"))
+    plan.close()
