@@ -215,7 +215,9 @@ def cpu_baseline(sigs, budget_s=20.0):
 # the plan's defaults (alpha 0.5, tol 1e-6, 7 + 7 hashes, B range [2^4, n/16]); the
 # formulas are listed in the design doc.
 L_LOC, L_EST, NH = 7, 7, 14
-SFU_PER_SM_CLK, SMS, SM_MAX_MHZ = 16, 152, 2070.0
+# MUFU (XU pipe) results per clock per SM: ncu rates the XU pipe at one warp instruction
+# per 4 cycles per SM sub-partition (4 x 32 / 4 = 32 lanes per clock per SM)
+SFU_PER_SM_CLK, SMS, SM_MAX_MHZ = 32, 152, 2070.0
 
 
 def _window_h(n, B, alpha=0.5, tol=1e-6):
@@ -300,7 +302,7 @@ def roofline(per_signal, traces, n):
             "unit": d["unit"], "frac": d["achieved"] / peak,
             "traffic": NCU_TRAFFIC[dom][0] if dom in NCU_TRAFFIC else None,
             "traffic_launch": NCU_TRAFFIC[dom][1] if dom in NCU_TRAFFIC else None,
-            "peak_source": ("derived: 16 SFU ops/clk/SM x 152 SMs x 2070 MHz / 2 SFU ops per "
+            "peak_source": ("derived: 32 SFU ops/clk/SM x 152 SMs x 2070 MHz / 2 SFU ops per "
                             "sample-hash pair") if d["bound"] == "alu" else f"{src} hbm_gbs",
             "ms_per_launch": d["ms_per_launch"]}
     return roof, out

@@ -108,6 +108,14 @@ __global__ void k_bin_gather_1d(const float2 *__restrict__ x, int logn, const Ha
 // accumulator per hash.  Hash l writes block (c * R/B_l + r / B_l) of B_l partial sums,
 // element r mod B_l (residue order); the bucket FFT adds the blocks up.
 // Per-hash constants live in the kernel parameter space.
+//
+// Window test folded into a table.  With t' = t + h mod n = sigma^{-1} a + c0 + h (mod n),
+// the tap is in the window iff t' <= 2h.  For all samples of one thread t' = Q B + rho with
+// rho fixed, so u = floor(t / B) = Q - kappa with kappa = ceil((h - rho) / B), and the
+// window test becomes u <= floor((h - delta) / B), delta = kappa B + rho - h in [0, B),
+// which takes one of two values (H - 1 or H, H = floor(h / B)).  Two tables per window,
+// E_v[i] = R_u for u = i - (H + 1) <= H - 1 + v and 0 beyond, indexed by Q plus a
+// per-thread offset, give R_u and the window test in one shared-memory read.
 // ---------------------------------------------------------------------------------
 constexpr int kMaxStream = 16;
 
@@ -115,7 +123,7 @@ struct StreamHash {
     uint32_t sinv, c0, tau;   // c0 = -sinv * tau (mod 2^32)
     int32_t logB, h;          // static passes: bucket count and window of this hash
     float k2, log2c, cAD;
-    int32_t rot_off;          // its R_u table in shared memory (2 D entries)
+    int32_t rot_off;          // its two E_v tables in shared memory (2 (D + 2) entries)
     int64_t out_off;          // its first partial block in `part`
 };
 
@@ -127,47 +135,81 @@ struct StreamArgs {
     StreamHash h[kMaxStream];
 };
 
+// Shared-memory entries of the two E_v tables of a window with D = n / B.
+__host__ __device__ constexpr int rot_entries(uint32_t D) { return 2 * ((int)D + 2); }
+
+// E_0, E_1 of one window (bucket count 2^lb, half-width h) at tab[0 .. 2 (D + 2)).
+__device__ __forceinline__ void fill_rot_tables(float2 *tab, int logn, int lb, int h)
+{
+    const uint32_t D = 1u << (logn - lb);
+    const int H = h >> lb;
+    for (int e = threadIdx.x; e < rot_entries(D); e += blockDim.x) {
+        const int v = e >= (int)D + 2;
+        const int u = e - v * ((int)D + 2) - (H + 1);
+        const uint32_t um = (uint32_t)u & (2 * D - 1);   // R_u has period 2D in u
+        float sn, cs;
+        sincospif(ldexpf((float)um, -(logn - lb)), &sn, &cs);
+        const float2 r = (um & 1) ? make_float2(-cs, -sn) : make_float2(cs, sn);
+        tab[e] = u <= H - 1 + v ? r : make_float2(0.f, 0.f);
+    }
+}
+
+// The thread's table entry offset for one hash (from the window's first table, which has
+// D + 2 entries): residue rho of t' mod B, kappa - H in {0, 1}, table v in {0, 1},
+// index i = Q + 1 - (kappa - H).
+__device__ __forceinline__ int rot_base(uint32_t rho, int h, int lb, int D2)
+{
+    const int B = 1 << lb, H = h >> lb, hr = h & (B - 1);
+    const int k1 = (int)rho < hr;
+    const int delta = (k1 ? B : 0) + (int)rho - hr;
+    const int v = ((h - delta) >> lb) - (H - 1);
+    return v * D2 + 1 - k1;
+}
+
+__device__ __forceinline__ float ld_shared_f32(uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+
 // Window constants of one hash inside the inner loop: uniform across the CTA.
 struct TapConst {
-    uint32_t c0h;        // c0 + h: t' = sigma^{-1} a + c0 + h (mod n) is in the window iff t' <= 2h
-    uint32_t two_h;
+    uint32_t c0h;        // c0 + h: t' = sigma^{-1} a + c0 + h (mod n)
     int h, logB;
-    int roff;
-    uint32_t rmask;
+    float mh;            // -(2^23 + h): t = float(2^23 + t') + mh, exact for n <= 2^23
     float k2, l2c;
 };
 
-// Exact int -> float for |v| < 2^22 without the conversion unit: the float with bits
-// 0x4B400000 + v is 1.5 * 2^23 + v.
-__device__ __forceinline__ float small_int_to_float(int v)
-{
-    return __int_as_float(0x4B400000 + v) - 12582912.0f;
-}
-
-// One (sample, hash) pair: t = sigma^{-1}(a - tau) mod n as a signed integer, window test
-// as a select (no branch), f_t R_u, complex multiply-add.  ts = 0 (centre tap, bucket 0
-// only) yields inf, which stays in bucket 0's discarded accumulator.
+// One (sample, hash) pair: t' from the exact integer index, E_v entry at the thread's
+// table address `tb` (bytes) plus 8 Q, f_t = exp2(l2c - k2 t^2) / t, complex multiply-add.
+// t = 0 (centre tap, bucket 0 only) yields inf, which stays in bucket 0's discarded
+// accumulator.
 template <bool SMALL_N>
 __device__ __forceinline__ void tap_mac(float2 &acc, float2 v, uint32_t a, uint32_t sinv,
-                                        uint32_t mask, const TapConst &T, const float2 *rot)
+                                        uint32_t mask, const TapConst &T, uint32_t tb)
 {
     const uint32_t tsh = (sinv * a + T.c0h) & mask;
-    const bool in = tsh <= T.two_h;
-    const int ts = (int)tsh - T.h;
-    const float2 Ru = rot[T.roff + ((uint32_t)(ts >> T.logB) & T.rmask)];
-    const float tf = SMALL_N ? small_int_to_float(ts) : (float)ts;
-    float f = fast_exp2(fmaf(-T.k2 * tf, tf, T.l2c)) * fast_rcp(tf);
-    f = in ? f : 0.f;
-    const float cr = f * Ru.x, ci = f * Ru.y;
+    const uint32_t e = tb + ((tsh >> T.logB) << 3);
+    const float ex = ld_shared_f32(e), ey = ld_shared_f32(e + 4);
+    const float tf = SMALL_N ? __uint_as_float(tsh | 0x4B000000u) + T.mh
+                             : (float)((int)tsh - T.h);
+    const float f = fast_exp2(fmaf(-T.k2 * tf, tf, T.l2c)) * fast_rcp(tf);
+    const float cr = f * ex, ci = f * ey;
     acc.x = fmaf(cr, v.x, fmaf(-ci, v.y, acc.x));
     acc.y = fmaf(cr, v.y, fmaf(ci, v.x, acc.y));
 }
 
+// Grid: kStreamCtas CTAs per SM of kStreamThreads threads, striding over the items
+// (measured: contiguous per-CTA item ranges balance a lone launch as well but slow the
+// transforms of a batch graph down, where other branches' kernels share the SMs).
+constexpr int kStreamThreads = 256;
+constexpr int kStreamCtas = 2;
+
 template <int NH, bool DYN>
-__global__ void __launch_bounds__(256) k_bin_stream(const float2 *__restrict__ x, int logn,
-                                                    const StreamArgs A, const Job *job_dev,
-                                                    const WindowParam *win,
-                                                    float2 *__restrict__ part, const int *skip)
+__global__ void __launch_bounds__(kStreamThreads, kStreamCtas)
+k_bin_stream(const float2 *__restrict__ x, int logn, const StreamArgs A, const Job *job_dev,
+             const WindowParam *win, float2 *__restrict__ part, const int *skip)
 {
     extern __shared__ float2 rot[];
     if (skip && *skip) return;
@@ -180,24 +222,12 @@ __global__ void __launch_bounds__(256) k_bin_stream(const float2 *__restrict__ x
         w = win[logR];
     }
     const uint32_t n = 1u << logn, mask = n - 1, R = 1u << logR;
-    // R_u = (-1)^u exp(i pi u / D), u in [0, 2D): one table (dynamic) or one per hash
     if (DYN) {
-        const uint32_t D = n >> logR;
-        for (uint32_t u = threadIdx.x; u < 2 * D; u += blockDim.x) {
-            float sn, cs;
-            sincospif(ldexpf((float)u, -(logn - logR)), &sn, &cs);
-            rot[u] = (u & 1) ? make_float2(-cs, -sn) : make_float2(cs, sn);
-        }
+        fill_rot_tables(rot, logn, logR, w.h);
     } else {
-        for (int g = 0; g < NH; g++) {
-            const int lb = A.h[g].logB;
-            const uint32_t D = n >> lb;
-            for (uint32_t u = threadIdx.x; u < 2 * D; u += blockDim.x) {
-                float sn, cs;
-                sincospif(ldexpf((float)u, -(logn - lb)), &sn, &cs);
-                rot[A.h[g].rot_off + u] = (u & 1) ? make_float2(-cs, -sn) : make_float2(cs, sn);
-            }
-        }
+        for (int g = 0; g < NH; g++)
+            if (g == 0 || A.h[g].rot_off != A.h[g - 1].rot_off)
+                fill_rot_tables(rot + A.h[g].rot_off, logn, A.h[g].logB, A.h[g].h);
     }
     __syncthreads();
     TapConst T[NH];
@@ -205,14 +235,13 @@ __global__ void __launch_bounds__(256) k_bin_stream(const float2 *__restrict__ x
     for (int g = 0; g < NH; g++) {
         const int h = DYN ? w.h : A.h[g].h;
         T[g].c0h = A.h[g].c0 + (uint32_t)h;
-        T[g].two_h = 2u * (uint32_t)h;
         T[g].h = h;
         T[g].logB = DYN ? logR : A.h[g].logB;
-        T[g].roff = DYN ? 0 : A.h[g].rot_off;
-        T[g].rmask = 2 * (n >> T[g].logB) - 1;
+        T[g].mh = -(8388608.0f + (float)h);
         T[g].k2 = DYN ? w.k2 : A.h[g].k2;
         T[g].l2c = DYN ? w.log2c : A.h[g].log2c;
     }
+    const uint32_t rot_s = (uint32_t)__cvta_generic_to_shared(rot);
     const uint32_t rows = (n >> logR) / (uint32_t)chunks;
     const int64_t items = (int64_t)R * chunks;
     const bool small_n = logn <= 23;
@@ -221,22 +250,29 @@ __global__ void __launch_bounds__(256) k_bin_stream(const float2 *__restrict__ x
         const uint32_t r = (uint32_t)(it & (R - 1));
         const uint32_t c = (uint32_t)(it >> logR);
         float2 acc[NH];
+        uint32_t tb[NH];
 #pragma unroll
-        for (int g = 0; g < NH; g++) acc[g] = make_float2(0.f, 0.f);
+        for (int g = 0; g < NH; g++) {
+            acc[g] = make_float2(0.f, 0.f);
+            const int lb = T[g].logB;
+            const uint32_t rho = (A.h[g].sinv * r + T[g].c0h) & ((1u << lb) - 1);
+            const int e = (DYN ? 0 : A.h[g].rot_off) + rot_base(rho, T[g].h, lb, (int)(n >> lb) + 2);
+            tb[g] = rot_s + 8u * (uint32_t)e;
+        }
         const uint32_t j0 = c * rows;
         if (small_n) {
             for (uint32_t j = j0; j < j0 + rows; j++) {
                 const uint32_t a = r + (j << logR);
                 const float2 v = __ldg(&x[a]);
 #pragma unroll
-                for (int g = 0; g < NH; g++) tap_mac<true>(acc[g], v, a, A.h[g].sinv, mask, T[g], rot);
+                for (int g = 0; g < NH; g++) tap_mac<true>(acc[g], v, a, A.h[g].sinv, mask, T[g], tb[g]);
             }
         } else {
             for (uint32_t j = j0; j < j0 + rows; j++) {
                 const uint32_t a = r + (j << logR);
                 const float2 v = __ldg(&x[a]);
 #pragma unroll
-                for (int g = 0; g < NH; g++) tap_mac<false>(acc[g], v, a, A.h[g].sinv, mask, T[g], rot);
+                for (int g = 0; g < NH; g++) tap_mac<false>(acc[g], v, a, A.h[g].sinv, mask, T[g], tb[g]);
             }
         }
 #pragma unroll
@@ -525,35 +561,23 @@ static StreamHash stream_hash(const atsfft_plan_s *P, const HashParam &hp, int b
     return h;
 }
 
-static int occupancy_grid(const atsfft_plan_s *P, const void *fn, size_t smem)
-{
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem);
-    if (per_sm < 1) per_sm = 1;
-    return P->num_sms * per_sm;
-}
-
 template <int NH, bool DYN>
 static void launch_stream(const atsfft_plan_s *P, const float2 *x, const StreamArgs &A,
-                          const Job *job_dev, size_t smem, int64_t items_hint, const int *skip,
-                          cudaStream_t s)
+                          const Job *job_dev, size_t smem, const int *skip, cudaStream_t s)
 {
     const void *fn = (const void *)k_bin_stream<NH, DYN>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int64_t grid = occupancy_grid(P, fn, smem);
-    const int64_t need = (items_hint + 255) / 256;
-    if (items_hint > 0 && need < grid) grid = need;
-    k_bin_stream<NH, DYN><<<(unsigned)grid, 256, smem, s>>>(x, P->logn, A, job_dev, P->d_win,
-                                                            P->d_part, skip);
+    k_bin_stream<NH, DYN><<<(unsigned)(P->num_sms * kStreamCtas), kStreamThreads, smem, s>>>(
+        x, P->logn, A, job_dev, P->d_win, P->d_part, skip);
     count_launch(P);
 }
 
 template <bool DYN>
 static void launch_stream_nh(const atsfft_plan_s *P, const float2 *x, const StreamArgs &A,
-                             const Job *job_dev, size_t smem, int64_t items_hint, cudaStream_t s,
+                             const Job *job_dev, size_t smem, cudaStream_t s,
                              const int *skip = nullptr)
 {
-#define ATSFFT_NH(k) case k: launch_stream<k, DYN>(P, x, A, job_dev, smem, items_hint, skip, s); break;
+#define ATSFFT_NH(k) case k: launch_stream<k, DYN>(P, x, A, job_dev, smem, skip, s); break;
     switch (A.nh) {
     ATSFFT_NH(1) ATSFFT_NH(2) ATSFFT_NH(3) ATSFFT_NH(4) ATSFFT_NH(5) ATSFFT_NH(6) ATSFFT_NH(7)
     ATSFFT_NH(8) ATSFFT_NH(9) ATSFFT_NH(10) ATSFFT_NH(11) ATSFFT_NH(12) ATSFFT_NH(13)
@@ -591,7 +615,7 @@ void launch_tuning(const atsfft_plan_s *P, const float2 *x, int stage, cudaStrea
                 StreamHash &h = S.h[S.nh++];
                 h = stream_hash(P, P->h_tune[b], b, P->tpart_off[b]);
                 h.rot_off = rot_total;
-                rot_total += 2 * (int)(P->n >> b);
+                rot_total += rot_entries((uint32_t)(P->n >> b));
             } else {
                 GatherHash &g = G.j[G.njobs++];
                 g = gather_hash(P, P->h_tune[b], b, P->tpart_off[b]);
@@ -615,8 +639,7 @@ void launch_tuning(const atsfft_plan_s *P, const float2 *x, int stage, cudaStrea
             S.logR = P->tstream_logR;
             S.chunks = P->tstream_chunks;
             if (stage == 2) skip = &P->d_state->tune_done;
-            launch_stream_nh<false>(P, x, S, nullptr, sizeof(float2) * rot_total,
-                                    ((int64_t)1 << S.logR) * S.chunks, s, skip);
+            launch_stream_nh<false>(P, x, S, nullptr, sizeof(float2) * rot_total, s, skip);
         }
     } else {
         if (stage != 1) {
@@ -644,11 +667,11 @@ void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
 {
     const int nh = P->nh_le;
     if (P->ndim == 1) {
-        // shared memory for the R_u table of the smallest B the stream form can take
+        // shared memory for the E_v tables of the smallest B the stream form can take
         size_t smem = 16;
         for (int b = P->b0; b <= P->b_hi; b++)
             if (P->h_tjob[b].stream) {
-                smem = sizeof(float2) * 2 * (size_t)(P->n >> b);
+                smem = sizeof(float2) * rot_entries((uint32_t)(P->n >> b));
                 break;
             }
         for (int g0 = 0; g0 < nh; g0 += kMaxStream) {
@@ -657,7 +680,7 @@ void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
             S.nh = nh - g0 < kMaxStream ? nh - g0 : kMaxStream;
             S.hash_base = g0;
             for (int g = 0; g < S.nh; g++) S.h[g] = stream_hash(P, P->h_le[g0 + g], -1, 0);
-            launch_stream_nh<true>(P, x, S, job_dev, smem, 0, s);
+            launch_stream_nh<true>(P, x, S, job_dev, smem, s);
         }
         prof_mark(P, 7, s);
         const int groups = (nh + kGroup - 1) / kGroup;
@@ -687,8 +710,7 @@ void launch_single_hash(const atsfft_plan_s *P, const float2 *x, int b, const Ha
             S.logR = b;
             S.chunks = j.chunks;
             S.h[0] = stream_hash(P, hp, b, 0);
-            launch_stream_nh<false>(P, x, S, nullptr, sizeof(float2) * 2 * (size_t)(P->n >> b),
-                                    ((int64_t)1 << b) * j.chunks, s);
+            launch_stream_nh<false>(P, x, S, nullptr, sizeof(float2) * rot_entries((uint32_t)(P->n >> b)), s);
         } else {
             GatherArgs G;
             G.njobs = 1;
@@ -724,10 +746,9 @@ int launch_est_bin(const atsfft_plan_s *P, const float2 *x, int b, cudaStream_t 
             for (int g = 0; g < S.nh; g++) {
                 S.h[g] = stream_hash(P, P->h_le[P->est_base + g0 + g], b,
                                      ((int64_t)(g0 + g) * j.chunks) << b);
-                S.h[g].rot_off = 0;   // one B: every hash's R_u table is the same
+                S.h[g].rot_off = 0;   // one B: every hash's E_v tables are the same
             }
-            launch_stream_nh<false>(P, x, S, nullptr, sizeof(float2) * 2 * (size_t)(P->n >> b),
-                                    ((int64_t)1 << b) * j.chunks, s);
+            launch_stream_nh<false>(P, x, S, nullptr, sizeof(float2) * rot_entries((uint32_t)(P->n >> b)), s);
         }
         return j.chunks;
     }

@@ -89,10 +89,11 @@ Job make_job(const atsfft_plan_s *P, int logB, int nh)
     if (P->ndim == 1) {
         j.stream = (5 * w >= P->n && D <= 4096) ? 1 : 0;
         if (j.stream) {
-            // about 2^18 threads: residues x row chunks
+            // at least 2^16 items (residues x row chunks), spread evenly over the SMs; every
+            // further chunk adds B partial sums per hash for the bucket FFT to read
             int64_t B = (int64_t)1 << logB;
             int64_t rows = P->n >> logB;
-            int64_t chunks = ((int64_t)1 << 18) / B;
+            int64_t chunks = ((int64_t)1 << 16) / B;
             if (chunks < 1) chunks = 1;
             if (chunks > rows) chunks = rows;
             j.chunks = (int32_t)chunks;
