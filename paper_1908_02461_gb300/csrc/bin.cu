@@ -18,12 +18,17 @@ namespace atsfft {
 constexpr int kGroup = 16;   // hashes accumulated together per thread
 
 // ---------------------------------------------------------------------------------
-// 1D, warp per bucket: lanes walk the taps t = b + u B of the window, each tap computed
-// once and applied to every hash of the group (gathering x at each hash's position).
+// 1D gather form: a group of kGatherLanes lanes per bucket walks the taps t = b + u B of
+// the window (about 2h / B + 1 of them, ~35 at the default window), each tap computed
+// once and applied to every hash of the group (gathering x at each hash's position);
+// the group's partial sums are added by shuffles and its first lane writes the buckets.
 // ---------------------------------------------------------------------------------
+constexpr int kGatherLanes = 8;
+
 __global__ void k_bin_gather_1d(const float2 *__restrict__ x, int logn, const HashParam *hashes,
                                 int nh, const WindowParam *win, const Job *job_dev,
-                                int logB_static, float2 *__restrict__ out)
+                                int logB_static, const float2 *__restrict__ phase, int phase_s,
+                                float2 *__restrict__ out)
 {
     int logB = logB_static;
     if (job_dev) {
@@ -35,10 +40,13 @@ __global__ void k_bin_gather_1d(const float2 *__restrict__ x, int logn, const Ha
     if (group0 >= nh) return;
     const int ng = min(kGroup, nh - group0);
     const uint32_t n = 1u << logn, mask = n - 1, B = 1u << logB;
-    const int D = (int)(n >> logB);
     const WindowParam w = win[logB];
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, q = lane & (kGatherLanes - 1);
+    constexpr int kPerWarp = 32 / kGatherLanes;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t tasks = ((int64_t)B + kPerWarp - 1) / kPerWarp;
+    float2 half;
+    sincospif(ldexpf(1.0f, -logn), &half.y, &half.x);
     uint32_t sig[kGroup], tau[kGroup];
 #pragma unroll
     for (int g = 0; g < kGroup; g++) {
@@ -46,23 +54,24 @@ __global__ void k_bin_gather_1d(const float2 *__restrict__ x, int logn, const Ha
         sig[g] = hp.sigma[0];
         tau[g] = hp.tau[0];
     }
-    for (int64_t bw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); bw < B; bw += warps) {
-        const int b = (int)bw;
+    for (int64_t wt = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wt < tasks;
+         wt += warps) {
+        const int64_t bb = wt * kPerWarp + lane / kGatherLanes;
+        const bool valid = bb < (int64_t)B;
+        const int b = valid ? (int)bb : 0;
         // taps t = b + u B with |t| <= h
         const int u_lo = -((w.h + b) >> logB);          // ceil((-h - b) / B)
-        const int u_hi = (w.h - b) >> logB;             // floor((h - b) / B)
+        const int u_hi = valid ? (w.h - b) >> logB : u_lo - 1;   // floor((h - b) / B)
         float2 acc[kGroup];
 #pragma unroll
         for (int g = 0; g < kGroup; g++) acc[g] = make_float2(0.f, 0.f);
-        for (int u = u_lo + lane; u <= u_hi; u += 32) {
+        for (int u = u_lo + q; u <= u_hi; u += kGatherLanes) {
             const int t = b + u * (int)B;
             if (t == 0) continue;                       // centre tap handled below
             const float tf = (float)t;
             const float f = fast_exp2(fmaf(-w.k2 * tf, tf, w.log2c)) * fast_rcp(tf);
-            float rs, rc;
-            sincospif(ldexpf((float)u, -(logn - logB)), &rs, &rc);
-            if (u & 1) { rs = -rs; rc = -rc; }
-            const float2 c = make_float2(f * rc, f * rs);
+            const float2 R = rot_factor(u, logB, mask, phase, phase_s);
+            const float2 c = make_float2(f * R.x, f * R.y);
 #pragma unroll
             for (int g = 0; g < kGroup; g++) {
                 if (g < ng) {
@@ -76,13 +85,13 @@ __global__ void k_bin_gather_1d(const float2 *__restrict__ x, int logn, const Ha
 #pragma unroll
         for (int g = 0; g < kGroup; g++) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int o = kGatherLanes / 2; o > 0; o >>= 1) {
                 acc[g].x += __shfl_xor_sync(0xffffffffu, acc[g].x, o);
                 acc[g].y += __shfl_xor_sync(0xffffffffu, acc[g].y, o);
             }
         }
-        if (lane == 0) {
-            const float2 Sb = bucket_factor((uint32_t)b, logB, logn);
+        if (valid && q == 0) {
+            const float2 Sb = bucket_factor_tab((uint32_t)b, logB, logn, phase, phase_s, half);
 #pragma unroll
             for (int g = 0; g < kGroup; g++) {
                 if (g < ng) {
@@ -98,7 +107,6 @@ __global__ void k_bin_gather_1d(const float2 *__restrict__ x, int logn, const Ha
             }
         }
     }
-    (void)D;
 }
 
 // ---------------------------------------------------------------------------------
@@ -209,7 +217,8 @@ constexpr int kStreamCtas = 2;
 template <int NH, bool DYN>
 __global__ void __launch_bounds__(kStreamThreads, kStreamCtas)
 k_bin_stream(const float2 *__restrict__ x, int logn, const StreamArgs A, const Job *job_dev,
-             const WindowParam *win, float2 *__restrict__ part, const int *skip)
+             const WindowParam *win, const float2 *__restrict__ phase, int phase_s,
+             float2 *__restrict__ part, const int *skip)
 {
     extern __shared__ float2 rot[];
     if (skip && *skip) return;
@@ -242,6 +251,8 @@ k_bin_stream(const float2 *__restrict__ x, int logn, const StreamArgs A, const J
         T[g].l2c = DYN ? w.log2c : A.h[g].log2c;
     }
     const uint32_t rot_s = (uint32_t)__cvta_generic_to_shared(rot);
+    float2 half;
+    sincospif(ldexpf(1.0f, -logn), &half.y, &half.x);
     const uint32_t rows = (n >> logR) / (uint32_t)chunks;
     const int64_t items = (int64_t)R * chunks;
     const bool small_n = logn <= 23;
@@ -289,7 +300,7 @@ k_bin_stream(const float2 *__restrict__ x, int logn, const StreamArgs A, const J
                 const float2 v = __ldg(&x[tau & mask]);
                 z = mine ? make_float2(cad * v.x, cad * v.y) : make_float2(0.f, 0.f);
             } else {
-                z = cmul(bucket_factor(b, logB, logn), acc[g]);
+                z = cmul(bucket_factor_tab(b, logB, logn, phase, phase_s, half), acc[g]);
             }
             const int64_t out_off = DYN ? (int64_t)(A.hash_base + g) * chunks * R : A.h[g].out_off;
             const uint32_t per_chunk = R >> logB;
@@ -303,53 +314,64 @@ struct GatherHash {
     int32_t logB, h;
     float k2, log2c, cAD;
     int64_t out_off;
-    int64_t warp_start;
+    int64_t bucket_start;    // first bucket of this hash in the launch's bucket list
 };
 
 struct GatherArgs {
     int njobs;
-    int64_t total_warps;
+    int64_t total_buckets;
     GatherHash j[kMaxLogB];
 };
 
-// Tuning hashes with small windows: warp per (hash, bucket) over all of them in one
-// launch; warp ids are assigned to hashes by prefix sums of their bucket counts.
+// Tuning hashes with small windows, all in one launch: a group of kTuneLanes lanes per
+// bucket (the buckets of all hashes listed back to back), as in k_bin_gather_1d with one
+// hash.  Bucket counts are multiples of 32 / kTuneLanes, so a warp's buckets share a hash.
+constexpr int kTuneLanes = 4;
+
 __global__ void k_bin_gather_tune(const float2 *__restrict__ x, int logn, const GatherArgs A,
+                                  const float2 *__restrict__ phase, int phase_s,
                                   float2 *__restrict__ part)
 {
     const uint32_t n = 1u << logn, mask = n - 1;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, q = lane & (kTuneLanes - 1);
+    constexpr int kPerWarp = 32 / kTuneLanes;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t wid = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-         wid < A.total_warps; wid += warps) {
+    const int64_t tasks = (A.total_buckets + kPerWarp - 1) / kPerWarp;
+    float2 half;
+    sincospif(ldexpf(1.0f, -logn), &half.y, &half.x);
+    for (int64_t wt = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wt < tasks;
+         wt += warps) {
+        const int64_t gb = wt * kPerWarp + lane / kTuneLanes;
+        const bool valid = gb < A.total_buckets;
+        // the hash whose bucket range holds gb (bucket_start ascending): binary search
+        static_assert(kMaxLogB <= 32, "job search covers 32 jobs");
         int jb = 0;
-        while (jb + 1 < A.njobs && wid >= A.j[jb + 1].warp_start) jb++;
+        for (int step = 16; step > 0; step >>= 1)
+            if (jb + step < A.njobs && gb >= A.j[jb + step].bucket_start) jb += step;
         const GatherHash &H = A.j[jb];
         const int logB = H.logB;
         const uint32_t B = 1u << logB;
-        const int b = (int)(wid - H.warp_start);
-        const int u_lo = -((H.h + b) >> logB), u_hi = (H.h - b) >> logB;
+        const int b = valid ? (int)(gb - H.bucket_start) : 0;
+        const int u_lo = -((H.h + b) >> logB), u_hi = valid ? (H.h - b) >> logB : u_lo - 1;
         float2 acc = make_float2(0.f, 0.f);
-        for (int u = u_lo + lane; u <= u_hi; u += 32) {
+        for (int u = u_lo + q; u <= u_hi; u += kTuneLanes) {
             const int t = b + u * (int)B;
             if (t == 0) continue;
             const float tf = (float)t;
             const float f = fast_exp2(fmaf(-H.k2 * tf, tf, H.log2c)) * fast_rcp(tf);
-            float rs, rc;
-            sincospif(ldexpf((float)u, -(logn - logB)), &rs, &rc);
-            if (u & 1) { rs = -rs; rc = -rc; }
-            const float2 c = make_float2(f * rc, f * rs);
+            const float2 R = rot_factor(u, logB, mask, phase, phase_s);
+            const float2 c = make_float2(f * R.x, f * R.y);
             const float2 v = __ldg(&x[(H.sig * (uint32_t)t + H.tau) & mask]);
             acc.x = fmaf(c.x, v.x, fmaf(-c.y, v.y, acc.x));
             acc.y = fmaf(c.x, v.y, fmaf(c.y, v.x, acc.y));
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = kTuneLanes / 2; o > 0; o >>= 1) {
             acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
             acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
         }
-        if (lane == 0) {
-            float2 z = cmul(bucket_factor((uint32_t)b, logB, logn), acc);
+        if (valid && q == 0) {
+            float2 z = cmul(bucket_factor_tab((uint32_t)b, logB, logn, phase, phase_s, half), acc);
             if (b == 0) {
                 const float2 v = __ldg(&x[H.tau & mask]);
                 z = make_float2(H.cAD * v.x, H.cAD * v.y);
@@ -538,8 +560,20 @@ static GatherHash gather_hash(const atsfft_plan_s *P, const HashParam &hp, int b
     g.log2c = w.log2c;
     g.cAD = w.cA_D;
     g.out_off = out_off;
-    g.warp_start = 0;
+    g.bucket_start = 0;
     return g;
+}
+
+// 256-thread CTAs, 8 warps of 32 / kTuneLanes buckets each per round, at most 8 per SM.
+static void launch_gather_tune(const atsfft_plan_s *P, const float2 *x, const GatherArgs &G,
+                               cudaStream_t s)
+{
+    const int64_t per_cta = 8 * (32 / kTuneLanes);
+    const int64_t blocks = (G.total_buckets + per_cta - 1) / per_cta;
+    const int64_t cap = (int64_t)P->num_sms * 8;
+    k_bin_gather_tune<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(
+        x, P->logn, G, P->d_phase, P->phase_s, P->d_part);
+    count_launch(P);
 }
 
 static StreamHash stream_hash(const atsfft_plan_s *P, const HashParam &hp, int b, int64_t out_off)
@@ -568,7 +602,7 @@ static void launch_stream(const atsfft_plan_s *P, const float2 *x, const StreamA
     const void *fn = (const void *)k_bin_stream<NH, DYN>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_bin_stream<NH, DYN><<<(unsigned)(P->num_sms * kStreamCtas), kStreamThreads, smem, s>>>(
-        x, P->logn, A, job_dev, P->d_win, P->d_part, skip);
+        x, P->logn, A, job_dev, P->d_win, P->d_phase, P->phase_s, P->d_part, skip);
     count_launch(P);
 }
 
@@ -606,7 +640,7 @@ void launch_tuning(const atsfft_plan_s *P, const float2 *x, int stage, cudaStrea
         }
         GatherArgs G;
         G.njobs = 0;
-        G.total_warps = 0;
+        G.total_buckets = 0;
         StreamArgs S;
         memset(&S, 0, sizeof(S));
         int rot_total = 0;
@@ -619,8 +653,8 @@ void launch_tuning(const atsfft_plan_s *P, const float2 *x, int stage, cudaStrea
             } else {
                 GatherHash &g = G.j[G.njobs++];
                 g = gather_hash(P, P->h_tune[b], b, P->tpart_off[b]);
-                g.warp_start = G.total_warps;
-                G.total_warps += (int64_t)1 << b;
+                g.bucket_start = G.total_buckets;
+                G.total_buckets += (int64_t)1 << b;
             }
             logB[nj] = b;
             chunks[nj] = P->tchunks[b];
@@ -628,13 +662,7 @@ void launch_tuning(const atsfft_plan_s *P, const float2 *x, int stage, cudaStrea
             out_off[nj] = P->tz_off[b];
             nj++;
         }
-        if (G.njobs) {
-            const int64_t blocks = (G.total_warps + 7) / 8;
-            const int64_t cap = (int64_t)P->num_sms * 8;
-            k_bin_gather_tune<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(x, P->logn, G,
-                                                                                     P->d_part);
-            count_launch(P);
-        }
+        if (G.njobs) launch_gather_tune(P, x, G, s);
         if (S.nh) {
             S.logR = P->tstream_logR;
             S.chunks = P->tstream_chunks;
@@ -686,7 +714,7 @@ void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
         const int groups = (nh + kGroup - 1) / kGroup;
         dim3 grid(P->num_sms * kPersistCtas, groups);
         k_bin_gather_1d<<<grid, 256, 0, s>>>(x, P->logn, P->d_le, nh, P->d_win, job_dev, 0,
-                                             P->d_part);
+                                             P->d_phase, P->phase_s, P->d_part);
         count_launch(P);
     } else {
         Job jl;
@@ -715,12 +743,8 @@ void launch_single_hash(const atsfft_plan_s *P, const float2 *x, int b, const Ha
             GatherArgs G;
             G.njobs = 1;
             G.j[0] = gather_hash(P, hp, b, 0);
-            G.total_warps = (int64_t)1 << b;
-            const int64_t blocks = (G.total_warps + 7) / 8;
-            const int64_t cap = (int64_t)P->num_sms * 8;
-            k_bin_gather_tune<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(x, P->logn, G,
-                                                                                     P->d_part);
-            count_launch(P);
+            G.total_buckets = (int64_t)1 << b;
+            launch_gather_tune(P, x, G, s);
             chunks = 1;
         }
     } else {
@@ -754,7 +778,7 @@ int launch_est_bin(const atsfft_plan_s *P, const float2 *x, int b, cudaStream_t 
     }
     dim3 grid(P->num_sms * kPersistCtas, (L + kGroup - 1) / kGroup);
     k_bin_gather_1d<<<grid, 256, 0, s>>>(x, P->logn, P->d_le + P->est_base, L, P->d_win, nullptr, b,
-                                         P->d_part);
+                                         P->d_phase, P->phase_s, P->d_part);
     count_launch(P);
     return 1;
 }

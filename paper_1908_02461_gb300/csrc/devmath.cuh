@@ -63,6 +63,39 @@ __device__ __forceinline__ float2 phase_lookup(uint64_t m, const float2 *tab, in
     return make_float2(lo.x * hi.x - lo.y * hi.y, lo.x * hi.y + lo.y * hi.x);
 }
 
+// exp(2 pi i m / n) for m taken mod n (32-bit indices, n <= 2^32).
+__device__ __forceinline__ float2 phase_lookup32(uint32_t m, uint32_t nmask, const float2 *tab,
+                                                 int s)
+{
+    m &= nmask;
+    const float2 lo = __ldg(&tab[m & ((1u << s) - 1)]);
+    const float2 hi = __ldg(&tab[(1u << s) + (m >> s)]);
+    return make_float2(lo.x * hi.x - lo.y * hi.y, lo.x * hi.y + lo.y * hi.x);
+}
+
+// R_u = (-1)^u exp(i pi u / D), D = n / B: exp(i pi u / D) = exp(2 pi i (u B / 2) / n).
+__device__ __forceinline__ float2 rot_factor(int u, int logB, uint32_t nmask, const float2 *tab,
+                                             int s)
+{
+    const float2 r = phase_lookup32((uint32_t)u << (logB - 1), nmask, tab, s);
+    return (u & 1) ? make_float2(-r.x, -r.y) : r;
+}
+
+// S_b = sin(pi b / B) exp(i pi b / n) from the same table: sin(pi b' / B) is the imaginary
+// part of exp(2 pi i (b' D / 2) / n) with b' = min(b, B - b) (an angle in [0, pi/2], so
+// no cancellation), and exp(i pi b / n) = exp(2 pi i floor(b / 2) / n) times
+// half = exp(i pi / n) when b is odd.
+__device__ __forceinline__ float2 bucket_factor_tab(uint32_t b, int logB, int logn,
+                                                    const float2 *tab, int s, float2 half)
+{
+    const uint32_t B = 1u << logB, nmask = (1u << logn) - 1;
+    const uint32_t bp = b <= B / 2 ? b : B - b;
+    const float s1 = phase_lookup32(bp << (logn - logB - 1), nmask, tab, s).y;
+    float2 e = phase_lookup32(b >> 1, nmask, tab, s);
+    if (b & 1) e = cmul(e, half);
+    return make_float2(s1 * e.x, s1 * e.y);
+}
+
 // Eq. (11) as a linear functional of the hash's P-order spectrum: the estimate of
 // coordinate `coord` (1D index, or i * N + j in 2D) is Pz[*idx] * C.
 __device__ __forceinline__ float2 estimate_coef(uint64_t coord, const HashParam &hp, int ndim,

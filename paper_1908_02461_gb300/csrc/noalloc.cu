@@ -18,7 +18,8 @@
 namespace atsfft {
 
 // 12 MiB: bucket partials, four-step intermediate and spectrum (3 x 2^18 complex64),
-// FFT twiddles, and the window-normalisation partial sums and table (FP64).
+// FFT twiddles, the window-normalisation partial sums and table (FP64), and the
+// two-level table of exp(2 pi i m / n).
 constexpr size_t kNoAllocBytes = (size_t)12 << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -42,7 +43,9 @@ constexpr size_t kOffTw = kOffZ + kElems18 * sizeof(float2);
 constexpr size_t kOffWin = kOffTw + (size_t)kTwEntries * sizeof(float2);
 constexpr size_t kOffS0 = kOffWin + 4096;                         // WindowParam table
 constexpr size_t kOffResp = kOffS0 + 256;
-constexpr size_t kOffPartial = kOffResp + kElems18 * sizeof(double);
+constexpr size_t kOffPhase = kOffResp + kElems18 * sizeof(double);   // exp(2 pi i m / n) table
+constexpr size_t kPhaseEntries = (size_t)2 << ((kNoAllocMaxLogN + 1) / 2);
+constexpr size_t kOffPartial = kOffPhase + kPhaseEntries * sizeof(float2);
 constexpr size_t kPartialDoubles = (kNoAllocBytes - kOffPartial) / sizeof(double);
 static_assert(kOffPartial < kNoAllocBytes, "no-alloc scratch layout overflows");
 static_assert(sizeof(WindowParam) * kMaxLogB <= 4096, "window table slot too small");
@@ -67,6 +70,7 @@ __global__ void k_twiddles(float2 *tw);
 __global__ void k_window_partial(int64_t n, int logB, double s, int h, double *partial, int nchunks);
 __global__ void k_window_finish(int64_t D, const double *partial, int nchunks, double *resp,
                                 double *S0_out);
+__global__ void k_phase_table(int logn, int s_bits, float2 *tab);
 
 // Once per device, with it current: the scratch's device address and the twiddles.
 static atsfft_status noalloc_setup(int dev, cudaStream_t s, unsigned char **base)
@@ -130,6 +134,8 @@ extern "C" atsfft_status atsfft_hash_spectrum_noalloc(const void *d_x, int64_t n
     P.d_z = (float2 *)(base + kOffZ);
     P.d_tw = (float2 *)(base + kOffTw);
     P.d_win = (WindowParam *)(base + kOffWin);
+    P.d_phase = (float2 *)(base + kOffPhase);
+    P.phase_s = (logn + 1) / 2;
     P.part_elems = kElems18;
 
     // window of this B (Section II-A-2): shape on the host, normalisation sum on the device
@@ -143,6 +149,7 @@ extern "C" atsfft_status atsfft_hash_spectrum_noalloc(const void *d_x, int64_t n
     double *S0_dev = (double *)(base + kOffS0);
     cudaGetLastError();
     dim3 grid((unsigned)((D + 1 + 127) / 128), (unsigned)nch);
+    k_phase_table<<<P.num_sms, 256, 0, s>>>(logn, P.phase_s, P.d_phase);
     k_window_partial<<<grid, 128, 0, s>>>(n, b, w.s, w.h, partial, nch);
     k_window_finish<<<1, 256, 0, s>>>(D, partial, nch, resp, S0_dev);
     double S0 = 0.0;
