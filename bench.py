@@ -371,7 +371,10 @@ def mixed_workload(args):
         res = autotune(n, k_range=(10, 1000), snr_db=SNR_DB, probes=3, reps=2, seed=SEED)
         tuned[n] = res
     t_tune = time.perf_counter() - t_tune
-    templates = {n: A.Plan((n,), params=A.params(coop_blocks_per_sm=1, **tuned[n].params),
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    coop_sms = num_sms // 4 if args.coop_sms < 0 else args.coop_sms
+    templates = {n: A.Plan((n,), params=A.params(coop_blocks_per_sm=1, coop_sms=coop_sms,
+                                                 **tuned[n].params),
                            seed=SEED) for n in sorted(set(sizes))}
     t0 = time.perf_counter()
     plans = [templates[n].clone() for n in sizes]
@@ -542,6 +545,9 @@ def main():
                     help="estimation loops reuse the location hashes (off: fresh hashes)")
     ap.add_argument("--fixed-k", action="store_true",
                     help="no tuning: B from the true k given as the hint (the SFFT setting)")
+    ap.add_argument("--coop-sms", type=int, default=-1,
+                    help="SMs of the cooperative tails when transforms run concurrently "
+                         "(-1: half the SMs, a quarter for mixed512; 0: all)")
     ap.add_argument("--no-graph", action="store_true",
                     help="time per-signal execs on streams instead of one graph launch per step")
     ap.add_argument("--workload", default="headline", choices=["headline", "mixed512", "grad64"],
@@ -581,12 +587,19 @@ def main():
     xs = [h.to(dev) for h in host]
     nstreams = max(1, min(args.streams, len(sigs)))
     use_graph = not args.no_graph
-    # concurrent transforms (graph branches or streams): tails at one CTA per SM so that
-    # several cooperative grids are resident together
-    pp = A.params(coop_blocks_per_sm=1 if (nstreams > 1 or use_graph) else 0,
-                  tune_stages=args.tune_stages, est_reuse_loc=int(args.est_reuse_loc),
+    # concurrent transforms (graph branches or streams): tails at one CTA per SM on a part
+    # of the SMs, so that several cooperative grids are resident together and the other
+    # transforms' kernels keep the rest
+    concurrent = nstreams > 1 or use_graph
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    coop_sms = (num_sms // 2 if args.coop_sms < 0 else args.coop_sms) if concurrent else 0
+    common = dict(tune_stages=args.tune_stages, est_reuse_loc=int(args.est_reuse_loc),
                   fixed_k=int(args.fixed_k))
+    pp = A.params(coop_blocks_per_sm=1 if concurrent else 0, coop_sms=coop_sms, **common)
     plans = [A.Plan((n,), params=pp, seed=SEED, k_hint=k if args.fixed_k else 0) for k in KS]
+    # the plain path (one transform at a time) with the tails on every SM
+    plain_plans = [A.Plan((n,), params=A.params(**common), seed=SEED,
+                          k_hint=k if args.fixed_k else 0) for k in KS]
     outs = []
     for _ in sigs:
         outs.append(dict(loc=torch.empty(CAPACITY, dtype=torch.int64, device=dev),
@@ -624,7 +637,7 @@ def main():
             stream.wait_event(ev)
 
     def plain_step():
-        for p, x, o in zip(plans, xs, outs):
+        for p, x, o in zip(plain_plans, xs, outs):
             p.exec_async(x, o["loc"], o["val"], o["count"], o["k"], o["status"], stream.cuda_stream)
 
     for _ in range(args.warmup):
@@ -636,7 +649,7 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     # ---- plain per-signal path, in order, with per-kernel phase events -----------------
-    for p in plans:
+    for p in plain_plans:
         p.set_profiling(True)
     plain_ms, phase_acc, stamp_acc = [], [], []
     for _ in range(max(3, args.steps // 4)):
@@ -646,13 +659,13 @@ def main():
         ev1.record(stream)
         ev1.synchronize()
         plain_ms.append(ev0.elapsed_time(ev1))
-        for p in plans:
+        for p in plain_plans:
             ph, _ = p.phase_times()
             phase_acc.append(ph)
             if args.phases:
                 st_ = p.tail_stamps()
                 stamp_acc.append([(b - st_[0]) / 1e3 for b in st_])
-    for p in plans:
+    for p in plain_plans:
         p.set_profiling(False)
     plain_value = len(sigs) * len(plain_ms) / (sum(plain_ms) / 1e3)
 
@@ -706,20 +719,36 @@ def main():
                      val=torch.empty(CAPACITY, dtype=torch.complex64).pin_memory(),
                      scal=torch.empty(3, dtype=torch.int64).pin_memory()) for _ in sigs]
 
+    copy_stream = torch.cuda.Stream(device=dev)
+
+    # largest k first: its transform is the longest, and the last input to land should be
+    # followed by the shortest one
+    order = sorted(range(len(sigs)), key=lambda i: -KS[i])
+
     def e2e_step():
+        # inputs one after another on a copy stream (each at the link's full rate), every
+        # transform on its own stream as soon as its input has landed, outputs back on it
         start = torch.cuda.Event()
         start.record(stream)
-        for i, (p, h, x, o, ho) in enumerate(zip(plans, host, xs, outs, host_out)):
-            st = side[i % nstreams]
-            st.wait_event(start)
+        copy_stream.wait_event(start)
+        landed = {}
+        for i in order:
+            with torch.cuda.stream(copy_stream):
+                xs[i].copy_(host[i], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(copy_stream)
+            landed[i] = ev
+        for j, i in enumerate(order):
+            p, x, o, ho = plans[i], xs[i], outs[i], host_out[i]
+            st = side[j % nstreams]
+            st.wait_event(landed[i])
             with torch.cuda.stream(st):
-                x.copy_(h, non_blocking=True)
                 p.exec_async(x, o["loc"], o["val"], o["count"], o["k"], o["status"], st.cuda_stream)
                 ho["loc"].copy_(o["loc"], non_blocking=True)
                 ho["val"].copy_(o["val"], non_blocking=True)
                 ho["scal"][0:1].copy_(o["count"], non_blocking=True)
                 ho["scal"][1:2].copy_(o["k"], non_blocking=True)
-        for st in side[1:]:
+        for st in side[1:] + [copy_stream]:
             ev = torch.cuda.Event()
             ev.record(st)
             stream.wait_event(ev)
@@ -754,7 +783,7 @@ def main():
                       file=sys.stderr)
     if batch is not None:
         batch.close()
-    for p in plans:
+    for p in plans + plain_plans:
         p.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -772,7 +801,7 @@ def main():
                    "plain_path_ms_per_step": float(np.mean(plain_ms)),
                    "k_star": kstar, "counts": counts, "status": status,
                    "tune_stages": args.tune_stages, "est_reuse_loc": bool(args.est_reuse_loc),
-                   "fixed_k": bool(args.fixed_k),
+                   "fixed_k": bool(args.fixed_k), "coop_sms": coop_sms,
                    "path": ("one CUDA graph per step (atsfft_batch_launch), a branch per signal"
                             if use_graph else
                             "plain per-signal path (one exec per transform)" if nstreams == 1 else

@@ -78,6 +78,12 @@ typedef struct {
                                    the estimation stage in FP64 (Eq. (11) values to
                                    ~1e-12 of an FP64 evaluation).  Slow: FP64 runs at
                                    1/64 of the FP32 rate on GB300                         */
+    int coop_sms;               /* SMs the two cooperative tail kernels spread over
+                                   (coop_blocks_per_sm CTAs on each); 0 (default) = all.
+                                   Transforms that run concurrently (a batch graph,
+                                   several streams) go faster with a fraction: a tail
+                                   mostly waits on its grid barriers, and the SMs it does
+                                   not hold stay free for the other transforms' kernels  */
 } atsfft_params;
 
 /* Fills *p with the defaults listed above. */

@@ -32,7 +32,7 @@ class atsfft_params(C.Structure):
         ("coop_blocks_per_sm", C.c_int),
         ("tune_stages", C.c_int),
         ("fixed_k", C.c_int), ("est_reuse_loc", C.c_int),
-        ("precision", C.c_int),
+        ("precision", C.c_int), ("coop_sms", C.c_int),
     ]
 
 

@@ -243,6 +243,7 @@ extern "C" void atsfft_default_params(atsfft_params *p)
     p->fixed_k = 0;
     p->est_reuse_loc = 0;
     p->precision = 0;
+    p->coop_sms = 0;
 }
 
 extern "C" const char *atsfft_status_string(atsfft_status s)
@@ -276,6 +277,7 @@ static bool params_ok(const atsfft_params *p)
     if (p->est_reuse_loc != 0 && p->est_reuse_loc != 1) return false;
     if (p->est_reuse_loc && p->loops_est > p->loops_loc) return false;
     if (p->precision != 0 && p->precision != 1) return false;
+    if (p->coop_sms < 0) return false;
     return true;
 }
 

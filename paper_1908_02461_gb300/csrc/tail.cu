@@ -1381,7 +1381,8 @@ static int coop_grid(const atsfft_plan_s *P, const void *fn)
     const int want = P->p.coop_blocks_per_sm > 0 ? P->p.coop_blocks_per_sm : 2;
     if (per_sm > want) per_sm = want;
     if (per_sm < 1) per_sm = 1;
-    return P->num_sms * per_sm;
+    const int sms = P->p.coop_sms > 0 && P->p.coop_sms < P->num_sms ? P->p.coop_sms : P->num_sms;
+    return sms * per_sm;
 }
 
 static TuneTailArgs tune_args(const atsfft_plan_s *P)

@@ -129,3 +129,45 @@ def test_autotune_meets_the_error_target(A):
     assert res.ms_per_transform == min(r[1] for r in res.table if r[4])
     p = A.Plan((1 << 14,), params=A.params(**res.params))
     p.close()
+
+
+def test_tail_grid_size_does_not_change_results(A):
+    """The cooperative tails spread over all SMs (default) or a part of them (coop_sms,
+    one CTA per SM) give bit-identical transforms, also inside a batch graph."""
+    import torch
+
+    from synth import sparse_signal_1d, sparse_signal_2d
+
+    cases = [((1 << 16,), sparse_signal_1d(1 << 16, 40, 31, snr_db=40.0).x),
+             ((1 << 20,), sparse_signal_1d(1 << 20, 500, 32, snr_db=40.0).x),
+             ((256, 256), sparse_signal_2d(256, 12, 33).x)]
+    cap = 1 << 12
+    small = A.params(coop_blocks_per_sm=1, coop_sms=19)
+    plans, xs, outs, refs = [], [], [], []
+    for shape, x in cases:
+        xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        ref = A.Plan(shape, seed=3)
+        o = _outputs(torch, cap)
+        ref.exec_async(xd, o["loc"], o["val"], o["count"], o["k"], o["status"])
+        torch.cuda.synchronize()
+        refs.append(_result(o))
+        ref.close()
+        p = A.Plan(shape, params=small, seed=3)
+        o = _outputs(torch, cap)
+        p.exec_async(xd, o["loc"], o["val"], o["count"], o["k"], o["status"])
+        torch.cuda.synchronize()
+        _same(_result(o), refs[-1])
+        plans.append(p)
+        xs.append(xd)
+        outs.append(_outputs(torch, cap))
+    batch = A.Batch([(p, x, o["loc"], o["val"], o["count"], o["k"], o["status"])
+                     for p, x, o in zip(plans, xs, outs)])
+    batch.launch()
+    torch.cuda.synchronize()
+    for o, ref in zip(outs, refs):
+        _same(_result(o), ref)
+    batch.close()
+    for p in plans:
+        p.close()
+    with pytest.raises(A.ATSFFTError):
+        A.Plan((1 << 14,), params=A.params(coop_sms=-1))
