@@ -176,8 +176,8 @@ atsfft_status atsfft_phase_times(atsfft_plan_t plan, float *h_ms, int max_phases
                                  int64_t *h_launches, void *stream);
 
 /* Diagnostics after an exec: device time stamps (ns, %globaltimer) taken at the start
- * of the two cooperative tail kernels and at every grid barrier inside them, in the
- * order they happened (at most 32).  Synchronises `stream`. */
+ * of the two cooperative tail kernels, at every grid barrier inside them and when their
+ * last CTA finishes, in the order they happened (at most 32).  Synchronises `stream`. */
 atsfft_status atsfft_tail_stamps(atsfft_plan_t plan, uint64_t *h_ns, int max_stamps,
                                  int *h_nstamps, void *stream);
 

@@ -95,7 +95,9 @@ struct GridBarrier {
     unsigned gen;
     int err;
     unsigned nstamp;
-    unsigned long long stamp[32];   // %globaltimer at kernel starts and barrier releases
+    unsigned done;                  // CTAs that finished the kernel (end stamp)
+    unsigned pad;
+    unsigned long long stamp[32];   // %globaltimer at kernel starts, barrier releases and ends
 };
 
 // Device-resident state of one exec.

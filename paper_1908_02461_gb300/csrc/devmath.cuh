@@ -44,13 +44,13 @@ __device__ __forceinline__ void axis_terms(uint64_t i, const HashParam &hp, int 
 {
     const uint64_t n = 1ull << logn, D = 1ull << (logn - logB), Bm = (1ull << logB) - 1;
     const uint64_t p = ((uint64_t)hp.sigma[axis] * i) & (n - 1);
-    const uint64_t q = (2 * p + 1 + D) / (2 * D);
+    const uint64_t q = (2 * p + 1 + D) >> (logn - logB + 1);            // / (2 D)
     const int64_t o2 = (int64_t)(2 * p + 1) - (int64_t)(2 * q * D);   // odd, in (-D, D)
     const uint64_t h = q & Bm;
     const uint64_t sp = (uint64_t)hp.sinv[axis] & Bm;                   // sigma^{-1} mod B
     jP = (sp * h) & Bm;
     kph = (jP * ((uint64_t)hp.tau[axis] & Bm)) & Bm;                    // h sigma' tau mod B
-    oidx = (o2 + (int64_t)D - 1) / 2;
+    oidx = (o2 + (int64_t)D - 1) >> 1;                                  // >= 0
     mtau = ((uint64_t)hp.tau[axis] * i) & (n - 1);
 }
 

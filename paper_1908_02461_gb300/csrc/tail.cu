@@ -44,6 +44,19 @@ __device__ __forceinline__ void stamp(GridBarrier *gb)
     if (i < 32) gb->stamp[i] = global_ns();
 }
 
+// Diagnostic end stamp: the last CTA to finish records the time (no waiting).
+__device__ __forceinline__ void end_stamp(GridBarrier *gb)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&gb->done, 1u) == gridDim.x - 1) {
+            stamp(gb);
+            atomicExch(&gb->done, 0u);
+        }
+    }
+}
+
 __device__ bool grid_sync(GridBarrier *gb, int *status)
 {
     __shared__ int ok;
@@ -238,7 +251,7 @@ constexpr int kSmallMedian = 8192;
 // energies by one block: the values are staged in shared memory and selected by rank
 // comparison when there are at most blockDim of them, else with three radix digits
 // (11, 11, 10 bits) over their bit patterns (E >= 0: bit order = value order).
-__device__ uint32_t block_median(const float *E, int nb)
+__device__ __noinline__ uint32_t block_median(const float *E, int nb)
 {
     extern __shared__ __align__(16) uint32_t dsm[];   // phase scratch shared by the tail's phases
     uint32_t *vals = dsm;               // kSmallMedian entries
@@ -414,10 +427,33 @@ __device__ __noinline__ void localmax_task_cold(const JobView &J, const StatsPar
     localmax_task(J, S, T, e0, e1, INFINITY);
 }
 
+// A hash that is one task (nb <= kTask) by the whole block: decide here whether the
+// median can exceed X (then compute it exactly) and count the local maxima with the final
+// threshold, so that such hashes need no median phase after the barrier.  Used by the
+// tuning tail, whose small-B trials often need the median (measured slower in the
+// location tail, where it rarely does).
+__device__ __noinline__ void localmax_whole_hash(const JobView &J, const StatsParams &S, float M,
+                                                 float X, int64_t nb)
+{
+    uint32_t above = 0;
+    for (int64_t j = threadIdx.x; j < nb; j += blockDim.x) above += __ldg(&J.E[j]) > X;
+    above = block_sum(above);
+    float T = S.thr_rel * M;
+    if ((int64_t)above > nb - nb / 2 - 1) {
+        const uint32_t m = block_median(J.E, (int)nb);
+        if (threadIdx.x == 0) {
+            J.st->need_median = 1;
+            J.st->med_bits = m;
+        }
+        T = fmaxf(T, S.thr_med * __uint_as_float(m));
+    }
+    localmax_task(J, S, T, 0, nb, INFINITY);
+}
+
 // Threshold and local maxima of njobs hashes whose energies and maxima the bucket FFTs
 // wrote.  Returns false if a barrier failed.
 __device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &S,
-                             GridBarrier *gb, int *status)
+                             GridBarrier *gb, int *status, bool settle_small)
 {
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
@@ -464,7 +500,11 @@ __device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &
         const int64_t e1 = min(e0 + kTask, nb);
         const float M = __uint_as_float(J.st->max_bits);
         const float X = S.use_median ? M * S.ratio : INFINITY;
-        localmax_task(J, S, S.thr_rel * M, e0, e1, X);
+        if (settle_small && S.use_median && nb <= kTask) {
+            localmax_whole_hash(J, S, M, X, nb);
+        } else {
+            localmax_task(J, S, S.thr_rel * M, e0, e1, X);
+        }
     }
     if (!grid_sync(gb, status)) return false;
     // C: exact median where it can matter, then recount those hashes' maxima.
@@ -473,7 +513,9 @@ __device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &
     if (threadIdx.x < njobs) {
         const JobView &J = jv[threadIdx.x];
         const int64_t nb = nb_of(S.ndim, J.logB);
-        med[threadIdx.x] = J.active && S.use_median && (int64_t)J.st->above > nb - nb / 2 - 1;
+        // (with settle_small, hashes of one task were settled in B)
+        med[threadIdx.x] = J.active && S.use_median && (!settle_small || nb > kTask) &&
+                           (int64_t)J.st->above > nb - nb / 2 - 1;
         mine_small = med[threadIdx.x] && nb <= kSmallMedian;
         mine_large = med[threadIdx.x] && nb > kSmallMedian;
     }
@@ -621,28 +663,43 @@ __device__ void publish_bstar(const TuneTailArgs &A, int b, int64_t k, int statu
 // already evaluated B/2); r = inf when either count is 0; a trial whose energies are
 // all exactly 0 ends with k* = 0.  Then it writes the jobs at B*.  A walk that would
 // step past limit_b (the trials evaluated so far) writes nothing and leaves tune_done
-// at 0 for the second stage, which walks again from B0 over all trials.
+// at 0 for the second stage, which walks again from B0 over all trials.  Called by the
+// first warp of a block: lane t stages trial B0 2^t's counts and its Eq. (12) ratio
+// r = |1 - k_t / k_(t-1)| (FP64, slow on this GPU: all trials' divisions at once instead
+// of one per step of the walk), then lane 0 walks.
 __device__ void controller(const TuneTailArgs &A)
 {
+    __shared__ uint32_t s_nmax[32], s_maxb[32];
+    __shared__ double s_r[32];
+    static_assert(kMaxLogB <= 32, "one lane per trial");
+    const int lane = threadIdx.x & 31;
     const HashStats *stats = A.S.stats;
+    const bool have = lane <= A.b_hi - A.b0;
+    const uint32_t kl = have ? __ldcg(&stats[A.b0 + lane].nmax) : 0u;
+    const uint32_t kp = __shfl_up_sync(0xffffffffu, kl, 1);
+    if (have) {
+        s_nmax[lane] = kl;
+        s_maxb[lane] = __ldcg(&stats[A.b0 + lane].max_bits);
+        s_r[lane] = (kp == 0 || kl == 0) ? INFINITY : fabs(1.0 - (double)kl / (double)kp);
+    }
+    __syncwarp();
+    if (lane != 0) return;
     ExecState *state = A.state;
     int b = A.b0, trial = 0;
-    int64_t kprev = 0, k = 0;
+    int64_t k = 0;
     int status = state->status, empty = 0;
     for (;; trial++) {
-        k = stats[b].nmax;
+        k = s_nmax[b - A.b0];
         if (trial < kMaxTrialsTrace) {
             state->trial_B[trial] = (int64_t)1 << b;
             state->trial_k[trial] = k;
         }
-        if (stats[b].max_bits == 0) {
+        if (s_maxb[b - A.b0] == 0) {
             empty = 1;
             k = 0;
             break;
         }
-        double r = NAN;
-        if (trial > 0) r = (kprev == 0 || k == 0) ? INFINITY : fabs(1.0 - (double)k / (double)kprev);
-        if (trial > 0 && r < A.delta2) break;
+        if (trial > 0 && s_r[b - A.b0] < A.delta2) break;   // r of this trial vs the previous
         if (b == A.b_hi) {
             if (trial > 0 && status == ATSFFT_OK) status = ATSFFT_E_NOT_SPARSE;
             break;
@@ -652,7 +709,6 @@ __device__ void controller(const TuneTailArgs &A)
             break;
         }
         if (b == A.limit_b) return;   // needs the trials of the second stage
-        kprev = k;
         b++;
     }
     if (k == 0) empty = 1;
@@ -669,8 +725,9 @@ __global__ void __launch_bounds__(256, 2) k_tune_tail(const TuneTailArgs A)
 {
     if (A.stage == 2 && A.state->tune_done) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) stamp(&A.state->bar);
-    if (!stats_phases(A.jobs, A.njobs, A.S, &A.state->bar, &A.state->status)) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) controller(A);
+    if (!stats_phases(A.jobs, A.njobs, A.S, &A.state->bar, &A.state->status, true)) return;
+    if (blockIdx.x == 0 && threadIdx.x < 32) controller(A);
+    end_stamp(&A.state->bar);
 }
 
 // ---------------------------------------------------------------------------------
@@ -901,17 +958,40 @@ __device__ __noinline__ float block_select_desc(const float *es, int cnt, uint32
     __shared__ uint32_t pg[kPivots];
     __shared__ float lo_sh, hi_sh, v_sh;
     __shared__ uint32_t nbr;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    if (threadIdx.x < kPivots) pv[threadIdx.x] = es[(int64_t)threadIdx.x * cnt / kPivots];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    static_assert(kPivots == 32, "the reduce-scatter leaves pivot p in lane p");
+    if (threadIdx.x < kPivots) {
+        pv[threadIdx.x] = es[(int64_t)threadIdx.x * cnt / kPivots];
+        pg[threadIdx.x] = 0;
+    }
     if (threadIdx.x == 0) nbr = 0;
     __syncthreads();
-    // g[p] = #{e > pv[p]}: a warp per pivot, lanes over the elements
-    for (int p = warp; p < kPivots; p += nwarp) {
-        const float v = pv[p];
-        uint32_t g = 0;
-        for (int j = lane; j < cnt; j += 32) g += es[j] > v;
-        g = warp_sum(g);
-        if (lane == 0) pg[p] = g;
+    // g[p] = #{e > pv[p]}: every thread counts its elements against all pivots (held in
+    // registers), a reduce-scatter over the warp leaves pivot p's warp total in lane p
+    {
+        float pr[kPivots];
+        uint32_t c[kPivots];
+#pragma unroll
+        for (int p = 0; p < kPivots; p++) {
+            pr[p] = pv[p];
+            c[p] = 0;
+        }
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+            const float e = es[j];
+#pragma unroll
+            for (int p = 0; p < kPivots; p++) c[p] += e > pr[p];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const bool upper = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < o; i++) {
+                const uint32_t send = upper ? c[i] : c[i + o];
+                const uint32_t keep = upper ? c[i + o] : c[i];
+                c[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+        atomicAdd(&pg[lane], c[0]);
     }
     __syncthreads();
     __shared__ uint32_t above_u;
@@ -1008,7 +1088,7 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
             A.bucketbits[(w / words) * A.bucket_words + (w % words)] = 0u;
     }
     // ---- P1 ----
-    if (!stats_phases(A.jobs, A.L_loc, A.S, gb, status)) return;
+    if (!stats_phases(A.jobs, A.L_loc, A.S, gb, status, false)) return;
 
     // ---- P2: top-num cutoff and the selected-bucket bitmaps ----
     // blocks [l G, (l + 1) G) serve hash l; each finds the pivot V itself and decides a
@@ -1293,6 +1373,7 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
                 if (inside) A.loc[r] = coord;
             }
         }
+        end_stamp(gb);
         return;
     }
     // fallback: ordered compaction of the coordinate bitmap, clearing it
@@ -1339,6 +1420,7 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
     }
     if (!grid_sync(gb, status)) return;
     if (!A.skip_est) estimate_all(A, min(K, A.capacity), b);
+    end_stamp(gb);
 }
 
 // ---------------------------------------------------------------------------------
