@@ -2,7 +2,7 @@
 // B x B in 2D): Zhat_c = sum_b z_b exp(-2 pi i c b / B), unscaled.
 //
 // One CTA transforms up to kSmallFFT points in shared memory (radix-2 decimation in
-// time, bit reversal folded into the first register pass, table twiddles).  Larger 1D transforms use the four-step
+// time, bit reversal folded into the loads, table twiddles).  Larger 1D transforms use the four-step
 // split B = P1 * P2 (j = j1 + P1 j2, k = k2 + P2 k1):
 //   pass 0: Y[j1 + P1 k2] = exp(-2 pi i j1 k2 / B) * sum_j2 z[j1 + P1 j2] w_P2^(j2 k2)
 //   pass 1: X[k2 + P2 k1] = sum_j1 Y[j1 + P1 k2] w_P1^(j1 k1).
@@ -142,30 +142,22 @@ __device__ __forceinline__ void radix8_first(float2 (&v)[8])
     bfly(v[3], v[7], make_float2((v[7].y - v[7].x) * r2, -(v[7].x + v[7].y) * r2));
 }
 
-// First group of stages (lm0 = 1): the inputs sit in natural order in shared memory and
-// the group at bit-reversed positions g 2^R + j reads natural index bitrev(g 2^R + j) of
-// its transform.  Every thread reads its group before any thread writes (the positions
-// differ), so a CTA does all TP / 2^R groups at once: TP / 2^R <= blockDim.x holds for
-// every tile (TP <= 4096 = 8 kFftThreads with R = 3).
+// Bit reversal of the low logP bits (positions inside one transform).
+__device__ __forceinline__ int bitrev_in(int j, int logP)
+{
+    return (int)(__brev((unsigned)j) >> (32 - logP));
+}
+
+// First group of stages (lm0 = 1), in place: the loads stored every transform in
+// bit-reversed order, so group g is the 2^R consecutive positions g 2^R + j.
 template <int R>
-__device__ __forceinline__ void first_stages(float2 *sm, int TP, int logP,
-                                             const float2 *__restrict__ tw)
+__device__ __forceinline__ void first_stages(float2 *sm, int TP, const float2 *__restrict__ tw)
 {
     constexpr int E = 1 << R;
-    const int g = threadIdx.x;
-    const bool have = g < (TP >> R);
-    float2 v[E];
-    if (have) {
-        const int P = 1 << logP;
+    for (int g = threadIdx.x; g < (TP >> R); g += blockDim.x) {
+        float2 v[E];
 #pragma unroll
-        for (int j = 0; j < E; j++) {
-            const int p = g * E + j;
-            const int nat = (p & ~(P - 1)) | (int)(__brev((unsigned)(p & (P - 1))) >> (32 - logP));
-            v[j] = sm[padi(nat)];
-        }
-    }
-    __syncthreads();
-    if (have) {
+        for (int j = 0; j < E; j++) v[j] = sm[padi(g * E + j)];
         if constexpr (R == 3)
             radix8_first(v);
         else
@@ -235,11 +227,12 @@ __device__ void fft_tile(const float2 *src, int in_es, int in_bs, int chunks,
                 v.x += w.x;
                 v.y += w.y;
             }
-            sm[padi((u << logP) + j)] = v;
+            sm[padi((u << logP) + bitrev_in(j, logP))] = v;
         }
     } else {
         for (int j = threadIdx.x; j < P; j += blockDim.x) {
             const float4 *p = reinterpret_cast<const float4 *>(src + j * in_es);
+            const int jr = bitrev_in(j, logP);
             // four transforms (two 16-byte loads per chunk) at a time
 #pragma unroll 1
             for (int u = 0; u < T; u += 4) {
@@ -254,22 +247,22 @@ __device__ void fft_tile(const float2 *src, int in_es, int in_bs, int chunks,
                         b.x += wb.x; b.y += wb.y; b.z += wb.z; b.w += wb.w;
                     }
                 }
-                sm[padi((u << logP) + j)] = make_float2(a.x, a.y);
-                sm[padi(((u + 1) << logP) + j)] = make_float2(a.z, a.w);
+                sm[padi((u << logP) + jr)] = make_float2(a.x, a.y);
+                sm[padi(((u + 1) << logP) + jr)] = make_float2(a.z, a.w);
                 if (two) {
-                    sm[padi(((u + 2) << logP) + j)] = make_float2(b.x, b.y);
-                    sm[padi(((u + 3) << logP) + j)] = make_float2(b.z, b.w);
+                    sm[padi(((u + 2) << logP) + jr)] = make_float2(b.x, b.y);
+                    sm[padi(((u + 3) << logP) + jr)] = make_float2(b.z, b.w);
                 }
             }
         }
     }
     __syncthreads();
-    // stages 1 .. logP: groups of three, the first one also doing the bit reversal
+    // stages 1 .. logP: groups of three (the loads already bit-reversed each transform)
     const int r0 = logP < kMaxRadixLog ? logP : kMaxRadixLog;
     switch (r0) {
-    case 3: first_stages<3>(sm, TP, logP, tw); break;
-    case 2: first_stages<2>(sm, TP, logP, tw); break;
-    case 1: first_stages<1>(sm, TP, logP, tw); break;
+    case 3: first_stages<3>(sm, TP, tw); break;
+    case 2: first_stages<2>(sm, TP, tw); break;
+    case 1: first_stages<1>(sm, TP, tw); break;
     default: break;
     }
     for (int lm0 = r0 + 1; lm0 <= logP;) {
