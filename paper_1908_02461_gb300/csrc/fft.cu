@@ -12,6 +12,10 @@
 
 namespace atsfft {
 
+// 1D transforms of up to 2^kSinglePassLog points run in one CTA; larger ones take the
+// four-step split over two passes (more CTAs per transform, each with a short chain).
+constexpr int kSinglePassLog = 10;
+
 struct FftShape {
     int logP;            // transform length
     int ntrans;          // transforms per hash
@@ -29,7 +33,7 @@ __device__ FftShape fft_shape(int ndim, int logB, int pass)
     if (ndim == 1) {
         const int64_t B = (int64_t)1 << logB;
         f.hash_stride = B;
-        if (logB <= 12) {
+        if (logB <= kSinglePassLog) {
             if (pass == 1) { f.valid = 0; return f; }
             f.logP = logB; f.ntrans = 1;
             f.in_es = 1; f.in_bs = B; f.out_es = 1; f.out_bs = B;
@@ -193,9 +197,11 @@ __device__ __forceinline__ void next_stages(float2 *sm, int TP, int lm0,
 
 constexpr int kMaxTile = 8;    // transforms per tile
 
-// exp(-2 pi i m / B) for B = 2^logB in (2^12, 2^24]: coarse table entry times fine entry.
+// exp(-2 pi i m / B) for B = 2^logB <= 2^24: the coarse table entry (times the fine entry
+// above 2^12).
 __device__ __forceinline__ float2 four_step_twiddle(uint32_t m, int logB, const float2 *__restrict__ tw)
 {
+    if (logB <= 12) return __ldg(&tw[m << (12 - logB)]);
     const int sh = logB - 12;
     const float2 c = __ldg(&tw[m >> sh]);
     const float2 f = __ldg(&tw[kSmallFFT + ((m & ((1u << sh) - 1)) << (24 - logB))]);
@@ -218,40 +224,66 @@ __device__ void fft_tile(const float2 *src, int in_es, int in_bs, int chunks,
     const int P = 1 << logP, T = 1 << logT;
     const int TP = T << logP;
     if (in_es == 1 || T == 1) {
-        for (int idx = threadIdx.x; idx < TP; idx += blockDim.x) {
-            const int u = idx >> logP, j = idx & (P - 1);
-            const float2 *p = src + u * in_bs + j;
-            float2 v = p[0];
-            for (int c = 1; c < chunks; c++) {
-                const float2 w = p[c * chunk_stride];
-                v.x += w.x;
-                v.y += w.y;
+        // four elements per thread at a time, their chunk loads issued together
+        for (int idx0 = threadIdx.x; idx0 < TP; idx0 += 4 * blockDim.x) {
+            const float2 *p[4];
+            float2 v[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int idx = idx0 + e * blockDim.x;
+                const int u = (idx < TP ? idx : 0) >> logP, j = (idx < TP ? idx : 0) & (P - 1);
+                p[e] = src + u * in_bs + j;
+                v[e] = idx < TP ? p[e][0] : make_float2(0.f, 0.f);
             }
-            sm[padi((u << logP) + bitrev_in(j, logP))] = v;
+#pragma unroll 2
+            for (int c = 1; c < chunks; c++) {
+                float2 w[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++)
+                    w[e] = idx0 + e * (int)blockDim.x < TP ? p[e][c * chunk_stride] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    v[e].x += w[e].x;
+                    v[e].y += w[e].y;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int idx = idx0 + e * blockDim.x;
+                if (idx < TP)
+                    sm[padi(((idx >> logP) << logP) + bitrev_in(idx & (P - 1), logP))] = v[e];
+            }
         }
     } else {
         for (int j = threadIdx.x; j < P; j += blockDim.x) {
             const float4 *p = reinterpret_cast<const float4 *>(src + j * in_es);
             const int jr = bitrev_in(j, logP);
-            // four transforms (two 16-byte loads per chunk) at a time
-#pragma unroll 1
-            for (int u = 0; u < T; u += 4) {
-                const bool two = u + 2 < T;
-                float4 a = p[u >> 1], b = two ? p[(u >> 1) + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            // up to eight transforms (four 16-byte loads per chunk) at a time, the loads of
+            // a chunk issued together
+            for (int u0 = 0; u0 < T; u0 += 8) {
+                const int nq = min(4, (T - u0) >> 1);   // 16-byte loads (two transforms each)
+                float4 a[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    a[q] = q < nq ? p[(u0 >> 1) + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
                 for (int c = 1; c < chunks; c++) {
-                    const float4 *pc = p + ((c * chunk_stride) >> 1);
-                    const float4 wa = pc[u >> 1];
-                    a.x += wa.x; a.y += wa.y; a.z += wa.z; a.w += wa.w;
-                    if (two) {
-                        const float4 wb = pc[(u >> 1) + 1];
-                        b.x += wb.x; b.y += wb.y; b.z += wb.z; b.w += wb.w;
+                    const float4 *pc = p + ((c * chunk_stride) >> 1) + (u0 >> 1);
+                    float4 w[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) w[q] = q < nq ? pc[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        a[q].x += w[q].x; a[q].y += w[q].y; a[q].z += w[q].z; a[q].w += w[q].w;
                     }
                 }
-                sm[padi((u << logP) + jr)] = make_float2(a.x, a.y);
-                sm[padi(((u + 1) << logP) + jr)] = make_float2(a.z, a.w);
-                if (two) {
-                    sm[padi(((u + 2) << logP) + jr)] = make_float2(b.x, b.y);
-                    sm[padi(((u + 3) << logP) + jr)] = make_float2(b.z, b.w);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    if (q < nq) {
+                        const int u = u0 + 2 * q;
+                        sm[padi((u << logP) + jr)] = make_float2(a[q].x, a[q].y);
+                        sm[padi(((u + 1) << logP) + jr)] = make_float2(a[q].z, a[q].w);
+                    }
                 }
             }
         }
@@ -348,7 +380,7 @@ constexpr int64_t kTileLoads = 8192;
 // Is `pass` the one that writes the final spectrum?
 __device__ __forceinline__ bool final_pass(int ndim, int logB, int pass)
 {
-    return (ndim == 1 && logB <= 12) ? pass == 0 : pass == 1;
+    return (ndim == 1 && logB <= kSinglePassLog) ? pass == 0 : pass == 1;
 }
 
 // Dynamic pass over the nh hashes of the job at B* (shape read on the device).
@@ -367,7 +399,7 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_fft_pass(int ndim, int pass,
     const int chunks = pass == 0 ? job->chunks : 1;
     const FftShape f = fft_shape(ndim, logB, pass);
     if (!f.valid) return;
-    const bool four_step = ndim == 1 && logB > 12;
+    const bool four_step = ndim == 1 && logB > kSinglePassLog;
     const float2 *in = pass == 0 ? part : (ndim == 1 ? tmp : fin);
     float2 *out = (pass == 0 && four_step) ? tmp : fin;
     const int64_t in_hash = (int64_t)chunks * f.hash_stride;
@@ -421,7 +453,7 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_fft_batch(int ndim, int pass
         const FftShape f = fft_shape(ndim, J.logB, pass);
         const int T = J.T;
         const int64_t t = (tr - J.tr_start) * T;
-        const bool four_step = ndim == 1 && J.logB > 12;
+        const bool four_step = ndim == 1 && J.logB > kSinglePassLog;
         const float2 *in =
             pass == 0 ? part + J.in_off : (ndim == 1 ? tmp + J.tmp_off : fin + J.out_off);
         float2 *out = (pass == 0 && four_step) ? tmp + J.tmp_off : fin + J.out_off;
@@ -442,7 +474,7 @@ void launch_bucket_fft_dynamic(const atsfft_plan_s *P, const Job *job, const flo
     k_fft_pass<<<grid, kFftThreads, 0, s>>>(P->ndim, 0, job, part, P->d_fft_tmp, out, P->d_tw,
                                             energy, P->d_stats, n_energy);
     count_launch(P);
-    if (P->ndim == 2 || P->b_hi > 12) {
+    if (P->ndim == 2 || P->b_hi > kSinglePassLog) {
         k_fft_pass<<<grid, kFftThreads, 0, s>>>(P->ndim, 1, job, part, P->d_fft_tmp, out, P->d_tw,
                                                 energy, P->d_stats, n_energy);
         count_launch(P);
@@ -465,7 +497,7 @@ void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB,
             int logP;
             bool strided;
             if (P->ndim == 1) {
-                if (lb <= 12) {
+                if (lb <= kSinglePassLog) {
                     if (pass == 1) continue;
                     ntrans = 1;
                     logP = lb;

@@ -448,8 +448,10 @@ static atsfft_status plan_create(atsfft_plan_t *out, int ndim, const int64_t *sh
     A((void **)&P->d_part, sizeof(float2) * part);
     A((void **)&P->d_tz, sizeof(float2) * tz_total);
     A((void **)&P->d_z, sizeof(float2) * nh_le * nb_max);
-    // four-step intermediate (1D) or per-axis tap tables, nh x 2 x N (2D)
+    // four-step intermediate (1D: the location pass's nh x B*, or every tuning trial's
+    // spectrum size at its tz offset) or per-axis tap tables, nh x 2 x N (2D)
     size_t tmp_elems = (size_t)nh_le * (size_t)nb_max;
+    if ((size_t)tz_total > tmp_elems) tmp_elems = (size_t)tz_total;
     if (ndim == 2 && (size_t)nh_le * 2 * (size_t)n > tmp_elems) tmp_elems = (size_t)nh_le * 2 * (size_t)n;
     A((void **)&P->d_fft_tmp, sizeof(float2) * tmp_elems);
     A((void **)&P->d_energy, sizeof(float) * (tz_total + P->L_loc * nb_max));
