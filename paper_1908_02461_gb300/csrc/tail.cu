@@ -945,6 +945,7 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t i, uint32_t sigma, int lo
 constexpr int kRankStage = 4096;   // top-num by ranking: candidates staged per block
 constexpr int kRankLanes = 8;      // lanes sharing one candidate's rank
 constexpr int kSelBlocks = 4;      // blocks per location hash in the cutoff
+constexpr uint32_t kBandRank = 128; // band sizes ranked by counting (larger: radix select)
 constexpr int kPivots = 32;   // one warp: lane p holds pivot p
 constexpr int kVoteUnroll = 8;     // location hashes whose bitmap words are fetched together
 
@@ -1151,23 +1152,40 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
             if (threadIdx.x == 0) nband = 0;
             __syncthreads();
             uint32_t mine = 0;
-            for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-                const float e = es[i];
-                mine += e > hi;
-                if (e >= lo && e <= hi) band[atomicAdd(&nband, 1u)] = cs[i];
+            for (int64_t i0 = 0; i0 < cnt; i0 += blockDim.x) {
+                // one shared atomic per warp (a unit-magnitude spectrum puts most maxima in
+                // the band: per-element atomics on one counter serialise)
+                const int64_t i = i0 + threadIdx.x;
+                const float e = i < cnt ? es[i] : 0.f;
+                mine += i < cnt && e > hi;
+                const bool in = i < cnt && e >= lo && e <= hi;
+                const unsigned bal = __ballot_sync(0xffffffffu, in);
+                uint32_t base = 0;
+                if (lane == 0 && bal) base = atomicAdd(&nband, (uint32_t)__popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (in) band[base + __popc(bal & ((1u << lane) - 1))] = cs[i];
             }
             const uint32_t nhi = block_sum(mine);   // (synchronises: nband complete)
             const uint32_t need_band = (uint32_t)num - nhi;
-            // the need_band-th smallest band bucket: the band member with that many below
+            // the need_band-th smallest band bucket (distinct indices): by rank counting in
+            // a small band, by radix selection in a large one (unit-magnitude spectra put
+            // most kept maxima inside the band)
             __shared__ uint32_t cthr;
-            for (uint32_t i = threadIdx.x; i < nband; i += blockDim.x) {
-                const uint32_t c = band[i];
-                uint32_t r = 0;
-                for (uint32_t j = 0; j < nband; j++) r += band[j] < c;
-                if (r == need_band - 1) cthr = c;
+            const uint32_t nbd = nband;
+            uint32_t ct;
+            if (nbd <= kBandRank) {
+                for (uint32_t i = threadIdx.x; i < nbd; i += blockDim.x) {
+                    const uint32_t c = band[i];
+                    uint32_t r = 0;
+                    for (uint32_t j = 0; j < nbd; j++) r += band[j] < c;
+                    if (r == need_band - 1) cthr = c;
+                }
+                __syncthreads();
+                ct = cthr;
+            } else {
+                ct = block_kth((int64_t)nbd, need_band - 1, [&](int64_t i) { return band[i]; },
+                               [](int64_t) { return true; });
             }
-            __syncthreads();
-            const uint32_t ct = cthr;
             for (int64_t i0 = (int64_t)sb * blockDim.x; i0 < cnt; i0 += (int64_t)G * blockDim.x) {
                 const int64_t i = i0 + threadIdx.x;
                 bool keep = false;
