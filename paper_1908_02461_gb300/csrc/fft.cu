@@ -383,12 +383,16 @@ __device__ __forceinline__ bool final_pass(int ndim, int logB, int pass)
     return (ndim == 1 && logB <= kSinglePassLog) ? pass == 0 : pass == 1;
 }
 
+// CTAs per SM of the location pass (measured: 3 beats 2 there; the tuning batches, whose
+// first pass also adds partial chunks, keep 2 and their registers).
+constexpr int kPassCtas = 3;
+
 // Dynamic pass over the nh hashes of the job at B* (shape read on the device).
 // part: [hash][chunk][B or B^2]; 1D four-step pass 0 writes `tmp`, pass 1 reads it;
 // everything else ends in `fin` (2D pass 1 in place).  The final pass also writes the
 // energies |Zhat|^2 of the first n_energy hashes (layout of `fin`, base `energy`) and
 // their maxima into stats[kMaxLogB + h].max_bits.
-__global__ void __launch_bounds__(kFftThreads, 2) k_fft_pass(int ndim, int pass, const Job *job,
+__global__ void __launch_bounds__(kFftThreads, kPassCtas) k_fft_pass(int ndim, int pass, const Job *job,
                                                   const float2 *__restrict__ part, float2 *tmp,
                                                   float2 *fin, const float2 *__restrict__ tw,
                                                   float *energy, HashStats *stats, int n_energy)
@@ -470,7 +474,7 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_fft_batch(int ndim, int pass
 void launch_bucket_fft_dynamic(const atsfft_plan_s *P, const Job *job, const float2 *part,
                                float2 *out, float *energy, int n_energy, cudaStream_t s)
 {
-    const int grid = P->num_sms * 2;   // resident CTAs; a grid-stride loop covers the tiles
+    const int grid = P->num_sms * kPassCtas;   // resident CTAs; a grid-stride loop covers the tiles
     k_fft_pass<<<grid, kFftThreads, 0, s>>>(P->ndim, 0, job, part, P->d_fft_tmp, out, P->d_tw,
                                             energy, P->d_stats, n_energy);
     count_launch(P);
