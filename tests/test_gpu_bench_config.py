@@ -1,0 +1,74 @@
+"""The benchmark's own workload in the benchmark's own launch configuration, against the
+oracle: the four signals of one step (n = 2^22, k in {50, 200, 1000, 2000}, 40 dB, the
+same seeds), as one CUDA graph with the tails at one CTA per SM on half the SMs.  Needs a
+GPU."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+KS = (50, 200, 1000, 2000)
+N = 1 << 22
+SEED = 7
+CAPACITY = 1 << 14
+MARGIN_SAFE = 2e-4
+
+
+@pytest.fixture(scope="module")
+def A():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1908_02461_gb300 as A
+
+    A.build()
+    return A
+
+
+def test_bench_step_matches_oracle(A):
+    import torch
+
+    import oracle as O
+    from synth import sparse_signal_1d
+
+    O.build()
+    sigs = [sparse_signal_1d(N, k, 1000 + k, snr_db=40.0) for k in KS]
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    pp = A.params(coop_blocks_per_sm=1, coop_sms=nsm // 2)
+    plans = [A.Plan((N,), params=pp, seed=SEED) for _ in KS]
+    xs = [torch.from_numpy(s.x).cuda() for s in sigs]
+    outs = [dict(loc=torch.empty(CAPACITY, dtype=torch.int64, device="cuda"),
+                 val=torch.empty(CAPACITY, dtype=torch.complex64, device="cuda"),
+                 count=torch.zeros(1, dtype=torch.int64, device="cuda"),
+                 k=torch.zeros(1, dtype=torch.int64, device="cuda"),
+                 status=torch.zeros(1, dtype=torch.int32, device="cuda")) for _ in KS]
+    batch = A.Batch([(p, x, o["loc"], o["val"], o["count"], o["k"], o["status"])
+                     for p, x, o in zip(plans, xs, outs)])
+    for _ in range(2):   # a relaunch gives the same outputs
+        batch.launch()
+    torch.cuda.synchronize()
+    for kk, p, s, o in zip(KS, plans, sigs, outs):
+        count, k, status = int(o["count"].item()), int(o["k"].item()), int(o["status"].item())
+        m = min(count, CAPACITY)
+        loc = o["loc"][:m].cpu().numpy()
+        val = o["val"][:m].cpu().numpy()
+        ref = O.atsfft_1d(s.x, seed=SEED, capacity=CAPACITY)
+        info = dict(k=(k, ref.k_star), count=(count, ref.count), margin=ref.min_margin)
+        if ref.min_margin > MARGIN_SAFE:
+            assert status == ref.status and k == ref.k_star and count == ref.count, info
+            assert loc.tolist() == ref.loc.tolist(), info
+            assert [(int(b), int(kk)) for b, kk, _ in ref.trials] == p.last_trace(), info
+            scale = max(np.max(np.abs(ref.val)) / 100.0, 1e-30) if len(ref.val) else 1.0
+            err = float((np.abs(val - ref.val) / np.maximum(np.abs(ref.val), scale)).max()) if m else 0.0
+            assert err <= 1e-4, (err, info)
+        else:
+            # near a decision boundary: the same trajectory up to one count, the same set
+            # to 99 %
+            assert status == ref.status and abs(k - ref.k_star) <= 1, info
+            common = np.intersect1d(loc, ref.loc)
+            assert len(common) >= 0.99 * min(len(loc), len(ref.loc)), info
+        print(f"[bench config] k={kk} {info}")
+    batch.close()
+    for p in plans:
+        p.close()
