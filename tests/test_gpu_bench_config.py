@@ -68,6 +68,14 @@ def test_bench_step_matches_oracle(A):
             assert status == ref.status and abs(k - ref.k_star) <= 1, info
             common = np.intersect1d(loc, ref.loc)
             assert len(common) >= 0.99 * min(len(loc), len(ref.loc)), info
+            if k == ref.k_star and len(common):
+                # same B* and estimation hashes: the common coordinates' values agree
+                vg = val[np.searchsorted(loc, common)]
+                vr = ref.val[np.searchsorted(ref.loc, common)]
+                scale = max(np.max(np.abs(vr)) / 100.0, 1e-30)
+                err = float((np.abs(vg - vr) / np.maximum(np.abs(vr), scale)).max())
+                assert err <= 1e-4, (err, info)
+                info["common_value_err"] = err
         print(f"[bench config] k={kk} {info}")
     batch.close()
     for p in plans:

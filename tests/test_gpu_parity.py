@@ -76,10 +76,17 @@ def _check_transform(A, O, x, seed, ndim, params_kw=None, capacity=1 << 16, k_hi
         assert err <= 1e-4, (err, info)
         print(f"[strict] {shape} k*={k} count={count} margin={ref.min_margin:.1e} value err={err:.1e}")
         return info, err
-    # near a decision boundary: same trajectory up to one count, mostly the same set
+    # near a decision boundary: same trajectory up to one count, mostly the same set; at
+    # the same k* (same B*, same estimation hashes) the common coordinates' values agree
     assert abs(k - ref.k_star) <= 1, info
     common = np.intersect1d(loc, ref.loc)
     assert len(common) >= 0.99 * min(len(loc), len(ref.loc)), info
+    if k == ref.k_star and len(common):
+        vg = val[np.searchsorted(loc, common)]
+        vr = ref.val[np.searchsorted(ref.loc, common)]
+        err = _compare_values(vg, vr)
+        assert err <= 1e-4, (err, info)
+        info["common_value_err"] = err
     info["weak"] = True
     print(f"[margin-limited] {shape} {info}")
     return info, None
