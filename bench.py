@@ -11,7 +11,7 @@ from fixed seeds and resident in HBM when the timed region starts; L2 is flushed
 value  = transforms / s over the whole job (all ranks), device time (CUDA events);
 e2e    = the same through the C ABI with host buffers: each step copies the four
          signals from pinned host memory, runs the transforms and reads the outputs
-         back, all inside the timed region;
+         back, all inside the timed region (one graph, atsfft_batch_create_io);
 roofline = the dominant kernel of the step, timed by the library's phase events on
          its launch stream during the timed steps;
 cpu_baseline = the FP64 oracle on the host cores, on a bounded sample.
@@ -230,21 +230,22 @@ def _window_h(n, B, alpha=0.5, tol=1e-6):
 
 
 def _chunks(n, B):
-    return max(1, min((1 << 18) // B, n // B))
+    return max(1, min((1 << 16) // B, n // B))
 
 
 def _stream(n, B):
     return 5 * (2 * _window_h(n, B) + 1) >= n and n // B <= 4096
 
 
-def roofline(per_signal, traces, n):
+def roofline(per_signal, traces, n, stages=3):
     """Algorithmic work of each profiled phase per launch, achieved rate, fraction of peak.
 
     Bytes (HBM-bound phases) count each input and output value once; pairs (the
     residue-stream binning, bound by its two MUFU operations per (sample, hash) pair)
-    count samples x hashes.  The two tuning stages split the trials at the last one
-    binned in the gather form; the second stage only counts for transforms whose
-    controller walked past that trial (it exits at once otherwise)."""
+    count samples x hashes.  The tuning stages split the trials at the last one binned in
+    the gather form and (three stages) before the largest; a later stage only counts for
+    transforms whose controller walked past the previous stage's last trial (its kernels
+    exit at once otherwise)."""
     peaks, src = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     pair_peak = SFU_PER_SM_CLK * SMS * SM_MAX_MHZ * 1e6 / 2.0   # 2 SFU ops per pair
@@ -253,26 +254,32 @@ def roofline(per_signal, traces, n):
     gB = [B for B in Bs if not _stream(n, B)]
     sB = [B for B in Bs if _stream(n, B)]
     split = max(gB) if gB else 0
+    s2B = sB[:-1] if stages == 3 and len(sB) >= 2 else sB
+    s3B = sB[-1:] if stages == 3 and len(sB) >= 2 else []
+    split2 = max(s2B) if s2B else split
 
     def fft_bytes(B, chunks):
-        return 8 * B * chunks + 8 * B + 4 * B + (16 * B if B > 4096 else 0)
+        return 8 * B * chunks + 8 * B + 4 * B + (16 * B if B > 1024 else 0)
 
     rows = {}
     for k, ph in per_signal.items():
         # the trace's last trial is B*; an empty trace (fixed-k mode) carries B* alone
         Bstar = traces[k][-1][0]
-        stage2 = len(traces[k]) > 1 and max(b for b, _ in traces[k]) > split
+        walked = max(b for b, _ in traces[k]) if len(traces[k]) > 1 else 0
+        stage2 = walked > split
+        stage3 = walked > split2
         tuned = len(traces[k]) > 1 or traces[k][0][1] is not None
         model = {}
         if tuned:
             model["tune1_bin"] = ("hbm", sum(8 * (2 * _window_h(n, B) + 1) + 8 * B for B in gB))
             model["tune1_fft"] = ("hbm", sum(fft_bytes(B, 1) for B in gB))
             model["tune1_tail"] = ("hbm", sum(4 * B + 4 * B for B in gB))
-        if sB and stage2:
-            R = max(sB)
-            model["tune2_bin"] = ("alu", len(sB) * n)
-            model["tune2_fft"] = ("hbm", sum(fft_bytes(B, _chunks(n, R) * R // B) for B in sB))
-            model["tune2_tail"] = ("hbm", sum(4 * B + 4 * B for B in sB))
+        for nm, tB, on in (("tune2", s2B, stage2), ("tune3", s3B, stage3)):
+            if tB and on:
+                R = max(tB)
+                model[nm + "_bin"] = ("alu", len(tB) * n)
+                model[nm + "_fft"] = ("hbm", sum(fft_bytes(B, _chunks(n, R) * R // B) for B in tB))
+                model[nm + "_tail"] = ("hbm", sum(4 * B + 4 * B for B in tB))
         if _stream(n, Bstar):
             model["le_bin_stream"] = ("alu", NH * n)
         else:
@@ -539,8 +546,9 @@ def main():
     ap.add_argument("--streams", type=int, default=4,
                     help="without --no-graph: ignored; with it, run the step's transforms on "
                          "this many CUDA streams (1 = in order)")
-    ap.add_argument("--tune-stages", type=int, default=2, choices=[1, 2],
-                    help="1D tuning in one batch (1) or small-window trials first (2)")
+    ap.add_argument("--tune-stages", type=int, default=3, choices=[1, 2, 3],
+                    help="1D tuning in one batch (1), small-window trials first (2), and "
+                         "the largest trial last (3)")
     ap.add_argument("--est-reuse-loc", action="store_true",
                     help="estimation loops reuse the location hashes (off: fresh hashes)")
     ap.add_argument("--fixed-k", action="store_true",
@@ -704,7 +712,7 @@ def main():
         rows = phase_acc[i::len(KS)]
         per_signal[k] = {nm: float(np.mean([r[nm] for r in rows])) for nm in names}
     bin_ms = {k: per_signal[k]["le_bin_stream"] + per_signal[k]["le_bin_gather"] for k in KS}
-    tune_stage2 = {k: per_signal[k]["tune2_bin"] + per_signal[k]["tune2_fft"] + per_signal[k]["tune2_tail"]
+    tune_stage2 = {k: sum(per_signal[k][f"tune{st}_{ph}"] for st in (2, 3) for ph in ("bin", "fft", "tail"))
                    for k in KS}
     traces = {}
     for k, p in zip(KS, plans):
@@ -712,46 +720,27 @@ def main():
         if not tr:   # fixed-k mode: no trials, B* from the plan's last result
             tr = [(A._lib.atsfft_last_result(p.handle)[1], None)]
         traces[k] = tr
-    roof, phase_rooflines = roofline(per_signal, traces, n)
+    roof, phase_rooflines = roofline(per_signal, traces, n, stages=args.tune_stages)
 
     # ---- end to end through the C ABI with host buffers -----------------------------
     host_out = [dict(loc=torch.empty(CAPACITY, dtype=torch.int64).pin_memory(),
-                     val=torch.empty(CAPACITY, dtype=torch.complex64).pin_memory(),
-                     scal=torch.empty(3, dtype=torch.int64).pin_memory()) for _ in sigs]
-
-    copy_stream = torch.cuda.Stream(device=dev)
+                     val=torch.empty(CAPACITY, dtype=torch.complex64).pin_memory()) for _ in sigs]
 
     # largest k first: its transform is the longest, and the last input to land should be
-    # followed by the shortest one
+    # followed by the shortest one.  One graph (atsfft_batch_create_io): the inputs are
+    # copied one after another from pinned host memory, each transform starts as soon as
+    # its input has landed, its outputs come back after it.
     order = sorted(range(len(sigs)), key=lambda i: -KS[i])
+    host_scal = [dict(count=torch.zeros(1, dtype=torch.int64).pin_memory(),
+                      k=torch.zeros(1, dtype=torch.int64).pin_memory(),
+                      status=torch.zeros(1, dtype=torch.int32).pin_memory()) for _ in sigs]
+    io_batch = A.Batch([(plans[i], xs[i], outs[i]["loc"], outs[i]["val"], outs[i]["count"],
+                         outs[i]["k"], outs[i]["status"]) for i in order],
+                       host=[dict(x=host[i], loc=host_out[i]["loc"], val=host_out[i]["val"],
+                                  **host_scal[i]) for i in order])
 
     def e2e_step():
-        # inputs one after another on a copy stream (each at the link's full rate), every
-        # transform on its own stream as soon as its input has landed, outputs back on it
-        start = torch.cuda.Event()
-        start.record(stream)
-        copy_stream.wait_event(start)
-        landed = {}
-        for i in order:
-            with torch.cuda.stream(copy_stream):
-                xs[i].copy_(host[i], non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(copy_stream)
-            landed[i] = ev
-        for j, i in enumerate(order):
-            p, x, o, ho = plans[i], xs[i], outs[i], host_out[i]
-            st = side[j % nstreams]
-            st.wait_event(landed[i])
-            with torch.cuda.stream(st):
-                p.exec_async(x, o["loc"], o["val"], o["count"], o["k"], o["status"], st.cuda_stream)
-                ho["loc"].copy_(o["loc"], non_blocking=True)
-                ho["val"].copy_(o["val"], non_blocking=True)
-                ho["scal"][0:1].copy_(o["count"], non_blocking=True)
-                ho["scal"][1:2].copy_(o["k"], non_blocking=True)
-        for st in side[1:] + [copy_stream]:
-            ev = torch.cuda.Event()
-            ev.record(st)
-            stream.wait_event(ev)
+        io_batch.launch(stream.cuda_stream)
 
     for _ in range(2):
         e2e_step()
@@ -767,7 +756,7 @@ def main():
     e2e_total = aggregate(sum(e2e_ms), ws, dev)
     cufft_ms = cufft_reference_ms(n, dev) if rank == 0 else None
     h2d = sum(h.numel() * 8 for h in host)
-    d2h = len(sigs) * (CAPACITY * 8 + CAPACITY * 8 + 16)
+    d2h = len(sigs) * (CAPACITY * 8 + CAPACITY * 8 + 8 + 8 + 4)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -781,6 +770,7 @@ def main():
             if stamp_acc:
                 print("tail stamps us k=%d:" % k, [round(v, 1) for v in stamp_acc[-len(KS) + i]],
                       file=sys.stderr)
+    io_batch.close()
     if batch is not None:
         batch.close()
     for p in plans + plain_plans:

@@ -62,10 +62,12 @@ typedef struct {
     int coop_blocks_per_sm;     /* blocks per SM of the two cooperative tail kernels
                                    (0 = 2); 1 lets several plans' tails run at once on
                                    different streams, all co-resident                   */
-    int tune_stages;            /* 1D tuning batches: 2 (default) evaluates the trials with
-                                   gather-form windows first and the residue-stream trials
-                                   only if the controller has not stopped; 1 evaluates
-                                   every trial in one batch.  Same results either way     */
+    int tune_stages;            /* 1D tuning batches: 3 (default) evaluates the trials with
+                                   gather-form windows first, then the residue-stream
+                                   trials but the largest, then the largest, each batch
+                                   only if the controller has not stopped; 2 keeps the
+                                   residue-stream trials in one batch; 1 evaluates every
+                                   trial in one batch.  Same results either way         */
     int fixed_k;                /* 1: no tuning (the SFFT setting): B is the smallest power of
                                    two with B^2 >= n k (2D: B^4 >= N^2 k) for k = k_hint,
                                    which must then be > 0; k* = k_hint.  0 (default): tune */
@@ -157,16 +159,17 @@ atsfft_status atsfft_last_trace(atsfft_plan_t plan, int64_t *h_B, int64_t *h_k, 
  * (synchronises `stream`). */
 atsfft_status atsfft_last_result(atsfft_plan_t plan, int64_t *h_B, int64_t *h_k, void *stream);
 
-/* Turns per-phase CUDA events on (1) or off (0) for later execs of this plan.  The ten
- * phases of one exec, in order: 0 binning of the first tuning stage (1D: the trials with
- * gather-form windows; 2D: every trial), 1 their bucket FFTs, 2 their statistics and the
- * controller, 3 binning of the second tuning stage (1D: the residue-stream trials, run
- * only when the controller did not stop within the first stage), 4 its bucket FFTs,
- * 5 its statistics and the controller, 6 binning of the location/estimation hashes in
- * the residue-stream form (1D; 2D: tap tables + stream form), 7 the same in the gather
- * form, 8 their bucket FFTs, 9 location statistics, top-num cutoff, votes, ordering,
- * estimation and median.  A form, shape or stage that does not apply exits at once (or
- * is not launched), so its phase measures only an empty launch or nothing. */
+/* Turns per-phase CUDA events on (1) or off (0) for later execs of this plan.  The
+ * thirteen phases of one exec, in order: 0 binning of the first tuning stage (1D: the
+ * trials with gather-form windows; 2D: every trial), 1 their bucket FFTs, 2 their
+ * statistics and the controller, 3-5 the same for the second tuning stage (1D: the
+ * residue-stream trials but the largest), 6-8 for the third (1D: the largest trial);
+ * a later stage runs only when the controller did not stop within the earlier ones,
+ * 9 binning of the location/estimation hashes in the residue-stream form (1D; 2D: tap
+ * tables + stream form), 10 the same in the gather form, 11 their bucket FFTs, 12
+ * location statistics, top-num cutoff, votes, ordering, estimation and median.  A form,
+ * shape or stage that does not apply exits at once (or is not launched), so its phase
+ * measures only an empty launch or nothing. */
 atsfft_status atsfft_set_profiling(atsfft_plan_t plan, int on);
 
 /* After an exec: per-phase device times in ms (h_ms[max_phases], read only if profiling
@@ -229,6 +232,24 @@ atsfft_status atsfft_batch_create(int n, const atsfft_plan_t *plans, const void 
                                   const int64_t *capacity, int64_t *const *d_count,
                                   int64_t *const *d_k, int32_t *const *d_status,
                                   atsfft_batch_t *out);
+
+/* atsfft_batch_create whose graph also moves the data between pinned host memory and
+ * the device: input i is copied from h_x[i] (ncoord complex values of the plan's
+ * precision) to d_x[i] on one copy chain in index order, and transform i starts as soon
+ * as its own input has landed, so every transform but the last overlaps the later
+ * copies; after transform i its outputs go back to h_loc[i] and h_val[i] (capacity[i]
+ * entries each) and its count, k* and status to *h_count[i], *h_k[i], *h_status[i].
+ * Any of the h_ arrays, or any of their entries, may be NULL (no copy).  The host
+ * buffers must be pinned (cudaHostAlloc / cudaHostRegister) and stay valid while the
+ * batch exists; the caller orders the inputs (e.g. the longest transform first). */
+atsfft_status atsfft_batch_create_io(int n, const atsfft_plan_t *plans, const void *const *h_x,
+                                     const void *const *d_x, int64_t *const *d_loc,
+                                     void *const *d_val, const int64_t *capacity,
+                                     int64_t *const *d_count, int64_t *const *d_k,
+                                     int32_t *const *d_status, int64_t *const *h_loc,
+                                     void *const *h_val, int64_t *const *h_count,
+                                     int64_t *const *h_k, int32_t *const *h_status,
+                                     atsfft_batch_t *out);
 
 /* Runs the n transforms of the batch on `stream` (one graph launch; asynchronous).  The
  * outputs of each branch are those of the corresponding plain exec. */

@@ -19,6 +19,7 @@ from ._lib import (  # noqa: F401
     E_NOT_SPARSE,
     OK,
     atsfft_batch_create,
+    atsfft_batch_create_io,
     atsfft_batch_destroy,
     atsfft_batch_kernels,
     atsfft_batch_launch,
@@ -245,17 +246,34 @@ class Batch:
     """Several plans' transforms recorded into one CUDA graph (atsfft_batch_create).
 
     `items` is a sequence of (plan, x, loc, val, count, k, status) with device tensors
-    that must stay alive and in place; `launch()` replays all transforms at once."""
+    that must stay alive and in place; `launch()` replays all transforms at once.  With
+    `host` (one dict per item with pinned CPU tensors under any of the keys x, loc, val,
+    count, k, status), the graph also copies each input from host memory first, in item
+    order, and the outputs back (atsfft_batch_create_io)."""
 
-    def __init__(self, items):
+    def __init__(self, items, host=None):
         import torch
 
         self._keep = list(items)   # the graph holds raw pointers into these tensors
         plans = [it[0].handle for it in items]
-        st, h = atsfft_batch_create(plans, [it[1] for it in items], [it[2] for it in items],
-                                    [it[3] for it in items], [it[2].numel() for it in items],
-                                    [it[4] for it in items], [it[5] for it in items],
-                                    [it[6] for it in items])
+        if host is None:
+            st, h = atsfft_batch_create(plans, [it[1] for it in items], [it[2] for it in items],
+                                        [it[3] for it in items], [it[2].numel() for it in items],
+                                        [it[4] for it in items], [it[5] for it in items],
+                                        [it[6] for it in items])
+        else:
+            for hd in host:
+                for t in hd.values():
+                    if t.device.type != "cpu" or not t.is_pinned():
+                        raise ValueError("host buffers must be pinned CPU tensors")
+            self._keep_host = list(host)
+            get = lambda key: [hd.get(key) for hd in host]
+            st, h = atsfft_batch_create_io(plans, get("x"), [it[1] for it in items],
+                                           [it[2] for it in items], [it[3] for it in items],
+                                           [it[2].numel() for it in items],
+                                           [it[4] for it in items], [it[5] for it in items],
+                                           [it[6] for it in items], get("loc"), get("val"),
+                                           get("count"), get("k"), get("status"))
         if st != OK:
             raise ATSFFTError(st, "atsfft_batch_create")
         self.handle = h

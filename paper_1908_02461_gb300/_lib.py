@@ -40,12 +40,14 @@ EXPORTED = ["atsfft_default_params", "atsfft_plan", "atsfft_exec", "atsfft_exec_
             "atsfft_destroy", "atsfft_status_string", "atsfft_hash_spectrum",
             "atsfft_window_response", "atsfft_last_trace", "atsfft_set_profiling",
             "atsfft_phase_times", "atsfft_tail_stamps", "atsfft_hash_spectrum_noalloc",
-            "atsfft_batch_create", "atsfft_batch_launch", "atsfft_batch_kernels",
+            "atsfft_batch_create", "atsfft_batch_create_io", "atsfft_batch_launch",
+            "atsfft_batch_kernels",
             "atsfft_batch_destroy", "atsfft_plan_clone", "atsfft_exec_sel",
             "atsfft_estimate_apply", "atsfft_estimate_adjoint", "atsfft_last_result"]
 
 PHASES = ["tune1_bin", "tune1_fft", "tune1_tail", "tune2_bin", "tune2_fft", "tune2_tail",
-          "le_bin_stream", "le_bin_gather", "le_fft", "loc_tail"]
+          "tune3_bin", "tune3_fft", "tune3_tail", "le_bin_stream", "le_bin_gather", "le_fft",
+          "loc_tail"]
 
 _lib = None
 
@@ -99,6 +101,9 @@ def load(path: str | None = None):
     L.atsfft_plan_clone.restype = i32
     L.atsfft_batch_create.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, P(vp)]
     L.atsfft_batch_create.restype = i32
+    L.atsfft_batch_create_io.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                         vp, P(vp)]
+    L.atsfft_batch_create_io.restype = i32
     L.atsfft_batch_launch.argtypes = [vp, vp]
     L.atsfft_batch_launch.restype = i32
     L.atsfft_batch_kernels.argtypes = [vp, P(i64)]
@@ -206,6 +211,19 @@ def atsfft_batch_create(plans, d_x, d_loc, d_val, capacity, d_count, d_k, d_stat
     st = load().atsfft_batch_create(n, (C.c_void_p * n)(*plans), arr(d_x), arr(d_loc), arr(d_val),
                                     (C.c_int64 * n)(*capacity), arr(d_count), arr(d_k),
                                     arr(d_status), C.byref(h))
+    return st, h.value
+
+
+def atsfft_batch_create_io(plans, h_x, d_x, d_loc, d_val, capacity, d_count, d_k, d_status,
+                           h_loc, h_val, h_count, h_k, h_status):
+    """Returns (status, batch handle); host sequences may hold None (no copy)."""
+    n = len(plans)
+    arr = lambda xs: (C.c_void_p * n)(*[_ptr(x) if x is not None else None for x in xs])
+    h = C.c_void_p()
+    st = load().atsfft_batch_create_io(n, (C.c_void_p * n)(*plans), arr(h_x), arr(d_x), arr(d_loc),
+                                       arr(d_val), (C.c_int64 * n)(*capacity), arr(d_count),
+                                       arr(d_k), arr(d_status), arr(h_loc), arr(h_val),
+                                       arr(h_count), arr(h_k), arr(h_status), C.byref(h))
     return st, h.value
 
 

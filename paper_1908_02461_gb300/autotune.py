@@ -22,7 +22,7 @@ DEFAULT_GRID = {
     "loops": [(7, 7), (5, 5)],
     "filter_tol": [1e-6, 1e-5],
     "filter_alpha": [0.5],
-    "tune_stages": [2, 1],
+    "tune_stages": [3, 2],
 }
 
 

@@ -43,25 +43,23 @@ static atsfft_status exec_common(atsfft_plan_t P, int ndim, const void *d_x, int
     prof_mark(P, 0, s);
     if (P->p.fixed_k) {
         launch_fixed_setup(P, s);   // B* and k* from the plan: the tuning phases are empty
-        for (int i = 1; i <= 6; i++) prof_mark(P, i, s);
+        for (int i = 1; i <= 9; i++) prof_mark(P, i, s);
     } else {
-        launch_tuning(P, x, 1, s);  // marks phase 1 between its binning and its FFTs
-        prof_mark(P, 2, s);
-        launch_tune_tail(P, 1, s);
-        prof_mark(P, 3, s);
-        launch_tuning(P, x, 2, s);  // marks phase 4
-        prof_mark(P, 5, s);
-        launch_tune_tail(P, 2, s);
-        prof_mark(P, 6, s);
+        for (int stage = 1; stage <= 3; stage++) {
+            launch_tuning(P, x, stage, s);   // marks 1 + 3 (stage - 1) after its binning
+            prof_mark(P, 3 * stage - 1, s);
+            launch_tune_tail(P, stage, s);
+            prof_mark(P, 3 * stage, s);
+        }
     }
     const Job *jd = &P->d_state->job;
-    launch_le_bin(P, x, jd, s);   // marks phase 7 after the stream-form kernel
-    prof_mark(P, 8, s);
+    launch_le_bin(P, x, jd, s);   // marks phase 10 after the stream-form kernel
+    prof_mark(P, 11, s);
     launch_bucket_fft_dynamic(P, jd, P->d_part, P->d_z, P->d_energy + P->e_loc_off, P->L_loc, s);
-    prof_mark(P, 9, s);
+    prof_mark(P, 12, s);
     launch_loc_tail(P, d_loc, (float2 *)d_val, d_msel, capacity, d_count, d_k, d_status, s);
     if (fp64) launch_estimate_fp64(P, d_x, d_loc, d_val, capacity, s);
-    prof_mark(P, 10, s);
+    prof_mark(P, 13, s);
     return cuda_status(cudaGetLastError());
 }
 
@@ -204,11 +202,18 @@ struct atsfft_batch_s {
     int64_t kernels;
 };
 
-extern "C" atsfft_status atsfft_batch_create(int n, const atsfft_plan_t *plans,
-                                             const void *const *d_x, int64_t *const *d_loc,
-                                             void *const *d_val, const int64_t *capacity,
-                                             int64_t *const *d_count, int64_t *const *d_k,
-                                             int32_t *const *d_status, atsfft_batch_t *out)
+// Records the batch graph.  With host buffers (any pointer of an h_ array may be null:
+// no copy), the graph also copies input i from pinned host memory on one copy chain in
+// index order (transform i starts as soon as its own input has landed) and copies its
+// outputs back after its exec.
+static atsfft_status batch_create_impl(int n, const atsfft_plan_t *plans, const void *const *h_x,
+                                       const void *const *d_x, int64_t *const *d_loc,
+                                       void *const *d_val, const int64_t *capacity,
+                                       int64_t *const *d_count, int64_t *const *d_k,
+                                       int32_t *const *d_status, int64_t *const *h_loc,
+                                       void *const *h_val, int64_t *const *h_count,
+                                       int64_t *const *h_k, int32_t *const *h_status,
+                                       atsfft_batch_t *out)
 {
     if (!out) return ATSFFT_E_INVALID_ARG;
     *out = nullptr;
@@ -222,17 +227,21 @@ extern "C" atsfft_status atsfft_batch_create(int n, const atsfft_plan_t *plans,
     atsfft_batch_s *B = new (std::nothrow) atsfft_batch_s;
     if (!B) return ATSFFT_E_NOMEM;
     memset(B, 0, sizeof(*B));
-    // capture: fork from `main` to one stream per plan, each runs its exec, join back
-    cudaStream_t main = nullptr;
+    // capture: fork from `main` to one stream per plan (and a copy stream for the host
+    // inputs), each runs its exec, join back
+    cudaStream_t main = nullptr, copy = nullptr;
     std::vector<cudaStream_t> side(n, nullptr);
-    std::vector<cudaEvent_t> done(n, nullptr);
-    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> done(n, nullptr), landed(n, nullptr);
+    cudaEvent_t fork = nullptr, copied = nullptr;
     atsfft_status st = ATSFFT_OK;
     cudaError_t e = cudaStreamCreateWithFlags(&main, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&copy, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied, cudaEventDisableTiming);
     for (int i = 0; i < n && e == cudaSuccess; i++) {
         e = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&landed[i], cudaEventDisableTiming);
     }
     bool capturing = false;
     if (e == cudaSuccess) e = cudaStreamBeginCapture(main, cudaStreamCaptureModeRelaxed);
@@ -240,16 +249,39 @@ extern "C" atsfft_status atsfft_batch_create(int n, const atsfft_plan_t *plans,
         capturing = true;
         e = cudaEventRecord(fork, main);
     }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(copy, fork, 0);
     for (int i = 0; i < n && e == cudaSuccess && st == ATSFFT_OK; i++) {
-        e = cudaStreamWaitEvent(side[i], fork, 0);
-        if (e != cudaSuccess) break;
         atsfft_plan_s *P = plans[i];
+        const size_t es = P->p.precision == 1 ? 16 : 8;   // complex value size
+        if (h_x && h_x[i]) {
+            e = cudaMemcpyAsync((void *)d_x[i], h_x[i], es * (size_t)P->ncoord,
+                                cudaMemcpyHostToDevice, copy);
+            if (e == cudaSuccess) e = cudaEventRecord(landed[i], copy);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(side[i], landed[i], 0);
+        } else {
+            e = cudaStreamWaitEvent(side[i], fork, 0);
+        }
+        if (e != cudaSuccess) break;
         st = exec_common(P, P->ndim, d_x[i], d_loc[i], d_val[i], capacity[i], d_count[i], d_k[i],
                          d_status[i], side[i]);
         B->kernels += P->launches;
-        if (st == ATSFFT_OK) e = cudaEventRecord(done[i], side[i]);
-        if (e == cudaSuccess && st == ATSFFT_OK) e = cudaStreamWaitEvent(main, done[i], 0);
+        if (st != ATSFFT_OK) break;
+        const size_t cap = (size_t)capacity[i];
+        if (h_loc && h_loc[i] && cap)
+            e = cudaMemcpyAsync(h_loc[i], d_loc[i], 8 * cap, cudaMemcpyDeviceToHost, side[i]);
+        if (e == cudaSuccess && h_val && h_val[i] && cap)
+            e = cudaMemcpyAsync(h_val[i], d_val[i], es * cap, cudaMemcpyDeviceToHost, side[i]);
+        if (e == cudaSuccess && h_count && h_count[i])
+            e = cudaMemcpyAsync(h_count[i], d_count[i], 8, cudaMemcpyDeviceToHost, side[i]);
+        if (e == cudaSuccess && h_k && h_k[i])
+            e = cudaMemcpyAsync(h_k[i], d_k[i], 8, cudaMemcpyDeviceToHost, side[i]);
+        if (e == cudaSuccess && h_status && h_status[i])
+            e = cudaMemcpyAsync(h_status[i], d_status[i], 4, cudaMemcpyDeviceToHost, side[i]);
+        if (e == cudaSuccess) e = cudaEventRecord(done[i], side[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(main, done[i], 0);
     }
+    if (e == cudaSuccess && st == ATSFFT_OK) e = cudaEventRecord(copied, copy);
+    if (e == cudaSuccess && st == ATSFFT_OK) e = cudaStreamWaitEvent(main, copied, 0);
     if (capturing) {
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(main, &g);
@@ -263,9 +295,12 @@ extern "C" atsfft_status atsfft_batch_create(int n, const atsfft_plan_t *plans,
     }
     for (int i = 0; i < n; i++) {
         if (done[i]) cudaEventDestroy(done[i]);
+        if (landed[i]) cudaEventDestroy(landed[i]);
         if (side[i]) cudaStreamDestroy(side[i]);
     }
     if (fork) cudaEventDestroy(fork);
+    if (copied) cudaEventDestroy(copied);
+    if (copy) cudaStreamDestroy(copy);
     if (main) cudaStreamDestroy(main);
     if (st == ATSFFT_OK && e != cudaSuccess) st = cuda_status(e);
     if (st != ATSFFT_OK) {
@@ -277,6 +312,26 @@ extern "C" atsfft_status atsfft_batch_create(int n, const atsfft_plan_t *plans,
     }
     *out = B;
     return ATSFFT_OK;
+}
+
+extern "C" atsfft_status atsfft_batch_create(int n, const atsfft_plan_t *plans,
+                                             const void *const *d_x, int64_t *const *d_loc,
+                                             void *const *d_val, const int64_t *capacity,
+                                             int64_t *const *d_count, int64_t *const *d_k,
+                                             int32_t *const *d_status, atsfft_batch_t *out)
+{
+    return batch_create_impl(n, plans, nullptr, d_x, d_loc, d_val, capacity, d_count, d_k, d_status,
+                             nullptr, nullptr, nullptr, nullptr, nullptr, out);
+}
+
+extern "C" atsfft_status atsfft_batch_create_io(
+    int n, const atsfft_plan_t *plans, const void *const *h_x, const void *const *d_x,
+    int64_t *const *d_loc, void *const *d_val, const int64_t *capacity, int64_t *const *d_count,
+    int64_t *const *d_k, int32_t *const *d_status, int64_t *const *h_loc, void *const *h_val,
+    int64_t *const *h_count, int64_t *const *h_k, int32_t *const *h_status, atsfft_batch_t *out)
+{
+    return batch_create_impl(n, plans, h_x, d_x, d_loc, d_val, capacity, d_count, d_k, d_status,
+                             h_loc, h_val, h_count, h_k, h_status, out);
 }
 
 extern "C" atsfft_status atsfft_batch_launch(atsfft_batch_t B, void *stream)

@@ -621,21 +621,23 @@ static void launch_stream_nh(const atsfft_plan_s *P, const float2 *x, const Stre
 #undef ATSFFT_NH
 }
 
-// Tuning: every B of the range, one hash each, in two stages.  1D stage 1: the
-// small-window trials (b <= tune_split) in one gather launch; stage 2: the large-window
-// ones in one residue-stream pass with R = the largest of their B, every kernel of it
-// returning at once when stage 1 already settled the controller.  2D: one stage, one
-// launch per B.  Each stage ends with the bucket FFTs of its trials in one batch.
+// Tuning: every B of the range, one hash each, in up to three stages (tune_hi).  1D
+// stage 1: the small-window trials in one gather launch; stages 2 and 3: the
+// large-window ones, each stage in one residue-stream pass with R = the largest of its
+// B, every kernel of it returning at once when an earlier stage already settled the
+// controller.  2D: one stage, one launch per B.  Each stage ends with the bucket FFTs of
+// its trials in one batch.  Profiling mark 1 + 3 (stage - 1) separates the two.
 void launch_tuning(const atsfft_plan_s *P, const float2 *x, int stage, cudaStream_t s)
 {
     int logB[kMaxLogB], chunks[kMaxLogB], nj = 0;
     int64_t in_off[kMaxLogB], out_off[kMaxLogB];
     const int *skip = nullptr;
+    const int mark = 1 + 3 * (stage - 1);
     if (P->ndim == 1) {
-        const int lo = stage == 1 ? P->b0 : P->tune_split + 1;
-        const int hi = stage == 1 ? P->tune_split : P->b_hi;
+        const int lo = P->tune_hi[stage - 1] + 1;
+        const int hi = P->tune_hi[stage];
         if (lo > hi) {
-            prof_mark(P, stage == 1 ? 1 : 4, s);
+            prof_mark(P, mark, s);
             return;
         }
         GatherArgs G;
@@ -663,15 +665,15 @@ void launch_tuning(const atsfft_plan_s *P, const float2 *x, int stage, cudaStrea
             nj++;
         }
         if (G.njobs) launch_gather_tune(P, x, G, s);
+        if (stage >= 2) skip = &P->d_state->tune_done;
         if (S.nh) {
-            S.logR = P->tstream_logR;
-            S.chunks = P->tstream_chunks;
-            if (stage == 2) skip = &P->d_state->tune_done;
+            S.logR = P->tstream_logR[stage];
+            S.chunks = P->tstream_chunks[stage];
             launch_stream_nh<false>(P, x, S, nullptr, sizeof(float2) * rot_total, s, skip);
         }
     } else {
         if (stage != 1) {
-            prof_mark(P, 4, s);
+            prof_mark(P, mark, s);
             return;
         }
         for (int b = P->b0; b <= P->b_hi; b++) {
@@ -684,7 +686,7 @@ void launch_tuning(const atsfft_plan_s *P, const float2 *x, int stage, cudaStrea
             nj++;
         }
     }
-    prof_mark(P, stage == 1 ? 1 : 4, s);
+    prof_mark(P, mark, s);
     launch_bucket_fft_batch(P, nj, logB, chunks, in_off, out_off, P->d_part, P->d_tz, P->d_energy,
                             skip, s);
 }
@@ -710,7 +712,7 @@ void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
             for (int g = 0; g < S.nh; g++) S.h[g] = stream_hash(P, P->h_le[g0 + g], -1, 0);
             launch_stream_nh<true>(P, x, S, job_dev, smem, s);
         }
-        prof_mark(P, 7, s);
+        prof_mark(P, 10, s);
         const int groups = (nh + kGroup - 1) / kGroup;
         dim3 grid(P->num_sms * kPersistCtas, groups);
         k_bin_gather_1d<<<grid, 256, 0, s>>>(x, P->logn, P->d_le, nh, P->d_win, job_dev, 0,
@@ -800,7 +802,7 @@ void launch_bin_2d(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
                                              job_host.chunks, taps, part);
         count_launch(P);
     }
-    if (dynamic) prof_mark(P, 7, s);
+    if (dynamic) prof_mark(P, 10, s);
     if (dynamic || !job_host.stream) {
         dim3 grid(persist, job_host.nh);
         k_bin_gather_2d<<<grid, 256, 0, s>>>(x, P->logn, hashes, job_host.nh, P->d_win, jd,

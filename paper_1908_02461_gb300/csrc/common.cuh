@@ -26,7 +26,7 @@ constexpr int kHistBins = 4096;      // radix-select histogram bins (12-bit digi
 constexpr int kKeptCap = 8192;       // kept coordinates ordered by rank (beyond: bitmap compaction)
 constexpr int kAdjRotMax = 8192;     // adjoint: R_u table entries kept in shared memory
 constexpr int kPersistCtas = 4;      // persistent CTAs per SM
-constexpr int kPhases = 10;          // profiled phases of one exec (see atsfft.h)
+constexpr int kPhases = 13;          // profiled phases of one exec (see atsfft.h)
 
 // Permutation of one hash (Def. 1), per axis.
 struct HashParam {
@@ -145,8 +145,11 @@ struct atsfft_plan_s {
     atsfft::Job h_tjob[atsfft::kMaxLogB];
     int64_t tpart_off[atsfft::kMaxLogB];          // tuning partial sums of each B in d_part
     int tchunks[atsfft::kMaxLogB];                // partial blocks the FFT adds up per B
-    int tstream_logR, tstream_chunks;             // the 1D multi-B residue-stream pass
-    int tune_split;        // last log2 B of the first tuning stage (b_hi: one stage)
+    // tuning stages s = 1..3 take the trials (tune_hi[s-1], tune_hi[s]] (tune_hi[0] = b0 - 1;
+    // an empty stage repeats the previous bound); the 1D residue-stream trials of stage s
+    // share one pass of modulus 2^tstream_logR[s] (-1: none) and tstream_chunks[s] chunks
+    int tune_hi[4];
+    int tstream_logR[4], tstream_chunks[4];
 
     atsfft::HashParam *d_tune, *d_le;
     atsfft::WindowParam *d_win;

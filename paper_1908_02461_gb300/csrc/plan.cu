@@ -239,7 +239,7 @@ extern "C" void atsfft_default_params(atsfft_params *p)
     p->b_min_log2 = 0;
     p->b_max_log2 = 0;
     p->coop_blocks_per_sm = 0;
-    p->tune_stages = 2;
+    p->tune_stages = 3;
     p->fixed_k = 0;
     p->est_reuse_loc = 0;
     p->precision = 0;
@@ -272,7 +272,7 @@ static bool params_ok(const atsfft_params *p)
     if (!(p->filter_tol > 0 && p->filter_tol < 1)) return false;
     if (!(p->thr_rel >= 0 && p->thr_med >= 0 && p->tie_eta >= 0 && p->tie_eta < 1)) return false;
     if (p->coop_blocks_per_sm < 0 || p->coop_blocks_per_sm > 8) return false;
-    if (p->tune_stages != 1 && p->tune_stages != 2) return false;
+    if (p->tune_stages < 1 || p->tune_stages > 3) return false;
     if (p->fixed_k != 0 && p->fixed_k != 1) return false;
     if (p->est_reuse_loc != 0 && p->est_reuse_loc != 1) return false;
     if (p->est_reuse_loc && p->loops_est > p->loops_loc) return false;
@@ -406,21 +406,37 @@ static atsfft_status plan_create(atsfft_plan_t *out, int ndim, const int64_t *sh
     // R = the largest of them; B's hash writes chunks(R) * R / B blocks of B values.
     {
         int64_t off = 0;
-        P->tstream_logR = -1;
-        for (int b = P->b0; b <= P->b_hi; b++)
-            if (ndim == 1 && P->h_tjob[b].stream) P->tstream_logR = b;
-        P->tstream_chunks = P->tstream_logR >= 0 ? P->h_tjob[P->tstream_logR].chunks : 1;
-        // two tuning stages in 1D: the leading gather-form trials, then the rest
-        P->tune_split = P->b_hi;
-        if (ndim == 1 && p.tune_stages == 2) {
-            P->tune_split = P->b0 - 1;
-            for (int b = P->b0; b <= P->b_hi && !P->h_tjob[b].stream; b++) P->tune_split = b;
+        // tuning stages in 1D: the leading gather-form trials; then the residue-stream
+        // trials; with three stages the largest trial alone last (rarely needed: it only
+        // runs when the controller walks past the one before it)
+        int s1 = P->b_hi, s2 = P->b_hi;
+        if (ndim == 1 && p.tune_stages >= 2) {
+            s1 = P->b0 - 1;
+            for (int b = P->b0; b <= P->b_hi && !P->h_tjob[b].stream; b++) s1 = b;
+            if (p.tune_stages == 3 && P->b_hi - 1 > s1) s2 = P->b_hi - 1;
         }
+        P->tune_hi[0] = P->b0 - 1;
+        P->tune_hi[1] = s1;
+        P->tune_hi[2] = s2;
+        P->tune_hi[3] = P->b_hi;
+        int stage_of[kMaxLogB];
+        for (int st = 1; st <= 3; st++) {
+            P->tstream_logR[st] = -1;
+            for (int b = P->tune_hi[st - 1] + 1; b <= P->tune_hi[st]; b++) {
+                stage_of[b] = st;
+                if (ndim == 1 && P->h_tjob[b].stream) P->tstream_logR[st] = b;
+            }
+            P->tstream_chunks[st] =
+                P->tstream_logR[st] >= 0 ? P->h_tjob[P->tstream_logR[st]].chunks : 1;
+        }
+        P->tstream_logR[0] = -1;
+        P->tstream_chunks[0] = 1;
         for (int b = P->b0; b <= P->b_hi; b++) {
             int64_t nb = ndim == 1 ? ((int64_t)1 << b) : ((int64_t)1 << (2 * b));
             P->tpart_off[b] = off;
             if (ndim == 1 && P->h_tjob[b].stream) {
-                P->tchunks[b] = P->tstream_chunks << (P->tstream_logR - b);
+                const int st = stage_of[b];
+                P->tchunks[b] = P->tstream_chunks[st] << (P->tstream_logR[st] - b);
             } else if (ndim == 1) {
                 P->tchunks[b] = 1;
             } else {

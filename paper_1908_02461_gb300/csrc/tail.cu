@@ -723,7 +723,7 @@ __global__ void k_fixed_setup(const TuneTailArgs A, int b, int64_t k)
 
 __global__ void __launch_bounds__(256, 2) k_tune_tail(const TuneTailArgs A)
 {
-    if (A.stage == 2 && A.state->tune_done) return;
+    if (A.stage >= 2 && A.state->tune_done) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) stamp(&A.state->bar);
     if (!stats_phases(A.jobs, A.njobs, A.S, &A.state->bar, &A.state->status, true)) return;
     if (blockIdx.x == 0 && threadIdx.x < 32) controller(A);
@@ -1515,14 +1515,14 @@ void launch_fixed_setup(const atsfft_plan_s *P, cudaStream_t s)
 void launch_tune_tail(const atsfft_plan_s *P, int stage, cudaStream_t s)
 {
     // the stage's trials: stat jobs are ordered by log2 B from b0
-    const int first = stage == 1 ? 0 : P->tune_split + 1 - P->b0;
-    const int last = stage == 1 ? P->tune_split - P->b0 : P->ntstat - 1;
+    const int first = P->tune_hi[stage - 1] + 1 - P->b0;
+    const int last = P->tune_hi[stage] - P->b0;
     if (first > last) return;
     TuneTailArgs A = tune_args(P);
     A.jobs = P->d_tstat + first;
     A.njobs = last - first + 1;
     A.stage = stage;
-    A.limit_b = stage == 1 ? P->tune_split : P->b_hi;
+    A.limit_b = P->tune_hi[stage];
     const void *fn = (const void *)k_tune_tail;
     launch_coop(fn, coop_grid(P, fn), &A, s);
     count_launch(P);

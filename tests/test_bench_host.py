@@ -55,7 +55,8 @@ def test_roofline_model_picks_dominant_phase():
 
     n = 1 << 22
     ph = {"tune1_bin": 0.02, "tune1_fft": 0.01, "tune1_tail": 0.02, "tune2_bin": 0.03,
-          "tune2_fft": 0.03, "tune2_tail": 0.02, "le_bin_stream": 0.06, "le_bin_gather": 0.006,
+          "tune2_fft": 0.03, "tune2_tail": 0.02, "tune3_bin": 0.01, "tune3_fft": 0.01,
+          "tune3_tail": 0.01, "le_bin_stream": 0.06, "le_bin_gather": 0.006,
           "le_fft": 0.035, "loc_tail": 0.12}
     traces = {2000: [(16, 0), (65536, 1900)]}
     roof, rows = bench.roofline({2000: ph}, traces, n)
@@ -63,8 +64,14 @@ def test_roofline_model_picks_dominant_phase():
     assert rows["le_bin_stream"]["bound"] == "alu"
     # 14 hashes x n pairs in 0.06 ms
     assert rows["le_bin_stream"]["achieved"] == pytest.approx(14 * n / 0.06e-3 / 1e9)
-    # the second tuning stage ran (the walk reached B = 2^16, past the gather trials)
+    # the second tuning stage ran (the walk reached B = 2^16, past the gather trials), the
+    # third (the largest trial, 2^18) did not
     assert rows["tune2_bin"]["bound"] == "alu"
+    assert rows["tune2_bin"]["achieved"] == pytest.approx(3 * n / 0.03e-3 / 1e9)
+    assert "tune3_bin" not in rows
+    # a walk to 2^18: the third stage's pass (one trial, n pairs) counts too
+    _, rows = bench.roofline({2000: ph}, {2000: [(16, 0), (1 << 18, 1900)]}, n)
+    assert rows["tune3_bin"]["achieved"] == pytest.approx(n / 0.01e-3 / 1e9)
 
 
 def test_roofline_model_skips_unused_second_stage():
@@ -72,7 +79,8 @@ def test_roofline_model_skips_unused_second_stage():
 
     n = 1 << 22
     ph = {nm: 0.01 for nm in ("tune1_bin", "tune1_fft", "tune1_tail", "tune2_bin", "tune2_fft",
-                              "tune2_tail", "le_bin_stream", "le_bin_gather", "le_fft", "loc_tail")}
+                              "tune2_tail", "tune3_bin", "tune3_fft", "tune3_tail",
+                              "le_bin_stream", "le_bin_gather", "le_fft", "loc_tail")}
     traces = {50: [(16, 0), (4096, 49)]}
     _, rows = bench.roofline({50: ph}, traces, n)
-    assert "tune2_bin" not in rows and "tune2_fft" not in rows
+    assert "tune2_bin" not in rows and "tune2_fft" not in rows and "tune3_bin" not in rows

@@ -121,7 +121,7 @@ def test_autotune_meets_the_error_target(A):
     from paper_1908_02461_gb300.autotune import autotune
 
     grid = {"loops": [(7, 7), (5, 5)], "filter_tol": [1e-6], "filter_alpha": [0.5],
-            "tune_stages": [2]}
+            "tune_stages": [3]}
     res = autotune(1 << 14, k_range=(8, 64), snr_db=40.0, error_target=1e-2, probes=2, reps=1,
                    grid=grid)
     assert len(res.table) == 2
@@ -171,3 +171,56 @@ def test_tail_grid_size_does_not_change_results(A):
         p.close()
     with pytest.raises(A.ATSFFTError):
         A.Plan((1 << 14,), params=A.params(coop_sms=-1))
+
+
+def test_io_batch_copies_and_matches_plain_execs(A):
+    """atsfft_batch_create_io: the graph copies the inputs from pinned host memory (one
+    chain, item order), runs the transforms and copies the outputs back; they equal the
+    plain execs' outputs, and a relaunch transforms new host data written in place."""
+    import torch
+
+    from synth import sparse_signal_1d
+
+    cases = [((1 << 16,), sparse_signal_1d(1 << 16, 30, 61, snr_db=40.0).x),
+             ((1 << 18,), sparse_signal_1d(1 << 18, 300, 62, snr_db=40.0).x),
+             ((1 << 14,), sparse_signal_1d(1 << 14, 16, 63).x)]
+    cap = 1 << 12
+    plans, xs, outs, host, refs = [], [], [], [], []
+    for shape, x in cases:
+        p = A.Plan(shape, seed=4)
+        ref = p(torch.from_numpy(x).cuda(), capacity=cap)
+        refs.append((ref[0].cpu().numpy(), ref[1].cpu().numpy(), ref[2], ref[3], ref[4]))
+        plans.append(p)
+        xs.append(torch.zeros(shape, dtype=torch.complex64, device="cuda"))
+        outs.append(_outputs(torch, cap))
+        host.append(dict(x=torch.from_numpy(x).pin_memory(),
+                         loc=torch.zeros(cap, dtype=torch.int64).pin_memory(),
+                         val=torch.zeros(cap, dtype=torch.complex64).pin_memory(),
+                         count=torch.zeros(1, dtype=torch.int64).pin_memory(),
+                         k=torch.zeros(1, dtype=torch.int64).pin_memory(),
+                         status=torch.zeros(1, dtype=torch.int32).pin_memory()))
+    batch = A.Batch([(p, x, o["loc"], o["val"], o["count"], o["k"], o["status"])
+                     for p, x, o in zip(plans, xs, outs)], host=host)
+    for _ in range(2):
+        batch.launch()
+        torch.cuda.synchronize()
+        for h, (loc, val, k, st, cnt) in zip(host, refs):
+            m = min(cnt, cap)
+            assert int(h["count"][0]) == cnt and int(h["k"][0]) == k and int(h["status"][0]) == st
+            assert np.array_equal(h["loc"][:m].numpy(), loc[:m])
+            assert np.array_equal(h["val"][:m].numpy(), val[:m])
+    # new host input in place: the next launch copies and transforms it
+    x2 = sparse_signal_1d(1 << 14, 16, 99).x
+    ref2 = plans[2](torch.from_numpy(x2).cuda(), capacity=cap)
+    host[2]["x"].copy_(torch.from_numpy(x2))
+    batch.launch()
+    torch.cuda.synchronize()
+    m = min(ref2[4], cap)
+    assert int(host[2]["count"][0]) == ref2[4]
+    assert np.array_equal(host[2]["loc"][:m].numpy(), ref2[0][:m].cpu().numpy())
+    batch.close()
+    with pytest.raises(ValueError):
+        A.Batch([(plans[0], xs[0], outs[0]["loc"], outs[0]["val"], outs[0]["count"],
+                  outs[0]["k"], outs[0]["status"])], host=[dict(x=torch.zeros(1 << 16, dtype=torch.complex64))])
+    for p in plans:
+        p.close()

@@ -351,3 +351,26 @@ def test_fp64_plan_rejects_fp32_entries(A):
     with pytest.raises(A.ATSFFTError):
         plan.estimate_adjoint(64, loc, msel, torch.zeros(1, dtype=torch.complex64, device="cuda"))
     plan.close()
+
+
+@pytest.mark.parametrize("n,k,seed", [(1 << 20, 50, 41), (1 << 20, 4000, 42), (1 << 22, 2000, 43),
+                                      (1 << 16, 1500, 44)])
+def test_tuning_stages_give_identical_transforms(A, n, k, seed):
+    """One, two or three tuning batches (Algorithm 2's trials evaluated up front, or in
+    stages that run only while the controller has not stopped) give bit-identical
+    trajectories and outputs; the cases walk to the last trial or stop before it."""
+    from synth import sparse_signal_1d
+
+    sig = sparse_signal_1d(n, k, seed, snr_db=40.0)
+    x = _cuda(sig.x)
+    res = []
+    for stages in (1, 2, 3):
+        plan = A.Plan((n,), params=A.params(tune_stages=stages), seed=5)
+        loc, val, kk, st, cnt = plan(x, capacity=1 << 14)
+        res.append((plan.last_trace(), kk, st, cnt, loc.cpu().numpy(), val.cpu().numpy()))
+        plan.close()
+    for r in res[1:]:
+        assert r[:4] == res[0][:4]
+        assert np.array_equal(r[4], res[0][4])
+        assert np.array_equal(r[5], res[0][5])
+    print(f"[stages] n={n} k={k} trials={len(res[0][0])} last B={res[0][0][-1][0]} status={res[0][2]}")
