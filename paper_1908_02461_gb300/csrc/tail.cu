@@ -1,9 +1,11 @@
 // tail.cu -- everything after the bucket FFTs, as two cooperative (persistent) kernels
 // whose phases are separated by a grid barrier:
 //
-//   k_tune_tail : bucket energies, threshold, local-maximum counts of every tuning trial
-//                 (Section III-A), then the controller walk over Eqs. (12)/(14)
-//                 (Algorithm 2) by one thread, which fixes B*, k* and the jobs at B*.
+//   k_tune_tail : threshold and local-maximum counts of the trials of one tuning stage
+//                 (Section III-A; the energies and their maxima come from the bucket
+//                 FFTs), then the controller walk over Eqs. (12)/(14) (Algorithm 2) by one
+//                 thread, which fixes B*, k* and the jobs at B* (or leaves the walk to the
+//                 next stage).
 //   k_loc_tail  : the same statistics for the location hashes at B* (with the maxima
 //                 listed), the top-num cutoff (Algorithm 1 "find num largest"), votes
 //                 (reverse hash), the ordered compaction of coordinates with votes >=
@@ -15,7 +17,8 @@
 // X' = (thr_rel/thr_med) maxE (1 - 2^-20) the median is <= X' and T = thr_rel * maxE
 // exactly, so the local maxima are found with that T at once; only when the count says
 // the median could matter is it found exactly (three-digit radix select on the energy
-// bit patterns) and the maxima recounted.
+// bit patterns) and the maxima recounted -- in the tuning tail, for trials of at most one
+// statistics task, before the first barrier.
 //
 // The grid barrier spins on a generation word with a bounded number of polls; when the
 // bound runs out the block records ATSFFT_E_CUDA in the exec state and every block
@@ -98,13 +101,6 @@ __device__ __forceinline__ int64_t nb_of(int ndim, int logB)
     return ndim == 1 ? ((int64_t)1 << logB) : ((int64_t)1 << (2 * logB));
 }
 
-__device__ __forceinline__ float warp_max(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
 __device__ __forceinline__ uint32_t warp_sum(uint32_t v)
 {
 #pragma unroll
@@ -113,18 +109,6 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t v)
 }
 
 constexpr int64_t kTask = 4096;   // buckets per statistics task
-
-__device__ float block_max(float v)
-{
-    __shared__ float red[8];
-    v = warp_max(v);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    float m = 0.f;
-    for (int i = 0; i < (int)(blockDim.x >> 5); i++) m = fmaxf(m, red[i]);
-    return m;
-}
 
 __device__ uint32_t block_sum(uint32_t v)
 {
@@ -943,16 +927,16 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t i, uint32_t sigma, int lo
 }
 
 constexpr int kRankStage = 4096;   // top-num by ranking: candidates staged per block
-constexpr int kRankLanes = 8;      // lanes sharing one candidate's rank
 constexpr int kSelBlocks = 4;      // blocks per location hash in the cutoff
 constexpr uint32_t kBandRank = 128; // band sizes ranked by counting (larger: radix select)
 constexpr int kPivots = 32;   // one warp: lane p holds pivot p
 constexpr int kVoteUnroll = 8;     // location hashes whose bitmap words are fetched together
 
 // Value of descending rank r (0-based; equal values ordered by index) among es[0..cnt),
-// by the whole block.  kPivots sampled values are counted against all elements; only the
-// elements between the two pivots that bracket rank r are then ranked exactly (a
-// group of kRankLanes lanes per element).  scratch: cnt entries of shared memory.
+// by the whole block.  kPivots sampled values are counted against all elements (every
+// thread against all pivots); only the elements between the two pivots that bracket
+// rank r are then ranked exactly, one thread per element.  scratch: cnt entries of
+// shared memory.
 __device__ __noinline__ float block_select_desc(const float *es, int cnt, uint32_t r, uint32_t *scratch)
 {
     __shared__ float pv[kPivots];
@@ -1047,11 +1031,13 @@ __device__ __noinline__ float block_select_desc(const float *es, int cnt, uint32
 
 // The location tail.  Phases, each ended by a grid barrier:
 //   P1  thresholds and local maxima of the L_loc location hashes (stats_phases);
-//   P2a top-num pivot: every candidate's rank by energy among its hash's maxima, the one
-//       of rank num - 1 publishes V (hashes with more than kRankStage maxima: one block
-//       does the whole cutoff with radix selection instead);
-//   P2b cutoff (keep E > V(1 + eta), fill from the band [V(1 - eta), V(1 + eta)] in
-//       ascending bucket order) and the selected-bucket bitmaps;
+//   P2  top-num cutoff: each of a few blocks per hash stages its maxima and their
+//       energies, finds the pivot V (the num-th largest; pivot bracketing), keeps
+//       E > V(1 + eta) and fills from the band [V(1 - eta), V(1 + eta)] in ascending
+//       bucket order (the band's cutoff bucket by rank counting or radix selection),
+//       for its share of the candidates, and sets the selected-bucket bitmaps (hashes
+//       with more than kRankStage maxima: one block does the whole cutoff with radix
+//       selection instead);
 //   P3  votes: a kept coordinate lies in >= need selected preimages, hence in one of the
 //       first L_loc - need + 1 hashes' preimages; each such preimage counts the hashes
 //       whose bucket of it is selected (emitted once, by the first hash that has it);
