@@ -2,8 +2,9 @@
 // B x B in 2D): Zhat_c = sum_b z_b exp(-2 pi i c b / B), unscaled.
 //
 // One CTA transforms up to kSmallFFT points in shared memory (radix-2 decimation in
-// time, bit reversal folded into the loads, table twiddles).  Larger 1D transforms use the four-step
-// split B = P1 * P2 (j = j1 + P1 j2, k = k2 + P2 k1):
+// time, bit reversal folded into the loads, table twiddles); 1D transforms of more than
+// 2^kSinglePassLog points use the four-step split B = P1 * P2 (j = j1 + P1 j2,
+// k = k2 + P2 k1), which spreads one transform over many CTAs:
 //   pass 0: Y[j1 + P1 k2] = exp(-2 pi i j1 k2 / B) * sum_j2 z[j1 + P1 j2] w_P2^(j2 k2)
 //   pass 1: X[k2 + P2 k1] = sum_j1 Y[j1 + P1 k2] w_P1^(j1 k1).
 // 2D is rows (pass 0) then columns (pass 1).  The first pass also sums the binning
