@@ -1329,10 +1329,11 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
         *A.d_status = st;
     }
     if (K <= A.kept_cap) {
-        // rank = number of kept coordinates below; a lane group per coordinate splits the
-        // comparisons, then computes the L_est estimates of its coordinate
-        const int grp = A.est_group;
-        const int gl = lane & (grp - 1);
+        // rank = number of kept coordinates below; a warp per coordinate splits the
+        // comparisons (measured: a group of L_est lanes left each lane a long chain of
+        // shared-memory reads), then its first L_est lanes compute the estimates
+        constexpr int grp = 32;
+        const int gl = lane;
         const int per_block = (int)blockDim.x / grp;
         uint32_t *ks = dsm;   // staged kept list chunk
         constexpr int kChunk = 3 * kRankStage;
@@ -1359,12 +1360,23 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
                     }
                 }
                 __syncthreads();
-                if (valid)
-                    for (int64_t i = c0 + gl; i < c1; i += grp) r += ks[i - c0] < coord;
+                if (valid) {
+                    // four independent partial counts per lane
+                    const int m = (int)(c1 - c0);
+                    uint32_t r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+                    int i = gl;
+                    for (; i + 3 * grp < m; i += 4 * grp) {
+                        r0 += ks[i] < coord;
+                        r1 += ks[i + grp] < coord;
+                        r2 += ks[i + 2 * grp] < coord;
+                        r3 += ks[i + 3 * grp] < coord;
+                    }
+                    for (; i < m; i += grp) r0 += ks[i] < coord;
+                    r += r0 + r1 + r2 + r3;
+                }
             }
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1)
-                if (o < grp) r += __shfl_xor_sync(0xffffffffu, r, o, grp);
+            for (int o = 1; o < 32; o <<= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
             const bool inside = valid && r < A.capacity;
             if (!A.skip_est) {
                 float2 v = make_float2(0.f, 0.f);
