@@ -170,6 +170,7 @@ struct atsfft_plan_s {
     atsfft::HashStats *d_stats;   // [kMaxLogB tuning slots][L_loc location slots]
     uint32_t *d_hist;             // [slots][kHistBins]
     int32_t *d_lmax;              // local-maximum lists [L_loc][lmax_cap]
+    float *d_lmax_e;              // their energies, same layout
     int32_t *d_sel;               // selected buckets    [L_loc][lmax_cap]
     int64_t lmax_cap;
     uint32_t *d_bucketbits;       // [L_loc][bucket_words] selected location buckets

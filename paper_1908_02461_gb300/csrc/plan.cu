@@ -284,7 +284,7 @@ static bool params_ok(const atsfft_params *p)
 static void plan_free(atsfft_plan_s *P)
 {
     void *ptrs[] = {P->d_tune, P->d_le, P->d_win, P->d_resp, P->d_rgain, P->d_phase, P->d_tw, P->d_part, P->d_tz,
-                    P->d_z, P->d_fft_tmp, P->d_energy, P->d_stats, P->d_hist, P->d_lmax,
+                    P->d_z, P->d_fft_tmp, P->d_energy, P->d_stats, P->d_hist, P->d_lmax, P->d_lmax_e,
                     P->d_sel, P->d_bucketbits, P->d_kept, P->d_coordbits, P->d_blk, P->d_x32, P->d_f64a,
                     P->d_f64b, P->d_tw64, P->d_state, P->d_tjob, P->d_tstat,
                     P->d_lstat};
@@ -474,6 +474,7 @@ static atsfft_status plan_create(atsfft_plan_t *out, int ndim, const int64_t *sh
     A((void **)&P->d_stats, sizeof(HashStats) * (kMaxLogB + kMaxLoops));
     A((void **)&P->d_hist, sizeof(uint32_t) * kHistBins * (kMaxLogB + kMaxLoops));
     A((void **)&P->d_lmax, sizeof(int32_t) * P->L_loc * P->lmax_cap);
+    A((void **)&P->d_lmax_e, sizeof(float) * P->L_loc * P->lmax_cap);
     A((void **)&P->d_sel, sizeof(int32_t) * P->L_loc * P->lmax_cap);
     A((void **)&P->d_bucketbits, sizeof(uint32_t) * (size_t)P->L_loc * (size_t)P->bucket_words);
     A((void **)&P->d_kept, sizeof(uint32_t) * (size_t)P->kept_cap);

@@ -139,6 +139,7 @@ struct StatsParams {
     HashStats *stats;
     uint32_t *hist;
     int32_t *lists;
+    float *list_e;         // the listed maxima's energies (same layout)
     int64_t cap;
 };
 
@@ -397,7 +398,10 @@ __device__ void localmax_task(const JobView &J, const StatsParams &S, float T, i
                 const uint32_t jA = (uint32_t)(j >> logB), jB = (uint32_t)(j & mask);
                 c = (int32_t)((((s1 * jA) & mask) << logB) | ((s2 * jB) & mask));
             }
-            if (pos < S.cap) lst[pos] = c;
+            if (pos < S.cap) {
+                lst[pos] = c;
+                S.list_e[(int64_t)J.list * S.cap + pos] = ev[u];
+            }
             pos++;
         }
     }
@@ -784,6 +788,40 @@ __device__ uint32_t block_kth(int64_t cnt, uint32_t k, KeyF key, PredF pred)
     return sh_prefix;
 }
 
+// k-th smallest (0-based) of the cnt keys key(i) < 2^bits (bits <= 22) in two radix
+// passes of up to 11 bits each (2048-bin shared histogram).  Whole block must call.
+template <class KeyF>
+__device__ uint32_t block_kth_narrow(int cnt, uint32_t k, int bits, KeyF key)
+{
+    __shared__ uint32_t hist[2048];
+    __shared__ uint32_t sh_prefix, sh_k;
+    const int lo_bits = bits / 2, hi_bits = bits - lo_bits;
+    if (threadIdx.x == 0) {
+        sh_prefix = 0;
+        sh_k = k;
+    }
+    for (int pass = 0; pass < 2; pass++) {
+        const int shift = pass == 0 ? lo_bits : 0;
+        const int width = pass == 0 ? hi_bits : lo_bits;
+        for (int b = threadIdx.x; b < 2048; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        const uint32_t prefix = sh_prefix;
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const uint32_t kk = key(i);
+            if (pass == 0 || (kk >> lo_bits) == prefix) hist_add(hist, (kk >> shift) & ((1u << width) - 1));
+        }
+        __syncthreads();
+        __shared__ uint32_t fb, fr;
+        block_find_rank(hist, 1 << width, sh_k, &fb, &fr);
+        if (threadIdx.x == 0) {
+            sh_prefix = pass == 0 ? fb : ((prefix << lo_bits) | fb);
+            sh_k = fr;
+        }
+        __syncthreads();
+    }
+    return sh_prefix;
+}
+
 constexpr int kTopStage = 4096;
 
 // Top-num cutoff of one location hash by one block: keep every maximum above
@@ -1103,9 +1141,9 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
             float *es = reinterpret_cast<float *>(dsm);   // kRankStage energies
             uint32_t *cs = dsm + kRankStage;              // kRankStage buckets
             uint32_t *band = dsm + 2 * kRankStage;        // band buckets / bracket members
-            const uint32_t mask = (uint32_t)(nb_of(1, b) - 1);
-            const uint32_t p1 = (uint32_t)J.hash->sinv[0] & mask, p2 = (uint32_t)J.hash->sinv[1] & mask;
-            // staged eight per thread at a time: the buckets, then their energies
+            const float *list_e = A.S.list_e + (int64_t)J.list * A.S.cap;
+            // staged eight per thread at a time: the buckets and their energies (listed
+            // together by the local-maximum search)
             for (int64_t i0 = 0; i0 < cnt; i0 += 8 * blockDim.x) {
                 uint32_t cc[8];
                 float ee[8];
@@ -1113,14 +1151,7 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
                 for (int u = 0; u < 8; u++) {
                     const int64_t i = i0 + u * blockDim.x + threadIdx.x;
                     cc[u] = i < cnt ? (uint32_t)list[i] : 0u;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; u++) {
-                    const uint32_t c = cc[u];
-                    const int64_t pj = ndim == 1 ? (int64_t)((p1 * c) & mask)
-                                                 : ((int64_t)((p1 * (c >> b)) & mask) << b) |
-                                                       ((p2 * (c & mask)) & mask);
-                    ee[u] = __ldg(&J.energy[pj]);
+                    ee[u] = i < cnt ? list_e[i] : 0.f;
                 }
 #pragma unroll
                 for (int u = 0; u < 8; u++) {
@@ -1169,8 +1200,13 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
                 __syncthreads();
                 ct = cthr;
             } else {
-                ct = block_kth((int64_t)nbd, need_band - 1, [&](int64_t i) { return band[i]; },
-                               [](int64_t) { return true; });
+                const int kbits = ndim == 1 ? b : 2 * b;   // bucket indices < B (B^2 in 2D)
+                if (kbits <= 22)
+                    ct = block_kth_narrow((int)nbd, need_band - 1, kbits,
+                                          [&](int i) { return band[i]; });
+                else
+                    ct = block_kth((int64_t)nbd, need_band - 1, [&](int64_t i) { return band[i]; },
+                                   [](int64_t) { return true; });
             }
             for (int64_t i0 = (int64_t)sb * blockDim.x; i0 < cnt; i0 += (int64_t)G * blockDim.x) {
                 const int64_t i = i0 + threadIdx.x;
@@ -1454,6 +1490,7 @@ static StatsParams stats_params(const atsfft_plan_s *P)
     S.stats = P->d_stats;
     S.hist = P->d_hist;
     S.lists = P->d_lmax;
+    S.list_e = P->d_lmax_e;
     S.cap = P->lmax_cap;
     return S;
 }
