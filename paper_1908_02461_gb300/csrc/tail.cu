@@ -1112,17 +1112,21 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
         for (int64_t w = gtid; w < (int64_t)A.L_loc * words; w += gthreads)
             A.bucketbits[(w / words) * A.bucket_words + (w % words)] = 0u;
     }
+    // blocks [l G, (l + 1) G) serve hash l in P2; their job is read now (the load overlaps
+    // P1, the barrier makes it visible)
+    const int G = min(kSelBlocks, (int)gridDim.x / A.L_loc);
+    const int l_mine = (int)blockIdx.x / G;
+    const int sb = (int)blockIdx.x % G;
+    __shared__ StatJob sJ;
+    if (threadIdx.x == 0 && l_mine < A.L_loc) sJ = A.jobs[l_mine];
+
     // ---- P1 ----
     if (!stats_phases(A.jobs, A.L_loc, A.S, gb, status, false)) return;
 
     // ---- P2: top-num cutoff and the selected-bucket bitmaps ----
-    // blocks [l G, (l + 1) G) serve hash l; each finds the pivot V itself and decides a
-    // share of the candidates
-    const int G = min(kSelBlocks, (int)gridDim.x / A.L_loc);
-    const int l_mine = (int)blockIdx.x / G;
-    const int sb = (int)blockIdx.x % G;
+    // each block of a hash finds the pivot V itself and decides a share of the candidates
     if (l_mine < A.L_loc) {
-        const StatJob &J = A.jobs[l_mine];
+        const StatJob &J = sJ;
         HashStats &st = A.S.stats[J.slot];
         const int64_t cnt = min((int64_t)st.nmax, A.S.cap);
         uint32_t *bits = A.bucketbits + (int64_t)l_mine * A.bucket_words;
