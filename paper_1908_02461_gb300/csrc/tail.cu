@@ -1255,13 +1255,19 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
         sh_sinv[threadIdx.x][0] = (uint32_t)A.le[threadIdx.x].sinv[0];
         sh_sinv[threadIdx.x][1] = (uint32_t)A.le[threadIdx.x].sinv[1];
     }
-    if (threadIdx.x == 0) {
-        int64_t acc = 0;
-        for (int l = 0; l < L_cand; l++) {
-            off[l] = acc;
-            acc += (int64_t)A.S.stats[kMaxLogB + l].nsel * Dd;
+    if (threadIdx.x < 32) {
+        // the candidate counts of the first L_cand hashes, loaded by one lane each and
+        // summed by a warp scan (one round trip instead of one per hash)
+        static_assert(kMaxLoops <= 32, "one lane per location hash");
+        const int l = threadIdx.x;
+        const int64_t c = l < L_cand ? (int64_t)A.S.stats[kMaxLogB + l].nsel * Dd : 0;
+        int64_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (l >= o) incl += u;
         }
-        off[L_cand] = acc;
+        if (l <= L_cand) off[l] = incl - c;   // exclusive prefix; off[L_cand] = total
     }
     __syncthreads();
     {
