@@ -56,7 +56,7 @@ def _peaks():
 # DRAM bytes of one launch of a phase's kernel, from one ncu capture of the current
 # kernel (dram__bytes_read.sum + dram__bytes_write.sum); None once the kernel changes.
 NCU_TRAFFIC = {
-    "loc_tail": (2877184, "k_loc_tail, 1D n=2^22 k=1000 (B*=2^16), one launch of bench.py --ncu-case 1000"),
+    "loc_tail": (2873600, "k_loc_tail, 1D n=2^22 k=1000 (B*=2^16), one launch of bench.py --ncu-case 1000"),
 }
 
 
