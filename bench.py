@@ -210,10 +210,40 @@ def cpu_baseline(sigs, budget_s=20.0):
             "sample": f"{done} transforms of the step's signals (k cycling), single-threaded FP64"}
 
 
+def _oracle_worker(k):
+    """One oracle transform of the step's signal for k (a separate process)."""
+    import oracle
+    from synth import sparse_signal_1d
+
+    oracle.build()
+    x = sparse_signal_1d(1 << N_LOG2, k, 1000 + k, snr_db=SNR_DB).x
+    t0 = time.perf_counter()
+    oracle.atsfft_1d(x, seed=SEED, capacity=CAPACITY)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(max_procs=16):
+    """The same oracle, one single-threaded process per host core, all at once
+    (independent transforms, k cycling): transforms/s = processes / the longest
+    transform's time (each process times its own oracle call, after generating its
+    signal)."""
+    import multiprocessing as mp
+
+    procs = max(1, min(max_procs, os.cpu_count() or 1))
+    ks = [KS[i % len(KS)] for i in range(procs)]
+    ctx = mp.get_context("spawn")   # spawned, not forked: the parent holds a CUDA context
+    with ctx.Pool(procs) as pool:
+        times = pool.map(_oracle_worker, ks, chunksize=1)
+    return {"value": procs / max(times), "unit": "transforms/s", "cores": procs,
+            "kind": "oracle",
+            "sample": f"{procs} transforms of the step's signals (k cycling) at once, one "
+                      f"single-threaded FP64 process per core"}
+
+
 # ---- roofline model ---------------------------------------------------------------------
 # Algorithmic bytes (or sample-hash pairs) per launch of each single-kernel phase, from
-# the plan's defaults (alpha 0.5, tol 1e-6, 7 + 7 hashes, B range [2^4, n/16]); the
-# formulas are listed in the design doc.
+# the plan's defaults (alpha 0.5, tol 1e-6, 7 + 7 hashes, B range [2^4, n/16]): each value
+# read and written once per launch (roofline() below lists the terms).
 L_LOC, L_EST, NH = 7, 7, 14
 # MUFU (XU pipe) results per clock per SM: ncu rates the XU pipe at one warp instruction
 # per 4 cycles per SM sub-partition (4 x 32 / 4 = 32 lanes per clock per SM)
@@ -758,9 +788,13 @@ def main():
     h2d = sum(h.numel() * 8 for h in host)
     d2h = len(sigs) * (CAPACITY * 8 + CAPACITY * 8 + 8 + 8 + 4)
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sigs)
+        try:
+            cpu_all = cpu_baseline_all_cores()
+        except Exception as exc:   # the single-threaded figure stands on its own
+            cpu_all = {"unavailable": f"{type(exc).__name__}: {exc}"}
 
     clocks = clk.summary()
     if args.phases and rank == 0:
@@ -805,6 +839,7 @@ def main():
         "roofline": roof,
         "phase_rooflines": phase_rooflines,
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
         "clocks": clocks,
     }
     print(json.dumps(line))

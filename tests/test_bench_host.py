@@ -84,3 +84,10 @@ def test_roofline_model_skips_unused_second_stage():
     traces = {50: [(16, 0), (4096, 49)]}
     _, rows = bench.roofline({50: ph}, traces, n)
     assert "tune2_bin" not in rows and "tune2_fft" not in rows and "tune3_bin" not in rows
+
+
+def test_all_cores_oracle_baseline_runs_in_spawned_processes():
+    import bench
+
+    r = bench.cpu_baseline_all_cores(max_procs=2)
+    assert r["kind"] == "oracle" and r["cores"] == 2 and r["value"] > 0
