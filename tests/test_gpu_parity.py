@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.  Needs a GPU.
 
-Tolerances (from the spec bar and FP32 arithmetic):
+Tolerances (the 1e-4 value bar of the hot path, and FP32 arithmetic):
   * window tables Ghat': both sides FP64, 1e-9 absolute;
   * bucket spectra (permute + window + bin + bucket FFT, FP32 on the GPU):
     max |Zhat_gpu - Zhat_oracle| <= 2e-5 * max |Zhat_oracle| (errors of FP32 taps and
