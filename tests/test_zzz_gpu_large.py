@@ -1,0 +1,77 @@
+"""The largest 1D sizes, where sample indices no longer fit the 2^23 exponent trick of
+the binning: n = 2^26 against the oracle (about half a minute of CPU time), and the
+maximum n = 2^28 on an exactly sparse input built on the device, checked against its
+exact spectrum (the oracle is too slow there).  At these sizes the vote rule keeps
+coordinates outside the support (about n C(7,4) (k/B*)^4 of them; the oracle keeps the
+same ones), whose estimates are zero to FP32 accuracy.  Needs a GPU."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def A():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1908_02461_gb300 as A
+
+    A.build()
+    return A
+
+
+def _exact_sparse(logn, k, seed):
+    import torch
+
+    n = 1 << logn
+    rng = np.random.default_rng(seed)
+    support = np.sort(rng.choice(n, size=k, replace=False)).astype(np.int64)
+    coeffs = np.exp(2j * np.pi * rng.uniform(size=k))
+    xhat = torch.zeros(n, dtype=torch.complex128, device="cuda")
+    xhat[torch.from_numpy(support).cuda()] = torch.from_numpy(coeffs).cuda()
+    x = torch.fft.ifft(xhat).to(torch.complex64).contiguous()   # x_t = (1/n) sum xhat e^{+}
+    return x, support, coeffs
+
+
+def test_n_2_26_matches_oracle(A):
+    import oracle as O
+
+    O.build()
+    x, support, coeffs = _exact_sparse(26, 300, 26)
+    plan = A.Plan((1 << 26,), seed=3)
+    loc, val, kk, st, cnt = plan(x, capacity=1 << 12)
+    trace = plan.last_trace()
+    plan.close()
+    loc = loc.cpu().numpy()
+    val = val.cpu().numpy()
+    ref = O.atsfft_1d(x.cpu().numpy(), seed=3, capacity=1 << 12)
+    info = dict(k=(kk, ref.k_star), count=(cnt, ref.count), margin=ref.min_margin)
+    print(f"[large] n=2^26 {info}")
+    assert st == ref.status and kk == ref.k_star and cnt == ref.count, info
+    if ref.min_margin > 2e-4:
+        assert loc.tolist() == ref.loc.tolist(), info
+        assert [(int(b), int(k)) for b, k, _ in ref.trials] == trace, info
+    assert np.isin(support, loc).all()
+    common, ig, ir = np.intersect1d(loc, ref.loc, return_indices=True)
+    assert len(common) >= 0.99 * len(ref.loc), info
+    assert float(np.abs(val[ig] - ref.val[ir]).max()) < 1e-4
+
+
+def test_maximum_n_2_28_exactly_sparse(A):
+    x, support, coeffs = _exact_sparse(28, 100, 28)
+    plan = A.Plan((1 << 28,), seed=3)
+    loc, val, kk, st, cnt = plan(x, capacity=1 << 14)
+    plan.close()
+    loc = loc.cpu().numpy()
+    val = val.cpu().numpy()
+    print(f"[large] n=2^28 k*={kk} count={cnt} status={st}")
+    assert st == A.OK
+    on = np.isin(loc, support)
+    assert on.sum() == len(support)   # every support location found
+    vs = val[on]
+    cs = coeffs[np.searchsorted(support, loc[on])]
+    assert float(np.abs(vs - cs).max()) < 2e-3
+    if (~on).any():
+        assert float(np.abs(val[~on]).max()) < 1e-3
