@@ -10,6 +10,7 @@ without sharing any of the method's code.
 from .signals import (  # noqa: F401
     SparseSignal,
     sparse_signal_1d,
+    sparse_spectrum_1d,
     sparse_signal_2d,
     l1_error_per_coefficient,
 )

@@ -44,6 +44,19 @@ def _add_noise(rng, x, snr_db):
     return x + (noise[..., 0] + 1j * noise[..., 1]), var
 
 
+def _spectrum(rng, size, k, mag):
+    support = np.sort(rng.choice(size, size=k, replace=False)).astype(np.int64)
+    phases = rng.uniform(0.0, 2.0 * np.pi, size=k)
+    mags = _magnitudes(rng, k, mag)
+    return support, mags * np.exp(1j * phases)
+
+
+def sparse_spectrum_1d(n: int, k: int, seed: int, mag="unit"):
+    """(support, coeffs) of `sparse_signal_1d(n, k, seed, mag=mag)` without forming the
+    signal (the same draws, so the same spectrum)."""
+    return _spectrum(np.random.default_rng(seed), n, k, mag)
+
+
 def sparse_signal_1d(n: int, k: int, seed: int, snr_db: float | None = None,
                      mag="unit", dtype=np.complex64) -> SparseSignal:
     """n-sample signal whose DFT has exactly k nonzero bins (plus optional noise).
@@ -53,10 +66,7 @@ def sparse_signal_1d(n: int, k: int, seed: int, snr_db: float | None = None,
     computed in FP64 and stored as `dtype` (complex64 by default).
     """
     rng = np.random.default_rng(seed)
-    support = np.sort(rng.choice(n, size=k, replace=False)).astype(np.int64)
-    phases = rng.uniform(0.0, 2.0 * np.pi, size=k)
-    mags = _magnitudes(rng, k, mag)
-    coeffs = mags * np.exp(1j * phases)
+    support, coeffs = _spectrum(rng, n, k, mag)
     xhat = np.zeros(n, dtype=np.complex128)
     xhat[support] = coeffs
     x = np.fft.ifft(xhat)
@@ -71,10 +81,7 @@ def sparse_signal_2d(N: int, k: int, seed: int, snr_db: float | None = None,
     The support is returned as linear indices u*N + v (row-major).
     """
     rng = np.random.default_rng(seed)
-    support = np.sort(rng.choice(N * N, size=k, replace=False)).astype(np.int64)
-    phases = rng.uniform(0.0, 2.0 * np.pi, size=k)
-    mags = _magnitudes(rng, k, mag)
-    coeffs = mags * np.exp(1j * phases)
+    support, coeffs = _spectrum(rng, N * N, k, mag)
     xhat = np.zeros(N * N, dtype=np.complex128)
     xhat[support] = coeffs
     x = np.fft.ifft2(xhat.reshape(N, N))

@@ -1,14 +1,23 @@
 """The largest 1D sizes, where sample indices no longer fit the 2^23 exponent trick of
-the binning: n = 2^26 against the oracle (about half a minute of CPU time), and the
-maximum n = 2^28 on an exactly sparse input built on the device, checked against its
-exact spectrum (the oracle is too slow there).  At these sizes the vote rule keeps
+the binning: n = 2^26 against the oracle run here (about half a minute of CPU time), and
+the maximum n = 2^28 against the oracle's stored result (tests/golden/
+oracle_1d_n2p28_k100.json, written by tests/golden/make_oracle_large.py: the oracle needs
+minutes there) and against the exact spectrum.  At these sizes the vote rule keeps
 coordinates outside the support (about n C(7,4) (k/B*)^4 of them; the oracle keeps the
 same ones), whose estimates are zero to FP32 accuracy.  Needs a GPU."""
+
+import json
+import os
 
 import numpy as np
 import pytest
 
+from synth import sparse_signal_1d
+
 pytestmark = pytest.mark.gpu
+
+GOLDEN_28 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                         "oracle_1d_n2p28_k100.json")
 
 
 @pytest.fixture(scope="module")
@@ -22,31 +31,24 @@ def A():
     return A
 
 
-def _exact_sparse(logn, k, seed):
+def _on_device(sig):
     import torch
 
-    n = 1 << logn
-    rng = np.random.default_rng(seed)
-    support = np.sort(rng.choice(n, size=k, replace=False)).astype(np.int64)
-    coeffs = np.exp(2j * np.pi * rng.uniform(size=k))
-    xhat = torch.zeros(n, dtype=torch.complex128, device="cuda")
-    xhat[torch.from_numpy(support).cuda()] = torch.from_numpy(coeffs).cuda()
-    x = torch.fft.ifft(xhat).to(torch.complex64).contiguous()   # x_t = (1/n) sum xhat e^{+}
-    return x, support, coeffs
+    return torch.from_numpy(sig.x).cuda()
 
 
 def test_n_2_26_matches_oracle(A):
     import oracle as O
 
     O.build()
-    x, support, coeffs = _exact_sparse(26, 300, 26)
+    sig = sparse_signal_1d(1 << 26, 300, 26)
     plan = A.Plan((1 << 26,), seed=3)
-    loc, val, kk, st, cnt = plan(x, capacity=1 << 12)
+    loc, val, kk, st, cnt = plan(_on_device(sig), capacity=1 << 12)
     trace = plan.last_trace()
     plan.close()
     loc = loc.cpu().numpy()
     val = val.cpu().numpy()
-    ref = O.atsfft_1d(x.cpu().numpy(), seed=3, capacity=1 << 12)
+    ref = O.atsfft_1d(sig.x, seed=3, capacity=1 << 12)
     info = dict(k=(kk, ref.k_star), count=(cnt, ref.count), margin=ref.min_margin)
     print(f"[large] n=2^26 {info}")
     assert st == ref.status, info
@@ -56,28 +58,38 @@ def test_n_2_26_matches_oracle(A):
         assert [(int(b), int(k)) for b, k, _ in ref.trials] == trace, info
     else:   # near a decision boundary: the same trajectory up to one count
         assert abs(kk - ref.k_star) <= 1, info
-    assert np.isin(support, loc).all()
+    assert np.isin(sig.support, loc).all()
     common, ig, ir = np.intersect1d(loc, ref.loc, return_indices=True)
     assert len(common) >= 0.99 * len(ref.loc), info
     if kk == ref.k_star:
         assert float(np.abs(val[ig] - ref.val[ir]).max()) < 1e-4
 
 
-def test_maximum_n_2_28_exactly_sparse(A):
-    x, support, coeffs = _exact_sparse(28, 100, 28)
-    plan = A.Plan((1 << 28,), seed=3)
-    loc, val, kk, st, cnt = plan(x, capacity=1 << 14)
+def test_maximum_n_2_28_matches_stored_oracle(A):
+    with open(GOLDEN_28) as f:
+        g = json.load(f)
+    sig = sparse_signal_1d(1 << g["logn"], g["k"], g["signal_seed"])
+    plan = A.Plan((1 << g["logn"],), seed=g["plan_seed"])
+    loc, val, kk, st, cnt = plan(_on_device(sig), capacity=g["capacity"])
+    trace = plan.last_trace()
     plan.close()
     loc = loc.cpu().numpy()
     val = val.cpu().numpy()
-    print(f"[large] n=2^28 k*={kk} count={cnt} status={st}")
-    assert st == A.OK
-    on = np.isin(loc, support)
-    assert on.sum() == len(support)   # every support location found
-    vs = val[on]
-    cs = coeffs[np.searchsorted(support, loc[on])]
-    assert float(np.abs(vs - cs).max()) < 2e-3
-    if (~on).any():
-        # a coordinate outside the support whose bucket holds a support coefficient in 4 of
-        # the 7 estimation hashes takes a nonzero median (probability ~C(7,4)(k/B*)^4 each)
-        assert float(np.mean(np.abs(val[~on]) > 1e-3)) < 0.01
+    print(f"[large] n=2^28 k*={kk} count={cnt} status={st} (oracle: k*={g['k_star']} "
+          f"count={g['count']})")
+    # the stored run is far from every decision boundary (relative margin ~2e-3 against
+    # FP32 rounding of ~1e-6), so the trajectory and the kept set are the oracle's
+    assert g["min_margin"] > 2e-4
+    assert st == g["status"] == A.OK
+    assert [list(t) for t in trace] == g["trials_B_k"]
+    assert kk == g["k_star"] and cnt == g["count"]
+    assert loc.tolist() == g["loc"]
+    # values against the exact spectrum: support coefficients to FP32 accuracy, the
+    # coordinates outside the support near zero (no estimation bucket of theirs holds a
+    # support coefficient in a majority of the hashes: the oracle's are below 1e-8)
+    assert g["max_abs_outside"] < 1e-6
+    on = np.isin(loc, sig.support)
+    assert on.sum() == len(sig.support)
+    cs = sig.coeffs[np.searchsorted(sig.support, loc[on])]
+    assert float(np.abs(val[on] - cs).max()) < 2e-3
+    assert float(np.abs(val[~on]).max()) < 1e-3
