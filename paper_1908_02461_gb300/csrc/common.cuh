@@ -53,7 +53,7 @@ struct Job {
     int32_t logB;        // per axis
     int32_t nh;          // hashes in this job
     int32_t chunks;      // residue-stream row chunks (partials summed by the FFT)
-    int32_t stream;      // 1: residue-stream binning, 0: warp-per-bucket gather
+    int32_t stream;      // 1: residue-stream binning, 0: gather form (lanes per bucket)
     int32_t active;      // 0: nothing to do (skipped by every kernel)
     int32_t pad[3];
 };
@@ -213,8 +213,9 @@ WindowParam window_shape(int64_t n, int logB, double alpha, double tol);
 Job make_job(const atsfft_plan_s *P, int logB, int nh);
 
 // bin.cu
-// Tuning stage 1 (every trial in 2D; the small-window trials in 1D) or stage 2 (1D: the
-// residue-stream trials, skipped on the device when stage 1 settled the controller).
+// Binning of tuning stage 1 (every trial in 2D; the small-window trials in 1D), 2 (1D: the
+// residue-stream trials but the largest) or 3 (1D: the largest trial); stages 2 and 3 are
+// skipped on the device when an earlier stage settled the controller.
 void launch_tuning(const atsfft_plan_s *P, const float2 *x, int stage, cudaStream_t s);
 void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, cudaStream_t s);
 void launch_single_hash(const atsfft_plan_s *P, const float2 *x, int b, const HashParam &hp,

@@ -76,7 +76,8 @@ WindowParam window_shape(int64_t n, int logB, double alpha, double tol)
 }
 
 // Residue-stream binning when the window covers at least a fifth of the signal and
-// the per-bucket rotation table fits in shared memory; warp-per-bucket gather below.
+// the per-bucket rotation table fits in shared memory; the gather form (a group of
+// lanes per bucket walking its taps) otherwise.
 Job make_job(const atsfft_plan_s *P, int logB, int nh)
 {
     Job j;

@@ -603,7 +603,7 @@ struct TuneTailArgs {
     StatsParams S;
     const StatJob *jobs;   // this stage's trials
     int njobs;
-    int stage;             // 2: return at once if stage 1 settled the controller
+    int stage;             // >= 2: return at once if an earlier stage settled the controller
     int limit_b;           // the controller may visit trials up to this log2 B
     int b0, b_hi, tune_max;
     double delta2;
@@ -651,7 +651,7 @@ __device__ void publish_bstar(const TuneTailArgs &A, int b, int64_t k, int statu
 // already evaluated B/2); r = inf when either count is 0; a trial whose energies are
 // all exactly 0 ends with k* = 0.  Then it writes the jobs at B*.  A walk that would
 // step past limit_b (the trials evaluated so far) writes nothing and leaves tune_done
-// at 0 for the second stage, which walks again from B0 over all trials.  Called by the
+// at 0 for the next stage, which walks again from B0 over all trials.  Called by the
 // first warp of a block: lane t stages trial B0 2^t's counts and its Eq. (12) ratio
 // r = |1 - k_t / k_(t-1)| (FP64, slow on this GPU: all trials' divisions at once instead
 // of one per step of the walk), then lane 0 walks.
@@ -696,7 +696,7 @@ __device__ void controller(const TuneTailArgs &A)
             if (status == ATSFFT_OK) status = ATSFFT_E_NOT_CONVERGED;
             break;
         }
-        if (b == A.limit_b) return;   // needs the trials of the second stage
+        if (b == A.limit_b) return;   // needs the trials of a later stage
         b++;
     }
     if (k == 0) empty = 1;
