@@ -52,6 +52,44 @@ class ATSFFTError(RuntimeError):
         self.status = status
 
 
+class ArgumentError(ATSFFTError, ValueError):
+    """A buffer the binding refuses before calling the library: the C ABI takes raw
+    pointers, so a tensor of the wrong element type, size or device would be read or
+    written out of bounds there."""
+
+    def __init__(self, what: str, detail: str):
+        RuntimeError.__init__(self, f"{what}: {detail}")
+        self.status = E_INVALID_ARG
+
+
+def check_buffer(what: str, name: str, t, dtype, device=None, numel=None, min_numel=None,
+                 pinned=False):
+    """Raises ArgumentError unless `t` is a contiguous tensor of `dtype` with exactly
+    `numel` (or at least `min_numel`) elements, on `device` (or, with pinned=True, in
+    pinned host memory)."""
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise ArgumentError(what, f"{name} must be a torch tensor, not {type(t).__name__}")
+    if t.dtype != dtype:
+        raise ArgumentError(what, f"{name} must be {dtype}, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ArgumentError(what, f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ArgumentError(what, f"{name} must hold {numel} elements, not {t.numel()}")
+    if min_numel is not None and t.numel() < min_numel:
+        raise ArgumentError(what, f"{name} must hold at least {min_numel} elements, not {t.numel()}")
+    if pinned:
+        if t.device.type != "cpu" or not t.is_pinned():
+            raise ArgumentError(what, f"{name} must be a pinned CPU tensor")
+    elif device is not None and t.device != device:
+        raise ArgumentError(what, f"{name} must be on {device}, not {t.device}")
+
+
+def _power_of_two(v) -> bool:
+    return isinstance(v, int) and v > 0 and (v & (v - 1)) == 0
+
+
 def params(**overrides) -> atsfft_params:
     p = atsfft_default_params()
     for k, v in overrides.items():
@@ -77,6 +115,25 @@ class Plan:
         self._scalars = torch.zeros(3, dtype=torch.int64, device=self.device)
         # input and value dtype: complex128 for the FP64 path
         self.dtype = torch.complex128 if (params is not None and params.precision == 1) else torch.complex64
+
+    @property
+    def numel(self) -> int:
+        """Samples of one input: n, or N * N."""
+        m = 1
+        for s in self.shape:
+            m *= s
+        return m
+
+    def check_exec_buffers(self, what, x, loc, val, count, k, status):
+        """The buffers of one transform (capacity = loc.numel())."""
+        import torch
+
+        check_buffer(what, "x", x, self.dtype, self.device, numel=self.numel)
+        check_buffer(what, "loc", loc, torch.int64, self.device)
+        check_buffer(what, "val", val, self.dtype, self.device, min_numel=loc.numel())
+        check_buffer(what, "count", count, torch.int64, self.device, min_numel=1)
+        check_buffer(what, "k", k, torch.int64, self.device, min_numel=1)
+        check_buffer(what, "status", status, torch.int32, self.device, min_numel=1)
 
     def clone(self) -> "Plan":
         """A plan with the same tables and its own scratch (atsfft_plan_clone)."""
@@ -106,6 +163,7 @@ class Plan:
         """Enqueue one transform into caller-provided device buffers."""
         import torch
 
+        self.check_exec_buffers("exec", x, loc, val, count, k, status)
         s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
         fn = atsfft_exec if self.ndim == 1 else atsfft_exec_2d
         st = fn(self.handle, x, loc, val, loc.numel(), count, k, status, s)
@@ -116,10 +174,9 @@ class Plan:
         """Transform x (complex64 CUDA tensor); returns (loc, val, k_star, status, count) after sync."""
         import torch
 
-        if x.dtype != self.dtype or not x.is_cuda or not x.is_contiguous():
-            raise ValueError(f"x must be a contiguous {self.dtype} CUDA tensor")
+        check_buffer("exec", "x", x, self.dtype, self.device, numel=self.numel)
         if tuple(x.shape) != self.shape:
-            raise ValueError(f"x has shape {tuple(x.shape)}, plan expects {self.shape}")
+            raise ArgumentError("exec", f"x has shape {tuple(x.shape)}, the plan {self.shape}")
         cap = capacity if capacity is not None else 1 << 16
         loc = torch.empty(cap, dtype=torch.int64, device=x.device)
         val = torch.empty(cap, dtype=self.dtype, device=x.device)
@@ -138,8 +195,7 @@ class Plan:
         [count, 2]: the estimation hash of the real and of the imaginary median."""
         import torch
 
-        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous():
-            raise ValueError("x must be a contiguous complex64 CUDA tensor")
+        check_buffer("exec_sel", "x", x, torch.complex64, self.device, numel=self.numel)
         cap = capacity if capacity is not None else 1 << 16
         loc = torch.empty(cap, dtype=torch.int64, device=x.device)
         val = torch.empty(cap, dtype=torch.complex64, device=x.device)
@@ -162,6 +218,10 @@ class Plan:
         """Eq. (11) at the fixed support `loc` with median selections `msel`, applied to u."""
         import torch
 
+        check_buffer("estimate_apply", "u", u, torch.complex64, self.device, numel=self.numel)
+        check_buffer("estimate_apply", "loc", loc, torch.int64, self.device)
+        check_buffer("estimate_apply", "msel", msel, torch.uint8, self.device,
+                     min_numel=2 * loc.numel())
         out = torch.empty(loc.numel(), dtype=torch.complex64, device=u.device)
         st = atsfft_estimate_apply(self.handle, B, u, loc, msel, loc.numel(), out,
                                    torch.cuda.current_stream().cuda_stream)
@@ -173,8 +233,14 @@ class Plan:
         """Adjoint of estimate_apply for the output gradient g (complex64 [count])."""
         import torch
 
-        gx = torch.empty(self.shape[0], dtype=torch.complex64, device=g.device)
-        st = atsfft_estimate_adjoint(self.handle, B, loc, msel, loc.numel(), g.contiguous(), gx,
+        g = g.contiguous()
+        check_buffer("estimate_adjoint", "loc", loc, torch.int64, self.device)
+        check_buffer("estimate_adjoint", "msel", msel, torch.uint8, self.device,
+                     min_numel=2 * loc.numel())
+        check_buffer("estimate_adjoint", "g", g, torch.complex64, self.device,
+                     min_numel=loc.numel())
+        gx = torch.empty(self.numel, dtype=torch.complex64, device=g.device)
+        st = atsfft_estimate_adjoint(self.handle, B, loc, msel, loc.numel(), g, gx,
                                      torch.cuda.current_stream().cuda_stream)
         if st != OK:
             raise ATSFFTError(st, "atsfft_estimate_adjoint")
@@ -183,6 +249,9 @@ class Plan:
     def hash_spectrum(self, x, B: int, phase: int, index: int):
         import torch
 
+        check_buffer("hash_spectrum", "x", x, torch.complex64, self.device, numel=self.numel)
+        if not _power_of_two(B) or B > self.shape[0]:
+            raise ArgumentError("hash_spectrum", f"B = {B} is not a power of two up to {self.shape[0]}")
         out = torch.empty((B,) if self.ndim == 1 else (B, B), dtype=torch.complex64, device=x.device)
         st = atsfft_hash_spectrum(self.handle, x, B, phase, index, out,
                                   torch.cuda.current_stream().cuda_stream)
@@ -255,6 +324,22 @@ class Batch:
         import torch
 
         self._keep = list(items)   # the graph holds raw pointers into these tensors
+        for it in items:
+            it[0].check_exec_buffers("batch", *it[1:7])
+        if host is not None:
+            if len(host) != len(items):
+                raise ArgumentError("batch", f"{len(host)} host dicts for {len(items)} items")
+            for it, hd in zip(items, host):
+                plan, cap = it[0], it[2].numel()
+                want = dict(x=(plan.dtype, plan.numel, None), loc=(torch.int64, None, cap),
+                            val=(plan.dtype, None, cap), count=(torch.int64, None, 1),
+                            k=(torch.int64, None, 1), status=(torch.int32, None, 1))
+                for key, t in hd.items():
+                    if key not in want:
+                        raise ArgumentError("batch", f"unknown host buffer {key!r}")
+                    dt, num, least = want[key]
+                    check_buffer("batch", f"host {key}", t, dt, numel=num, min_numel=least,
+                                 pinned=True)
         plans = [it[0].handle for it in items]
         if host is None:
             st, h = atsfft_batch_create(plans, [it[1] for it in items], [it[2] for it in items],
@@ -262,10 +347,6 @@ class Batch:
                                         [it[4] for it in items], [it[5] for it in items],
                                         [it[6] for it in items])
         else:
-            for hd in host:
-                for t in hd.values():
-                    if t.device.type != "cpu" or not t.is_pinned():
-                        raise ValueError("host buffers must be pinned CPU tensors")
             self._keep_host = list(host)
             get = lambda key: [hd.get(key) for hd in host]
             st, h = atsfft_batch_create_io(plans, get("x"), [it[1] for it in items],

@@ -1,0 +1,71 @@
+"""Argument checks of the Python binding, on the CPU: the C ABI takes raw pointers, so the
+binding refuses buffers of the wrong element type, size, layout or device before any
+library call (ArgumentError, which is both an ATSFFTError with the invalid-argument
+status and a ValueError)."""
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1908_02461_gb300 as A  # noqa: E402
+
+CPU = torch.device("cpu")
+
+
+def _raises(fn, match):
+    with pytest.raises(A.ArgumentError, match=match) as ei:
+        fn()
+    assert isinstance(ei.value, ValueError) and isinstance(ei.value, A.ATSFFTError)
+    assert ei.value.status == A.E_INVALID_ARG
+
+
+def test_accepts_a_matching_buffer():
+    A.check_buffer("exec", "loc", torch.zeros(8, dtype=torch.int64), torch.int64, CPU,
+                   numel=8)
+    A.check_buffer("exec", "val", torch.zeros(9, dtype=torch.complex64), torch.complex64, CPU,
+                   min_numel=8)
+
+
+def test_refuses_wrong_type_layout_size_and_device():
+    c = lambda t, **kw: (lambda: A.check_buffer("exec", "loc", t, torch.int64, **kw))
+    _raises(c([0, 1], device=CPU), "must be a torch tensor")
+    _raises(c(torch.zeros(8, dtype=torch.int32), device=CPU), "must be torch.int64")
+    _raises(c(torch.zeros(8, 2, dtype=torch.int64)[:, 0], device=CPU), "contiguous")
+    _raises(c(torch.zeros(7, dtype=torch.int64), device=CPU, numel=8), "hold 8 elements")
+    _raises(c(torch.zeros(7, dtype=torch.int64), device=CPU, min_numel=8), "at least 8")
+    _raises(c(torch.zeros(8, dtype=torch.int64), device=torch.device("cuda", 0)), "must be on")
+    _raises(c(torch.zeros(8, dtype=torch.int64), pinned=True), "pinned")
+
+
+class _FakePlan:
+    """Stands in for a Plan in the host-buffer checks of Batch, which run before any
+    library call (every case below fails them)."""
+
+    handle = None
+    dtype = torch.complex64
+    numel = 1 << 10
+
+    def check_exec_buffers(self, what, *bufs):
+        pass
+
+
+def _item(cap=16):
+    return (_FakePlan(), torch.zeros(1 << 10, dtype=torch.complex64),
+            torch.zeros(cap, dtype=torch.int64), torch.zeros(cap, dtype=torch.complex64),
+            torch.zeros(1, dtype=torch.int64), torch.zeros(1, dtype=torch.int64),
+            torch.zeros(1, dtype=torch.int32))
+
+
+def test_batch_refuses_host_buffers_that_do_not_match():
+    # (not pinned: the size and type checks come first, so every case fails on them or
+    # on the pinning, never reaching the library)
+    _raises(lambda: A.Batch([_item()], host=[]), "host dicts")
+    _raises(lambda: A.Batch([_item()], host=[dict(y=torch.zeros(1))]), "unknown host buffer")
+    _raises(lambda: A.Batch([_item()], host=[dict(x=torch.zeros(512, dtype=torch.complex64))]),
+            "hold 1024 elements")
+    _raises(lambda: A.Batch([_item()], host=[dict(loc=torch.zeros(8, dtype=torch.int64))]),
+            "at least 16")
+    _raises(lambda: A.Batch([_item()], host=[dict(status=torch.zeros(1, dtype=torch.int64))]),
+            "torch.int32")
+    _raises(lambda: A.Batch([_item()], host=[dict(x=torch.zeros(1 << 10, dtype=torch.complex64))]),
+            "pinned")
