@@ -21,6 +21,7 @@ from .oracle import (  # noqa: F401
     hash_spectrum_2d,
     local_maxima,
     controller_branch,
+    top_num,
     median_componentwise,
     atsfft_1d,
     atsfft_2d,

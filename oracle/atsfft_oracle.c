@@ -545,6 +545,14 @@ static int64_t top_num(const double *E, const int64_t *lm, int64_t cnt, int64_t 
     return ns;
 }
 
+int64_t orc_top_num(const double *E, const int64_t *lm, int64_t cnt, int64_t num, double eta,
+                    int64_t *sel)
+{
+    if (num < 1 || cnt < 0) return -1;
+    double margin = INFINITY;
+    return top_num(E, lm, cnt, num, sel, eta, &margin);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Hash index arithmetic (Eq. (10), offset of Eq. (11))                        */
 /* ------------------------------------------------------------------------- */

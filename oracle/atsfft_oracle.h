@@ -104,6 +104,13 @@ int64_t orc_local_maxima(const double *E, int64_t side, int ndim, double thr_rel
                          double thr_med, double eta, int64_t *list, double *T_out,
                          double *margin_out);
 
+/* The "num largest" cutoff of the location step (Algorithm 1) on a list of local maxima:
+ * lm holds cnt bucket indices in ascending order, E the energies by bucket.  Writes the
+ * kept buckets (ascending) to sel (capacity cnt) and returns how many; -1 for num < 1
+ * or cnt < 0. */
+int64_t orc_top_num(const double *E, const int64_t *lm, int64_t cnt, int64_t num, double eta,
+                    int64_t *sel);
+
 /* Componentwise median of L complex values (interleaved); out = {re, im}. */
 int orc_median_componentwise(const double *v, int L, double *out);
 

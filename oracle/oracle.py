@@ -76,7 +76,10 @@ def build(force: bool = False) -> str:
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
+        # ATSFFT_ORACLE_LIB: load a prebuilt copy instead (the mutation test's builds of
+        # the oracle with one planted mistake each)
+        override = os.environ.get("ATSFFT_ORACLE_LIB")
+        L = C.CDLL(override if override else build())
         i64, i32, dbl, u64 = C.c_int64, C.c_int, C.c_double, C.c_uint64
         P = C.POINTER
         L.orc_default_params.argtypes = [P(OracleParams)]
@@ -94,6 +97,8 @@ def lib():
                                        P(dbl), P(dbl)]
         L.orc_local_maxima.restype = i64
         L.orc_controller_branch.argtypes = [i64, i64, dbl, dbl]
+        L.orc_top_num.argtypes = [C.c_void_p, C.c_void_p, i64, i64, dbl, C.c_void_p]
+        L.orc_top_num.restype = i64
         L.orc_median_componentwise.argtypes = [C.c_void_p, i32, C.c_void_p]
         L.orc_atsfft_1d.argtypes = [C.c_void_p, i64, i64, P(OracleParams), u64, C.c_void_p,
                                     C.c_void_p, i64, P(_CResult)]
@@ -188,6 +193,18 @@ def local_maxima(E, ndim=1, thr_rel=1e-3, thr_med=20.0, eta=1e-2):
     cnt = lib().orc_local_maxima(_ptr(E), side, ndim, thr_rel, thr_med, eta, _ptr(lst),
                                  C.byref(T), C.byref(m))
     return lst[:cnt].copy(), T.value, m.value
+
+
+def top_num(E, lm, num, eta=1e-2):
+    """The location step's "num largest" cutoff (Algorithm 1) of the ascending local-maximum
+    list lm with energies E (indexed by bucket): the kept buckets, ascending."""
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    lm = np.ascontiguousarray(lm, dtype=np.int64)
+    sel = np.zeros(max(len(lm), 1), dtype=np.int64)
+    ns = lib().orc_top_num(_ptr(E), _ptr(lm), len(lm), num, eta, _ptr(sel))
+    if ns < 0:
+        raise ValueError(f"orc_top_num: invalid num {num}")
+    return sel[:ns].copy()
 
 
 def median_componentwise(v):

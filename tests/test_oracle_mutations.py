@@ -1,0 +1,144 @@
+"""The oracle's pins catch plausible mistakes: each case below plants one mistake in a
+copy of oracle/atsfft_oracle.c (a flipped sign, a swapped index, a dropped term, an
+off-by-one), builds it with gcc and runs tests/test_oracle_pins.py against that build;
+at least one pin must fail.  The unchanged copy must pass them all (the control case),
+so a failure is the mistake's doing.  CPU only; the planted mistakes live in temporary
+copies and never touch the oracle itself."""
+
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(ROOT, "oracle", "atsfft_oracle.c")
+HDR = os.path.join(ROOT, "oracle", "atsfft_oracle.h")
+PINS = os.path.join(HERE, "test_oracle_pins.py")
+
+# name -> (text in the oracle, replacement, the step of the paper it breaks)
+MUTANTS = {
+    "estimate_phase_sign": (
+        "double ang = -2.0 * M_PI * (double)m / (double)n; /* omega^{tau i} */",
+        "double ang = 2.0 * M_PI * (double)m / (double)n; /* omega^{tau i} */",
+        "Eq. (11): the phase omega^{tau i}"),
+    "estimate_gain_multiplied": (
+        "est[s * L + l] = Z[bucket] * ph / gain;",
+        "est[s * L + l] = Z[bucket] * ph * gain;",
+        "Eq. (11): division by the window gain"),
+    "reverse_hash_sigma_not_inverse": (
+        "votes[mulmod(si1, pp, n)]++;",
+        "votes[mulmod(hp[0], pp, n)]++;",
+        "Section II-B: reverse hash through sigma^{-1}"),
+    "median_index": (
+        "return re[L / 2] + I * im[L / 2];",
+        "return re[L / 2 - 1] + I * im[L / 2 - 1];",
+        "Section II-B: median of the L estimates"),
+    "bins_2d_transposed": (
+        "Z[b1 * B + b2] += g1",
+        "Z[b2 * B + b1] += g1",
+        "Eq. (2) / Lemma 2 in 2D: bucket (b1, b2) row-major"),
+    "half_bin_modulation_sign": (
+        "double ang = M_PI * (double)t / (double)n;",
+        "double ang = -M_PI * (double)t / (double)n;",
+        "flat window of Section II-A-2: pass band centred on the bucket"),
+    "gaussian_width": (
+        "double ss = (double)B * q / (M_PI * alpha);",
+        "double ss = (double)B * q / (2.0 * M_PI * alpha);",
+        "Eq. (9): Gaussian width of the flat window"),
+    "response_offset_grid": (
+        "int64_t o2 = 2 * j - D + 1; /* 2*o, an odd integer */",
+        "int64_t o2 = 2 * j - D; /* 2*o, an odd integer */",
+        "Eq. (11): window gain at the half-integer offset"),
+    "vote_threshold": (
+        "int need = (p->loops_loc + 1) / 2;",
+        "int need = p->loops_loc / 2;",
+        "Section II-B: votes in at least half of the location loops"),
+    "tie_direction": (
+        "return d1 < 0 || (d1 == 0 && d2 < 0);",
+        "return d1 > 0 || (d1 == 0 && d2 > 0);",
+        "Section III-A local maxima: ties go to the later bucket"),
+    "neighbourhood_2d_four": (
+        "if (d1 == 0 && d2 == 0) continue;",
+        "if ((d1 == 0 && d2 == 0) || (d1 != 0 && d2 != 0)) continue;",
+        "Section III-A / Fig. 5: eight neighbours in 2D"),
+    "threshold_median_term_dropped": (
+        "return fmax(thr_rel * mx, thr_med * med);",
+        "return thr_rel * mx;",
+        "Section III-A: threshold against the median"),
+    "bucket_floor_not_round": (
+        "int64_t q = (2 * p + 1 + D) / (2 * D);",
+        "int64_t q = (2 * p + 1) / (2 * D);",
+        "Eq. (10): bucket of a coordinate by rounding"),
+    "controller_stop_delta1": (
+        "if (trial > 0 && r < p->delta2) break;",
+        "if (trial > 0 && r < p->delta1) break;",
+        "Eqs. (12)-(14): stop below delta2"),
+    "top_num_pivot_off_by_one": (
+        "double V = v[num - 1].e,",
+        "double V = v[num].e,",
+        "Algorithm 1 'find num largest': the num-th largest"),
+    "fft_twiddle_sign": (
+        "double ang = -2.0 * M_PI * (double)j / (double)m;",
+        "double ang = 2.0 * M_PI * (double)j / (double)m;",
+        "the B-point DFT's sign convention"),
+    "inverse_mod_too_few_steps": (
+        "for (int it = 0; it < 6; it++) x = x * (2 - s * x);",
+        "for (int it = 0; it < 2; it++) x = x * (2 - s * x);",
+        "Def. 1: sigma^{-1} mod n"),
+    "tap_envelope_width": (
+        "double env = exp(-((double)t * (double)t) / (2.0 * s * s));",
+        "double env = exp(-((double)t * (double)t) / (4.0 * s * s));",
+        "Eq. (9): the Gaussian envelope of the taps"),
+}
+
+
+def _build(tmp_path, name):
+    src = open(SRC).read()
+    if name != "control":
+        old, new, _ = MUTANTS[name]
+        assert src.count(old) == 1, f"{name}: the text to mutate is not unique in the oracle"
+        src = src.replace(old, new)
+    work = tmp_path / name
+    work.mkdir()
+    (work / "atsfft_oracle.c").write_text(src)
+    shutil.copy(HDR, work / "atsfft_oracle.h")
+    so = work / "liboracle_mutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", str(so),
+                    str(work / "atsfft_oracle.c"), "-lm"], check=True)
+    return str(so)
+
+
+def _run_pins(so):
+    env = dict(os.environ, ATSFFT_ORACLE_LIB=so, OMP_NUM_THREADS="1",
+               OPENBLAS_NUM_THREADS="1")
+    return subprocess.run([sys.executable, "-m", "pytest", PINS, "-x", "-q",
+                           "-p", "no:cacheprovider"], cwd=ROOT, env=env,
+                          capture_output=True, text=True, timeout=600)
+
+
+@pytest.fixture(scope="module")
+def runs(tmp_path_factory):
+    """Every build (the control and each mutant) against the pins, several at a time."""
+    tmp = tmp_path_factory.mktemp("mutants")
+    names = ["control"] + sorted(MUTANTS)
+    libs = {nm: _build(tmp, nm) for nm in names}
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        futs = {nm: ex.submit(_run_pins, libs[nm]) for nm in names}
+        return {nm: f.result() for nm, f in futs.items()}
+
+
+def test_control_copy_passes_every_pin(runs):
+    r = runs["control"]
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_fails_a_pin(runs, name):
+    r = runs[name]
+    # pytest exit code 1: some tests failed (anything else is a harness problem)
+    assert r.returncode == 1, (f"{name} ({MUTANTS[name][2]}) survived the pins"
+                               if r.returncode == 0 else r.stdout[-2000:] + r.stderr[-2000:])

@@ -294,6 +294,60 @@ def test_controller_branches_eq14():
     assert O.controller_branch(0, 5) == 1 and O.controller_branch(7, 0) == 1
 
 
+@pytest.mark.parametrize("logn,k,seed", [(14, 32, 3), (13, 32, 0)])
+def test_transform_walk_stops_at_the_first_ratio_below_delta2(logn, k, seed):
+    """Eqs. (12)-(14) in a whole transform: B doubles from 16 while r = |1 - k_t/k_(t-1)|
+    >= delta2 (a zero count reads as an unbounded change) and the walk stops at the first
+    r < delta2.  These seeds end on the keep branch (delta1 <= r < delta2), where a walk
+    that stopped only below delta1 would go on."""
+    sig = sparse_signal_1d(1 << logn, k, seed)
+    res = O.atsfft_1d(sig.x, seed=seed)
+    Bs = [int(t[0]) for t in res.trials]
+    ks = [int(t[1]) for t in res.trials]
+    assert res.status == 0
+    assert Bs == [16 << t for t in range(len(Bs))]
+
+    def ratio(prev, cur):
+        return math.inf if prev == 0 or cur == 0 else abs(1.0 - cur / prev)
+
+    rs = [ratio(ks[t - 1], ks[t]) for t in range(1, len(ks))]
+    assert all(r >= 0.05 for r in rs[:-1]) and rs[-1] < 0.05, rs
+    assert rs[-1] >= 0.02, rs   # the keep branch
+    assert (res.B_star, res.k_star) == (Bs[-1], ks[-1])
+
+
+def test_top_num_keeps_the_num_largest_when_energies_are_apart():
+    """Algorithm 1 "find num largest": with energies more than the tie band apart the
+    cutoff is the num largest local maxima, by brute force."""
+    rng = np.random.default_rng(3)
+    for trial in range(20):
+        nb = 256
+        lm = np.sort(rng.choice(nb, size=int(rng.integers(1, 60)), replace=False))
+        E = np.zeros(nb)
+        E[lm] = 1.1 ** rng.permutation(len(lm))   # distinct, 10 % apart
+        for num in (1, 3, len(lm) // 2 + 1, len(lm), len(lm) + 5):
+            want = np.sort(lm[np.argsort(-E[lm], kind="stable")[:num]])
+            assert O.top_num(E, lm, num).tolist() == want.tolist(), (trial, num)
+
+
+def test_top_num_fills_the_tie_band_in_ascending_bucket_order():
+    """Energies within the relative band eta of the num-th largest count as tied and the
+    lower bucket index wins (the reading of the ties).  Worked case, eta = 1 %, num = 3:
+    energies 2.0 (bucket 20), 1.005 (11), 1.000 (3), 0.995 (7), 0.5 (25); the pivot is
+    the third largest, 1.000; 2.0 lies above the band [0.99, 1.01] and is kept; the band
+    holds buckets 3, 7 and 11, of which the two lowest, 3 and 7, fill the cut."""
+    E = np.zeros(32)
+    E[[3, 7, 11, 20, 25]] = [1.000, 0.995, 1.005, 2.0, 0.5]
+    assert O.top_num(E, [3, 7, 11, 20, 25], 3, eta=1e-2).tolist() == [3, 7, 20]
+    # without a tie band the three largest energies
+    assert O.top_num(E, [3, 7, 11, 20, 25], 3, eta=0.0).tolist() == [3, 11, 20]
+    # all equal: the num lowest buckets; at most num kept: all of them
+    F = np.zeros(16)
+    F[[2, 4, 6, 8, 10]] = 1.0
+    assert O.top_num(F, [2, 4, 6, 8, 10], 2).tolist() == [2, 4]
+    assert O.top_num(F, [2, 4, 6, 8, 10], 9).tolist() == [2, 4, 6, 8, 10]
+
+
 def test_median_componentwise_matches_numpy():
     rng = np.random.default_rng(5)
     for L in (1, 3, 5, 7, 9):
