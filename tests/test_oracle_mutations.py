@@ -89,6 +89,66 @@ MUTANTS = {
         "for (int it = 0; it < 6; it++) x = x * (2 - s * x);",
         "for (int it = 0; it < 2; it++) x = x * (2 - s * x);",
         "Def. 1: sigma^{-1} mod n"),
+    "estimate_with_location_hashes": (
+        "orc_hash_params(cx->seed, cx->p->est_reuse_loc ? 1 : 2, l, n, ndim, hp);",
+        "orc_hash_params(cx->seed, 1, l, n, ndim, hp);",
+        "Eq. (11): the estimation hash's own permutation"),
+    "reverse_hash_no_half_bucket_shift": (
+        "int64_t pp = emod(c * D - D / 2 + q, n);",
+        "int64_t pp = emod(c * D + q, n);",
+        "Section II-B: preimage of a bucket centred at c D - 1/2"),
+    "reverse_hash_2d_no_half_bucket_shift": (
+        "int64_t i = mulmod(si1, emod(c1 * D - D / 2 + q1, n), n);",
+        "int64_t i = mulmod(si1, emod(c1 * D + q1, n), n);",
+        "Section II-B in 2D: preimage rows of a bucket"),
+    "window_normalisation": (
+        "double A = (double)n / sum;",
+        "double A = 1.0 / sum;",
+        "Section II-A-2: window normalised to unit gain"),
+    "response_scale": (
+        "resp[j] = acc / (double)n;",
+        "resp[j] = acc;",
+        "Eq. (11): window gain Ghat'"),
+    "default_thr_med": (
+        "p->thr_med = 20.0;",
+        "p->thr_med = 10.0;",
+        "Section III-A: the median factor of the threshold"),
+    "default_thr_rel": (
+        "p->thr_rel = 1e-3;",
+        "p->thr_rel = 1e-2;",
+        "Section III-A: the relative factor of the threshold"),
+    "default_delta2": (
+        "p->delta2 = 0.05;",
+        "p->delta2 = 0.04;",
+        "Eq. (14): delta2 = 5 %"),
+    "default_tie_band": (
+        "p->tie_eta = 1e-2;",
+        "p->tie_eta = 0.0;",
+        "Section III-A local maxima: the tie band"),
+    "sigma_not_forced_odd": (
+        "out[2 * d + 0] = (int64_t)((orc_splitmix64_next(&st) & mask) | 1);",
+        "out[2 * d + 0] = (int64_t)(orc_splitmix64_next(&st) & mask);",
+        "Def. 1: sigma invertible mod n"),
+    "estimate_2d_phase_sign": (
+        "m = (m + mulmod(hp[3], j, n)) % n;",
+        "m = emod(m - mulmod(hp[3], j, n), n);",
+        "Eq. (11) in 2D: omega^{tau1 i + tau2 j}"),
+    "neighbour_before_skipped": (
+        "for (int d2 = -1; d2 <= 1; d2++) {",
+        "for (int d2 = 0; d2 <= 1; d2++) {",
+        "Section III-A: both neighbours of a local maximum"),
+    "tuning_previous_count_kept": (
+        "k_prev = k_cur;",
+        "(void)k_prev;",
+        "Eq. (12): r against the previous trial's count"),
+    "half_bin_missing_second_axis": (
+        "(w->taps[t2 + w->h] * half_bin(t2, N))",
+        "(w->taps[t2 + w->h])",
+        "flat window in 2D: half-bin modulation on both axes"),
+    "location_loop_dropped": (
+        "for (int l = 0; l < p->loops_loc; l++) {",
+        "for (int l = 0; l < p->loops_loc - 1; l++) {",
+        "Section II-B: votes over all L_loc location hashes"),
     "tap_envelope_width": (
         "double env = exp(-((double)t * (double)t) / (2.0 * s * s));",
         "double env = exp(-((double)t * (double)t) / (4.0 * s * s));",

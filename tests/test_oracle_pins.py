@@ -294,6 +294,22 @@ def test_controller_branches_eq14():
     assert O.controller_branch(0, 5) == 1 and O.controller_branch(7, 0) == 1
 
 
+def test_default_parameters_are_the_papers_and_the_readings():
+    """The defaults of a whole transform: Eq. (14)'s constants as the paper prints them
+    (golden file), and where the paper leaves a value open the readings taken for it:
+    threshold T = max(1e-3 max E, 20 median E) and a 1 % tie band for Section III-A's
+    undefined `threshold` and ties, seven location and seven estimation hashes for the
+    unstated `loops`, and the window tolerance 1e-6 with alpha = 1/2 for the flat window
+    whose parameters Eqs. (8)-(9) leave open."""
+    g = _gold("eq14_controller.json")
+    p = O.default_params()
+    assert (p.delta1, p.delta2, p.eps1, p.eps2) == (g["delta1"], g["delta2"], g["eps1"], g["eps2"])
+    assert (p.thr_rel, p.thr_med, p.tie_eta) == (1e-3, 20.0, 1e-2)
+    assert (p.loops_loc, p.loops_est) == (7, 7)
+    assert (p.filter_tol, p.filter_alpha) == (1e-6, 0.5)
+    assert (p.b_min_log2, p.b_max_log2, p.fixed_k, p.est_reuse_loc) == (0, 0, 0, 0)
+
+
 @pytest.mark.parametrize("logn,k,seed", [(14, 32, 3), (13, 32, 0)])
 def test_transform_walk_stops_at_the_first_ratio_below_delta2(logn, k, seed):
     """Eqs. (12)-(14) in a whole transform: B doubles from 16 while r = |1 - k_t/k_(t-1)|
