@@ -91,3 +91,34 @@ def test_all_cores_oracle_baseline_runs_in_spawned_processes():
 
     r = bench.cpu_baseline_all_cores(max_procs=2)
     assert r["kind"] == "oracle" and r["cores"] == 2 and r["value"] > 0
+
+
+def test_reference_arm_prints_one_contract_line(capsys):
+    """--impl reference: the oracle in spawned single-threaded processes (two here, on
+    n = 2^12 signals instead of the bench's 2^22), one JSON line with the reference
+    arm's keys."""
+    import argparse
+    import json
+
+    import bench
+
+    args = argparse.Namespace(gpus=1, steps=6, warmup=2)
+    bench.run_reference(args, n_log2=12, max_procs=2)
+    out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert out["impl"] == "reference" and out["metric"] == "transforms/s"
+    assert out["steps"] == 6 and out["warmup"] == 2 and out["value"] > 0
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] == 2
+    assert out["cpu_baseline"]["value"] == out["value"]
+    assert out["e2e"] == {"value": out["value"], "unit": "transforms/s",
+                          "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    import argparse
+
+    import bench
+
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    assert bench.run_reference(argparse.Namespace(gpus=2, steps=1, warmup=0), n_log2=12) is None
+    assert capsys.readouterr().out == ""
