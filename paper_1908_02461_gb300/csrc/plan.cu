@@ -500,14 +500,16 @@ static atsfft_status plan_create(atsfft_plan_t *out, int ndim, const int64_t *sh
     // ---- window tables (plan time, synchronous) ----
     cudaError_t e = cudaSuccess;
     double *d_partial = nullptr, *d_S0 = nullptr;
-    int64_t max_nch = 0, max_D = 0;
-    for (int b = P->b0; b <= P->b_hi; b++) {
-        int64_t nch = (P->h_win[b].h + kRespChunk) / kRespChunk;
-        if (nch > max_nch) max_nch = nch;
-        if ((n >> b) > max_D) max_D = n >> b;
+    // one B at a time uses (D + 1) offsets x its chunks of taps; the largest such product
+    // (the largest D and the most chunks belong to opposite ends of the B range, so their
+    // product would be far larger: terabytes at n = 2^28)
+    int64_t partial_elems = 1;
+    for (int b = P->b0; b <= P->b_hi && !tmpl; b++) {
+        const int64_t nch = (P->h_win[b].h + kRespChunk) / kRespChunk;
+        const int64_t need = ((n >> b) + 1) * nch;
+        if (need > partial_elems) partial_elems = need;
     }
-    if (tmpl) max_nch = 0;   // no window kernels: the tables come from the template
-    e = cudaMalloc(&d_partial, sizeof(double) * (size_t)(max_D + 1) * (size_t)(max_nch ? max_nch : 1));
+    e = cudaMalloc(&d_partial, sizeof(double) * (size_t)partial_elems);
     if (e == cudaSuccess) e = cudaMalloc(&d_S0, sizeof(double) * kMaxLogB);
     for (int b = P->b0; b <= P->b_hi && e == cudaSuccess && !tmpl; b++) {
         WindowParam &w = P->h_win[b];
