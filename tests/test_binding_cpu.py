@@ -69,3 +69,36 @@ def test_batch_refuses_host_buffers_that_do_not_match():
             "torch.int32")
     _raises(lambda: A.Batch([_item()], host=[dict(x=torch.zeros(1 << 10, dtype=torch.complex64))]),
             "pinned")
+
+
+def _cpu_plan(shape, dtype=torch.complex64):
+    """A Plan object without a library handle, its buffers checked against the CPU."""
+    p = A.Plan.__new__(A.Plan)
+    p.shape, p.ndim, p.dtype, p.device, p.handle = tuple(shape), len(shape), dtype, CPU, None
+    return p
+
+
+def _outs(cap, dtype=torch.complex64):
+    return (torch.empty(cap, dtype=torch.int64), torch.empty(cap, dtype=dtype),
+            torch.zeros(1, dtype=torch.int64), torch.zeros(1, dtype=torch.int64),
+            torch.zeros(1, dtype=torch.int32))
+
+
+def test_the_buffers_the_benchmark_and_tests_pass_are_accepted():
+    # 1D and 2D inputs with the output set of the benchmark (capacity 2^14) and the FP64 path
+    _cpu_plan((1 << 14,)).check_exec_buffers(
+        "exec", torch.zeros(1 << 14, dtype=torch.complex64), *_outs(1 << 14))
+    _cpu_plan((256, 256)).check_exec_buffers(
+        "exec", torch.zeros(256, 256, dtype=torch.complex64), *_outs(1 << 12))
+    _cpu_plan((1 << 14,), torch.complex128).check_exec_buffers(
+        "exec", torch.zeros(1 << 14, dtype=torch.complex128), *_outs(16, torch.complex128))
+    # a value buffer longer than the location buffer is fine; shorter is not
+    loc, val, c, k, s = _outs(16)
+    _cpu_plan((1 << 10,)).check_exec_buffers(
+        "exec", torch.zeros(1 << 10, dtype=torch.complex64), loc, torch.zeros(32, dtype=torch.complex64), c, k, s)
+    _raises(lambda: _cpu_plan((1 << 10,)).check_exec_buffers(
+        "exec", torch.zeros(1 << 10, dtype=torch.complex64), loc, val[:8], c, k, s), "at least 16")
+    _raises(lambda: _cpu_plan((1 << 10,)).check_exec_buffers(
+        "exec", torch.zeros(1 << 11, dtype=torch.complex64), loc, val, c, k, s), "hold 1024")
+    _raises(lambda: _cpu_plan((1 << 10,)).check_exec_buffers(
+        "exec", torch.zeros(1 << 10, dtype=torch.complex64), loc.int(), val, c, k, s), "torch.int64")
