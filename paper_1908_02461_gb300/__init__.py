@@ -87,7 +87,13 @@ def check_buffer(what: str, name: str, t, dtype, device=None, numel=None, min_nu
 
 
 def _power_of_two(v) -> bool:
-    return isinstance(v, int) and v > 0 and (v & (v - 1)) == 0
+    import operator
+
+    try:
+        v = operator.index(v)   # Python and NumPy integers
+    except TypeError:
+        return False
+    return v > 0 and (v & (v - 1)) == 0
 
 
 def params(**overrides) -> atsfft_params:

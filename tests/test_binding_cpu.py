@@ -102,3 +102,10 @@ def test_the_buffers_the_benchmark_and_tests_pass_are_accepted():
         "exec", torch.zeros(1 << 11, dtype=torch.complex64), loc, val, c, k, s), "hold 1024")
     _raises(lambda: _cpu_plan((1 << 10,)).check_exec_buffers(
         "exec", torch.zeros(1 << 10, dtype=torch.complex64), loc.int(), val, c, k, s), "torch.int64")
+
+
+def test_bucket_count_check_takes_python_and_numpy_integers():
+    import numpy as np
+
+    assert A._power_of_two(64) and A._power_of_two(np.int64(4096))
+    assert not any(A._power_of_two(v) for v in (0, -8, 48, 64.0, "64"))
