@@ -84,7 +84,7 @@ def autotune(n: int, k_range=(10, 1000), snr_db: float | None = 40.0, error_targ
         errs, ratios = [], []
         for (x, loc, coef), xd, k in zip(sigs, xs, ks):
             # every status is a result (NOT_SPARSE / NOT_CONVERGED / CAPACITY still return
-            # locations and values); Eq. (15) judges it
+            # locations and values); Eq. (15) scores it
             gl, gv, kk, st, cnt = plan(xd, capacity=capacity)
             errs.append(_l1_error(loc, coef, gl.cpu().numpy(), gv.cpu().numpy().astype(complex)))
             ratios.append(kk / k)
