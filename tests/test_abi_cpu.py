@@ -62,3 +62,49 @@ def test_product_package_never_imports_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 for bad in ("import oracle", "from oracle", "atsfft_oracle", "orc_"):
                     assert bad not in txt, (f, bad)
+
+
+def _prototypes():
+    """name -> list of parameter declarations, from the header's function prototypes."""
+    txt = open(os.path.join(ROOT, "include", "atsfft.h")).read()
+    txt = re.sub(r"/\*.*?\*/", " ", txt, flags=re.S)   # comments out
+    protos = {}
+    for m in re.finditer(r"\b(atsfft_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", txt, flags=re.S):
+        params = [p.strip() for p in m.group(2).split(",")]
+        protos[m.group(1)] = [] if params == ["void"] else params
+    return protos
+
+
+def _ctype_class(decl):
+    """The ctypes argument class a C parameter declaration needs."""
+    if "*" in decl or re.match(r"(const\s+)?atsfft_(plan|batch)_t\b", decl):
+        return "pointer"
+    if re.match(r"(const\s+)?uint64_t\b", decl):
+        return "u64"
+    if re.match(r"(const\s+)?int64_t\b", decl):
+        return "i64"
+    if re.match(r"(const\s+)?(int|int32_t|atsfft_status)\b", decl):
+        return "i32"
+    raise AssertionError(f"unclassified parameter {decl!r}")
+
+
+def test_binding_argument_lists_match_the_prototypes():
+    """Every ctypes argtypes list has the prototype's length and, position by position,
+    the same kind of argument (pointer, 32-bit int, signed or unsigned 64-bit int): a
+    mismatch would hand the library garbage without any error."""
+    import ctypes as C
+
+    import paper_1908_02461_gb300._lib as L
+
+    lib = L.load()
+    protos = _prototypes()
+    assert set(protos) == set(L.EXPORTED)
+    kinds = {C.c_void_p: "pointer", C.c_char_p: "pointer", C.c_int64: "i64",
+             C.c_uint64: "u64", C.c_int: "i32", C.c_int32: "i32"}
+    for name, params in protos.items():
+        argtypes = getattr(lib, name).argtypes
+        assert argtypes is not None, name
+        assert len(argtypes) == len(params), (name, len(argtypes), len(params))
+        for a, decl in zip(argtypes, params):
+            got = "pointer" if hasattr(a, "_type_") and issubclass(a, C._Pointer) else kinds.get(a)
+            assert got == _ctype_class(decl), (name, decl, a)
