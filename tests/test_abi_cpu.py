@@ -108,3 +108,19 @@ def test_binding_argument_lists_match_the_prototypes():
         for a, decl in zip(argtypes, params):
             got = "pointer" if hasattr(a, "_type_") and issubclass(a, C._Pointer) else kinds.get(a)
             assert got == _ctype_class(decl), (name, decl, a)
+
+
+def test_binding_return_types_match_the_prototypes():
+    import ctypes as C
+
+    import paper_1908_02461_gb300._lib as L
+
+    lib = L.load()
+    txt = re.sub(r"/\*.*?\*/", " ", open(os.path.join(ROOT, "include", "atsfft.h")).read(),
+                 flags=re.S)
+    want = {"atsfft_status": C.c_int, "void": None, "const char *": C.c_char_p}
+    found = re.findall(r"^(atsfft_status|void|const char \*)\s*(atsfft_[a-z0-9_]+)\s*\(", txt,
+                       flags=re.M)
+    assert {nm for _, nm in found} == set(L.EXPORTED)
+    for ret, name in found:
+        assert getattr(lib, name).restype is want[ret], (name, ret)
