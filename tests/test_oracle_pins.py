@@ -575,3 +575,47 @@ def test_estimation_reusing_location_hashes():
     assert not np.allclose(est_loc, est_new, atol=0, rtol=0)
     bad = O.default_params(est_reuse_loc=1, loops_loc=5, loops_est=7)
     assert O.atsfft_1d(sig.x, seed=9, params=bad).status == 1   # invalid argument
+
+
+# --------------------------------------------------------------------------
+# The ctypes wrapper against the oracle's C prototypes
+# --------------------------------------------------------------------------
+
+def test_wrapper_argument_and_return_types_match_the_prototypes():
+    """Each ctypes declaration of the oracle's wrapper has its C prototype's parameter
+    count and kinds (pointer, int, int64, uint64, double) and return kind."""
+    import ctypes as C
+    import re
+
+    hdr = os.path.join(os.path.dirname(O.__file__), "atsfft_oracle.h")
+    txt = re.sub(r"/\*.*?\*/", " ", open(hdr).read(), flags=re.S)
+    protos = re.findall(r"^(void|int|int64_t|uint64_t)\s+(orc_[a-z0-9_]+)\s*\(([^;]*?)\)\s*;",
+                        txt, flags=re.M | re.S)
+    assert len(protos) >= 15
+
+    def kind_of_decl(d):
+        d = d.strip()
+        if "*" in d:
+            return "ptr"
+        for t, k in (("uint64_t", "u64"), ("int64_t", "i64"), ("double", "f64"), ("int", "i32")):
+            if re.match(rf"(const\s+)?{t}\b", d):
+                return k
+        raise AssertionError(d)
+
+    def kind_of_ctype(a):
+        if a is None:
+            return "void"
+        if isinstance(a, type) and issubclass(a, C._Pointer) or a in (C.c_void_p, C.c_char_p):
+            return "ptr"
+        return {C.c_int: "i32", C.c_int64: "i64", C.c_uint64: "u64", C.c_double: "f64"}[a]
+
+    lib = O.lib()
+    for ret, name, params in protos:
+        fn = getattr(lib, name)
+        decls = [p for p in params.split(",") if p.strip() and p.strip() != "void"]
+        if fn.argtypes is not None or decls:
+            assert fn.argtypes is not None, name
+            assert [kind_of_ctype(a) for a in fn.argtypes] == [kind_of_decl(d) for d in decls], name
+        want_ret = {"void": ("void", "i32"), "int": ("i32",), "int64_t": ("i64",),
+                    "uint64_t": ("u64",)}[ret]
+        assert kind_of_ctype(fn.restype) in want_ret, (name, ret, fn.restype)
