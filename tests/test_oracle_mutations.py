@@ -149,6 +149,58 @@ MUTANTS = {
         "for (int l = 0; l < p->loops_loc; l++) {",
         "for (int l = 0; l < p->loops_loc - 1; l++) {",
         "Section II-B: votes over all L_loc location hashes"),
+    "fixed_k_bucket_rule_1d": (
+        "int bf = ndim == 1 ? (m + 1) / 2 : (m + 3) / 4;",
+        "int bf = ndim == 1 ? m / 2 : (m + 3) / 4;",
+        "fixed-k mode: the smallest B with B^2 >= n k"),
+    "fixed_k_bucket_rule_2d": (
+        "int bf = ndim == 1 ? (m + 1) / 2 : (m + 3) / 4;",
+        "int bf = ndim == 1 ? (m + 1) / 2 : (m + 1) / 4;",
+        "fixed-k mode in 2D: the smallest B with B^4 >= N^2 k"),
+    "reuse_estimates_from_fresh_hashes": (
+        "hash_any(cx, B, p->est_reuse_loc ? 1 : 2, l, &w, Z);",
+        "hash_any(cx, B, 2, l, &w, Z);",
+        "estimation reusing the location hashes"),
+    "k_hint_start": (
+        "int want = ndim == 1 ? ilog2(2 * k_hint) : (ilog2(2 * k_hint) + 1) / 2;",
+        "int want = ndim == 1 ? ilog2(k_hint) : (ilog2(2 * k_hint) + 1) / 2;",
+        "Algorithm 2's initial B from a sparsity hint"),
+    "capacity_status_off_by_one": (
+        "if (count > capacity && status == ORC_OK) status = ORC_E_CAPACITY;",
+        "if (count >= capacity && status == ORC_OK) status = ORC_E_CAPACITY;",
+        "output capacity: an error only when the outputs do not fit"),
+    "not_sparse_on_first_trial": (
+        "if (trial > 0) status = ORC_E_NOT_SPARSE;",
+        "status = ORC_E_NOT_SPARSE;",
+        "Eq. (14): doubling past the largest B"),
+    "trial_cap_off_by_one": (
+        "if (trial + 1 >= p->tune_max) {",
+        "if (trial >= p->tune_max) {",
+        "Algorithm 2: at most tune_max trials"),
+    "largest_b_default": (
+        "int b_hi = p->b_max_log2 ? p->b_max_log2 : (ndim == 1 ? lgn - 4 : lgn - 2);",
+        "int b_hi = p->b_max_log2 ? p->b_max_log2 : (ndim == 1 ? lgn - 3 : lgn - 2);",
+        "the B range's upper end (bucket width >= 16 bins)"),
+    "smallest_b_default_2d": (
+        "int b_lo = p->b_min_log2 ? p->b_min_log2 : (ndim == 1 ? 4 : 3);",
+        "int b_lo = p->b_min_log2 ? p->b_min_log2 : (ndim == 1 ? 4 : 4);",
+        "Algorithm 2's smallest B in 2D"),
+    "zero_signal_not_detected": (
+        "if (maxE == 0.0) { /* nothing in the window: the signal is zero there */",
+        "if (0) { /* nothing in the window: the signal is zero there */",
+        "a zero signal gives an empty output"),
+    "threshold_median_rank": (
+        "double med = tmp[nb / 2], mx = tmp[nb - 1];",
+        "double med = tmp[nb / 2 - 1], mx = tmp[nb - 1];",
+        "Section III-A: the median of the energies"),
+    "reverse_hash_2d_second_axis_sigma": (
+        "int64_t si2 = ndim == 2 ? orc_inv_mod(hp[2], n) : 0;",
+        "int64_t si2 = ndim == 2 ? hp[2] : 0;",
+        "Section II-B in 2D: sigma_2^{-1} on the second axis"),
+    "estimate_2d_second_axis_gain": (
+        "gain *= resp[(o2 + D - 1) / 2];",
+        "gain *= 1.0;",
+        "Eq. (11) in 2D: the second axis's window gain"),
     "tap_envelope_width": (
         "double env = exp(-((double)t * (double)t) / (2.0 * s * s));",
         "double env = exp(-((double)t * (double)t) / (4.0 * s * s));",

@@ -272,6 +272,15 @@ def test_local_maxima_synthetic_1d():
     E3[5] = 15.0
     lm3, T3, _ = O.local_maxima(E3)
     assert T3 == pytest.approx(20.0) and lm3.tolist() == []
+    # the median is the element of rank floor(B/2) of the ascending energies (the upper of
+    # the two middle ones for even B): half the buckets at 1, half at 2, so the median is 2
+    # and T = 40; a spike of 30 lies between 20 * 1 and 20 * 2 and is not a maximum
+    E4 = np.where(np.arange(B) % 2 == 0, 1.0, 2.0)
+    E4[9] = 30.0
+    lm4, T4, _ = O.local_maxima(E4)
+    assert T4 == 20.0 * np.sort(E4)[B // 2] == 40.0 and lm4.tolist() == []
+    E4[9] = 50.0
+    assert O.local_maxima(E4)[0].tolist() == [9]
 
 
 def test_local_maxima_synthetic_2d():
@@ -438,6 +447,12 @@ def test_capacity_reports_needed_count():
     sig = sparse_signal_1d(4096, 4, 1)
     r = O.atsfft_1d(sig.x, seed=1, capacity=2)
     assert r.status == 6 and r.count >= 4 and len(r.loc) == 2
+    # exactly enough room is no error; one less is
+    c = O.atsfft_1d(sig.x, seed=1).count
+    r = O.atsfft_1d(sig.x, seed=1, capacity=c)
+    assert r.status == 0 and r.count == c and len(r.loc) == c
+    r = O.atsfft_1d(sig.x, seed=1, capacity=c - 1)
+    assert r.status == 6 and r.count == c and len(r.loc) == c - 1
 
 
 def test_trial_cap_not_converged():
@@ -523,6 +538,61 @@ def test_fixed_support_estimates_are_linear_and_equal_the_dft_on_sparse_inputs()
     lhs = O.estimates_1d(a * u + b * v, B, loc, seed=5)
     rhs = a * O.estimates_1d(u, B, loc, seed=5) + b * O.estimates_1d(v, B, loc, seed=5)
     assert np.abs(lhs - rhs).max() < 1e-9 * np.abs(rhs).max()
+
+
+def test_fixed_k_bucket_count_by_brute_force():
+    """Fixed-k mode's B is the smallest power of two with B^2 >= n k in 1D and B^4 >= N^2 k
+    in 2D (the bucket count of the SFFT setting, per axis), within the B range: found here
+    by doubling B until the inequality holds."""
+    def smallest(side_pow, total, lo, hi):
+        B = 1
+        while B ** side_pow < total:
+            B *= 2
+        return min(max(B, lo), hi)
+
+    for n in (1 << 12, 1 << 16):
+        for k in (1, 2, 3, 16, 17, 100, 1000):
+            r = O.atsfft_1d(np.zeros(n, np.complex64), k_hint=k, seed=1,
+                            params=O.default_params(fixed_k=1))
+            assert r.B_star == smallest(2, n * k, 16, n // 16), (n, k)
+    for N in (64, 256):
+        for k in (1, 2, 3, 4, 5, 10, 100, 1000):
+            r = O.atsfft_2d(np.zeros((N, N), np.complex64), k_hint=k, seed=1,
+                            params=O.default_params(fixed_k=1))
+            assert r.B_star == smallest(4, N * N * k, 8, N // 4), (N, k)
+
+
+def test_a_single_trial_range_is_not_an_error():
+    """With one B to try (n = 256: B in [16, 16]; or a hint that starts at the largest B)
+    Eq. (12) has no previous count, so Eq. (14) never asks to double past the range: the
+    transform ends OK at that B (the reading of the stop rule), and exactly sparse inputs
+    are recovered."""
+    sig = sparse_signal_1d(256, 2, 0)
+    r = O.atsfft_1d(sig.x, seed=0)
+    assert r.status == 0 and [int(t[0]) for t in r.trials] == [16] and r.B_star == 16
+    assert r.loc.tolist() == sorted(sig.support.tolist())
+    sig = sparse_signal_1d(1 << 14, 16, 1)
+    r = O.atsfft_1d(sig.x, seed=1, k_hint=600)   # ceil(log2(1200)) = 11 > n/16 = 2^10
+    assert r.status == 0 and [int(t[0]) for t in r.trials] == [1 << 10]
+    assert r.loc.tolist() == sorted(sig.support.tolist())
+
+
+@pytest.mark.parametrize("N,k,seed,status", [(256, 10, 0, 0), (512, 40, 1, 0), (256, 20, 3, 5)])
+def test_2d_walk_starts_at_8_and_follows_eq14(N, k, seed, status):
+    """2D: B (per axis) doubles from 8 while r >= delta2 and stops at the first r < delta2;
+    a walk that would double past N/4 ends NOT_SPARSE (status 5) there."""
+    sig = sparse_signal_2d(N, k, seed)
+    res = O.atsfft_2d(sig.x, seed=seed)
+    Bs = [int(t[0]) for t in res.trials]
+    ks = [int(t[1]) for t in res.trials]
+    assert Bs == [8 << t for t in range(len(Bs))]
+    rs = [math.inf if a == 0 or b == 0 else abs(1.0 - b / a) for a, b in zip(ks, ks[1:])]
+    assert all(r >= 0.05 for r in rs[:-1])
+    assert res.status == status
+    if status == 0:
+        assert rs[-1] < 0.05
+    else:
+        assert rs[-1] >= 0.05 and Bs[-1] == N // 4
 
 
 def test_fixed_k_mode_bucket_count_and_recovery():
