@@ -201,6 +201,26 @@ MUTANTS = {
         "gain *= resp[(o2 + D - 1) / 2];",
         "gain *= 1.0;",
         "Eq. (11) in 2D: the second axis's window gain"),
+    "clamped_window_keeps_its_width": (
+        "*s = (double)hmax / q;",
+        "*s = ss;",
+        "flat window clamped to the signal: the Gaussian narrowed to fit"),
+    "tap_box_scale": (
+        "double box = (t == 0) ? D : sin_pi_t_over_B(t, B) / (M_PI * (double)t / (double)n);",
+        "double box = (t == 0) ? D : sin_pi_t_over_B(t, B) / (M_PI * (double)t / (double)B);",
+        "Eq. (8): the box car's samples against its centre tap"),
+    "permutation_tau_sign": (
+        "int64_t a = (mulmod(sigma, emod(t, n), n) + tau) % n;",
+        "int64_t a = emod(mulmod(sigma, emod(t, n), n) - tau, n);",
+        "Def. 1: x at sigma t + tau"),
+    "estimate_phase_uses_sigma": (
+        "int64_t m = mulmod(hp[1], i, n);",
+        "int64_t m = mulmod(hp[0], i, n);",
+        "Eq. (11): the phase omega^{tau i}, tau not sigma"),
+    "dominance_without_tie_band": (
+        "if (Ec > (1.0 + eta) * Em) return 1;",
+        "if (Ec > Em) return 1;",
+        "Section III-A local maxima: energies within the band are tied"),
     "tap_envelope_width": (
         "double env = exp(-((double)t * (double)t) / (2.0 * s * s));",
         "double env = exp(-((double)t * (double)t) / (4.0 * s * s));",
