@@ -41,3 +41,12 @@ def test_l1_error_metric():
     assert abs(l1_error_per_coefficient(s, s.support[:2], s.coeffs[:2]) - 1 / 3) < 1e-12
     e = l1_error_per_coefficient(s, np.r_[s.support, [0]], np.r_[s.coeffs, [0.5]])
     assert abs(e - (0.5 / 3 if 0 not in s.support else e)) < 1e-12
+
+
+def test_spectrum_alone_is_the_signals_spectrum():
+    from synth import sparse_spectrum_1d
+
+    for n, k, seed, kw in [(4096, 12, 5, {}), (1 << 14, 40, 2, {"mag": ("loguniform", 0.1, 1.0)})]:
+        s = sparse_signal_1d(n, k, seed, snr_db=30.0, **kw)
+        support, coeffs = sparse_spectrum_1d(n, k, seed, **kw)
+        assert np.array_equal(support, s.support) and np.array_equal(coeffs, s.coeffs)
