@@ -163,20 +163,27 @@ def _dist():
 
 
 _REF_SIGS = None
+_REF_ERR = None
 
 
 def _ref_init(n_log2):
     """Worker of the reference arm: builds the oracle and its own copy of the step's
-    signals before any step is timed."""
-    global _REF_SIGS
-    import oracle
-    from synth import sparse_signal_1d
+    signals before any step is timed.  A failure is kept and raised by the worker's
+    first task (an initializer that raises makes the pool respawn workers forever)."""
+    global _REF_SIGS, _REF_ERR
+    try:
+        import oracle
+        from synth import sparse_signal_1d
 
-    oracle.build()
-    _REF_SIGS = [sparse_signal_1d(1 << n_log2, k, 1000 + k, snr_db=SNR_DB).x for k in KS]
+        oracle.build()
+        _REF_SIGS = [sparse_signal_1d(1 << n_log2, k, 1000 + k, snr_db=SNR_DB).x for k in KS]
+    except Exception as exc:
+        _REF_ERR = f"{type(exc).__name__}: {exc}"
 
 
 def _ref_ready(_):
+    if _REF_ERR:
+        raise RuntimeError(f"reference worker setup failed: {_REF_ERR}")
     time.sleep(0.05)
     return os.getpid()
 
@@ -185,6 +192,8 @@ def _ref_step(i):
     """One reference step: the oracle transform of the step's signal i."""
     import oracle
 
+    if _REF_ERR:
+        raise RuntimeError(f"reference worker setup failed: {_REF_ERR}")
     oracle.atsfft_1d(_REF_SIGS[i], seed=SEED, capacity=CAPACITY)
     return i
 

@@ -122,3 +122,18 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     assert bench.run_reference(argparse.Namespace(gpus=2, steps=1, warmup=0), n_log2=12) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_worker_setup_failure_is_raised_not_respawned(monkeypatch):
+    """A failing worker setup surfaces as an error from the first task (an initializer
+    that raised would make the pool respawn workers forever)."""
+    import bench
+
+    monkeypatch.setattr(bench, "KS", ())   # no signals to build: setup succeeds
+    bench._ref_init(8)
+    assert bench._REF_ERR is None and bench._REF_SIGS == []
+    monkeypatch.setattr(bench, "_REF_ERR", "ImportError: no oracle")
+    with pytest.raises(RuntimeError, match="setup failed"):
+        bench._ref_ready(0)
+    with pytest.raises(RuntimeError, match="setup failed"):
+        bench._ref_step(0)
