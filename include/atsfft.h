@@ -23,6 +23,9 @@
  * tables and scratch.  Calls that take a stream only enqueue work on it and never
  * synchronise, except where stated.  A plan may be used by one stream at a time
  * (one scratch set).  Errors are returned as status codes; nothing aborts or throws.
+ * A CUDA error already pending on the calling thread when a call starts (left by the
+ * caller's own earlier work) makes the call return ATSFFT_E_CUDA before it does anything,
+ * and stays pending: the library never clears an error it did not cause.
  */
 #ifndef ATSFFT_H
 #define ATSFFT_H
@@ -280,7 +283,9 @@ atsfft_status atsfft_batch_destroy(atsfft_batch_t batch);
  * call before any stream capture.  Each call synchronises `stream` once (to read back
  * the window normalisation).  All calls share the one array and every call writes all
  * of it that it reads, so nothing needs clearing between calls; calls that overlap on
- * the GPU (other streams, other threads) race on it. */
+ * the GPU (other streams, other threads) race on it.  The device address found by the
+ * first call is kept for the life of the process: a cudaDeviceReset between calls is
+ * not supported. */
 atsfft_status atsfft_hash_spectrum_noalloc(const void *d_x, int64_t n, int64_t B, uint64_t seed,
                                            int phase, int index, void *d_zhat, void *stream);
 

@@ -25,5 +25,11 @@ from .oracle import (  # noqa: F401
     median_componentwise,
     atsfft_1d,
     atsfft_2d,
+    atsfft_log,
     estimates_1d,
+    local_maxima_log,
+    location_select_log,
+    bucket_of,
+    Decision,
+    DEC_KIND,
 )

@@ -350,6 +350,31 @@ static double rel_gap(double a, double b)
     return m > 0.0 ? fabs(a - b) / m : INFINITY;
 }
 
+/* Log of the outcome-deciding comparisons whose relative margin lies below `band`
+ * (see orc_decision): an FP32 implementation can only decide otherwise there. */
+typedef struct {
+    double band;
+    orc_decision *rec;   /* may be NULL: count only */
+    int64_t cap, n;      /* n counts every record, also those beyond cap */
+    int phase, hash;     /* stamped on each record */
+} declog_t;
+
+static void log_decision(declog_t *lg, int kind, int64_t c, int64_t m, double margin)
+{
+    if (!lg || !(margin < lg->band)) return;
+    if (lg->rec && lg->n < lg->cap) {
+        orc_decision *d = &lg->rec[lg->n];
+        d->phase = lg->phase;
+        d->hash = lg->hash;
+        d->kind = kind;
+        d->pad = 0;
+        d->c = c;
+        d->m = m;
+        d->margin = margin;
+    }
+    lg->n++;
+}
+
 /* Does bucket c dominate its neighbour at displacement (d1, d2) (energy Em)?
  * Strictly larger beyond the relative tie band eta wins.  Inside the band the tie
  * goes to the bucket that is later in cyclic order along the first axis that
@@ -421,7 +446,7 @@ static int counted_with_flip(const double *E, int64_t c, int64_t side, int ndim,
  * would change that outcome. */
 static int64_t local_maxima_mode(const double *E, int64_t side, int ndim, double thr_rel,
                                  double thr_med, double eta, int64_t *list, double *T_out,
-                                 double *margin_out, int mode)
+                                 double *margin_out, int mode, declog_t *lg)
 {
     int64_t nb = ndim == 1 ? side : side * side;
     double maxE;
@@ -440,6 +465,7 @@ static int64_t local_maxima_mode(const double *E, int64_t side, int ndim, double
         if (dom && T > 0.0) {
             double g = rel_gap(E[c], T);
             if (g < margin) margin = g;
+            log_decision(lg, ORC_DEC_THRESHOLD, c, -1, g);
         }
         /* pair comparisons, each unordered pair once */
         for (int j = 0; j < nn; j++) {
@@ -453,6 +479,7 @@ static int64_t local_maxima_mode(const double *E, int64_t side, int ndim, double
                 double g = INFINITY;
                 dominates(E[c], E[m[j]], d1[j], d2[j], eta, &g);
                 if (g < margin) margin = g;
+                log_decision(lg, ORC_DEC_DOMINANCE, c, m[j], g);
             }
         }
         if (is_max) {
@@ -469,7 +496,20 @@ int64_t orc_local_maxima(const double *E, int64_t side, int ndim, double thr_rel
                          double thr_med, double eta, int64_t *list, double *T_out,
                          double *margin_out)
 {
-    return local_maxima_mode(E, side, ndim, thr_rel, thr_med, eta, list, T_out, margin_out, 1);
+    return local_maxima_mode(E, side, ndim, thr_rel, thr_med, eta, list, T_out, margin_out, 1,
+                             NULL);
+}
+
+int64_t orc_local_maxima_log(const double *E, int64_t side, int ndim, double thr_rel,
+                             double thr_med, double eta, int mode, double band, int64_t *list,
+                             double *T_out, double *margin_out, orc_decision *rec, int64_t cap,
+                             int64_t *n_rec)
+{
+    declog_t lg = {band, rec, cap, 0, 0, 0};
+    int64_t cnt = local_maxima_mode(E, side, ndim, thr_rel, thr_med, eta, list, T_out, margin_out,
+                                    mode ? 1 : 0, &lg);
+    if (n_rec) *n_rec = lg.n;
+    return cnt;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -519,7 +559,7 @@ static int cmp_i64(const void *a, const void *b)
  * maximum above V(1+eta) is kept, and the rest are filled from those within
  * [V(1-eta), V(1+eta)] in ascending index order.  Result in sel (ascending). */
 static int64_t top_num(const double *E, const int64_t *lm, int64_t cnt, int64_t num,
-                       int64_t *sel, double eta, double *margin)
+                       int64_t *sel, double eta, double *margin, declog_t *lg)
 {
     if (cnt <= num) {
         memcpy(sel, lm, sizeof(int64_t) * (size_t)cnt);
@@ -534,6 +574,7 @@ static int64_t top_num(const double *E, const int64_t *lm, int64_t cnt, int64_t 
         double e = E[lm[i]];
         double g = fmin(rel_gap(e, hi), rel_gap(e, lo));
         if (g < *margin) *margin = g;
+        log_decision(lg, ORC_DEC_TOPNUM, lm[i], -1, g);
         if (e > hi) sel[ns++] = lm[i];
     }
     for (int64_t i = 0; i < cnt && ns < num; i++) { /* lm is ascending */
@@ -550,7 +591,99 @@ int64_t orc_top_num(const double *E, const int64_t *lm, int64_t cnt, int64_t num
 {
     if (num < 1 || cnt < 0) return -1;
     double margin = INFINITY;
-    return top_num(E, lm, cnt, num, sel, eta, &margin);
+    return top_num(E, lm, cnt, num, sel, eta, &margin, NULL);
+}
+
+/* The location step of one hash on its energies (Algorithm 1: the local maxima, then the
+ * num largest of them): the selected buckets, ascending, in sel and their number as the
+ * return value; *margin is lowered to the smallest margin of a deciding comparison.
+ * With a log, the near decisions are recorded, and for each recorded flip of a local
+ * maximum (each alone, and all of them at once) the buckets whose selection that flip
+ * would change: a maximum that enters or leaves the list moves the num-th largest
+ * energy by one rank and the band fill by one place (ORC_DEC_PIVOT, m = the flipped
+ * bucket, or -1 for all at once; margin = the flip's). */
+static int64_t location_select(const double *E, int64_t side, int ndim, const orc_params *p,
+                               int64_t num, int64_t *lm, int64_t *sel, double *margin,
+                               declog_t *lg)
+{
+    int64_t nb = ndim == 1 ? side : side * side;
+    double T = 0.0, marg = INFINITY;
+    int64_t first = lg ? lg->n : 0;
+    int64_t cnt = local_maxima_mode(E, side, ndim, p->thr_rel, p->thr_med, p->tie_eta, lm, &T,
+                                    &marg, 1, lg);
+    int64_t nflip = lg ? lg->n - first : 0;
+    int64_t ns = top_num(E, lm, cnt, num, sel, p->tie_eta, &marg, lg);
+    if (marg < *margin) *margin = marg;
+    if (!lg || nflip == 0 || !lg->rec || first + nflip > lg->cap) return ns;
+
+    unsigned char *base = (unsigned char *)calloc((size_t)nb, 1);
+    unsigned char *alt = (unsigned char *)malloc((size_t)nb);
+    int64_t *lm2 = (int64_t *)malloc(sizeof(int64_t) * (size_t)nb);
+    int64_t *sel2 = (int64_t *)malloc(sizeof(int64_t) * (size_t)nb);
+    orc_decision *fl = (orc_decision *)malloc(sizeof(orc_decision) * (size_t)nflip);
+    memcpy(fl, lg->rec + first, sizeof(orc_decision) * (size_t)nflip);
+    for (int64_t i = 0; i < cnt; i++) base[lm[i]] = 1;
+    int64_t nalt = nflip > 1 ? nflip + 1 : nflip;
+    for (int64_t a = 0; a < nalt; a++) {
+        memcpy(alt, base, (size_t)nb);
+        int64_t r0 = a < nflip ? a : 0, r1 = a < nflip ? a + 1 : nflip;
+        double gmin = INFINITY;
+        for (int64_t r = r0; r < r1; r++) {
+            const orc_decision *d = &fl[r];
+            if (d->margin < gmin) gmin = d->margin;
+            if (d->kind == ORC_DEC_THRESHOLD) {
+                alt[d->c] = !base[d->c];
+            } else {
+                alt[d->c] = (unsigned char)counted_with_flip(E, d->c, side, ndim, T, p->tie_eta, d->m);
+                alt[d->m] = (unsigned char)counted_with_flip(E, d->m, side, ndim, T, p->tie_eta, d->c);
+            }
+        }
+        int64_t cnt2 = 0;
+        for (int64_t c = 0; c < nb; c++)
+            if (alt[c]) lm2[cnt2++] = c;
+        double dummy = INFINITY;
+        int64_t ns2 = top_num(E, lm2, cnt2, num, sel2, p->tie_eta, &dummy, NULL);
+        /* both selections are ascending: walk them together */
+        int64_t i = 0, j = 0;
+        while (i < ns || j < ns2) {
+            if (j >= ns2 || (i < ns && sel[i] < sel2[j])) {
+                log_decision(lg, ORC_DEC_PIVOT, sel[i++], a < nflip ? fl[a].c : -1, gmin);
+            } else if (i >= ns || sel2[j] < sel[i]) {
+                log_decision(lg, ORC_DEC_PIVOT, sel2[j++], a < nflip ? fl[a].c : -1, gmin);
+            } else {
+                i++;
+                j++;
+            }
+        }
+    }
+    free(base);
+    free(alt);
+    free(lm2);
+    free(sel2);
+    free(fl);
+    return ns;
+}
+
+int64_t orc_location_select_log(const double *E, int64_t side, int ndim, const orc_params *p,
+                                int64_t num, double band, int64_t *sel, double *margin_out,
+                                orc_decision *rec, int64_t cap, int64_t *n_rec)
+{
+    orc_params dp;
+    if (!p) {
+        orc_default_params(&dp);
+        p = &dp;
+    }
+    if (!E || !sel || side < 1 || (ndim != 1 && ndim != 2) || num < 1) return -1;
+    int64_t nb = ndim == 1 ? side : side * side;
+    int64_t *lm = (int64_t *)malloc(sizeof(int64_t) * (size_t)nb);
+    if (!lm) return -1;
+    declog_t lg = {band, rec, cap, 0, 1, 0};
+    double margin = INFINITY;
+    int64_t ns = location_select(E, side, ndim, p, num, lm, sel, &margin, &lg);
+    free(lm);
+    if (margin_out) *margin_out = margin;
+    if (n_rec) *n_rec = lg.n;
+    return ns;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -567,6 +700,15 @@ static void bucket_of(int64_t i, int64_t sigma, int64_t n, int64_t B, int64_t *h
     int64_t q = (2 * p + 1 + D) / (2 * D);
     *o2 = 2 * p + 1 - 2 * q * D;
     *h = q % B;
+}
+
+int64_t orc_bucket_of(int64_t i, int64_t sigma, int64_t n, int64_t B)
+{
+    if (!is_pow2(n) || !is_pow2(B) || B > n || i < 0 || i >= n || sigma < 0 || sigma >= n)
+        return -1;
+    int64_t h, o2;
+    bucket_of(i, sigma, n, B, &h, &o2);
+    return h;
 }
 
 static int cmp_double_plain(const void *a, const void *b) { return cmp_double(a, b); }
@@ -666,7 +808,7 @@ static void estimate_hash(const ctx_t *cx, int64_t B, int l, const cplx *Z, cons
 }
 
 static int atsfft_any(const ctx_t *cx, int64_t k_hint, int64_t *loc, double *val_,
-                      int64_t capacity, orc_result *res)
+                      int64_t capacity, orc_result *res, declog_t *lg)
 {
     const orc_params *p = cx->p;
     int64_t n = cx->n;
@@ -732,8 +874,12 @@ static int atsfft_any(const ctx_t *cx, int64_t k_hint, int64_t *loc, double *val
             if (E[c] > maxE) maxE = E[c];
         }
         double marg = INFINITY;
+        if (lg) {
+            lg->phase = 0;
+            lg->hash = b;
+        }
         k_cur = maxE > 0.0 ? local_maxima_mode(E, B, ndim, p->thr_rel, p->thr_med, p->tie_eta,
-                                               NULL, NULL, &marg, 0)
+                                               NULL, NULL, &marg, 0, lg)
                            : 0;
         if (marg < res->min_margin) res->min_margin = marg;
         double r = trial == 0 ? NAN : change_ratio(k_prev, k_cur);
@@ -780,11 +926,11 @@ static int atsfft_any(const ctx_t *cx, int64_t k_hint, int64_t *loc, double *val
             hash_any(cx, B, 1, l, &w, Z);
             for (int64_t c = 0; c < nb; c++)
                 E[c] = creal(Z[c]) * creal(Z[c]) + cimag(Z[c]) * cimag(Z[c]);
-            double marg = INFINITY;
-            int64_t cnt = orc_local_maxima(E, B, ndim, p->thr_rel, p->thr_med, p->tie_eta, lm,
-                                           NULL, &marg);
-            int64_t ns = top_num(E, lm, cnt, kstar, sel, p->tie_eta, &marg);
-            if (marg < res->min_margin) res->min_margin = marg;
+            if (lg) {
+                lg->phase = 1;
+                lg->hash = l;
+            }
+            int64_t ns = location_select(E, B, ndim, p, kstar, lm, sel, &res->min_margin, lg);
             int64_t hp[4];
             orc_hash_params(cx->seed, 1, l, n, ndim, hp);
             int64_t si1 = orc_inv_mod(hp[0], n);
@@ -863,7 +1009,7 @@ int orc_atsfft_1d(const double *x, int64_t n, int64_t k_hint, const orc_params *
         return ORC_E_INVALID_ARG;
     }
     ctx_t cx = {(const cplx *)x, n, 1, p, seed};
-    return atsfft_any(&cx, k_hint, loc, val, capacity, res);
+    return atsfft_any(&cx, k_hint, loc, val, capacity, res, NULL);
 }
 
 int orc_atsfft_2d(const double *x, int64_t N, int64_t k_hint, const orc_params *p,
@@ -881,7 +1027,29 @@ int orc_atsfft_2d(const double *x, int64_t N, int64_t k_hint, const orc_params *
         return ORC_E_INVALID_ARG;
     }
     ctx_t cx = {(const cplx *)x, N, 2, p, seed};
-    return atsfft_any(&cx, k_hint, loc, val, capacity, res);
+    return atsfft_any(&cx, k_hint, loc, val, capacity, res, NULL);
+}
+
+int orc_atsfft_log(const double *x, int ndim, int64_t side, int64_t k_hint, const orc_params *p,
+                   uint64_t seed, int64_t *loc, double *val, int64_t capacity, orc_result *res,
+                   double band, orc_decision *rec, int64_t cap, int64_t *n_rec)
+{
+    orc_params dp;
+    if (!p) {
+        orc_default_params(&dp);
+        p = &dp;
+    }
+    int64_t lo = ndim == 1 ? 256 : 32, hi = ndim == 1 ? ((int64_t)1 << 31) : ((int64_t)1 << 15);
+    if (!x || !res || (ndim != 1 && ndim != 2) || !is_pow2(side) || side < lo || side > hi ||
+        capacity < 0 || cap < 0 || !check_params(p)) {
+        if (res) res->status = ORC_E_INVALID_ARG;
+        return ORC_E_INVALID_ARG;
+    }
+    ctx_t cx = {(const cplx *)x, side, ndim, p, seed};
+    declog_t lg = {band, rec, cap, 0, 0, 0};
+    int st = atsfft_any(&cx, k_hint, loc, val, capacity, res, &lg);
+    if (n_rec) *n_rec = lg.n;
+    return st;
 }
 
 /* The L_est estimates of Eq. (11) of each coordinate loc[0..count) of a 1D signal at B

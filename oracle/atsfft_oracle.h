@@ -50,6 +50,31 @@ typedef struct {
 
 #define ORC_MAX_TRIALS 64
 
+/* A discrete decision close to its boundary.  An implementation that computes the
+ * energies in lower precision (FP32) can only decide differently from this FP64 oracle
+ * where a deciding comparison has a relative margin within its rounding error, so a
+ * transform can log every such comparison below a chosen band; a test then demands that
+ * each difference between the two traces back to a logged one.  Kinds:
+ *   THRESHOLD  E_c against the threshold T, for a bucket c that dominates its
+ *              neighbours (Section III-A local maxima);
+ *   DOMINANCE  the pair (c, m) against the edges of the tie band, where reversing it
+ *              changes the outcome (tuning: the count; location: the maxima set);
+ *   TOPNUM     a local maximum c against the cutoff band edges V(1 +- eta)
+ *              (Algorithm 1 "find num largest");
+ *   PIVOT      a bucket c whose selection changes if the logged local-maximum flip of
+ *              bucket m (-1: all of the hash's flips at once) happened: the num-th
+ *              largest energy moves by a rank and the band fill by a place. */
+enum { ORC_DEC_THRESHOLD = 1, ORC_DEC_DOMINANCE = 2, ORC_DEC_TOPNUM = 3, ORC_DEC_PIVOT = 4 };
+
+typedef struct {
+    int32_t phase;    /* 0: a tuning trial, 1: a location hash */
+    int32_t hash;     /* tuning: log2 B (per axis) of the trial; location: hash index l */
+    int32_t kind;     /* ORC_DEC_* */
+    int32_t pad;
+    int64_t c, m;     /* bucket indices (linear c1 * B + c2 in 2D); m = -1 if unused */
+    double margin;    /* relative margin of the comparison (PIVOT: of the flip) */
+} orc_decision;
+
 typedef struct {
     int status;
     int64_t B_star;             /* bucket count chosen by the tuning (per axis in 2D) */
@@ -104,6 +129,29 @@ int64_t orc_local_maxima(const double *E, int64_t side, int ndim, double thr_rel
                          double thr_med, double eta, int64_t *list, double *T_out,
                          double *margin_out);
 
+/* orc_local_maxima with a choice of what counts as the outcome (mode 0: the number of
+ * maxima, as in a tuning trial; 1: which buckets are maxima, as in a location hash) and
+ * a log: the comparisons deciding it with a margin below `band` go to rec (capacity
+ * cap); *n_rec receives their number (which may exceed cap: then only cap are stored). */
+int64_t orc_local_maxima_log(const double *E, int64_t side, int ndim, double thr_rel,
+                             double thr_med, double eta, int mode, double band, int64_t *list,
+                             double *T_out, double *margin_out, orc_decision *rec, int64_t cap,
+                             int64_t *n_rec);
+
+/* The location step of one hash on its energies E, exactly as the transform takes it
+ * (local maxima, then the num largest of them, parameters from p, NULL = defaults):
+ * the selected buckets (ascending) in sel (capacity: the number of buckets), their
+ * number returned (-1 on bad arguments); *margin_out the smallest margin; the near
+ * decisions, including the PIVOT consequences of each local-maximum flip, logged as in
+ * orc_local_maxima_log (records stamped phase 1, hash 0). */
+int64_t orc_location_select_log(const double *E, int64_t side, int ndim, const orc_params *p,
+                                int64_t num, double band, int64_t *sel, double *margin_out,
+                                orc_decision *rec, int64_t cap, int64_t *n_rec);
+
+/* Bucket h(i) of coordinate i under a hash with this sigma, one axis (Eq. (10) as read
+ * here); -1 on bad arguments. */
+int64_t orc_bucket_of(int64_t i, int64_t sigma, int64_t n, int64_t B);
+
 /* The "num largest" cutoff of the location step (Algorithm 1) on a list of local maxima:
  * lm holds cnt bucket indices in ascending order, E the energies by bucket.  Writes the
  * kept buckets (ascending) to sel (capacity cnt) and returns how many; -1 for num < 1
@@ -128,6 +176,14 @@ int orc_atsfft_1d(const double *x, int64_t n, int64_t k_hint, const orc_params *
 int orc_atsfft_2d(const double *x, int64_t N, int64_t k_hint, const orc_params *p,
                   uint64_t seed, int64_t *loc, double *val, int64_t capacity,
                   orc_result *res);
+
+/* orc_atsfft_1d (ndim 1, side = n) or orc_atsfft_2d (ndim 2, side = N) that also logs
+ * every outcome-deciding comparison of the tuning trials and the location hashes whose
+ * margin lies below `band` (see orc_decision) into rec (capacity cap); *n_rec receives
+ * the number of records (only cap are stored when it is larger). */
+int orc_atsfft_log(const double *x, int ndim, int64_t side, int64_t k_hint, const orc_params *p,
+                   uint64_t seed, int64_t *loc, double *val, int64_t capacity, orc_result *res,
+                   double band, orc_decision *rec, int64_t cap, int64_t *n_rec);
 
 /* The loops_est estimates of Eq. (11) (no median) of coordinates loc[0..count) of a 1D
  * signal at B buckets; out: count x loops_est complex values, interleaved (re, im). */

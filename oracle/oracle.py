@@ -48,6 +48,27 @@ class _CResult(C.Structure):
     ]
 
 
+class OracleDecision(C.Structure):
+    _fields_ = [
+        ("phase", C.c_int32), ("hash", C.c_int32), ("kind", C.c_int32), ("pad", C.c_int32),
+        ("c", C.c_int64), ("m", C.c_int64), ("margin", C.c_double),
+    ]
+
+
+DEC_THRESHOLD, DEC_DOMINANCE, DEC_TOPNUM, DEC_PIVOT = 1, 2, 3, 4
+DEC_KIND = {1: "threshold", 2: "dominance", 3: "topnum", 4: "pivot"}
+
+
+@dataclass
+class Decision:
+    phase: int      # 0 tuning trial, 1 location hash
+    hash: int       # tuning: log2 B of the trial; location: hash index l
+    kind: str       # threshold, dominance, topnum, pivot
+    c: int
+    m: int          # -1 when one bucket decides
+    margin: float
+
+
 @dataclass
 class OracleResult:
     status: int
@@ -105,6 +126,16 @@ def lib():
         L.orc_atsfft_2d.argtypes = L.orc_atsfft_1d.argtypes
         L.orc_estimates_1d.argtypes = [C.c_void_p, i64, i64, P(OracleParams), u64, C.c_void_p, i64,
                                        C.c_void_p]
+        L.orc_local_maxima_log.argtypes = [C.c_void_p, i64, i32, dbl, dbl, dbl, i32, dbl,
+                                           C.c_void_p, P(dbl), P(dbl), C.c_void_p, i64, P(i64)]
+        L.orc_local_maxima_log.restype = i64
+        L.orc_location_select_log.argtypes = [C.c_void_p, i64, i32, P(OracleParams), i64, dbl,
+                                              C.c_void_p, P(dbl), C.c_void_p, i64, P(i64)]
+        L.orc_location_select_log.restype = i64
+        L.orc_bucket_of.argtypes = [i64, i64, i64, i64]
+        L.orc_bucket_of.restype = i64
+        L.orc_atsfft_log.argtypes = [C.c_void_p, i32, i64, i64, P(OracleParams), u64, C.c_void_p,
+                                     C.c_void_p, i64, P(_CResult), dbl, C.c_void_p, i64, P(i64)]
         _lib = L
     return _lib
 
@@ -207,6 +238,57 @@ def top_num(E, lm, num, eta=1e-2):
     return sel[:ns].copy()
 
 
+def _decisions(buf, n):
+    return [Decision(d.phase, d.hash, DEC_KIND[d.kind], d.c, d.m, d.margin) for d in buf[:n]]
+
+
+def _logged(call, cap=4096):
+    """Runs call(buffer, capacity, byref(count)) with a record buffer large enough for
+    every record (once more with the exact size if the first buffer was too small)."""
+    while True:
+        buf = (OracleDecision * max(cap, 1))()
+        n = C.c_int64()
+        out = call(buf, cap, C.byref(n))
+        if n.value <= cap:
+            return out, _decisions(buf, n.value)
+        cap = n.value
+
+
+def local_maxima_log(E, ndim=1, mode=1, band=np.inf, thr_rel=1e-3, thr_med=20.0, eta=1e-2):
+    """orc_local_maxima_log: (list, T, margin, decisions) with every deciding comparison
+    whose margin is below `band` (mode 0: the count is the outcome; 1: the maxima set)."""
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    side = E.shape[0]
+    lst = np.zeros(E.size, dtype=np.int64)
+    T, m = C.c_double(), C.c_double()
+    cnt, dec = _logged(lambda buf, cap, n: lib().orc_local_maxima_log(
+        _ptr(E), side, ndim, thr_rel, thr_med, eta, mode, band, _ptr(lst), C.byref(T),
+        C.byref(m), buf, cap, n))
+    return lst[:cnt].copy(), T.value, m.value, dec
+
+
+def location_select_log(E, num, ndim=1, band=np.inf, params=None):
+    """orc_location_select_log: (selected buckets, margin, decisions) of one location hash."""
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    side = E.shape[0]
+    sel = np.zeros(E.size, dtype=np.int64)
+    m = C.c_double()
+    p = params or default_params()
+    ns, dec = _logged(lambda buf, cap, n: lib().orc_location_select_log(
+        _ptr(E), side, ndim, C.byref(p), num, band, _ptr(sel), C.byref(m), buf, cap, n))
+    if ns < 0:
+        raise ValueError("orc_location_select_log: invalid arguments")
+    return sel[:ns].copy(), m.value, dec
+
+
+def bucket_of(i, sigma, n, B):
+    """Bucket of coordinate i under a hash with this sigma on one axis (Eq. (10))."""
+    h = lib().orc_bucket_of(int(i), int(sigma), int(n), int(B))
+    if h < 0:
+        raise ValueError("orc_bucket_of: invalid arguments")
+    return h
+
+
 def median_componentwise(v):
     v = np.ascontiguousarray(v, dtype=np.complex128)
     out = np.zeros(2)
@@ -244,6 +326,32 @@ def atsfft_1d(x, k_hint=0, params=None, seed=0, capacity=None) -> OracleResult:
 def atsfft_2d(x, k_hint=0, params=None, seed=0, capacity=None) -> OracleResult:
     x = np.asarray(x)
     return _run(lib().orc_atsfft_2d, x, x.shape[0], k_hint, params, seed, capacity)
+
+
+def atsfft_log(x, k_hint=0, params=None, seed=0, capacity=None, band=2e-4):
+    """atsfft_1d / atsfft_2d (by x's shape) that also returns the decisions whose margin
+    lies below `band`: (OracleResult, [Decision, ...])."""
+    x = np.asarray(x)
+    ndim = x.ndim
+    xx = _as_c128(x)
+    if params is None:
+        params = default_params()
+    if capacity is None:
+        capacity = 1 << 20
+    loc = np.zeros(max(capacity, 1), dtype=np.int64)
+    val = np.zeros(max(capacity, 1), dtype=np.complex128)
+    r = _CResult()
+
+    def call(buf, cap, n):
+        lib().orc_atsfft_log(_ptr(xx), ndim, x.shape[0], k_hint, C.byref(params), seed,
+                             _ptr(loc), _ptr(val), capacity, C.byref(r), band, buf, cap, n)
+
+    _, dec = _logged(call)
+    cnt = min(r.count, capacity)
+    trials = [(r.trial_B[i], r.trial_k[i], r.trial_r[i]) for i in range(r.n_trials)]
+    res = OracleResult(r.status, r.B_star, r.k_star, r.count, trials, r.min_margin,
+                       loc[:cnt].copy(), val[:cnt].copy())
+    return res, dec
 
 
 def estimates_1d(x, B, loc, params=None, seed=0):

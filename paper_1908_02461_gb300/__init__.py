@@ -31,7 +31,6 @@ from ._lib import (  # noqa: F401
     atsfft_exec,
     atsfft_exec_2d,
     atsfft_hash_spectrum,
-    atsfft_hash_spectrum_noalloc,
     atsfft_last_result,
     atsfft_last_trace,
     atsfft_params,
@@ -94,6 +93,24 @@ def _power_of_two(v) -> bool:
     except TypeError:
         return False
     return v > 0 and (v & (v - 1)) == 0
+
+
+def atsfft_hash_spectrum_noalloc(d_x, n, B, seed, phase, index, d_zhat, stream=None) -> int:
+    """The allocation-free bucket spectrum of one hash (include/atsfft.h), with the two
+    buffers checked first: d_x must be a contiguous complex64 tensor of n values and
+    d_zhat one of at least B values, both on the current CUDA device (the C call reads
+    and writes them through raw pointers).  Returns the status code."""
+    import torch
+
+    what = "atsfft_hash_spectrum_noalloc"
+    if not (_power_of_two(n) and _power_of_two(B)):
+        return E_INVALID_ARG
+    dev = (torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available()
+           else torch.device("cuda"))
+    check_buffer(what, "d_x", d_x, torch.complex64, dev, numel=int(n))
+    check_buffer(what, "d_zhat", d_zhat, torch.complex64, dev, min_numel=int(B))
+    return _lib.atsfft_hash_spectrum_noalloc(d_x, int(n), int(B), seed, phase, index, d_zhat,
+                                             stream)
 
 
 def params(**overrides) -> atsfft_params:

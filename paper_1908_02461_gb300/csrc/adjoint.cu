@@ -180,7 +180,7 @@ extern "C" atsfft_status atsfft_estimate_apply(atsfft_plan_t P, int64_t B, const
     if (st != ATSFFT_OK) return st;
     if (!d_u || (count > 0 && !d_out)) return ATSFFT_E_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaGetLastError();
+    if (caller_error_pending()) return ATSFFT_E_CUDA;
     // the L_est estimation spectra of u at B, as the transform computes them
     const int chunks = launch_est_bin(P, (const float2 *)d_u, b, s);
     int lb[kMaxLoops], ch[kMaxLoops];
@@ -208,7 +208,7 @@ extern "C" atsfft_status atsfft_estimate_adjoint(atsfft_plan_t P, int64_t B, con
     if (st != ATSFFT_OK) return st;
     if (!d_gx || (count > 0 && !d_gval)) return ATSFFT_E_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaGetLastError();
+    if (caller_error_pending()) return ATSFFT_E_CUDA;
     const int64_t LB = (int64_t)P->L_est << b;
     float2 *Q = P->d_part, *F = P->d_z;
     cudaError_t e = cudaMemsetAsync(Q, 0, sizeof(float2) * (size_t)LB, s);

@@ -31,7 +31,7 @@ static atsfft_status exec_common(atsfft_plan_t P, int ndim, const void *d_x, int
         return ATSFFT_E_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const float2 *x = (const float2 *)d_x;
-    cudaGetLastError();   // clear a stale error so the status below is this call's
+    if (caller_error_pending()) return ATSFFT_E_CUDA;
     P->launches = 0;
     const bool fp64 = P->p.precision == 1;
     if (fp64) {
@@ -101,7 +101,7 @@ extern "C" atsfft_status atsfft_hash_spectrum(atsfft_plan_t P, const void *d_x, 
     hash_params_for(P->seed, phase, index, P->n, P->ndim, &hp);
     // the inspection hash lives in the spare slot after the location/estimation hashes
     HashParam *d_hp = P->d_le + 2 * kMaxLoops;
-    cudaGetLastError();
+    if (caller_error_pending()) return ATSFFT_E_CUDA;
     cudaError_t e = cudaMemcpyAsync(d_hp, &hp, sizeof(hp), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_status(e);
     launch_single_hash(P, (const float2 *)d_x, b, hp, d_hp, P->d_z, s);

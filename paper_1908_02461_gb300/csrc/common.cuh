@@ -196,6 +196,12 @@ namespace atsfft {
 
 atsfft_status cuda_status(cudaError_t e);
 
+// True when a CUDA error is already pending on the calling thread as an entry point
+// starts (the caller's own earlier work).  Entry points then return ATSFFT_E_CUDA before
+// doing anything and leave the error pending, so the library never consumes an error it
+// did not cause; the errors of its own calls are read (and cleared) after its launches.
+inline bool caller_error_pending() { return cudaPeekAtLastError() != cudaSuccess; }
+
 inline void prof_mark(const atsfft_plan_s *P, int i, cudaStream_t s)
 {
     if (P->prof) cudaEventRecord(P->ev[i], s);

@@ -50,6 +50,10 @@ constexpr size_t kPartialDoubles = (kNoAllocBytes - kOffPartial) / sizeof(double
 static_assert(kOffPartial < kNoAllocBytes, "no-alloc scratch layout overflows");
 static_assert(sizeof(WindowParam) * kMaxLogB <= 4096, "window table slot too small");
 
+// Stores this call's window parameters in the scratch's window table (passed by value,
+// so nothing on the host stack has to outlive the call).
+__global__ void k_noalloc_store_window(WindowParam *slot, WindowParam w) { *slot = w; }
+
 // Bucket order: Zhat[c] = P[sigma' c] exp(2 pi i c sigma' tau / B), hash passed by value.
 __global__ void k_noalloc_unpermute(const float2 *spec, HashParam hp, int logB, float2 *out)
 {
@@ -73,6 +77,8 @@ __global__ void k_window_finish(int64_t D, const double *partial, int nchunks, d
 __global__ void k_phase_table(int logn, int s_bits, float2 *tab);
 
 // Once per device, with it current: the scratch's device address and the twiddles.
+// The result is kept for the life of the process, so a cudaDeviceReset (which
+// reinitialises the array) is not supported between calls.
 static atsfft_status noalloc_setup(int dev, cudaStream_t s, unsigned char **base)
 {
     std::lock_guard<std::mutex> lock(g_dev_mutex);
@@ -107,6 +113,7 @@ extern "C" atsfft_status atsfft_hash_spectrum_noalloc(const void *d_x, int64_t n
     while (((int64_t)1 << logn) < n) logn++;
     while (((int64_t)1 << b) < B) b++;
     if (logn < 8 || logn > kNoAllocMaxLogN || b < 4 || b > logn - 4) return ATSFFT_E_INVALID_ARG;
+    if (caller_error_pending()) return ATSFFT_E_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -147,7 +154,6 @@ extern "C" atsfft_status atsfft_hash_spectrum_noalloc(const void *d_x, int64_t n
     double *partial = (double *)(base + kOffPartial);
     double *resp = (double *)(base + kOffResp);
     double *S0_dev = (double *)(base + kOffS0);
-    cudaGetLastError();
     dim3 grid((unsigned)((D + 1 + 127) / 128), (unsigned)nch);
     k_phase_table<<<P.num_sms, 256, 0, s>>>(logn, P.phase_s, P.d_phase);
     k_window_partial<<<grid, 128, 0, s>>>(n, b, w.s, w.h, partial, nch);
@@ -162,6 +168,8 @@ extern "C" atsfft_status atsfft_hash_spectrum_noalloc(const void *d_x, int64_t n
     P.h_win[b] = w;
     P.h_tjob[b] = make_job(&P, b, 1);
     if ((size_t)P.h_tjob[b].chunks * (size_t)B > kElems18) return ATSFFT_E_INVALID_ARG;
+    // the device copy of the window, as a plan's table holds it (P.d_win[b])
+    k_noalloc_store_window<<<1, 1, 0, s>>>(P.d_win + b, w);
 
     HashParam hp;
     hash_params_for(seed, phase, index, n, 1, &hp);

@@ -109,3 +109,19 @@ def test_bucket_count_check_takes_python_and_numpy_integers():
 
     assert A._power_of_two(64) and A._power_of_two(np.int64(4096))
     assert not any(A._power_of_two(v) for v in (0, -8, 48, 64.0, "64"))
+
+
+def test_noalloc_wrapper_refuses_buffers_before_the_library_call():
+    """atsfft_hash_spectrum_noalloc takes raw pointers: the package's wrapper checks that
+    the input holds n complex64 values and the output at least B, on the current CUDA
+    device, before calling it (on this CPU-only host every CPU tensor is refused)."""
+    n, B = 1 << 10, 64
+    x = torch.zeros(n, dtype=torch.complex64)
+    z = torch.zeros(B, dtype=torch.complex64)
+    if torch.cuda.is_available():
+        pytest.skip("CPU-only check")
+    with pytest.raises(A.ArgumentError, match="must be on cuda"):
+        A.atsfft_hash_spectrum_noalloc(x, n, B, 0, 1, 0, z)
+    with pytest.raises(A.ArgumentError, match="hold 1024 elements"):
+        A.atsfft_hash_spectrum_noalloc(x[:100], n, B, 0, 1, 0, z)
+    assert A.atsfft_hash_spectrum_noalloc(x, 1000, B, 0, 1, 0, z) == A.E_INVALID_ARG

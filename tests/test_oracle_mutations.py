@@ -221,6 +221,42 @@ MUTANTS = {
         "if (Ec > (1.0 + eta) * Em) return 1;",
         "if (Ec > Em) return 1;",
         "Section III-A local maxima: energies within the band are tied"),
+    "threshold_margin_skipped": (
+        "            if (g < margin) margin = g;\n            log_decision(lg, ORC_DEC_THRESHOLD, c, -1, g);",
+        "            log_decision(lg, ORC_DEC_THRESHOLD, c, -1, g);",
+        "decision margins: the threshold test of Section III-A"),
+    "threshold_decision_not_logged": (
+        "            log_decision(lg, ORC_DEC_THRESHOLD, c, -1, g);",
+        "            (void)0;",
+        "near-decision log: the threshold test of Section III-A"),
+    "dominance_margin_skipped": (
+        "                if (g < margin) margin = g;\n                log_decision(lg, ORC_DEC_DOMINANCE",
+        "                log_decision(lg, ORC_DEC_DOMINANCE",
+        "decision margins: the tie band of Section III-A"),
+    "dominance_gap_one_edge": (
+        "double g = fmin(rel_gap(Ec, (1.0 + eta) * Em), rel_gap(Em, (1.0 + eta) * Ec));",
+        "double g = rel_gap(Ec, (1.0 + eta) * Em);",
+        "decision margins: both edges of the tie band"),
+    "margin_mode_ignored": (
+        "int changes = mode == 0 ? (before_c + before_m != after_c + after_m)",
+        "int changes = 1 ? (before_c + before_m != after_c + after_m)",
+        "decision margins: the location outcome is the maxima set, not their number"),
+    "topnum_gap_one_edge": (
+        "double g = fmin(rel_gap(e, hi), rel_gap(e, lo));",
+        "double g = rel_gap(e, hi);",
+        "decision margins: both edges of Algorithm 1's cutoff band"),
+    "pivot_shifts_not_logged": (
+        "if (!lg || nflip == 0 || !lg->rec || first + nflip > lg->cap) return ns;",
+        "return ns;",
+        "near-decision log: selections moved by a local-maximum flip"),
+    "location_margin_not_kept": (
+        "    if (marg < *margin) *margin = marg;",
+        "    (void)marg;",
+        "decision margins of the location hashes"),
+    "tuning_margin_not_kept": (
+        "        if (marg < res->min_margin) res->min_margin = marg;",
+        "        (void)marg;",
+        "decision margins of the tuning trials (Eqs. (12)-(14))"),
     "tap_envelope_width": (
         "double env = exp(-((double)t * (double)t) / (2.0 * s * s));",
         "double env = exp(-((double)t * (double)t) / (4.0 * s * s));",

@@ -373,6 +373,169 @@ def test_top_num_fills_the_tie_band_in_ascending_bucket_order():
     assert O.top_num(F, [2, 4, 6, 8, 10], 9).tolist() == [2, 4, 6, 8, 10]
 
 
+# --------------------------------------------------------------------------
+# Decision margins and the near-decision log (the switch of the GPU parity rule)
+# --------------------------------------------------------------------------
+
+def _rel(a, b):
+    return abs(a - b) / max(abs(a), abs(b))
+
+
+def test_margin_of_a_threshold_decision_worked_case():
+    """Section III-A local maxima, threshold T = max(thr_rel maxE, thr_med medianE).
+    Worked case: 64 buckets at 1e-9 (median term 2e-8), a spike of 1 at bucket 10
+    (T = 1e-3) and an isolated bucket 30 at T (1 + 3e-5).  The only comparison near its
+    boundary is E_30 against T, relative margin 3e-5 / (1 + 3e-5); the noise buckets tie
+    within the band but are below T, so reversing their pairs changes nothing and is not
+    a deciding comparison."""
+    E = np.full(64, 1e-9)
+    E[10] = 1.0
+    E[30] = 1e-3 * (1 + 3e-5)
+    for mode in (0, 1):
+        lm, T, m, dec = O.local_maxima_log(E, mode=mode, band=1e-3)
+        assert lm.tolist() == [10, 30] and T == pytest.approx(1e-3, rel=1e-15)
+        assert m == pytest.approx(_rel(E[30], 1e-3), rel=1e-9)
+        assert [(d.kind, d.c, d.m) for d in dec] == [("threshold", 30, -1)]
+        assert dec[0].margin == pytest.approx(m, rel=1e-12)
+    # just below T: the same margin, bucket 30 no longer a maximum
+    E[30] = 1e-3 * (1 - 3e-5)
+    lm, _, m, dec = O.local_maxima_log(E, band=1e-3)
+    assert lm.tolist() == [10] and m == pytest.approx(_rel(E[30], 1e-3), rel=1e-9)
+    assert [(d.kind, d.c) for d in dec] == [("threshold", 30)]
+
+
+def test_margin_of_a_dominance_decision_depends_on_what_the_outcome_is():
+    """Two neighbours 0.5 and 0.5 (1 + eta)(1 + 2e-5): the later one dominates by a
+    relative 2e-5 beyond the tie band.  Reversing the pair swaps which bucket is the
+    maximum: that changes the maxima set (location, mode 1: logged, margin 2e-5/(1+2e-5))
+    but not their number (tuning, mode 0: not a deciding comparison)."""
+    eta = 1e-2
+    E = np.full(64, 1e-9)
+    E[10] = 1.0
+    E[40] = 0.5
+    E[41] = 0.5 * (1 + eta) * (1 + 2e-5)
+    lm, _, m1, dec1 = O.local_maxima_log(E, mode=1, band=1e-3)
+    assert lm.tolist() == [10, 41]
+    assert [(d.kind, d.c, d.m) for d in dec1] == [("dominance", 40, 41)]
+    assert m1 == pytest.approx(_rel(E[41], (1 + eta) * E[40]), rel=1e-9)
+    lm0, _, m0, dec0 = O.local_maxima_log(E, mode=0, band=1e-3)
+    assert lm0.tolist() == [10, 41] and dec0 == [] and m0 > 1e-3
+    # the same pair reversed in position: the earlier bucket dominates; still logged
+    E[40], E[41] = E[41], E[40]
+    lm, _, m, dec = O.local_maxima_log(E, mode=1, band=1e-3)
+    assert lm.tolist() == [10, 40] and [(d.kind, d.c, d.m) for d in dec] == [("dominance", 40, 41)]
+
+
+def test_margin_of_the_cutoff_band_worked_case():
+    """Algorithm 1 "find num largest" with the tie band: maxima 1.0 (bucket 5), 0.9 (15),
+    0.5 (25) and 0.9 (1 - eta)(1 - 4e-5) (35), num = 2.  The pivot is 0.9, the band
+    [0.891, 0.909]; bucket 35 lies just below its lower edge (relative 4e-5) and is the
+    only comparison near a boundary; the cut keeps 5 and 15."""
+    eta = 1e-2
+    E = np.full(64, 1e-9)
+    E[[5, 15, 25]] = [1.0, 0.9, 0.5]
+    E[35] = 0.9 * (1 - eta) * (1 - 4e-5)
+    sel, m, dec = O.location_select_log(E, 2, band=1e-3)
+    assert sel.tolist() == [5, 15]
+    assert [(d.kind, d.c) for d in dec] == [("topnum", 35)]
+    assert m == pytest.approx(_rel(E[35], 0.9 * (1 - eta)), rel=1e-9)
+
+
+def test_a_near_local_maximum_flip_logs_the_buckets_whose_selection_it_moves():
+    """A near dominance decision in a location hash moves the cut: maxima 1.0 (bucket 5),
+    0.935 (15) and the pair 34 < 35 with E_35 = 0.95 just beyond the tie band above E_34.
+    num = 2: the pivot is E_35, the band [0.9405, 0.9595], the cut {5, 35}.  Were the pair
+    reversed, 34 would be the maximum instead, the pivot E_34 = 0.9406 and its band
+    [0.9312, 0.9500] would hold 15 and 34, of which the lower bucket fills the cut: {5, 15}.
+    So the log names the pair and, as moved by that flip, buckets 15 and 35 (bucket 15 is
+    nowhere near a boundary itself)."""
+    eta = 1e-2
+    E = np.full(64, 1e-9)
+    E[5], E[15] = 1.0, 0.935
+    E[35] = 0.95
+    E[34] = 0.95 / ((1 + eta) * (1 + 2e-5))
+    sel, m, dec = O.location_select_log(E, 2, band=1e-3)
+    assert sel.tolist() == [5, 35]
+    got = sorted((d.kind, d.c, d.m) for d in dec)
+    assert got == [("dominance", 34, 35), ("pivot", 15, 34), ("pivot", 35, 34)], got
+    assert m == pytest.approx(_rel(E[35], (1 + eta) * E[34]), rel=1e-9)
+    # the flipped hash, computed directly (bucket 35 no longer a maximum), has the cut
+    # the log predicts
+    G = np.full(64, 1e-9)
+    G[5], G[15], G[34] = 1.0, 0.935, E[34]
+    assert O.location_select_log(G, 2, band=1e-3)[0].tolist() == [5, 15]
+
+
+def test_margin_bounds_every_outcome_change_under_perturbation():
+    """The margin is the smallest relative distance of a deciding comparison from its
+    boundary, so scaling every energy by its own factor within (1 +- margin/3) can change
+    neither the count (tuning) nor the maxima set (location) nor the cut; energies drawn
+    from a few levels make exact and near ties frequent."""
+    rng = np.random.default_rng(11)
+    for trial in range(40):
+        ndim = 1 if trial % 2 == 0 else 2
+        side = 128 if ndim == 1 else 12
+        shape = (side,) if ndim == 1 else (side, side)
+        levels = np.array([1e-9, 1e-4, 1e-3, 1.02e-3, 0.3, 0.302, 0.5, 0.505, 1.0])
+        E = levels[rng.integers(0, len(levels), size=shape)] * (1 + 1e-4 * rng.random(shape))
+        for mode in (0, 1):
+            lm, _, m, _ = O.local_maxima_log(E, ndim=ndim, mode=mode, band=0.0)
+            if not np.isfinite(m) or m <= 0:
+                continue
+            for _ in range(10):
+                P = E * (1 + (m / 3) * rng.uniform(-1, 1, size=shape))
+                lp, _, _, _ = O.local_maxima_log(P, ndim=ndim, mode=mode, band=0.0)
+                if mode == 0:
+                    assert len(lp) == len(lm), (trial, m)
+                else:
+                    assert lp.tolist() == lm.tolist(), (trial, m)
+        num = max(1, len(O.local_maxima(E, ndim=ndim)[0]) // 2)
+        sel, m, _ = O.location_select_log(E, num, ndim=ndim, band=0.0)
+        for _ in range(10):
+            P = E * (1 + (m / 3) * rng.uniform(-1, 1, size=shape))
+            assert O.location_select_log(P, num, ndim=ndim, band=0.0)[0].tolist() == sel.tolist()
+
+
+@pytest.mark.parametrize("ndim,seed", [(1, 4), (1, 18), (2, 2), (2, 6)])
+def test_logged_transform_margins_agree_with_the_result(ndim, seed):
+    """Whole transforms (Algorithm 2): the log with an unbounded band holds every
+    deciding comparison, so its smallest margin is the result's min_margin; a narrower
+    band keeps exactly those below it; and logging changes no output.  (Seeds 4 and 2
+    have their smallest margin in a location hash, 18 and 6 in a tuning trial.)"""
+    if ndim == 1:
+        sig = sparse_signal_1d(1 << 12, 12, seed, snr_db=30)
+    else:
+        sig = sparse_signal_2d(64, 6, seed, snr_db=30)
+    ref = (O.atsfft_1d if ndim == 1 else O.atsfft_2d)(sig.x, seed=seed)
+    r_all, d_all = O.atsfft_log(sig.x, seed=seed, band=np.inf)
+    r_cut, d_cut = O.atsfft_log(sig.x, seed=seed, band=3e-2)
+    for r in (r_all, r_cut):
+        assert r.loc.tolist() == ref.loc.tolist() and r.k_star == ref.k_star
+        assert r.min_margin == ref.min_margin
+    base = [d for d in d_all if d.kind != "pivot"]
+    assert {d.phase for d in base} == {0, 1}
+    assert min(d.margin for d in base) == ref.min_margin
+    key = lambda d: (d.phase, d.hash, d.kind, d.c, d.m)
+    assert sorted(map(key, (d for d in d_cut if d.kind != "pivot"))) == \
+        sorted(map(key, (d for d in base if d.margin < 3e-2)))
+    # tuning records name the trials' log2 B, location records the hash index
+    tB = {int(b).bit_length() - 1 for b, _, _ in ref.trials}
+    assert {d.hash for d in base if d.phase == 0} <= tB
+    assert {d.hash for d in base if d.phase == 1} <= set(range(7))
+
+
+def test_bucket_of_matches_the_reverse_hash_preimages():
+    """Eq. (10): coordinate i lies in bucket h(i) exactly when sigma i mod n is one of the
+    D permuted positions [c D - D/2, c D + D/2) the reverse hash visits."""
+    n, B = 1 << 10, 32
+    D = n // B
+    sigma = O.hash_params(5, 1, 0, n)[0]
+    for i in range(n):
+        c = O.bucket_of(i, sigma, n, B)
+        p = sigma * i % n
+        assert (p - (c * D - D // 2)) % n < D
+
+
 def test_median_componentwise_matches_numpy():
     rng = np.random.default_rng(5)
     for L in (1, 3, 5, 7, 9):
