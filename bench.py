@@ -309,7 +309,21 @@ def _stream(n, B):
     return 5 * (2 * _window_h(n, B) + 1) >= n and n // B <= 4096
 
 
-def roofline(per_signal, traces, n, stages=3):
+def mufu_pair_peak(stream=None):
+    """Sample-hash pairs per second the MUFU pipe allows, measured: atsfft_mufu_probe
+    times independent ex2.approx + rcp.approx chains on every SM (two operations per
+    pair).  Returns (pairs/s, source string); the derived figure if the probe fails."""
+    import paper_1908_02461_gb300 as A
+
+    st, ops = A.atsfft_mufu_probe(4096, stream)
+    if st == A.OK and ops > 0:
+        return ops / 2.0, ("measured: atsfft_mufu_probe (ex2.approx + rcp.approx chains on "
+                           f"every SM) {ops / 1e12:.2f} Tops/s / 2 ops per sample-hash pair")
+    return SFU_PER_SM_CLK * SMS * SM_MAX_MHZ * 1e6 / 2.0, (
+        "derived: 32 SFU ops/clk/SM x 152 SMs x 2070 MHz / 2 SFU ops per sample-hash pair")
+
+
+def roofline(per_signal, traces, n, stages=3, pair_peak=None, pair_src=None):
     """Algorithmic work of each profiled phase per launch, achieved rate, fraction of peak.
 
     Bytes (HBM-bound phases) count each input and output value once; pairs (the
@@ -320,7 +334,9 @@ def roofline(per_signal, traces, n, stages=3):
     exit at once otherwise)."""
     peaks, src = _peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    pair_peak = SFU_PER_SM_CLK * SMS * SM_MAX_MHZ * 1e6 / 2.0   # 2 SFU ops per pair
+    if pair_peak is None:
+        pair_peak = SFU_PER_SM_CLK * SMS * SM_MAX_MHZ * 1e6 / 2.0   # 2 SFU ops per pair
+        pair_src = "derived: 32 SFU ops/clk/SM x 152 SMs x 2070 MHz / 2 SFU ops per sample-hash pair"
     logn = n.bit_length() - 1
     Bs = [1 << b for b in range(4, logn - 4 + 1)]
     gB = [B for B in Bs if not _stream(n, B)]
@@ -366,7 +382,7 @@ def roofline(per_signal, traces, n, stages=3):
             ach = units / t / 1e9
             frac = ach / (pair_peak / 1e9) if bound == "alu" else ach / hbm
             rows.setdefault(nm, []).append((t, ach, frac, units, bound))
-    out = {}
+    out = {"_alu_peak": {"pairs_per_s": pair_peak, "source": pair_src}}
     for nm, lst in rows.items():
         t = float(np.mean([r[0] for r in lst]))
         ach = float(np.mean([r[1] for r in lst]))
@@ -374,17 +390,124 @@ def roofline(per_signal, traces, n, stages=3):
                    "unit": "Gpair/s" if lst[0][4] == "alu" else "GB/s",
                    "frac": float(np.mean([r[2] for r in lst])), "launches_per_step": len(lst)}
     # dominant single-kernel phase: largest total time per step
-    dom = max(out, key=lambda nm: out[nm]["ms_per_launch"] * out[nm]["launches_per_step"])
+    dom = max((nm for nm in out if not nm.startswith("_")),
+              key=lambda nm: out[nm]["ms_per_launch"] * out[nm]["launches_per_step"])
     d = out[dom]
     peak = pair_peak / 1e9 if d["bound"] == "alu" else hbm
     roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": peak,
             "unit": d["unit"], "frac": d["achieved"] / peak,
             "traffic": NCU_TRAFFIC[dom][0] if dom in NCU_TRAFFIC else None,
             "traffic_launch": NCU_TRAFFIC[dom][1] if dom in NCU_TRAFFIC else None,
-            "peak_source": ("derived: 32 SFU ops/clk/SM x 152 SMs x 2070 MHz / 2 SFU ops per "
-                            "sample-hash pair") if d["bound"] == "alu" else f"{src} hbm_gbs",
+            "peak_source": pair_src if d["bound"] == "alu" else f"{src} hbm_gbs",
             "ms_per_launch": d["ms_per_launch"]}
     return roof, out
+
+
+def accuracy(sig, loc, val, k_star):
+    """Eq. (15) against the generator's noise-free spectrum, k*/k, and how many kept
+    coordinates lie outside the true support (the vote rule's noise floor)."""
+    from synth import l1_error_per_coefficient
+
+    on = np.isin(loc, sig.support)
+    return {"l1_err_per_coef": float(l1_error_per_coefficient(sig, loc, val.astype(complex))),
+            "k_star_over_k": k_star / len(sig.support), "kept": int(len(loc)),
+            "kept_outside_support": int((~on).sum()),
+            "support_found": float(on.sum() / len(sig.support))}
+
+
+IMG_N, IMG_K, IMG_SNR, IMG_SEED = 4096, 1000, 30.0, 5
+IMG_WORKLOAD = ("2D-SFFT, 4096x4096 complex64, k=1000 unknown to the solver, magnitudes "
+                "log-uniform in [0.1,1], 30 dB complex Gaussian noise; one step = 1 transform")
+
+
+def cufft2_reference_ms(N, dev, reps=20):
+    """Dense 2D cuFFT C2C complex64 of N x N (torch.fft.fft2), median of event timings with
+    L2 flushed in between -- a comparison only."""
+    import torch
+
+    x = torch.randn(N, N, dtype=torch.complex64, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        torch.fft.fft2(x)
+    ts = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(reps):
+        flush.zero_()
+        e0.record()
+        torch.fft.fft2(x)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(statistics.median(ts))
+
+
+def image_summary(dev, steps, warmup):
+    """The 2D workload (4096 x 4096, k = 1000, 30 dB) on the plain per-image path: device
+    time per transform (CUDA events, L2 flushed between transforms; the 128 MiB input is
+    larger than L2 anyway), the dense 2D cuFFT of the same size, and the accuracy."""
+    import torch
+
+    import paper_1908_02461_gb300 as A
+    from synth import sparse_signal_2d
+
+    sig = sparse_signal_2d(IMG_N, IMG_K, IMG_SEED, snr_db=IMG_SNR, mag=("loguniform", 0.1, 1.0))
+    x = torch.from_numpy(sig.x).to(dev)
+    plan = A.Plan((IMG_N, IMG_N), seed=SEED)
+    o = dict(loc=torch.empty(CAPACITY, dtype=torch.int64, device=dev),
+             val=torch.empty(CAPACITY, dtype=torch.complex64, device=dev),
+             count=torch.zeros(1, dtype=torch.int64, device=dev),
+             k=torch.zeros(1, dtype=torch.int64, device=dev),
+             status=torch.zeros(1, dtype=torch.int32, device=dev))
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, warmup)):
+        plan.exec_async(x, o["loc"], o["val"], o["count"], o["k"], o["status"], stream.cuda_stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0.record(stream)
+        plan.exec_async(x, o["loc"], o["val"], o["count"], o["k"], o["status"], stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    count, kstar, status = int(o["count"].item()), int(o["k"].item()), int(o["status"].item())
+    m = min(count, CAPACITY)
+    loc = o["loc"][:m].cpu().numpy()
+    val = o["val"][:m].cpu().numpy()
+    B, _ = plan.last_trace()[-1]
+    plan.close()
+    cu = cufft2_reference_ms(IMG_N, dev)
+    t = float(np.mean(ms))
+    return {"workload": IMG_WORKLOAD, "transforms_per_s": 1e3 / t, "ms_per_transform": t,
+            "gsamples_per_s": IMG_N * IMG_N / (t * 1e-3) / 1e9,
+            "cufft2d_c2c_ms": cu, "cufft2d_transforms_per_s": 1e3 / cu, "vs_cufft2d": cu / t,
+            "status": status, "k_star": kstar, "B_star_per_axis": B,
+            "accuracy": accuracy(sig, loc, val, kstar), "steps": steps}
+
+
+def image_workload(args):
+    """--workload image4096: the 2D line on its own (one JSON line)."""
+    import torch
+
+    import paper_1908_02461_gb300 as A
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    A.build()
+    dev = torch.device("cuda", local)
+    steps = max(5, min(args.steps, 200))
+    with ClockSampler(local) as clk:
+        r = image_summary(dev, steps, args.warmup)
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": "transforms/s", "value": r["transforms_per_s"], "unit": "transforms/s",
+        "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": r["ms_per_transform"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": dict(r, l2="flushed between steps (256 MiB write)"),
+        "clocks": clk.summary()}))
 
 
 def ncu_case(k):
@@ -630,7 +753,10 @@ def main():
                          "(-1: half the SMs, a quarter for mixed512; 0: all)")
     ap.add_argument("--no-graph", action="store_true",
                     help="time per-signal execs on streams instead of one graph launch per step")
-    ap.add_argument("--workload", default="headline", choices=["headline", "mixed512", "grad64"],
+    ap.add_argument("--no-image", action="store_true",
+                    help="skip the 2D (4096x4096) summary in the headline line")
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "mixed512", "grad64", "image4096"],
                     help="mixed512: the 512-signal mixed-size batch; grad64: 64 transforms with "
                          "the gradient of a loss at their supports (instead of the headline)")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="K",
@@ -647,6 +773,9 @@ def main():
         return
     if args.workload == "grad64":
         grad_workload(args)
+        return
+    if args.workload == "image4096":
+        image_workload(args)
         return
 
     import torch
@@ -792,7 +921,14 @@ def main():
         if not tr:   # fixed-k mode: no trials, B* from the plan's last result
             tr = [(A._lib.atsfft_last_result(p.handle)[1], None)]
         traces[k] = tr
-    roof, phase_rooflines = roofline(per_signal, traces, n, stages=args.tune_stages)
+    pair_peak, pair_src = mufu_pair_peak(stream.cuda_stream)
+    roof, phase_rooflines = roofline(per_signal, traces, n, stages=args.tune_stages,
+                                     pair_peak=pair_peak, pair_src=pair_src)
+    acc = {}
+    for k, sg, o in zip(KS, sigs, outs):
+        m = min(int(o["count"].item()), CAPACITY)
+        acc[str(k)] = accuracy(sg, o["loc"][:m].cpu().numpy(), o["val"][:m].cpu().numpy(),
+                               int(o["k"].item()))
 
     # ---- end to end through the C ABI with host buffers -----------------------------
     host_out = [dict(loc=torch.empty(CAPACITY, dtype=torch.int64).pin_memory(),
@@ -829,6 +965,13 @@ def main():
     cufft_ms = cufft_reference_ms(n, dev) if rank == 0 else None
     h2d = sum(h.numel() * 8 for h in host)
     d2h = len(sigs) * (CAPACITY * 8 + CAPACITY * 8 + 8 + 8 + 4)
+
+    image = None
+    if rank == 0 and not args.no_image:
+        try:
+            image = image_summary(dev, 20, 3)
+        except Exception as exc:   # the 1D line stands on its own
+            image = {"unavailable": f"{type(exc).__name__}: {exc}"}
 
     cpu = cpu_all = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -874,6 +1017,9 @@ def main():
                             f"per-signal execs on {nstreams} concurrent streams"),
                    "cufft_c2c_ms": cufft_ms,
                    "cufft_c2c_transforms_per_s": (1e3 / cufft_ms) if cufft_ms else None,
+                   "vs_cufft": (value * cufft_ms / 1e3) if cufft_ms else None,
+                   "plain_vs_cufft": (plain_value * cufft_ms / 1e3) if cufft_ms else None,
+                   "accuracy": acc,
                    "bin_pass_ms": bin_ms, "tune_stage2_ms": tune_stage2, "wall_s": wall},
         "e2e": {"value": ntrans / (e2e_total / 1e3), "unit": "transforms/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -882,6 +1028,7 @@ def main():
         "phase_rooflines": phase_rooflines,
         "cpu_baseline": cpu,
         "cpu_baseline_all_cores": cpu_all,
+        "image4096": image,
         "clocks": clocks,
     }
     print(json.dumps(line))

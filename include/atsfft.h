@@ -187,6 +187,15 @@ atsfft_status atsfft_phase_times(atsfft_plan_t plan, float *h_ms, int max_phases
 atsfft_status atsfft_tail_stamps(atsfft_plan_t plan, uint64_t *h_ns, int max_stamps,
                                  int *h_nstamps, void *stream);
 
+/* The measured rate of the GPU's special-function unit on the two operations every
+ * window tap of the residue-stream binning costs (an exp2 and a reciprocal: the
+ * Gaussian envelope and the box car's 1/t of Section II-A-2): a kernel of independent
+ * ex2.approx / rcp.approx chains on every SM (iters iterations of 8 chains per thread,
+ * 2048 threads per SM, in [1, 2^24]), timed with CUDA events on `stream`.  Writes the
+ * operations per second to *h_ops_per_s (half of it is the sample-hash pairs per
+ * second).  Synchronises `stream`.  A diagnostic: the paper has no counterpart. */
+atsfft_status atsfft_mufu_probe(int64_t iters, double *h_ops_per_s, void *stream);
+
 /* ---- gradients at a fixed recovered support (1D) ---------------------------------- */
 
 /* atsfft_exec (or atsfft_exec_2d) that also writes, for each output position p <

@@ -33,6 +33,7 @@ from ._lib import (  # noqa: F401
     atsfft_hash_spectrum,
     atsfft_last_result,
     atsfft_last_trace,
+    atsfft_mufu_probe,
     atsfft_params,
     atsfft_phase_times,
     atsfft_plan,

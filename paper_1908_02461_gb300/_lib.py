@@ -43,7 +43,8 @@ EXPORTED = ["atsfft_default_params", "atsfft_plan", "atsfft_exec", "atsfft_exec_
             "atsfft_batch_create", "atsfft_batch_create_io", "atsfft_batch_launch",
             "atsfft_batch_kernels",
             "atsfft_batch_destroy", "atsfft_plan_clone", "atsfft_exec_sel",
-            "atsfft_estimate_apply", "atsfft_estimate_adjoint", "atsfft_last_result"]
+            "atsfft_estimate_apply", "atsfft_estimate_adjoint", "atsfft_last_result",
+            "atsfft_mufu_probe"]
 
 PHASES = ["tune1_bin", "tune1_fft", "tune1_tail", "tune2_bin", "tune2_fft", "tune2_tail",
           "tune3_bin", "tune3_fft", "tune3_tail", "le_bin_stream", "le_bin_gather", "le_fft",
@@ -110,6 +111,8 @@ def load(path: str | None = None):
     L.atsfft_batch_kernels.restype = i32
     L.atsfft_batch_destroy.argtypes = [vp]
     L.atsfft_batch_destroy.restype = i32
+    L.atsfft_mufu_probe.argtypes = [i64, P(C.c_double), vp]
+    L.atsfft_mufu_probe.restype = i32
     if path is None:
         _lib = L
     return L
@@ -270,3 +273,10 @@ def atsfft_last_result(plan, stream=None):
     B, k = C.c_int64(), C.c_int64()
     st = load().atsfft_last_result(plan, C.byref(B), C.byref(k), _ptr(stream))
     return st, B.value, k.value
+
+
+def atsfft_mufu_probe(iters, stream=None):
+    """Returns (status, measured exp2 + reciprocal operations per second)."""
+    r = C.c_double()
+    st = load().atsfft_mufu_probe(int(iters), C.byref(r), _ptr(stream))
+    return st, r.value

@@ -3,9 +3,11 @@ level): times candidate parameter sets on synthetic probe signals with a known s
 spectrum and keeps the fastest whose accuracy meets a target.
 
 The candidates vary what trades speed for robustness -- location and estimation loop
-counts, the window tolerance (which sets the window support) and the window's
-transition width alpha -- and the launch knobs that do not change results (tuning
-stages, cooperative blocks per SM).  Accuracy is measured with Eq. (15) (the L1 error
+counts, the window tolerance and the window's transition width alpha (together they set
+the window support, Eqs. (8)-(9)), the range of bucket counts the tuning walks (Eq. (14):
+a smallest B sized to the smallest expected k skips trials that cannot hold it, a largest
+B sized to the largest k skips the widest windows) -- and the launch knobs that do not
+change results (tuning stages).  Accuracy is measured with Eq. (15) (the L1 error
 per true coefficient over the whole grid) and the detected k* against the true k; the
 transform itself always runs on the GPU through the C ABI.
 """
@@ -21,9 +23,24 @@ import numpy as np
 DEFAULT_GRID = {
     "loops": [(7, 7), (5, 5)],
     "filter_tol": [1e-6, 1e-5],
-    "filter_alpha": [0.5],
+    "filter_alpha": [0.5, 1.0],
+    "b_range": ["default", "k_range"],
     "tune_stages": [3, 2],
 }
+
+
+def b_range_for(n: int, k_range, which: str):
+    """(b_min_log2, b_max_log2) of a candidate: "default" keeps the plan's range
+    ([4, log2 n - 4]); "k_range" starts at the smallest B >= 2 k_lo (the k-hint rule of
+    Algorithm 2's initial B) and ends at the smallest B >= 128 k_hi (the walk stops near
+    64 k: one doubling of room), both clamped to the default range."""
+    logn = n.bit_length() - 1
+    lo_d, hi_d = 4, logn - 4
+    if which == "default":
+        return 0, 0
+    lo = max(lo_d, math.ceil(math.log2(2 * k_range[0])))
+    hi = min(hi_d, max(lo + 1, math.ceil(math.log2(128 * k_range[1]))))
+    return (lo if lo != lo_d else 0), (hi if hi != hi_d else 0)
 
 
 @dataclass
@@ -76,10 +93,17 @@ def autotune(n: int, k_range=(10, 1000), snr_db: float | None = 40.0, error_targ
     xs = [torch.from_numpy(x).cuda() for x, _, _ in sigs]
     table = []
     best = None
-    for (ll, le), tol, alpha, stages in itertools.product(grid["loops"], grid["filter_tol"],
-                                                           grid["filter_alpha"], grid["tune_stages"]):
+    seen = set()
+    for (ll, le), tol, alpha, br, stages in itertools.product(
+            grid["loops"], grid["filter_tol"], grid["filter_alpha"],
+            grid.get("b_range", ["default"]), grid["tune_stages"]):
+        b_lo, b_hi = b_range_for(n, k_range, br)
         over = dict(loops_loc=ll, loops_est=le, filter_tol=tol, filter_alpha=alpha,
-                    tune_stages=stages)
+                    b_min_log2=b_lo, b_max_log2=b_hi, tune_stages=stages)
+        key = tuple(sorted(over.items()))
+        if key in seen:   # a k-derived range equal to the default one
+            continue
+        seen.add(key)
         plan = Plan((n,), params=params(**over), seed=seed)
         errs, ratios = [], []
         for (x, loc, coef), xd, k in zip(sigs, xs, ks):

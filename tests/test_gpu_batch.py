@@ -118,16 +118,22 @@ def test_clone_gives_identical_transforms(A):
 
 
 def test_autotune_meets_the_error_target(A):
-    from paper_1908_02461_gb300.autotune import autotune
+    """The candidate grid spans the loop counts, the window's alpha and the tuning's B
+    range (Eqs. (8), (9), (14)); the choice is the fastest candidate that meets the Eq. (15)
+    error target with k*/k in [0.9, 1.1]."""
+    from paper_1908_02461_gb300.autotune import autotune, b_range_for
 
-    grid = {"loops": [(7, 7), (5, 5)], "filter_tol": [1e-6], "filter_alpha": [0.5],
-            "tune_stages": [3]}
-    res = autotune(1 << 14, k_range=(8, 64), snr_db=40.0, error_target=1e-2, probes=2, reps=1,
-                   grid=grid)
-    assert len(res.table) == 2
+    n, kr = 1 << 16, (20, 64)
+    assert b_range_for(n, kr, "k_range") == (6, 0)   # B from 2^6 >= 2 k_lo; top as default
+    grid = {"loops": [(7, 7), (5, 5)], "filter_tol": [1e-6], "filter_alpha": [0.5, 1.0],
+            "b_range": ["default", "k_range"], "tune_stages": [3]}
+    res = autotune(n, k_range=kr, snr_db=40.0, error_target=1e-2, probes=2, reps=1, grid=grid)
+    assert len(res.table) == 8
+    assert {r[0]["filter_alpha"] for r in res.table} == {0.5, 1.0}
+    assert {r[0]["b_min_log2"] for r in res.table} == {0, 6}
     assert res.error <= 1e-2 and 0.9 <= res.k_ratio <= 1.1
     assert res.ms_per_transform == min(r[1] for r in res.table if r[4])
-    p = A.Plan((1 << 14,), params=A.params(**res.params))
+    p = A.Plan((n,), params=A.params(**res.params))
     p.close()
 
 
