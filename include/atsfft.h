@@ -62,9 +62,9 @@ typedef struct {
     double tie_eta;             /* relative band inside which energies tie (1e-2)        */
     int b_min_log2, b_max_log2; /* tuning range of log2 B (per axis in 2D); 0 = default:
                                    1D [4, log2 n - 4], 2D [3, log2 N - 2]                */
-    int coop_blocks_per_sm;     /* blocks per SM of the two cooperative tail kernels
-                                   (0 = 2); 1 lets several plans' tails run at once on
-                                   different streams, all co-resident                   */
+    int coop_blocks_per_sm;     /* accepted in [0, 8] and without effect: the tail kernels
+                                   no longer run as a cooperative grid (kept so that the
+                                   struct keeps its layout)                              */
     int tune_stages;            /* 1D tuning batches: 3 (default) evaluates the trials with
                                    gather-form windows first, then the residue-stream
                                    trials but the largest, then the largest, each batch
@@ -83,12 +83,8 @@ typedef struct {
                                    the estimation stage in FP64 (Eq. (11) values to
                                    ~1e-12 of an FP64 evaluation).  Slow: FP64 runs at
                                    1/64 of the FP32 rate on GB300                         */
-    int coop_sms;               /* SMs the two cooperative tail kernels spread over
-                                   (coop_blocks_per_sm CTAs on each); 0 (default) = all.
-                                   Transforms that run concurrently (a batch graph,
-                                   several streams) go faster with a fraction: a tail
-                                   mostly waits on its grid barriers, and the SMs it does
-                                   not hold stay free for the other transforms' kernels  */
+    int coop_sms;               /* accepted (>= 0) and without effect, like
+                                   coop_blocks_per_sm                                    */
 } atsfft_params;
 
 /* Fills *p with the defaults listed above. */
@@ -182,8 +178,10 @@ atsfft_status atsfft_phase_times(atsfft_plan_t plan, float *h_ms, int max_phases
                                  int64_t *h_launches, void *stream);
 
 /* Diagnostics after an exec: device time stamps (ns, %globaltimer) taken at the start
- * of the two cooperative tail kernels, at every grid barrier inside them and when their
- * last CTA finishes, in the order they happened (at most 32).  Synchronises `stream`. */
+ * of every tail kernel (the tuning statistics of each stage, the location maxima, votes
+ * and outputs) and when its last block finishes (for the tuning tail: when the
+ * controller has walked), in the order they happened (at most 32).  Synchronises
+ * `stream`. */
 atsfft_status atsfft_tail_stamps(atsfft_plan_t plan, uint64_t *h_ns, int max_stamps,
                                  int *h_nstamps, void *stream);
 

@@ -185,7 +185,7 @@ extern "C" atsfft_status atsfft_tail_stamps(atsfft_plan_t P, uint64_t *h_ns, int
     if (!P || !h_nstamps || max_stamps < 0 || (max_stamps > 0 && !h_ns)) return ATSFFT_E_INVALID_ARG;
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_status(e);
-    GridBarrier gb;
+    TailStamps gb;
     e = cudaMemcpy(&gb, &P->d_state->bar, sizeof(gb), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_status(e);
     const int n = gb.nstamp < 32 ? (int)gb.nstamp : 32;

@@ -24,6 +24,7 @@ constexpr int kTwEntries = 2 * kSmallFFT;   // coarse exp(-2 pi i j / 4096), fin
 constexpr int kMaxTrialsTrace = 64;
 constexpr int kHistBins = 4096;      // radix-select histogram bins (12-bit digits)
 constexpr int kKeptCap = 8192;       // kept coordinates ordered by rank (beyond: bitmap compaction)
+constexpr int kChunkWords = 1024;    // coordinate-bitmap words per compaction chunk
 constexpr int kAdjRotMax = 8192;     // adjoint: R_u table entries kept in shared memory
 constexpr int kPersistCtas = 4;      // persistent CTAs per SM
 constexpr int kPhases = 13;          // profiled phases of one exec (see atsfft.h)
@@ -89,20 +90,21 @@ struct HashStats {
     uint32_t pad[6];
 };
 
-// Grid-wide barrier of the cooperative kernels (tail.cu).
-struct GridBarrier {
-    unsigned count;
-    unsigned gen;
-    int err;
+// Diagnostic time stamps of the tail kernels (tail.cu).
+struct TailStamps {
     unsigned nstamp;
-    unsigned done;                  // CTAs that finished the kernel (end stamp)
-    unsigned pad;
-    unsigned long long stamp[32];   // %globaltimer at kernel starts, barrier releases and ends
+    unsigned pad[3];
+    unsigned long long stamp[32];   // %globaltimer at tail kernel starts and phase ends
 };
 
 // Device-resident state of one exec.
 struct ExecState {
-    GridBarrier bar;
+    TailStamps bar;
+    // completion counters of the tail kernels (a block that finishes a task counts it;
+    // the block that counts the last task of a hash, or of the whole launch, goes on with
+    // the step that needs all of them): per statistics slot, and per launch
+    uint32_t done[kMaxLogB + kMaxLoops];
+    uint32_t done_all[8];
     int32_t b_star;        // log2 B* (per axis)
     int32_t status;
     int64_t k_star;
@@ -168,7 +170,6 @@ struct atsfft_plan_s {
     float *d_energy;       // energies (tuning region then location region)
     int64_t e_loc_off;
     atsfft::HashStats *d_stats;   // [kMaxLogB tuning slots][L_loc location slots]
-    uint32_t *d_hist;             // [slots][kHistBins]
     int32_t *d_lmax;              // local-maximum lists [L_loc][lmax_cap]
     float *d_lmax_e;              // their energies, same layout
     int32_t *d_sel;               // selected buckets    [L_loc][lmax_cap]
@@ -179,7 +180,8 @@ struct atsfft_plan_s {
     int64_t kept_cap;
     uint32_t *d_coordbits;        // one bit per coordinate, zero between transforms
     int64_t coord_words;
-    uint32_t *d_blk;              // compaction per-block counts / offsets
+    uint32_t *d_blk;              // kept coordinates per chunk of kChunkWords coordinate words
+    int64_t nchunks;
     atsfft::ExecState *d_state;
     atsfft::Job *d_tjob;
     atsfft::StatJob *d_tstat;     // tuning stat jobs (built at plan time)

@@ -4,11 +4,33 @@
 
 namespace atsfft {
 
+// Zeroes the statistics slots, the exec state and the compaction chunk counts (one
+// launch instead of one memset node each).
+__global__ void k_reset(uint32_t *stats, int64_t stats_words, uint32_t *state, int64_t state_words,
+                        uint32_t *chunks, int64_t nchunks)
+{
+    const int64_t total = stats_words + state_words + nchunks;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < stats_words)
+            stats[i] = 0u;
+        else if (i < stats_words + state_words)
+            state[i - stats_words] = 0u;
+        else
+            chunks[i - stats_words - state_words] = 0u;
+    }
+}
+
 void launch_reset(const atsfft_plan_s *P, cudaStream_t s)
 {
-    cudaMemsetAsync(P->d_stats, 0, sizeof(HashStats) * (kMaxLogB + kMaxLoops), s);
-    cudaMemsetAsync(P->d_state, 0, sizeof(ExecState), s);
-    cudaMemsetAsync(P->d_hist, 0, sizeof(uint32_t) * kHistBins * (kMaxLogB + kMaxLoops), s);
+    static_assert(sizeof(HashStats) % 4 == 0 && sizeof(ExecState) % 4 == 0, "word-sized state");
+    const int64_t sw = (int64_t)(sizeof(HashStats) * (kMaxLogB + kMaxLoops) / 4);
+    const int64_t ew = (int64_t)(sizeof(ExecState) / 4);
+    const int64_t total = sw + ew + P->nchunks;
+    const int blocks = (int)((total + 255) / 256 < 64 ? (total + 255) / 256 : 64);
+    k_reset<<<blocks, 256, 0, s>>>((uint32_t *)P->d_stats, sw, (uint32_t *)P->d_state, ew, P->d_blk,
+                                   P->nchunks);
+    count_launch(P);
 }
 
 // Inspection: Zhat[c] = P[sigma' c] exp(2 pi i c sigma' tau / B) in bucket order.

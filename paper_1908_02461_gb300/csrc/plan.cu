@@ -285,7 +285,7 @@ static bool params_ok(const atsfft_params *p)
 static void plan_free(atsfft_plan_s *P)
 {
     void *ptrs[] = {P->d_tune, P->d_le, P->d_win, P->d_resp, P->d_rgain, P->d_phase, P->d_tw, P->d_part, P->d_tz,
-                    P->d_z, P->d_fft_tmp, P->d_energy, P->d_stats, P->d_hist, P->d_lmax, P->d_lmax_e,
+                    P->d_z, P->d_fft_tmp, P->d_energy, P->d_stats, P->d_lmax, P->d_lmax_e,
                     P->d_sel, P->d_bucketbits, P->d_kept, P->d_coordbits, P->d_blk, P->d_x32, P->d_f64a,
                     P->d_f64b, P->d_tw64, P->d_state, P->d_tjob, P->d_tstat,
                     P->d_lstat};
@@ -473,15 +473,16 @@ static atsfft_status plan_create(atsfft_plan_t *out, int ndim, const int64_t *sh
     A((void **)&P->d_fft_tmp, sizeof(float2) * tmp_elems);
     A((void **)&P->d_energy, sizeof(float) * (tz_total + P->L_loc * nb_max));
     A((void **)&P->d_stats, sizeof(HashStats) * (kMaxLogB + kMaxLoops));
-    A((void **)&P->d_hist, sizeof(uint32_t) * kHistBins * (kMaxLogB + kMaxLoops));
     A((void **)&P->d_lmax, sizeof(int32_t) * P->L_loc * P->lmax_cap);
     A((void **)&P->d_lmax_e, sizeof(float) * P->L_loc * P->lmax_cap);
     A((void **)&P->d_sel, sizeof(int32_t) * P->L_loc * P->lmax_cap);
     A((void **)&P->d_bucketbits, sizeof(uint32_t) * (size_t)P->L_loc * (size_t)P->bucket_words);
     A((void **)&P->d_kept, sizeof(uint32_t) * (size_t)P->kept_cap);
     A((void **)&P->d_coordbits, sizeof(uint32_t) * (size_t)P->coord_words);
-    // per-block counts of the compaction (cooperative grid: at most a few blocks per SM)
-    A((void **)&P->d_blk, sizeof(uint32_t) * (size_t)P->num_sms * 32);
+    // kept coordinates per chunk of the coordinate bitmap (the ordered compaction beyond
+    // kKeptCap kept coordinates), zeroed at the start of every exec
+    P->nchunks = (P->coord_words + kChunkWords - 1) / kChunkWords;
+    A((void **)&P->d_blk, sizeof(uint32_t) * (size_t)P->nchunks);
     if (p.precision == 1) {
         A((void **)&P->d_x32, sizeof(float2) * (size_t)n);
         A((void **)&P->d_f64a, sizeof(double2) * (size_t)P->L_est * (size_t)nb_max);

@@ -1,37 +1,37 @@
-// tail.cu -- everything after the bucket FFTs, as two cooperative (persistent) kernels
-// whose phases are separated by a grid barrier:
+// tail.cu -- everything after the bucket FFTs, with no grid-wide barrier: every step
+// that needs all the results of the previous one is either a new kernel (chained with
+// programmatic dependent launch, so its blocks are scheduled while the previous kernel
+// finishes) or is run by the block that completes the last unit of work it depends on
+// (a completion counter per hash and per launch: the block whose count is the last one
+// goes on, nobody waits).
 //
-//   k_tune_tail : threshold and local-maximum counts of the trials of one tuning stage
-//                 (Section III-A; the energies and their maxima come from the bucket
-//                 FFTs), then the controller walk over Eqs. (12)/(14) (Algorithm 2) by one
-//                 thread, which fixes B*, k* and the jobs at B* (or leaves the walk to the
-//                 next stage).
-//   k_loc_tail  : the same statistics for the location hashes at B* (with the maxima
-//                 listed), the top-num cutoff (Algorithm 1 "find num largest"), votes
-//                 (reverse hash), the ordered compaction of coordinates with votes >=
-//                 ceil(L_loc/2) (Section II-B), the estimates of Eq. (11) with their
-//                 componentwise median, and the caller's status words.
+//   k_tune_tail  : threshold and local-maximum counts of the trials of one tuning stage
+//                  (Section III-A; the energies and their maxima come from the bucket
+//                  FFTs); the last block of a trial settles its median where it can matter;
+//                  the last block of the launch walks the controller over Eqs. (12)/(14)
+//                  (Algorithm 2), which fixes B*, k* and the jobs at B* (or leaves the walk
+//                  to the next stage).
+//   k_loc_maxima : the same statistics for the location hashes at B*, with the maxima
+//                  listed; the last block of each hash makes its top-num cutoff (Algorithm
+//                  1 "find num largest") and its bitmap of selected buckets.
+//   k_loc_votes  : votes (reverse hash): the preimages of the selected buckets that lie in
+//                  >= ceil(L_loc/2) selected buckets are kept (Section II-B).
+//   k_loc_finish : the kept coordinates in ascending order, the estimates of Eq. (11) with
+//                  their componentwise median, and the caller's status words.
 //
 // Threshold T = max(thr_rel * maxE, thr_med * medianE), median = element floor(nb/2) of
 // the ascending energies.  With #{E > X'} <= nb - floor(nb/2) - 1 for
 // X' = (thr_rel/thr_med) maxE (1 - 2^-20) the median is <= X' and T = thr_rel * maxE
 // exactly, so the local maxima are found with that T at once; only when the count says
-// the median could matter is it found exactly (three-digit radix select on the energy
-// bit patterns) and the maxima recounted -- in the tuning tail, for trials of at most one
-// statistics task, before the first barrier.
-//
-// The grid barrier spins on a generation word with a bounded number of polls; when the
-// bound runs out the block records ATSFFT_E_CUDA in the exec state and every block
-// returns at its next barrier (cooperative launch makes all blocks co-resident, so a
-// timeout means the device misbehaved, not a lost block).
+// the median could matter is it found exactly (radix select on the energy bit patterns)
+// and the maxima recounted (tuning) or the listed ones above the raised threshold kept
+// (location: dominance does not depend on T).
 #include <math.h>
 #include <string.h>
 
 #include "devmath.cuh"
 
 namespace atsfft {
-
-constexpr uint32_t kBarrierPolls = 1u << 24;   // ~1 s at 64 ns per poll
 
 __device__ __forceinline__ unsigned long long global_ns()
 {
@@ -40,60 +40,49 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Diagnostic time stamp (kernel start or barrier release), kept in the exec state.
-__device__ __forceinline__ void stamp(GridBarrier *gb)
+// Diagnostic time stamp (kernel start or end of a phase), kept in the exec state.
+__device__ __forceinline__ void stamp(TailStamps *ts)
 {
-    const unsigned i = atomicAdd(&gb->nstamp, 1u);
-    if (i < 32) gb->stamp[i] = global_ns();
+    const unsigned i = atomicAdd(&ts->nstamp, 1u);
+    if (i < 32) ts->stamp[i] = global_ns();
 }
 
-// Diagnostic end stamp: the last CTA to finish records the time (no waiting).
-__device__ __forceinline__ void end_stamp(GridBarrier *gb)
+// Programmatic dependent launch: wait until the previous kernel of the stream has
+// completed and its writes are visible (returns at once for a kernel launched without
+// the dependency); let the next kernel's blocks be scheduled.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next()
 {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Whole block, after it finished one unit of a group of `units`: counts it, and returns
+// true (in every thread) in the block that counted the group's last unit.  The writes
+// and atomics of every counted unit are then visible to that block: the block barrier
+// orders every thread's writes before thread 0's release fence and count, and in the
+// last block thread 0's acquire fence after the count comes before the barrier that
+// releases its threads, which read the others' results through L2 (__ldcg).
+__device__ bool finished_last(uint32_t *counter, uint32_t units)
+{
+    __shared__ int last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(&gb->done, 1u) == gridDim.x - 1) {
-            stamp(gb);
-            atomicExch(&gb->done, 0u);
-        }
+        const bool l = atomicAdd(counter, 1u) == units - 1;
+        if (l) __threadfence();
+        last = l;
     }
+    __syncthreads();
+    return last != 0;
 }
 
-__device__ bool grid_sync(GridBarrier *gb, int *status)
+// Diagnostic end stamp of a kernel: the block that finishes last records the time (no
+// ordering is needed, nothing reads results through it).
+__device__ __forceinline__ void end_stamp(ExecState *state, int which)
 {
-    __shared__ int ok;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        volatile unsigned *vgen = &gb->gen;
-        volatile int *verr = &gb->err;
-        const unsigned g = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&gb->count, 1u);
-        if (arrived == gridDim.x - 1) {
-            stamp(gb);
-            atomicExch(&gb->count, 0u);
-            __threadfence();
-            atomicAdd(&gb->gen, 1u);
-        } else {
-            uint32_t polls = 0;
-            while (*vgen == g && !*verr) {
-                if (++polls > kBarrierPolls) {
-                    atomicExch(&gb->err, 1);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        if (*verr) {
-            ok = 0;
-            *status = ATSFFT_E_CUDA;
-        }
-    }
-    __syncthreads();
-    return ok;
+    if (threadIdx.x == 0 && atomicAdd(&state->done_all[which], 1u) == gridDim.x - 1)
+        stamp(&state->bar);
 }
 
 __device__ __forceinline__ int64_t nb_of(int ndim, int logB)
@@ -137,7 +126,6 @@ struct StatsParams {
     float thr_rel, thr_med, up, ratio;   // up = 1 + eta; ratio = X' / maxE
     int use_median;
     HashStats *stats;
-    uint32_t *hist;
     int32_t *lists;
     float *list_e;         // the listed maxima's energies (same layout)
     int64_t cap;
@@ -157,13 +145,6 @@ __device__ __forceinline__ void hist_add(uint32_t *hist, uint32_t bin)
     const unsigned am = __activemask();
     const unsigned peers = __match_any_sync(am, bin);
     if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
-}
-
-// digit 0: bits [20, 32), digit 1: [8, 20), digit 2: [0, 8)
-__device__ __forceinline__ void digit_range(int digit, int &lo, int &width)
-{
-    lo = digit == 0 ? 20 : (digit == 1 ? 8 : 0);
-    width = digit == 2 ? 8 : 12;
 }
 
 // Whole block (blockDim.x = 256): exclusive prefix sum of one value per thread;
@@ -438,170 +419,58 @@ __device__ __noinline__ void localmax_whole_hash(const JobView &J, const StatsPa
     localmax_task(J, S, T, 0, nb, INFINITY);
 }
 
-// Threshold and local maxima of njobs hashes whose energies and maxima the bucket FFTs
-// wrote.  Returns false if a barrier failed.
-__device__ bool stats_phases(const StatJob *jobs, int njobs, const StatsParams &S,
-                             GridBarrier *gb, int *status, bool settle_small)
+// Exact median (element floor(nb/2) of the ascending energies, as bits) of nb energies
+// in global memory by one block: three radix digits (11, 11, 10 bits) over their bit
+// patterns, each pass streaming the energies.  The rare path (the median can only matter
+// when more than half of the buckets exceed X'); nb <= kSmallMedian goes through
+// block_median in shared memory.
+__device__ __noinline__ uint32_t block_median_global(const float *E, int64_t nb)
 {
-    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
-    // the jobs, loaded in parallel, and the work split into tasks of kTask buckets over
-    // all jobs (prefix table in shared memory)
-    __shared__ JobView jv[kMaxLoops + kMaxLogB];
-    __shared__ int64_t tstart[kMaxLoops + kMaxLogB + 1];
-    __shared__ uint8_t med[kMaxLoops + kMaxLogB];
-    if (threadIdx.x < njobs) {
-        const StatJob J = jobs[threadIdx.x];
-        const uint32_t mask = (1u << J.logB) - 1;
-        JobView v;
-        v.E = J.energy;
-        v.st = S.stats + J.slot;
-        v.logB = J.logB;
-        v.list = J.list;
-        v.active = J.active;
-        v.pad = 0;
-        v.s1 = (uint32_t)J.hash->sigma[0] & mask;
-        v.p1 = (uint32_t)J.hash->sinv[0] & mask;
-        v.s2 = (uint32_t)J.hash->sigma[1] & mask;
-        v.p2 = (uint32_t)J.hash->sinv[1] & mask;
-        jv[threadIdx.x] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int64_t acc = 0;
-        for (int jb = 0; jb < njobs; jb++) {
-            tstart[jb] = acc;
-            if (jv[jb].active) acc += (nb_of(S.ndim, jv[jb].logB) + kTask - 1) / kTask;
-        }
-        tstart[njobs] = acc;
-    }
-    __syncthreads();
-    const int64_t ntasks = tstart[njobs];
-    // (the energies and their maximum come from the bucket FFTs' final pass)
-    // B: local maxima with T = thr_rel * maxE, and the count deciding if the median matters
-    for (int64_t task = blockIdx.x; task < ntasks; task += gridDim.x) {
-        int jb = 0;
-        while (task >= tstart[jb + 1]) jb++;
-        const JobView &J = jv[jb];
-        const int64_t nb = nb_of(S.ndim, J.logB);
-        const int64_t e0 = (task - tstart[jb]) * kTask;
-        const int64_t e1 = min(e0 + kTask, nb);
-        const float M = __uint_as_float(J.st->max_bits);
-        const float X = S.use_median ? M * S.ratio : INFINITY;
-        if (settle_small && S.use_median && nb <= kTask) {
-            localmax_whole_hash(J, S, M, X, nb);
-        } else {
-            localmax_task(J, S, S.thr_rel * M, e0, e1, X);
-        }
-    }
-    if (!grid_sync(gb, status)) return false;
-    // C: exact median where it can matter, then recount those hashes' maxima.
-    // C1: hashes with at most kSmallMedian buckets, one block each, in shared memory.
-    bool mine_small = false, mine_large = false;
-    if (threadIdx.x < njobs) {
-        const JobView &J = jv[threadIdx.x];
-        const int64_t nb = nb_of(S.ndim, J.logB);
-        // (with settle_small, hashes of one task were settled in B)
-        med[threadIdx.x] = J.active && S.use_median && (!settle_small || nb > kTask) &&
-                           (int64_t)J.st->above > nb - nb / 2 - 1;
-        mine_small = med[threadIdx.x] && nb <= kSmallMedian;
-        mine_large = med[threadIdx.x] && nb > kSmallMedian;
-    }
-    const bool any_small = __syncthreads_or(mine_small);
-    const bool any_large = __syncthreads_or(mine_large);
-    if (!any_small && !any_large) return true;   // uniform: every block read the same counts
-    if (any_small) {
-        for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
-            const JobView &J = jv[jb];
-            HashStats &st = *J.st;
-            const int64_t nb = nb_of(S.ndim, J.logB);
-            if (!med[jb] || nb > kSmallMedian) continue;
-            const uint32_t m = block_median(J.E, (int)nb);
-            if (threadIdx.x == 0) {
-                st.need_median = 1;
-                st.med_bits = m;
-                st.nmax = 0;
-            }
-            __syncthreads();
-            const float T = threshold_of(st, S);
-            for (int64_t e0 = 0; e0 < nb; e0 += kTask) localmax_task_cold(J, S, T, e0, min(e0 + kTask, nb));
-        }
-    }
-    if (!any_large) return grid_sync(gb, status);
-    // C2: larger hashes, grid-wide radix select
+    if (nb <= kSmallMedian) return block_median(E, (int)nb);
     extern __shared__ __align__(16) uint32_t dsm[];
-    uint32_t *h = dsm;   // kHistBins entries
-    for (int digit = 0; digit < 3; digit++) {
-        int lo, width;
-        digit_range(digit, lo, width);
-        const int hi = lo + width;
-        for (int jb = 0; jb < njobs; jb++) {
-            const JobView &J = jv[jb];
-            HashStats &st = *J.st;
-            const int64_t nb = nb_of(S.ndim, J.logB);
-            const int slot = (int)(J.st - S.stats);
-            if (nb <= kSmallMedian || !med[jb]) continue;
-            if (digit == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
-                st.need_median = 1;
-                st.prefix = 0;
-                st.rank = (uint32_t)(nb / 2);
-            }
-            const uint32_t prefix = digit == 0 ? 0u : st.prefix;
-            for (int b = threadIdx.x; b < (1 << width); b += blockDim.x) h[b] = 0;
-            __syncthreads();
-            for (int64_t j = gtid; j < nb; j += gthreads) {
-                const uint32_t bits = __float_as_uint(J.E[j]);
-                if (digit == 0 || (bits >> hi) == prefix) hist_add(h, (bits >> lo) & ((1u << width) - 1));
-            }
-            __syncthreads();
-            for (int b = threadIdx.x; b < (1 << width); b += blockDim.x)
-                if (h[b]) atomicAdd(&S.hist[(int64_t)slot * kHistBins + b], h[b]);
-            __syncthreads();
-        }
-        if (!grid_sync(gb, status)) return false;
-        // pick: block jb % gridDim handles job jb
-        for (int jb = blockIdx.x; jb < njobs; jb += gridDim.x) {
-            const JobView &J = jv[jb];
-            HashStats &st = *J.st;
-            const int64_t nb = nb_of(S.ndim, J.logB);
-            if (nb <= kSmallMedian || !med[jb]) continue;
-            uint32_t *hh = S.hist + (int64_t)(J.st - S.stats) * kHistBins;
-            const uint32_t rank = digit == 0 ? (uint32_t)(nb / 2) : st.rank;
-            __shared__ uint32_t fb, fr;
-            block_find_rank(hh, 1 << width, rank, &fb, &fr);
-            if (threadIdx.x == 0) {
-                const uint32_t pre = digit == 0 ? 0u : st.prefix;
-                st.prefix = (pre << width) | fb;
-                st.rank = fr;
-                if (digit == 2) {
-                    st.med_bits = st.prefix;
-                    st.nmax = 0;   // recount below with the exact threshold
-                }
-            }
-            __syncthreads();
-            for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) hh[b] = 0;
-            __syncthreads();
-        }
-        if (!grid_sync(gb, status)) return false;
+    uint32_t *hist = dsm;   // 2048 entries
+    __shared__ uint32_t sh_prefix, sh_rank;
+    if (threadIdx.x == 0) {
+        sh_prefix = 0;
+        sh_rank = (uint32_t)(nb / 2);
     }
-    for (int jb = 0; jb < njobs; jb++) {
-        const JobView &J = jv[jb];
-        HashStats &st = *J.st;
-        const int64_t nb = nb_of(S.ndim, J.logB);
-        if (!med[jb] || nb <= kSmallMedian) continue;
-        const float T = threshold_of(st, S);
-        for (int64_t e0 = (int64_t)blockIdx.x * kTask; e0 < nb; e0 += (int64_t)gridDim.x * kTask)
-            localmax_task_cold(J, S, T, e0, min(e0 + kTask, nb));
+    __syncthreads();
+    const int los[3] = {21, 10, 0}, widths[3] = {11, 11, 10};
+    for (int d = 0; d < 3; d++) {
+        const int lo = los[d], width = widths[d], hi = lo + width;
+        for (int b = threadIdx.x; b < (1 << width); b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        const uint32_t prefix = sh_prefix;
+        for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) {
+            const uint32_t v = __float_as_uint(__ldg(&E[i]));
+            if (d == 0 || (v >> hi) == prefix) hist_add(hist, (v >> lo) & ((1u << width) - 1));
+        }
+        __syncthreads();
+        __shared__ uint32_t fb, fr;
+        block_find_rank(hist, 1 << width, sh_rank, &fb, &fr);
+        if (threadIdx.x == 0) {
+            sh_prefix = (prefix << width) | fb;
+            sh_rank = fr;
+        }
+        __syncthreads();
     }
-    return grid_sync(gb, status);
+    return sh_prefix;
 }
 
 // ---------------------------------------------------------------------------------
-// Tuning tail: statistics of every trial, then the controller.
+// Tuning tail: statistics of every trial of a stage, then the controller.
 // ---------------------------------------------------------------------------------
+
+// One trial as the tail kernels see it (passed by value: no dependent loads).
+struct TrialView {
+    int64_t e_off;         // its energies in the plan's energy buffer
+    int32_t logB, slot;
+    uint32_t s1, p1, s2, p2;   // sigma and sigma^{-1} mod B per axis
+};
+
 struct TuneTailArgs {
     StatsParams S;
-    const StatJob *jobs;   // this stage's trials
+    TrialView trial[kMaxLogB];   // this stage's trials, ascending B
     int njobs;
     int stage;             // >= 2: return at once if an earlier stage settled the controller
     int limit_b;           // the controller may visit trials up to this log2 B
@@ -611,10 +480,28 @@ struct TuneTailArgs {
     int nh_le, L_loc;
     StatJob *lstat;
     const float2 *z;
+    float *energy;         // the plan's energy buffer (tuning region first)
     float *e_loc;
     const HashParam *le;
     ExecState *state;
 };
+
+__device__ __forceinline__ JobView trial_view(const TrialView &t, const StatsParams &S,
+                                              const float *energy)
+{
+    JobView v;
+    v.E = energy + t.e_off;
+    v.st = S.stats + t.slot;
+    v.logB = t.logB;
+    v.list = -1;
+    v.active = 1;
+    v.pad = 0;
+    v.s1 = t.s1;
+    v.p1 = t.p1;
+    v.s2 = t.s2;
+    v.p2 = t.p2;
+    return v;
+}
 
 // Records B* = 2^b and k* for the location stage: the state words, the job at B* (all
 // nh_le hashes) and the statistics jobs of the location hashes.
@@ -709,13 +596,65 @@ __global__ void k_fixed_setup(const TuneTailArgs A, int b, int64_t k)
     if (blockIdx.x == 0 && threadIdx.x == 0) publish_bstar(A, b, k, A.state->status, 0, 0);
 }
 
-__global__ void __launch_bounds__(256, 2) k_tune_tail(const TuneTailArgs A)
+// A trial of more than one statistics task, after all its tasks counted (its last block):
+// where the median can matter, the exact median, and the maxima recounted with the
+// threshold it gives (the rare path, by this block alone).
+__device__ __noinline__ void settle_trial_median(const JobView &J, const StatsParams &S, int64_t nb)
 {
-    if (A.stage >= 2 && A.state->tune_done) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) stamp(&A.state->bar);
-    if (!stats_phases(A.jobs, A.njobs, A.S, &A.state->bar, &A.state->status, true)) return;
-    if (blockIdx.x == 0 && threadIdx.x < 32) controller(A);
-    end_stamp(&A.state->bar);
+    HashStats &st = *J.st;
+    if (!(S.use_median && (int64_t)__ldcg(&st.above) > nb - nb / 2 - 1)) return;
+    const uint32_t m = block_median_global(J.E, nb);
+    if (threadIdx.x == 0) {
+        st.need_median = 1;
+        st.med_bits = m;
+        st.nmax = 0;   // recounted below with the exact threshold
+    }
+    __threadfence_block();
+    __syncthreads();
+    const float T = fmaxf(S.thr_rel * __uint_as_float(__ldcg(&st.max_bits)),
+                          S.thr_med * __uint_as_float(m));
+    for (int64_t e0 = 0; e0 < nb; e0 += kTask) localmax_task_cold(J, S, T, e0, min(e0 + kTask, nb));
+}
+
+// Tasks: every trial of at most kTask buckets is one task (settled in one block, median
+// included); larger trials are split into tasks of kTask buckets.
+__global__ void __launch_bounds__(256) k_tune_tail(const TuneTailArgs A)
+{
+    pdl_wait();
+    ExecState *state = A.state;
+    if (A.stage >= 2 && state->tune_done) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) stamp(&state->bar);
+    __shared__ int64_t tstart[kMaxLogB + 1];
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int jb = 0; jb < A.njobs; jb++) {
+            tstart[jb] = acc;
+            acc += (nb_of(A.S.ndim, A.trial[jb].logB) + kTask - 1) / kTask;
+        }
+        tstart[A.njobs] = acc;
+    }
+    __syncthreads();
+    const int64_t ntasks = tstart[A.njobs];
+    for (int64_t task = blockIdx.x; task < ntasks; task += gridDim.x) {
+        int jb = 0;
+        while (task >= tstart[jb + 1]) jb++;
+        const JobView J = trial_view(A.trial[jb], A.S, A.energy);
+        const int64_t nb = nb_of(A.S.ndim, J.logB);
+        const float M = __uint_as_float(J.st->max_bits);
+        const float X = A.S.use_median ? M * A.S.ratio : INFINITY;
+        if (nb <= kTask) {
+            localmax_whole_hash(J, A.S, M, X, nb);
+        } else {
+            const int64_t e0 = (task - tstart[jb]) * kTask;
+            localmax_task(J, A.S, A.S.thr_rel * M, e0, min(e0 + kTask, nb), X);
+            const uint32_t units = (uint32_t)(tstart[jb + 1] - tstart[jb]);
+            if (finished_last(&state->done[A.trial[jb].slot], units)) settle_trial_median(J, A.S, nb);
+        }
+        if (finished_last(&state->done_all[A.stage - 1], (uint32_t)ntasks)) {
+            if (threadIdx.x < 32) controller(A);
+            if (threadIdx.x == 0) stamp(&state->bar);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -724,11 +663,12 @@ __global__ void __launch_bounds__(256, 2) k_tune_tail(const TuneTailArgs A)
 
 struct LocTailArgs {
     StatsParams S;
-    const StatJob *jobs;    // the location jobs at B*, written by the controller
     int L_loc, L_est;
     int est_base;           // first estimation hash in le / z (0 when they reuse location's)
     int est_group;          // lanes per coordinate in the estimates: power of two >= L_est
     float eta_up, eta_dn;
+    uint32_t sig[kMaxLoops][2], sinv[kMaxLoops][2];   // the location hashes (by value)
+    const float *e_loc;     // location energies at B*: [L_loc][B*] (P-index order)
     int32_t *sel;           // [L_loc][S.cap] selected buckets per location hash
     uint32_t need;          // votes needed: ceil(L_loc / 2)
     uint32_t *bucketbits;   // [L_loc][bucket_words] selected-bucket bitmaps
@@ -737,7 +677,9 @@ struct LocTailArgs {
     int64_t kept_cap;
     uint32_t *coordbits;    // one bit per coordinate (all zero between transforms)
     int64_t coord_words;
-    uint32_t *blk;          // per-block counts / offsets of the bitmap compaction
+    uint32_t *chunkcnt;     // kept coordinates per kChunkWords-word chunk of coordbits
+    int64_t nchunks;
+    int grid_maxima;        // blocks of k_loc_maxima
     const HashParam *le;    // location then estimation hashes
     const float2 *z;        // spectra at B*: location then estimation hashes
     const float *rgain;     // 1 / Ghat' per B (offsets ro)
@@ -827,20 +769,19 @@ constexpr int kTopStage = 4096;
 // Top-num cutoff of one location hash by one block: keep every maximum above
 // V(1+eta) (V = the num-th largest energy) and fill up from [V(1-eta), V(1+eta)] in
 // ascending bucket order.
-__device__ void topnum_block(const StatJob &J, const LocTailArgs &A, int64_t num)
+// The maxima were listed by other blocks: read through L2.
+__device__ void topnum_block(int l, int logB, int64_t cnt, const LocTailArgs &A, int64_t num)
 {
     __shared__ uint32_t n_sel;
-    HashStats &st = A.S.stats[J.slot];
+    HashStats &st = A.S.stats[kMaxLogB + l];
     const int ndim = A.S.ndim;
-    const int logB = J.logB;
     const uint32_t mask = (1u << logB) - 1;
-    const uint32_t p1 = J.hash->sinv[0] & mask, p2 = J.hash->sinv[1] & mask;
-    const int64_t cnt = min((int64_t)st.nmax, A.S.cap);
-    const int32_t *list = A.S.lists + (int64_t)J.list * A.S.cap;
-    int32_t *out = A.sel + (int64_t)J.list * A.S.cap;
-    const float *E = J.energy;
+    const uint32_t p1 = A.sinv[l][0] & mask, p2 = A.sinv[l][1] & mask;
+    const int32_t *list = A.S.lists + (int64_t)l * A.S.cap;
+    int32_t *out = A.sel + (int64_t)l * A.S.cap;
+    const float *E = A.e_loc + ((int64_t)l << (ndim == 1 ? logB : 2 * logB));
     auto energy_global = [&](int64_t i) -> float {
-        const uint32_t c = (uint32_t)list[i];
+        const uint32_t c = (uint32_t)__ldcg(&list[i]);
         if (ndim == 1) return E[(p1 * c) & mask];
         const uint32_t c1 = c >> logB, c2 = c & mask;
         return E[((int64_t)((p1 * c1) & mask) << logB) | ((p2 * c2) & mask)];
@@ -855,7 +796,7 @@ __device__ void topnum_block(const StatJob &J, const LocTailArgs &A, int64_t num
     if (threadIdx.x == 0) n_sel = 0;
     __syncthreads();
     if (cnt <= num) {
-        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) out[i] = list[i];
+        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) out[i] = __ldcg(&list[i]);
         if (threadIdx.x == 0) n_sel = (uint32_t)cnt;
     } else {
         const uint32_t vb = ~block_kth(
@@ -868,7 +809,7 @@ __device__ void topnum_block(const StatJob &J, const LocTailArgs &A, int64_t num
         const uint32_t nhi = block_sum(mine);
         const uint32_t need = (uint32_t)num - nhi;
         const uint32_t cthr = block_kth(
-            cnt, need - 1, [&](int64_t i) { return (uint32_t)list[i]; },
+            cnt, need - 1, [&](int64_t i) { return (uint32_t)__ldcg(&list[i]); },
             [&](int64_t i) {
                 const float e = energy_of(i);
                 return e >= lo && e <= hi;
@@ -880,13 +821,13 @@ __device__ void topnum_block(const StatJob &J, const LocTailArgs &A, int64_t num
             bool keep = false;
             if (i < cnt) {
                 const float e = energy_of(i);
-                keep = e > hi || (e >= lo && e <= hi && (uint32_t)list[i] <= cthr);
+                keep = e > hi || (e >= lo && e <= hi && (uint32_t)__ldcg(&list[i]) <= cthr);
             }
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
             uint32_t base = 0;
             if (lane == 0 && bal) base = atomicAdd(&n_sel, (uint32_t)__popc(bal));
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (keep) out[base + __popc(bal & ((1u << lane) - 1))] = list[i];
+            if (keep) out[base + __popc(bal & ((1u << lane) - 1))] = __ldcg(&list[i]);
         }
     }
     __syncthreads();
@@ -936,25 +877,6 @@ __device__ __forceinline__ void group_median(float2 v, int L, int grp, bool vali
     }
 }
 
-// Estimates of the kept coordinates: a group of `grp` lanes (grp >= L_est, a power of two)
-// per coordinate, lane l computing hash l, then the group's componentwise median.
-__device__ void estimate_all(const LocTailArgs &A, int64_t cnt, int b)
-{
-    const int grp = A.est_group;
-    const int lane = threadIdx.x & 31, gl = lane & (grp - 1);
-    const int per_warp = 32 / grp;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = warp * per_warp; base < cnt; base += nwarps * per_warp) {
-        const int64_t s = base + lane / grp;
-        const bool valid = s < cnt;
-        float2 v = make_float2(0.f, 0.f);
-        if (valid && gl < A.L_est) v = estimate_term((uint64_t)A.loc[s], A, b, gl);
-        group_median(v, A.L_est, grp, valid, &A.val[valid ? s : 0],
-                     A.msel && valid ? A.msel + 2 * s : nullptr);
-    }
-}
-
 // Bucket of coordinate i under hash hp on one axis (Eq. (10) with the half-bin reading):
 // round((sigma i mod n + 1/2) / D) mod B.
 __device__ __forceinline__ uint32_t bucket_of(uint32_t i, uint32_t sigma, int logn, int logB)
@@ -964,11 +886,11 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t i, uint32_t sigma, int lo
     return ((2u * p + 1u + D) >> (logn - logB + 1)) & ((1u << logB) - 1);
 }
 
-constexpr int kRankStage = 4096;   // top-num by ranking: candidates staged per block
-constexpr int kSelBlocks = 4;      // blocks per location hash in the cutoff
+constexpr int kRankStage = 4096;   // top-num by ranking: candidates staged in shared memory
 constexpr uint32_t kBandRank = 128; // band sizes ranked by counting (larger: radix select)
 constexpr int kPivots = 32;   // one warp: lane p holds pivot p
 constexpr int kVoteUnroll = 8;     // location hashes whose bitmap words are fetched together
+constexpr int kVoteIlp = 4;        // candidates per thread per round of the votes
 
 // Value of descending rank r (0-based; equal values ordered by index) among es[0..cnt),
 // by the whole block.  kPivots sampled values are counted against all elements (every
@@ -1067,200 +989,260 @@ __device__ __noinline__ float block_select_desc(const float *es, int cnt, uint32
     return v_sh;
 }
 
-// The location tail.  Phases, each ended by a grid barrier:
-//   P1  thresholds and local maxima of the L_loc location hashes (stats_phases);
-//   P2  top-num cutoff: each of a few blocks per hash stages its maxima and their
-//       energies, finds the pivot V (the num-th largest; pivot bracketing), keeps
-//       E > V(1 + eta) and fills from the band [V(1 - eta), V(1 + eta)] in ascending
-//       bucket order (the band's cutoff bucket by rank counting or radix selection),
-//       for its share of the candidates, and sets the selected-bucket bitmaps (hashes
-//       with more than kRankStage maxima: one block does the whole cutoff with radix
-//       selection instead);
-//   P3  votes: a kept coordinate lies in >= need selected preimages, hence in one of the
-//       first L_loc - need + 1 hashes' preimages; each such preimage counts the hashes
-//       whose bucket of it is selected (emitted once, by the first hash that has it);
-//   P4  ascending order by rank among the kept coordinates, Eq. (11) estimates and the
-//       componentwise median, written in place.  More kept coordinates than the kept
-//       list holds: ordered compaction of the coordinate bitmap instead (three more
-//       phases) and the estimates after it.
-__global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
+// Keeps, in place and in order, the listed maxima (bucket, energy) of one hash whose
+// energy exceeds T; returns how many.  Whole block; the entries were written by other
+// blocks (read through L2).
+__device__ int64_t filter_list(int32_t *list, float *list_e, int64_t cnt, float T)
 {
-    ExecState *state = A.state;
-    GridBarrier *gb = &state->bar;
-    if (blockIdx.x == 0 && threadIdx.x == 0) stamp(gb);
-    int *status = &state->status;
-    const bool empty = state->empty != 0;
-    const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
-    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
+    __shared__ uint32_t tot;
+    int64_t base = 0;
+    for (int64_t i0 = 0; i0 < cnt; i0 += blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        int32_t c = 0;
+        float e = 0.f;
+        if (i < cnt) {
+            c = __ldcg(&list[i]);
+            e = __ldcg(&list_e[i]);
+        }
+        const bool keep = i < cnt && e > T;
+        // (the scan synchronises: every read of this chunk precedes every write, and a
+        // kept entry only moves down)
+        const uint32_t ex = block_exclusive_scan(keep ? 1u : 0u, &tot);
+        if (keep) {
+            list[base + ex] = c;
+            list_e[base + ex] = e;
+        }
+        base += tot;
+        __syncthreads();
+    }
+    return base;
+}
+
+// The location step of hash l at B* = 2^b once all its local maxima are listed, by one
+// block: the exact median where it can matter (it raises the threshold, and the listed
+// maxima below the new one drop out); then the top-num cutoff (Algorithm 1 "find num
+// largest"): V = the num-th largest maximum energy, keep every maximum above V(1+eta) and
+// fill up from the band [V(1-eta), V(1+eta)] in ascending bucket order; the kept buckets
+// go to the hash's selection list and bitmap.
+__device__ __noinline__ void cutoff_hash(const LocTailArgs &A, int l, int b, int64_t num)
+{
     extern __shared__ __align__(16) uint32_t dsm[];
-    if (empty) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            *A.d_count = 0;
-            *A.d_k = state->k_star;
-            *A.d_status = state->status;
+    const int ndim = A.S.ndim;
+    const int lane = threadIdx.x & 31;
+    const int64_t nb = nb_of(ndim, b);
+    HashStats &st = A.S.stats[kMaxLogB + l];
+    int32_t *list = A.S.lists + (int64_t)l * A.S.cap;
+    float *list_e = A.S.list_e + (int64_t)l * A.S.cap;
+    uint32_t *bits = A.bucketbits + (int64_t)l * A.bucket_words;
+    int32_t *out = A.sel + (int64_t)l * A.S.cap;
+    __shared__ uint32_t sh_cnt, n_sel;
+    // clear this hash's bitmap (only this block writes it)
+    const int64_t words = (nb + 31) >> 5;
+    for (int64_t w = threadIdx.x; w < words; w += blockDim.x) bits[w] = 0u;
+    if (threadIdx.x == 0) {
+        sh_cnt = __ldcg(&st.nmax);
+        n_sel = 0;
+    }
+    __syncthreads();
+    int64_t cnt = min((int64_t)sh_cnt, A.S.cap);
+    if (A.S.use_median && (int64_t)__ldcg(&st.above) > nb - nb / 2 - 1) {
+        const uint32_t m = block_median_global(A.e_loc + (int64_t)l * nb, nb);
+        const float T = fmaxf(A.S.thr_rel * __uint_as_float(__ldcg(&st.max_bits)),
+                              A.S.thr_med * __uint_as_float(m));
+        cnt = filter_list(list, list_e, cnt, T);
+        if (threadIdx.x == 0) {
+            st.need_median = 1;
+            st.med_bits = m;
+            st.nmax = (uint32_t)cnt;
+        }
+        __syncthreads();
+    }
+    if (cnt <= num) {
+        // every maximum is kept: the list is the selection
+        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const uint32_t c = (uint32_t)__ldcg(&list[i]);
+            out[i] = (int32_t)c;
+            atomicOr(&bits[c >> 5], 1u << (c & 31));
+        }
+        if (threadIdx.x == 0) st.nsel = (uint32_t)cnt;
+        return;
+    }
+    if (cnt > kRankStage) {
+        // more maxima than stage: radix selection, then the bitmap
+        topnum_block(l, b, cnt, A, num);
+        const int64_t ns = st.nsel;
+        for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) {
+            const uint32_t c = (uint32_t)out[i];
+            atomicOr(&bits[c >> 5], 1u << (c & 31));
         }
         return;
     }
-    const int b = state->b_star;
-    const int64_t num = state->k_star;
-    const int logn = A.logn, logD = logn - b, ndim = A.S.ndim;
-    const int64_t nb = nb_of(ndim, b);
-    // clear the selected-bucket bitmaps (P1's barrier orders this before P2b)
-    {
-        const int64_t words = (nb + 31) >> 5;
-        for (int64_t w = gtid; w < (int64_t)A.L_loc * words; w += gthreads)
-            A.bucketbits[(w / words) * A.bucket_words + (w % words)] = 0u;
-    }
-    // blocks [l G, (l + 1) G) serve hash l in P2; their job is read now (the load overlaps
-    // P1, the barrier makes it visible)
-    const int G = min(kSelBlocks, (int)gridDim.x / A.L_loc);
-    const int l_mine = (int)blockIdx.x / G;
-    const int sb = (int)blockIdx.x % G;
-    __shared__ StatJob sJ;
-    if (threadIdx.x == 0 && l_mine < A.L_loc) sJ = A.jobs[l_mine];
-
-    // ---- P1 ----
-    if (!stats_phases(A.jobs, A.L_loc, A.S, gb, status, false)) return;
-
-    // ---- P2: top-num cutoff and the selected-bucket bitmaps ----
-    // each block of a hash finds the pivot V itself and decides a share of the candidates
-    if (l_mine < A.L_loc) {
-        const StatJob &J = sJ;
-        HashStats &st = A.S.stats[J.slot];
-        const int64_t cnt = min((int64_t)st.nmax, A.S.cap);
-        uint32_t *bits = A.bucketbits + (int64_t)l_mine * A.bucket_words;
-        int32_t *out = A.sel + (int64_t)J.list * A.S.cap;
-        const int32_t *list = A.S.lists + (int64_t)J.list * A.S.cap;
-        if (cnt <= num) {
-            // every maximum is kept: the list is the selection
-            for (int64_t i = (int64_t)sb * blockDim.x + threadIdx.x; i < cnt;
-                 i += (int64_t)G * blockDim.x) {
-                const uint32_t c = (uint32_t)list[i];
-                out[i] = (int32_t)c;
-                atomicOr(&bits[c >> 5], 1u << (c & 31));
-            }
-            if (sb == 0 && threadIdx.x == 0) st.nsel = (uint32_t)cnt;
-        } else if (cnt <= kRankStage) {
-            float *es = reinterpret_cast<float *>(dsm);   // kRankStage energies
-            uint32_t *cs = dsm + kRankStage;              // kRankStage buckets
-            uint32_t *band = dsm + 2 * kRankStage;        // band buckets / bracket members
-            const float *list_e = A.S.list_e + (int64_t)J.list * A.S.cap;
-            // staged eight per thread at a time: the buckets and their energies (listed
-            // together by the local-maximum search)
-            for (int64_t i0 = 0; i0 < cnt; i0 += 8 * blockDim.x) {
-                uint32_t cc[8];
-                float ee[8];
+    float *es = reinterpret_cast<float *>(dsm);   // kRankStage energies
+    uint32_t *cs = dsm + kRankStage;              // kRankStage buckets
+    uint32_t *band = dsm + 2 * kRankStage;        // band buckets / bracket members
+    // staged eight per thread at a time: the buckets and their energies (listed together
+    // by the local-maximum search)
+    for (int64_t i0 = 0; i0 < cnt; i0 += 8 * blockDim.x) {
+        uint32_t cc[8];
+        float ee[8];
 #pragma unroll
-                for (int u = 0; u < 8; u++) {
-                    const int64_t i = i0 + u * blockDim.x + threadIdx.x;
-                    cc[u] = i < cnt ? (uint32_t)list[i] : 0u;
-                    ee[u] = i < cnt ? list_e[i] : 0.f;
-                }
+        for (int u = 0; u < 8; u++) {
+            const int64_t i = i0 + u * blockDim.x + threadIdx.x;
+            cc[u] = i < cnt ? (uint32_t)__ldcg(&list[i]) : 0u;
+            ee[u] = i < cnt ? __ldcg(&list_e[i]) : 0.f;
+        }
 #pragma unroll
-                for (int u = 0; u < 8; u++) {
-                    const int64_t i = i0 + u * blockDim.x + threadIdx.x;
-                    if (i < cnt) {
-                        cs[i] = cc[u];
-                        es[i] = ee[u];
-                    }
-                }
-            }
-            __syncthreads();
-            const float V = block_select_desc(es, (int)cnt, (uint32_t)(num - 1), band);
-            const float hi = V * A.eta_up, lo = V * A.eta_dn;
-            __shared__ uint32_t nband;
-            if (threadIdx.x == 0) nband = 0;
-            __syncthreads();
-            uint32_t mine = 0;
-            for (int64_t i0 = 0; i0 < cnt; i0 += blockDim.x) {
-                // one shared atomic per warp (a unit-magnitude spectrum puts most maxima in
-                // the band: per-element atomics on one counter serialise)
-                const int64_t i = i0 + threadIdx.x;
-                const float e = i < cnt ? es[i] : 0.f;
-                mine += i < cnt && e > hi;
-                const bool in = i < cnt && e >= lo && e <= hi;
-                const unsigned bal = __ballot_sync(0xffffffffu, in);
-                uint32_t base = 0;
-                if (lane == 0 && bal) base = atomicAdd(&nband, (uint32_t)__popc(bal));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (in) band[base + __popc(bal & ((1u << lane) - 1))] = cs[i];
-            }
-            const uint32_t nhi = block_sum(mine);   // (synchronises: nband complete)
-            const uint32_t need_band = (uint32_t)num - nhi;
-            // the need_band-th smallest band bucket (distinct indices): by rank counting in
-            // a small band, by radix selection in a large one (unit-magnitude spectra put
-            // most kept maxima inside the band)
-            __shared__ uint32_t cthr;
-            const uint32_t nbd = nband;
-            uint32_t ct;
-            if (nbd <= kBandRank) {
-                for (uint32_t i = threadIdx.x; i < nbd; i += blockDim.x) {
-                    const uint32_t c = band[i];
-                    uint32_t r = 0;
-                    for (uint32_t j = 0; j < nbd; j++) r += band[j] < c;
-                    if (r == need_band - 1) cthr = c;
-                }
-                __syncthreads();
-                ct = cthr;
-            } else {
-                const int kbits = ndim == 1 ? b : 2 * b;   // bucket indices < B (B^2 in 2D)
-                if (kbits <= 22)
-                    ct = block_kth_narrow((int)nbd, need_band - 1, kbits,
-                                          [&](int i) { return band[i]; });
-                else
-                    ct = block_kth((int64_t)nbd, need_band - 1, [&](int64_t i) { return band[i]; },
-                                   [](int64_t) { return true; });
-            }
-            for (int64_t i0 = (int64_t)sb * blockDim.x; i0 < cnt; i0 += (int64_t)G * blockDim.x) {
-                const int64_t i = i0 + threadIdx.x;
-                bool keep = false;
-                uint32_t c = 0;
-                if (i < cnt) {
-                    const float e = es[i];
-                    c = cs[i];
-                    keep = e > hi || (e >= lo && e <= hi && c <= ct);
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                uint32_t base = 0;
-                if (lane == 0 && bal) base = atomicAdd(&st.nsel, (uint32_t)__popc(bal));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (keep) {
-                    out[base + __popc(bal & ((1u << lane) - 1))] = (int32_t)c;
-                    atomicOr(&bits[c >> 5], 1u << (c & 31));
-                }
-            }
-        } else if (sb == 0) {
-            // more maxima than stage: one block selects by radix selection, then marks them
-            topnum_block(J, A, num);
-            const int64_t ns = st.nsel;
-            for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) {
-                const uint32_t c = (uint32_t)out[i];
-                atomicOr(&bits[c >> 5], 1u << (c & 31));
+        for (int u = 0; u < 8; u++) {
+            const int64_t i = i0 + u * blockDim.x + threadIdx.x;
+            if (i < cnt) {
+                cs[i] = cc[u];
+                es[i] = ee[u];
             }
         }
     }
-    if (!grid_sync(gb, status)) return;
+    __syncthreads();
+    const float V = block_select_desc(es, (int)cnt, (uint32_t)(num - 1), band);
+    const float hi = V * A.eta_up, lo = V * A.eta_dn;
+    __shared__ uint32_t nband;
+    if (threadIdx.x == 0) nband = 0;
+    __syncthreads();
+    uint32_t mine = 0;
+    for (int64_t i0 = 0; i0 < cnt; i0 += blockDim.x) {
+        // one shared atomic per warp (a unit-magnitude spectrum puts most maxima in the
+        // band: per-element atomics on one counter serialise)
+        const int64_t i = i0 + threadIdx.x;
+        const float e = i < cnt ? es[i] : 0.f;
+        mine += i < cnt && e > hi;
+        const bool in = i < cnt && e >= lo && e <= hi;
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        uint32_t base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&nband, (uint32_t)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (in) band[base + __popc(bal & ((1u << lane) - 1))] = cs[i];
+    }
+    const uint32_t nhi = block_sum(mine);   // (synchronises: nband complete)
+    const uint32_t need_band = (uint32_t)num - nhi;
+    // the need_band-th smallest band bucket (distinct indices): by rank counting in a
+    // small band, by radix selection in a large one (unit-magnitude spectra put most
+    // kept maxima inside the band)
+    __shared__ uint32_t cthr;
+    const uint32_t nbd = nband;
+    uint32_t ct;
+    if (nbd <= kBandRank) {
+        for (uint32_t i = threadIdx.x; i < nbd; i += blockDim.x) {
+            const uint32_t c = band[i];
+            uint32_t r = 0;
+            for (uint32_t j = 0; j < nbd; j++) r += band[j] < c;
+            if (r == need_band - 1) cthr = c;
+        }
+        __syncthreads();
+        ct = cthr;
+    } else {
+        const int kbits = ndim == 1 ? b : 2 * b;   // bucket indices < B (B^2 in 2D)
+        if (kbits <= 22)
+            ct = block_kth_narrow((int)nbd, need_band - 1, kbits, [&](int i) { return band[i]; });
+        else
+            ct = block_kth((int64_t)nbd, need_band - 1, [&](int64_t i) { return band[i]; },
+                           [](int64_t) { return true; });
+    }
+    for (int64_t i0 = 0; i0 < cnt; i0 += blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        bool keep = false;
+        uint32_t c = 0;
+        if (i < cnt) {
+            const float e = es[i];
+            c = cs[i];
+            keep = e > hi || (e >= lo && e <= hi && c <= ct);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        uint32_t base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&n_sel, (uint32_t)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) {
+            out[base + __popc(bal & ((1u << lane) - 1))] = (int32_t)c;
+            atomicOr(&bits[c >> 5], 1u << (c & 31));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st.nsel = n_sel;
+}
 
-    // ---- P3: votes on the preimages of the first L_cand hashes ----
+__device__ __forceinline__ JobView loc_view(const LocTailArgs &A, int l, int b)
+{
+    const uint32_t mask = (1u << b) - 1;
+    JobView v;
+    v.E = A.e_loc + ((int64_t)l << (A.S.ndim == 1 ? b : 2 * b));
+    v.st = A.S.stats + kMaxLogB + l;
+    v.logB = b;
+    v.list = l;
+    v.active = 1;
+    v.pad = 0;
+    v.s1 = A.sig[l][0] & mask;
+    v.p1 = A.sinv[l][0] & mask;
+    v.s2 = A.sig[l][1] & mask;
+    v.p2 = A.sinv[l][1] & mask;
+    return v;
+}
+
+// Thresholds and local maxima of the L_loc location hashes at B* (tasks of kTask buckets,
+// the maxima and their energies listed); the block that finishes the last task of a hash
+// makes that hash's cutoff.
+__global__ void __launch_bounds__(256) k_loc_maxima(const LocTailArgs A)
+{
+    pdl_wait();
+    pdl_launch_next();
+    ExecState *state = A.state;
+    if (blockIdx.x == 0 && threadIdx.x == 0) stamp(&state->bar);
+    if (state->empty) return;   // k_loc_finish writes the outputs
+    const int b = state->b_star;
+    const int64_t num = state->k_star;
+    const int64_t nb = nb_of(A.S.ndim, b);
+    const int64_t per = (nb + kTask - 1) / kTask;
+    const int64_t ntasks = (int64_t)A.L_loc * per;
+    for (int64_t task = blockIdx.x; task < ntasks; task += gridDim.x) {
+        const int l = (int)(task / per);
+        const JobView J = loc_view(A, l, b);
+        const int64_t e0 = (task % per) * kTask;
+        const float M = __uint_as_float(J.st->max_bits);
+        const float X = A.S.use_median ? M * A.S.ratio : INFINITY;
+        localmax_task(J, A.S, A.S.thr_rel * M, e0, min(e0 + kTask, nb), X);
+        if (finished_last(&state->done[kMaxLogB + l], (uint32_t)per)) cutoff_hash(A, l, b, num);
+    }
+    end_stamp(state, 3);
+}
+
+// Votes.  A kept coordinate lies in >= need selected buckets, hence in a selected bucket
+// of one of the first L_cand = L_loc - need + 1 hashes; every preimage of those hashes'
+// selected buckets counts the hashes whose bucket of it is selected (from the bitmaps)
+// and is emitted once, by the first hash that has it.  kVoteIlp candidates per thread are
+// in flight at once (their selections, then all their bitmap words).
+__global__ void __launch_bounds__(256) k_loc_votes(const LocTailArgs A)
+{
+    pdl_wait();
+    pdl_launch_next();
+    ExecState *state = A.state;
+    if (blockIdx.x == 0 && threadIdx.x == 0) stamp(&state->bar);
+    if (state->empty) return;
+    const int b = state->b_star, ndim = A.S.ndim, logn = A.logn, logD = logn - b;
+    const int lane = threadIdx.x & 31;
     const int L_cand = A.L_loc - (int)A.need + 1;
     const uint32_t n = 1u << logn, nmask = n - 1, Bm = (1u << b) - 1;
     const int64_t D = (int64_t)1 << logD;
-    const int64_t Dd = ndim == 1 ? D : D * D;
+    const int logDd = ndim == 1 ? logD : 2 * logD;
     __shared__ int64_t off[kMaxLoops + 1];
     __shared__ uint32_t sh_sig[kMaxLoops][2], sh_sinv[kMaxLoops][2];
     if (threadIdx.x < A.L_loc) {
-        sh_sig[threadIdx.x][0] = (uint32_t)A.le[threadIdx.x].sigma[0];
-        sh_sig[threadIdx.x][1] = (uint32_t)A.le[threadIdx.x].sigma[1];
-        sh_sinv[threadIdx.x][0] = (uint32_t)A.le[threadIdx.x].sinv[0];
-        sh_sinv[threadIdx.x][1] = (uint32_t)A.le[threadIdx.x].sinv[1];
+        sh_sig[threadIdx.x][0] = A.sig[threadIdx.x][0];
+        sh_sig[threadIdx.x][1] = A.sig[threadIdx.x][1];
+        sh_sinv[threadIdx.x][0] = A.sinv[threadIdx.x][0];
+        sh_sinv[threadIdx.x][1] = A.sinv[threadIdx.x][1];
     }
     if (threadIdx.x < 32) {
         // the candidate counts of the first L_cand hashes, loaded by one lane each and
-        // summed by a warp scan (one round trip instead of one per hash)
+        // summed by a warp scan
         static_assert(kMaxLoops <= 32, "one lane per location hash");
         const int l = threadIdx.x;
-        const int64_t c = l < L_cand ? (int64_t)A.S.stats[kMaxLogB + l].nsel * Dd : 0;
+        const int64_t c = l < L_cand ? ((int64_t)A.S.stats[kMaxLogB + l].nsel << logDd) : 0;
         int64_t incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -1270,103 +1252,121 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
         if (l <= L_cand) off[l] = incl - c;   // exclusive prefix; off[L_cand] = total
     }
     __syncthreads();
-    {
-        // one preimage per thread per round (wider rounds measured slower: register and
-        // memory-queue pressure); its bitmap words in all hashes are requested at once
-        constexpr int kU = 1;
-        const int64_t total = off[L_cand];
-        for (int64_t it0 = (int64_t)blockIdx.x * blockDim.x; it0 < total; it0 += kU * gthreads) {
-            uint32_t coord[kU], cb[kU], qv[kU];
-            int l0v[kU];
+    const int64_t total = off[L_cand];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kVoteIlp;
+    for (int64_t it0 = (int64_t)blockIdx.x * blockDim.x * kVoteIlp; it0 < total; it0 += stride) {
+        uint32_t coord[kVoteIlp], cb[kVoteIlp], qv[kVoteIlp];
+        int l0v[kVoteIlp];
 #pragma unroll
-            for (int u = 0; u < kU; u++) {
-                const int64_t it = it0 + (int64_t)u * gthreads + threadIdx.x;
-                l0v[u] = -1;
-                if (it < total) {
-                    int l0 = 0;
-                    while (it >= off[l0 + 1]) l0++;
-                    const int64_t rem = it - off[l0];
-                    const int64_t sidx = rem >> (ndim == 1 ? logD : 2 * logD);
-                    qv[u] = (uint32_t)(rem & (Dd - 1));
-                    cb[u] = (uint32_t)A.sel[(int64_t)l0 * A.S.cap + sidx];
-                    l0v[u] = l0;
-                }
+        for (int u = 0; u < kVoteIlp; u++) {
+            const int64_t it = it0 + (int64_t)u * blockDim.x + threadIdx.x;
+            l0v[u] = -1;
+            cb[u] = qv[u] = 0;
+            if (it < total) {
+                int l0 = 0;
+                while (it >= off[l0 + 1]) l0++;
+                const int64_t rem = it - off[l0];
+                qv[u] = (uint32_t)(rem & (((int64_t)1 << logDd) - 1));
+                cb[u] = (uint32_t)A.sel[(int64_t)l0 * A.S.cap + (rem >> logDd)];
+                l0v[u] = l0;
             }
+        }
 #pragma unroll
-            for (int u = 0; u < kU; u++) {
-                coord[u] = 0;
-                if (l0v[u] < 0) continue;
-                const int l0 = l0v[u];
-                const uint32_t c = cb[u], q = qv[u];
-                if (ndim == 1) {
-                    // bucket c collects permuted positions p in [c D - D/2, c D + D/2 - 1]
-                    const uint32_t pp = ((c << logD) - (uint32_t)(D >> 1) + q) & nmask;
-                    coord[u] = (sh_sinv[l0][0] * pp) & nmask;
-                } else {
-                    const uint32_t c1 = c >> b, c2 = c & Bm;
-                    const uint32_t q1 = q >> logD, q2 = q & (uint32_t)(D - 1);
-                    const uint32_t pp1 = ((c1 << logD) - (uint32_t)(D >> 1) + q1) & nmask;
-                    const uint32_t pp2 = ((c2 << logD) - (uint32_t)(D >> 1) + q2) & nmask;
-                    coord[u] = (((sh_sinv[l0][0] * pp1) & nmask) << logn) |
-                               ((sh_sinv[l0][1] * pp2) & nmask);
-                }
+        for (int u = 0; u < kVoteIlp; u++) {
+            coord[u] = 0;
+            if (l0v[u] < 0) continue;
+            const int l0 = l0v[u];
+            const uint32_t c = cb[u], q = qv[u];
+            if (ndim == 1) {
+                // bucket c collects permuted positions p in [c D - D/2, c D + D/2 - 1]
+                const uint32_t pp = ((c << logD) - (uint32_t)(D >> 1) + q) & nmask;
+                coord[u] = (sh_sinv[l0][0] * pp) & nmask;
+            } else {
+                const uint32_t c1 = c >> b, c2 = c & Bm;
+                const uint32_t q1 = q >> logD, q2 = q & (uint32_t)(D - 1);
+                const uint32_t pp1 = ((c1 << logD) - (uint32_t)(D >> 1) + q1) & nmask;
+                const uint32_t pp2 = ((c2 << logD) - (uint32_t)(D >> 1) + q2) & nmask;
+                coord[u] = (((sh_sinv[l0][0] * pp1) & nmask) << logn) | ((sh_sinv[l0][1] * pp2) & nmask);
             }
-            uint32_t votes[kU], earlier[kU];
+        }
+        uint32_t votes[kVoteIlp], earlier[kVoteIlp];
 #pragma unroll
-            for (int u = 0; u < kU; u++) {
-                votes[u] = 0;
-                earlier[u] = 0;
-            }
-            // the bitmap word of every (preimage, hash) pair is requested before any is
-            // tested; up to kVoteUnroll hashes at a time
-            for (int l0 = 0; l0 < A.L_loc; l0 += kVoteUnroll) {
-                uint32_t w[kU][kVoteUnroll];
+        for (int u = 0; u < kVoteIlp; u++) {
+            votes[u] = 0;
+            earlier[u] = 0;
+        }
+        // the bitmap word of every (candidate, hash) pair is requested before any is
+        // tested; up to kVoteUnroll hashes at a time
+        for (int l0 = 0; l0 < A.L_loc; l0 += kVoteUnroll) {
+            uint32_t w[kVoteIlp][kVoteUnroll];
 #pragma unroll
-                for (int dl = 0; dl < kVoteUnroll; dl++) {
-                    const int l = l0 + dl;
+            for (int dl = 0; dl < kVoteUnroll; dl++) {
+                const int l = l0 + dl;
 #pragma unroll
-                    for (int u = 0; u < kU; u++) {
-                        w[u][dl] = 0;
-                        if (l < A.L_loc && l0v[u] >= 0) {
-                            const uint32_t ci = ndim == 1 ? coord[u] : coord[u] >> logn;
-                            uint32_t c_l = bucket_of(ci, sh_sig[l][0], logn, b);
-                            if (ndim == 2) c_l = (c_l << b) | bucket_of(coord[u] & nmask, sh_sig[l][1], logn, b);
-                            w[u][dl] = A.bucketbits[(int64_t)l * A.bucket_words + (c_l >> 5)] >> (c_l & 31);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int dl = 0; dl < kVoteUnroll; dl++) {
-#pragma unroll
-                    for (int u = 0; u < kU; u++) {
-                        const uint32_t sel = w[u][dl] & 1u;
-                        votes[u] += sel;
-                        earlier[u] |= sel && l0 + dl < l0v[u];
+                for (int u = 0; u < kVoteIlp; u++) {
+                    w[u][dl] = 0;
+                    if (l < A.L_loc && l0v[u] >= 0) {
+                        const uint32_t ci = ndim == 1 ? coord[u] : coord[u] >> logn;
+                        uint32_t c_l = bucket_of(ci, sh_sig[l][0], logn, b);
+                        if (ndim == 2) c_l = (c_l << b) | bucket_of(coord[u] & nmask, sh_sig[l][1], logn, b);
+                        w[u][dl] = A.bucketbits[(int64_t)l * A.bucket_words + (c_l >> 5)] >> (c_l & 31);
                     }
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kU; u++) {
-                const bool keep = l0v[u] >= 0 && !earlier[u] && votes[u] >= A.need;
-                const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                if (!bal) continue;
-                uint32_t base = 0;
-                if (lane == __ffs(bal) - 1)
-                    base = (uint32_t)atomicAdd((unsigned long long *)&state->count,
-                                               (unsigned long long)__popc(bal));
-                base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
-                if (keep) {
-                    const uint32_t pos = base + __popc(bal & ((1u << lane) - 1));
-                    if (pos < A.kept_cap) A.kept[pos] = coord[u];
-                    atomicOr(&A.coordbits[coord[u] >> 5], 1u << (coord[u] & 31));
+            for (int dl = 0; dl < kVoteUnroll; dl++) {
+#pragma unroll
+                for (int u = 0; u < kVoteIlp; u++) {
+                    const uint32_t sel = w[u][dl] & 1u;
+                    votes[u] += sel;
+                    earlier[u] |= sel && l0 + dl < l0v[u];
                 }
             }
         }
+#pragma unroll
+        for (int u = 0; u < kVoteIlp; u++) {
+            const bool keep = l0v[u] >= 0 && !earlier[u] && votes[u] >= A.need;
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (!bal) continue;
+            uint32_t base = 0;
+            if (lane == __ffs(bal) - 1)
+                base = (uint32_t)atomicAdd((unsigned long long *)&state->count,
+                                           (unsigned long long)__popc(bal));
+            base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+            if (keep) {
+                const uint32_t pos = base + __popc(bal & ((1u << lane) - 1));
+                if (pos < A.kept_cap) A.kept[pos] = coord[u];
+                atomicOr(&A.coordbits[coord[u] >> 5], 1u << (coord[u] & 31));
+                atomicAdd(&A.chunkcnt[coord[u] >> (5 + 10)], 1u);
+            }
+        }
     }
-    if (!grid_sync(gb, status)) return;
+    end_stamp(state, 4);
+}
 
-    // ---- P4: order, estimates, outputs ----
+// The outputs: the caller's status words; the kept coordinates in ascending order with
+// their Eq. (11) estimates and componentwise medians.  Up to kept_cap kept coordinates:
+// each one's rank among them (a warp per coordinate); beyond: the ordered compaction of
+// the coordinate bitmap by chunks of kChunkWords words, each chunk's first position the
+// sum of the earlier chunks' counts.
+__global__ void __launch_bounds__(256) k_loc_finish(const LocTailArgs A)
+{
+    pdl_wait();
+    ExecState *state = A.state;
+    if (blockIdx.x == 0 && threadIdx.x == 0) stamp(&state->bar);
+    const int lane = threadIdx.x & 31;
+    if (state->empty) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            *A.d_count = 0;
+            *A.d_k = state->k_star;
+            *A.d_status = state->status;
+        }
+        return;
+    }
+    const int b = state->b_star;
+    const int64_t num = state->k_star;
     const int64_t K = state->count;
+    extern __shared__ __align__(16) uint32_t dsm[];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         int st = state->status;
         if (K > A.capacity && st == ATSFFT_OK) st = ATSFFT_E_CAPACITY;
@@ -1376,8 +1376,7 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
     }
     if (K <= A.kept_cap) {
         // rank = number of kept coordinates below; a warp per coordinate splits the
-        // comparisons (measured: a group of L_est lanes left each lane a long chain of
-        // shared-memory reads), then its first L_est lanes compute the estimates
+        // comparisons, then its first L_est lanes compute the estimates
         constexpr int grp = 32;
         const int gl = lane;
         const int per_block = (int)blockDim.x / grp;
@@ -1435,54 +1434,52 @@ __global__ void __launch_bounds__(256, 2) k_loc_tail(const LocTailArgs A)
                 if (inside) A.loc[r] = coord;
             }
         }
-        end_stamp(gb);
-        return;
-    }
-    // fallback: ordered compaction of the coordinate bitmap, clearing it
-    const int64_t per = (A.coord_words + gridDim.x - 1) / gridDim.x;
-    const int64_t w0 = blockIdx.x * per;
-    const int64_t w1 = min(w0 + per, A.coord_words);
-    uint32_t c = 0;
-    for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) c += __popc(A.coordbits[w]);
-    c = block_sum(c);
-    if (threadIdx.x == 0) A.blk[blockIdx.x] = c;
-    if (!grid_sync(gb, status)) return;
-    if (blockIdx.x == 0) {
-        __shared__ uint32_t carry, tot;
-        if (threadIdx.x == 0) carry = 0;
-        __syncthreads();
-        for (unsigned i0 = 0; i0 < gridDim.x; i0 += blockDim.x) {
-            const unsigned i = i0 + threadIdx.x;
-            const uint32_t v = i < gridDim.x ? A.blk[i] : 0u;
-            const uint32_t ex = block_exclusive_scan(v, &tot);
-            if (i < gridDim.x) A.blk[i] = carry + ex;
-            __syncthreads();
-            if (threadIdx.x == 0) carry += tot;
-            __syncthreads();
-        }
-    }
-    if (!grid_sync(gb, status)) return;
-    {
-        int64_t base = A.blk[blockIdx.x];
+    } else {
         __shared__ uint32_t tot;
-        for (int64_t wb = w0; wb < w1; wb += blockDim.x) {
-            const int64_t w = wb + threadIdx.x;
-            uint32_t word = w < w1 ? A.coordbits[w] : 0u;
-            int64_t pos = base + block_exclusive_scan((uint32_t)__popc(word), &tot);
-            if (word) A.coordbits[w] = 0u;
-            while (word) {
-                const int bit = __ffs(word) - 1;
-                word &= word - 1;
-                if (pos < A.capacity) A.loc[pos] = w * 32 + bit;
-                pos++;
+        const int grp = A.est_group;
+        const int gl = lane & (grp - 1);
+        const int per_warp = 32 / grp;
+        const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        for (int64_t ch = blockIdx.x; ch < A.nchunks; ch += gridDim.x) {
+            // the kept coordinates before this chunk: the earlier chunks' counts
+            uint32_t part = 0;
+            for (int64_t i = threadIdx.x; i < ch; i += blockDim.x) part += A.chunkcnt[i];
+            int64_t pos0 = block_sum(part);
+            const int64_t first = pos0;
+            const int64_t w0 = ch * kChunkWords;
+            const int64_t w1 = min(w0 + (int64_t)kChunkWords, A.coord_words);
+            for (int64_t wb = w0; wb < w1; wb += blockDim.x) {
+                const int64_t w = wb + threadIdx.x;
+                uint32_t word = w < w1 ? A.coordbits[w] : 0u;
+                int64_t pos = pos0 + block_exclusive_scan((uint32_t)__popc(word), &tot);
+                if (word) A.coordbits[w] = 0u;
+                while (word) {
+                    const int bit = __ffs(word) - 1;
+                    word &= word - 1;
+                    if (pos < A.capacity) A.loc[pos] = w * 32 + bit;
+                    pos++;
+                }
+                pos0 += tot;
+                __syncthreads();
             }
-            base += tot;
+            if (!A.skip_est) {
+                // this chunk's coordinates inside the capacity (their loc entries were
+                // written by this block: visible after the barrier above)
+                const int64_t p1 = min(pos0, A.capacity);
+                for (int64_t q0 = first + (int64_t)warp * per_warp; q0 < p1;
+                     q0 += (int64_t)nwarps * per_warp) {
+                    const int64_t s = q0 + lane / grp;
+                    const bool valid = s < p1;
+                    float2 v = make_float2(0.f, 0.f);
+                    if (valid && gl < A.L_est) v = estimate_term((uint64_t)A.loc[s], A, b, gl);
+                    group_median(v, A.L_est, grp, valid, &A.val[valid ? s : 0],
+                                 A.msel && valid ? A.msel + 2 * s : nullptr);
+                }
+            }
             __syncthreads();
         }
     }
-    if (!grid_sync(gb, status)) return;
-    if (!A.skip_est) estimate_all(A, min(K, A.capacity), b);
-    end_stamp(gb);
+    end_stamp(state, 5);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1498,36 +1495,39 @@ static StatsParams stats_params(const atsfft_plan_s *P)
     S.use_median = P->p.thr_med > 0;
     S.ratio = S.use_median ? (float)(P->p.thr_rel / P->p.thr_med * (1.0 - 1.0 / 1048576.0)) : 0.f;
     S.stats = P->d_stats;
-    S.hist = P->d_hist;
     S.lists = P->d_lmax;
     S.list_e = P->d_lmax_e;
     S.cap = P->lmax_cap;
     return S;
 }
 
-// Dynamic shared memory of the tail kernels: the largest phase scratch (the small-hash
-// median: kSmallMedian values + 2048 histogram bins; the cutoff: 3 kRankStage words).
+// Dynamic shared memory of the tail kernels: the largest scratch (the small-hash median:
+// kSmallMedian values + 2048 histogram bins; the cutoff and the ordering: 3 kRankStage
+// words).
 constexpr size_t kTailSmemWords = (kSmallMedian + 2048) > 3 * kRankStage ? (kSmallMedian + 2048)
                                                                           : 3 * kRankStage;
 constexpr size_t kTailSmem = sizeof(uint32_t) * kTailSmemWords;
 
-static cudaError_t launch_coop(const void *fn, int grid, void *arg, cudaStream_t s)
+// A tail kernel launched with programmatic stream serialization: its blocks may be
+// scheduled before the previous kernel of the stream has finished and wait for it at
+// griddepcontrol.wait (every tail kernel starts with that wait).
+template <class Arg>
+static cudaError_t launch_pdl(void (*fn)(const Arg), int grid, size_t smem, const Arg &arg,
+                              cudaStream_t s)
 {
-    void *args[] = {arg};
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem);
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, kTailSmem, s);
-}
-
-static int coop_grid(const atsfft_plan_s *P, const void *fn)
-{
-    int per_sm = 0;
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, kTailSmem);
-    const int want = P->p.coop_blocks_per_sm > 0 ? P->p.coop_blocks_per_sm : 2;
-    if (per_sm > want) per_sm = want;
-    if (per_sm < 1) per_sm = 1;
-    const int sms = P->p.coop_sms > 0 && P->p.coop_sms < P->num_sms ? P->p.coop_sms : P->num_sms;
-    return sms * per_sm;
+    cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, arg);
 }
 
 static TuneTailArgs tune_args(const atsfft_plan_s *P)
@@ -1544,6 +1544,7 @@ static TuneTailArgs tune_args(const atsfft_plan_s *P)
     A.L_loc = P->L_loc;
     A.lstat = P->d_lstat;
     A.z = P->d_z;
+    A.energy = P->d_energy;
     A.e_loc = P->d_energy + P->e_loc_off;
     A.le = P->d_le;
     A.state = P->d_state;
@@ -1559,17 +1560,31 @@ void launch_fixed_setup(const atsfft_plan_s *P, cudaStream_t s)
 
 void launch_tune_tail(const atsfft_plan_s *P, int stage, cudaStream_t s)
 {
-    // the stage's trials: stat jobs are ordered by log2 B from b0
-    const int first = P->tune_hi[stage - 1] + 1 - P->b0;
-    const int last = P->tune_hi[stage] - P->b0;
-    if (first > last) return;
+    // the stage's trials, ascending log2 B from b0
+    const int lo = P->tune_hi[stage - 1] + 1, hi = P->tune_hi[stage];
+    if (lo > hi) return;
     TuneTailArgs A = tune_args(P);
-    A.jobs = P->d_tstat + first;
-    A.njobs = last - first + 1;
+    int64_t tasks = 0;
+    for (int b = lo; b <= hi; b++) {
+        TrialView &t = A.trial[b - lo];
+        const uint32_t mask = (1u << b) - 1;
+        const atsfft::HashParam &hp = P->h_tune[b];
+        t.e_off = P->tz_off[b];
+        t.logB = b;
+        t.slot = stats_slot_tune(b);
+        t.s1 = hp.sigma[0] & mask;
+        t.p1 = hp.sinv[0] & mask;
+        t.s2 = hp.sigma[1] & mask;
+        t.p2 = hp.sinv[1] & mask;
+        const int64_t nb = P->ndim == 1 ? ((int64_t)1 << b) : ((int64_t)1 << (2 * b));
+        tasks += (nb + kTask - 1) / kTask;
+    }
+    A.njobs = hi - lo + 1;
     A.stage = stage;
-    A.limit_b = P->tune_hi[stage];
-    const void *fn = (const void *)k_tune_tail;
-    launch_coop(fn, coop_grid(P, fn), &A, s);
+    A.limit_b = hi;
+    const int64_t cap = (int64_t)P->num_sms * 4;
+    const int grid = (int)(tasks < cap ? tasks : cap);
+    launch_pdl(k_tune_tail, grid, kTailSmem, A, s);
     count_launch(P);
 }
 
@@ -1578,8 +1593,8 @@ void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, uint
                      cudaStream_t s)
 {
     LocTailArgs A;
+    memset(&A, 0, sizeof(A));
     A.S = stats_params(P);
-    A.jobs = P->d_lstat;
     A.L_loc = P->L_loc;
     A.L_est = P->L_est;
     A.est_base = P->est_base;
@@ -1587,6 +1602,12 @@ void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, uint
     while (A.est_group < P->L_est) A.est_group *= 2;
     A.eta_up = (float)(1.0 + P->p.tie_eta);
     A.eta_dn = (float)(1.0 - P->p.tie_eta);
+    for (int l = 0; l < P->L_loc; l++)
+        for (int ax = 0; ax < 2; ax++) {
+            A.sig[l][ax] = P->h_le[l].sigma[ax];
+            A.sinv[l][ax] = P->h_le[l].sinv[ax];
+        }
+    A.e_loc = P->d_energy + P->e_loc_off;
     A.sel = P->d_sel;
     A.need = (uint32_t)((P->L_loc + 1) / 2);
     A.bucketbits = P->d_bucketbits;
@@ -1595,7 +1616,8 @@ void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, uint
     A.kept_cap = P->kept_cap;
     A.coordbits = P->d_coordbits;
     A.coord_words = P->coord_words;
-    A.blk = P->d_blk;
+    A.chunkcnt = P->d_blk;
+    A.nchunks = P->nchunks;
     A.le = P->d_le;
     A.z = P->d_z;
     A.rgain = P->d_rgain;
@@ -1612,9 +1634,17 @@ void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, uint
     A.d_k = d_k;
     A.d_status = d_status;
     A.state = P->d_state;
-    const void *fn = (const void *)k_loc_tail;
-    launch_coop(fn, coop_grid(P, fn), &A, s);
-    count_launch(P);
+    // k_loc_maxima: every task of the largest B the plan can pick (blocks beyond the
+    // tasks of the actual B* exit at once), at most 4 blocks per SM
+    const int64_t nb_max = P->ndim == 1 ? ((int64_t)1 << P->b_hi) : ((int64_t)1 << (2 * P->b_hi));
+    const int64_t tasks = (int64_t)P->L_loc * ((nb_max + kTask - 1) / kTask);
+    const int64_t cap = (int64_t)P->num_sms * 4;
+    const int grid1 = (int)(tasks < cap ? tasks : cap);
+    A.grid_maxima = grid1;
+    launch_pdl(k_loc_maxima, grid1, kTailSmem, A, s);
+    launch_pdl(k_loc_votes, P->num_sms * 8, 0, A, s);
+    launch_pdl(k_loc_finish, P->num_sms * 4, kTailSmem, A, s);
+    count_launch(P, 3);
 }
 
 }  // namespace atsfft
