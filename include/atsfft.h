@@ -78,7 +78,7 @@ typedef struct {
                                    (requires loops_est <= loops_loc): half the binning and
                                    FFT work at B*.  0 (default): fresh estimation hashes  */
     int precision;              /* 0 (default): complex64 input and values, FP32 path.
-                                   1 (1D only): complex128 input and values; locations
+                                   1: complex128 input and values (1D and 2D); locations
                                    as in the FP32 path (on the input rounded to complex64),
                                    the estimation stage in FP64 (Eq. (11) values to
                                    ~1e-12 of an FP64 evaluation).  Slow: FP64 runs at
@@ -178,10 +178,10 @@ atsfft_status atsfft_phase_times(atsfft_plan_t plan, float *h_ms, int max_phases
                                  int64_t *h_launches, void *stream);
 
 /* Diagnostics after an exec: device time stamps (ns, %globaltimer) taken at the start
- * of every tail kernel (the tuning statistics of each stage, the location maxima, votes
- * and outputs) and when its last block finishes (for the tuning tail: when the
- * controller has walked), in the order they happened (at most 32).  Synchronises
- * `stream`. */
+ * of every tail kernel, once the kernel before it has completed (the tuning statistics
+ * of each stage, the location maxima with their cutoffs, the votes and the outputs),
+ * and when a tuning stage's controller has walked, in the order they happened (at most
+ * 32).  Synchronises `stream`. */
 atsfft_status atsfft_tail_stamps(atsfft_plan_t plan, uint64_t *h_ns, int max_stamps,
                                  int *h_nstamps, void *stream);
 

@@ -133,9 +133,10 @@ struct atsfft_plan_s {
     int est_base;          // index of the first estimation hash in h_le / d_le
     int nh_le;             // location + estimation hashes binned at B* (distinct ones)
     // FP64 path (precision 1): FP32 copy of the input, FP64 estimation spectra (two
-    // Stockham buffers, [L_est][B*]) and their twiddles
+    // Stockham buffers, [L_est][B*] or [L_est][B* x B*]) and their twiddles
     float2 *d_x32;
     double2 *d_f64a, *d_f64b, *d_tw64;
+    double2 *d_wtab64;     // 2D: the modulated window taps of B* in FP64 (2h + 1 <= N - 1)
     int L_loc, L_est;
     int device;
     int num_sms;

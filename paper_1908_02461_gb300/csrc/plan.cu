@@ -287,7 +287,7 @@ static void plan_free(atsfft_plan_s *P)
     void *ptrs[] = {P->d_tune, P->d_le, P->d_win, P->d_resp, P->d_rgain, P->d_phase, P->d_tw, P->d_part, P->d_tz,
                     P->d_z, P->d_fft_tmp, P->d_energy, P->d_stats, P->d_lmax, P->d_lmax_e,
                     P->d_sel, P->d_bucketbits, P->d_kept, P->d_coordbits, P->d_blk, P->d_x32, P->d_f64a,
-                    P->d_f64b, P->d_tw64, P->d_state, P->d_tjob, P->d_tstat,
+                    P->d_f64b, P->d_tw64, P->d_wtab64, P->d_state, P->d_tjob, P->d_tstat,
                     P->d_lstat};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -323,7 +323,6 @@ static atsfft_status plan_create(atsfft_plan_t *out, int ndim, const int64_t *sh
     if (n <= 0 || (n & (n - 1))) return ATSFFT_E_INVALID_ARG;
     if (ndim == 1 && (n < 256 || n > ((int64_t)1 << 28))) return ATSFFT_E_INVALID_ARG;
     if (ndim == 2 && (shape[1] != n || n < 32 || n > ((int64_t)1 << 14))) return ATSFFT_E_INVALID_ARG;
-    if (ndim == 2 && p.precision == 1) return ATSFFT_E_INVALID_ARG;   // the FP64 path is 1D
 
     atsfft_plan_s *P = new (std::nothrow) atsfft_plan_s;
     if (!P) return ATSFFT_E_NOMEM;
@@ -484,10 +483,11 @@ static atsfft_status plan_create(atsfft_plan_t *out, int ndim, const int64_t *sh
     P->nchunks = (P->coord_words + kChunkWords - 1) / kChunkWords;
     A((void **)&P->d_blk, sizeof(uint32_t) * (size_t)P->nchunks);
     if (p.precision == 1) {
-        A((void **)&P->d_x32, sizeof(float2) * (size_t)n);
+        A((void **)&P->d_x32, sizeof(float2) * (size_t)P->ncoord);
         A((void **)&P->d_f64a, sizeof(double2) * (size_t)P->L_est * (size_t)nb_max);
         A((void **)&P->d_f64b, sizeof(double2) * (size_t)P->L_est * (size_t)nb_max);
-        A((void **)&P->d_tw64, sizeof(double2) * (size_t)(nb_max / 2 + 1));
+        A((void **)&P->d_tw64, sizeof(double2) * (size_t)(((int64_t)1 << P->b_hi) / 2 + 1));
+        if (ndim == 2) A((void **)&P->d_wtab64, sizeof(double2) * (size_t)n);   // 2h + 1 <= N - 1
     }
     A((void **)&P->d_state, sizeof(ExecState));
     A((void **)&P->d_tjob, sizeof(Job) * kMaxLogB);

@@ -76,14 +76,6 @@ __device__ bool finished_last(uint32_t *counter, uint32_t units)
     return last != 0;
 }
 
-// Diagnostic end stamp of a kernel: the block that finishes last records the time (no
-// ordering is needed, nothing reads results through it).
-__device__ __forceinline__ void end_stamp(ExecState *state, int which)
-{
-    __syncthreads();
-    if (threadIdx.x == 0 && atomicAdd(&state->done_all[which], 1u) == gridDim.x - 1)
-        stamp(&state->bar);
-}
 
 __device__ __forceinline__ int64_t nb_of(int ndim, int logB)
 {
@@ -1035,17 +1027,18 @@ __device__ __noinline__ void cutoff_hash(const LocTailArgs &A, int l, int b, int
     float *list_e = A.S.list_e + (int64_t)l * A.S.cap;
     uint32_t *bits = A.bucketbits + (int64_t)l * A.bucket_words;
     int32_t *out = A.sel + (int64_t)l * A.S.cap;
-    __shared__ uint32_t sh_cnt, n_sel;
+    __shared__ uint32_t sh_cnt, sh_above, n_sel;
     // clear this hash's bitmap (only this block writes it)
     const int64_t words = (nb + 31) >> 5;
     for (int64_t w = threadIdx.x; w < words; w += blockDim.x) bits[w] = 0u;
     if (threadIdx.x == 0) {
         sh_cnt = __ldcg(&st.nmax);
+        sh_above = __ldcg(&st.above);
         n_sel = 0;
     }
     __syncthreads();
     int64_t cnt = min((int64_t)sh_cnt, A.S.cap);
-    if (A.S.use_median && (int64_t)__ldcg(&st.above) > nb - nb / 2 - 1) {
+    if (A.S.use_median && (int64_t)sh_above > nb - nb / 2 - 1) {
         const uint32_t m = block_median_global(A.e_loc + (int64_t)l * nb, nb);
         const float T = fmaxf(A.S.thr_rel * __uint_as_float(__ldcg(&st.max_bits)),
                               A.S.thr_med * __uint_as_float(m));
@@ -1208,7 +1201,6 @@ __global__ void __launch_bounds__(256) k_loc_maxima(const LocTailArgs A)
         localmax_task(J, A.S, A.S.thr_rel * M, e0, min(e0 + kTask, nb), X);
         if (finished_last(&state->done[kMaxLogB + l], (uint32_t)per)) cutoff_hash(A, l, b, num);
     }
-    end_stamp(state, 3);
 }
 
 // Votes.  A kept coordinate lies in >= need selected buckets, hence in a selected bucket
@@ -1341,7 +1333,6 @@ __global__ void __launch_bounds__(256) k_loc_votes(const LocTailArgs A)
             }
         }
     }
-    end_stamp(state, 4);
 }
 
 // The outputs: the caller's status words; the kept coordinates in ascending order with
@@ -1479,7 +1470,6 @@ __global__ void __launch_bounds__(256) k_loc_finish(const LocTailArgs A)
             __syncthreads();
         }
     }
-    end_stamp(state, 5);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1642,7 +1632,7 @@ void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, uint
     const int grid1 = (int)(tasks < cap ? tasks : cap);
     A.grid_maxima = grid1;
     launch_pdl(k_loc_maxima, grid1, kTailSmem, A, s);
-    launch_pdl(k_loc_votes, P->num_sms * 8, 0, A, s);
+    launch_pdl(k_loc_votes, P->num_sms * 4, 0, A, s);
     launch_pdl(k_loc_finish, P->num_sms * 4, kTailSmem, A, s);
     count_launch(P, 3);
 }

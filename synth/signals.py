@@ -75,10 +75,11 @@ def sparse_signal_1d(n: int, k: int, seed: int, snr_db: float | None = None,
 
 
 def sparse_signal_2d(N: int, k: int, seed: int, snr_db: float | None = None,
-                     mag="unit") -> SparseSignal:
+                     mag="unit", dtype=np.complex64) -> SparseSignal:
     """N x N image whose 2D DFT has exactly k nonzero bins at distinct (u, v).
 
-    The support is returned as linear indices u*N + v (row-major).
+    The support is returned as linear indices u*N + v (row-major); the pixels are
+    computed in FP64 and stored as `dtype` (complex64 by default).
     """
     rng = np.random.default_rng(seed)
     support, coeffs = _spectrum(rng, N * N, k, mag)
@@ -86,7 +87,7 @@ def sparse_signal_2d(N: int, k: int, seed: int, snr_db: float | None = None,
     xhat[support] = coeffs
     x = np.fft.ifft2(xhat.reshape(N, N))
     x, var = _add_noise(rng, x, snr_db)
-    return SparseSignal(x.astype(np.complex64), support, coeffs, var)
+    return SparseSignal(x.astype(dtype), support, coeffs, var)
 
 
 def l1_error_per_coefficient(sig: SparseSignal, loc: np.ndarray, val: np.ndarray) -> float:

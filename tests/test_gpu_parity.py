@@ -312,6 +312,35 @@ def test_fp64_path_values(A, O, n, k, seed, snr):
     assert err < 1e-10, err
 
 
+@pytest.mark.parametrize("N,k,seed,snr", [(256, 10, 4, None), (1024, 100, 5, 30.0)])
+def test_fp64_path_values_2d(A, O, N, k, seed, snr):
+    """The FP64 path on images: locations by the FP32 stages on the rounded input (the
+    parity rule against the oracle on that input), values within 1e-10 of the FP64
+    oracle's on the complex128 input (Eq. (11) in 2D with the separable window)."""
+    import torch
+
+    from synth import sparse_signal_2d
+
+    sig = sparse_signal_2d(N, k, seed, snr_db=snr, mag=("loguniform", 0.1, 1.0),
+                           dtype=np.complex128)
+    plan = A.Plan((N, N), params=A.params(precision=1), seed=7)
+    loc, val, kk, st, cnt = plan(torch.from_numpy(sig.x).cuda(), capacity=1 << 14)
+    assert val.dtype == torch.complex128
+    trace = plan.last_trace()
+    plan.close()
+    ref = O.atsfft_2d(sig.x, seed=7, capacity=1 << 14)
+    ref32, dec = O.atsfft_log(sig.x.astype(np.complex64), seed=7, capacity=1 << 14, band=BAND)
+    loc = loc.cpu().numpy()
+    v = val.cpu().numpy()
+    gpu = dict(trace=trace, k=kk, status=st, count=cnt, loc=loc, val=v.astype(np.complex64))
+    info = check(gpu, ref32, dec, (N, N), 7, capacity=1 << 14)
+    common, ig, ir = np.intersect1d(loc, ref.loc, return_indices=True)
+    assert len(common) > 0
+    err = np.abs(v[ig] - ref.val[ir]).max() / np.abs(ref.val).max()
+    print(f"[fp64 2d] N={N} k*={kk} count={cnt} value err={err:.1e} {info}")
+    assert err < 1e-10, err
+
+
 def test_fp64_plan_rejects_fp32_entries(A):
     """hash_spectrum and the fixed-support estimate map read complex64 input: an FP64
     plan refuses them with an argument error before any launch."""
