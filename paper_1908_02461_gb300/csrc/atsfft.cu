@@ -40,6 +40,7 @@ static atsfft_status exec_common(atsfft_plan_t P, int ndim, const void *d_x, int
         x = P->d_x32;
     }
     launch_reset(P, s);
+    P->pdl = 1;   // the kernels after the reset: programmatic dependent launches
     prof_mark(P, 0, s);
     if (P->p.fixed_k) {
         launch_fixed_setup(P, s);   // B* and k* from the plan: the tuning phases are empty
@@ -58,6 +59,7 @@ static atsfft_status exec_common(atsfft_plan_t P, int ndim, const void *d_x, int
     launch_bucket_fft_dynamic(P, jd, P->d_part, P->d_z, P->d_energy + P->e_loc_off, P->L_loc, s);
     prof_mark(P, 12, s);
     launch_loc_tail(P, d_loc, (float2 *)d_val, d_msel, capacity, d_count, d_k, d_status, s);
+    P->pdl = 0;
     if (fp64) launch_estimate_fp64(P, d_x, d_loc, d_val, capacity, s);
     prof_mark(P, 13, s);
     return cuda_status(cudaGetLastError());

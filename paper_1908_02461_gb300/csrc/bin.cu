@@ -30,6 +30,8 @@ __global__ void k_bin_gather_1d(const float2 *__restrict__ x, int logn, const Ha
                                 int logB_static, const float2 *__restrict__ phase, int phase_s,
                                 float2 *__restrict__ out)
 {
+    chain_wait();
+    chain_next();
     int logB = logB_static;
     if (job_dev) {
         if (!job_dev->active || job_dev->stream) return;
@@ -220,6 +222,8 @@ k_bin_stream(const float2 *__restrict__ x, int logn, const StreamArgs A, const J
              const WindowParam *win, const float2 *__restrict__ phase, int phase_s,
              float2 *__restrict__ part, const int *skip)
 {
+    chain_wait();
+    chain_next();
     extern __shared__ float2 rot[];
     if (skip && *skip) return;
     int logR = A.logR, chunks = A.chunks;
@@ -332,6 +336,8 @@ __global__ void k_bin_gather_tune(const float2 *__restrict__ x, int logn, const 
                                   const float2 *__restrict__ phase, int phase_s,
                                   float2 *__restrict__ part)
 {
+    chain_wait();
+    chain_next();
     const uint32_t n = 1u << logn, mask = n - 1;
     const int lane = threadIdx.x & 31, q = lane & (kTuneLanes - 1);
     constexpr int kPerWarp = 32 / kTuneLanes;
@@ -389,6 +395,8 @@ __global__ void k_bin_gather_tune(const float2 *__restrict__ x, int logn, const 
 __global__ void k_taps_2d(int logn, const HashParam *hashes, int nh, const WindowParam *win,
                           const Job *job_dev, int logB_static, float2 *taps)
 {
+    chain_wait();
+    chain_next();
     int logB = logB_static;
     if (job_dev) {
         if (!job_dev->active) return;
@@ -436,6 +444,8 @@ __global__ void __launch_bounds__(256) k_bin_stream_2d(const float2 *__restrict_
                                                        const float2 *__restrict__ taps,
                                                        float2 *__restrict__ part)
 {
+    chain_wait();
+    chain_next();
     int logB = logB_static, chunks = chunks_static;
     if (job_dev) {
         if (!job_dev->active) return;
@@ -497,6 +507,8 @@ __global__ void k_bin_gather_2d(const float2 *__restrict__ x, int logn, const Ha
                                 int logB_static, const float2 *__restrict__ taps,
                                 float2 *__restrict__ out)
 {
+    chain_wait();
+    chain_next();
     int logB = logB_static;
     if (job_dev) {
         if (!job_dev->active || job_dev->stream) return;
@@ -571,7 +583,7 @@ static void launch_gather_tune(const atsfft_plan_s *P, const float2 *x, const Ga
     const int64_t per_cta = 8 * (32 / kTuneLanes);
     const int64_t blocks = (G.total_buckets + per_cta - 1) / per_cta;
     const int64_t cap = (int64_t)P->num_sms * 8;
-    k_bin_gather_tune<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(
+    launch_k(P, k_bin_gather_tune, dim3((unsigned)(blocks < cap ? blocks : cap)), dim3(256), 0, s, 
         x, P->logn, G, P->d_phase, P->phase_s, P->d_part);
     count_launch(P);
 }
@@ -601,7 +613,7 @@ static void launch_stream(const atsfft_plan_s *P, const float2 *x, const StreamA
 {
     const void *fn = (const void *)k_bin_stream<NH, DYN>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_bin_stream<NH, DYN><<<(unsigned)(P->num_sms * kStreamCtas), kStreamThreads, smem, s>>>(
+    launch_k(P, k_bin_stream<NH, DYN>, dim3((unsigned)(P->num_sms * kStreamCtas)), dim3(kStreamThreads), smem, s, 
         x, P->logn, A, job_dev, P->d_win, P->d_phase, P->phase_s, P->d_part, skip);
     count_launch(P);
 }
@@ -715,7 +727,7 @@ void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
         prof_mark(P, 10, s);
         const int groups = (nh + kGroup - 1) / kGroup;
         dim3 grid(P->num_sms * kPersistCtas, groups);
-        k_bin_gather_1d<<<grid, 256, 0, s>>>(x, P->logn, P->d_le, nh, P->d_win, job_dev, 0,
+        launch_k(P, k_bin_gather_1d, dim3(grid), dim3(256), 0, s, x, P->logn, P->d_le, nh, P->d_win, job_dev, 0,
                                              P->d_phase, P->phase_s, P->d_part);
         count_launch(P);
     } else {
@@ -779,7 +791,7 @@ int launch_est_bin(const atsfft_plan_s *P, const float2 *x, int b, cudaStream_t 
         return j.chunks;
     }
     dim3 grid(P->num_sms * kPersistCtas, (L + kGroup - 1) / kGroup);
-    k_bin_gather_1d<<<grid, 256, 0, s>>>(x, P->logn, P->d_le + P->est_base, L, P->d_win, nullptr, b,
+    launch_k(P, k_bin_gather_1d, dim3(grid), dim3(256), 0, s, x, P->logn, P->d_le + P->est_base, L, P->d_win, nullptr, b,
                                          P->d_phase, P->phase_s, P->d_part);
     count_launch(P);
     return 1;
@@ -793,19 +805,19 @@ void launch_bin_2d(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
     const int groups = (job_host.nh + kGroup - 1) / kGroup;
     const Job *jd = dynamic ? job_dev : nullptr;
     float2 *taps = P->d_fft_tmp;   // per-axis tap tables: nh x 2 x N
-    k_taps_2d<<<P->num_sms * 2, 256, 0, s>>>(P->logn, hashes, job_host.nh, P->d_win, jd,
+    launch_k(P, k_taps_2d, dim3(P->num_sms * 2), dim3(256), 0, s, P->logn, hashes, job_host.nh, P->d_win, jd,
                                               logB_static, taps);
     count_launch(P);
     if (dynamic || job_host.stream) {
         dim3 grid(persist, groups);
-        k_bin_stream_2d<<<grid, 256, 0, s>>>(x, P->logn, job_host.nh, jd, logB_static,
+        launch_k(P, k_bin_stream_2d, dim3(grid), dim3(256), 0, s, x, P->logn, job_host.nh, jd, logB_static,
                                              job_host.chunks, taps, part);
         count_launch(P);
     }
     if (dynamic) prof_mark(P, 10, s);
     if (dynamic || !job_host.stream) {
         dim3 grid(persist, job_host.nh);
-        k_bin_gather_2d<<<grid, 256, 0, s>>>(x, P->logn, hashes, job_host.nh, P->d_win, jd,
+        launch_k(P, k_bin_gather_2d, dim3(grid), dim3(256), 0, s, x, P->logn, hashes, job_host.nh, P->d_win, jd,
                                              logB_static, taps, part);
         count_launch(P);
     }

@@ -189,6 +189,9 @@ struct atsfft_plan_s {
     atsfft::StatJob *d_lstat;     // location stat jobs (written by the controller)
     int ntstat;
 
+    // 1 while an exec is being enqueued: its kernels after the reset are launched with
+    // programmatic stream serialization (each waits for its predecessor at its top)
+    mutable int pdl;
     // profiling: events at phase boundaries (when enabled) and a launch counter
     int prof;
     cudaEvent_t ev[atsfft::kPhases + 1];
@@ -210,6 +213,34 @@ inline void prof_mark(const atsfft_plan_s *P, int i, cudaStream_t s)
     if (P->prof) cudaEventRecord(P->ev[i], s);
 }
 inline void count_launch(const atsfft_plan_s *P, int k = 1) { P->launches += k; }
+
+// Programmatic dependent launch inside an exec.  Every kernel of the exec chain starts
+// with chain_wait(): it touches no memory before the kernel ahead of it in the stream has
+// completed (exactly the order of a plain launch), but its blocks can be scheduled while
+// that kernel finishes; chain_next() lets the next kernel's blocks be scheduled.  Both
+// return at once in a kernel launched without the dependency.
+__device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void chain_next()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(const atsfft_plan_s *P, void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                            size_t smem, cudaStream_t s, Args &&...args)
+{
+    cudaLaunchConfig_t cfg;
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = P->pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
 
 inline int stats_slot_tune(int logB) { return logB; }
 inline int stats_slot_loc(int l) { return kMaxLogB + l; }

@@ -398,6 +398,8 @@ __global__ void __launch_bounds__(kFftThreads, kPassCtas) k_fft_pass(int ndim, i
                                                   float2 *fin, const float2 *__restrict__ tw,
                                                   float *energy, HashStats *stats, int n_energy)
 {
+    chain_wait();
+    chain_next();
     __shared__ float2 sm[kSmemPadded];
     if (!job->active) return;
     const int logB = job->logB, nh = job->nh;
@@ -449,6 +451,8 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_fft_batch(int ndim, int pass
                                                    float *energy, HashStats *stats,
                                                    const int *skip)
 {
+    chain_wait();
+    chain_next();
     __shared__ float2 sm[kSmemPadded];
     if (skip && *skip) return;
     for (int64_t tr = blockIdx.x; tr < Bt.total; tr += gridDim.x) {
@@ -476,11 +480,11 @@ void launch_bucket_fft_dynamic(const atsfft_plan_s *P, const Job *job, const flo
                                float2 *out, float *energy, int n_energy, cudaStream_t s)
 {
     const int grid = P->num_sms * kPassCtas;   // resident CTAs; a grid-stride loop covers the tiles
-    k_fft_pass<<<grid, kFftThreads, 0, s>>>(P->ndim, 0, job, part, P->d_fft_tmp, out, P->d_tw,
+    launch_k(P, k_fft_pass, dim3(grid), dim3(kFftThreads), 0, s, P->ndim, 0, job, part, P->d_fft_tmp, out, P->d_tw,
                                             energy, P->d_stats, n_energy);
     count_launch(P);
     if (P->ndim == 2 || P->b_hi > kSinglePassLog) {
-        k_fft_pass<<<grid, kFftThreads, 0, s>>>(P->ndim, 1, job, part, P->d_fft_tmp, out, P->d_tw,
+        launch_k(P, k_fft_pass, dim3(grid), dim3(kFftThreads), 0, s, P->ndim, 1, job, part, P->d_fft_tmp, out, P->d_tw,
                                                 energy, P->d_stats, n_energy);
         count_launch(P);
     }
@@ -542,7 +546,7 @@ void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB,
         if (Bt.njobs == 0) continue;
         const int64_t cap = (int64_t)P->num_sms * 2;
         const int64_t grid = Bt.total < cap ? Bt.total : cap;
-        k_fft_batch<<<(unsigned)grid, kFftThreads, 0, s>>>(P->ndim, pass, Bt, part, P->d_fft_tmp, out,
+        launch_k(P, k_fft_batch, dim3((unsigned)grid), dim3(kFftThreads), 0, s, P->ndim, pass, Bt, part, P->d_fft_tmp, out,
                                                    P->d_tw, energy, P->d_stats, skip);
         count_launch(P);
     }

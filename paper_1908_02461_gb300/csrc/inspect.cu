@@ -9,6 +9,7 @@ namespace atsfft {
 __global__ void k_reset(uint32_t *stats, int64_t stats_words, uint32_t *state, int64_t state_words,
                         uint32_t *chunks, int64_t nchunks)
 {
+    chain_next();   // (launched plainly: the exec's first kernel follows whatever came before)
     const int64_t total = stats_words + state_words + nchunks;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {

@@ -585,6 +585,8 @@ __device__ void controller(const TuneTailArgs &A)
 // Fixed-k mode: B* and k* come from the plan (no trials); one thread.
 __global__ void k_fixed_setup(const TuneTailArgs A, int b, int64_t k)
 {
+    chain_wait();
+    chain_next();
     if (blockIdx.x == 0 && threadIdx.x == 0) publish_bstar(A, b, k, A.state->status, 0, 0);
 }
 
@@ -613,6 +615,7 @@ __device__ __noinline__ void settle_trial_median(const JobView &J, const StatsPa
 __global__ void __launch_bounds__(256) k_tune_tail(const TuneTailArgs A)
 {
     pdl_wait();
+    pdl_launch_next();
     ExecState *state = A.state;
     if (A.stage >= 2 && state->tune_done) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) stamp(&state->bar);
@@ -1544,7 +1547,7 @@ static TuneTailArgs tune_args(const atsfft_plan_s *P)
 void launch_fixed_setup(const atsfft_plan_s *P, cudaStream_t s)
 {
     const TuneTailArgs A = tune_args(P);
-    k_fixed_setup<<<1, 32, 0, s>>>(A, P->b_fixed, P->k_hint);
+    launch_k(P, k_fixed_setup, dim3(1), dim3(32), 0, s, A, P->b_fixed, P->k_hint);
     count_launch(P);
 }
 
