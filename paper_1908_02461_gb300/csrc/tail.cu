@@ -1,9 +1,10 @@
 // tail.cu -- everything after the bucket FFTs, with no grid-wide barrier: every step
 // that needs all the results of the previous one is either a new kernel (chained with
 // programmatic dependent launch, so its blocks are scheduled while the previous kernel
-// finishes) or is run by the block that completes the last unit of work it depends on
+// finishes), or is run by the block that completes the last unit of work it depends on
 // (a completion counter per hash and per launch: the block whose count is the last one
-// goes on, nobody waits).
+// goes on, nobody waits), or stays inside one thread-block cluster (whose CTAs are
+// scheduled together: a hardware cluster barrier).
 //
 //   k_tune_tail  : threshold and local-maximum counts of the trials of one tuning stage
 //                  (Section III-A; the energies and their maxima come from the bucket
@@ -11,11 +12,13 @@
 //                  the last block of the launch walks the controller over Eqs. (12)/(14)
 //                  (Algorithm 2), which fixes B*, k* and the jobs at B* (or leaves the walk
 //                  to the next stage).
-//   k_loc_maxima : the same statistics for the location hashes at B*, with the maxima
-//                  listed; the last block of each hash makes its top-num cutoff (Algorithm
-//                  1 "find num largest") and its bitmap of selected buckets.
+//   k_loc_select : the same statistics for the location hashes at B*, one thread-block
+//                  cluster per hash: its CTAs gather the maxima in the shared memory of the
+//                  first one (distributed shared memory), which makes the top-num cutoff
+//                  (Algorithm 1 "find num largest") and the bitmap of selected buckets.
 //   k_loc_votes  : votes (reverse hash): the preimages of the selected buckets that lie in
-//                  >= ceil(L_loc/2) selected buckets are kept (Section II-B).
+//                  >= ceil(L_loc/2) selected buckets are kept (Section II-B); one CTA per
+//                  SM with the bitmaps in shared memory.
 //   k_loc_finish : the kept coordinates in ascending order, the estimates of Eq. (11) with
 //                  their componentwise median, and the caller's status words.
 //
@@ -91,16 +94,16 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t v)
 
 constexpr int64_t kTask = 4096;   // buckets per statistics task
 
+// Whole block (blockDim.x <= 1024, a multiple of 32): the sum of one value per thread.
 __device__ uint32_t block_sum(uint32_t v)
 {
-    __shared__ uint32_t red[8];
+    __shared__ uint32_t red[32];
+    const int lane = threadIdx.x & 31;
     v = warp_sum(v);
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    if (lane == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    uint32_t t = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += red[i];
-    return t;
+    return warp_sum(lane < (int)(blockDim.x >> 5) ? red[lane] : 0u);
 }
 
 // Does a bucket of energy ec dominate its neighbour (displacement d1, d2) of energy em?
@@ -139,55 +142,60 @@ __device__ __forceinline__ void hist_add(uint32_t *hist, uint32_t bin)
     if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
 }
 
-// Whole block (blockDim.x = 256): exclusive prefix sum of one value per thread;
-// *total (shared) receives the block sum.
-__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total)
+// Inclusive prefix sum over the lanes of a warp.
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
 {
-    __shared__ uint32_t wtot[8];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t incl = v;
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += u;
+        const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
     }
+    return v;
+}
+
+// Whole block (blockDim.x <= 1024, a multiple of 32): exclusive prefix sum of one value
+// per thread and the block total, with one barrier (the warp totals are scanned by every
+// warp at once, a lane per warp total).  The caller synchronises before the next call.
+__device__ __forceinline__ uint32_t block_scan_core(uint32_t v, uint32_t &all)
+{
+    __shared__ uint32_t wtot[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t incl = warp_incl_scan(v);
     if (lane == 31) wtot[w] = incl;
     __syncthreads();
-    uint32_t before = incl - v;
-    uint32_t all = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
-        if (i < w) before += wtot[i];
-        all += wtot[i];
-    }
+    const uint32_t t = lane < (int)(blockDim.x >> 5) ? wtot[lane] : 0u;
+    const uint32_t tincl = warp_incl_scan(t);
+    all = __shfl_sync(0xffffffffu, tincl, 31);
+    return incl - v + __shfl_sync(0xffffffffu, tincl - t, w);
+}
+
+// Whole block: exclusive prefix sum of one value per thread; *total (shared) receives the
+// block sum.
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total)
+{
+    uint32_t all;
+    const uint32_t before = block_scan_core(v, all);
     if (total && threadIdx.x == 0) *total = all;
     __syncthreads();
     return before;
 }
 
-// Whole block (blockDim.x = 256): find the bin b of hist[0..nbins) (shared or global)
-// with cum(b) <= rank < cum(b) + hist[b], where cum is the exclusive prefix sum.  The
-// block's thread t sums bins [t*per, (t+1)*per); a warp-shuffle scan gives each thread
-// its offset; the owner walks its few bins.  Result in *bin, *rem (shared), after a sync.
+// Whole block (blockDim.x <= 1024, a multiple of 32; nbins a power of two): find the
+// bin b of hist[0..nbins) (shared or global) with cum(b) <= rank < cum(b) + hist[b],
+// where cum is the exclusive prefix sum.  The block's thread t sums bins
+// [t*per, (t+1)*per); a block scan gives each thread its offset; the owner walks its few
+// bins.  Result in *bin, *rem (shared), after a sync.
 __device__ void block_find_rank(const uint32_t *hist, int nbins, uint32_t rank, uint32_t *bin,
                                 uint32_t *rem)
 {
-    __shared__ uint32_t wtot[8];
-    const int per = nbins >= 256 ? nbins / 256 : 1;
+    const int per = nbins >= (int)blockDim.x ? nbins / (int)blockDim.x : 1;
     const int t = threadIdx.x;
     uint32_t sum = 0;
     if (t * per < nbins)
         for (int k = 0; k < per; k++) sum += hist[t * per + k];
-    const int lane = t & 31, w = t >> 5;
-    uint32_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) wtot[w] = incl;
-    __syncthreads();
-    uint32_t before = incl - sum;
-    for (int i = 0; i < w; i++) before += wtot[i];
+    uint32_t all;
+    const uint32_t before = block_scan_core(sum, all);
     if (sum && rank >= before && rank < before + sum) {
         uint32_t cum = before;
         for (int k = 0; k < per; k++) {
@@ -269,39 +277,42 @@ struct JobView {
     uint32_t s1, p1, s2, p2;   // sigma and sigma^{-1} mod B per axis
 };
 
-// Local maxima of buckets [e0, e1) of one job by the whole block (e1 - e0 <= 16 x 256):
-// thread t tests P-indices e0 + t + 256 u, u < 16, from energies loaded up front; the
-// block's maxima are appended with one atomic, and the count of energies above X with
-// another.
-__device__ void localmax_task(const JobView &J, const StatsParams &S, float T, int64_t e0,
-                              int64_t e1, float X)
+constexpr int kPerTask = (int)(kTask / 256);   // buckets per thread of a statistics task
+
+// The local-maximum test of P-indices [e0, e1) of one job by a block of NT threads
+// (e1 - e0 <= 16 NT): thread t tests e0 + t + NT u, u < 16, from energies loaded up front
+// (ev[u]); bit u of `found` marks a maximum above T, `above` counts the thread's energies
+// above X.
+template <int NT>
+__device__ __forceinline__ void localmax_scan(const JobView &J, const StatsParams &S, float T,
+                                              int64_t e0, int64_t e1, float X,
+                                              float (&ev)[kPerTask], uint32_t &found,
+                                              uint32_t &above)
 {
-    constexpr int kPer = (int)(kTask / 256);
-    HashStats &st = *J.st;
     const int logB = J.logB;
     const uint32_t mask = (1u << logB) - 1;
     const float *__restrict__ E = J.E;
-    const uint32_t s1 = J.s1, p1 = J.p1, s2 = J.s2, p2 = J.p2;
-    float ev[kPer];
+    const uint32_t p1 = J.p1, p2 = J.p2;
 #pragma unroll
-    for (int u = 0; u < kPer; u++) {
-        const int64_t j = e0 + threadIdx.x + 256 * u;
+    for (int u = 0; u < kPerTask; u++) {
+        const int64_t j = e0 + threadIdx.x + NT * u;
         ev[u] = j < e1 ? __ldg(&E[j]) : 0.f;
     }
-    uint32_t above = 0, found = 0;
+    above = 0;
+    found = 0;
     if (S.ndim == 1) {
         // both neighbours of every element requested at once (coalesced: consecutive
         // threads hold consecutive P-indices)
-        float el[kPer], er[kPer];
+        float el[kPerTask], er[kPerTask];
 #pragma unroll
-        for (int u = 0; u < kPer; u++) {
-            const uint32_t jj = (uint32_t)(e0 + threadIdx.x + 256 * u);
+        for (int u = 0; u < kPerTask; u++) {
+            const uint32_t jj = (uint32_t)(e0 + threadIdx.x + NT * u);
             el[u] = __ldg(&E[(jj - p1) & mask]);
             er[u] = __ldg(&E[(jj + p1) & mask]);
         }
 #pragma unroll
-        for (int u = 0; u < kPer; u++) {
-            const int64_t j = e0 + threadIdx.x + 256 * u;
+        for (int u = 0; u < kPerTask; u++) {
+            const int64_t j = e0 + threadIdx.x + NT * u;
             const float e = ev[u];
             above += j < e1 && e > X;
             if (j < e1 && e > T && dominates(e, el[u], S.up, 0, -1) && dominates(e, er[u], S.up, 0, 1))
@@ -310,11 +321,11 @@ __device__ void localmax_task(const JobView &J, const StatsParams &S, float T, i
     } else {
         // eight neighbours, four elements at a time
 #pragma unroll
-        for (int u0 = 0; u0 < kPer; u0 += 4) {
+        for (int u0 = 0; u0 < kPerTask; u0 += 4) {
             float nbv[4][8];
 #pragma unroll
             for (int v = 0; v < 4; v++) {
-                const int64_t j = e0 + threadIdx.x + 256 * (u0 + v);
+                const int64_t j = e0 + threadIdx.x + NT * (u0 + v);
                 const uint32_t jA = (uint32_t)(j >> logB) & mask, jB = (uint32_t)(j & mask);
                 int q = 0;
 #pragma unroll
@@ -330,7 +341,7 @@ __device__ void localmax_task(const JobView &J, const StatsParams &S, float T, i
 #pragma unroll
             for (int v = 0; v < 4; v++) {
                 const int u = u0 + v;
-                const int64_t j = e0 + threadIdx.x + 256 * u;
+                const int64_t j = e0 + threadIdx.x + NT * u;
                 const float e = ev[u];
                 above += j < e1 && e > X;
                 if (!(j < e1 && e > T)) continue;
@@ -348,6 +359,27 @@ __device__ void localmax_task(const JobView &J, const StatsParams &S, float T, i
             }
         }
     }
+}
+
+// Bucket index of P-index j of a job (c = sigma j mod B, per axis).
+__device__ __forceinline__ int32_t bucket_of_pindex(const JobView &J, int ndim, int64_t j)
+{
+    const uint32_t mask = (1u << J.logB) - 1;
+    if (ndim == 1) return (int32_t)((J.s1 * (uint32_t)j) & mask);
+    const uint32_t jA = (uint32_t)(j >> J.logB), jB = (uint32_t)(j & mask);
+    return (int32_t)((((J.s1 * jA) & mask) << J.logB) | ((J.s2 * jB) & mask));
+}
+
+// Local maxima of buckets [e0, e1) of one job by a block of 256 threads
+// (e1 - e0 <= kTask): the block's maxima are appended to the job's list with one atomic,
+// and the count of energies above X with another.
+__device__ void localmax_task(const JobView &J, const StatsParams &S, float T, int64_t e0,
+                              int64_t e1, float X)
+{
+    HashStats &st = *J.st;
+    float ev[kPerTask];
+    uint32_t found, above;
+    localmax_scan<256>(J, S, T, e0, e1, X, ev, found, above);
     __shared__ uint32_t base_sh;
     uint32_t total;
     const uint32_t before = block_exclusive_scan((uint32_t)__popc(found), &total);
@@ -361,16 +393,10 @@ __device__ void localmax_task(const JobView &J, const StatsParams &S, float T, i
         uint32_t pos = base_sh + before;
         int32_t *lst = S.lists + (int64_t)J.list * S.cap;
 #pragma unroll
-        for (int u = 0; u < kPer; u++) {
+        for (int u = 0; u < kPerTask; u++) {
             if (!(found & (1u << u))) continue;
             const int64_t j = e0 + threadIdx.x + 256 * u;
-            int32_t c;
-            if (S.ndim == 1) {
-                c = (int32_t)((s1 * (uint32_t)j) & mask);
-            } else {
-                const uint32_t jA = (uint32_t)(j >> logB), jB = (uint32_t)(j & mask);
-                c = (int32_t)((((s1 * jA) & mask) << logB) | ((s2 * jB) & mask));
-            }
+            const int32_t c = bucket_of_pindex(J, S.ndim, j);
             if (pos < S.cap) {
                 lst[pos] = c;
                 S.list_e[(int64_t)J.list * S.cap + pos] = ev[u];
@@ -674,8 +700,8 @@ struct LocTailArgs {
     int64_t coord_words;
     uint32_t *chunkcnt;     // kept coordinates per kChunkWords-word chunk of coordbits
     int64_t nchunks;
-    int grid_maxima;        // blocks of k_loc_maxima
-    const HashParam *le;    // location then estimation hashes
+    int64_t vote_words;     // bitmap words k_loc_votes stages in shared memory (0: none)
+    HashParam est[kMaxLoops];   // the estimation hashes (by value)
     const float2 *z;        // spectra at B*: location then estimation hashes
     const float *rgain;     // 1 / Ghat' per B (offsets ro)
     RespOffsets ro;
@@ -838,7 +864,7 @@ __device__ float2 estimate_term(uint64_t coord, const LocTailArgs &A, int b, int
     const int64_t nb = nb_of(A.S.ndim, b);
     const float2 *Pz = A.z + (int64_t)(A.est_base + l) * nb;
     int64_t idx;
-    const float2 c = estimate_coef(coord, A.le[A.est_base + l], A.S.ndim, A.logn, b,
+    const float2 c = estimate_coef(coord, A.est[l], A.S.ndim, A.logn, b,
                                    A.rgain + A.ro.off[b], A.phase, A.phase_s, &idx);
     return cmul(Pz[idx], c);
 }
@@ -882,10 +908,13 @@ __device__ __forceinline__ uint32_t bucket_of(uint32_t i, uint32_t sigma, int lo
 }
 
 constexpr int kRankStage = 4096;   // top-num by ranking: candidates staged in shared memory
-constexpr uint32_t kBandRank = 128; // band sizes ranked by counting (larger: radix select)
 constexpr int kPivots = 32;   // one warp: lane p holds pivot p
-constexpr int kVoteUnroll = 8;     // location hashes whose bitmap words are fetched together
-constexpr int kVoteIlp = 4;        // candidates per thread per round of the votes
+constexpr int kSelCluster = 8;     // CTAs per location hash in k_loc_select (one cluster)
+constexpr int kSelThreads = 512;   // threads per CTA of k_loc_select
+constexpr int64_t kSelTask = kTask * kSelThreads / 256;   // buckets per task of k_loc_select
+constexpr int kVoteThreads = 1024; // k_loc_votes: one CTA per SM
+constexpr int kVoteIlp = 2;        // candidates per thread per round of the votes
+constexpr int kVoteSmem = 96 * 1024;   // largest bitmap staging of k_loc_votes (bytes)
 
 // Value of descending rank r (0-based; equal values ordered by index) among es[0..cnt),
 // by the whole block.  kPivots sampled values are counted against all elements (every
@@ -1013,35 +1042,232 @@ __device__ int64_t filter_list(int32_t *list, float *list_e, int64_t cnt, float 
     return base;
 }
 
-// The location step of hash l at B* = 2^b once all its local maxima are listed, by one
-// block: the exact median where it can matter (it raises the threshold, and the listed
-// maxima below the new one drop out); then the top-num cutoff (Algorithm 1 "find num
-// largest"): V = the num-th largest maximum energy, keep every maximum above V(1+eta) and
-// fill up from the band [V(1-eta), V(1+eta)] in ascending bucket order; the kept buckets
-// go to the hash's selection list and bitmap.
-__device__ __noinline__ void cutoff_hash(const LocTailArgs &A, int l, int b, int64_t num)
+// Thread-block clusters: rank and size of the calling CTA's cluster, shared-memory
+// addresses in another CTA of the cluster (distributed shared memory) and the cluster
+// barrier, split into arrive and wait.
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_nctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(r)
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, uint32_t v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t atom_add_cluster(uint32_t addr, uint32_t v)
+{
+    uint32_t old;
+    asm volatile("atom.shared::cluster.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(addr), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void red_add_cluster(uint32_t addr, uint32_t v)
+{
+    asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+// (release: this thread's earlier memory operations, shared, distributed shared and
+// global, are visible to the cluster's threads after their matching wait)
+__device__ __forceinline__ void cluster_arrive()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait()
+{
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Layout of the dynamic shared memory of k_loc_select (words): the gathered maxima, energy
+// bits es[0, kRankStage) and buckets cs[kRankStage, 2 kRankStage); an auxiliary region
+// aux[2 kRankStage, 3 kRankStage): the coarse and the fine energy histograms (kDigitBins
+// words each), later the band list; and the band bitmap [3 kRankStage, 4 kRankStage).
+constexpr int kDigitBins = 2048;
+static_assert(2 * kDigitBins <= kRankStage, "both histograms fit the auxiliary region");
+constexpr size_t kSelSmem = sizeof(uint32_t) * 4 * kRankStage;
+
+// Selection key of a maximum of energy e below the hash's maximum energy maxE (both > 0:
+// their bit patterns order like their values): key = bits(maxE) - bits(e), ascending
+// with descending energy; its coarse digit is key >> 16, clamped to the last bin.
+__device__ __forceinline__ uint32_t coarse_digit(uint32_t key)
+{
+    return min(key >> 16, (uint32_t)kDigitBins - 1);
+}
+
+// Top-num cutoff of location hash l (Algorithm 1 "find num largest") from its cnt local
+// maxima staged in shared memory (cnt <= kRankStage, cnt > num), by one block: V = the
+// num-th largest energy; every maximum above V(1+eta) is kept and the band
+// [V(1-eta), V(1+eta)] fills up in ascending bucket order.  The kept buckets go to the
+// hash's selection list and bitmap (cleared before).  V is found from the coarse digit
+// histogram (have_hist: summed by the cluster while the maxima were gathered, and the
+// fine histograms and band bitmap already zero; else built here), one fine pass over the
+// 11 digits below the coarse one and a 32-bin pass over the last 5 bits; the band's
+// cutoff bucket from a bitmap of the band buckets by a block prefix popcount.
+__device__ __noinline__ void cutoff_staged(const LocTailArgs &A, int l, int b, int64_t num, int cnt,
+                                           uint32_t mbits, bool have_hist)
 {
     extern __shared__ __align__(16) uint32_t dsm[];
     const int ndim = A.S.ndim;
     const int lane = threadIdx.x & 31;
+    HashStats &st = A.S.stats[kMaxLogB + l];
+    uint32_t *bits = A.bucketbits + (int64_t)l * A.bucket_words;
+    int32_t *out = A.sel + (int64_t)l * A.S.cap;
+    const uint32_t *eb = dsm;   // energy bits
+    const float *es = reinterpret_cast<const float *>(dsm);
+    const uint32_t *cs = dsm + kRankStage;   // buckets
+    uint32_t *aux = dsm + 2 * kRankStage;
+    uint32_t *h1 = aux, *h2 = aux + kDigitBins;
+    uint32_t *bandbits = dsm + 3 * kRankStage;
+    const int64_t words = (nb_of(ndim, b) + 31) >> 5;
+    const bool use_bitmap = words <= kRankStage;
+    __shared__ uint32_t n_sel, nband, fb, fr, cthr;
+    __shared__ uint32_t h3[32];
+    if (threadIdx.x == 0) {
+        n_sel = 0;
+        nband = 0;
+    }
+    if (threadIdx.x < 32) h3[threadIdx.x] = 0;
+    if (!have_hist) {
+        for (int i = threadIdx.x; i < 2 * kDigitBins; i += blockDim.x) h1[i] = 0;   // h1, h2
+        if (use_bitmap)
+            for (int64_t w = threadIdx.x; w < words; w += blockDim.x) bandbits[w] = 0u;
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) hist_add(h1, coarse_digit(mbits - eb[i]));
+        __syncthreads();
+    }
+    // V: the key of ascending rank num - 1
+    const uint32_t r = (uint32_t)(num - 1);
+    block_find_rank(h1, kDigitBins, r, &fb, &fr);
+    const uint32_t beta = fb, r1 = fr;
+    float V;
+    if (beta == (uint32_t)kDigitBins - 1) {
+        // (V more than 2^-16 below maxE: the clamped bin, only with a threshold far below
+        // the default) the generic selection
+        V = block_select_desc(es, cnt, r, aux);
+    } else {
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const uint32_t key = mbits - eb[i];
+            if ((key >> 16) == beta) hist_add(h2, (key >> 5) & (kDigitBins - 1));
+        }
+        __syncthreads();
+        block_find_rank(h2, kDigitBins, r1, &fb, &fr);
+        const uint32_t pre = (beta << 11) | fb, r2 = fr;
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const uint32_t key = mbits - eb[i];
+            if ((key >> 5) == pre) hist_add(h3, key & 31u);
+        }
+        __syncthreads();
+        // every warp reads the 32 bins and finds the one of rank r2
+        const uint32_t v = h3[lane];
+        const uint32_t incl = warp_incl_scan(v);
+        const unsigned at = __ballot_sync(0xffffffffu, v && r2 >= incl - v && r2 < incl);
+        V = __uint_as_float(mbits - ((pre << 5) | (uint32_t)(__ffs(at) - 1)));
+    }
+    const float hi = V * A.eta_up, lo = V * A.eta_dn;
+    uint32_t mine = 0;
+    for (int i0 = 0; i0 < cnt; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const float e = i < cnt ? es[i] : 0.f;
+        mine += i < cnt && e > hi;
+        const bool in = i < cnt && e >= lo && e <= hi;
+        if (use_bitmap) {
+            if (in) atomicOr(&bandbits[cs[i] >> 5], 1u << (cs[i] & 31));
+        } else {
+            // the band's buckets listed (one shared atomic per warp)
+            const unsigned bal = __ballot_sync(0xffffffffu, in);
+            uint32_t base = 0;
+            if (lane == 0 && bal) base = atomicAdd(&nband, (uint32_t)__popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (in) aux[base + __popc(bal & ((1u << lane) - 1))] = cs[i];
+        }
+    }
+    const uint32_t nhi = block_sum(mine);   // (synchronises: the band complete)
+    const uint32_t need_band = (uint32_t)num - nhi;   // >= 1: V itself is in the band
+    // the need_band-th smallest band bucket
+    uint32_t ct;
+    if (use_bitmap) {
+        const int64_t per = words >= (int64_t)blockDim.x ? words / blockDim.x : 1;
+        const int64_t w0 = (int64_t)threadIdx.x * per;
+        uint32_t sum = 0;
+        if (w0 < words)
+            for (int64_t k = 0; k < per; k++) sum += __popc(bandbits[w0 + k]);
+        uint32_t all;
+        const uint32_t before = block_scan_core(sum, all);
+        const uint32_t rk = need_band - 1;
+        if (sum && rk >= before && rk < before + sum) {
+            uint32_t cum = before;
+            for (int64_t k = 0; k < per; k++) {
+                const uint32_t w = bandbits[w0 + k], pc = (uint32_t)__popc(w);
+                if (rk < cum + pc) {
+                    cthr = (uint32_t)(w0 + k) * 32u + __fns(w, 0, (int)(rk - cum) + 1);
+                    break;
+                }
+                cum += pc;
+            }
+        }
+        __syncthreads();
+        ct = cthr;
+    } else {
+        const uint32_t nbd = nband;
+        const int kbits = ndim == 1 ? b : 2 * b;   // bucket indices < B (B^2 in 2D)
+        if (kbits <= 22)
+            ct = block_kth_narrow((int)nbd, need_band - 1, kbits, [&](int i) { return aux[i]; });
+        else
+            ct = block_kth((int64_t)nbd, need_band - 1, [&](int64_t i) { return aux[i]; },
+                           [](int64_t) { return true; });
+    }
+    for (int i0 = 0; i0 < cnt; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        bool keep = false;
+        uint32_t c = 0;
+        if (i < cnt) {
+            const float e = es[i];
+            c = cs[i];
+            keep = e > hi || (e >= lo && e <= hi && c <= ct);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        uint32_t base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&n_sel, (uint32_t)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) {
+            out[base + __popc(bal & ((1u << lane) - 1))] = (int32_t)c;
+            atomicOr(&bits[c >> 5], 1u << (c & 31));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st.nsel = n_sel;
+}
+
+// The cutoff of hash l from its maxima list in global memory (cnt entries), by one
+// block: the rare paths of k_loc_select.  With `median` the exact median first (it can
+// only matter when more than half of the energies exceed X: it may raise the threshold,
+// and the listed maxima below the new one drop out); more maxima than kRankStage go to
+// the radix selection over the list; otherwise the list is staged and cut as usual.
+__device__ __noinline__ void cutoff_global(const LocTailArgs &A, int l, int b, int64_t num,
+                                           int64_t cnt, bool median)
+{
+    extern __shared__ __align__(16) uint32_t dsm[];
+    const int ndim = A.S.ndim;
     const int64_t nb = nb_of(ndim, b);
     HashStats &st = A.S.stats[kMaxLogB + l];
     int32_t *list = A.S.lists + (int64_t)l * A.S.cap;
     float *list_e = A.S.list_e + (int64_t)l * A.S.cap;
     uint32_t *bits = A.bucketbits + (int64_t)l * A.bucket_words;
     int32_t *out = A.sel + (int64_t)l * A.S.cap;
-    __shared__ uint32_t sh_cnt, sh_above, n_sel;
-    // clear this hash's bitmap (only this block writes it)
-    const int64_t words = (nb + 31) >> 5;
-    for (int64_t w = threadIdx.x; w < words; w += blockDim.x) bits[w] = 0u;
-    if (threadIdx.x == 0) {
-        sh_cnt = __ldcg(&st.nmax);
-        sh_above = __ldcg(&st.above);
-        n_sel = 0;
-    }
-    __syncthreads();
-    int64_t cnt = min((int64_t)sh_cnt, A.S.cap);
-    if (A.S.use_median && (int64_t)sh_above > nb - nb / 2 - 1) {
+    cnt = min(cnt, A.S.cap);
+    if (median) {
         const uint32_t m = block_median_global(A.e_loc + (int64_t)l * nb, nb);
         const float T = fmaxf(A.S.thr_rel * __uint_as_float(__ldcg(&st.max_bits)),
                               A.S.thr_med * __uint_as_float(m));
@@ -1073,94 +1299,12 @@ __device__ __noinline__ void cutoff_hash(const LocTailArgs &A, int l, int b, int
         }
         return;
     }
-    float *es = reinterpret_cast<float *>(dsm);   // kRankStage energies
-    uint32_t *cs = dsm + kRankStage;              // kRankStage buckets
-    uint32_t *band = dsm + 2 * kRankStage;        // band buckets / bracket members
-    // staged eight per thread at a time: the buckets and their energies (listed together
-    // by the local-maximum search)
-    for (int64_t i0 = 0; i0 < cnt; i0 += 8 * blockDim.x) {
-        uint32_t cc[8];
-        float ee[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            const int64_t i = i0 + u * blockDim.x + threadIdx.x;
-            cc[u] = i < cnt ? (uint32_t)__ldcg(&list[i]) : 0u;
-            ee[u] = i < cnt ? __ldcg(&list_e[i]) : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            const int64_t i = i0 + u * blockDim.x + threadIdx.x;
-            if (i < cnt) {
-                cs[i] = cc[u];
-                es[i] = ee[u];
-            }
-        }
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        dsm[kRankStage + i] = (uint32_t)__ldcg(&list[i]);
+        dsm[i] = __float_as_uint(__ldcg(&list_e[i]));
     }
     __syncthreads();
-    const float V = block_select_desc(es, (int)cnt, (uint32_t)(num - 1), band);
-    const float hi = V * A.eta_up, lo = V * A.eta_dn;
-    __shared__ uint32_t nband;
-    if (threadIdx.x == 0) nband = 0;
-    __syncthreads();
-    uint32_t mine = 0;
-    for (int64_t i0 = 0; i0 < cnt; i0 += blockDim.x) {
-        // one shared atomic per warp (a unit-magnitude spectrum puts most maxima in the
-        // band: per-element atomics on one counter serialise)
-        const int64_t i = i0 + threadIdx.x;
-        const float e = i < cnt ? es[i] : 0.f;
-        mine += i < cnt && e > hi;
-        const bool in = i < cnt && e >= lo && e <= hi;
-        const unsigned bal = __ballot_sync(0xffffffffu, in);
-        uint32_t base = 0;
-        if (lane == 0 && bal) base = atomicAdd(&nband, (uint32_t)__popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (in) band[base + __popc(bal & ((1u << lane) - 1))] = cs[i];
-    }
-    const uint32_t nhi = block_sum(mine);   // (synchronises: nband complete)
-    const uint32_t need_band = (uint32_t)num - nhi;
-    // the need_band-th smallest band bucket (distinct indices): by rank counting in a
-    // small band, by radix selection in a large one (unit-magnitude spectra put most
-    // kept maxima inside the band)
-    __shared__ uint32_t cthr;
-    const uint32_t nbd = nband;
-    uint32_t ct;
-    if (nbd <= kBandRank) {
-        for (uint32_t i = threadIdx.x; i < nbd; i += blockDim.x) {
-            const uint32_t c = band[i];
-            uint32_t r = 0;
-            for (uint32_t j = 0; j < nbd; j++) r += band[j] < c;
-            if (r == need_band - 1) cthr = c;
-        }
-        __syncthreads();
-        ct = cthr;
-    } else {
-        const int kbits = ndim == 1 ? b : 2 * b;   // bucket indices < B (B^2 in 2D)
-        if (kbits <= 22)
-            ct = block_kth_narrow((int)nbd, need_band - 1, kbits, [&](int i) { return band[i]; });
-        else
-            ct = block_kth((int64_t)nbd, need_band - 1, [&](int64_t i) { return band[i]; },
-                           [](int64_t) { return true; });
-    }
-    for (int64_t i0 = 0; i0 < cnt; i0 += blockDim.x) {
-        const int64_t i = i0 + threadIdx.x;
-        bool keep = false;
-        uint32_t c = 0;
-        if (i < cnt) {
-            const float e = es[i];
-            c = cs[i];
-            keep = e > hi || (e >= lo && e <= hi && c <= ct);
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        uint32_t base = 0;
-        if (lane == 0 && bal) base = atomicAdd(&n_sel, (uint32_t)__popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (keep) {
-            out[base + __popc(bal & ((1u << lane) - 1))] = (int32_t)c;
-            atomicOr(&bits[c >> 5], 1u << (c & 31));
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) st.nsel = n_sel;
+    cutoff_staged(A, l, b, num, (int)cnt, __ldcg(&st.max_bits), false);
 }
 
 __device__ __forceinline__ JobView loc_view(const LocTailArgs &A, int l, int b)
@@ -1180,161 +1324,273 @@ __device__ __forceinline__ JobView loc_view(const LocTailArgs &A, int l, int b)
     return v;
 }
 
-// Thresholds and local maxima of the L_loc location hashes at B* (tasks of kTask buckets,
-// the maxima and their energies listed); the block that finishes the last task of a hash
-// makes that hash's cutoff.
-__global__ void __launch_bounds__(256) k_loc_maxima(const LocTailArgs A)
+// Thresholds, local maxima and top-num cutoff of the L_loc location hashes at B*: one
+// thread-block cluster per hash.  Every CTA of the cluster takes a contiguous range of
+// P-indices (tasks of kSelTask buckets) and clears its share of the hash's bucket bitmap;
+// the maxima it finds go straight into the shared memory of the cluster's first CTA, at
+// positions taken from a counter there (distributed shared memory; positions beyond
+// kRankStage go to the hash's list in global memory, at the same positions), and the
+// coarse digits of their selection keys into a histogram, summed into the first CTA's.
+// After the cluster barrier the first CTA holds them all and makes the cutoff.
+__global__ void __launch_bounds__(kSelThreads) k_loc_select(const LocTailArgs A)
 {
     pdl_wait();
     pdl_launch_next();
+    __shared__ uint32_t sh_cnt, sh_above, sh_base, sh_tot;
+    extern __shared__ __align__(16) uint32_t dsm[];
+    uint32_t *hist = dsm + 2 * kRankStage;   // coarse digits of this CTA's maxima
+    const uint32_t rank = cluster_ctarank(), csize = cluster_nctarank();
+    const int l = (int)(blockIdx.x / csize);
+    if (l >= A.L_loc) return;   // (whole clusters: the grid is L_loc clusters)
     ExecState *state = A.state;
     if (blockIdx.x == 0 && threadIdx.x == 0) stamp(&state->bar);
-    if (state->empty) return;   // k_loc_finish writes the outputs
+    // zero: every CTA its coarse histogram; the first CTA also its fine histogram and band
+    // bitmap (used by its cutoff)
+    for (int i = threadIdx.x; i < (rank == 0 ? 2 * kRankStage : kDigitBins); i += blockDim.x) hist[i] = 0;
+    if (threadIdx.x == 0) {
+        sh_cnt = 0;
+        sh_above = 0;
+    }
+    cluster_arrive();   // the first CTA's counters and histogram are zero before any adds
+    const int empty = state->empty;
     const int b = state->b_star;
     const int64_t num = state->k_star;
-    const int64_t nb = nb_of(A.S.ndim, b);
-    const int64_t per = (nb + kTask - 1) / kTask;
-    const int64_t ntasks = (int64_t)A.L_loc * per;
-    for (int64_t task = blockIdx.x; task < ntasks; task += gridDim.x) {
-        const int l = (int)(task / per);
-        const JobView J = loc_view(A, l, b);
-        const int64_t e0 = (task % per) * kTask;
-        const float M = __uint_as_float(J.st->max_bits);
-        const float X = A.S.use_median ? M * A.S.ratio : INFINITY;
-        localmax_task(J, A.S, A.S.thr_rel * M, e0, min(e0 + kTask, nb), X);
-        if (finished_last(&state->done[kMaxLogB + l], (uint32_t)per)) cutoff_hash(A, l, b, num);
+    const JobView J = loc_view(A, l, b);
+    const uint32_t mbits = J.st->max_bits;
+    cluster_wait();
+    if (empty) return;   // (the same in every CTA: nothing else touches the cluster)
+    const int ndim = A.S.ndim;
+    const int64_t nb = nb_of(ndim, b);
+    uint32_t *bits = A.bucketbits + (int64_t)l * A.bucket_words;
+    const int64_t words = (nb + 31) >> 5;
+    for (int64_t w = words * rank / csize + threadIdx.x; w < words * (rank + 1) / csize; w += blockDim.x)
+        bits[w] = 0u;
+    int32_t *list = A.S.lists + (int64_t)l * A.S.cap;
+    float *list_e = A.S.list_e + (int64_t)l * A.S.cap;
+    const uint32_t es_r = cluster_addr(dsm, 0), cs_r = cluster_addr(dsm + kRankStage, 0);
+    const float M = __uint_as_float(mbits);
+    const float X = A.S.use_median ? M * A.S.ratio : INFINITY;
+    const float T = A.S.thr_rel * M;
+    uint32_t above_all = 0;
+    for (int64_t e0 = nb * rank / csize, r1 = nb * (rank + 1) / csize; e0 < r1; e0 += kSelTask) {
+        float ev[kPerTask];
+        uint32_t found, above;
+        localmax_scan<kSelThreads>(J, A.S, T, e0, min(e0 + kSelTask, r1), X, ev, found, above);
+        above_all += above;
+        const uint32_t before = block_exclusive_scan((uint32_t)__popc(found), &sh_tot);
+        if (threadIdx.x == 0) sh_base = sh_tot ? atom_add_cluster(cluster_addr(&sh_cnt, 0), sh_tot) : 0u;
+        __syncthreads();
+        uint32_t pos = sh_base + before;
+#pragma unroll
+        for (int u = 0; u < kPerTask; u++) {
+            if (!(found & (1u << u))) continue;
+            const int32_t c = bucket_of_pindex(J, ndim, e0 + threadIdx.x + kSelThreads * u);
+            const uint32_t eb = __float_as_uint(ev[u]);
+            hist_add(hist, coarse_digit(mbits - eb));
+            if (pos < (uint32_t)kRankStage) {
+                st_cluster(es_r + 4 * pos, eb);
+                st_cluster(cs_r + 4 * pos, (uint32_t)c);
+            } else if (pos < A.S.cap) {
+                list[pos] = c;
+                list_e[pos] = ev[u];
+            }
+            pos++;
+        }
+    }
+    const uint32_t nabove = block_sum(above_all);   // (synchronises: this CTA's histogram is complete)
+    if (rank != 0) {
+        const uint32_t h_r = cluster_addr(hist, 0);
+        for (int i = threadIdx.x; i < kDigitBins; i += blockDim.x) {
+            const uint32_t v = hist[i];
+            if (v) red_add_cluster(h_r + 4 * i, v);
+        }
+    }
+    if (threadIdx.x == 0 && nabove) red_add_cluster(cluster_addr(&sh_above, 0), nabove);
+    cluster_arrive();   // this CTA's maxima, counts, digits and bitmap clears, for the first CTA
+    if (rank != 0) return;
+    cluster_wait();
+    HashStats &st = *J.st;
+    const uint32_t cnt = sh_cnt, above = sh_above;
+    if (threadIdx.x == 0) {
+        st.nmax = cnt;
+        st.above = above;
+    }
+    const bool median = A.S.use_median && (int64_t)above > nb - nb / 2 - 1;
+    if (median || cnt > (uint32_t)kRankStage) {
+        // rare: the whole list in global memory first (the staged part is this CTA's)
+        const uint32_t ns = min(cnt, (uint32_t)kRankStage);
+        for (uint32_t i = threadIdx.x; i < ns; i += blockDim.x) {
+            list[i] = (int32_t)dsm[kRankStage + i];
+            list_e[i] = __uint_as_float(dsm[i]);
+        }
+        __syncthreads();
+        cutoff_global(A, l, b, num, (int64_t)cnt, median);
+        return;
+    }
+    if ((int64_t)cnt <= num) {
+        // every maximum is kept: the list is the selection
+        int32_t *out = A.sel + (int64_t)l * A.S.cap;
+        for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const uint32_t c = dsm[kRankStage + i];
+            out[i] = (int32_t)c;
+            atomicOr(&bits[c >> 5], 1u << (c & 31));
+        }
+        if (threadIdx.x == 0) st.nsel = cnt;
+        return;
+    }
+    cutoff_staged(A, l, b, num, (int)cnt, mbits, true);
+}
+
+// Geometry of the votes at B* = 2^b (per axis): D = n / B preimages per bucket and axis.
+struct VoteGeom {
+    int b, logn, logD, logDd, lw, L_loc;
+    uint32_t need, nmask, Bm, Dh;   // Dh = D / 2
+};
+
+// Votes of the candidates it = base + u * stride (u < kVoteIlp) below `total`: candidate
+// it is preimage q of the s-th selected bucket of hash l0 (off[l0] <= it < off[l0 + 1]);
+// it is kept when >= need of the L_loc hashes selected its bucket and none of the hashes
+// before l0 did (so that it is emitted once).  STAGED: the bitmaps are in shared memory
+// (L_loc x 2^lw words), else read through the read-only cache.
+template <int NDIM, bool STAGED>
+__device__ __forceinline__ void vote_round(const LocTailArgs &A, const VoteGeom &G,
+                                           const uint32_t *bm, const uint32_t *off,
+                                           const uint32_t (*sig)[2], const uint32_t (*sinv)[2],
+                                           int L_cand, uint32_t base, uint32_t stride,
+                                           uint32_t total)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t coord[kVoteIlp], cb[kVoteIlp], qv[kVoteIlp];
+    int l0v[kVoteIlp];
+#pragma unroll
+    for (int u = 0; u < kVoteIlp; u++) {
+        const uint32_t it = base + (uint32_t)u * stride;
+        l0v[u] = -1;
+        cb[u] = qv[u] = 0;
+        if (it < total) {
+            int l0 = 0;
+            while (l0 + 1 < L_cand && it >= off[l0 + 1]) l0++;
+            const uint32_t rem = it - off[l0];
+            qv[u] = rem & ((1u << G.logDd) - 1);
+            cb[u] = (uint32_t)__ldg(&A.sel[(int64_t)l0 * A.S.cap + (rem >> G.logDd)]);
+            l0v[u] = l0;
+        }
+    }
+    // the preimage: bucket c collects permuted positions p in [c D - D/2, c D + D/2 - 1]
+#pragma unroll
+    for (int u = 0; u < kVoteIlp; u++) {
+        const int l0 = l0v[u] < 0 ? 0 : l0v[u];
+        const uint32_t c = cb[u], q = qv[u];
+        if (NDIM == 1) {
+            const uint32_t pp = ((c << G.logD) - G.Dh + q) & G.nmask;
+            coord[u] = (sinv[l0][0] * pp) & G.nmask;
+        } else {
+            const uint32_t c1 = c >> G.b, c2 = c & G.Bm;
+            const uint32_t q1 = q >> G.logD, q2 = q & ((1u << G.logD) - 1);
+            const uint32_t pp1 = ((c1 << G.logD) - G.Dh + q1) & G.nmask;
+            const uint32_t pp2 = ((c2 << G.logD) - G.Dh + q2) & G.nmask;
+            coord[u] = (((sinv[l0][0] * pp1) & G.nmask) << G.logn) | ((sinv[l0][1] * pp2) & G.nmask);
+        }
+    }
+    uint32_t votes[kVoteIlp], earlier[kVoteIlp];
+#pragma unroll
+    for (int u = 0; u < kVoteIlp; u++) votes[u] = earlier[u] = 0;
+#pragma unroll 4
+    for (int l = 0; l < G.L_loc; l++) {
+        const uint32_t s0 = sig[l][0], s1 = NDIM == 2 ? sig[l][1] : 0u;
+#pragma unroll
+        for (int u = 0; u < kVoteIlp; u++) {
+            const uint32_t ci = NDIM == 1 ? coord[u] : coord[u] >> G.logn;
+            uint32_t c_l = bucket_of(ci, s0, G.logn, G.b);
+            if (NDIM == 2) c_l = (c_l << G.b) | bucket_of(coord[u] & G.nmask, s1, G.logn, G.b);
+            const uint32_t w = STAGED ? bm[((uint32_t)l << G.lw) + (c_l >> 5)]
+                                      : __ldg(&A.bucketbits[(int64_t)l * A.bucket_words + (c_l >> 5)]);
+            const uint32_t sel = (w >> (c_l & 31)) & 1u;
+            votes[u] += sel;
+            earlier[u] |= sel & (uint32_t)(l < l0v[u]);
+        }
+    }
+    ExecState *state = A.state;
+#pragma unroll
+    for (int u = 0; u < kVoteIlp; u++) {
+        const bool keep = l0v[u] >= 0 && !earlier[u] && votes[u] >= G.need;
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (!bal) continue;
+        uint32_t first = 0;
+        if (lane == __ffs(bal) - 1)
+            first = (uint32_t)atomicAdd((unsigned long long *)&state->count,
+                                        (unsigned long long)__popc(bal));
+        first = __shfl_sync(0xffffffffu, first, __ffs(bal) - 1);
+        if (keep) {
+            const uint32_t pos = first + __popc(bal & ((1u << lane) - 1));
+            if (pos < A.kept_cap) A.kept[pos] = coord[u];
+            atomicOr(&A.coordbits[coord[u] >> 5], 1u << (coord[u] & 31));
+            atomicAdd(&A.chunkcnt[coord[u] >> (5 + 10)], 1u);
+        }
     }
 }
 
 // Votes.  A kept coordinate lies in >= need selected buckets, hence in a selected bucket
 // of one of the first L_cand = L_loc - need + 1 hashes; every preimage of those hashes'
-// selected buckets counts the hashes whose bucket of it is selected (from the bitmaps)
-// and is emitted once, by the first hash that has it.  kVoteIlp candidates per thread are
-// in flight at once (their selections, then all their bitmap words).
-__global__ void __launch_bounds__(256) k_loc_votes(const LocTailArgs A)
+// selected buckets counts the hashes whose bucket of it is selected and is emitted once,
+// by the first hash that has it.  One CTA per SM: the bitmaps of the L_loc hashes are
+// staged in its shared memory when they fit (vote_words > 0), and the candidates are
+// spread evenly over all threads (consecutive lanes: consecutive preimages of a bucket).
+// The selections and bitmaps were written by the previous kernel: read-only here.
+template <int NDIM>
+__global__ void __launch_bounds__(kVoteThreads) k_loc_votes(const LocTailArgs A)
 {
     pdl_wait();
     pdl_launch_next();
     ExecState *state = A.state;
     if (blockIdx.x == 0 && threadIdx.x == 0) stamp(&state->bar);
     if (state->empty) return;
-    const int b = state->b_star, ndim = A.S.ndim, logn = A.logn, logD = logn - b;
-    const int lane = threadIdx.x & 31;
-    const int L_cand = A.L_loc - (int)A.need + 1;
-    const uint32_t n = 1u << logn, nmask = n - 1, Bm = (1u << b) - 1;
-    const int64_t D = (int64_t)1 << logD;
-    const int logDd = ndim == 1 ? logD : 2 * logD;
-    __shared__ int64_t off[kMaxLoops + 1];
+    extern __shared__ __align__(16) uint32_t bm[];
+    __shared__ uint32_t off[kMaxLoops + 1];
     __shared__ uint32_t sh_sig[kMaxLoops][2], sh_sinv[kMaxLoops][2];
+    VoteGeom G;
+    G.b = state->b_star;
+    G.logn = A.logn;
+    G.logD = A.logn - G.b;
+    G.logDd = NDIM == 1 ? G.logD : 2 * G.logD;
+    G.lw = max((NDIM == 1 ? G.b : 2 * G.b) - 5, 0);   // bitmap words per hash: 2^lw
+    G.L_loc = A.L_loc;
+    G.need = A.need;
+    G.nmask = (uint32_t)((1ull << A.logn) - 1);
+    G.Bm = (1u << G.b) - 1;
+    G.Dh = 1u << (G.logD - 1);
+    const int L_cand = A.L_loc - (int)A.need + 1;
+    if (threadIdx.x < 32) {
+        // the candidate counts of the first L_cand hashes (< 2^32 in all: at most 16
+        // hashes of B/2 (1D) or B^2/4 (2D) selected buckets of n/B or N^2/B^2 preimages),
+        // loaded by one lane each and summed by a warp scan
+        static_assert(kMaxLoops <= 32, "one lane per location hash");
+        const int l = threadIdx.x;
+        const uint32_t c = l < L_cand ? (__ldcg(&A.S.stats[kMaxLogB + l].nsel) << G.logDd) : 0u;
+        const uint32_t incl = warp_incl_scan(c);
+        if (l <= L_cand) off[l] = incl - c;   // exclusive prefix; off[L_cand] = total
+    }
+    const bool staged = ((int64_t)A.L_loc << G.lw) <= A.vote_words;
+    if (staged) {
+        const int64_t nw = (int64_t)A.L_loc << G.lw;
+        const uint32_t wm = (1u << G.lw) - 1;
+        for (int64_t w = threadIdx.x; w < nw; w += blockDim.x)
+            bm[w] = __ldg(&A.bucketbits[(w >> G.lw) * A.bucket_words + (w & wm)]);
+    }
     if (threadIdx.x < A.L_loc) {
         sh_sig[threadIdx.x][0] = A.sig[threadIdx.x][0];
         sh_sig[threadIdx.x][1] = A.sig[threadIdx.x][1];
         sh_sinv[threadIdx.x][0] = A.sinv[threadIdx.x][0];
         sh_sinv[threadIdx.x][1] = A.sinv[threadIdx.x][1];
     }
-    if (threadIdx.x < 32) {
-        // the candidate counts of the first L_cand hashes, loaded by one lane each and
-        // summed by a warp scan
-        static_assert(kMaxLoops <= 32, "one lane per location hash");
-        const int l = threadIdx.x;
-        const int64_t c = l < L_cand ? ((int64_t)A.S.stats[kMaxLogB + l].nsel << logDd) : 0;
-        int64_t incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (l >= o) incl += u;
-        }
-        if (l <= L_cand) off[l] = incl - c;   // exclusive prefix; off[L_cand] = total
-    }
     __syncthreads();
-    const int64_t total = off[L_cand];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kVoteIlp;
-    for (int64_t it0 = (int64_t)blockIdx.x * blockDim.x * kVoteIlp; it0 < total; it0 += stride) {
-        uint32_t coord[kVoteIlp], cb[kVoteIlp], qv[kVoteIlp];
-        int l0v[kVoteIlp];
-#pragma unroll
-        for (int u = 0; u < kVoteIlp; u++) {
-            const int64_t it = it0 + (int64_t)u * blockDim.x + threadIdx.x;
-            l0v[u] = -1;
-            cb[u] = qv[u] = 0;
-            if (it < total) {
-                int l0 = 0;
-                while (it >= off[l0 + 1]) l0++;
-                const int64_t rem = it - off[l0];
-                qv[u] = (uint32_t)(rem & (((int64_t)1 << logDd) - 1));
-                cb[u] = (uint32_t)A.sel[(int64_t)l0 * A.S.cap + (rem >> logDd)];
-                l0v[u] = l0;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kVoteIlp; u++) {
-            coord[u] = 0;
-            if (l0v[u] < 0) continue;
-            const int l0 = l0v[u];
-            const uint32_t c = cb[u], q = qv[u];
-            if (ndim == 1) {
-                // bucket c collects permuted positions p in [c D - D/2, c D + D/2 - 1]
-                const uint32_t pp = ((c << logD) - (uint32_t)(D >> 1) + q) & nmask;
-                coord[u] = (sh_sinv[l0][0] * pp) & nmask;
-            } else {
-                const uint32_t c1 = c >> b, c2 = c & Bm;
-                const uint32_t q1 = q >> logD, q2 = q & (uint32_t)(D - 1);
-                const uint32_t pp1 = ((c1 << logD) - (uint32_t)(D >> 1) + q1) & nmask;
-                const uint32_t pp2 = ((c2 << logD) - (uint32_t)(D >> 1) + q2) & nmask;
-                coord[u] = (((sh_sinv[l0][0] * pp1) & nmask) << logn) | ((sh_sinv[l0][1] * pp2) & nmask);
-            }
-        }
-        uint32_t votes[kVoteIlp], earlier[kVoteIlp];
-#pragma unroll
-        for (int u = 0; u < kVoteIlp; u++) {
-            votes[u] = 0;
-            earlier[u] = 0;
-        }
-        // the bitmap word of every (candidate, hash) pair is requested before any is
-        // tested; up to kVoteUnroll hashes at a time
-        for (int l0 = 0; l0 < A.L_loc; l0 += kVoteUnroll) {
-            uint32_t w[kVoteIlp][kVoteUnroll];
-#pragma unroll
-            for (int dl = 0; dl < kVoteUnroll; dl++) {
-                const int l = l0 + dl;
-#pragma unroll
-                for (int u = 0; u < kVoteIlp; u++) {
-                    w[u][dl] = 0;
-                    if (l < A.L_loc && l0v[u] >= 0) {
-                        const uint32_t ci = ndim == 1 ? coord[u] : coord[u] >> logn;
-                        uint32_t c_l = bucket_of(ci, sh_sig[l][0], logn, b);
-                        if (ndim == 2) c_l = (c_l << b) | bucket_of(coord[u] & nmask, sh_sig[l][1], logn, b);
-                        w[u][dl] = A.bucketbits[(int64_t)l * A.bucket_words + (c_l >> 5)] >> (c_l & 31);
-                    }
-                }
-            }
-#pragma unroll
-            for (int dl = 0; dl < kVoteUnroll; dl++) {
-#pragma unroll
-                for (int u = 0; u < kVoteIlp; u++) {
-                    const uint32_t sel = w[u][dl] & 1u;
-                    votes[u] += sel;
-                    earlier[u] |= sel && l0 + dl < l0v[u];
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kVoteIlp; u++) {
-            const bool keep = l0v[u] >= 0 && !earlier[u] && votes[u] >= A.need;
-            const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (!bal) continue;
-            uint32_t base = 0;
-            if (lane == __ffs(bal) - 1)
-                base = (uint32_t)atomicAdd((unsigned long long *)&state->count,
-                                           (unsigned long long)__popc(bal));
-            base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
-            if (keep) {
-                const uint32_t pos = base + __popc(bal & ((1u << lane) - 1));
-                if (pos < A.kept_cap) A.kept[pos] = coord[u];
-                atomicOr(&A.coordbits[coord[u] >> 5], 1u << (coord[u] & 31));
-                atomicAdd(&A.chunkcnt[coord[u] >> (5 + 10)], 1u);
-            }
-        }
+    const uint32_t total = off[L_cand];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t base = blockIdx.x * blockDim.x + threadIdx.x; base < total; base += kVoteIlp * stride) {
+        if (staged)
+            vote_round<NDIM, true>(A, G, bm, off, sh_sig, sh_sinv, L_cand, base, stride, total);
+        else
+            vote_round<NDIM, false>(A, G, bm, off, sh_sig, sh_sinv, L_cand, base, stride, total);
     }
 }
 
@@ -1503,23 +1759,31 @@ constexpr size_t kTailSmem = sizeof(uint32_t) * kTailSmemWords;
 
 // A tail kernel launched with programmatic stream serialization: its blocks may be
 // scheduled before the previous kernel of the stream has finished and wait for it at
-// griddepcontrol.wait (every tail kernel starts with that wait).
+// griddepcontrol.wait (every tail kernel starts with that wait); cluster > 0: in
+// thread-block clusters of that many CTAs.
 template <class Arg>
-static cudaError_t launch_pdl(void (*fn)(const Arg), int grid, size_t smem, const Arg &arg,
-                              cudaStream_t s)
+static cudaError_t launch_pdl(void (*fn)(const Arg), int grid, int block, size_t smem,
+                              const Arg &arg, cudaStream_t s, int cluster = 0)
 {
     cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg;
     memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3((unsigned)block);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (cluster > 0) {
+        attr[1].id = cudaLaunchAttributeClusterDimension;
+        attr[1].val.clusterDim.x = (unsigned)cluster;
+        attr[1].val.clusterDim.y = 1;
+        attr[1].val.clusterDim.z = 1;
+        cfg.numAttrs = 2;
+    }
+    cfg.attrs = attr;
     return cudaLaunchKernelEx(&cfg, fn, arg);
 }
 
@@ -1577,7 +1841,7 @@ void launch_tune_tail(const atsfft_plan_s *P, int stage, cudaStream_t s)
     A.limit_b = hi;
     const int64_t cap = (int64_t)P->num_sms * 4;
     const int grid = (int)(tasks < cap ? tasks : cap);
-    launch_pdl(k_tune_tail, grid, kTailSmem, A, s);
+    launch_pdl(k_tune_tail, grid, 256, kTailSmem, A, s);
     count_launch(P);
 }
 
@@ -1611,7 +1875,7 @@ void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, uint
     A.coord_words = P->coord_words;
     A.chunkcnt = P->d_blk;
     A.nchunks = P->nchunks;
-    A.le = P->d_le;
+    for (int l = 0; l < P->L_est; l++) A.est[l] = P->h_le[P->est_base + l];
     A.z = P->d_z;
     A.rgain = P->d_rgain;
     for (int b = 0; b < kMaxLogB; b++) A.ro.off[b] = P->resp_off[b];
@@ -1627,16 +1891,16 @@ void launch_loc_tail(const atsfft_plan_s *P, int64_t *d_loc, float2 *d_val, uint
     A.d_k = d_k;
     A.d_status = d_status;
     A.state = P->d_state;
-    // k_loc_maxima: every task of the largest B the plan can pick (blocks beyond the
-    // tasks of the actual B* exit at once), at most 4 blocks per SM
-    const int64_t nb_max = P->ndim == 1 ? ((int64_t)1 << P->b_hi) : ((int64_t)1 << (2 * P->b_hi));
-    const int64_t tasks = (int64_t)P->L_loc * ((nb_max + kTask - 1) / kTask);
-    const int64_t cap = (int64_t)P->num_sms * 4;
-    const int grid1 = (int)(tasks < cap ? tasks : cap);
-    A.grid_maxima = grid1;
-    launch_pdl(k_loc_maxima, grid1, kTailSmem, A, s);
-    launch_pdl(k_loc_votes, P->num_sms * 4, 0, A, s);
-    launch_pdl(k_loc_finish, P->num_sms * 4, kTailSmem, A, s);
+    // the votes stage the bitmaps of every B* whose L_loc bitmaps fit kVoteSmem
+    const int64_t vote_bytes = (int64_t)P->L_loc * P->bucket_words * 4;
+    const size_t vsmem = (size_t)(vote_bytes < kVoteSmem ? vote_bytes : kVoteSmem);
+    A.vote_words = (int64_t)(vsmem / 4);
+    launch_pdl(k_loc_select, P->L_loc * kSelCluster, kSelThreads, kSelSmem, A, s, kSelCluster);
+    if (P->ndim == 1)
+        launch_pdl(k_loc_votes<1>, P->num_sms, kVoteThreads, vsmem, A, s);
+    else
+        launch_pdl(k_loc_votes<2>, P->num_sms, kVoteThreads, vsmem, A, s);
+    launch_pdl(k_loc_finish, P->num_sms * 4, 256, kTailSmem, A, s);
     count_launch(P, 3);
 }
 
