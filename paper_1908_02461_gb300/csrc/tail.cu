@@ -306,9 +306,10 @@ __device__ __forceinline__ void localmax_scan(const JobView &J, const StatsParam
         float el[kPerTask], er[kPerTask];
 #pragma unroll
         for (int u = 0; u < kPerTask; u++) {
-            const uint32_t jj = (uint32_t)(e0 + threadIdx.x + NT * u);
-            el[u] = __ldg(&E[(jj - p1) & mask]);
-            er[u] = __ldg(&E[(jj + p1) & mask]);
+            const int64_t j = e0 + threadIdx.x + NT * u;
+            const uint32_t jj = (uint32_t)j;
+            el[u] = j < e1 ? __ldg(&E[(jj - p1) & mask]) : 0.f;
+            er[u] = j < e1 ? __ldg(&E[(jj + p1) & mask]) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < kPerTask; u++) {
@@ -335,7 +336,7 @@ __device__ __forceinline__ void localmax_scan(const JobView &J, const StatsParam
                         if (d1 == 0 && d2 == 0) continue;
                         const uint32_t m1 = (jA + (uint32_t)d1 * p1) & mask;
                         const uint32_t m2 = (jB + (uint32_t)d2 * p2) & mask;
-                        nbv[v][q++] = __ldg(&E[((int64_t)m1 << logB) | m2]);
+                        nbv[v][q++] = j < e1 ? __ldg(&E[((int64_t)m1 << logB) | m2]) : 0.f;
                     }
             }
 #pragma unroll
@@ -915,6 +916,8 @@ constexpr int64_t kSelTask = kTask * kSelThreads / 256;   // buckets per task of
 constexpr int kVoteThreads = 1024; // k_loc_votes: one CTA per SM
 constexpr int kVoteIlp = 2;        // candidates per thread per round of the votes
 constexpr int kVoteSmem = 96 * 1024;   // largest bitmap staging of k_loc_votes (bytes)
+constexpr int kVoteKeep = 2048;    // kept coordinates a CTA of k_loc_votes collects before
+                                   // reserving their places in the kept list at once
 
 // Value of descending rank r (0-based; equal values ordered by index) among es[0..cnt),
 // by the whole block.  kPivots sampled values are counted against all elements (every
@@ -1457,7 +1460,7 @@ __device__ __forceinline__ void vote_round(const LocTailArgs &A, const VoteGeom 
                                            const uint32_t *bm, const uint32_t *off,
                                            const uint32_t (*sig)[2], const uint32_t (*sinv)[2],
                                            int L_cand, uint32_t base, uint32_t stride,
-                                           uint32_t total)
+                                           uint32_t total, uint32_t *keep_s, uint32_t *keep_n)
 {
     const int lane = threadIdx.x & 31;
     uint32_t coord[kVoteIlp], cb[kVoteIlp], qv[kVoteIlp];
@@ -1510,20 +1513,34 @@ __device__ __forceinline__ void vote_round(const LocTailArgs &A, const VoteGeom 
             earlier[u] |= sel & (uint32_t)(l < l0v[u]);
         }
     }
+    // the kept ones: into the CTA's list (one shared atomic per warp); beyond its
+    // kVoteKeep entries, straight into the kept list (one global atomic per warp)
     ExecState *state = A.state;
+    const unsigned below = (1u << lane) - 1;
 #pragma unroll
     for (int u = 0; u < kVoteIlp; u++) {
         const bool keep = l0v[u] >= 0 && !earlier[u] && votes[u] >= G.need;
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (!bal) continue;
-        uint32_t first = 0;
-        if (lane == __ffs(bal) - 1)
-            first = (uint32_t)atomicAdd((unsigned long long *)&state->count,
-                                        (unsigned long long)__popc(bal));
-        first = __shfl_sync(0xffffffffu, first, __ffs(bal) - 1);
+        const int lead = __ffs(bal) - 1;
+        uint32_t lb = 0;
+        if (lane == lead) lb = atomicAdd(keep_n, (uint32_t)__popc(bal));
+        const uint32_t li = __shfl_sync(0xffffffffu, lb, lead) + __popc(bal & below);
+        const unsigned ovf = __ballot_sync(0xffffffffu, keep && li >= (uint32_t)kVoteKeep);
+        uint32_t gb = 0;
+        if (ovf) {
+            if (lane == __ffs(ovf) - 1)
+                gb = (uint32_t)atomicAdd((unsigned long long *)&state->count,
+                                         (unsigned long long)__popc(ovf));
+            gb = __shfl_sync(0xffffffffu, gb, __ffs(ovf) - 1);
+        }
         if (keep) {
-            const uint32_t pos = first + __popc(bal & ((1u << lane) - 1));
-            if (pos < A.kept_cap) A.kept[pos] = coord[u];
+            if (li < (uint32_t)kVoteKeep) {
+                keep_s[li] = coord[u];
+            } else {
+                const uint32_t pos = gb + __popc(ovf & below);
+                if (pos < A.kept_cap) A.kept[pos] = coord[u];
+            }
             atomicOr(&A.coordbits[coord[u] >> 5], 1u << (coord[u] & 31));
             atomicAdd(&A.chunkcnt[coord[u] >> (5 + 10)], 1u);
         }
@@ -1548,6 +1565,7 @@ __global__ void __launch_bounds__(kVoteThreads) k_loc_votes(const LocTailArgs A)
     extern __shared__ __align__(16) uint32_t bm[];
     __shared__ uint32_t off[kMaxLoops + 1];
     __shared__ uint32_t sh_sig[kMaxLoops][2], sh_sinv[kMaxLoops][2];
+    __shared__ uint32_t keep_s[kVoteKeep], keep_n, keep_base;
     VoteGeom G;
     G.b = state->b_star;
     G.logn = A.logn;
@@ -1577,6 +1595,7 @@ __global__ void __launch_bounds__(kVoteThreads) k_loc_votes(const LocTailArgs A)
         for (int64_t w = threadIdx.x; w < nw; w += blockDim.x)
             bm[w] = __ldg(&A.bucketbits[(w >> G.lw) * A.bucket_words + (w & wm)]);
     }
+    if (threadIdx.x == 0) keep_n = 0;
     if (threadIdx.x < A.L_loc) {
         sh_sig[threadIdx.x][0] = A.sig[threadIdx.x][0];
         sh_sig[threadIdx.x][1] = A.sig[threadIdx.x][1];
@@ -1586,11 +1605,29 @@ __global__ void __launch_bounds__(kVoteThreads) k_loc_votes(const LocTailArgs A)
     __syncthreads();
     const uint32_t total = off[L_cand];
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t base = blockIdx.x * blockDim.x + threadIdx.x; base < total; base += kVoteIlp * stride) {
+    // (the trip count is the same for every lane of a warp: vote_round's warp-wide
+    // ballots and shuffles need all 32 lanes; each candidate is checked against total)
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t wbase = blockIdx.x * blockDim.x + (threadIdx.x - lane); wbase < total;
+         wbase += kVoteIlp * stride) {
+        const uint32_t base = wbase + lane;
         if (staged)
-            vote_round<NDIM, true>(A, G, bm, off, sh_sig, sh_sinv, L_cand, base, stride, total);
+            vote_round<NDIM, true>(A, G, bm, off, sh_sig, sh_sinv, L_cand, base, stride, total,
+                                   keep_s, &keep_n);
         else
-            vote_round<NDIM, false>(A, G, bm, off, sh_sig, sh_sinv, L_cand, base, stride, total);
+            vote_round<NDIM, false>(A, G, bm, off, sh_sig, sh_sinv, L_cand, base, stride, total,
+                                    keep_s, &keep_n);
+    }
+    // this CTA's kept coordinates: their places in the kept list with one atomic
+    __syncthreads();
+    const uint32_t nk = min(keep_n, (uint32_t)kVoteKeep);
+    if (nk == 0) return;
+    if (threadIdx.x == 0)
+        keep_base = (uint32_t)atomicAdd((unsigned long long *)&state->count, (unsigned long long)nk);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < nk; i += blockDim.x) {
+        const uint64_t pos = (uint64_t)keep_base + i;
+        if (pos < (uint64_t)A.kept_cap) A.kept[pos] = keep_s[i];
     }
 }
 
