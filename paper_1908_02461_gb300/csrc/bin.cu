@@ -183,6 +183,14 @@ __device__ __forceinline__ float ld_shared_f32(uint32_t addr)
     return v;
 }
 
+// One complex table entry (8-byte aligned) in one shared-memory load.
+__device__ __forceinline__ float2 ld_shared_f32x2(uint32_t addr)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
 // Window constants of one hash inside the inner loop: uniform across the CTA.
 struct TapConst {
     uint32_t c0h;        // c0 + h: t' = sigma^{-1} a + c0 + h (mod n)
@@ -201,7 +209,8 @@ __device__ __forceinline__ void tap_mac(float2 &acc, float2 v, uint32_t a, uint3
 {
     const uint32_t tsh = (sinv * a + T.c0h) & mask;
     const uint32_t e = tb + ((tsh >> T.logB) << 3);
-    const float ex = ld_shared_f32(e), ey = ld_shared_f32(e + 4);
+    const float2 ev = ld_shared_f32x2(e);
+    const float ex = ev.x, ey = ev.y;
     const float tf = SMALL_N ? __uint_as_float(tsh | 0x4B000000u) + T.mh
                              : (float)((int)tsh - T.h);
     const float f = fast_exp2(fmaf(-T.k2 * tf, tf, T.l2c)) * fast_rcp(tf);

@@ -1448,6 +1448,7 @@ __global__ void __launch_bounds__(kSelThreads) k_loc_select(const LocTailArgs A)
 struct VoteGeom {
     int b, logn, logD, logDd, lw, L_loc;
     uint32_t need, nmask, Bm, Dh;   // Dh = D / 2
+    uint32_t cap;                    // selection list stride (L_loc x cap < 2^31)
 };
 
 // Votes of the candidates it = base + u * stride (u < kVoteIlp) below `total`: candidate
@@ -1475,7 +1476,7 @@ __device__ __forceinline__ void vote_round(const LocTailArgs &A, const VoteGeom 
             while (l0 + 1 < L_cand && it >= off[l0 + 1]) l0++;
             const uint32_t rem = it - off[l0];
             qv[u] = rem & ((1u << G.logDd) - 1);
-            cb[u] = (uint32_t)__ldg(&A.sel[(int64_t)l0 * A.S.cap + (rem >> G.logDd)]);
+            cb[u] = (uint32_t)__ldg(&A.sel[(uint32_t)l0 * G.cap + (rem >> G.logDd)]);
             l0v[u] = l0;
         }
     }
@@ -1498,14 +1499,16 @@ __device__ __forceinline__ void vote_round(const LocTailArgs &A, const VoteGeom 
     uint32_t votes[kVoteIlp], earlier[kVoteIlp];
 #pragma unroll
     for (int u = 0; u < kVoteIlp; u++) votes[u] = earlier[u] = 0;
+    // bucket of i under sigma (the half-bin rule of bucket_of, in three operations):
+    // floor((2p + 1 + D) / 2D) mod B = ((sigma i + D/2) mod n) >> log2 D, p = sigma i mod n
 #pragma unroll 4
     for (int l = 0; l < G.L_loc; l++) {
         const uint32_t s0 = sig[l][0], s1 = NDIM == 2 ? sig[l][1] : 0u;
 #pragma unroll
         for (int u = 0; u < kVoteIlp; u++) {
             const uint32_t ci = NDIM == 1 ? coord[u] : coord[u] >> G.logn;
-            uint32_t c_l = bucket_of(ci, s0, G.logn, G.b);
-            if (NDIM == 2) c_l = (c_l << G.b) | bucket_of(coord[u] & G.nmask, s1, G.logn, G.b);
+            uint32_t c_l = ((s0 * ci + G.Dh) & G.nmask) >> G.logD;
+            if (NDIM == 2) c_l = (c_l << G.b) | (((s1 * (coord[u] & G.nmask) + G.Dh) & G.nmask) >> G.logD);
             const uint32_t w = STAGED ? bm[((uint32_t)l << G.lw) + (c_l >> 5)]
                                       : __ldg(&A.bucketbits[(int64_t)l * A.bucket_words + (c_l >> 5)]);
             const uint32_t sel = (w >> (c_l & 31)) & 1u;
@@ -1577,6 +1580,7 @@ __global__ void __launch_bounds__(kVoteThreads) k_loc_votes(const LocTailArgs A)
     G.nmask = (uint32_t)((1ull << A.logn) - 1);
     G.Bm = (1u << G.b) - 1;
     G.Dh = 1u << (G.logD - 1);
+    G.cap = (uint32_t)A.S.cap;
     const int L_cand = A.L_loc - (int)A.need + 1;
     if (threadIdx.x < 32) {
         // the candidate counts of the first L_cand hashes (< 2^32 in all: at most 16

@@ -21,6 +21,14 @@ def bucket_of_u32(i, sigma, logn, logB):
     return (t >> (logn - logB + 1)) & ((1 << logB) - 1)
 
 
+def bucket_shift_u32(i, sigma, logn, logB):
+    """The votes kernel's form of the same bucket: ((sigma i + D/2) mod n) >> log2 D in
+    32-bit unsigned arithmetic (floor((2p + 1 + D) / 2D) = floor((p + D/2) / D) for
+    integers p, D >= 2, and the reduction mod n commutes with the shift mod B, n = B D)."""
+    nmask, logD = (1 << logn) - 1, logn - logB
+    return ((((sigma * i) & M32) + (1 << (logD - 1))) & M32 & nmask) >> logD
+
+
 def preimage_u32(c, q, sinv, logn, logB):
     """The kernel's q-th preimage of bucket c: sigma^{-1} (c D - D/2 + q) mod n, 32-bit."""
     nmask, logD = (1 << logn) - 1, logn - logB
@@ -45,10 +53,12 @@ def test_1d_bucket_and_preimages_match_exact_arithmetic(logn):
             i = rng.randrange(n)
             p = sigma * i % n
             assert bucket_of_u32(i, sigma, logn, logB) == ((2 * p + 1 + D) // (2 * D)) % B
+            assert bucket_shift_u32(i, sigma, logn, logB) == ((2 * p + 1 + D) // (2 * D)) % B
             c, q = rng.randrange(B), rng.randrange(D)
             coord = preimage_u32(c, q, sinv, logn, logB)
             assert coord == sinv * ((c * D - D // 2 + q) % n) % n
             assert bucket_of_u32(coord, sigma, logn, logB) == c
+            assert bucket_shift_u32(coord, sigma, logn, logB) == c
         # the D preimages of a bucket are distinct and all hash back to it (small D only)
         if D <= 4096:
             sigma = rng.randrange(n) | 1
@@ -57,6 +67,7 @@ def test_1d_bucket_and_preimages_match_exact_arithmetic(logn):
             pre = {preimage_u32(c, q, sinv, logn, logB) for q in range(D)}
             assert len(pre) == D
             assert all(bucket_of_u32(x, sigma, logn, logB) == c for x in pre)
+            assert all(bucket_shift_u32(x, sigma, logn, logB) == c for x in pre)
 
 
 @pytest.mark.parametrize("logN", [5, 10, 14])
@@ -75,3 +86,15 @@ def test_2d_coordinates_fit_and_hash_back(logN):
             assert coord == i * N + j < 1 << 28
             assert bucket_of_u32(coord >> logN, s1, logN, logB) == c1
             assert bucket_of_u32(coord & (N - 1), s2, logN, logB) == c2
+            assert bucket_shift_u32(coord >> logN, s1, logN, logB) == c1
+            assert bucket_shift_u32(coord & (N - 1), s2, logN, logB) == c2
+
+
+def test_shift_form_equals_half_bin_rule_exhaustively_small_n():
+    """Every coordinate, odd sigma and bucket count at n = 2^8: the two bucket forms agree."""
+    logn = 8
+    n = 1 << logn
+    for logB in range(1, logn):
+        for sigma in range(1, n, 2):
+            for i in range(n):
+                assert bucket_shift_u32(i, sigma, logn, logB) == bucket_of_u32(i, sigma, logn, logB)
