@@ -53,10 +53,18 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# DRAM bytes of one launch of a phase's kernel, from one ncu capture of the current
-# kernel (dram__bytes_read.sum + dram__bytes_write.sum); None once the kernel changes.
-NCU_TRAFFIC = {
-    "loc_tail": (2873600, "k_loc_tail, 1D n=2^22 k=1000 (B*=2^16), one launch of bench.py --ncu-case 1000"),
+# DRAM bytes of one launch of a phase's kernels, from one ncu capture of the current
+# kernels (dram__bytes_read.sum + dram__bytes_write.sum); None once a kernel changes.
+NCU_TRAFFIC = {}
+
+# The kernels of each profiled phase (the location tail is three kernels chained with
+# programmatic dependent launch; its phase time covers all three).
+PHASE_KERNELS = {
+    "tune1_bin": "k_bin_gather_tune", "tune1_fft": "k_fft_batch x2", "tune1_tail": "k_tune_tail",
+    "tune2_bin": "k_bin_stream<3,0>", "tune2_fft": "k_fft_batch x2", "tune2_tail": "k_tune_tail",
+    "tune3_bin": "k_bin_stream<1,0>", "tune3_fft": "k_fft_batch x2", "tune3_tail": "k_tune_tail",
+    "le_bin_stream": "k_bin_stream<14,1>", "le_bin_gather": "k_bin_gather_1d",
+    "le_fft": "k_fft_pass x2", "loc_tail": "k_loc_select + k_loc_votes + k_loc_finish",
 }
 
 
@@ -323,7 +331,7 @@ def mufu_pair_peak(stream=None):
         "derived: 32 SFU ops/clk/SM x 152 SMs x 2070 MHz / 2 SFU ops per sample-hash pair")
 
 
-def roofline(per_signal, traces, n, stages=3, pair_peak=None, pair_src=None):
+def roofline(per_signal, traces, n, stages=3, pair_peak=None, pair_src=None, kept=None):
     """Algorithmic work of each profiled phase per launch, achieved rate, fraction of peak.
 
     Bytes (HBM-bound phases) count each input and output value once; pairs (the
@@ -374,7 +382,12 @@ def roofline(per_signal, traces, n, stages=3, pair_peak=None, pair_src=None):
             model["le_bin_gather"] = ("hbm", NH * 8 * (2 * _window_h(n, Bstar) + 1) + 8 * NH * Bstar)
         ch = _chunks(n, Bstar) if _stream(n, Bstar) else 1
         model["le_fft"] = ("hbm", sum(fft_bytes(Bstar, ch) for _ in range(NH)))
-        model["loc_tail"] = ("hbm", L_LOC * Bstar * (4 + 4))
+        # local maxima and cutoff: energies and lists, 8 B* per location hash; votes: at
+        # most 4 k* D bytes per location hash (k* selected buckets of D = n / B*
+        # preimages); estimates: 8 bytes per kept coordinate and estimation hash
+        k_star = traces[k][-1][1] or 0
+        model["loc_tail"] = ("hbm", L_LOC * Bstar * (4 + 4) + L_LOC * 4 * k_star * (n // Bstar)
+                             + 8 * L_EST * ((kept or {}).get(k) or 0))
         for nm, (bound, units) in model.items():
             t = ph[nm] / 1e3
             if t <= 0:
@@ -394,7 +407,8 @@ def roofline(per_signal, traces, n, stages=3, pair_peak=None, pair_src=None):
               key=lambda nm: out[nm]["ms_per_launch"] * out[nm]["launches_per_step"])
     d = out[dom]
     peak = pair_peak / 1e9 if d["bound"] == "alu" else hbm
-    roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": peak,
+    roof = {"kernel": dom, "kernels": PHASE_KERNELS.get(dom, dom), "bound": d["bound"],
+            "achieved": d["achieved"], "peak": peak,
             "unit": d["unit"], "frac": d["achieved"] / peak,
             "traffic": NCU_TRAFFIC[dom][0] if dom in NCU_TRAFFIC else None,
             "traffic_launch": NCU_TRAFFIC[dom][1] if dom in NCU_TRAFFIC else None,
@@ -922,8 +936,9 @@ def main():
             tr = [(A._lib.atsfft_last_result(p.handle)[1], None)]
         traces[k] = tr
     pair_peak, pair_src = mufu_pair_peak(stream.cuda_stream)
+    kept = {k: min(int(o["count"].item()), CAPACITY) for k, o in zip(KS, outs)}
     roof, phase_rooflines = roofline(per_signal, traces, n, stages=args.tune_stages,
-                                     pair_peak=pair_peak, pair_src=pair_src)
+                                     pair_peak=pair_peak, pair_src=pair_src, kept=kept)
     acc = {}
     for k, sg, o in zip(KS, sigs, outs):
         m = min(int(o["count"].item()), CAPACITY)

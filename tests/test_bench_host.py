@@ -61,6 +61,14 @@ def test_roofline_model_picks_dominant_phase():
     traces = {2000: [(16, 0), (65536, 1900)]}
     roof, rows = bench.roofline({2000: ph}, traces, n)
     assert roof["kernel"] == "loc_tail" and roof["bound"] == "hbm"
+    assert roof["kernels"] == "k_loc_select + k_loc_votes + k_loc_finish"
+    # the location tail: 8 B* per location hash, 4 k* D per location hash for the votes,
+    # 8 bytes per kept coordinate and estimation hash
+    B = 65536
+    loc_bytes = 7 * B * 8 + 7 * 4 * 1900 * (n // B)
+    assert rows["loc_tail"]["achieved"] == pytest.approx(loc_bytes / 0.12e-3 / 1e9)
+    _, rows_k = bench.roofline({2000: ph}, traces, n, kept={2000: 2100})
+    assert rows_k["loc_tail"]["achieved"] == pytest.approx((loc_bytes + 8 * 7 * 2100) / 0.12e-3 / 1e9)
     assert rows["le_bin_stream"]["bound"] == "alu"
     # 14 hashes x n pairs in 0.06 ms
     assert rows["le_bin_stream"]["achieved"] == pytest.approx(14 * n / 0.06e-3 / 1e9)
