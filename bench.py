@@ -587,11 +587,8 @@ def mixed_workload(args):
         res = autotune(n, k_range=(10, 1000), snr_db=SNR_DB, probes=3, reps=2, seed=SEED)
         tuned[n] = res
     t_tune = time.perf_counter() - t_tune
-    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    coop_sms = num_sms // 4 if args.coop_sms < 0 else args.coop_sms
-    templates = {n: A.Plan((n,), params=A.params(coop_blocks_per_sm=1, coop_sms=coop_sms,
-                                                 **tuned[n].params),
-                           seed=SEED) for n in sorted(set(sizes))}
+    templates = {n: A.Plan((n,), params=A.params(**tuned[n].params), seed=SEED)
+                 for n in sorted(set(sizes))}
     t0 = time.perf_counter()
     plans = [templates[n].clone() for n in sizes]
     t_clone = time.perf_counter() - t0
@@ -762,9 +759,6 @@ def main():
                     help="estimation loops reuse the location hashes (off: fresh hashes)")
     ap.add_argument("--fixed-k", action="store_true",
                     help="no tuning: B from the true k given as the hint (the SFFT setting)")
-    ap.add_argument("--coop-sms", type=int, default=-1,
-                    help="SMs of the cooperative tails when transforms run concurrently "
-                         "(-1: half the SMs, a quarter for mixed512; 0: all)")
     ap.add_argument("--no-graph", action="store_true",
                     help="time per-signal execs on streams instead of one graph launch per step")
     ap.add_argument("--no-image", action="store_true",
@@ -810,17 +804,11 @@ def main():
     xs = [h.to(dev) for h in host]
     nstreams = max(1, min(args.streams, len(sigs)))
     use_graph = not args.no_graph
-    # concurrent transforms (graph branches or streams): tails at one CTA per SM on a part
-    # of the SMs, so that several cooperative grids are resident together and the other
-    # transforms' kernels keep the rest
-    concurrent = nstreams > 1 or use_graph
-    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    coop_sms = (num_sms // 2 if args.coop_sms < 0 else args.coop_sms) if concurrent else 0
     common = dict(tune_stages=args.tune_stages, est_reuse_loc=int(args.est_reuse_loc),
                   fixed_k=int(args.fixed_k))
-    pp = A.params(coop_blocks_per_sm=1 if concurrent else 0, coop_sms=coop_sms, **common)
+    pp = A.params(**common)
     plans = [A.Plan((n,), params=pp, seed=SEED, k_hint=k if args.fixed_k else 0) for k in KS]
-    # the plain path (one transform at a time) with the tails on every SM
+    # the plain path (one transform at a time): its own plans, profiled per phase
     plain_plans = [A.Plan((n,), params=A.params(**common), seed=SEED,
                           k_hint=k if args.fixed_k else 0) for k in KS]
     outs = []
@@ -1025,7 +1013,7 @@ def main():
                    "plain_path_ms_per_step": float(np.mean(plain_ms)),
                    "k_star": kstar, "counts": counts, "status": status,
                    "tune_stages": args.tune_stages, "est_reuse_loc": bool(args.est_reuse_loc),
-                   "fixed_k": bool(args.fixed_k), "coop_sms": coop_sms,
+                   "fixed_k": bool(args.fixed_k),
                    "path": ("one CUDA graph per step (atsfft_batch_launch), a branch per signal"
                             if use_graph else
                             "plain per-signal path (one exec per transform)" if nstreams == 1 else

@@ -138,8 +138,9 @@ def test_autotune_meets_the_error_target(A):
 
 
 def test_tail_grid_size_does_not_change_results(A):
-    """The cooperative tails spread over all SMs (default) or a part of them (coop_sms,
-    one CTA per SM) give bit-identical transforms, also inside a batch graph."""
+    """The coop_* launch parameters (accepted for the ABI, without effect since the tail
+    kernels stopped being cooperative grids) leave transforms bit-identical, also inside a
+    batch graph."""
     import torch
 
     from synth import sparse_signal_1d, sparse_signal_2d

@@ -6,9 +6,9 @@ boundary).  Needs a GPU.
 
 The batch is a reduced form of the 512-signal workload: n over {2^16, 2^18, 2^20} five
 times each and one 2^22, k log-uniform in [10, 1000], 40 dB noise, one plan clone per
-signal, all 16 transforms as branches of one graph with the cooperative tails on a
-quarter of the SMs.  Half the branches take the autotuner's choice for their n, the other
-half a fixed non-default set (5 + 5 loops, window tolerance 1e-5, alpha 1, tuning from
+signal, all 16 transforms as branches of one graph (the coop_* launch parameters are
+still passed; they no longer change anything).  Half the branches take the autotuner's
+choice for their n, the other half a fixed non-default set (5 + 5 loops, window tolerance 1e-5, alpha 1, tuning from
 B = 32), so that parameters other than the defaults are compared whatever the autotuner
 picks.
 """
