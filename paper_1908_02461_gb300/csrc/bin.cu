@@ -142,6 +142,7 @@ struct StreamArgs {
     int hash_base;            // dynamic pass: index of the first hash (output block offset)
     int logR;                 // residue modulus (static passes)
     int chunks;               // row chunks (static passes)
+    int ring_off;             // first float2 of the sample ring in shared memory
     StreamHash h[kMaxStream];
 };
 
@@ -219,11 +220,33 @@ __device__ __forceinline__ void tap_mac(float2 &acc, float2 v, uint32_t a, uint3
     acc.y = fmaf(cr, v.y, fmaf(ci, v.x, acc.y));
 }
 
-// Grid: kStreamCtas CTAs per SM of kStreamThreads threads, striding over the items
-// (measured: contiguous per-CTA item ranges balance a lone launch as well but slow the
-// transforms of a batch graph down, where other branches' kernels share the SMs).
+// Grid: one thread per item (up to the CTAs per SM below), striding beyond.  The
+// location pass (B* read on the device) takes CTAs of kStreamThreadsLE threads, which
+// spread its usual 2^16 items over the SMs within one CTA of each other (1024 CTAs: 6 or
+// 7 per SM, where 256-thread CTAs left SMs with 8 or with 16 warps); the tuning passes,
+// whose CTAs fill E_v tables for several windows, take kStreamThreads.
 constexpr int kStreamThreads = 256;
 constexpr int kStreamCtas = 2;
+constexpr int kStreamThreadsLE = 64;
+constexpr int kStreamCtasLE = 8;
+
+// Samples reach shared memory kRing rows ahead of their use: each thread copies its own
+// sample of a row with cp.async into its own ring slot and reads it back after
+// cp.async.wait_group, so no barrier is involved and no register holds a sample in flight.
+constexpr int kRing = 8;
+
+__device__ __forceinline__ void cp_async8(uint32_t dst, const float2 *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 template <int NH, bool DYN>
 __global__ void __launch_bounds__(kStreamThreads, kStreamCtas)
@@ -264,6 +287,7 @@ k_bin_stream(const float2 *__restrict__ x, int logn, const StreamArgs A, const J
         T[g].l2c = DYN ? w.log2c : A.h[g].log2c;
     }
     const uint32_t rot_s = (uint32_t)__cvta_generic_to_shared(rot);
+    const uint32_t ring_s = rot_s + 8u * ((uint32_t)A.ring_off + threadIdx.x);
     float2 half;
     sincospif(ldexpf(1.0f, -logn), &half.y, &half.x);
     const uint32_t rows = (n >> logR) / (uint32_t)chunks;
@@ -283,22 +307,41 @@ k_bin_stream(const float2 *__restrict__ x, int logn, const StreamArgs A, const J
             const int e = (DYN ? 0 : A.h[g].rot_off) + rot_base(rho, T[g].h, lb, (int)(n >> lb) + 2);
             tb[g] = rot_s + 8u * (uint32_t)e;
         }
-        const uint32_t j0 = c * rows;
+        const uint32_t j0 = c * rows, j1 = j0 + rows;
+        // ring prologue: rows j0 .. j0 + kRing - 1, one commit group per row (empty past j1)
+#pragma unroll
+        for (int p = 0; p < kRing; p++) {
+            if (j0 + p < j1) cp_async8(ring_s + 8u * (uint32_t)(p * blockDim.x), &x[r + ((j0 + p) << logR)]);
+            cp_async_commit();
+        }
+        uint32_t slot = 0;
         if (small_n) {
-            for (uint32_t j = j0; j < j0 + rows; j++) {
+            for (uint32_t j = j0; j < j1; j++) {
                 const uint32_t a = r + (j << logR);
-                const float2 v = __ldg(&x[a]);
+                cp_async_wait<kRing - 1>();
+                const uint32_t sa = ring_s + 8u * slot * blockDim.x;
+                const float2 v = ld_shared_f32x2(sa);
 #pragma unroll
                 for (int g = 0; g < NH; g++) tap_mac<true>(acc[g], v, a, A.h[g].sinv, mask, T[g], tb[g]);
+                // the slot's sample has been used: refill it with row j + kRing
+                if (j + kRing < j1) cp_async8(sa, &x[a + ((uint32_t)kRing << logR)]);
+                cp_async_commit();
+                slot = (slot + 1) & (kRing - 1);
             }
         } else {
-            for (uint32_t j = j0; j < j0 + rows; j++) {
+            for (uint32_t j = j0; j < j1; j++) {
                 const uint32_t a = r + (j << logR);
-                const float2 v = __ldg(&x[a]);
+                cp_async_wait<kRing - 1>();
+                const uint32_t sa = ring_s + 8u * slot * blockDim.x;
+                const float2 v = ld_shared_f32x2(sa);
 #pragma unroll
                 for (int g = 0; g < NH; g++) tap_mac<false>(acc[g], v, a, A.h[g].sinv, mask, T[g], tb[g]);
+                if (j + kRing < j1) cp_async8(sa, &x[a + ((uint32_t)kRing << logR)]);
+                cp_async_commit();
+                slot = (slot + 1) & (kRing - 1);
             }
         }
+        cp_async_wait<0>();
 #pragma unroll
         for (int g = 0; g < NH; g++) {
             const int logB = DYN ? logR : A.h[g].logB;
@@ -616,13 +659,30 @@ static StreamHash stream_hash(const atsfft_plan_s *P, const HashParam &hp, int b
     return h;
 }
 
+// `smem` holds the E_v tables; the sample ring follows them.  One thread per item
+// (residues x row chunks; for a dynamic pass the most any stream-form B* can have).
 template <int NH, bool DYN>
-static void launch_stream(const atsfft_plan_s *P, const float2 *x, const StreamArgs &A,
+static void launch_stream(const atsfft_plan_s *P, const float2 *x, const StreamArgs &A0,
                           const Job *job_dev, size_t smem, const int *skip, cudaStream_t s)
 {
+    StreamArgs A = A0;
+    const int threads = DYN ? kStreamThreadsLE : kStreamThreads;
+    const int per_sm = DYN ? kStreamCtasLE : kStreamCtas;
+    A.ring_off = (int)((smem + sizeof(float2) - 1) / sizeof(float2));
+    smem = sizeof(float2) * ((size_t)A.ring_off + (size_t)kRing * threads);
+    int64_t items = (int64_t)A.chunks << A.logR;
+    if (DYN) {
+        items = 0;
+        for (int b = P->b0; b <= P->b_hi; b++)
+            if (P->h_tjob[b].stream && ((int64_t)P->h_tjob[b].chunks << b) > items)
+                items = (int64_t)P->h_tjob[b].chunks << b;
+    }
+    int64_t grid = (items + threads - 1) / threads;
+    if (grid > (int64_t)P->num_sms * per_sm) grid = (int64_t)P->num_sms * per_sm;
+    if (grid < 1) grid = 1;
     const void *fn = (const void *)k_bin_stream<NH, DYN>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    launch_k(P, k_bin_stream<NH, DYN>, dim3((unsigned)(P->num_sms * kStreamCtas)), dim3(kStreamThreads), smem, s, 
+    launch_k(P, k_bin_stream<NH, DYN>, dim3((unsigned)grid), dim3((unsigned)threads), smem, s,
         x, P->logn, A, job_dev, P->d_win, P->d_phase, P->phase_s, P->d_part, skip);
     count_launch(P);
 }

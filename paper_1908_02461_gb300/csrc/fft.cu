@@ -2,7 +2,8 @@
 // B x B in 2D): Zhat_c = sum_b z_b exp(-2 pi i c b / B), unscaled.
 //
 // One CTA transforms up to kSmallFFT points in shared memory (radix-2 decimation in
-// time, bit reversal folded into the loads, table twiddles); 1D transforms of more than
+// time, bit reversal folded into the loads, twiddles from a shared-memory copy of the
+// table entries of its length, loaded together with the data); 1D transforms of more than
 // 2^kSinglePassLog points use the four-step split B = P1 * P2 (j = j1 + P1 j2,
 // k = k2 + P2 k1), which spreads one transform over many CTAs:
 //   pass 0: Y[j1 + P1 k2] = exp(-2 pi i j1 k2 / B) * sum_j2 z[j1 + P1 j2] w_P2^(j2 k2)
@@ -16,6 +17,8 @@ namespace atsfft {
 // 1D transforms of up to 2^kSinglePassLog points run in one CTA; larger ones take the
 // four-step split over two passes (more CTAs per transform, each with a short chain).
 constexpr int kSinglePassLog = 10;
+constexpr int kSmallFFTLog = 12;
+static_assert((1 << kSmallFFTLog) == kSmallFFT, "kSmallFFTLog");
 
 struct FftShape {
     int logP;            // transform length
@@ -79,20 +82,21 @@ __device__ __forceinline__ void butterfly(float2 &a, float2 &b, float2 w)
 // R consecutive radix-2 decimation-in-time stages lm0 .. lm0+R-1 on one group of 2^R
 // values held in registers: v[j] is the value at position base + q + j * 2^(lm0-1).
 // Stage lm pairs positions p and p + 2^(lm-1) with the twiddle w_(2^lm)^(p mod 2^(lm-1)),
-// exactly as the one-stage-at-a-time form.
+// exactly as the one-stage-at-a-time form.  stw[m] = w_P^m (m < P / 2, P = 2^logP), so
+// w_(2^lm)^qq = stw[qq << (logP - lm)].
 template <int R>
 __device__ __forceinline__ void group_stages(float2 (&v)[1 << R], int q, int lm0,
-                                             const float2 *__restrict__ tw)
+                                             const float2 *stw, int logP)
 {
     const int half = 1 << (lm0 - 1);
 #pragma unroll
     for (int s = 0; s < R; s++) {
-        const int twstep = kSmallFFT >> (lm0 + s);
+        const int twsh = logP - (lm0 + s);
 #pragma unroll
         for (int j0 = 0; j0 < (1 << R); j0++) {
             if (j0 & (1 << s)) continue;
             const int qq = q + (j0 & ((1 << s) - 1)) * half;
-            butterfly(v[j0], v[j0 | (1 << s)], __ldg(&tw[qq * twstep]));
+            butterfly(v[j0], v[j0 | (1 << s)], stw[qq << twsh]);
         }
     }
 }
@@ -156,7 +160,7 @@ __device__ __forceinline__ int bitrev_in(int j, int logP)
 // First group of stages (lm0 = 1), in place: the loads stored every transform in
 // bit-reversed order, so group g is the 2^R consecutive positions g 2^R + j.
 template <int R>
-__device__ __forceinline__ void first_stages(float2 *sm, int TP, const float2 *__restrict__ tw)
+__device__ __forceinline__ void first_stages(float2 *sm, int TP, const float2 *stw, int logP)
 {
     constexpr int E = 1 << R;
     for (int g = threadIdx.x; g < (TP >> R); g += blockDim.x) {
@@ -166,7 +170,7 @@ __device__ __forceinline__ void first_stages(float2 *sm, int TP, const float2 *_
         if constexpr (R == 3)
             radix8_first(v);
         else
-            group_stages<R>(v, 0, 1, tw);
+            group_stages<R>(v, 0, 1, stw, logP);
 #pragma unroll
         for (int j = 0; j < E; j++) sm[padi(g * E + j)] = v[j];
     }
@@ -175,8 +179,8 @@ __device__ __forceinline__ void first_stages(float2 *sm, int TP, const float2 *_
 
 // Later groups of stages, in place: each group reads and writes only its own positions.
 template <int R>
-__device__ __forceinline__ void next_stages(float2 *sm, int TP, int lm0,
-                                            const float2 *__restrict__ tw)
+__device__ __forceinline__ void next_stages(float2 *sm, int TP, int lm0, const float2 *stw,
+                                            int logP)
 {
     constexpr int E = 1 << R;
     const int half = 1 << (lm0 - 1);
@@ -187,9 +191,9 @@ __device__ __forceinline__ void next_stages(float2 *sm, int TP, int lm0,
 #pragma unroll
         for (int j = 0; j < E; j++) v[j] = sm[padi(base + j * half)];
         if constexpr (R == 3)
-            radix8_stages(v, __ldg(&tw[q * (kSmallFFT >> (lm0 + 2))]));
+            radix8_stages(v, stw[q << (logP - (lm0 + 2))]);   // w_(2^(lm0+2))^q
         else
-            group_stages<R>(v, q, lm0, tw);
+            group_stages<R>(v, q, lm0, stw, logP);
 #pragma unroll
         for (int j = 0; j < E; j++) sm[padi(base + j * half)] = v[j];
     }
@@ -198,15 +202,26 @@ __device__ __forceinline__ void next_stages(float2 *sm, int TP, int lm0,
 
 constexpr int kMaxTile = 8;    // transforms per tile
 
-// exp(-2 pi i m / B) for B = 2^logB <= 2^24: the coarse table entry (times the fine entry
-// above 2^12).
-__device__ __forceinline__ float2 four_step_twiddle(uint32_t m, int logB, const float2 *__restrict__ tw)
+// Shared memory of the FFT kernels: the padded tile, then the stage twiddles of the
+// current length (w_P^m, m < P / 2 <= kSmallFFT / 2).
+constexpr int kStwEntries = kSmallFFT / 2;
+constexpr size_t kFftSmemBytes = sizeof(float2) * (size_t)(kSmemPadded + kStwEntries);
+
+// stw[m] = w_P^m = exp(-2 pi i m / P) for m < P / 2, from the table entry tw[m 4096 / P];
+// the caller's next barrier (the one after a tile's loads) makes it visible.
+__device__ __forceinline__ void load_stage_twiddles(float2 *stw, int logP, const float2 *__restrict__ tw)
 {
-    if (logB <= 12) return __ldg(&tw[m << (12 - logB)]);
-    const int sh = logB - 12;
-    const float2 c = __ldg(&tw[m >> sh]);
-    const float2 f = __ldg(&tw[kSmallFFT + ((m & ((1u << sh) - 1)) << (24 - logB))]);
-    return make_float2(c.x * f.x - c.y * f.y, c.x * f.y + c.y * f.x);
+    for (int m = threadIdx.x; m < ((1 << logP) >> 1); m += blockDim.x)
+        stw[m] = __ldg(&tw[m << (kSmallFFTLog - logP)]);
+}
+
+// exp(-2 pi i m / B) for B = 2^logB <= 2^24, m < B: sincospif of the exact dyadic
+// argument 2 m / B (no table, so no memory round trip in the tile's epilogue).
+__device__ __forceinline__ float2 four_step_twiddle(uint32_t m, int logB)
+{
+    float sn, cs;
+    sincospif(ldexpf((float)m, 1 - logB), &sn, &cs);
+    return make_float2(cs, -sn);
 }
 
 // T = 2^logT adjacent transforms t0..t0+T-1 by the whole CTA (T * P <= kSmallFFT):
@@ -220,7 +235,7 @@ __device__ __forceinline__ float2 four_step_twiddle(uint32_t m, int logB, const 
 __device__ void fft_tile(const float2 *src, int in_es, int in_bs, int chunks,
                          int chunk_stride, float2 *dst, int out_es, int out_bs,
                          int logP, int logT, int tw_logB, int64_t t0, float2 *sm,
-                         const float2 *__restrict__ tw, float *edst, uint32_t *emax)
+                         const float2 *stw, float *edst, uint32_t *emax)
 {
     const int P = 1 << logP, T = 1 << logT;
     const int TP = T << logP;
@@ -293,17 +308,17 @@ __device__ void fft_tile(const float2 *src, int in_es, int in_bs, int chunks,
     // stages 1 .. logP: groups of three (the loads already bit-reversed each transform)
     const int r0 = logP < kMaxRadixLog ? logP : kMaxRadixLog;
     switch (r0) {
-    case 3: first_stages<3>(sm, TP, tw); break;
-    case 2: first_stages<2>(sm, TP, tw); break;
-    case 1: first_stages<1>(sm, TP, tw); break;
+    case 3: first_stages<3>(sm, TP, stw, logP); break;
+    case 2: first_stages<2>(sm, TP, stw, logP); break;
+    case 1: first_stages<1>(sm, TP, stw, logP); break;
     default: break;
     }
     for (int lm0 = r0 + 1; lm0 <= logP;) {
         const int r = logP - lm0 + 1 < kMaxRadixLog ? logP - lm0 + 1 : kMaxRadixLog;
         switch (r) {
-        case 3: next_stages<3>(sm, TP, lm0, tw); break;
-        case 2: next_stages<2>(sm, TP, lm0, tw); break;
-        default: next_stages<1>(sm, TP, lm0, tw); break;
+        case 3: next_stages<3>(sm, TP, lm0, stw, logP); break;
+        case 2: next_stages<2>(sm, TP, lm0, stw, logP); break;
+        default: next_stages<1>(sm, TP, lm0, stw, logP); break;
         }
         lm0 += r;
     }
@@ -314,7 +329,7 @@ __device__ void fft_tile(const float2 *src, int in_es, int in_bs, int chunks,
             const int u = idx >> logP, k = idx & (P - 1);
             float2 v = sm[padi(idx)];
             if (tw_logB >= 0) {
-                const float2 w = four_step_twiddle((uint32_t)((t0 + u) * k) & bmask, tw_logB, tw);
+                const float2 w = four_step_twiddle((uint32_t)((t0 + u) * k) & bmask, tw_logB);
                 v = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
             }
             const int o = u * out_bs + k;
@@ -326,26 +341,26 @@ __device__ void fft_tile(const float2 *src, int in_es, int in_bs, int chunks,
             }
         }
     } else {
-        for (int k = threadIdx.x; k < P; k += blockDim.x) {
-            float4 *q = reinterpret_cast<float4 *>(dst + k * out_es);
-            float *eo = edst ? edst + k * out_es : nullptr;
-            // two transforms at a time: one 16-byte store
-#pragma unroll 1
-            for (int u = 0; u < T; u += 2) {
-                float2 a = sm[padi((u << logP) + k)], c = sm[padi(((u + 1) << logP) + k)];
-                if (tw_logB >= 0) {
-                    const float2 wa = four_step_twiddle((uint32_t)((t0 + u) * k) & bmask, tw_logB, tw);
-                    const float2 wc = four_step_twiddle((uint32_t)((t0 + u + 1) * k) & bmask, tw_logB, tw);
-                    a = make_float2(a.x * wa.x - a.y * wa.y, a.x * wa.y + a.y * wa.x);
-                    c = make_float2(c.x * wc.x - c.y * wc.y, c.x * wc.y + c.y * wc.x);
-                }
-                q[u >> 1] = make_float4(a.x, a.y, c.x, c.y);
-                if (eo) {
-                    const float ea = fmaf(a.x, a.x, a.y * a.y), ec = fmaf(c.x, c.x, c.y * c.y);
-                    eo[u] = ea;
-                    eo[u + 1] = ec;
-                    emx = fmaxf(emx, fmaxf(ea, ec));
-                }
+        // items (k, pair of transforms u, u + 1), consecutive threads on consecutive k: every
+        // thread of the CTA takes part; one 16-byte store per item
+        const int items = P * (T >> 1);
+#pragma unroll 2
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            const int k = it & (P - 1), u = (it >> logP) << 1;
+            float2 a = sm[padi((u << logP) + k)], c = sm[padi(((u + 1) << logP) + k)];
+            if (tw_logB >= 0) {
+                const float2 wa = four_step_twiddle((uint32_t)((t0 + u) * k) & bmask, tw_logB);
+                const float2 wc = four_step_twiddle((uint32_t)((t0 + u + 1) * k) & bmask, tw_logB);
+                a = make_float2(a.x * wa.x - a.y * wa.y, a.x * wa.y + a.y * wa.x);
+                c = make_float2(c.x * wc.x - c.y * wc.y, c.x * wc.y + c.y * wc.x);
+            }
+            reinterpret_cast<float4 *>(dst + k * out_es)[u >> 1] = make_float4(a.x, a.y, c.x, c.y);
+            if (edst) {
+                float *eo = edst + k * out_es;
+                const float ea = fmaf(a.x, a.x, a.y * a.y), ec = fmaf(c.x, c.x, c.y * c.y);
+                eo[u] = ea;
+                eo[u + 1] = ec;
+                emx = fmaxf(emx, fmaxf(ea, ec));
             }
         }
     }
@@ -400,7 +415,8 @@ __global__ void __launch_bounds__(kFftThreads, kPassCtas) k_fft_pass(int ndim, i
 {
     chain_wait();
     chain_next();
-    __shared__ float2 sm[kSmemPadded];
+    extern __shared__ float2 fft_dsm[];
+    float2 *sm = fft_dsm, *stw = fft_dsm + kSmemPadded;
     if (!job->active) return;
     const int logB = job->logB, nh = job->nh;
     const int chunks = pass == 0 ? job->chunks : 1;
@@ -416,13 +432,14 @@ __global__ void __launch_bounds__(kFftThreads, kPassCtas) k_fft_pass(int ndim, i
     const int64_t tiles = f.ntrans / T;
     const int64_t total = (int64_t)nh * tiles;
     const bool fin_pass = energy && final_pass(ndim, logB, pass);
+    if ((int64_t)blockIdx.x < total) load_stage_twiddles(stw, f.logP, tw);   // one length per pass
     for (int64_t tr = blockIdx.x; tr < total; tr += gridDim.x) {
         const int64_t h = tr / tiles, t = (tr % tiles) * T;
         const bool e = fin_pass && h < n_energy;
         fft_tile(in + h * in_hash + t * f.in_bs, f.in_es, f.in_bs, chunks, f.hash_stride,
                  out + h * f.hash_stride + t * f.out_bs, f.out_es, f.out_bs, f.logP, __ffs(T) - 1,
                  f.tw_logB,
-                 t, sm, tw, e ? energy + h * f.hash_stride + t * f.out_bs : nullptr,
+                 t, sm, stw, e ? energy + h * f.hash_stride + t * f.out_bs : nullptr,
                  e ? &stats[kMaxLogB + h].max_bits : nullptr);
     }
 }
@@ -453,8 +470,10 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_fft_batch(int ndim, int pass
 {
     chain_wait();
     chain_next();
-    __shared__ float2 sm[kSmemPadded];
+    extern __shared__ float2 fft_dsm[];
+    float2 *sm = fft_dsm, *stw = fft_dsm + kSmemPadded;
     if (skip && *skip) return;
+    int stw_logP = -1;   // length whose stage twiddles stw holds (a CTA's tiles span jobs)
     for (int64_t tr = blockIdx.x; tr < Bt.total; tr += gridDim.x) {
         int jb = 0;
         while (jb + 1 < Bt.njobs && tr >= Bt.j[jb + 1].tr_start) jb++;
@@ -468,8 +487,12 @@ __global__ void __launch_bounds__(kFftThreads, 2) k_fft_batch(int ndim, int pass
         float2 *out = (pass == 0 && four_step) ? tmp + J.tmp_off : fin + J.out_off;
         const int chunks = pass == 0 ? J.chunks : 1;
         const bool e = energy && final_pass(ndim, J.logB, pass);
+        if (f.logP != stw_logP) {   // the previous tile ended with a barrier
+            load_stage_twiddles(stw, f.logP, tw);
+            stw_logP = f.logP;
+        }
         fft_tile(in + t * f.in_bs, f.in_es, f.in_bs, chunks, f.hash_stride, out + t * f.out_bs,
-                 f.out_es, f.out_bs, f.logP, __ffs(T) - 1, f.tw_logB, t, sm, tw,
+                 f.out_es, f.out_bs, f.logP, __ffs(T) - 1, f.tw_logB, t, sm, stw,
                  e ? energy + J.out_off + t * f.out_bs : nullptr,
                  e ? &stats[J.logB].max_bits : nullptr);
     }
@@ -480,11 +503,13 @@ void launch_bucket_fft_dynamic(const atsfft_plan_s *P, const Job *job, const flo
                                float2 *out, float *energy, int n_energy, cudaStream_t s)
 {
     const int grid = P->num_sms * kPassCtas;   // resident CTAs; a grid-stride loop covers the tiles
-    launch_k(P, k_fft_pass, dim3(grid), dim3(kFftThreads), 0, s, P->ndim, 0, job, part, P->d_fft_tmp, out, P->d_tw,
+    cudaFuncSetAttribute((const void *)k_fft_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kFftSmemBytes);
+    launch_k(P, k_fft_pass, dim3(grid), dim3(kFftThreads), kFftSmemBytes, s, P->ndim, 0, job, part, P->d_fft_tmp, out, P->d_tw,
                                             energy, P->d_stats, n_energy);
     count_launch(P);
     if (P->ndim == 2 || P->b_hi > kSinglePassLog) {
-        launch_k(P, k_fft_pass, dim3(grid), dim3(kFftThreads), 0, s, P->ndim, 1, job, part, P->d_fft_tmp, out, P->d_tw,
+        launch_k(P, k_fft_pass, dim3(grid), dim3(kFftThreads), kFftSmemBytes, s, P->ndim, 1, job, part, P->d_fft_tmp, out, P->d_tw,
                                                 energy, P->d_stats, n_energy);
         count_launch(P);
     }
@@ -546,7 +571,9 @@ void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB,
         if (Bt.njobs == 0) continue;
         const int64_t cap = (int64_t)P->num_sms * 2;
         const int64_t grid = Bt.total < cap ? Bt.total : cap;
-        launch_k(P, k_fft_batch, dim3((unsigned)grid), dim3(kFftThreads), 0, s, P->ndim, pass, Bt, part, P->d_fft_tmp, out,
+        cudaFuncSetAttribute((const void *)k_fft_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kFftSmemBytes);
+        launch_k(P, k_fft_batch, dim3((unsigned)grid), dim3(kFftThreads), kFftSmemBytes, s, P->ndim, pass, Bt, part, P->d_fft_tmp, out,
                                                    P->d_tw, energy, P->d_stats, skip);
         count_launch(P);
     }
