@@ -22,8 +22,14 @@ constexpr int kGroup = 16;   // hashes accumulated together per thread
 // the window (about 2h / B + 1 of them, ~35 at the default window), each tap computed
 // once and applied to every hash of the group (gathering x at each hash's position);
 // the group's partial sums are added by shuffles and its first lane writes the buckets.
+// A lane issues the gathers of kTapBatch1D taps (all hashes of its group) before it
+// uses any of them, so its scattered loads overlap instead of following one another;
+// groups of kGroup1D hashes (one grid row each) give the small B* of this form enough
+// warps to cover that latency.
 // ---------------------------------------------------------------------------------
 constexpr int kGatherLanes = 8;
+constexpr int kGroup1D = 4;
+constexpr int kTapBatch1D = 6;
 
 __global__ void k_bin_gather_1d(const float2 *__restrict__ x, int logn, const HashParam *hashes,
                                 int nh, const WindowParam *win, const Job *job_dev,
@@ -38,9 +44,9 @@ __global__ void k_bin_gather_1d(const float2 *__restrict__ x, int logn, const Ha
         logB = job_dev->logB;
         nh = job_dev->nh;
     }
-    const int group0 = blockIdx.y * kGroup;
+    const int group0 = blockIdx.y * kGroup1D;
     if (group0 >= nh) return;
-    const int ng = min(kGroup, nh - group0);
+    const int ng = min(kGroup1D, nh - group0);
     const uint32_t n = 1u << logn, mask = n - 1, B = 1u << logB;
     const WindowParam w = win[logB];
     const int lane = threadIdx.x & 31, q = lane & (kGatherLanes - 1);
@@ -49,9 +55,9 @@ __global__ void k_bin_gather_1d(const float2 *__restrict__ x, int logn, const Ha
     const int64_t tasks = ((int64_t)B + kPerWarp - 1) / kPerWarp;
     float2 half;
     sincospif(ldexpf(1.0f, -logn), &half.y, &half.x);
-    uint32_t sig[kGroup], tau[kGroup];
+    uint32_t sig[kGroup1D], tau[kGroup1D];
 #pragma unroll
-    for (int g = 0; g < kGroup; g++) {
+    for (int g = 0; g < kGroup1D; g++) {
         const HashParam hp = hashes[group0 + (g < ng ? g : 0)];
         sig[g] = hp.sigma[0];
         tau[g] = hp.tau[0];
@@ -64,28 +70,38 @@ __global__ void k_bin_gather_1d(const float2 *__restrict__ x, int logn, const Ha
         // taps t = b + u B with |t| <= h
         const int u_lo = -((w.h + b) >> logB);          // ceil((-h - b) / B)
         const int u_hi = valid ? (w.h - b) >> logB : u_lo - 1;   // floor((h - b) / B)
-        float2 acc[kGroup];
+        float2 acc[kGroup1D];
 #pragma unroll
-        for (int g = 0; g < kGroup; g++) acc[g] = make_float2(0.f, 0.f);
-        for (int u = u_lo + q; u <= u_hi; u += kGatherLanes) {
-            const int t = b + u * (int)B;
-            if (t == 0) continue;                       // centre tap handled below
-            const float tf = (float)t;
-            const float f = fast_exp2(fmaf(-w.k2 * tf, tf, w.log2c)) * fast_rcp(tf);
-            const float2 R = rot_factor(u, logB, mask, phase, phase_s);
-            const float2 c = make_float2(f * R.x, f * R.y);
+        for (int g = 0; g < kGroup1D; g++) acc[g] = make_float2(0.f, 0.f);
+        for (int u0 = u_lo + q; u0 <= u_hi; u0 += kGatherLanes * kTapBatch1D) {
+            float2 v[kTapBatch1D][kGroup1D];
 #pragma unroll
-            for (int g = 0; g < kGroup; g++) {
-                if (g < ng) {
-                    const uint32_t a = (sig[g] * (uint32_t)t + tau[g]) & mask;
-                    const float2 v = __ldg(&x[a]);
-                    acc[g].x = fmaf(c.x, v.x, fmaf(-c.y, v.y, acc[g].x));
-                    acc[g].y = fmaf(c.x, v.y, fmaf(c.y, v.x, acc[g].y));
+            for (int i = 0; i < kTapBatch1D; i++) {
+                const int u = u0 + i * kGatherLanes;
+                const uint32_t t = (uint32_t)(b + u * (int)B);
+#pragma unroll
+                for (int g = 0; g < kGroup1D; g++)
+                    v[i][g] = (u <= u_hi && g < ng) ? __ldg(&x[(sig[g] * t + tau[g]) & mask])
+                                                   : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < kTapBatch1D; i++) {
+                const int u = u0 + i * kGatherLanes;
+                const int t = b + u * (int)B;
+                if (u > u_hi || t == 0) continue;      // centre tap handled below
+                const float tf = (float)t;
+                const float f = fast_exp2(fmaf(-w.k2 * tf, tf, w.log2c)) * fast_rcp(tf);
+                const float2 R = rot_factor(u, logB, mask, phase, phase_s);
+                const float2 c = make_float2(f * R.x, f * R.y);
+#pragma unroll
+                for (int g = 0; g < kGroup1D; g++) {
+                    acc[g].x = fmaf(c.x, v[i][g].x, fmaf(-c.y, v[i][g].y, acc[g].x));
+                    acc[g].y = fmaf(c.x, v[i][g].y, fmaf(c.y, v[i][g].x, acc[g].y));
                 }
             }
         }
 #pragma unroll
-        for (int g = 0; g < kGroup; g++) {
+        for (int g = 0; g < kGroup1D; g++) {
 #pragma unroll
             for (int o = kGatherLanes / 2; o > 0; o >>= 1) {
                 acc[g].x += __shfl_xor_sync(0xffffffffu, acc[g].x, o);
@@ -95,7 +111,7 @@ __global__ void k_bin_gather_1d(const float2 *__restrict__ x, int logn, const Ha
         if (valid && q == 0) {
             const float2 Sb = bucket_factor_tab((uint32_t)b, logB, logn, phase, phase_s, half);
 #pragma unroll
-            for (int g = 0; g < kGroup; g++) {
+            for (int g = 0; g < kGroup1D; g++) {
                 if (g < ng) {
                     float2 z = cmul(Sb, acc[g]);
                     if (b == 0) {
@@ -230,9 +246,10 @@ constexpr int kStreamCtas = 2;
 constexpr int kStreamThreadsLE = 64;
 constexpr int kStreamCtasLE = 8;
 
-// Samples reach shared memory kRing rows ahead of their use: each thread copies its own
-// sample of a row with cp.async into its own ring slot and reads it back after
-// cp.async.wait_group, so no barrier is involved and no register holds a sample in flight.
+// Location pass: samples reach shared memory kRing rows ahead of their use.  Each thread
+// copies its own sample of a row with cp.async into its own ring slot and reads it back
+// after cp.async.wait_group, so no barrier is involved and no register holds a sample in
+// flight (long-scoreboard stalls 2.35 -> 0.26 per issued instruction under ncu).
 constexpr int kRing = 8;
 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const float2 *src)
@@ -308,40 +325,58 @@ k_bin_stream(const float2 *__restrict__ x, int logn, const StreamArgs A, const J
             tb[g] = rot_s + 8u * (uint32_t)e;
         }
         const uint32_t j0 = c * rows, j1 = j0 + rows;
-        // ring prologue: rows j0 .. j0 + kRing - 1, one commit group per row (empty past j1)
+        if (DYN) {
+            // ring prologue: rows j0 .. j0 + kRing - 1, one commit group per row (empty past j1)
 #pragma unroll
-        for (int p = 0; p < kRing; p++) {
-            if (j0 + p < j1) cp_async8(ring_s + 8u * (uint32_t)(p * blockDim.x), &x[r + ((j0 + p) << logR)]);
-            cp_async_commit();
-        }
-        uint32_t slot = 0;
-        if (small_n) {
+            for (int p = 0; p < kRing; p++) {
+                if (j0 + p < j1) cp_async8(ring_s + 8u * (uint32_t)(p * blockDim.x), &x[r + ((j0 + p) << logR)]);
+                cp_async_commit();
+            }
+            uint32_t slot = 0;
+            if (small_n) {
+                for (uint32_t j = j0; j < j1; j++) {
+                    const uint32_t a = r + (j << logR);
+                    cp_async_wait<kRing - 1>();
+                    const uint32_t sa = ring_s + 8u * slot * blockDim.x;
+                    const float2 v = ld_shared_f32x2(sa);
+#pragma unroll
+                    for (int g = 0; g < NH; g++) tap_mac<true>(acc[g], v, a, A.h[g].sinv, mask, T[g], tb[g]);
+                    // the slot's sample has been used: refill it with row j + kRing
+                    if (j + kRing < j1) cp_async8(sa, &x[a + ((uint32_t)kRing << logR)]);
+                    cp_async_commit();
+                    slot = (slot + 1) & (kRing - 1);
+                }
+            } else {
+                for (uint32_t j = j0; j < j1; j++) {
+                    const uint32_t a = r + (j << logR);
+                    cp_async_wait<kRing - 1>();
+                    const uint32_t sa = ring_s + 8u * slot * blockDim.x;
+                    const float2 v = ld_shared_f32x2(sa);
+#pragma unroll
+                    for (int g = 0; g < NH; g++) tap_mac<false>(acc[g], v, a, A.h[g].sinv, mask, T[g], tb[g]);
+                    if (j + kRing < j1) cp_async8(sa, &x[a + ((uint32_t)kRing << logR)]);
+                    cp_async_commit();
+                    slot = (slot + 1) & (kRing - 1);
+                }
+            }
+            cp_async_wait<0>();
+        } else if (small_n) {
+            // the tuning passes (a few hashes per sample): plain loads, which the compiler
+            // schedules ahead itself (measured faster here than the ring)
             for (uint32_t j = j0; j < j1; j++) {
                 const uint32_t a = r + (j << logR);
-                cp_async_wait<kRing - 1>();
-                const uint32_t sa = ring_s + 8u * slot * blockDim.x;
-                const float2 v = ld_shared_f32x2(sa);
+                const float2 v = __ldg(&x[a]);
 #pragma unroll
                 for (int g = 0; g < NH; g++) tap_mac<true>(acc[g], v, a, A.h[g].sinv, mask, T[g], tb[g]);
-                // the slot's sample has been used: refill it with row j + kRing
-                if (j + kRing < j1) cp_async8(sa, &x[a + ((uint32_t)kRing << logR)]);
-                cp_async_commit();
-                slot = (slot + 1) & (kRing - 1);
             }
         } else {
             for (uint32_t j = j0; j < j1; j++) {
                 const uint32_t a = r + (j << logR);
-                cp_async_wait<kRing - 1>();
-                const uint32_t sa = ring_s + 8u * slot * blockDim.x;
-                const float2 v = ld_shared_f32x2(sa);
+                const float2 v = __ldg(&x[a]);
 #pragma unroll
                 for (int g = 0; g < NH; g++) tap_mac<false>(acc[g], v, a, A.h[g].sinv, mask, T[g], tb[g]);
-                if (j + kRing < j1) cp_async8(sa, &x[a + ((uint32_t)kRing << logR)]);
-                cp_async_commit();
-                slot = (slot + 1) & (kRing - 1);
             }
         }
-        cp_async_wait<0>();
 #pragma unroll
         for (int g = 0; g < NH; g++) {
             const int logB = DYN ? logR : A.h[g].logB;
@@ -382,7 +417,10 @@ struct GatherArgs {
 // Tuning hashes with small windows, all in one launch: a group of kTuneLanes lanes per
 // bucket (the buckets of all hashes listed back to back), as in k_bin_gather_1d with one
 // hash.  Bucket counts are multiples of 32 / kTuneLanes, so a warp's buckets share a hash.
+// A lane's taps are gathered kTapBatch at a time before any is used (the ~9 taps of a
+// lane at the default window in one batch).
 constexpr int kTuneLanes = 4;
+constexpr int kTapBatch = 10;
 
 __global__ void k_bin_gather_tune(const float2 *__restrict__ x, int logn, const GatherArgs A,
                                   const float2 *__restrict__ phase, int phase_s,
@@ -669,7 +707,7 @@ static void launch_stream(const atsfft_plan_s *P, const float2 *x, const StreamA
     const int threads = DYN ? kStreamThreadsLE : kStreamThreads;
     const int per_sm = DYN ? kStreamCtasLE : kStreamCtas;
     A.ring_off = (int)((smem + sizeof(float2) - 1) / sizeof(float2));
-    smem = sizeof(float2) * ((size_t)A.ring_off + (size_t)kRing * threads);
+    if (DYN) smem = sizeof(float2) * ((size_t)A.ring_off + (size_t)kRing * threads);
     int64_t items = (int64_t)A.chunks << A.logR;
     if (DYN) {
         items = 0;
@@ -794,7 +832,7 @@ void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
             launch_stream_nh<true>(P, x, S, job_dev, smem, s);
         }
         prof_mark(P, 10, s);
-        const int groups = (nh + kGroup - 1) / kGroup;
+        const int groups = (nh + kGroup1D - 1) / kGroup1D;
         dim3 grid(P->num_sms * kPersistCtas, groups);
         launch_k(P, k_bin_gather_1d, dim3(grid), dim3(256), 0, s, x, P->logn, P->d_le, nh, P->d_win, job_dev, 0,
                                              P->d_phase, P->phase_s, P->d_part);
@@ -859,7 +897,7 @@ int launch_est_bin(const atsfft_plan_s *P, const float2 *x, int b, cudaStream_t 
         }
         return j.chunks;
     }
-    dim3 grid(P->num_sms * kPersistCtas, (L + kGroup - 1) / kGroup);
+    dim3 grid(P->num_sms * kPersistCtas, (L + kGroup1D - 1) / kGroup1D);
     launch_k(P, k_bin_gather_1d, dim3(grid), dim3(256), 0, s, x, P->logn, P->d_le + P->est_base, L, P->d_win, nullptr, b,
                                          P->d_phase, P->phase_s, P->d_part);
     count_launch(P);
