@@ -17,6 +17,18 @@ namespace atsfft {
 
 constexpr int kGroup = 16;   // hashes accumulated together per thread
 
+// Column form of the location pass (k_bin_cols, below)
+constexpr int kColWarps = 3;        // warps per CTA, each with its own tile
+constexpr int kColTile = 1024;      // samples per tile (8 KB)
+constexpr int kColTileLog = 10;
+constexpr int kColMaxLogD = 8;      // D <= 256: at least four columns per tile
+
+// Does the column form take the location pass at B* = 2^logB?
+__host__ __device__ __forceinline__ bool column_form(int logn, int logB)
+{
+    return logn >= kColTileLog && logn - logB <= kColMaxLogD;
+}
+
 // ---------------------------------------------------------------------------------
 // 1D gather form: a group of kGatherLanes lanes per bucket walks the taps t = b + u B of
 // the window (about 2h / B + 1 of them, ~35 at the default window), each tap computed
@@ -280,6 +292,7 @@ k_bin_stream(const float2 *__restrict__ x, int logn, const StreamArgs A, const J
     if (DYN) {
         if (!job_dev->active || !job_dev->stream) return;
         logR = job_dev->logB;
+        if (column_form(logn, logR)) return;   // k_bin_cols takes this B*
         chunks = job_dev->chunks;
         w = win[logR];
     }
@@ -400,6 +413,100 @@ k_bin_stream(const float2 *__restrict__ x, int logn, const StreamArgs A, const J
     }
 }
 
+// ---------------------------------------------------------------------------------
+// 1D column form of the location pass (B* read on the device, D = n / B* <= 2^kColMaxLogD).
+// The samples of bucket b of a hash all lie in one residue column r = (sigma b + tau) mod B
+// (rows j = a >> log2 B of a = r + j B), and its taps t = b + u B, u_lo <= u <= u_hi, reach
+// rows j0 + (u - u_lo) sigma (mod D): a walk over about 35 of the D rows of that column.
+// Each warp stages a tile of 1024 samples -- 1024 / D whole columns, all D rows -- in
+// shared memory ([row][column], so the lanes of a half-warp, on consecutive columns, hit
+// different banks whatever rows they read), then every (column, hash) of the tile walks
+// its own taps in u order: f_t from exp2 and a reciprocal as in the other forms, R_u by the
+// recurrence R_(u+1) = R_u R_1 from the exact R_(u_lo), the sample from the tile.  Only the
+// taps inside the window are evaluated (the residue stream evaluates every row of every
+// hash, about 64 where ~35 are inside at B* = n / 64), and each bucket sum is complete:
+// the first partial block holds it, further row chunks of the job are written as zeros.
+// Lanes: 2^logLC consecutive columns side by side, the hashes dealt out among the lanes of
+// one column (lpc of them), more columns per lane where the tile is wider than a warp.
+// ---------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(32 * kColWarps, 9) k_bin_cols(const float2 *__restrict__ x, int logn,
+                                                             const HashParam *__restrict__ hashes,
+                                                             const Job *job_dev, const WindowParam *win,
+                                                             const float2 *__restrict__ phase, int phase_s,
+                                                             float2 *__restrict__ part)
+{
+    chain_wait();
+    chain_next();
+    extern __shared__ float2 col_tiles[];
+    if (!job_dev->active || !job_dev->stream) return;
+    const int logB = job_dev->logB, nh = job_dev->nh, chunks = job_dev->chunks;
+    const int logD = logn - logB;
+    if (!column_form(logn, logB)) return;   // the residue-stream kernel takes these
+    const WindowParam w = win[logB];
+    const uint32_t n = 1u << logn, mask = n - 1, B = 1u << logB, Bm = B - 1, Dm = (1u << logD) - 1;
+    const int logTC = kColTileLog - logD;          // columns per tile
+    const int logLC = logTC < 5 ? logTC : 5;       // columns side by side in a warp
+    const int lpc = 32 >> logLC;                   // lanes per column
+    const int cps = 1 << (logTC - logLC);          // columns per lane
+    const int lane = threadIdx.x & 31;
+    const int cl = lane & ((1 << logLC) - 1), sub = lane >> logLC;
+    float2 *tile = col_tiles + (threadIdx.x >> 5) * kColTile;
+    const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);
+    float2 half;
+    sincospif(ldexpf(1.0f, -logn), &half.y, &half.x);
+    const float2 r1 = rot_factor(1, logB, mask, phase, phase_s);   // R_1 = -exp(i pi / D)
+    const float Bf = (float)B;
+    const int64_t tiles = (int64_t)1 << (logn - kColTileLog);
+    const int64_t nw = (int64_t)gridDim.x * kColWarps;
+    for (int64_t tl = (int64_t)blockIdx.x * kColWarps + (threadIdx.x >> 5); tl < tiles; tl += nw) {
+        const uint32_t col0 = (uint32_t)tl << logTC;
+        __syncwarp();   // the previous tile's reads are done
+#pragma unroll 8
+        for (int e = lane; e < kColTile; e += 32)
+            tile[e] = __ldg(&x[col0 + ((uint32_t)e & ((1u << logTC) - 1)) + ((uint32_t)(e >> logTC) << logB)]);
+        __syncwarp();
+        for (int sl = 0; sl < cps; sl++) {
+            const uint32_t c = (uint32_t)cl + ((uint32_t)sl << logLC);
+            const uint32_t r = col0 + c;
+            const uint32_t cbase = tile_s + 8u * c;
+            for (int g = sub; g < nh; g += lpc) {
+                const HashParam hp = hashes[g];
+                const uint32_t sig = hp.sigma[0], tau = hp.tau[0];
+                const uint32_t b = (hp.sinv[0] * (r - tau)) & Bm;
+                float2 z;
+                if (b == 0) {
+                    // only the centre tap G_0 = A D (on sample tau) reaches bucket 0
+                    const float2 v = __ldg(&x[tau & mask]);
+                    z = make_float2(w.cA_D * v.x, w.cA_D * v.y);
+                } else {
+                    const int u_lo = -((w.h + (int)b) >> logB), u_hi = (w.h - (int)b) >> logB;
+                    const int t0 = (int)b + u_lo * (int)B;
+                    uint32_t j = ((sig * (uint32_t)t0 + tau) & mask) >> logB;
+                    const uint32_t dj = sig & Dm;
+                    float tf = (float)t0;
+                    float2 R = rot_factor(u_lo, logB, mask, phase, phase_s);
+                    float2 acc = make_float2(0.f, 0.f);
+                    for (int u = u_lo; u <= u_hi; u++) {
+                        const float2 v = ld_shared_f32x2(cbase + (j << (logTC + 3)));
+                        const float f = fast_exp2(fmaf(-w.k2 * tf, tf, w.log2c)) * fast_rcp(tf);
+                        const float cr = f * R.x, ci = f * R.y;
+                        acc.x = fmaf(cr, v.x, fmaf(-ci, v.y, acc.x));
+                        acc.y = fmaf(cr, v.y, fmaf(ci, v.x, acc.y));
+                        R = cmul(R, r1);
+                        tf += Bf;
+                        j = (j + dj) & Dm;
+                    }
+                    z = cmul(bucket_factor_tab(b, logB, logn, phase, phase_s, half), acc);
+                }
+                float2 *o = part + (int64_t)g * chunks * B + r;
+                o[0] = z;
+                for (int ch = 1; ch < chunks; ch++) o[(int64_t)ch * B] = make_float2(0.f, 0.f);
+            }
+        }
+    }
+}
+
 struct GatherHash {
     uint32_t sig, tau;
     int32_t logB, h;
@@ -417,10 +524,7 @@ struct GatherArgs {
 // Tuning hashes with small windows, all in one launch: a group of kTuneLanes lanes per
 // bucket (the buckets of all hashes listed back to back), as in k_bin_gather_1d with one
 // hash.  Bucket counts are multiples of 32 / kTuneLanes, so a warp's buckets share a hash.
-// A lane's taps are gathered kTapBatch at a time before any is used (the ~9 taps of a
-// lane at the default window in one batch).
 constexpr int kTuneLanes = 4;
-constexpr int kTapBatch = 10;
 
 __global__ void k_bin_gather_tune(const float2 *__restrict__ x, int logn, const GatherArgs A,
                                   const float2 *__restrict__ phase, int phase_s,
@@ -816,20 +920,33 @@ void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
 {
     const int nh = P->nh_le;
     if (P->ndim == 1) {
-        // shared memory for the E_v tables of the smallest B the stream form can take
+        // shared memory for the E_v tables of the smallest B the stream form can take; the
+        // column form takes every stream-form B* with D <= 2^kColMaxLogD
         size_t smem = 16;
+        bool stream_needed = false;
         for (int b = P->b0; b <= P->b_hi; b++)
             if (P->h_tjob[b].stream) {
-                smem = sizeof(float2) * rot_entries((uint32_t)(P->n >> b));
-                break;
+                if (smem == 16) smem = sizeof(float2) * rot_entries((uint32_t)(P->n >> b));
+                if (!column_form(P->logn, b)) stream_needed = true;
             }
-        for (int g0 = 0; g0 < nh; g0 += kMaxStream) {
-            StreamArgs S;
-            memset(&S, 0, sizeof(S));
-            S.nh = nh - g0 < kMaxStream ? nh - g0 : kMaxStream;
-            S.hash_base = g0;
-            for (int g = 0; g < S.nh; g++) S.h[g] = stream_hash(P, P->h_le[g0 + g], -1, 0);
-            launch_stream_nh<true>(P, x, S, job_dev, smem, s);
+        if (stream_needed) {
+            for (int g0 = 0; g0 < nh; g0 += kMaxStream) {
+                StreamArgs S;
+                memset(&S, 0, sizeof(S));
+                S.nh = nh - g0 < kMaxStream ? nh - g0 : kMaxStream;
+                S.hash_base = g0;
+                for (int g = 0; g < S.nh; g++) S.h[g] = stream_hash(P, P->h_le[g0 + g], -1, 0);
+                launch_stream_nh<true>(P, x, S, job_dev, smem, s);
+            }
+        }
+        {
+            const size_t csm = sizeof(float2) * (size_t)kColTile * kColWarps;
+            const int64_t tiles = P->logn < kColTileLog ? 0 : P->n >> kColTileLog;
+            const int64_t grid = (tiles + kColWarps - 1) / kColWarps;
+            cudaFuncSetAttribute((const void *)k_bin_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+            launch_k(P, k_bin_cols, dim3((unsigned)(grid > 0 ? grid : 1)), dim3(32 * kColWarps), csm, s, x,
+                     P->logn, (const HashParam *)P->d_le, job_dev, P->d_win, P->d_phase, P->phase_s, P->d_part);
+            count_launch(P);
         }
         prof_mark(P, 10, s);
         const int groups = (nh + kGroup1D - 1) / kGroup1D;
