@@ -63,7 +63,8 @@ PHASE_KERNELS = {
     "tune1_bin": "k_bin_gather_tune", "tune1_fft": "k_fft_batch x2", "tune1_tail": "k_tune_tail",
     "tune2_bin": "k_bin_stream<3,0>", "tune2_fft": "k_fft_batch x2", "tune2_tail": "k_tune_tail",
     "tune3_bin": "k_bin_stream<1,0>", "tune3_fft": "k_fft_batch x2", "tune3_tail": "k_tune_tail",
-    "le_bin_stream": "k_bin_stream<14,1>", "le_bin_gather": "k_bin_gather_1d",
+    "le_bin_stream": "k_bin_cols (D = n / B* <= 256; else k_bin_stream<14,1>)",
+    "le_bin_gather": "k_bin_gather_1d",
     "le_fft": "k_fft_pass x2", "loc_tail": "k_loc_select + k_loc_votes + k_loc_finish",
 }
 
@@ -317,6 +318,11 @@ def _stream(n, B):
     return 5 * (2 * _window_h(n, B) + 1) >= n and n // B <= 4096
 
 
+def _column_form(n, B):
+    """The location pass at B takes the column form (only its in-window taps)."""
+    return n >= 1024 and n // B <= 256
+
+
 def mufu_pair_peak(stream=None):
     """Sample-hash pairs per second the MUFU pipe allows, measured: atsfft_mufu_probe
     times independent ex2.approx + rcp.approx chains on every SM (two operations per
@@ -335,8 +341,9 @@ def roofline(per_signal, traces, n, stages=3, pair_peak=None, pair_src=None, kep
     """Algorithmic work of each profiled phase per launch, achieved rate, fraction of peak.
 
     Bytes (HBM-bound phases) count each input and output value once; pairs (the
-    residue-stream binning, bound by its two MUFU operations per (sample, hash) pair)
-    count samples x hashes.  The tuning stages split the trials at the last one binned in
+    stream-form binning, bound by its two MUFU operations per (sample, hash) pair) count
+    the in-window taps x hashes in the column form of the location pass, samples x hashes
+    in the residue stream.  The tuning stages split the trials at the last one binned in
     the gather form and (three stages) before the largest; a later stage only counts for
     transforms whose controller walked past the previous stage's last trial (its kernels
     exit at once otherwise)."""
@@ -377,7 +384,8 @@ def roofline(per_signal, traces, n, stages=3, pair_peak=None, pair_src=None, kep
                 model[nm + "_fft"] = ("hbm", sum(fft_bytes(B, _chunks(n, R) * R // B) for B in tB))
                 model[nm + "_tail"] = ("hbm", sum(4 * B + 4 * B for B in tB))
         if _stream(n, Bstar):
-            model["le_bin_stream"] = ("alu", NH * n)
+            taps = min(2 * _window_h(n, Bstar) + 1, n) if _column_form(n, Bstar) else n
+            model["le_bin_stream"] = ("alu", NH * taps)
         else:
             model["le_bin_gather"] = ("hbm", NH * 8 * (2 * _window_h(n, Bstar) + 1) + 8 * NH * Bstar)
         ch = _chunks(n, Bstar) if _stream(n, Bstar) else 1
