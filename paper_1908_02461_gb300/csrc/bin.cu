@@ -456,6 +456,8 @@ __global__ void __launch_bounds__(32 * kColWarps, 9) k_bin_cols(const float2 *__
     float2 half;
     sincospif(ldexpf(1.0f, -logn), &half.y, &half.x);
     const float2 r1 = rot_factor(1, logB, mask, phase, phase_s);   // R_1 = -exp(i pi / D)
+    const int rsh = logTC + 3;   // row -> byte offset in the tile
+    const uint32_t rmask = Dm << rsh;
     const float Bf = (float)B;
     const int64_t tiles = (int64_t)1 << (logn - kColTileLog);
     const int64_t nw = (int64_t)gridDim.x * kColWarps;
@@ -482,20 +484,22 @@ __global__ void __launch_bounds__(32 * kColWarps, 9) k_bin_cols(const float2 *__
                 } else {
                     const int u_lo = -((w.h + (int)b) >> logB), u_hi = (w.h - (int)b) >> logB;
                     const int t0 = (int)b + u_lo * (int)B;
-                    uint32_t j = ((sig * (uint32_t)t0 + tau) & mask) >> logB;
-                    const uint32_t dj = sig & Dm;
+                    // byte offset of the tap's row in the tile, stepping by sigma rows (mod D)
+                    uint32_t jo = (((sig * (uint32_t)t0 + tau) & mask) >> logB) << rsh;
+                    const uint32_t djo = (sig & Dm) << rsh;
                     float tf = (float)t0;
                     float2 R = rot_factor(u_lo, logB, mask, phase, phase_s);
                     float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 2
                     for (int u = u_lo; u <= u_hi; u++) {
-                        const float2 v = ld_shared_f32x2(cbase + (j << (logTC + 3)));
+                        const float2 v = ld_shared_f32x2(cbase + jo);
                         const float f = fast_exp2(fmaf(-w.k2 * tf, tf, w.log2c)) * fast_rcp(tf);
                         const float cr = f * R.x, ci = f * R.y;
                         acc.x = fmaf(cr, v.x, fmaf(-ci, v.y, acc.x));
                         acc.y = fmaf(cr, v.y, fmaf(ci, v.x, acc.y));
                         R = cmul(R, r1);
                         tf += Bf;
-                        j = (j + dj) & Dm;
+                        jo = (jo + djo) & rmask;
                     }
                     z = cmul(bucket_factor_tab(b, logB, logn, phase, phase_s, half), acc);
                 }
