@@ -633,6 +633,8 @@ __global__ void k_taps_2d(int logn, const HashParam *hashes, int nh, const Windo
     }
 }
 
+constexpr uint32_t kRowBatch = 4;   // pixels of a row in flight per thread (2D stream)
+
 // 2D residue stream: thread = (residue pair (r1, r2), chunk of rows j1).  Pixels
 // (r1 + j1 B, r2 + j2 B) all feed bucket (b1, b2) of each hash.  Output
 // part[(chunk * nh + l) * B^2 + r1 * B + r2].
@@ -668,12 +670,36 @@ __global__ void __launch_bounds__(256) k_bin_stream_2d(const float2 *__restrict_
         for (int g = 0; g < kGroup; g++) acc[g] = make_float2(0.f, 0.f);
         for (uint32_t j1 = ch * rows; j1 < (ch + 1) * rows; j1++) {
             const uint32_t a1 = r1 + (j1 << logB);
+            const float2 *xrow = x + (int64_t)a1 * N;
             float2 row[kGroup];
 #pragma unroll
             for (int g = 0; g < kGroup; g++) row[g] = make_float2(0.f, 0.f);
-            for (uint32_t j2 = 0; j2 < D; j2++) {
+            uint32_t j2 = 0;
+            // kRowBatch pixels of the row (and each hash's taps for them) requested before
+            // any is used: one memory round trip per batch instead of per pixel; the sums
+            // keep the pixel order
+            for (; j2 + kRowBatch <= D; j2 += kRowBatch) {
+                float2 v[kRowBatch];
+#pragma unroll
+                for (int q = 0; q < kRowBatch; q++) v[q] = __ldg(&xrow[r2 + ((j2 + q) << logB)]);
+#pragma unroll
+                for (int g = 0; g < kGroup; g++) {
+                    if (g < ng) {
+                        const float2 *tg = taps + ((int64_t)(group0 + g) * 2 + 1) * N + r2;
+                        float2 tp[kRowBatch];
+#pragma unroll
+                        for (int q = 0; q < kRowBatch; q++) tp[q] = __ldg(&tg[(j2 + q) << logB]);
+#pragma unroll
+                        for (int q = 0; q < kRowBatch; q++) {
+                            row[g].x = fmaf(tp[q].x, v[q].x, fmaf(-tp[q].y, v[q].y, row[g].x));
+                            row[g].y = fmaf(tp[q].x, v[q].y, fmaf(tp[q].y, v[q].x, row[g].y));
+                        }
+                    }
+                }
+            }
+            for (; j2 < D; j2++) {
                 const uint32_t a2 = r2 + (j2 << logB);
-                const float2 v = __ldg(&x[(int64_t)a1 * N + a2]);
+                const float2 v = __ldg(&xrow[a2]);
 #pragma unroll
                 for (int g = 0; g < kGroup; g++) {
                     if (g < ng) {

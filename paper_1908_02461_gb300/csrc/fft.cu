@@ -379,10 +379,10 @@ __device__ void fft_tile(const float2 *src, int in_es, int in_bs, int chunks,
     __syncthreads();
 }
 
-// Transforms per CTA: a tile of adjacent ones when they are strided, one otherwise.
+// Transforms per CTA: a tile of adjacent ones (strided, or contiguous rows of a 2D pass),
+// up to kSmallFFT points; one where a hash has a single transform.
 __device__ __forceinline__ int tile_of(const FftShape &f)
 {
-    if (f.in_es == 1 && f.out_es == 1) return 1;
     int T = kSmallFFT >> f.logP;
     if (T > kMaxTile) T = kMaxTile;
     if (T > f.ntrans) T = f.ntrans;
@@ -429,6 +429,8 @@ __global__ void __launch_bounds__(kFftThreads, kPassCtas) k_fft_pass(int ndim, i
     int T = tile_of(f);
     if (f.in_es != 1 || f.out_es != 1)
         while (T > 4 && ((int64_t)T << f.logP) * chunks > kTileLoads) T >>= 1;
+    else
+        while (T > 1 && ((int64_t)T << f.logP) * chunks > kTileLoads) T >>= 1;
     const int64_t tiles = f.ntrans / T;
     const int64_t total = (int64_t)nh * tiles;
     const bool fin_pass = energy && final_pass(ndim, logB, pass);
@@ -548,13 +550,13 @@ void launch_bucket_fft_batch(const atsfft_plan_s *P, int njobs, const int *logB,
             }
             // tiles of adjacent transforms (whole 32-byte sectors: T >= 4 when strided),
             // smaller where the partial chunks make a tile's input large
-            int64_t T = 1;
-            if (strided) {
-                T = (int64_t)kSmallFFT >> logP;
-                if (T > kMaxTile) T = kMaxTile;
-                if (T > ntrans) T = ntrans;
+            int64_t T = (int64_t)kSmallFFT >> logP;
+            if (T > kMaxTile) T = kMaxTile;
+            if (T > ntrans) T = ntrans;
+            {
                 const int64_t ch = pass == 0 ? chunks[i] : 1;
-                while (T > 4 && (T << logP) * ch > kTileLoads) T >>= 1;
+                const int64_t floor_T = strided ? 4 : 1;
+                while (T > floor_T && (T << logP) * ch > kTileLoads) T >>= 1;
             }
             ntrans /= T;
             FftJob &J = Bt.j[Bt.njobs++];

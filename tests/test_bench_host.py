@@ -70,8 +70,14 @@ def test_roofline_model_picks_dominant_phase():
     _, rows_k = bench.roofline({2000: ph}, traces, n, kept={2000: 2100})
     assert rows_k["loc_tail"]["achieved"] == pytest.approx((loc_bytes + 8 * 7 * 2100) / 0.12e-3 / 1e9)
     assert rows["le_bin_stream"]["bound"] == "alu"
-    # 14 hashes x n pairs in 0.06 ms
-    assert rows["le_bin_stream"]["achieved"] == pytest.approx(14 * n / 0.06e-3 / 1e9)
+    # the column form at B* = 2^16 (D = 64): 14 hashes x the window's 2h + 1 taps, with
+    # h = 1152809 at the default alpha = 0.5, tol = 1e-6 (Eqs. (8)-(9)), in 0.06 ms
+    assert rows["le_bin_stream"]["achieved"] == pytest.approx(14 * 2305619 / 0.06e-3 / 1e9)
+    # at B* = 2^18 (D = 16) the window is clamped to n - 1 taps: every sample meets every
+    # hash's window
+    tr16 = {2000: [(16, 0), (1 << 18, 1900)]}
+    _, rows16 = bench.roofline({2000: ph}, tr16, n)
+    assert rows16["le_bin_stream"]["achieved"] == pytest.approx(14 * n / 0.06e-3 / 1e9)
     # the second tuning stage ran (the walk reached B = 2^16, past the gather trials), the
     # third (the largest trial, 2^18) did not
     assert rows["tune2_bin"]["bound"] == "alu"

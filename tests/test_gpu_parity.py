@@ -149,6 +149,24 @@ def test_noisy_1d_mid(A, O, n, k, seed):
     _check_transform(A, O, sig.x, seed, 1)
 
 
+@pytest.mark.parametrize("k,seed,D", [(250, 52, 128), (400, 57, 64), (800, 54, 32), (1500, 56, 16)])
+def test_location_binning_forms(A, O, k, seed, D):
+    """n = 2^20, 40 dB, signals whose B* (the oracle's) puts D = n / B* at 128, 64, 32 and
+    16: the column form of the location pass, whose tile holds 1024 / D whole columns (8,
+    16, 32 and 64: four lanes per column, two, one, and two columns per lane).  The whole
+    transform against the oracle, and B* as the oracle's."""
+    from synth import sparse_signal_1d
+
+    n = 1 << 20
+    sig = sparse_signal_1d(n, k, seed, snr_db=40)
+    plan = A.Plan((n,), params=A.params(), seed=5)
+    plan(_cuda(sig.x), capacity=1 << 16)
+    b_star = plan.last_trace()[-1][0]
+    plan.close()
+    assert n // b_star == D
+    _check_transform(A, O, sig.x, 5, 1)
+
+
 @pytest.mark.parametrize("k", [50, 200, 1000, 2000])
 def test_config2_full_size(A, O, k):
     """n = 2^22, 40 dB, the sweep of the benchmark."""
