@@ -550,6 +550,25 @@ def ncu_case(k):
     plan.close()
 
 
+def ncu_image():
+    """Small fixed 2D case for ncu captures: one plan, the 4096^2 headline image, three
+    transforms, no timing."""
+    import torch
+
+    import paper_1908_02461_gb300 as A
+    from synth import sparse_signal_2d
+
+    A.build()
+    sig = sparse_signal_2d(IMG_N, IMG_K, IMG_SEED, snr_db=IMG_SNR, mag=("loguniform", 0.1, 1.0))
+    x = torch.from_numpy(sig.x).cuda()
+    plan = A.Plan((IMG_N, IMG_N), seed=SEED)
+    for _ in range(3):
+        loc, val, kk, st, cnt = plan(x, capacity=CAPACITY)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_image": IMG_N, "k_star": kk, "status": st, "count": cnt}))
+    plan.close()
+
+
 MIXED_SIGNALS = 512
 MIXED_LOGN = (16, 18, 20, 22)
 MIXED_BRANCHES = 64      # graph branches per batch
@@ -777,9 +796,14 @@ def main():
                          "the gradient of a loss at their supports (instead of the headline)")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="K",
                     help="profiling case for ncu: one plan, the k=K signal, three transforms")
+    ap.add_argument("--ncu-image", action="store_true",
+                    help="profiling case for ncu: one plan, the 4096^2 image, three transforms")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.ncu_image:
+        ncu_image()
         return
     if args.ncu_case:
         ncu_case(args.ncu_case)
