@@ -641,7 +641,7 @@ constexpr uint32_t kRowBatch = 4;   // pixels of a row in flight per thread (2D 
 __global__ void __launch_bounds__(256) k_bin_stream_2d(const float2 *__restrict__ x, int logn,
                                                        int nh, const Job *job_dev,
                                                        int logB_static, int chunks_static,
-                                                       const float2 *__restrict__ taps,
+                                                       const float2 *__restrict__ taps, int64_t tstride,
                                                        float2 *__restrict__ part)
 {
     chain_wait();
@@ -652,6 +652,7 @@ __global__ void __launch_bounds__(256) k_bin_stream_2d(const float2 *__restrict_
         logB = job_dev->logB;
         nh = job_dev->nh;
         chunks = job_dev->chunks;
+        taps += (int64_t)logB * tstride;   // the plan's tables of B* (tstride 0: tables of this exec)
     }
     const int group0 = blockIdx.y * kGroup;
     if (group0 >= nh) return;
@@ -728,7 +729,7 @@ __global__ void __launch_bounds__(256) k_bin_stream_2d(const float2 *__restrict_
 // (u1, u2) pairs; taps from the per-axis tables at the permuted positions.
 __global__ void k_bin_gather_2d(const float2 *__restrict__ x, int logn, const HashParam *hashes,
                                 int nh, const WindowParam *win, const Job *job_dev,
-                                int logB_static, const float2 *__restrict__ taps,
+                                int logB_static, const float2 *__restrict__ taps, int64_t tstride,
                                 float2 *__restrict__ out)
 {
     chain_wait();
@@ -738,6 +739,7 @@ __global__ void k_bin_gather_2d(const float2 *__restrict__ x, int logn, const Ha
         if (!job_dev->active || job_dev->stream) return;
         logB = job_dev->logB;
         nh = job_dev->nh;
+        taps += (int64_t)logB * tstride;
     }
     const uint32_t N = 1u << logn, mask = N - 1, B = 1u << logB;
     const int64_t B2 = (int64_t)B * B;
@@ -931,7 +933,7 @@ void launch_tuning(const atsfft_plan_s *P, const float2 *x, int stage, cudaStrea
         }
         for (int b = P->b0; b <= P->b_hi; b++) {
             launch_bin_2d(P, x, nullptr, P->h_tjob[b], false, P->d_tune + b, b,
-                          P->d_part + P->tpart_off[b], s);
+                          P->d_part + P->tpart_off[b], s, P->d_taps_tune + ((size_t)b << (P->logn + 1)));
             logB[nj] = b;
             chunks[nj] = P->tchunks[b];
             in_off[nj] = P->tpart_off[b];
@@ -988,7 +990,8 @@ void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
         Job jl;
         memset(&jl, 0, sizeof(jl));
         jl.nh = nh;
-        launch_bin_2d(P, x, job_dev, jl, true, P->d_le, 0, P->d_part, s);
+        launch_bin_2d(P, x, job_dev, jl, true, P->d_le, 0, P->d_part, s, P->d_taps_le,
+                      (int64_t)nh << (P->logn + 1));
     }
 }
 
@@ -1051,28 +1054,36 @@ int launch_est_bin(const atsfft_plan_s *P, const float2 *x, int b, cudaStream_t 
     return 1;
 }
 
+// pre_taps: the plan's tap tables of these hashes (static: of B = 2^logB_static; dynamic:
+// those of B = 2^b at pre_taps + b * pre_stride); null: built here into the scratch.
 void launch_bin_2d(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, const Job &job_host,
                    bool dynamic, const HashParam *hashes, int logB_static, float2 *part,
-                   cudaStream_t s)
+                   cudaStream_t s, const float2 *pre_taps, int64_t pre_stride)
 {
     const int persist = P->num_sms * kPersistCtas;
     const int groups = (job_host.nh + kGroup - 1) / kGroup;
     const Job *jd = dynamic ? job_dev : nullptr;
-    float2 *taps = P->d_fft_tmp;   // per-axis tap tables: nh x 2 x N
-    launch_k(P, k_taps_2d, dim3(P->num_sms * 2), dim3(256), 0, s, P->logn, hashes, job_host.nh, P->d_win, jd,
-                                              logB_static, taps);
-    count_launch(P);
+    const float2 *taps = pre_taps;
+    int64_t tstride = dynamic ? pre_stride : 0;
+    if (!taps) {
+        float2 *t = P->d_fft_tmp;   // per-axis tap tables: nh x 2 x N
+        launch_k(P, k_taps_2d, dim3(P->num_sms * 2), dim3(256), 0, s, P->logn, hashes, job_host.nh, P->d_win, jd,
+                                                  logB_static, t);
+        count_launch(P);
+        taps = t;
+        tstride = 0;
+    }
     if (dynamic || job_host.stream) {
         dim3 grid(persist, groups);
         launch_k(P, k_bin_stream_2d, dim3(grid), dim3(256), 0, s, x, P->logn, job_host.nh, jd, logB_static,
-                                             job_host.chunks, taps, part);
+                                             job_host.chunks, taps, tstride, part);
         count_launch(P);
     }
     if (dynamic) prof_mark(P, 10, s);
     if (dynamic || !job_host.stream) {
         dim3 grid(persist, job_host.nh);
         launch_k(P, k_bin_gather_2d, dim3(grid), dim3(256), 0, s, x, P->logn, hashes, job_host.nh, P->d_win, jd,
-                                             logB_static, taps, part);
+                                             logB_static, taps, tstride, part);
         count_launch(P);
     }
 }

@@ -161,6 +161,10 @@ struct atsfft_plan_s {
     float2 *d_phase;       // exp(2 pi i m / n): [2^phase_s] low part, [n >> phase_s] high part
     int phase_s;
     float2 *d_tw;          // [0, 4096): exp(-2 pi i j / 4096); [4096, 8192): exp(-2 pi i j / 2^24)
+    // 2D: per-axis tap tables built at plan time (they depend on the hashes and windows
+    // only): the tuning hash of B = 2^b at d_taps_tune + b * 2N, the nh_le location and
+    // estimation hashes at B = 2^b at d_taps_le + b * nh_le * 2N (layout as k_taps_2d)
+    float2 *d_taps_tune, *d_taps_le;
 
     float2 *d_part;        // binning partial sums (residue order)
     size_t part_elems;
@@ -261,9 +265,11 @@ void launch_le_bin(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, 
 void launch_single_hash(const atsfft_plan_s *P, const float2 *x, int b, const HashParam &hp,
                         const HashParam *hp_dev, float2 *out, cudaStream_t s);
 int launch_est_bin(const atsfft_plan_s *P, const float2 *x, int b, cudaStream_t s);
+__global__ void k_taps_2d(int logn, const HashParam *hashes, int nh, const WindowParam *win,
+                          const Job *job_dev, int logB_static, float2 *taps);
 void launch_bin_2d(const atsfft_plan_s *P, const float2 *x, const Job *job_dev, const Job &job_host,
                    bool dynamic, const HashParam *hashes, int logB_static, float2 *part,
-                   cudaStream_t s);
+                   cudaStream_t s, const float2 *pre_taps = nullptr, int64_t pre_stride = 0);
 
 // fft.cu
 // Bucket FFTs.  energy != nullptr: the final pass also writes |Zhat|^2 (same layout as

@@ -288,7 +288,7 @@ static void plan_free(atsfft_plan_s *P)
                     P->d_z, P->d_fft_tmp, P->d_energy, P->d_stats, P->d_lmax, P->d_lmax_e,
                     P->d_sel, P->d_bucketbits, P->d_kept, P->d_coordbits, P->d_blk, P->d_x32, P->d_f64a,
                     P->d_f64b, P->d_tw64, P->d_wtab64, P->d_state, P->d_tjob, P->d_tstat,
-                    P->d_lstat};
+                    P->d_lstat, P->d_taps_tune, P->d_taps_le};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (P->prof)
@@ -489,6 +489,12 @@ static atsfft_status plan_create(atsfft_plan_t *out, int ndim, const int64_t *sh
         A((void **)&P->d_tw64, sizeof(double2) * (size_t)(((int64_t)1 << P->b_hi) / 2 + 1));
         if (ndim == 2) A((void **)&P->d_wtab64, sizeof(double2) * (size_t)n);   // 2h + 1 <= N - 1
     }
+    if (ndim == 2) {
+        // per-axis tap tables of every B of the range (tuning hash; location and estimation
+        // hashes), built once below
+        A((void **)&P->d_taps_tune, sizeof(float2) * (size_t)(P->b_hi + 1) * 2 * (size_t)n);
+        A((void **)&P->d_taps_le, sizeof(float2) * (size_t)(P->b_hi + 1) * (size_t)nh_le * 2 * (size_t)n);
+    }
     A((void **)&P->d_state, sizeof(ExecState));
     A((void **)&P->d_tjob, sizeof(Job) * kMaxLogB);
     A((void **)&P->d_tstat, sizeof(StatJob) * kMaxLogB);
@@ -555,6 +561,15 @@ static atsfft_status plan_create(atsfft_plan_t *out, int ndim, const int64_t *sh
     }
     if (e == cudaSuccess) e = cudaMemcpy(P->d_tune, P->h_tune, sizeof(P->h_tune), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->d_le, P->h_le, sizeof(P->h_le), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && ndim == 2) {
+        for (int b = P->b0; b <= P->b_hi; b++) {
+            k_taps_2d<<<P->num_sms * 2, 256>>>(P->logn, P->d_tune + b, 1, P->d_win, nullptr, b,
+                                               P->d_taps_tune + (size_t)b * 2 * (size_t)n);
+            k_taps_2d<<<P->num_sms * 2, 256>>>(P->logn, P->d_le, nh_le, P->d_win, nullptr, b,
+                                               P->d_taps_le + (size_t)b * (size_t)nh_le * 2 * (size_t)n);
+        }
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaMemcpy(P->d_tjob, P->h_tjob, sizeof(P->h_tjob), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         // tuning stat jobs: one per B of the range, spectra and energies at tz_off[b]
