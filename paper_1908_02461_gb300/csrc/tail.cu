@@ -1678,6 +1678,10 @@ __global__ void __launch_bounds__(256) k_loc_finish(const LocTailArgs A)
             const int64_t k = base + threadIdx.x / grp;
             const bool valid = k < K;
             const uint32_t coord = valid ? A.kept[k] : 0u;
+            // the estimates need only the coordinate: their loads go out before the rank
+            // (a coordinate ranked beyond the capacity discards its estimate)
+            float2 v = make_float2(0.f, 0.f);
+            if (!A.skip_est && valid && gl < A.L_est) v = estimate_term(coord, A, b, gl);
             uint32_t r = 0;
             for (int64_t c0 = 0; c0 < K; c0 += kChunk) {
                 const int64_t c1 = min(c0 + (int64_t)kChunk, K);
@@ -1715,8 +1719,7 @@ __global__ void __launch_bounds__(256) k_loc_finish(const LocTailArgs A)
             for (int o = 1; o < 32; o <<= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
             const bool inside = valid && r < A.capacity;
             if (!A.skip_est) {
-                float2 v = make_float2(0.f, 0.f);
-                if (inside && gl < A.L_est) v = estimate_term(coord, A, b, gl);
+                if (!inside) v = make_float2(0.f, 0.f);
                 group_median(v, A.L_est, grp, inside, &A.val[inside ? r : 0],
                              A.msel && inside ? A.msel + 2 * (int64_t)r : nullptr);
             }
