@@ -22,6 +22,7 @@ constexpr int kColWarps = 3;        // warps per CTA, each with its own tile
 constexpr int kColTile = 1024;      // samples per tile (8 KB)
 constexpr int kColTileLog = 10;
 constexpr int kColMaxLogD = 8;      // D <= 256: at least four columns per tile
+constexpr int kColCtas = 9;         // CTAs per SM: 9 x 24 KB of tiles, all 4096 tiles of n = 2^22 in one wave
 
 // Does the column form take the location pass at B* = 2^logB?
 __host__ __device__ __forceinline__ bool column_form(int logn, int logB)
@@ -430,7 +431,7 @@ k_bin_stream(const float2 *__restrict__ x, int logn, const StreamArgs A, const J
 // one column (lpc of them), more columns per lane where the tile is wider than a warp.
 // ---------------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(32 * kColWarps, 9) k_bin_cols(const float2 *__restrict__ x, int logn,
+__global__ void __launch_bounds__(32 * kColWarps, kColCtas) k_bin_cols(const float2 *__restrict__ x, int logn,
                                                              const HashParam *__restrict__ hashes,
                                                              const Job *job_dev, const WindowParam *win,
                                                              const float2 *__restrict__ phase, int phase_s,
